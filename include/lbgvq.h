@@ -1,0 +1,174 @@
+/*
+ * lbgvq.h -- C ABI of the GB300 (sm_103a) LBG vector-quantizer library.
+ *
+ * The library designs a vector-quantization codebook with the LBG algorithm
+ * as described by Annaji & Rao, "Parallelization of the LBG Vector
+ * Quantization Algorithm for Shared Memory Systems":
+ *   - Sec. 2.2 "LBG Algorithm": minimum-distortion partition, distortion,
+ *     relative stop test, replacement of each codevector by its cell centroid;
+ *   - Sec. 3.2 / Algorithm 1: initial codebook = centroid of the training set
+ *     (Table 1), codebook splitting [c + delta], [c - delta], cell allocation
+ *     (nearest codevector per training vector = the cell table), integration
+ *     of distortions, updation (cell centroids);
+ *   - Abstract / Sec. 1: replacement of arbitrary data by the nearest
+ *     codevector (encoding).
+ * Every step runs in CUDA kernels of this library on the calling device.
+ *
+ * Conventions for every entry point
+ *   - Matrices are row-major and contiguous: X is [M x L] (M vectors of
+ *     dimension L, the paper's M x k training matrix), a codebook is
+ *     [N x L] float32.
+ *   - Array arguments may be DEVICE pointers (cudaMalloc / managed memory)
+ *     or HOST pointers (pageable or pinned).  Host arrays are copied to and
+ *     from device scratch inside the call; device arrays are used in place.
+ *     Scalars returned through `double *D` are always host memory.
+ *   - The caller owns every array it passes.  The library owns only its
+ *     internal device scratch, cached per device and released by
+ *     lbg_release_workspace().  Calls on one device are serialised by an
+ *     internal lock; each call synchronises its stream before it returns.
+ *   - Work is issued on opts->stream (a cudaStream_t; NULL = the legacy
+ *     default stream) of the current CUDA device.
+ *   - Distance is the squared Euclidean distance; ties go to the lowest
+ *     codevector index.  D is the SUM over vectors of the minimum distance
+ *     (the paper's total distortion TD; the mean is D / M).
+ *   - Arguments are validated before any device work: invalid arguments
+ *     return an error and leave outputs untouched.  Device-side failures
+ *     (non-finite input, a wait that timed out) are reported by status.
+ *
+ * Limits: 1 <= L <= LBG_MAX_DIM, 1 <= N <= LBG_MAX_CODEBOOK, N a power of 2
+ * for lbg_train (Sec. 2.2: codebook sizes are powers of 2), M < 2^31.
+ */
+#ifndef LBGVQ_H
+#define LBGVQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBG_MAX_DIM 128
+#define LBG_MAX_CODEBOOK 8192
+
+typedef enum lbg_status {
+    LBG_OK = 0,
+    LBG_WARN_MAXPASS = 1,     /* a stage hit max_passes before the stop test held */
+    LBG_ERR_ARG = -1,         /* invalid size, pointer or parameter */
+    LBG_ERR_NOT_POW2 = -2,    /* N (or n_init) is not a power of 2 */
+    LBG_ERR_NONFINITE = -3,   /* NaN or Inf in X or in a codebook */
+    LBG_ERR_CUDA = -4,        /* a CUDA runtime call failed */
+    LBG_ERR_NOMEM = -5,       /* device scratch could not be allocated */
+    LBG_ERR_TIMEOUT = -6,     /* a bounded device wait gave up */
+    LBG_ERR_UNSUPPORTED = -7  /* option not available on this device/build */
+} lbg_status;
+
+typedef enum lbg_precision {
+    LBG_PREC_FP32 = 0         /* FP32 FFMA distances, certified; exact FP32 fallback */
+} lbg_precision;
+
+/* Actions a pass of lbg_train can end with (lbg_pass_record.action). */
+enum { LBG_ACT_UPDATE = 0, LBG_ACT_SPLIT = 1, LBG_ACT_FINISH = 2 };
+
+/* Indices into lbg_opts.phase_ms. */
+enum {
+    LBG_PHASE_PREP = 0,    /* codebook preparation (centring, layout) */
+    LBG_PHASE_ASSIGN = 1,  /* nearest-codevector kernel */
+    LBG_PHASE_EXACT = 2,   /* exact re-scoring of uncertified rows */
+    LBG_PHASE_UPDATE = 3,  /* cell table + centroid update (incl. distortion) */
+    LBG_PHASE_TOTAL = 4,   /* whole call on the device (excl. host copies) */
+    LBG_NUM_PHASES = 5
+};
+
+/* One pass of lbg_train (one cell allocation of Algorithm 1). */
+typedef struct lbg_pass_record {
+    int32_t stage_n;   /* codebook size of the stage */
+    int32_t pass;      /* pass index within the stage, from 0 */
+    int32_t action;    /* LBG_ACT_* taken after the stop test */
+    int32_t n_exact;   /* rows re-scored exactly by the fallback kernel */
+    double D;          /* total distortion of the pass */
+} lbg_pass_record;
+
+typedef struct lbg_opts {
+    int32_t precision;          /* lbg_precision; default LBG_PREC_FP32 */
+    int32_t max_passes;         /* per stage (lbg_train); <= 0 means 1000 */
+    void *stream;               /* cudaStream_t; NULL = legacy default stream */
+    lbg_pass_record *records;   /* host array for lbg_train's pass trace, or NULL */
+    int32_t max_records;        /* capacity of records */
+    int32_t *n_records;         /* host: number of passes run (may exceed capacity), or NULL */
+    float *phase_ms;            /* host float[LBG_NUM_PHASES]: device time per phase, or NULL */
+    int32_t *n_exact;           /* host: rows re-scored exactly (step / encode), or NULL */
+} lbg_opts;
+
+/* Fill *opts with the defaults (FP32, 1000 passes, default stream, no trace). */
+void lbg_opts_init(lbg_opts *opts);
+
+/*
+ * lbg_train -- design an N-level codebook (Sec. 2.2 + Algorithm 1).
+ *
+ *   X        [M x L] training vectors (read only).
+ *   N        final codebook size, a power of 2.
+ *   delta    split offset >= 0: every centroid c becomes c + delta (child 2i)
+ *            and c - delta (child 2i + 1), added to every component
+ *            (Sec. 3.2 "Codebook Splitting").
+ *   theta    stop threshold >= 0: a stage ends when D == 0 or
+ *            (D_prev - D) / D <= theta, D_prev = +inf at the start of each
+ *            stage (Sec. 2.2 step 2).
+ *   C        [N x L] out: final codebook.  If n_init > 0 its first n_init
+ *            rows are read first as the starting codebook (resume).
+ *   n_init   0: start from the centroid of X (Table 1); else a power of 2
+ *            <= N: resume from the n_init-entry codebook held in C.
+ *   assign   [M] out, nullable: the cell table of the final codebook.
+ *   D        host out, nullable: total distortion of (C, assign).
+ * A finished stage keeps the codebook that produced its D (before any
+ * update), so (C, assign, D) are mutually consistent.  An empty cell keeps
+ * its codevector.  Returns LBG_OK, LBG_WARN_MAXPASS (some stage was cut at
+ * max_passes and training went on), or an error.
+ */
+lbg_status lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double delta,
+                     double theta, float *C, int32_t n_init, int32_t *assign, double *D,
+                     const lbg_opts *opts);
+
+/*
+ * lbg_lloyd_step -- one Lloyd pass from a given codebook: cell allocation,
+ * integration of distortions and updation (Algorithm 1), without stop test
+ * or split.
+ *
+ *   X      [M x L] vectors; M may be 0 (every cell is then empty).
+ *   C_in   [N x L] codebook used for the allocation (N >= 1, any value).
+ *   C_out  [N x L] out: centroid of every cell; empty cells copy C_in.
+ *          May alias C_in.
+ *   assign [M] out, nullable: nearest codevector of every row under C_in.
+ *   D      host out, nullable: sum of the minimum distances under C_in.
+ */
+lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N,
+                          const float *C_in, float *C_out, int32_t *assign, double *D,
+                          const lbg_opts *opts);
+
+/*
+ * vq_encode -- replace arbitrary vectors by their nearest codevector
+ * (Abstract; Sec. 1).
+ *
+ *   X     [M x L] vectors to encode; M may be 0.
+ *   C     [N x L] codebook (N >= 1).
+ *   idx   [M] out: index of the nearest codevector.
+ *   Xhat  [M x L] out, nullable: the decoded vectors C[idx[m]].
+ *   D     host out, nullable: sum of the squared distances.
+ */
+lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32_t N,
+                     int32_t *idx, float *Xhat, double *D, const lbg_opts *opts);
+
+/* Human-readable text of a status code (static storage). */
+const char *lbg_status_string(lbg_status s);
+
+/* Free the cached device scratch of the current device. */
+lbg_status lbg_release_workspace(void);
+
+/* Library ABI version (this header: 1). */
+int32_t lbg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBGVQ_H */

@@ -76,8 +76,8 @@ def _load():
         lib.oracle_distortion_fixed.argtypes = [P, i64, i32, P, P]
         lib.oracle_distortion_fixed.restype = f64
         lib.oracle_grad.argtypes = [P, i64, i32, P, i32, P, P, P]
-        lib.oracle_lbg_train.argtypes = [P, i64, i32, i32, f64, f64, i32, i32, P, P, P,
-                                         P, P, P, i32, P]
+        lib.oracle_lbg_train.argtypes = [P, i64, i32, i32, f64, f64, i32, i32, P, i32, P, P,
+                                         P, P, P, P, i32, P]
         _lib = lib
         return lib
 
@@ -217,9 +217,12 @@ class Train:
 
 
 def lbg_train(X, N: int, delta: float, theta: float, max_passes: int = 1000,
-              nthreads: int = 0, trace_cap: int = 100000) -> Train:
-    """The whole LBG design from the centroid up to N codevectors."""
+              nthreads: int = 0, trace_cap: int = 100000, C_init=None) -> Train:
+    """The whole LBG design up to N codevectors, from the centroid of X or,
+    if C_init ([n_init, L]) is given, from that initial alphabet (Sec. 2.2)."""
     X = _x(X)
+    Ci = None if C_init is None else _c(C_init)
+    n_init = 0 if Ci is None else Ci.shape[0]
     M, L = X.shape
     C = np.empty((N, L), np.float64)
     a = np.empty(M, np.int32)
@@ -229,7 +232,8 @@ def lbg_train(X, N: int, delta: float, theta: float, max_passes: int = 1000,
     rD = np.empty(trace_cap, np.float64)
     cnt = ctypes.c_int32()
     rc = _load().oracle_lbg_train(_ptr(X), M, L, int(N), float(delta), float(theta),
-                                  int(max_passes), int(nthreads), _ptr(C), _ptr(a),
+                                  int(max_passes), int(nthreads), _ptr(Ci), n_init, _ptr(C),
+                                  _ptr(a),
                                   ctypes.byref(D), _ptr(rn), _ptr(rp), _ptr(rD), trace_cap,
                                   ctypes.byref(cnt))
     _check(rc, "lbg_train")

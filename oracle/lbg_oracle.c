@@ -265,7 +265,8 @@ static int is_pow2(int32_t n) { return n > 0 && (n & (n - 1)) == 0; }
 
 /* The whole LBG design (Algorithm 1 with the Sec. 2.2 iteration inside each
  * stage):
- *   C <- [centroid(X)]; n <- 1
+ *   C <- [centroid(X)]; n <- 1   (or, if n_init > 0, C <- C_init, n <- n_init:
+ *                                 the initial alphabet A_0 of Sec. 2.2)
  *   stage: D_prev <- +inf (R3)
  *     pass: cell allocation -> a, e;  D <- sum e
  *           if D == 0 or (D_prev - D)/D <= theta: stage done (R1, R2, R4)
@@ -277,7 +278,8 @@ static int is_pow2(int32_t n) { return n > 0 && (n & (n - 1)) == 0; }
  * rec_cap records; rec_count receives the number of passes run (which may
  * exceed rec_cap).  Returns 0, 1 (WARN_MAXPASS) or a negative error. */
 int oracle_lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double delta,
-                     double theta, int32_t max_passes, int32_t nthreads, double *C_out,
+                     double theta, int32_t max_passes, int32_t nthreads,
+                     const double *C_init, int32_t n_init, double *C_out,
                      int32_t *a_out, double *D_out, int32_t *rec_n, int32_t *rec_pass,
                      double *rec_D, int32_t rec_cap, int32_t *rec_count)
 {
@@ -285,6 +287,8 @@ int oracle_lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double del
         return ORACLE_ERR_ARG;
     if (!(delta >= 0.0) || !(theta >= 0.0)) return ORACLE_ERR_ARG;
     if (!is_pow2(N)) return ORACLE_ERR_NOT_POW2;
+    if (n_init < 0 || n_init > N || (n_init > 0 && !C_init)) return ORACLE_ERR_ARG;
+    if (n_init > 0 && !is_pow2(n_init)) return ORACLE_ERR_NOT_POW2;
 
     double *C = (double *)malloc((size_t)N * L * sizeof(double));
     double *Cn = (double *)malloc((size_t)N * L * sizeof(double));
@@ -298,7 +302,12 @@ int oracle_lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double del
     int status = ORACLE_OK;
     int32_t n = 1, total = 0;
     double D = 0.0;
-    oracle_mean(X, M, L, C);
+    if (n_init > 0) {
+        n = n_init;
+        memcpy(C, C_init, (size_t)n * L * sizeof(double));
+    } else {
+        oracle_mean(X, M, L, C);
+    }
     for (;;) {
         double D_prev = INFINITY;
         for (int32_t pass = 0;; ++pass) {

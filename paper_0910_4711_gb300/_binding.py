@@ -1,0 +1,266 @@
+"""ctypes binding of ``_lib/liblbgvq.so`` (the C ABI of ``include/lbgvq.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of the library.  Arrays may be torch tensors (CUDA or CPU) or numpy
+arrays; CUDA tensors are passed as device pointers on torch's current
+stream, CPU tensors and numpy arrays as host pointers (the library copies
+them to the device and back inside the call).  If the library is missing or
+cannot be loaded, every call raises ``RuntimeError``: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblbgvq.so")
+
+LBG_OK, LBG_WARN_MAXPASS = 0, 1
+STATUS = {0: "LBG_OK", 1: "LBG_WARN_MAXPASS", -1: "LBG_ERR_ARG", -2: "LBG_ERR_NOT_POW2",
+          -3: "LBG_ERR_NONFINITE", -4: "LBG_ERR_CUDA", -5: "LBG_ERR_NOMEM", -6: "LBG_ERR_TIMEOUT",
+          -7: "LBG_ERR_UNSUPPORTED"}
+PHASES = ("prep", "assign", "exact", "update", "total")
+ACTIONS = ("update", "split", "finish")
+EXPORTS = ("lbg_opts_init", "lbg_train", "lbg_lloyd_step", "vq_encode", "lbg_status_string",
+           "lbg_release_workspace", "lbg_version")
+
+
+class LBGError(RuntimeError):
+    def __init__(self, status: int, text: str):
+        super().__init__(f"{STATUS.get(status, status)}: {text}")
+        self.status = status
+
+
+class PassRecord(ctypes.Structure):
+    _fields_ = [("stage_n", ctypes.c_int32), ("pass_", ctypes.c_int32), ("action", ctypes.c_int32),
+                ("n_exact", ctypes.c_int32), ("D", ctypes.c_double)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("max_passes", ctypes.c_int32),
+                ("stream", ctypes.c_void_p), ("records", ctypes.POINTER(PassRecord)),
+                ("max_records", ctypes.c_int32), ("n_records", ctypes.POINTER(ctypes.c_int32)),
+                ("phase_ms", ctypes.POINTER(ctypes.c_float)),
+                ("n_exact", ctypes.POINTER(ctypes.c_int32))]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded library (raises RuntimeError if it is not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"liblbgvq is not built ({LIB_PATH} missing); run "
+                               "paper_0910_4711_gb300.build.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i64, i32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        L.lbg_opts_init.argtypes = [ctypes.POINTER(Opts)]
+        L.lbg_opts_init.restype = None
+        L.lbg_train.argtypes = [P, i64, i32, i32, f64, f64, P, i32, P, P, ctypes.POINTER(Opts)]
+        L.lbg_train.restype = ctypes.c_int
+        L.lbg_lloyd_step.argtypes = [P, i64, i32, i32, P, P, P, P, ctypes.POINTER(Opts)]
+        L.lbg_lloyd_step.restype = ctypes.c_int
+        L.vq_encode.argtypes = [P, i64, i32, P, i32, P, P, P, ctypes.POINTER(Opts)]
+        L.vq_encode.restype = ctypes.c_int
+        L.lbg_status_string.argtypes = [ctypes.c_int]
+        L.lbg_status_string.restype = ctypes.c_char_p
+        L.lbg_release_workspace.argtypes = []
+        L.lbg_release_workspace.restype = ctypes.c_int
+        L.lbg_version.argtypes = []
+        L.lbg_version.restype = ctypes.c_int32
+        _lib = L
+        return L
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise LBGError(rc, lib().lbg_status_string(rc).decode())
+    return rc
+
+
+# ------------------------------------------------------------ marshalling
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _prep(a, dtype: str, name: str):
+    """Return (array object kept alive, pointer, is_cuda)."""
+    if a is None:
+        return None, None, False
+    if _is_torch(a):
+        import torch
+        want = {"f32": torch.float32, "i32": torch.int32}[dtype]
+        if a.dtype != want:
+            raise TypeError(f"{name} must be {want}, got {a.dtype}")
+        if not a.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        return a, a.data_ptr(), a.is_cuda
+    want = {"f32": np.float32, "i32": np.int32}[dtype]
+    if not isinstance(a, np.ndarray) or a.dtype != want or not a.flags.c_contiguous:
+        raise TypeError(f"{name} must be a C-contiguous numpy {want.__name__} array or torch tensor")
+    return a, a.ctypes.data, False
+
+
+def _empty_like_src(src, shape, dtype: str):
+    if _is_torch(src):
+        import torch
+        t = {"f32": torch.float32, "i32": torch.int32}[dtype]
+        return torch.empty(shape, dtype=t, device=src.device)
+    return np.empty(shape, dtype={"f32": np.float32, "i32": np.int32}[dtype])
+
+
+def _opts(cuda_ref, max_passes=1000, records=0, phase=False, stream=None):
+    o = Opts()
+    lib().lbg_opts_init(ctypes.byref(o))
+    o.max_passes = int(max_passes)
+    keep = {}
+    if stream is not None:
+        o.stream = ctypes.c_void_p(int(stream))
+    elif cuda_ref is not None:
+        import torch
+        o.stream = ctypes.c_void_p(torch.cuda.current_stream(cuda_ref.device).cuda_stream)
+    if records:
+        keep["rec"] = (PassRecord * records)()
+        keep["nrec"] = ctypes.c_int32(0)
+        o.records = ctypes.cast(keep["rec"], ctypes.POINTER(PassRecord))
+        o.max_records = records
+        o.n_records = ctypes.pointer(keep["nrec"])
+    if phase:
+        keep["ph"] = (ctypes.c_float * 5)()
+        o.phase_ms = ctypes.cast(keep["ph"], ctypes.POINTER(ctypes.c_float))
+    keep["nex"] = ctypes.c_int32(0)
+    o.n_exact = ctypes.pointer(keep["nex"])
+    return o, keep
+
+
+def _cuda_ref(*arrays):
+    for a in arrays:
+        if a is not None and _is_torch(a) and a.is_cuda:
+            return a
+    return None
+
+
+def _phases(keep):
+    if "ph" not in keep:
+        return None
+    return {k: float(v) for k, v in zip(PHASES, keep["ph"])}
+
+
+@dataclass
+class TrainResult:
+    status: int
+    C: object
+    assign: object
+    D: float
+    records: list
+    n_passes: int
+    phase_ms: dict | None
+
+    def passes_per_stage(self):
+        out = []
+        for r in self.records:
+            if r["pass"] == 0:
+                out.append(0)
+            out[-1] += 1
+        return out
+
+
+@dataclass
+class StepResult:
+    status: int
+    C: object
+    assign: object
+    D: float
+    n_exact: int
+    phase_ms: dict | None
+
+
+@dataclass
+class EncodeResult:
+    status: int
+    idx: object
+    Xhat: object
+    D: float
+    n_exact: int
+    phase_ms: dict | None
+
+
+# ------------------------------------------------------------ entry points
+def lbg_train(X, N: int, delta: float = 0.01, theta: float = 1e-3, C_init=None,
+              max_passes: int = 1000, trace: int = 4096, phase_ms: bool = False, C_out=None,
+              assign_out=None, stream=None) -> TrainResult:
+    """Design an N-entry codebook from X [M, L] (see lbg_train in lbgvq.h)."""
+    Xo, xp, _ = _prep(X, "f32", "X")
+    M, L = int(X.shape[0]), int(X.shape[1])
+    C = C_out if C_out is not None else _empty_like_src(X, (N, L), "f32")
+    n_init = 0
+    if C_init is not None:
+        n_init = int(C_init.shape[0])
+        C[:n_init] = C_init
+    A = assign_out if assign_out is not None else _empty_like_src(X, (M,), "i32")
+    Co, cp, _ = _prep(C, "f32", "C")
+    Ao, ap, _ = _prep(A, "i32", "assign")
+    o, keep = _opts(_cuda_ref(X, C, A), max_passes, trace, phase_ms, stream)
+    D = ctypes.c_double(0.0)
+    rc = _check(lib().lbg_train(xp, M, L, int(N), float(delta), float(theta), cp, n_init, ap,
+                                ctypes.byref(D), ctypes.byref(o)))
+    recs = []
+    if trace:
+        n = min(keep["nrec"].value, trace)
+        for r in keep["rec"][:n]:
+            recs.append({"stage_n": r.stage_n, "pass": r.pass_, "action": ACTIONS[r.action],
+                         "n_exact": r.n_exact, "D": r.D})
+    return TrainResult(rc, C, A, D.value, recs, keep["nrec"].value if trace else -1, _phases(keep))
+
+
+def lbg_lloyd_step(X, C_in, C_out=None, assign_out=None, phase_ms: bool = False,
+                   stream=None) -> StepResult:
+    """One Lloyd pass from C_in (see lbg_lloyd_step in lbgvq.h)."""
+    Xo, xp, _ = _prep(X, "f32", "X")
+    M, L = int(X.shape[0]), int(X.shape[1])
+    N = int(C_in.shape[0])
+    Ci, cip, _ = _prep(C_in, "f32", "C_in")
+    Co = C_out if C_out is not None else _empty_like_src(C_in, (N, L), "f32")
+    Co, cop, _ = _prep(Co, "f32", "C_out")
+    A = assign_out if assign_out is not None else _empty_like_src(X, (M,), "i32")
+    A, ap, _ = _prep(A, "i32", "assign")
+    o, keep = _opts(_cuda_ref(X, C_in, Co, A), stream=stream, phase=phase_ms)
+    D = ctypes.c_double(0.0)
+    rc = _check(lib().lbg_lloyd_step(xp, M, L, N, cip, cop, ap, ctypes.byref(D), ctypes.byref(o)))
+    return StepResult(rc, Co, A, D.value, keep["nex"].value, _phases(keep))
+
+
+def vq_encode(X, C, decode: bool = False, with_distortion: bool = True, phase_ms: bool = False,
+              idx_out=None, stream=None) -> EncodeResult:
+    """Nearest codevector of every row of X (see vq_encode in lbgvq.h)."""
+    Xo, xp, _ = _prep(X, "f32", "X")
+    M, L = int(X.shape[0]), int(X.shape[1])
+    N = int(C.shape[0])
+    Co, cp, _ = _prep(C, "f32", "C")
+    I = idx_out if idx_out is not None else _empty_like_src(X, (M,), "i32")
+    I, ip, _ = _prep(I, "i32", "idx")
+    H = _empty_like_src(X, (M, L), "f32") if decode else None
+    H, hp, _ = _prep(H, "f32", "Xhat")
+    o, keep = _opts(_cuda_ref(X, C, I), stream=stream, phase=phase_ms)
+    D = ctypes.c_double(0.0)
+    rc = _check(lib().vq_encode(xp, M, L, cp, N, ip, hp, ctypes.byref(D) if with_distortion else None,
+                                ctypes.byref(o)))
+    return EncodeResult(rc, I, H, D.value if with_distortion else float("nan"), keep["nex"].value,
+                        _phases(keep))
+
+
+def release_workspace() -> None:
+    _check(lib().lbg_release_workspace())
+
+
+def version() -> int:
+    return int(lib().lbg_version())

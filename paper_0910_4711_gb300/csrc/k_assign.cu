@@ -1,0 +1,495 @@
+// k_assign.cu -- cell allocation (nearest codevector) kernels.
+//
+// Paper: Algorithm 1 "Cell Allocation" and Sec. 2.2 step 1 (minimum
+// distortion partition): every training vector gets the index of the
+// codevector at the smallest squared Euclidean distance (ties: lowest
+// index) and its distance is added to the distortion.  The same kernels
+// serve encoding (Abstract: replacement by the nearest codevector).
+//
+// GB300 design.  The search is the contraction -2 x.c over L plus the
+// per-codevector norm, done with FP32 FFMA:
+//   * a CTA owns BM = 128 rows of X (centred by mu, staged once in shared
+//     memory, k-major) and streams the whole prepared codebook through two
+//     shared-memory buffers of BN = 128 codevectors, each filled by one TMA
+//     bulk copy (cp.async.bulk + mbarrier, bounded waits);
+//   * every thread keeps an 8 x 8 register tile of accumulators whose FMA
+//     chain starts at a per-codevector constant, so the tile needs no
+//     epilogue arithmetic besides a running top-2 (3 FMNMX per distance);
+//   * the index of the minimum is recovered after the sweep by recomputing
+//     the one winning 8-codevector group bit-identically;
+//   * a rigorous rounding-error bound certifies the minimum; rows it cannot
+//     certify (about 0.2% on image blocks) are re-scored exactly in FP32
+//     direct form by k_assign_exact.
+//
+// Certification.  Let x~ = fl(x - mu), c~_n = fl(c_n - mu), u = 2^-24 and
+//   k_n = 2 (L+2) u ||c~_n||^2,  R = (L+2) u ||x~||^2.
+// The chain computes v_n ~ f_n - k_n with f_n = ||c~_n||^2 - 2 x~.c~_n and
+// |v_n - (f_n - k_n)| <= (L+1)(1+Lu) u (||c~_n||^2 + 2||x~|| ||c~_n||)
+//                     <= k_n + R          (2ab <= a^2 + b^2),
+// hence v_n - R <= f_n <= v_n + 2 k_n + R.  If V1 = v_i1 is the minimum and V2
+// the second smallest, V2 - V1 > 2R + 2k_i1 proves f_n > f_i1 for all n != i1,
+// i.e. ||x~ - c~_n|| > ||x~ - c~_i1||.  Centring moves each distance
+// ||x - c_n|| by at most eta = u (||x~|| + max ||c~||); the extra term
+// 4 eta (g1 + eta), g1 >= ||x~ - c~_i1||, keeps the proof valid for the
+// original x and c_n.  A certified i1 is therefore the exact argmin.
+#include "lbg_internal.cuh"
+
+#include <math.h>
+
+namespace lbg {
+namespace {
+
+constexpr float U32 = 5.9604644775390625e-8f;   // 2^-24
+constexpr float SLOP = 1.0000305175781250f;     // 1 + 2^-15, covers FP32 evaluation of bounds
+constexpr int EX_ROWS = 4;                      // flagged rows per warp in k_assign_exact
+constexpr int EX_WARPS = 8;
+
+__device__ __forceinline__ int cur_n(const int32_t *n_dev, int n_host)
+{
+    return n_dev ? *n_dev : n_host;
+}
+
+// mu[l] = mean over the N codevectors (FP32 partials, FP64 final); used as
+// the centring vector of lbg_lloyd_step / vq_encode.  One CTA of 1024.
+__global__ void __launch_bounds__(1024) k_codebook_mean(const float *__restrict__ C, int N, int L,
+                                                        float *__restrict__ mu)
+{
+    __shared__ float part[1024];
+    const int per = 1024 / L;
+    const int t = threadIdx.x;
+    const int l = t % L, r = t / L;
+    float s = 0.f;
+    if (r < per)
+        for (int n = r; n < N; n += per) s += C[(size_t)n * L + l];
+    part[t] = s;
+    __syncthreads();
+    if (t < L) {
+        double acc = 0.0;
+        for (int q = 0; q < per; ++q) acc += part[q * L + t];
+        mu[t] = (float)(acc / (double)N);
+    }
+}
+
+// Prepared codebook, chunk-major: chunk k holds (Lp + 1) x BN floats; row 0
+// is the chain start s0_n = fl(||c~_n||^2 - k_n) (+inf for padding), rows
+// 1..Lp are -2 c~_{n,l} (0 for l >= L or padding).  Also writes k_n,
+// the original codebook transposed CT[l][n] (stride NP) for the exact
+// fallback, max ||c~_n|| into st->cmax_bits, and flags non-finite entries.
+__global__ void k_prep(const float *__restrict__ C, const int32_t *n_dev, int n_host, int L, int Lp,
+                       const float *__restrict__ mu, float *__restrict__ Cp, float *__restrict__ kn,
+                       float *__restrict__ CT, int NP, DevState *st)
+{
+    if (st->finished) return;
+    const int N = cur_n(n_dev, n_host);
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int npad = round_up(N, BN);
+    if (n >= npad) return;
+    const int chunk = n / BN, j = n % BN;
+    float *blk = Cp + (size_t)chunk * (Lp + 1) * BN;
+    if (n < N) {
+        double sq = 0.0;
+        bool finite = true;
+        for (int l = 0; l < L; ++l) {
+            const float c = C[(size_t)n * L + l];
+            finite = finite && isfinite(c);
+            const float ct = c - mu[l];
+            blk[(size_t)(1 + l) * BN + j] = -2.0f * ct;
+            CT[(size_t)l * NP + n] = c;
+            sq += (double)ct * (double)ct;
+        }
+        for (int l = L; l < Lp; ++l) {
+            blk[(size_t)(1 + l) * BN + j] = 0.f;
+            CT[(size_t)l * NP + n] = 0.f;
+        }
+        if (!finite) flag_error(st, ERR_NONFINITE);
+        const double k = 2.0 * (double)(L + 2) * 5.9604644775390625e-8 * sq;
+        const float kf = __double2float_ru(k);
+        blk[j] = __double2float_rn(sq - (double)kf);
+        kn[n] = kf;
+        atomicMax(&st->cmax_bits, __float_as_uint(__double2float_ru(sqrt(sq))));
+    } else {
+        blk[j] = INFINITY;
+        for (int l = 0; l < Lp; ++l) blk[(size_t)(1 + l) * BN + j] = 0.f;
+        kn[n] = 0.f;
+    }
+}
+
+__device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+
+// Nearest codevector of BM rows per CTA (see the file header).
+__global__ void __launch_bounds__(ASSIGN_THREADS, 2)
+    k_assign_f32(const float *__restrict__ X, int64_t M, int L, int Lp, const float *__restrict__ Cp,
+                 const float *__restrict__ kn, const int32_t *n_dev, int n_host,
+                 const float *__restrict__ mu, const float *__restrict__ C, DevState *st,
+                 int32_t *__restrict__ assign, float *__restrict__ e, int32_t *__restrict__ flags)
+{
+    if (st->finished) return;
+    extern __shared__ __align__(128) float smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_abort;
+    __shared__ float rec_v1[2][BM], rec_v2[2][BM];
+    __shared__ int rec_id[2][BM];
+
+    const int tid = threadIdx.x;
+    const int N = cur_n(n_dev, n_host);
+    const int nchunk = (N + BN - 1) / BN;
+    const int chunk_floats = (Lp + 1) * BN;
+    const uint32_t chunk_bytes = (uint32_t)chunk_floats * 4u;
+    float *xs = smem;                       // [Lp][BM]
+    float *cbuf0 = xs + Lp * BM;            // [Lp + 1][BN]
+    float *cbuf1 = cbuf0 + chunk_floats;
+    const int64_t m0 = (int64_t)blockIdx.x * BM;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int k = 0; k < 2 && k < nchunk; ++k) {
+            mbar_expect_tx(&bar[k], chunk_bytes);
+            bulk_load(k ? cbuf1 : cbuf0, Cp + (size_t)k * chunk_floats, chunk_bytes, &bar[k]);
+        }
+    }
+
+    // Stage the centred x tile, transposed: xs[l][r] (zero outside M x L).
+    bool bad = false;
+    for (int i = tid; i < BM * Lp; i += ASSIGN_THREADS) {
+        const int r = i % BM, l = i / BM;
+        const int64_t m = m0 + r;
+        float v = 0.f;
+        if (m < M && l < L) {
+            const float xv = X[m * L + l];
+            bad = bad || !isfinite(xv);
+            v = xv - mu[l];
+        }
+        xs[l * BM + r] = v;
+    }
+    if (bad) flag_error(st, ERR_NONFINITE);
+
+    const int warp = tid >> 5, lane = tid & 31;
+    const int wr = warp >> 1, wc = warp & 1;
+    const int ly = lane >> 3, lx = lane & 7;
+    const int rA = wr * 32 + ly * 4;   // rows rA..rA+3 and rA+16..rA+19
+    const int cA = wc * 64 + lx * 4;   // codevectors cA..cA+3 and cA+32..cA+35
+
+    float v1[8], v2[8];
+    int mk[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        v1[i] = INFINITY;
+        v2[i] = INFINITY;
+        mk[i] = 0;
+    }
+    __syncthreads();
+
+    int k_stop = nchunk;
+    for (int k = 0; k < nchunk; ++k) {
+        const int b = k & 1;
+        const float *cb = b ? cbuf1 : cbuf0;
+        const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)(k >> 1) & 1u);
+        if (!ok) s_abort = 1;
+        if (ok) {
+            float acc[8][8];
+            {
+                const float4 s0a = lds4(&cb[cA]), s0b = lds4(&cb[cA + 32]);
+                const float4 xa = lds4(&xs[rA]), xb = lds4(&xs[rA + 16]);
+                const float4 ca = lds4(&cb[BN + cA]), cc = lds4(&cb[BN + cA + 32]);
+                const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+                const float cv[8] = {ca.x, ca.y, ca.z, ca.w, cc.x, cc.y, cc.z, cc.w};
+                const float s0[8] = {s0a.x, s0a.y, s0a.z, s0a.w, s0b.x, s0b.y, s0b.z, s0b.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(xv[i], cv[j], s0[j]);
+            }
+#pragma unroll 4
+            for (int l = 1; l < Lp; ++l) {
+                const float4 xa = lds4(&xs[l * BM + rA]), xb = lds4(&xs[l * BM + rA + 16]);
+                const float4 ca = lds4(&cb[(1 + l) * BN + cA]), cc = lds4(&cb[(1 + l) * BN + cA + 32]);
+                const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+                const float cv[8] = {ca.x, ca.y, ca.z, ca.w, cc.x, cc.y, cc.z, cc.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(xv[i], cv[j], acc[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float old = v1[i];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float a = acc[i][j];
+                    v2[i] = fminf(v2[i], fmaxf(v1[i], a));
+                    v1[i] = fminf(v1[i], a);
+                }
+                mk[i] = (v1[i] < old) ? k : mk[i];
+            }
+        }
+        __syncthreads();
+        if (s_abort) {
+            k_stop = k;
+            break;
+        }
+        if (tid == 0 && k + 2 < nchunk) {
+            mbar_expect_tx(&bar[b], chunk_bytes);
+            bulk_load(cbuf0 + b * chunk_floats, Cp + (size_t)(k + 2) * chunk_floats, chunk_bytes,
+                      &bar[b]);
+        }
+    }
+    if (k_stop < nchunk) {
+        // A bulk copy did not land in time: wait (bounded) for the copies
+        // still in flight, report, and leave the rows unwritten.
+        if (tid == 0) {
+            for (int kk = k_stop; kk < nchunk && kk < k_stop + 2; ++kk)
+                (void)mbar_wait_bounded(&bar[kk & 1], (uint32_t)(kk >> 1) & 1u);
+            flag_error(st, ERR_TIMEOUT);
+        }
+        return;
+    }
+
+    // Merge the 8 lanes that share rows (lx = 0..7), then the two warps (wc).
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        int id = mk[i] * 16 + wc * 8 + lx;
+        float a1 = v1[i], a2 = v2[i];
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const float b1 = __shfl_xor_sync(0xffffffffu, a1, o);
+            const float b2 = __shfl_xor_sync(0xffffffffu, a2, o);
+            const int bid = __shfl_xor_sync(0xffffffffu, id, o);
+            a2 = fminf(fminf(a2, b2), fmaxf(a1, b1));
+            const bool take = (b1 < a1) || (b1 == a1 && bid < id);
+            a1 = take ? b1 : a1;
+            id = take ? bid : id;
+        }
+        if (lx == 0) {
+            const int r = (i < 4) ? rA + i : rA + 12 + i;
+            rec_v1[wc][r] = a1;
+            rec_v2[wc][r] = a2;
+            rec_id[wc][r] = id;
+        }
+    }
+    __syncthreads();
+    if (tid >= BM) return;
+    const int r = tid;
+    const int64_t m = m0 + r;
+    if (m >= M) return;
+    float V1, V2;
+    int ID;
+    {
+        const float a1 = rec_v1[0][r], a2 = rec_v2[0][r], b1 = rec_v1[1][r], b2 = rec_v2[1][r];
+        const int ia = rec_id[0][r], ib = rec_id[1][r];
+        V2 = fminf(fminf(a2, b2), fmaxf(a1, b1));
+        const bool take = (b1 < a1) || (b1 == a1 && ib < ia);
+        V1 = take ? b1 : a1;
+        ID = take ? ib : ia;
+    }
+
+    // Recover the index: recompute the winning group's 8 chains exactly.
+    const int kw = ID >> 4, nl = ((ID >> 3) & 1) * 64 + (ID & 7) * 4;
+    const float *blk = Cp + (size_t)kw * chunk_floats;
+    float s[8];
+    {
+        const float4 t0 = __ldg(reinterpret_cast<const float4 *>(blk + nl));
+        const float4 t1 = __ldg(reinterpret_cast<const float4 *>(blk + nl + 32));
+        const float4 c0 = __ldg(reinterpret_cast<const float4 *>(blk + BN + nl));
+        const float4 c1 = __ldg(reinterpret_cast<const float4 *>(blk + BN + nl + 32));
+        const float x0 = xs[r];
+        s[0] = fmaf(x0, c0.x, t0.x);
+        s[1] = fmaf(x0, c0.y, t0.y);
+        s[2] = fmaf(x0, c0.z, t0.z);
+        s[3] = fmaf(x0, c0.w, t0.w);
+        s[4] = fmaf(x0, c1.x, t1.x);
+        s[5] = fmaf(x0, c1.y, t1.y);
+        s[6] = fmaf(x0, c1.z, t1.z);
+        s[7] = fmaf(x0, c1.w, t1.w);
+    }
+#pragma unroll 4
+    for (int l = 1; l < Lp; ++l) {
+        const float4 c0 = __ldg(reinterpret_cast<const float4 *>(blk + (1 + l) * BN + nl));
+        const float4 c1 = __ldg(reinterpret_cast<const float4 *>(blk + (1 + l) * BN + nl + 32));
+        const float x = xs[l * BM + r];
+        s[0] = fmaf(x, c0.x, s[0]);
+        s[1] = fmaf(x, c0.y, s[1]);
+        s[2] = fmaf(x, c0.z, s[2]);
+        s[3] = fmaf(x, c0.w, s[3]);
+        s[4] = fmaf(x, c1.x, s[4]);
+        s[5] = fmaf(x, c1.y, s[5]);
+        s[6] = fmaf(x, c1.z, s[6]);
+        s[7] = fmaf(x, c1.w, s[7]);
+    }
+    int i1 = -1;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        if (i1 < 0 && s[j] == V1) i1 = kw * BN + nl + (j < 4 ? j : 28 + j);
+
+    bool certified = false;
+    if (i1 >= 0 && i1 < N && V1 < INFINITY) {
+        float xn2 = 0.f;
+        for (int l = 0; l < L; ++l) xn2 = fmaf(xs[l * BM + r], xs[l * BM + r], xn2);
+        const float xn2u = xn2 * SLOP;
+        const float R = (float)(L + 2) * U32 * xn2u * SLOP;
+        const float kc = kn[i1];
+        const float cmax = __uint_as_float(st->cmax_bits);
+        const float eta = U32 * (sqrtf(xn2u) + cmax) * SLOP;
+        const float g1sq = xn2u + V1 + 2.f * kc + R + 4.f * U32 * (xn2u + fabsf(V1));
+        const float g1 = sqrtf(fmaxf(g1sq, 0.f)) * SLOP;
+        const float margin = (2.f * R + 2.f * kc + 4.f * eta * (g1 + eta)) * SLOP;
+        certified = (V2 - V1) > margin;
+    }
+    if (certified) {
+        const float *xr = X + m * L;
+        const float *cr = C + (size_t)i1 * L;
+        float d2 = 0.f;
+        for (int l = 0; l < L; ++l) {
+            const float d = xr[l] - cr[l];
+            d2 = fmaf(d, d, d2);
+        }
+        assign[m] = i1;
+        e[m] = d2;
+    } else {
+        flags[atomicAdd(&st->nflag, 1)] = (int32_t)m;
+    }
+}
+
+// Exact FP32 direct-form re-scoring of the rows k_assign_f32 could not
+// certify: d = sum_l (x_l - c_l)^2 in index order for every codevector,
+// minimum with the lowest index on ties.  A warp takes EX_ROWS rows so each
+// codebook value read serves several rows; lanes stride the codevectors
+// (coalesced reads of the transposed codebook CT).
+__global__ void __launch_bounds__(EX_WARPS * 32)
+    k_assign_exact(const float *__restrict__ X, int L, const float *__restrict__ CT, int NP,
+                   const int32_t *n_dev, int n_host, DevState *st, const int32_t *__restrict__ flags,
+                   int32_t *__restrict__ assign, float *__restrict__ e)
+{
+    if (st->finished) return;
+    __shared__ float xsh[EX_WARPS][EX_ROWS][LMAX];
+    const int nflag = st->nflag;
+    const int N = cur_n(n_dev, n_host);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ngroups = (nflag + EX_ROWS - 1) / EX_ROWS;
+    for (int g = blockIdx.x * EX_WARPS + warp; g < ngroups; g += gridDim.x * EX_WARPS) {
+        const int nr = min(EX_ROWS, nflag - g * EX_ROWS);
+        int rows[EX_ROWS];
+#pragma unroll
+        for (int q = 0; q < EX_ROWS; ++q) rows[q] = (q < nr) ? flags[g * EX_ROWS + q] : -1;
+#pragma unroll
+        for (int q = 0; q < EX_ROWS; ++q)
+            for (int l = lane; l < L; l += 32)
+                xsh[warp][q][l] = rows[q] >= 0 ? X[(int64_t)rows[q] * L + l] : 0.f;
+        __syncwarp();
+        float best[EX_ROWS];
+        int bi[EX_ROWS];
+#pragma unroll
+        for (int q = 0; q < EX_ROWS; ++q) {
+            best[q] = INFINITY;
+            bi[q] = 0x7fffffff;
+        }
+        for (int n = lane; n < N; n += 32) {
+            float d2[EX_ROWS];
+#pragma unroll
+            for (int q = 0; q < EX_ROWS; ++q) d2[q] = 0.f;
+            for (int l = 0; l < L; ++l) {
+                const float c = __ldg(CT + (size_t)l * NP + n);
+#pragma unroll
+                for (int q = 0; q < EX_ROWS; ++q) {
+                    const float d = xsh[warp][q][l] - c;
+                    d2[q] = fmaf(d, d, d2[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < EX_ROWS; ++q)
+                if (d2[q] < best[q]) {
+                    best[q] = d2[q];
+                    bi[q] = n;
+                }
+        }
+#pragma unroll
+        for (int q = 0; q < EX_ROWS; ++q) {
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best[q], o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi[q], o);
+                if (ob < best[q] || (ob == best[q] && oi < bi[q])) {
+                    best[q] = ob;
+                    bi[q] = oi;
+                }
+            }
+        }
+        if (lane == 0) {
+            for (int q = 0; q < nr; ++q) {
+                const bool valid = bi[q] >= 0 && bi[q] < N;
+                if (!valid) flag_error(st, ERR_NONFINITE);   // only NaN rows compare false everywhere
+                assign[rows[q]] = valid ? bi[q] : 0;
+                e[rows[q]] = valid ? best[q] : 0.f;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_decode(const int32_t *__restrict__ assign, int64_t M, int L,
+                         const float *__restrict__ C, float *__restrict__ Xhat)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M * L) return;
+    const int64_t m = i / L;
+    const int l = (int)(i - m * L);
+    Xhat[i] = C[(size_t)assign[m] * L + l];
+}
+
+}  // namespace
+
+void launch_codebook_mean(const float *C, int N, int L, float *mu, cudaStream_t s)
+{
+    k_codebook_mean<<<1, 1024, 0, s>>>(C, N, L, mu);
+}
+
+void launch_prep(const float *C, int N_alloc, const int32_t *n_dev, int n_host, int L, int Lp,
+                 const float *mu, float *Cp, float *kn, float *CT, int NP, DevState *st,
+                 cudaStream_t s)
+{
+    const int threads = 256;
+    const int total = round_up(N_alloc, BN);
+    k_prep<<<(total + threads - 1) / threads, threads, 0, s>>>(C, n_dev, n_host, L, Lp, mu, Cp, kn,
+                                                              CT, NP, st);
+}
+
+size_t assign_smem_bytes(int Lp) { return (size_t)(Lp * BM + 2 * (Lp + 1) * BN) * sizeof(float); }
+
+void launch_assign(const float *X, int64_t M, int L, int Lp, const float *Cp, const float *kn,
+                   const int32_t *n_dev, int n_host, const float *mu, const float *C, DevState *st,
+                   int32_t *assign, float *e, int32_t *flags, cudaStream_t s)
+{
+    const size_t smem = assign_smem_bytes(Lp);
+    cudaFuncSetAttribute(k_assign_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int64_t grid = (M + BM - 1) / BM;
+    if (grid == 0) return;
+    k_assign_f32<<<(unsigned)grid, ASSIGN_THREADS, smem, s>>>(X, M, L, Lp, Cp, kn, n_dev, n_host, mu,
+                                                              C, st, assign, e, flags);
+}
+
+void launch_exact(const float *X, int L, const float *CT, int NP, const int32_t *n_dev, int n_host,
+                  DevState *st, const int32_t *flags, int32_t *assign, float *e, int64_t M,
+                  cudaStream_t s)
+{
+    // Enough warps for every SM; each warp loops over groups of flagged rows.
+    int64_t groups = (M + EX_ROWS - 1) / EX_ROWS;
+    int64_t blocks = (groups + EX_WARPS - 1) / EX_WARPS;
+    if (blocks > 152 * 4) blocks = 152 * 4;
+    if (blocks < 1) blocks = 1;
+    k_assign_exact<<<(unsigned)blocks, EX_WARPS * 32, 0, s>>>(X, L, CT, NP, n_dev, n_host, st, flags,
+                                                             assign, e);
+}
+
+void launch_decode(const int32_t *assign, int64_t M, int L, const float *C, float *Xhat,
+                   cudaStream_t s)
+{
+    const int64_t total = M * L;
+    if (total == 0) return;
+    k_decode<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(assign, M, L, C, Xhat);
+}
+
+}  // namespace lbg

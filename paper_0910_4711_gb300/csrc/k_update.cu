@@ -1,0 +1,573 @@
+// k_update.cu -- initial centroid, distortion integration, stop test, cell
+// table and centroid update, codebook splitting.
+//
+// Paper: Algorithm 1 -- "compute centroid(input)" (Table 1),
+// "IntegratePartialCellTables" / "IntegrateDistortions" (the cell table and
+// TD = sum of the per-processor distortions), the stop test
+// (D_prev - D)/D <= eps (Sec. 2.2 step 2), "Updation" (ExtractVectors of a
+// cell + its centroid), and "Codebook Splitting" ([c + delta], [c - delta]).
+//
+// GB300 design: the paper's per-processor partial cell tables and round-robin
+// centroid updates become a deterministic counting sort of the rows by cell
+// followed by a segmented reduction; no floating-point atomics anywhere, and
+// every floating-point sum has a fixed order, so two runs give identical bits.
+//   k_hist     per-chunk cell counts (integer shared-memory atomics) and
+//              per-chunk distortion partials (fixed-order tree, FP64 out);
+//   k_ctl      D = fixed-order FP64 sum of the chunk partials, stop test;
+//   k_scan     per cell, exclusive prefix of its chunk counts + cell size;
+//   k_offsets  exclusive prefix of the cell sizes (cell start offsets);
+//   k_scatter  stable placement of every row into perm[] (rows grouped by
+//              cell, original order inside a cell);
+//   k_cellsum  one warp per SEG consecutive perm entries: FP32 sums of the
+//              gathered rows per cell piece (coalesced 16-byte row reads);
+//   k_combine  per codevector: FP64 sum of its pieces in order / count.
+#include "lbg_internal.cuh"
+
+#include <math.h>
+
+namespace lbg {
+namespace {
+
+__device__ __forceinline__ int cur_n(const int32_t *n_dev, int n_host)
+{
+    return n_dev ? *n_dev : n_host;
+}
+
+__device__ __forceinline__ bool skip_update(const DevState *st, int train)
+{
+    return train && (st->finished || st->action != ACT_UPDATE);
+}
+
+// ---------------------------------------------------------------- mean
+// Column sums of X per CTA over a contiguous row range: FP32 runs of 8 rows
+// accumulated in FP64, then a fixed-order reduction.  part[b*L + l].
+__global__ void __launch_bounds__(256) k_mean_part(const float *__restrict__ X, int64_t M, int L,
+                                                   double *__restrict__ part, DevState *st)
+{
+    __shared__ double red[256];
+    const int per = 256 / L;   // rows in parallel
+    const int t = threadIdx.x;
+    const int l = t % L, rr = t / L;
+    const int64_t R = (M + gridDim.x - 1) / gridDim.x;
+    const int64_t m0 = (int64_t)blockIdx.x * R, m1 = m0 + R < M ? m0 + R : M;
+    double acc = 0.0;
+    bool bad = false;
+    if (rr < per) {
+        float run = 0.f;
+        int cnt = 0;
+        for (int64_t m = m0 + rr; m < m1; m += per) {
+            const float v = X[m * L + l];
+            bad = bad || !isfinite(v);
+            run += v;
+            if (++cnt == 8) {
+                acc += run;
+                run = 0.f;
+                cnt = 0;
+            }
+        }
+        acc += run;
+    }
+    if (bad) flag_error(st, ERR_NONFINITE);
+    red[t] = acc;
+    __syncthreads();
+    if (t < L) {
+        double s = 0.0;
+        for (int q = 0; q < per; ++q) s += red[q * L + t];
+        part[(size_t)blockIdx.x * L + t] = s;
+    }
+}
+
+// mu = C0 = fl32(sum of the partials in block order / M).
+__global__ void k_mean_final(const double *__restrict__ part, int G, int64_t M, int L,
+                             float *__restrict__ mu, float *__restrict__ C0)
+{
+    const int l = threadIdx.x;
+    if (l >= L) return;
+    double s = 0.0;
+    for (int b = 0; b < G; ++b) s += part[(size_t)b * L + l];
+    const float c = (float)(s / (double)M);
+    mu[l] = c;
+    if (C0) C0[l] = c;
+}
+
+// ---------------------------------------------------------------- hist
+// CTA per chunk of R rows: cell counts of the chunk -> table[chunk][n]
+// (stride n_cur) and the chunk's distortion partial -> dpart[chunk].
+__global__ void __launch_bounds__(HIST_THREADS)
+    k_hist(const int32_t *__restrict__ assign, const float *__restrict__ e, int64_t M, int64_t R,
+           const int32_t *n_dev, int n_host, int do_hist, int32_t *__restrict__ table,
+           double *__restrict__ dpart, DevState *st, int train)
+{
+    if (train && st->finished) return;
+    extern __shared__ int h[];
+    __shared__ double red[HIST_THREADS];
+    const int N = cur_n(n_dev, n_host);
+    const int tid = threadIdx.x;
+    const int64_t m0 = (int64_t)blockIdx.x * R, m1 = m0 + R < M ? m0 + R : M;
+    if (do_hist)
+        for (int n = tid; n < N; n += HIST_THREADS) h[n] = 0;
+    __syncthreads();
+    double acc = 0.0;
+    float run = 0.f;
+    int cnt = 0;
+    bool clamped = false;
+    for (int64_t m = m0 + tid; m < m1; m += HIST_THREADS) {
+        if (do_hist) {
+            int a = assign[m];
+            if (a < 0 || a >= N) {
+                clamped = true;
+                a = a < 0 ? 0 : N - 1;
+            }
+            atomicAdd(&h[a], 1);
+        }
+        run += e[m];
+        if (++cnt == 8) {
+            acc += run;
+            run = 0.f;
+            cnt = 0;
+        }
+    }
+    acc += run;
+    if (clamped) flag_error(st, ERR_INTERNAL);
+    red[tid] = acc;
+    __syncthreads();
+    for (int s = HIST_THREADS / 2; s > 0; s >>= 1) {
+        if (tid < s) red[tid] += red[tid + s];
+        __syncthreads();
+    }
+    if (tid == 0) dpart[blockIdx.x] = red[0];
+    if (do_hist)
+        for (int n = tid; n < N; n += HIST_THREADS) table[(size_t)blockIdx.x * N + n] = h[n];
+}
+
+// ---------------------------------------------------------------- control
+// D = sum of the chunk partials in chunk order.  In MODE_TRAIN also the
+// stop test of Sec. 2.2 with the readings of the library: the stage ends if
+// D == 0 or (D_prev - D)/D <= theta, or when it has run max_passes passes.
+__global__ void k_ctl(const double *__restrict__ dpart, int CH, DevState *st, int mode, double theta,
+                      int max_passes, int N_target, PassRecord *rec, int max_rec)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (mode == MODE_TRAIN && st->finished) return;
+    double D = 0.0;
+    for (int c = 0; c < CH; ++c) D += dpart[c];
+    const int nflag = st->nflag;
+    st->n_exact_last = nflag;
+    st->nflag = 0;
+    st->D = D;
+    if (mode != MODE_TRAIN) {
+        st->action = ACT_UPDATE;
+        return;
+    }
+    bool done = (D == 0.0) || ((st->D_prev - D) / D <= theta);
+    if (!done && st->pass + 1 >= max_passes) {
+        done = true;
+        st->warn = 1;
+    }
+    const int act = !done ? ACT_UPDATE : (st->n_cur >= N_target ? ACT_FINISH : ACT_SPLIT);
+    if (rec && st->total < max_rec) {
+        PassRecord r;
+        r.stage_n = st->n_cur;
+        r.pass = st->pass;
+        r.action = act;
+        r.n_exact = nflag;
+        r.D = D;
+        rec[st->total] = r;
+    }
+    st->total += 1;
+    st->action = act;
+    if (act == ACT_UPDATE) {
+        st->D_prev = D;
+        st->pass += 1;
+    }
+}
+
+// ---------------------------------------------------------------- scan
+// CTA of 1024 threads per 32 cells: lane = cell, warp w covers a range of
+// chunks.  table[c][n] becomes the exclusive prefix over c; counts[n] = total.
+__global__ void __launch_bounds__(1024) k_scan(int32_t *__restrict__ table, int CH,
+                                               const int32_t *n_dev, int n_host,
+                                               int32_t *__restrict__ counts, DevState *st, int train)
+{
+    if (skip_update(st, train)) return;
+    const int N = cur_n(n_dev, n_host);
+    if ((int)blockIdx.x * 32 >= N) return;
+    __shared__ int part[32][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int n = blockIdx.x * 32 + lane;
+    const int per = (CH + 31) / 32;
+    const int c0 = w * per, c1 = c0 + per < CH ? c0 + per : CH;
+    int s = 0;
+    if (n < N)
+        for (int c = c0; c < c1; ++c) s += table[(size_t)c * N + n];
+    part[w][lane] = s;
+    __syncthreads();
+    if (w == 0) {
+        int run = 0;
+        for (int q = 0; q < 32; ++q) {
+            const int v = part[q][lane];
+            part[q][lane] = run;
+            run += v;
+        }
+        if (n < N) counts[n] = run;
+    }
+    __syncthreads();
+    int run = part[w][lane];
+    if (n < N)
+        for (int c = c0; c < c1; ++c) {
+            const int v = table[(size_t)c * N + n];
+            table[(size_t)c * N + n] = run;
+            run += v;
+        }
+}
+
+// One CTA: off[n] = sum_{n' < n} counts[n'], off[N] = total.
+__global__ void __launch_bounds__(1024) k_offsets(const int32_t *__restrict__ counts,
+                                                  const int32_t *n_dev, int n_host,
+                                                  int32_t *__restrict__ off, DevState *st, int train)
+{
+    if (skip_update(st, train)) return;
+    __shared__ int wsum[32];
+    const int N = cur_n(n_dev, n_host);
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int per = (N + 1023) / 1024;
+    const int a = t * per, b = a + per < N ? a + per : N;
+    int loc = 0;
+    for (int i = a; i < b; ++i) loc += counts[i];
+    int inc = loc;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int v = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        wsum[lane] = v;
+    }
+    __syncthreads();
+    int run = inc - loc + (w > 0 ? wsum[w - 1] : 0);
+    for (int i = a; i < b; ++i) {
+        off[i] = run;
+        run += counts[i];
+    }
+    if (t == 1023) off[N] = run;
+}
+
+// ---------------------------------------------------------------- scatter
+// CTA per chunk (same chunks as k_hist).  Rows are taken in rounds of 256 in
+// index order; inside a round a row's slot is
+//   run[cell] + (rows of that cell in lower warps of the round) + (rank among
+//   equal cells in its warp, __match_any_sync),
+// which is the stable counting-sort position.  run[] starts at the cell
+// offset plus the chunk's exclusive prefix.  Integer atomics only.
+__global__ void __launch_bounds__(256) k_scatter(const int32_t *__restrict__ assign, int64_t M,
+                                                 int64_t R, const int32_t *__restrict__ table,
+                                                 const int32_t *__restrict__ off,
+                                                 const int32_t *n_dev, int n_host,
+                                                 int32_t *__restrict__ perm, DevState *st, int train)
+{
+    if (skip_update(st, train)) return;
+    extern __shared__ int sm[];
+    const int N = cur_n(n_dev, n_host);
+    int *run = sm;                                                   // [N]
+    unsigned char *wcnt = reinterpret_cast<unsigned char *>(sm + N);  // [8][N]
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int64_t m0 = (int64_t)blockIdx.x * R, m1 = m0 + R < M ? m0 + R : M;
+    for (int n = tid; n < N; n += 256) run[n] = off[n] + table[(size_t)blockIdx.x * N + n];
+    for (int i = tid; i < 2 * N; i += 256) reinterpret_cast<int *>(wcnt)[i] = 0;
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    for (int64_t base = m0; base < m1; base += 256) {
+        const int64_t m = base + tid;
+        const bool valid = m < m1;
+        int a = valid ? assign[m] : -1 - w;
+        if (valid && (a < 0 || a >= N)) a = a < 0 ? 0 : N - 1;   // same clamp as k_hist
+        const unsigned peers = __match_any_sync(0xffffffffu, a);
+        const int rank = __popc(peers & lt);
+        const bool leader = (peers & lt) == 0u;
+        const int cnt = __popc(peers);
+        if (valid && leader) wcnt[w * N + a] = (unsigned char)cnt;
+        __syncthreads();
+        if (valid) {
+            int pre = 0;
+            for (int q = 0; q < w; ++q) pre += wcnt[q * N + a];
+            perm[run[a] + pre + rank] = (int32_t)m;
+        }
+        __syncthreads();
+        if (valid && leader) {
+            atomicAdd(&run[a], cnt);
+            wcnt[w * N + a] = 0;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- cellsum
+__device__ __forceinline__ int first_cell(const int32_t *off, int N, int64_t p)
+{
+    // largest n with off[n] <= p (then off[n + 1] > p because off[N] = M > p)
+    int lo = 0, hi = N - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= p)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void add4(float4 &a, const float4 &b)
+{
+    a.x += b.x;
+    a.y += b.y;
+    a.z += b.z;
+    a.w += b.w;
+}
+
+// Warp q sums perm[q*S, (q+1)*S) cell piece by cell piece; G lanes cover a
+// row with float4 loads (L = 4G), 32/G rows per step, four steps in flight.
+// Piece (cell n, warp q) -> pieces[(n + q) * L ...] (unique slot per piece).
+template <int G>
+__global__ void __launch_bounds__(256)
+    k_cellsum_v4(const float *__restrict__ X, int64_t M, const int32_t *__restrict__ perm,
+                 const int32_t *__restrict__ off, const int32_t *n_dev, int n_host, int64_t S,
+                 float *__restrict__ pieces, DevState *st, int train)
+{
+    if (skip_update(st, train)) return;
+    constexpr int RPG = 32 / G;
+    constexpr int L = 4 * G;
+    const int N = cur_n(n_dev, n_host);
+    const int64_t q = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int64_t p0 = q * S;
+    if (p0 >= M) return;
+    const int64_t p1 = p0 + S < M ? p0 + S : M;
+    const int rs = lane / G, qd = lane % G;
+    const float4 *X4 = reinterpret_cast<const float4 *>(X);
+    int n = first_cell(off, N, p0);
+    int64_t p = p0;
+    while (p < p1) {
+        const int64_t pe = (int64_t)off[n + 1] < p1 ? (int64_t)off[n + 1] : p1;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        int64_t pp = p + rs;
+        for (; pp + 3 * RPG < pe; pp += 4 * RPG) {
+            const int r0 = perm[pp], r1 = perm[pp + RPG], r2 = perm[pp + 2 * RPG],
+                      r3 = perm[pp + 3 * RPG];
+            const float4 v0 = __ldg(X4 + (int64_t)r0 * G + qd);
+            const float4 v1 = __ldg(X4 + (int64_t)r1 * G + qd);
+            const float4 v2 = __ldg(X4 + (int64_t)r2 * G + qd);
+            const float4 v3 = __ldg(X4 + (int64_t)r3 * G + qd);
+            add4(acc, v0);
+            add4(acc, v1);
+            add4(acc, v2);
+            add4(acc, v3);
+        }
+        for (; pp < pe; pp += RPG) add4(acc, __ldg(X4 + (int64_t)perm[pp] * G + qd));
+#pragma unroll
+        for (int o = G; o < 32; o <<= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+            acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+            acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+        }
+        if (rs == 0) reinterpret_cast<float4 *>(pieces + (size_t)(n + q) * L)[qd] = acc;
+        p = pe;
+        while (n + 1 < N && off[n + 1] <= p) ++n;
+    }
+}
+
+// Any L: lanes own dims l = lane, lane + 32, ...; rows in order.
+__global__ void __launch_bounds__(256)
+    k_cellsum_any(const float *__restrict__ X, int64_t M, int L, const int32_t *__restrict__ perm,
+                  const int32_t *__restrict__ off, const int32_t *n_dev, int n_host, int64_t S,
+                  float *__restrict__ pieces, DevState *st, int train)
+{
+    if (skip_update(st, train)) return;
+    const int N = cur_n(n_dev, n_host);
+    const int64_t q = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int64_t p0 = q * S;
+    if (p0 >= M) return;
+    const int64_t p1 = p0 + S < M ? p0 + S : M;
+    int n = first_cell(off, N, p0);
+    int64_t p = p0;
+    while (p < p1) {
+        const int64_t pe = (int64_t)off[n + 1] < p1 ? (int64_t)off[n + 1] : p1;
+        float acc[LMAX / 32] = {0.f, 0.f, 0.f, 0.f};
+        for (int64_t pp = p; pp < pe; ++pp) {
+            const int64_t r = perm[pp];
+#pragma unroll
+            for (int k = 0; k < LMAX / 32; ++k) {
+                const int l = lane + 32 * k;
+                if (l < L) acc[k] += __ldg(X + r * L + l);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < LMAX / 32; ++k) {
+            const int l = lane + 32 * k;
+            if (l < L) pieces[(size_t)(n + q) * L + l] = acc[k];
+        }
+        p = pe;
+        while (n + 1 < N && off[n + 1] <= p) ++n;
+    }
+}
+
+// c_n = (sum of its pieces, in piece order, in FP64) / count_n; an empty
+// cell copies C_in (may alias C_out).
+__global__ void k_combine(const float *__restrict__ pieces, const int32_t *__restrict__ off,
+                          const int32_t *n_dev, int n_host, int L, int64_t S, const float *C_in,
+                          float *C_out, DevState *st, int train)
+{
+    if (skip_update(st, train)) return;
+    const int N = cur_n(n_dev, n_host);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)N * L) return;
+    const int n = (int)(i / L), l = (int)(i - (int64_t)n * L);
+    const int64_t a = off[n], b = off[n + 1];
+    if (b == a) {
+        C_out[i] = C_in[i];
+        return;
+    }
+    const int64_t q0 = a / S, q1 = (b - 1) / S;
+    double s = 0.0;
+    for (int64_t q = q0; q <= q1; ++q) s += (double)pieces[(size_t)(n + q) * L + l];
+    C_out[i] = (float)(s / (double)(b - a));
+}
+
+// ---------------------------------------------------------------- split
+// [c + delta], [c - delta] per centroid, interleaved, rounded once from FP64.
+__global__ void k_split(const float *__restrict__ C_cur, float *__restrict__ C_alt, int L,
+                        double delta, DevState *st)
+{
+    if (st->finished || st->action != ACT_SPLIT) return;
+    const int n = st->n_cur;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n * L) return;
+    const int64_t c = i / L, l = i - c * L;
+    const double v = (double)C_cur[i];
+    C_alt[(2 * c) * L + l] = (float)(v + delta);
+    C_alt[(2 * c + 1) * L + l] = (float)(v - delta);
+}
+
+__global__ void k_copy_split(const float *__restrict__ C_alt, float *__restrict__ C_cur, int L,
+                             DevState *st)
+{
+    if (st->finished || st->action != ACT_SPLIT) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 2 * (int64_t)st->n_cur * L) C_cur[i] = C_alt[i];
+}
+
+// End of a training pass: a split doubles the stage size and resets the
+// stage (D_prev = +inf, reading of the library); a finish ends training.
+__global__ void k_stage(DevState *st)
+{
+    if (threadIdx.x != 0 || st->finished) return;
+    if (st->action == ACT_SPLIT) {
+        st->n_cur *= 2;
+        st->pass = 0;
+        st->D_prev = INFINITY;
+    } else if (st->action == ACT_FINISH) {
+        st->finished = 1;
+    }
+}
+
+}  // namespace
+
+void launch_mean(const float *X, int64_t M, int L, double *part, int G, float *mu, float *C0,
+                 DevState *st, cudaStream_t s)
+{
+    k_mean_part<<<G, 256, 0, s>>>(X, M, L, part, st);
+    k_mean_final<<<1, 128, 0, s>>>(part, G, M, L, mu, C0);
+}
+
+void launch_hist(const int32_t *assign, const float *e, int64_t M, int64_t R, int CH,
+                 const int32_t *n_dev, int n_host, bool do_hist, int32_t *table, double *dpart,
+                 DevState *st, bool train, cudaStream_t s)
+{
+    const size_t smem = do_hist ? (size_t)n_host * sizeof(int) : 0;
+    cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_hist<<<CH, HIST_THREADS, smem, s>>>(assign, e, M, R, n_dev, n_host, do_hist ? 1 : 0, table,
+                                          dpart, st, train ? 1 : 0);
+}
+
+void launch_ctl(const double *dpart, int CH, DevState *st, int mode, double theta, int max_passes,
+                int N_target, PassRecord *records, int max_records, cudaStream_t s)
+{
+    k_ctl<<<1, 32, 0, s>>>(dpart, CH, st, mode, theta, max_passes, N_target, records, max_records);
+}
+
+void launch_scan(int32_t *table, int CH, const int32_t *n_dev, int n_host, int32_t *counts,
+                 DevState *st, bool train, cudaStream_t s)
+{
+    k_scan<<<(n_host + 31) / 32, 1024, 0, s>>>(table, CH, n_dev, n_host, counts, st, train ? 1 : 0);
+}
+
+void launch_offsets(const int32_t *counts, const int32_t *n_dev, int n_host, int64_t M,
+                    int32_t *off, DevState *st, bool train, cudaStream_t s)
+{
+    (void)M;
+    k_offsets<<<1, 1024, 0, s>>>(counts, n_dev, n_host, off, st, train ? 1 : 0);
+}
+
+void launch_scatter(const int32_t *assign, int64_t M, int64_t R, int CH, const int32_t *table,
+                    const int32_t *off, const int32_t *n_dev, int n_host, int32_t *perm,
+                    DevState *st, bool train, cudaStream_t s)
+{
+    const size_t smem = (size_t)n_host * (sizeof(int) + 8);
+    cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_scatter<<<CH, 256, smem, s>>>(assign, M, R, table, off, n_dev, n_host, perm, st,
+                                    train ? 1 : 0);
+}
+
+void launch_cellsum(const float *X, int64_t M, int L, const int32_t *perm, const int32_t *off,
+                    const int32_t *n_dev, int n_host, int64_t S, float *pieces, DevState *st,
+                    bool train, cudaStream_t s)
+{
+    const int64_t warps = (M + S - 1) / S;
+    if (warps == 0) return;
+    const unsigned blocks = (unsigned)((warps + 7) / 8);
+    const int t = train ? 1 : 0;
+    const bool al = (reinterpret_cast<uintptr_t>(X) & 15u) == 0;
+    switch (al ? L : 0) {
+    case 4: k_cellsum_v4<1><<<blocks, 256, 0, s>>>(X, M, perm, off, n_dev, n_host, S, pieces, st, t); break;
+    case 8: k_cellsum_v4<2><<<blocks, 256, 0, s>>>(X, M, perm, off, n_dev, n_host, S, pieces, st, t); break;
+    case 16: k_cellsum_v4<4><<<blocks, 256, 0, s>>>(X, M, perm, off, n_dev, n_host, S, pieces, st, t); break;
+    case 32: k_cellsum_v4<8><<<blocks, 256, 0, s>>>(X, M, perm, off, n_dev, n_host, S, pieces, st, t); break;
+    case 64: k_cellsum_v4<16><<<blocks, 256, 0, s>>>(X, M, perm, off, n_dev, n_host, S, pieces, st, t); break;
+    case 128: k_cellsum_v4<32><<<blocks, 256, 0, s>>>(X, M, perm, off, n_dev, n_host, S, pieces, st, t); break;
+    default:
+        k_cellsum_any<<<blocks, 256, 0, s>>>(X, M, L, perm, off, n_dev, n_host, S, pieces, st, t);
+    }
+}
+
+void launch_combine(const float *pieces, const int32_t *off, const int32_t *n_dev, int n_host,
+                    int L, int64_t S, const float *C_in, float *C_out, DevState *st, bool train,
+                    cudaStream_t s)
+{
+    const int64_t total = (int64_t)n_host * L;
+    k_combine<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(pieces, off, n_dev, n_host, L, S, C_in,
+                                                             C_out, st, train ? 1 : 0);
+}
+
+void launch_split(const float *C_cur, float *C_alt, int N_alloc, int L, double delta, DevState *st,
+                  cudaStream_t s)
+{
+    const int64_t total = (int64_t)(N_alloc / 2 > 0 ? N_alloc / 2 : 1) * L;
+    k_split<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(C_cur, C_alt, L, delta, st);
+}
+
+void launch_advance(const float *C_alt, float *C_cur, int N_alloc, int L, DevState *st,
+                    cudaStream_t s)
+{
+    const int64_t total = (int64_t)N_alloc * L;
+    k_copy_split<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(C_alt, C_cur, L, st);
+    k_stage<<<1, 32, 0, s>>>(st);
+}
+
+}  // namespace lbg

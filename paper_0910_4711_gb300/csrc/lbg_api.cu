@@ -1,0 +1,542 @@
+// lbg_api.cu -- host side of the C ABI declared in include/lbgvq.h:
+// argument validation, per-device workspace, host<->device staging and the
+// launch sequences of lbg_train / lbg_lloyd_step / vq_encode.
+#include "lbgvq.h"
+#include "lbg_internal.cuh"
+
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+
+using namespace lbg;
+
+namespace {
+
+constexpr int MAX_DEVICES = 64;
+
+struct Workspace {
+    void *base = nullptr;
+    size_t bytes = 0;
+};
+
+std::mutex g_mu;
+Workspace g_ws[MAX_DEVICES];
+
+// Byte offsets of the scratch arrays of one call inside the workspace.
+struct Plan {
+    int64_t M = 0, R = 0, S = 0, nq = 0;
+    int L = 0, Lp = 0, N = 0, NP = 0, CH = 0, G = 0, max_rec = 0;
+    size_t state, rec, Cp, kn, CT, mu, Ccur, Calt, assign, e, flags, table, dpart, counts, off, perm,
+        pieces, mpart, Xs, Cin, Cout, Xhat;
+    size_t total = 0;
+    size_t take(size_t bytes)
+    {
+        const size_t at = total;
+        total += (bytes + 255) / 256 * 256;
+        return at;
+    }
+};
+
+Plan make_plan(int64_t M, int L, int N, int max_rec, bool host_X, bool need_assign, bool host_C,
+               bool host_Xhat)
+{
+    Plan p;
+    p.M = M;
+    p.L = L;
+    p.Lp = round_up(L, 4);
+    p.N = N;
+    p.NP = round_up(N, BN);
+    p.max_rec = max_rec;
+    // histogram / scatter chunks: <= HIST_CHUNKS_MAX CTAs of R rows (R a multiple of 256)
+    int64_t ch = (M + 1023) / 1024;
+    if (ch > HIST_CHUNKS_MAX) ch = HIST_CHUNKS_MAX;
+    if (ch < 1) ch = 1;
+    p.R = round_up64((M + ch - 1) / ch, 256);
+    if (p.R < 256) p.R = 256;
+    p.CH = (int)((M + p.R - 1) / p.R);
+    if (p.CH < 1) p.CH = 1;
+    // centroid pieces: one warp per S cell-sorted rows, aiming at >= 32 warps per SM
+    int64_t S = round_up64((M + 152 * 32 - 1) / (152 * 32), 32);
+    if (S < 256) S = 256;
+    if (S > 4096) S = 4096;
+    p.S = S;
+    p.nq = (M + S - 1) / S;
+    int64_t g = (M + 4095) / 4096;
+    if (g > 304) g = 304;
+    if (g < 1) g = 1;
+    p.G = (int)g;
+
+    p.state = p.take(sizeof(DevState));
+    p.rec = p.take(sizeof(PassRecord) * (size_t)(max_rec > 0 ? max_rec : 1));
+    p.Cp = p.take(sizeof(float) * (size_t)(p.NP / BN) * (p.Lp + 1) * BN);
+    p.kn = p.take(sizeof(float) * (size_t)p.NP);
+    p.CT = p.take(sizeof(float) * (size_t)p.Lp * p.NP);
+    p.mu = p.take(sizeof(float) * (size_t)p.Lp);
+    p.Ccur = p.take(sizeof(float) * (size_t)N * L);
+    p.Calt = p.take(sizeof(float) * (size_t)N * L);
+    p.assign = need_assign ? p.take(sizeof(int32_t) * (size_t)(M > 0 ? M : 1)) : 0;
+    p.e = p.take(sizeof(float) * (size_t)(M > 0 ? M : 1));
+    p.flags = p.take(sizeof(int32_t) * (size_t)(M > 0 ? M : 1));
+    p.table = p.take(sizeof(int32_t) * (size_t)p.CH * N);
+    p.dpart = p.take(sizeof(double) * (size_t)p.CH);
+    p.counts = p.take(sizeof(int32_t) * (size_t)N);
+    p.off = p.take(sizeof(int32_t) * (size_t)(N + 1));
+    p.perm = p.take(sizeof(int32_t) * (size_t)(M > 0 ? M : 1));
+    p.pieces = p.take(sizeof(float) * (size_t)(N + p.nq) * L);
+    p.mpart = p.take(sizeof(double) * (size_t)p.G * L);
+    p.Xs = host_X ? p.take(sizeof(float) * (size_t)M * L) : 0;
+    p.Cin = host_C ? p.take(sizeof(float) * (size_t)N * L) : 0;
+    p.Cout = host_C ? p.take(sizeof(float) * (size_t)N * L) : 0;
+    p.Xhat = host_Xhat ? p.take(sizeof(float) * (size_t)M * L) : 0;
+    return p;
+}
+
+struct Call {
+    int dev = 0;
+    cudaStream_t s = nullptr;
+    char *ws = nullptr;
+    template <class T>
+    T *at(size_t off) const
+    {
+        return reinterpret_cast<T *>(ws + off);
+    }
+};
+
+#define CK(expr)                                    \
+    do {                                            \
+        if ((expr) != cudaSuccess) {                \
+            (void)cudaGetLastError();               \
+            return LBG_ERR_CUDA;                    \
+        }                                           \
+    } while (0)
+
+lbg_status ensure_workspace(Call &c, size_t bytes)
+{
+    Workspace &w = g_ws[c.dev];
+    if (w.bytes < bytes) {
+        if (w.base) {
+            CK(cudaDeviceSynchronize());
+            cudaFree(w.base);
+            w.base = nullptr;
+            w.bytes = 0;
+        }
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return LBG_ERR_NOMEM;
+        }
+        w.base = p;
+        w.bytes = bytes;
+    }
+    c.ws = static_cast<char *>(w.base);
+    return LBG_OK;
+}
+
+// 1 = device-accessible, 0 = host memory, -1 = device memory of another GPU.
+int where(const void *p, int dev)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    if (a.type == cudaMemoryTypeManaged) return 1;
+    if (a.type == cudaMemoryTypeDevice) return a.device == dev ? 1 : -1;
+    return 0;
+}
+
+bool is_pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
+
+lbg_opts resolve(const lbg_opts *o)
+{
+    lbg_opts r;
+    lbg_opts_init(&r);
+    if (o) r = *o;
+    if (r.max_passes <= 0) r.max_passes = 1000;
+    if (!r.records) r.max_records = 0;
+    return r;
+}
+
+lbg_status begin(Call &c, const lbg_opts &o)
+{
+    CK(cudaGetDevice(&c.dev));
+    if (c.dev < 0 || c.dev >= MAX_DEVICES) return LBG_ERR_UNSUPPORTED;
+    c.s = static_cast<cudaStream_t>(o.stream);
+    return LBG_OK;
+}
+
+lbg_status finish_status(const DevState &st)
+{
+    if (st.err & ERR_NONFINITE) return LBG_ERR_NONFINITE;
+    if (st.err & ERR_TIMEOUT) return LBG_ERR_TIMEOUT;
+    if (st.err & ERR_INTERNAL) return LBG_ERR_CUDA;
+    return st.warn ? LBG_WARN_MAXPASS : LBG_OK;
+}
+
+struct Timer {
+    bool on = false;
+    cudaEvent_t ev[5] = {};
+    lbg_status init(bool want)
+    {
+        on = want;
+        if (!on) return LBG_OK;
+        for (auto &e : ev) CK(cudaEventCreate(&e));
+        return LBG_OK;
+    }
+    void mark(int i, cudaStream_t s)
+    {
+        if (on) cudaEventRecord(ev[i], s);
+    }
+    void report(float *out, bool per_phase)
+    {
+        if (!on) return;
+        for (int i = 0; i < LBG_NUM_PHASES; ++i) out[i] = 0.f;
+        if (per_phase) {
+            for (int i = 0; i < 4; ++i) cudaEventElapsedTime(&out[i], ev[i], ev[i + 1]);
+        }
+        cudaEventElapsedTime(&out[LBG_PHASE_TOTAL], ev[0], ev[4]);
+    }
+    ~Timer()
+    {
+        if (on)
+            for (auto &e : ev) cudaEventDestroy(e);
+    }
+};
+
+void init_state(DevState &h, int n_cur)
+{
+    memset(&h, 0, sizeof(h));
+    h.n_cur = n_cur;
+    h.D_prev = INFINITY;
+}
+
+// Prepared codebook + one allocation (cell table of C under X) -> assign, e.
+void run_prepare(const Call &c, const Plan &p, const float *C, const int32_t *n_dev, int n_host,
+                 const float *mu, DevState *st)
+{
+    cudaMemsetAsync(&st->cmax_bits, 0, sizeof(uint32_t), c.s);
+    launch_prep(C, p.N, n_dev, n_host, p.L, p.Lp, mu, c.at<float>(p.Cp), c.at<float>(p.kn),
+                c.at<float>(p.CT), p.NP, st, c.s);
+}
+
+void run_assign(const Call &c, const Plan &p, const float *X, const float *C, const int32_t *n_dev,
+                int n_host, const float *mu, DevState *st, int32_t *assign)
+{
+    launch_assign(X, p.M, p.L, p.Lp, c.at<float>(p.Cp), c.at<float>(p.kn), n_dev, n_host, mu, C, st,
+                  assign, c.at<float>(p.e), c.at<int32_t>(p.flags), c.s);
+}
+
+void run_exact(const Call &c, const Plan &p, const float *X, const int32_t *n_dev, int n_host,
+               DevState *st, int32_t *assign)
+{
+    launch_exact(X, p.L, c.at<float>(p.CT), p.NP, n_dev, n_host, st, c.at<int32_t>(p.flags), assign,
+                 c.at<float>(p.e), p.M, c.s);
+}
+
+void run_update(const Call &c, const Plan &p, const float *X, const int32_t *n_dev, int n_host,
+                DevState *st, const int32_t *assign, const float *C_in, float *C_out, bool train)
+{
+    int32_t *table = c.at<int32_t>(p.table), *off = c.at<int32_t>(p.off);
+    launch_scan(table, p.CH, n_dev, n_host, c.at<int32_t>(p.counts), st, train, c.s);
+    launch_offsets(c.at<int32_t>(p.counts), n_dev, n_host, p.M, off, st, train, c.s);
+    launch_scatter(assign, p.M, p.R, p.CH, table, off, n_dev, n_host, c.at<int32_t>(p.perm), st,
+                   train, c.s);
+    launch_cellsum(X, p.M, p.L, c.at<int32_t>(p.perm), off, n_dev, n_host, p.S,
+                   c.at<float>(p.pieces), st, train, c.s);
+    launch_combine(c.at<float>(p.pieces), off, n_dev, n_host, p.L, p.S, C_in, C_out, st, train, c.s);
+}
+
+lbg_status check_dims(int64_t M, int32_t L, int32_t N)
+{
+    if (M < 0 || M > INT32_MAX) return LBG_ERR_ARG;
+    if (L < 1 || L > LBG_MAX_DIM) return LBG_ERR_ARG;
+    if (N < 1 || N > LBG_MAX_CODEBOOK) return LBG_ERR_ARG;
+    return LBG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbg_opts_init(lbg_opts *o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->precision = LBG_PREC_FP32;
+    o->max_passes = 1000;
+}
+
+int32_t lbg_version(void) { return 1; }
+
+const char *lbg_status_string(lbg_status s)
+{
+    switch (s) {
+    case LBG_OK: return "ok";
+    case LBG_WARN_MAXPASS: return "a stage reached max_passes before the stop test held";
+    case LBG_ERR_ARG: return "invalid argument";
+    case LBG_ERR_NOT_POW2: return "codebook size is not a power of 2";
+    case LBG_ERR_NONFINITE: return "non-finite value in the input vectors or codebook";
+    case LBG_ERR_CUDA: return "CUDA runtime error";
+    case LBG_ERR_NOMEM: return "device scratch allocation failed";
+    case LBG_ERR_TIMEOUT: return "a bounded device wait timed out";
+    case LBG_ERR_UNSUPPORTED: return "unsupported option";
+    }
+    return "unknown status";
+}
+
+lbg_status lbg_release_workspace(void)
+{
+    std::lock_guard<std::mutex> lock(g_mu);
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= MAX_DEVICES) return LBG_ERR_UNSUPPORTED;
+    if (g_ws[dev].base) {
+        CK(cudaDeviceSynchronize());
+        cudaFree(g_ws[dev].base);
+        g_ws[dev].base = nullptr;
+        g_ws[dev].bytes = 0;
+    }
+    return LBG_OK;
+}
+
+lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32_t N, int32_t *idx,
+                     float *Xhat, double *D, const lbg_opts *opts)
+{
+    lbg_status rc = check_dims(M, L, N);
+    if (rc != LBG_OK) return rc;
+    if (!C || (M > 0 && (!X || !idx))) return LBG_ERR_ARG;
+    const lbg_opts o = resolve(opts);
+    if (o.precision != LBG_PREC_FP32) return LBG_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_mu);
+    Call c;
+    if ((rc = begin(c, o)) != LBG_OK) return rc;
+    if (M == 0) {
+        if (D) *D = 0.0;
+        if (o.n_exact) *o.n_exact = 0;
+        return LBG_OK;
+    }
+    const int wX = where(X, c.dev), wC = where(C, c.dev), wI = where(idx, c.dev);
+    const int wH = Xhat ? where(Xhat, c.dev) : 1;
+    if (wX < 0 || wC < 0 || wI < 0 || wH < 0) return LBG_ERR_ARG;
+    const Plan p = make_plan(M, L, N, 0, wX == 0, wI == 0, wC == 0, wH == 0);
+    if ((rc = ensure_workspace(c, p.total)) != LBG_OK) return rc;
+    DevState *st = c.at<DevState>(p.state);
+    DevState h;
+    init_state(h, N);
+    CK(cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, c.s));
+    const float *dX = X;
+    const float *dC = C;
+    if (wX == 0) {
+        CK(cudaMemcpyAsync(c.at<float>(p.Xs), X, sizeof(float) * M * L, cudaMemcpyHostToDevice, c.s));
+        dX = c.at<float>(p.Xs);
+    }
+    if (wC == 0) {
+        CK(cudaMemcpyAsync(c.at<float>(p.Cin), C, sizeof(float) * (size_t)N * L,
+                           cudaMemcpyHostToDevice, c.s));
+        dC = c.at<float>(p.Cin);
+    }
+    int32_t *dI = wI ? idx : c.at<int32_t>(p.assign);
+    Timer tm;
+    if ((rc = tm.init(o.phase_ms != nullptr)) != LBG_OK) return rc;
+    float *mu = c.at<float>(p.mu);
+    tm.mark(0, c.s);
+    launch_codebook_mean(dC, N, L, mu, c.s);
+    run_prepare(c, p, dC, nullptr, N, mu, st);
+    tm.mark(1, c.s);
+    run_assign(c, p, dX, dC, nullptr, N, mu, st, dI);
+    tm.mark(2, c.s);
+    run_exact(c, p, dX, nullptr, N, st, dI);
+    tm.mark(3, c.s);
+    if (D) {
+        launch_hist(dI, c.at<float>(p.e), M, p.R, p.CH, nullptr, N, false, nullptr,
+                    c.at<double>(p.dpart), st, false, c.s);
+        launch_ctl(c.at<double>(p.dpart), p.CH, st, MODE_STEP, 0.0, 1, N, nullptr, 0, c.s);
+    }
+    if (Xhat) launch_decode(dI, M, L, dC, wH ? Xhat : c.at<float>(p.Xhat), c.s);
+    tm.mark(4, c.s);
+    CK(cudaGetLastError());
+    if (wI == 0) CK(cudaMemcpyAsync(idx, dI, sizeof(int32_t) * M, cudaMemcpyDeviceToHost, c.s));
+    if (Xhat && wH == 0)
+        CK(cudaMemcpyAsync(Xhat, c.at<float>(p.Xhat), sizeof(float) * M * L, cudaMemcpyDeviceToHost,
+                           c.s));
+    CK(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, c.s));
+    CK(cudaStreamSynchronize(c.s));
+    tm.report(o.phase_ms, true);
+    if (D) *D = h.D;
+    if (o.n_exact) *o.n_exact = D ? h.n_exact_last : h.nflag;
+    return finish_status(h);
+}
+
+lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const float *C_in,
+                          float *C_out, int32_t *assign, double *D, const lbg_opts *opts)
+{
+    lbg_status rc = check_dims(M, L, N);
+    if (rc != LBG_OK) return rc;
+    if (!C_in || !C_out || (M > 0 && !X)) return LBG_ERR_ARG;
+    const lbg_opts o = resolve(opts);
+    if (o.precision != LBG_PREC_FP32) return LBG_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_mu);
+    Call c;
+    if ((rc = begin(c, o)) != LBG_OK) return rc;
+    const int wX = M > 0 ? where(X, c.dev) : 1, wCi = where(C_in, c.dev), wCo = where(C_out, c.dev);
+    const int wA = assign ? where(assign, c.dev) : 0;
+    if (wX < 0 || wCi < 0 || wCo < 0 || wA < 0) return LBG_ERR_ARG;
+    const bool hostC = (wCi == 0) || (wCo == 0);
+    const Plan p = make_plan(M, L, N, 0, wX == 0, !(assign && wA == 1), hostC, false);
+    if ((rc = ensure_workspace(c, p.total)) != LBG_OK) return rc;
+    const size_t cbytes = sizeof(float) * (size_t)N * L;
+    if (M == 0) {
+        if (C_out != C_in) CK(cudaMemcpyAsync(C_out, C_in, cbytes, cudaMemcpyDefault, c.s));
+        CK(cudaStreamSynchronize(c.s));
+        if (D) *D = 0.0;
+        if (o.n_exact) *o.n_exact = 0;
+        if (o.phase_ms)
+            for (int i = 0; i < LBG_NUM_PHASES; ++i) o.phase_ms[i] = 0.f;
+        return LBG_OK;
+    }
+    DevState *st = c.at<DevState>(p.state);
+    DevState h;
+    init_state(h, N);
+    CK(cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, c.s));
+    const float *dX = X;
+    if (wX == 0) {
+        CK(cudaMemcpyAsync(c.at<float>(p.Xs), X, sizeof(float) * M * L, cudaMemcpyHostToDevice, c.s));
+        dX = c.at<float>(p.Xs);
+    }
+    const float *dCi = C_in;
+    float *dCo = C_out;
+    if (hostC) {
+        CK(cudaMemcpyAsync(c.at<float>(p.Cin), C_in, cbytes, cudaMemcpyDefault, c.s));
+        dCi = c.at<float>(p.Cin);
+        dCo = c.at<float>(p.Cout);
+    }
+    int32_t *dA = (assign && wA == 1) ? assign : c.at<int32_t>(p.assign);
+    Timer tm;
+    if ((rc = tm.init(o.phase_ms != nullptr)) != LBG_OK) return rc;
+    float *mu = c.at<float>(p.mu);
+    tm.mark(0, c.s);
+    launch_codebook_mean(dCi, N, L, mu, c.s);
+    run_prepare(c, p, dCi, nullptr, N, mu, st);
+    tm.mark(1, c.s);
+    run_assign(c, p, dX, dCi, nullptr, N, mu, st, dA);
+    tm.mark(2, c.s);
+    run_exact(c, p, dX, nullptr, N, st, dA);
+    tm.mark(3, c.s);
+    launch_hist(dA, c.at<float>(p.e), M, p.R, p.CH, nullptr, N, true, c.at<int32_t>(p.table),
+                c.at<double>(p.dpart), st, false, c.s);
+    launch_ctl(c.at<double>(p.dpart), p.CH, st, MODE_STEP, 0.0, 1, N, nullptr, 0, c.s);
+    run_update(c, p, dX, nullptr, N, st, dA, dCi, dCo, false);
+    tm.mark(4, c.s);
+    CK(cudaGetLastError());
+    if (hostC) CK(cudaMemcpyAsync(C_out, dCo, cbytes, cudaMemcpyDefault, c.s));
+    if (assign && wA == 0)
+        CK(cudaMemcpyAsync(assign, dA, sizeof(int32_t) * M, cudaMemcpyDeviceToHost, c.s));
+    CK(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, c.s));
+    CK(cudaStreamSynchronize(c.s));
+    tm.report(o.phase_ms, true);
+    if (D) *D = h.D;
+    if (o.n_exact) *o.n_exact = h.n_exact_last;
+    return finish_status(h);
+}
+
+lbg_status lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double delta, double theta,
+                     float *C, int32_t n_init, int32_t *assign, double *D, const lbg_opts *opts)
+{
+    lbg_status rc = check_dims(M, L, N);
+    if (rc != LBG_OK) return rc;
+    if (M < 1 || !X || !C) return LBG_ERR_ARG;
+    if (!(delta >= 0.0) || !(theta >= 0.0) || !isfinite(delta) || !isfinite(theta))
+        return LBG_ERR_ARG;
+    if (!is_pow2(N)) return LBG_ERR_NOT_POW2;
+    if (n_init < 0 || n_init > N) return LBG_ERR_ARG;
+    if (n_init > 0 && !is_pow2(n_init)) return LBG_ERR_NOT_POW2;
+    const lbg_opts o = resolve(opts);
+    if (o.precision != LBG_PREC_FP32) return LBG_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_mu);
+    Call c;
+    if ((rc = begin(c, o)) != LBG_OK) return rc;
+    const int wX = where(X, c.dev), wC = where(C, c.dev);
+    const int wA = assign ? where(assign, c.dev) : 0;
+    if (wX < 0 || wC < 0 || wA < 0) return LBG_ERR_ARG;
+    int stages = 1;
+    for (int n = n_init > 0 ? n_init : 1; n < N; n *= 2) ++stages;
+    const int64_t max_total = (int64_t)stages * o.max_passes;
+    const int max_rec = o.max_records < max_total ? o.max_records : (int)max_total;
+    const Plan p = make_plan(M, L, N, max_rec, wX == 0, !(assign && wA == 1), false, false);
+    if ((rc = ensure_workspace(c, p.total)) != LBG_OK) return rc;
+    DevState *st = c.at<DevState>(p.state);
+    DevState h;
+    init_state(h, n_init > 0 ? n_init : 1);
+    CK(cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, c.s));
+    const float *dX = X;
+    if (wX == 0) {
+        CK(cudaMemcpyAsync(c.at<float>(p.Xs), X, sizeof(float) * M * L, cudaMemcpyHostToDevice, c.s));
+        dX = c.at<float>(p.Xs);
+    }
+    float *Ccur = c.at<float>(p.Ccur), *Calt = c.at<float>(p.Calt), *mu = c.at<float>(p.mu);
+    int32_t *dA = (assign && wA == 1) ? assign : c.at<int32_t>(p.assign);
+    if (n_init > 0)
+        CK(cudaMemcpyAsync(Ccur, C, sizeof(float) * (size_t)n_init * L, cudaMemcpyDefault, c.s));
+    Timer tm;
+    if ((rc = tm.init(o.phase_ms != nullptr)) != LBG_OK) return rc;
+    tm.mark(0, c.s);
+    // Initialization (Algorithm 1): centroid of the training set; it is also
+    // the centring vector of every allocation of the run.
+    launch_mean(dX, M, L, c.at<double>(p.mpart), p.G, mu, n_init > 0 ? nullptr : Ccur, st, c.s);
+    const int32_t *n_dev = &st->n_cur;
+    PassRecord *rec = c.at<PassRecord>(p.rec);
+    int64_t issued = 0;
+    int batch = 2;
+    DevState *hs = nullptr;
+    CK(cudaMallocHost(&hs, sizeof(DevState)));
+    lbg_status out = LBG_OK;
+    for (;;) {
+        for (int b = 0; b < batch && issued < max_total; ++b, ++issued) {
+            run_prepare(c, p, Ccur, n_dev, N, mu, st);
+            run_assign(c, p, dX, Ccur, n_dev, N, mu, st, dA);
+            run_exact(c, p, dX, n_dev, N, st, dA);
+            launch_hist(dA, c.at<float>(p.e), M, p.R, p.CH, n_dev, N, true, c.at<int32_t>(p.table),
+                        c.at<double>(p.dpart), st, true, c.s);
+            launch_ctl(c.at<double>(p.dpart), p.CH, st, MODE_TRAIN, theta, o.max_passes, N, rec,
+                       max_rec, c.s);
+            run_update(c, p, dX, n_dev, N, st, dA, Ccur, Ccur, true);
+            launch_split(Ccur, Calt, N, L, delta, st, c.s);
+            launch_advance(Calt, Ccur, N, L, st, c.s);
+        }
+        if (cudaGetLastError() != cudaSuccess) {
+            out = LBG_ERR_CUDA;
+            break;
+        }
+        if (cudaMemcpyAsync(hs, st, sizeof(DevState), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+            cudaStreamSynchronize(c.s) != cudaSuccess) {
+            (void)cudaGetLastError();
+            out = LBG_ERR_CUDA;
+            break;
+        }
+        if (hs->finished || hs->err || issued >= max_total) break;
+        if (batch < 32) batch *= 2;
+    }
+    tm.mark(4, c.s);
+    if (out == LBG_OK) {
+        h = *hs;
+        if (!h.finished && !h.err) out = LBG_ERR_CUDA;   // pass bound reached without finishing
+    }
+    cudaFreeHost(hs);
+    if (out != LBG_OK) return out;
+    CK(cudaMemcpyAsync(C, Ccur, sizeof(float) * (size_t)N * L, cudaMemcpyDefault, c.s));
+    if (assign && wA == 0)
+        CK(cudaMemcpyAsync(assign, dA, sizeof(int32_t) * M, cudaMemcpyDeviceToHost, c.s));
+    const int nrec = h.total < max_rec ? h.total : max_rec;
+    if (o.records && nrec > 0) {
+        static_assert(sizeof(PassRecord) == sizeof(lbg_pass_record), "record layout");
+        CK(cudaMemcpyAsync(o.records, rec, sizeof(PassRecord) * nrec, cudaMemcpyDeviceToHost, c.s));
+    }
+    CK(cudaStreamSynchronize(c.s));
+    tm.report(o.phase_ms, false);
+    if (o.n_records) *o.n_records = h.total;
+    if (D) *D = h.D;
+    return finish_status(h);
+}
+
+}  // extern "C"

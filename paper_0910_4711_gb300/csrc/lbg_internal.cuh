@@ -1,0 +1,169 @@
+// lbg_internal.cuh -- device state, tile constants and PTX helpers shared by
+// the kernels of the LBG library (internal; not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbg {
+
+// Nearest-codevector tile: a CTA owns BM training rows and streams the
+// codebook through shared memory in chunks of BN codevectors.
+constexpr int BM = 128;
+constexpr int BN = 128;
+constexpr int ASSIGN_THREADS = 256;
+constexpr int LMAX = 128;     // = LBG_MAX_DIM
+constexpr int NMAX = 8192;    // = LBG_MAX_CODEBOOK
+
+// Cell-table build: rows are cut into at most HIST_CHUNKS_MAX contiguous
+// chunks (one CTA each); the segmented centroid sums cut the cell-sorted
+// row order into pieces of SEG rows (one warp each).
+constexpr int HIST_CHUNKS_MAX = 304;   // 2 x 152 SMs
+constexpr int HIST_THREADS = 256;
+
+// Error bits in DevState::err.
+constexpr uint32_t ERR_NONFINITE = 1u;
+constexpr uint32_t ERR_TIMEOUT = 2u;
+constexpr uint32_t ERR_INTERNAL = 4u;
+
+// Pass modes of the control kernel.
+constexpr int MODE_STEP = 0;    // lbg_lloyd_step / vq_encode: no stop test
+constexpr int MODE_TRAIN = 1;   // lbg_train: stop test, split, finish
+
+constexpr int ACT_UPDATE = 0, ACT_SPLIT = 1, ACT_FINISH = 2, ACT_NONE = 3;
+
+// Device-resident state of one call.  lbg_train keeps the whole stage/pass
+// control here so that passes can be issued without host round trips.
+struct DevState {
+    int32_t n_cur;        // codebook size of the current stage
+    int32_t pass;         // pass index within the stage
+    int32_t total;        // passes run so far
+    int32_t action;       // decision of the last stop test (ACT_*)
+    int32_t finished;     // 1 once training has ended (all kernels then no-op)
+    int32_t warn;         // 1 if some stage was cut at max_passes
+    int32_t nflag;        // rows flagged for exact re-scoring in this pass
+    int32_t n_exact_last; // nflag of the last pass (for step / encode reports)
+    uint32_t err;         // ERR_* bits
+    uint32_t cmax_bits;   // bits of max_n ||c_n - mu|| (non-negative float)
+    double D;             // total distortion of the last pass
+    double D_prev;        // distortion of the previous pass of the stage
+};
+
+// Device pass record (mirrors lbg_pass_record).
+struct PassRecord {
+    int32_t stage_n, pass, action, n_exact;
+    double D;
+};
+
+__host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+__host__ __device__ inline int64_t round_up64(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// ------------------------------------------------------------------ PTX
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared through the TMA unit, completing on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of `bar`, giving up after ~2 s of wall time.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255u) == 0u && global_ns() - t0 > 2000000000ull) return false;
+    }
+}
+
+__device__ __forceinline__ void flag_error(DevState *st, uint32_t bits) { atomicOr(&st->err, bits); }
+
+// ------------------------------------------------------------ launchers
+// Codebook preparation (k_assign.cu).
+void launch_codebook_mean(const float *C, int N, int L, float *mu, cudaStream_t s);
+void launch_prep(const float *C, int N_alloc, const int32_t *n_dev, int n_host, int L, int Lp,
+                 const float *mu, float *Cp, float *kn, float *CT, int NP, DevState *st,
+                 cudaStream_t s);
+void launch_assign(const float *X, int64_t M, int L, int Lp, const float *Cp, const float *kn,
+                   const int32_t *n_dev, int n_host, const float *mu, const float *C, DevState *st,
+                   int32_t *assign, float *e, int32_t *flags, cudaStream_t s);
+void launch_exact(const float *X, int L, const float *CT, int NP, const int32_t *n_dev, int n_host,
+                  DevState *st, const int32_t *flags, int32_t *assign, float *e, int64_t M,
+                  cudaStream_t s);
+void launch_decode(const int32_t *assign, int64_t M, int L, const float *C, float *Xhat,
+                   cudaStream_t s);
+
+// Cell table, distortion and centroid update (k_update.cu).
+void launch_mean(const float *X, int64_t M, int L, double *part, int G, float *mu, float *C0,
+                 DevState *st, cudaStream_t s);
+void launch_hist(const int32_t *assign, const float *e, int64_t M, int64_t R, int CH,
+                 const int32_t *n_dev, int n_host, bool do_hist, int32_t *table, double *dpart,
+                 DevState *st, bool train, cudaStream_t s);
+void launch_ctl(const double *dpart, int CH, DevState *st, int mode, double theta, int max_passes,
+                int N_target, PassRecord *records, int max_records, cudaStream_t s);
+void launch_scan(int32_t *table, int CH, const int32_t *n_dev, int n_host, int32_t *counts,
+                 DevState *st, bool train, cudaStream_t s);
+void launch_offsets(const int32_t *counts, const int32_t *n_dev, int n_host, int64_t M,
+                    int32_t *off, DevState *st, bool train, cudaStream_t s);
+void launch_scatter(const int32_t *assign, int64_t M, int64_t R, int CH, const int32_t *table,
+                    const int32_t *off, const int32_t *n_dev, int n_host, int32_t *perm,
+                    DevState *st, bool train, cudaStream_t s);
+void launch_cellsum(const float *X, int64_t M, int L, const int32_t *perm, const int32_t *off,
+                    const int32_t *n_dev, int n_host, int64_t S, float *pieces, DevState *st,
+                    bool train, cudaStream_t s);
+void launch_combine(const float *pieces, const int32_t *off, const int32_t *n_dev, int n_host,
+                    int L, int64_t S, const float *C_in, float *C_out, DevState *st, bool train,
+                    cudaStream_t s);
+void launch_split(const float *C_cur, float *C_alt, int N_alloc, int L, double delta, DevState *st,
+                  cudaStream_t s);
+void launch_advance(const float *C_alt, float *C_cur, int N_alloc, int L, DevState *st,
+                    cudaStream_t s);
+
+}  // namespace lbg

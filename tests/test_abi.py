@@ -1,0 +1,73 @@
+"""The C-ABI library builds, loads without a GPU, exports every function that
+include/lbgvq.h declares, and rejects invalid arguments before any device work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_0910_4711_gb300 as lbgvq
+from paper_0910_4711_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "lbgvq.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(\w+)\s*\([^;{]*\)\s*;", text)) - {"if", "while"})
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return lbgvq.lib()
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for n in ("lbg_train", "lbg_lloyd_step", "vq_encode", "lbg_status_string"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert isinstance(getattr(lib, name), ctypes._CFuncPtr)
+
+
+def test_status_strings_and_version(lib):
+    assert lib.lbg_version() == 1
+    for s in (0, 1, -1, -2, -3, -4, -5, -6, -7):
+        assert lib.lbg_status_string(s)
+
+
+def _err(fn, *args):
+    with pytest.raises(lbgvq.LBGError) as ei:
+        fn(*args)
+    return ei.value.status
+
+
+def test_train_rejects_bad_arguments(lib):
+    X = np.zeros((8, 4), np.float32)
+    assert _err(lbgvq.lbg_train, X, 3) == -2          # N not a power of 2
+    assert _err(lbgvq.lbg_train, X, 0) == -1
+    assert _err(lbgvq.lbg_train, X, 2 * 8192) == -1   # above LBG_MAX_CODEBOOK
+    assert _err(lbgvq.lbg_train, X, 4, -0.5) == -1    # delta < 0
+    assert _err(lbgvq.lbg_train, X, 4, 0.1, -1.0) == -1
+    assert _err(lbgvq.lbg_train, X, 4, 0.1, float("nan")) == -1
+    assert _err(lbgvq.lbg_train, np.zeros((8, 129), np.float32), 4) == -1   # L > LBG_MAX_DIM
+    assert _err(lbgvq.lbg_train, np.zeros((0, 4), np.float32), 4) == -1     # M = 0
+    assert _err(lbgvq.lbg_train, X, 4, 0.1, 0.1, np.zeros((3, 4), np.float32)) == -2  # n_init
+
+
+def test_step_and_encode_reject_bad_arguments(lib):
+    X = np.zeros((8, 4), np.float32)
+    assert _err(lbgvq.lbg_lloyd_step, np.zeros((8, 0), np.float32), np.zeros((2, 0), np.float32)) == -1
+    assert _err(lbgvq.vq_encode, X, np.zeros((0, 4), np.float32)) == -1
+    assert _err(lbgvq.vq_encode, X, np.zeros((9000, 4), np.float32)) == -1
+    P = ctypes.c_void_p
+    # null codebook through the raw ABI
+    assert lib.vq_encode(None, 8, 4, None, 2, None, None, None, None) == -1
+    assert lib.lbg_lloyd_step(None, 8, 4, 2, None, None, None, None, None) == -1

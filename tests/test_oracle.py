@@ -199,6 +199,26 @@ def test_max_passes_cap_warns_and_continues():
     assert t.D == pytest.approx(9005 / 144, rel=1e-15)
 
 
+def test_initial_alphabet_resume():
+    """Starting from A_0 = the centroid (Sec. 2.2 Initialization) is the
+    default run; starting from a finished stage's codebook runs that stage's
+    Lloyd iteration again and then continues the splits."""
+    X, _ = _random_problem(30, M=1500, L=3)
+    t = oracle.lbg_train(X, 16, 0.01, 1e-3)
+    t1 = oracle.lbg_train(X, 16, 0.01, 1e-3, C_init=oracle.mean(X))
+    np.testing.assert_array_equal(t.C, t1.C)
+    np.testing.assert_array_equal(t.trace_D, t1.trace_D)
+    # uniform quantizer: resuming from the finished N/2 codebook ends at the same closed form
+    M = 64
+    U = np.arange(M, dtype=np.float32)[:, None]
+    half = oracle.lbg_train(U, 4, 0.25, 1e-3)
+    full = oracle.lbg_train(U, 8, 0.25, 1e-3, C_init=half.C)
+    w = 8
+    mids = np.array([(c * w + (c + 1) * w - 1) / 2.0 for c in range(8)])[::-1]
+    np.testing.assert_array_equal(full.C[:, 0], mids)
+    assert full.passes_per_stage() == [2, 3]
+
+
 def test_arguments_rejected():
     X = np.zeros((4, 2), np.float32)
     with pytest.raises(ValueError):
