@@ -1,0 +1,377 @@
+"""Benchmark of one Lloyd pass of LBG on image-block data (one GB300 per rank).
+
+Workload (default ``img2048x8_b8_n4096``): eight seeded synthetic 2048x2048
+8-bit images cut into 8x8 blocks -> X [524288 x 64] float32, codebook grown by
+splitting to N = 4096 (delta = 0.01, theta = 1e-3).
+
+A *step* is one Lloyd pass through the C ABI (``lbg_lloyd_step``): cell
+allocation of all M rows against the trained N = 4096 codebook, integration
+of the distortion, cell table and centroid update -- every kernel of the hot
+path.  ``value`` = M * N distance evaluations / device time per step.
+
+Other legs in the same run:
+* full LBG design time (``lbg_train`` from the centroid to N = 4096);
+* ``e2e``: the same step through the C ABI with HOST buffers (pinned), the
+  host->device copy of X and C and the device->host read of C, the cell
+  table and D inside the timed region;
+* ``roofline``: the nearest-codevector kernel, FP32 FFMA work 2*L*M*N per
+  launch over its CUDA-event time, against the FP32 CUDA-core peak
+  152 SMs x 128 FP32 lanes x 2 flop x max SM clock;
+* ``cpu_baseline``: the FP64 oracle's Lloyd pass on a bounded row sample on
+  the host cores.
+``--impl reference`` times only the oracle (the baseline arm).
+With ``--gpus N`` (under torchrun) every rank runs an independent replica.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "vector·codevector distance evals/s per Lloyd pass; full LBG time, bf16 vs fp32"
+UNIT = "evals/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="img2048x8_b8_n4096")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="target wall time of the CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_desc(name, X, N):
+    w = {"img2048x8_b8_n4096": "8 synthetic 2048x2048 8-bit images, 8x8 blocks",
+         "img512_b4_n256": "1 synthetic 512x512 8-bit image, 4x4 blocks",
+         "img2048x64_b4_n4096": "64 synthetic 2048x2048 8-bit images, 4x4 blocks"}[name]
+    return f"{name}: {w}, M={X.shape[0]}, L={X.shape[1]}, N={N}, delta=0.01, theta=1e-3"
+
+
+# ------------------------------------------------------------------ distributed
+def dist_setup(n):
+    if n <= 1 or "RANK" not in os.environ:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    rank, world = int(os.environ["RANK"]), int(os.environ["WORLD_SIZE"])
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
+    dist.init_process_group("nccl")
+    return rank, world, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, v):
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+def gpu_uuid(dev):
+    """nvidia-smi id of the CUDA device `dev` (its UUID; the box may list other GPUs)."""
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        return vis.split(",")[dev] if vis else str(dev)
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}",
+                                       f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.p is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1].split()[0]), float(parts[2].split()[0]),
+                             parts[5], parts[6], parts[7], parts[8], parts[3]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[2 + k] == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+# ------------------------------------------------------------------ cpu baseline
+def cpu_baseline(X, C, seconds, seed=0):
+    """FP64 oracle Lloyd pass (allocation + distortion + updation) on a row
+    sample of X against C, on all host cores; sample grown to ~`seconds`."""
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    Cd = np.asarray(C, np.float64)
+    # calibrate on 1024 rows, then time one sample sized to take ~`seconds`
+    S = np.ascontiguousarray(X[np.sort(rng.choice(X.shape[0], min(1024, X.shape[0]), replace=False))])
+    t0 = time.perf_counter()
+    oracle.lloyd_step(S, Cd)
+    t1 = time.perf_counter() - t0
+    rows = int(min(X.shape[0], max(1024, 1024 * seconds / max(t1, 1e-4))))
+    idx = np.sort(rng.choice(X.shape[0], rows, replace=False))
+    S = np.ascontiguousarray(X[idx])
+    t0 = time.perf_counter()
+    oracle.lloyd_step(S, Cd)
+    t = time.perf_counter() - t0
+    evals = S.shape[0] * Cd.shape[0]
+    return {"value": evals / t, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "seconds": t,
+            "sample": (f"one FP64 oracle Lloyd pass (allocation, distortion, updation) over "
+                       f"{S.shape[0]} random rows of the same X against the same N={Cd.shape[0]} "
+                       f"codebook")}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_0910_4711_gb300 import synth
+    import oracle
+    oracle.build()
+    X, N = synth.workload(args.workload)
+    rng = np.random.default_rng(7)
+    C = X[rng.choice(X.shape[0], N, replace=False)].astype(np.float64)
+    # size each step's row sample so one step takes ~ a few seconds
+    rows = 256
+    while True:
+        S = X[:rows]
+        t0 = time.perf_counter()
+        oracle.lloyd_step(S, C)
+        t = time.perf_counter() - t0
+        if t > 1.0 or rows >= 65536:
+            break
+        rows *= 2
+    for _ in range(args.warmup):
+        oracle.lloyd_step(X[:rows], C)
+    times = []
+    for k in range(args.steps):
+        lo = (k * rows) % max(1, X.shape[0] - rows)
+        S = np.ascontiguousarray(X[lo:lo + rows])
+        t0 = time.perf_counter()
+        oracle.lloyd_step(S, C)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = rows * N / (ms / 1e3)
+    sample = (f"each step: one FP64 oracle Lloyd pass over {rows} consecutive rows of X against an "
+              f"N={N} codebook of seeded rows of X (a trained codebook needs the GPU)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_desc(args.workload, X, N), "rows_per_step": rows},
+            "cpu_baseline": {"kind": "oracle", "cores": oracle.max_threads(), "sample": sample,
+                             "value": value, "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    rank, world, dist = dist_setup(args.gpus)
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}))
+        return 1
+    dev = torch.cuda.current_device()
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_0910_4711_gb300 as lbg
+    from paper_0910_4711_gb300 import synth
+
+    X_np, N = synth.workload(args.workload)
+    M, L = X_np.shape
+    X = torch.from_numpy(X_np).cuda()
+    stream = torch.cuda.current_stream()
+
+    # full LBG design (also produces the codebook the step runs against)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tr = lbg.lbg_train(X, N, delta=0.01, theta=1e-3, trace=100000)
+    torch.cuda.synchronize()
+    full_lbg_s = time.perf_counter() - t0
+    C = tr.C.clone()
+    C_out = torch.empty_like(C)
+    A = torch.empty(M, dtype=torch.int32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step(phases):
+        r = lbg.lbg_lloyd_step(X, C, C_out=C_out, assign_out=A, phase_ms=True)
+        phases.append(r.phase_ms)
+        return r
+
+    scratch = []
+    for _ in range(max(3, args.warmup)):
+        flush.zero_()
+        step(scratch)
+    torch.cuda.synchronize()
+    phases, ev_ms, n_exact = [], [], []
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(gpu_uuid(dev)) as clk:
+        barrier(dist)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed_steps")
+        w0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            r = step(phases)
+            ends[k].record(stream)
+            n_exact.append(r.n_exact)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        torch.cuda.nvtx.range_pop()
+        barrier(dist)
+    ev_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = statistics.mean(ev_ms)
+    ms = max_over_ranks(dist, ms)
+    value = world * M * N / (ms / 1e3)
+
+    assign_ms = statistics.mean(p["assign"] for p in phases)
+    update_ms = statistics.mean(p["update"] for p in phases)
+    exact_ms = statistics.mean(p["exact"] for p in phases)
+    prep_ms = statistics.mean(p["prep"] for p in phases)
+    clocks = clk.summary()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+    flops = 2.0 * L * M * N
+    achieved = flops / (assign_ms / 1e3) / 1e12
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    upd_bytes = M * L * 4 + M * 4 + N * L * 4 + N * 4
+    upd_gbs = upd_bytes / (update_ms / 1e3) / 1e9
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(args.workload, X_np, N), "M": M, "L": L, "N": N,
+                       "precision": "fp32",
+                       "step": "one Lloyd pass (lbg_lloyd_step) against the trained N-entry codebook",
+                       "l2": f"flushed: {L2_FLUSH_BYTES >> 20} MiB device write between steps",
+                       "full_lbg_s": full_lbg_s, "full_lbg_passes": tr.n_passes,
+                       "full_lbg_passes_per_stage": tr.passes_per_stage(),
+                       "full_lbg_D": tr.D, "exact_rows_per_step": statistics.mean(n_exact),
+                       "phase_ms": {"prep": prep_ms, "assign": assign_ms, "exact": exact_ms,
+                                    "update": update_ms},
+                       "wall_s_timed_region": wall, "data_sha256": synth.digest(X_np)[:16],
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "alu", "kernel": "k_assign_f32",
+                         "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak, "traffic": None,
+                         "peak_source": f"FP32 CUDA cores: {SM_COUNT} SMs x {FP32_LANES_PER_SM} "
+                                        f"lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
+                         "work": "2*L*M*N flop per launch"},
+            "update_roofline": {"bound": "hbm", "achieved": upd_gbs, "peak": hbm, "unit": "GB/s",
+                                "frac": upd_gbs / hbm, "bytes": upd_bytes,
+                                "work": "M*L*4 + M*4 + N*L*4 + N*4 bytes (read X, cell table; "
+                                        "write codebook, counts)",
+                                "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+            "clocks": clocks,
+            "gpu_launches": 11 * args.steps}
+
+    # end to end through the public API with host buffers
+    if not args.no_e2e:
+        Xh = torch.from_numpy(X_np).pin_memory()
+        Ch = tr.C.cpu().pin_memory()
+        Coh = torch.empty_like(Ch).pin_memory()
+        Ah = torch.empty(M, dtype=torch.int32).pin_memory()
+        for _ in range(2):
+            lbg.lbg_lloyd_step(Xh, Ch, C_out=Coh, assign_out=Ah)
+        times = []
+        for _ in range(max(3, min(args.steps, 10))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = lbg.lbg_lloyd_step(Xh, Ch, C_out=Coh, assign_out=Ah)
+            times.append(time.perf_counter() - t0)
+        e2e_s = max_over_ranks(dist, statistics.mean(times))
+        line["e2e"] = {"value": world * M * N / e2e_s, "unit": UNIT,
+                       "h2d_bytes_per_step": M * L * 4 + N * L * 4,
+                       "d2h_bytes_per_step": N * L * 4 + M * 4 + 8,
+                       "ms_per_step": 1e3 * e2e_s}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(X_np, tr.C.cpu().numpy(), args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

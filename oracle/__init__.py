@@ -77,7 +77,7 @@ def _load():
         lib.oracle_distortion_fixed.restype = f64
         lib.oracle_grad.argtypes = [P, i64, i32, P, i32, P, P, P]
         lib.oracle_lbg_train.argtypes = [P, i64, i32, i32, f64, f64, i32, i32, P, i32, P, P,
-                                         P, P, P, P, i32, P]
+                                         P, P, P, P, P, f64, i32, P]
         _lib = lib
         return lib
 
@@ -205,6 +205,11 @@ class Train:
     trace_n: np.ndarray = field(default_factory=lambda: np.empty(0, np.int32))
     trace_pass: np.ndarray = field(default_factory=lambda: np.empty(0, np.int32))
     trace_D: np.ndarray = field(default_factory=lambda: np.empty(0, np.float64))
+    trace_near: np.ndarray = field(default_factory=lambda: np.empty(0, np.int32))
+
+    def near_ties(self) -> int:
+        """Rows that were near-ties (gap <= near_tol), summed over all passes."""
+        return int(self.trace_near.sum())
 
     def passes_per_stage(self):
         """Number of passes run at each stage size, in stage order."""
@@ -217,7 +222,8 @@ class Train:
 
 
 def lbg_train(X, N: int, delta: float, theta: float, max_passes: int = 1000,
-              nthreads: int = 0, trace_cap: int = 100000, C_init=None) -> Train:
+              nthreads: int = 0, trace_cap: int = 100000, C_init=None,
+              near_tol: float = 1e-5) -> Train:
     """The whole LBG design up to N codevectors, from the centroid of X or,
     if C_init ([n_init, L]) is given, from that initial alphabet (Sec. 2.2)."""
     X = _x(X)
@@ -230,12 +236,13 @@ def lbg_train(X, N: int, delta: float, theta: float, max_passes: int = 1000,
     rn = np.empty(trace_cap, np.int32)
     rp = np.empty(trace_cap, np.int32)
     rD = np.empty(trace_cap, np.float64)
+    rnear = np.empty(trace_cap, np.int32)
     cnt = ctypes.c_int32()
     rc = _load().oracle_lbg_train(_ptr(X), M, L, int(N), float(delta), float(theta),
                                   int(max_passes), int(nthreads), _ptr(Ci), n_init, _ptr(C),
                                   _ptr(a),
-                                  ctypes.byref(D), _ptr(rn), _ptr(rp), _ptr(rD), trace_cap,
-                                  ctypes.byref(cnt))
+                                  ctypes.byref(D), _ptr(rn), _ptr(rp), _ptr(rD), _ptr(rnear),
+                                  float(near_tol), trace_cap, ctypes.byref(cnt))
     _check(rc, "lbg_train")
     k = min(cnt.value, trace_cap)
-    return Train(rc, C, a, D.value, rn[:k].copy(), rp[:k].copy(), rD[:k].copy())
+    return Train(rc, C, a, D.value, rn[:k].copy(), rp[:k].copy(), rD[:k].copy(), rnear[:k].copy())

@@ -274,14 +274,17 @@ static int is_pow2(int32_t n) { return n > 0 && (n & (n - 1)) == 0; }
  *           else C <- centroids of the cells; D_prev <- D; next pass
  *     if n == N: stop; else C <- split(C); n <- 2n; next stage
  * Outputs: C_out [N x L] (double), a_out [M], D_out.  Optional pass trace:
- * rec_n (stage size), rec_pass (pass index within the stage), rec_D, up to
- * rec_cap records; rec_count receives the number of passes run (which may
- * exceed rec_cap).  Returns 0, 1 (WARN_MAXPASS) or a negative error. */
+ * rec_n (stage size), rec_pass (pass index within the stage), rec_D and
+ * rec_near (rows of the pass whose relative gap is <= near_tol, i.e. whose
+ * nearest codevector is a near-tie), up to rec_cap records; rec_count
+ * receives the number of passes run (which may exceed rec_cap).  Returns 0,
+ * 1 (WARN_MAXPASS) or a negative error. */
 int oracle_lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double delta,
                      double theta, int32_t max_passes, int32_t nthreads,
                      const double *C_init, int32_t n_init, double *C_out,
                      int32_t *a_out, double *D_out, int32_t *rec_n, int32_t *rec_pass,
-                     double *rec_D, int32_t rec_cap, int32_t *rec_count)
+                     double *rec_D, int32_t *rec_near, double near_tol, int32_t rec_cap,
+                     int32_t *rec_count)
 {
     if (!X || !C_out || !a_out || !D_out || M < 1 || L < 1 || N < 1 || max_passes < 1)
         return ORACLE_ERR_ARG;
@@ -293,10 +296,12 @@ int oracle_lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double del
     double *C = (double *)malloc((size_t)N * L * sizeof(double));
     double *Cn = (double *)malloc((size_t)N * L * sizeof(double));
     double *e = (double *)malloc((size_t)M * sizeof(double));
-    if (!C || !Cn || !e) {
+    double *gap = rec_near ? (double *)malloc((size_t)M * sizeof(double)) : NULL;
+    if (!C || !Cn || !e || (rec_near && !gap)) {
         free(C);
         free(Cn);
         free(e);
+        free(gap);
         return ORACLE_ERR_NOMEM;
     }
     int status = ORACLE_OK;
@@ -311,12 +316,17 @@ int oracle_lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double del
     for (;;) {
         double D_prev = INFINITY;
         for (int32_t pass = 0;; ++pass) {
-            oracle_assign(X, M, L, C, n, a_out, e, NULL, nthreads);
+            oracle_assign(X, M, L, C, n, a_out, e, gap, nthreads);
             D = oracle_sum(e, M);
             if (rec_count && total < rec_cap) {
                 if (rec_n) rec_n[total] = n;
                 if (rec_pass) rec_pass[total] = pass;
                 if (rec_D) rec_D[total] = D;
+                if (rec_near) {
+                    int32_t near = 0;
+                    for (int64_t m = 0; m < M; ++m) near += gap[m] <= near_tol;
+                    rec_near[total] = near;
+                }
             }
             ++total;
             int done = (D == 0.0) || ((D_prev - D) / D <= theta);
@@ -340,5 +350,6 @@ int oracle_lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double del
     free(C);
     free(Cn);
     free(e);
+    free(gap);
     return status;
 }

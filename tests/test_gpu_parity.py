@@ -215,7 +215,8 @@ def test_train_image_blocks_matches_oracle(lbg):
     check_assign(X, C, host(r.assign), a_ref, e_ref, gap)
     check_D(r.D, float(e_ref.sum()))
     t = oracle.lbg_train(X, 64, 0.01, 1e-3)
-    if r.passes_per_stage() == t.passes_per_stage():
+    if t.near_ties() == 0:
+        assert r.passes_per_stage() == t.passes_per_stage()
         check_codebook(C, t.C)
         check_D(r.D, t.D)
     sizes = [rec["stage_n"] for rec in r.records if rec["pass"] == 0]
@@ -235,15 +236,19 @@ def test_train_resume_from_codebook(lbg):
     a_ref, e_ref, gap = oracle.assign(X, C.astype(np.float64))
     check_assign(X, C, host(res.assign), a_ref, e_ref, gap)
     check_D(res.D, float(e_ref.sum()))
-    if res.passes_per_stage() == t.passes_per_stage():
+    if t.near_ties() == 0:
+        assert res.passes_per_stage() == t.passes_per_stage()
         check_codebook(C, t.C)
 
 
 def test_train_fewer_rows_than_codevectors(lbg):
+    """M < N: most cells end empty and keep split copies c +- delta, which tie
+    exactly; a dyadic delta keeps those ties exact in FP32 too, so the whole
+    run must match the oracle (ties to the lowest index on both sides)."""
     rng = np.random.default_rng(4)
     X = rng.integers(0, 50, (20, 8)).astype(np.float32)
-    r = lbg.lbg_train(dev(X), 64, 0.01, 1e-3)
-    t = oracle.lbg_train(X, 64, 0.01, 1e-3)
+    r = lbg.lbg_train(dev(X), 64, 0.25, 1e-3)
+    t = oracle.lbg_train(X, 64, 0.25, 1e-3)
     assert r.passes_per_stage() == t.passes_per_stage()
     check_codebook(host(r.C), t.C)
     check_D(r.D, t.D)
