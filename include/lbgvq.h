@@ -158,6 +158,37 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N,
 lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32_t N,
                      int32_t *idx, float *Xhat, double *D, const lbg_opts *opts);
 
+/*
+ * vq_encode_noalloc -- vq_encode for callers that cannot allocate device
+ * memory.  (The paper has no counterpart: it concerns how this library gets
+ * its scratch, not the method.)
+ *
+ * Who needs it: a serving loop that reserved its device memory up front and
+ * must not pay for, or be stalled by, a cudaMalloc in steady state
+ * (cudaMalloc can synchronise the device); a process whose framework
+ * allocator already holds nearly all device memory, so a raw cudaMalloc
+ * would fail; code that may allocate only during initialisation.  vq_encode
+ * and the other entry points grow a cached workspace with cudaMalloc; this
+ * one calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Its scratch is one fixed 16 MiB __device__ array inside the library, held
+ * on every GPU that loads the library until the process exits.  The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress
+ * with the device current); make that first call before any stream capture.
+ * All calls share the array and each re-initialises what it needs, so calls
+ * whose work overlaps on the GPU (other streams, other host threads) race.
+ *
+ *   X     [M x L] DEVICE array; M >= 0 (any size: processed in chunks).
+ *   C     [N x L] DEVICE codebook.
+ *   idx   [M] DEVICE out: nearest codevector (same rule as vq_encode).
+ *   D     host out, nullable: sum of the squared distances.
+ *   stream  cudaStream_t (NULL = legacy default stream); synchronised before return.
+ * Limits of the fixed scratch: N <= 4096 and L <= 128; larger sizes return
+ * LBG_ERR_UNSUPPORTED.  Host pointers return LBG_ERR_ARG.
+ */
+lbg_status vq_encode_noalloc(const float *X, int64_t M, int32_t L, const float *C, int32_t N,
+                             int32_t *idx, double *D, void *stream);
+
 /* Human-readable text of a status code (static storage). */
 const char *lbg_status_string(lbg_status s);
 
