@@ -41,76 +41,106 @@ namespace {
 
 constexpr float U32 = 5.9604644775390625e-8f;   // 2^-24
 constexpr float SLOP = 1.0000305175781250f;     // 1 + 2^-15, covers FP32 evaluation of bounds
-constexpr int EX_ROWS = 4;                      // flagged rows per warp in k_assign_exact
-constexpr int EX_WARPS = 8;
+constexpr int EX_R = 8;                         // flagged rows per CTA group in k_assign_exact
+constexpr int EX_SW = 128;                      // codevectors per staged chunk (= BN)
+constexpr int EX_THREADS = 256;
 
 __device__ __forceinline__ int cur_n(const int32_t *n_dev, int n_host)
 {
     return n_dev ? *n_dev : n_host;
 }
 
-// mu[l] = mean over the N codevectors (FP32 partials, FP64 final); used as
-// the centring vector of lbg_lloyd_step / vq_encode.  One CTA of 1024.
-__global__ void __launch_bounds__(1024) k_codebook_mean(const float *__restrict__ C, int N, int L,
-                                                        float *__restrict__ mu)
+// mu[l] = mean over the N codevectors (fixed-order FP32 tree); the centring
+// vector of lbg_lloyd_step / vq_encode.  One CTA of 256 threads per dimension.
+__global__ void __launch_bounds__(256) k_codebook_mean(const float *__restrict__ C, int N, int L,
+                                                       float *__restrict__ mu)
 {
-    __shared__ float part[1024];
-    const int per = 1024 / L;
-    const int t = threadIdx.x;
-    const int l = t % L, r = t / L;
+    __shared__ float part[256];
+    const int l = blockIdx.x, t = threadIdx.x;
     float s = 0.f;
-    if (r < per)
-        for (int n = r; n < N; n += per) s += C[(size_t)n * L + l];
+    for (int n = t; n < N; n += 256) s += C[(size_t)n * L + l];
     part[t] = s;
     __syncthreads();
-    if (t < L) {
-        double acc = 0.0;
-        for (int q = 0; q < per; ++q) acc += part[q * L + t];
-        mu[t] = (float)(acc / (double)N);
+    for (int h = 128; h > 0; h >>= 1) {
+        if (t < h) part[t] += part[t + h];
+        __syncthreads();
     }
+    if (t == 0) mu[l] = part[0] / (float)N;
 }
 
 // Prepared codebook, chunk-major: chunk k holds (Lp + 1) x BN floats; row 0
 // is the chain start s0_n = fl(||c~_n||^2 - k_n) (+inf for padding), rows
-// 1..Lp are -2 c~_{n,l} (0 for l >= L or padding).  Also writes k_n,
-// the original codebook transposed CT[l][n] (stride NP) for the exact
-// fallback, max ||c~_n|| into st->cmax_bits, and flags non-finite entries.
-__global__ void k_prep(const float *__restrict__ C, const int32_t *n_dev, int n_host, int L, int Lp,
-                       const float *__restrict__ mu, float *__restrict__ Cp, float *__restrict__ kn,
-                       float *__restrict__ CT, int NP, DevState *st)
+// 1..Lp are -2 c~_{n,l} (0 for l >= L or padding).  Also writes k_n, the
+// original codebook in chunks of EX_SW codevectors, k-major inside a chunk
+// (CT[(n / EX_SW) * Lp + l][n % EX_SW]) for the exact fallback, max ||c~_n||
+// into st->cmax_bits, and flags non-finite entries.
+// A CTA takes PREP_TILE codevectors: coalesced row loads into shared memory,
+// FP64 norms (warp per codevector, fixed shuffle tree), coalesced transposed
+// stores.
+constexpr int PREP_TILE = 32;
+
+__global__ void __launch_bounds__(256)
+    k_prep(const float *__restrict__ C, const int32_t *n_dev, int n_host, int L, int Lp,
+           const float *__restrict__ mu, float *__restrict__ Cp, float *__restrict__ kn,
+           float *__restrict__ CT, int NP, DevState *st)
 {
     if (st->finished) return;
+    __shared__ float orig[PREP_TILE][LMAX + 1];
+    __shared__ float cen[PREP_TILE][LMAX + 1];
+    __shared__ double sqs[PREP_TILE];
     const int N = cur_n(n_dev, n_host);
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
     const int npad = round_up(N, BN);
-    if (n >= npad) return;
-    const int chunk = n / BN, j = n % BN;
-    float *blk = Cp + (size_t)chunk * (Lp + 1) * BN;
-    if (n < N) {
-        double sq = 0.0;
-        bool finite = true;
-        for (int l = 0; l < L; ++l) {
-            const float c = C[(size_t)n * L + l];
+    const int n0 = blockIdx.x * PREP_TILE;
+    if (n0 >= npad) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    bool finite = true;
+    for (int i = tid; i < PREP_TILE * L; i += 256) {
+        const int j = i / L, l = i - (i / L) * L;
+        const int n = n0 + j;
+        float c = 0.f, v = 0.f;
+        if (n < N) {
+            c = C[(size_t)n * L + l];
             finite = finite && isfinite(c);
-            const float ct = c - mu[l];
-            blk[(size_t)(1 + l) * BN + j] = -2.0f * ct;
-            CT[(size_t)l * NP + n] = c;
-            sq += (double)ct * (double)ct;
+            v = c - mu[l];
         }
-        for (int l = L; l < Lp; ++l) {
-            blk[(size_t)(1 + l) * BN + j] = 0.f;
-            CT[(size_t)l * NP + n] = 0.f;
+        orig[j][l] = c;
+        cen[j][l] = v;
+    }
+    if (!finite) flag_error(st, ERR_NONFINITE);
+    __syncthreads();
+    for (int j = warp; j < PREP_TILE; j += 8) {
+        double sq = 0.0;
+        for (int l = lane; l < L; l += 32) {
+            const double v = cen[j][l];
+            sq += v * v;
         }
-        if (!finite) flag_error(st, ERR_NONFINITE);
-        const double k = 2.0 * (double)(L + 2) * 5.9604644775390625e-8 * sq;
-        const float kf = __double2float_ru(k);
-        blk[j] = __double2float_rn(sq - (double)kf);
-        kn[n] = kf;
-        atomicMax(&st->cmax_bits, __float_as_uint(__double2float_ru(sqrt(sq))));
-    } else {
-        blk[j] = INFINITY;
-        for (int l = 0; l < Lp; ++l) blk[(size_t)(1 + l) * BN + j] = 0.f;
-        kn[n] = 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (lane == 0) sqs[j] = sq;
+    }
+    __syncthreads();
+    if (tid < PREP_TILE) {
+        const int n = n0 + tid;
+        float *blk = Cp + (size_t)(n / BN) * (Lp + 1) * BN;
+        if (n < N) {
+            const double sq = sqs[tid];
+            const double k = 2.0 * (double)(L + 2) * 5.9604644775390625e-8 * sq;
+            const float kf = __double2float_ru(k);
+            blk[n % BN] = __double2float_rn(sq - (double)kf);
+            kn[n] = kf;
+            atomicMax(&st->cmax_bits, __float_as_uint(__double2float_ru(sqrt(sq))));
+        } else if (n < npad) {
+            blk[n % BN] = INFINITY;
+            kn[n] = 0.f;
+        }
+    }
+    for (int i = tid; i < Lp * PREP_TILE; i += 256) {
+        const int l = i / PREP_TILE, j = i % PREP_TILE;
+        const int n = n0 + j;
+        if (n >= npad) continue;
+        const bool real = n < N && l < L;
+        Cp[(size_t)(n / BN) * (Lp + 1) * BN + (size_t)(1 + l) * BN + n % BN] = real ? -2.0f * cen[j][l] : 0.f;
+        CT[((size_t)(n / EX_SW) * Lp + l) * EX_SW + n % EX_SW] = real ? orig[j][l] : 0.f;
     }
 }
 
@@ -356,59 +386,115 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 2)
 }
 
 // Exact FP32 direct-form re-scoring of the rows k_assign_f32 could not
-// certify: d = sum_l (x_l - c_l)^2 in index order for every codevector,
-// minimum with the lowest index on ties.  A warp takes EX_ROWS rows so each
-// codebook value read serves several rows; lanes stride the codevectors
-// (coalesced reads of the transposed codebook CT).
-__global__ void __launch_bounds__(EX_WARPS * 32)
-    k_assign_exact(const float *__restrict__ X, int L, const float *__restrict__ CT, int NP,
+// certify: d = sum_l (x_l - c_l)^2 in index order (the same expression as a
+// certified row's e), minimum with the lowest index on ties.  A CTA takes a
+// group of EX_R flagged rows (k-major in shared memory) and streams the
+// original codebook through two shared buffers of EX_SW codevectors (one TMA
+// bulk copy each, bounded mbarrier waits); thread t scores codevector
+// t % EX_SW of each chunk against rows 4 * (t / EX_SW) .. + 3.  The
+// (distance, index) minimum is reduced in a fixed order (shuffles, then the
+// warps of a row half in order).
+__global__ void __launch_bounds__(EX_THREADS)
+    k_assign_exact(const float *__restrict__ X, int L, int Lp, const float *__restrict__ CT,
                    const int32_t *n_dev, int n_host, DevState *st, const int32_t *__restrict__ flags,
                    int32_t *__restrict__ assign, float *__restrict__ e)
 {
     if (st->finished) return;
-    __shared__ float xsh[EX_WARPS][EX_ROWS][LMAX];
     const int nflag = st->nflag;
+    if (nflag == 0) return;
+    extern __shared__ __align__(128) float cbuf[];   // [2][Lp][EX_SW]
+    __shared__ __align__(16) float xs[LMAX][EX_R];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_abort;
+    __shared__ float rb[EX_THREADS / 32][4];
+    __shared__ int ri[EX_THREADS / 32][4];
     const int N = cur_n(n_dev, n_host);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ngroups = (nflag + EX_ROWS - 1) / EX_ROWS;
-    for (int g = blockIdx.x * EX_WARPS + warp; g < ngroups; g += gridDim.x * EX_WARPS) {
-        const int nr = min(EX_ROWS, nflag - g * EX_ROWS);
-        int rows[EX_ROWS];
+    const int nchunk = (N + EX_SW - 1) / EX_SW;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int j = tid % EX_SW, half = tid / EX_SW;
+    const uint32_t chunk_floats = (uint32_t)Lp * EX_SW;
+    const uint32_t chunk_bytes = chunk_floats * 4u;
+    const int ngroups = (nflag + EX_R - 1) / EX_R;
+    if ((int)blockIdx.x >= ngroups) return;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    uint32_t uses[2] = {0u, 0u};   // completed phases of each buffer's barrier
+    for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
+        const int nr = min(EX_R, nflag - g * EX_R);
+        for (int i = tid; i < EX_R * L; i += EX_THREADS) {
+            const int r = i % EX_R, l = i / EX_R;
+            xs[l][r] = r < nr ? X[(int64_t)flags[g * EX_R + r] * L + l] : 0.f;
+        }
+        if (tid == 0)
+            for (int k = 0; k < 2 && k < nchunk; ++k) {
+                mbar_expect_tx(&bar[k], chunk_bytes);
+                bulk_load(cbuf + k * chunk_floats, CT + (size_t)k * chunk_floats, chunk_bytes, &bar[k]);
+            }
+        __syncthreads();
+        float best[4];
+        int bi[4];
 #pragma unroll
-        for (int q = 0; q < EX_ROWS; ++q) rows[q] = (q < nr) ? flags[g * EX_ROWS + q] : -1;
-#pragma unroll
-        for (int q = 0; q < EX_ROWS; ++q)
-            for (int l = lane; l < L; l += 32)
-                xsh[warp][q][l] = rows[q] >= 0 ? X[(int64_t)rows[q] * L + l] : 0.f;
-        __syncwarp();
-        float best[EX_ROWS];
-        int bi[EX_ROWS];
-#pragma unroll
-        for (int q = 0; q < EX_ROWS; ++q) {
+        for (int q = 0; q < 4; ++q) {
             best[q] = INFINITY;
             bi[q] = 0x7fffffff;
         }
-        for (int n = lane; n < N; n += 32) {
-            float d2[EX_ROWS];
-#pragma unroll
-            for (int q = 0; q < EX_ROWS; ++q) d2[q] = 0.f;
-            for (int l = 0; l < L; ++l) {
-                const float c = __ldg(CT + (size_t)l * NP + n);
-#pragma unroll
-                for (int q = 0; q < EX_ROWS; ++q) {
-                    const float d = xsh[warp][q][l] - c;
-                    d2[q] = fmaf(d, d, d2[q]);
+        int k_stop = nchunk;
+        for (int k = 0; k < nchunk; ++k) {
+            const int b = k & 1;
+            const bool ok = mbar_wait_bounded(&bar[b], uses[b] & 1u);
+            uses[b] += 1u;
+            if (!ok) s_abort = 1;
+            const float *cb = cbuf + b * chunk_floats;
+            const int n = k * EX_SW + j;
+            if (ok && n < N) {
+                float d2[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+                for (int l = 0; l < L; ++l) {
+                    const float c = cb[l * EX_SW + j];
+                    const float4 x4 = lds4(&xs[l][half * 4]);
+                    float d = x4.x - c;
+                    d2[0] = fmaf(d, d, d2[0]);
+                    d = x4.y - c;
+                    d2[1] = fmaf(d, d, d2[1]);
+                    d = x4.z - c;
+                    d2[2] = fmaf(d, d, d2[2]);
+                    d = x4.w - c;
+                    d2[3] = fmaf(d, d, d2[3]);
                 }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (d2[q] < best[q]) {
+                        best[q] = d2[q];
+                        bi[q] = n;
+                    }
             }
-#pragma unroll
-            for (int q = 0; q < EX_ROWS; ++q)
-                if (d2[q] < best[q]) {
-                    best[q] = d2[q];
-                    bi[q] = n;
-                }
+            __syncthreads();
+            if (s_abort) {
+                k_stop = k;
+                break;
+            }
+            if (tid == 0 && k + 2 < nchunk) {
+                mbar_expect_tx(&bar[b], chunk_bytes);
+                bulk_load(cbuf + b * chunk_floats, CT + (size_t)(k + 2) * chunk_floats, chunk_bytes,
+                          &bar[b]);
+            }
+        }
+        if (k_stop < nchunk) {
+            if (tid == 0) {
+                for (int kk = k_stop + 1; kk < nchunk && kk < k_stop + 2; ++kk)
+                    (void)mbar_wait_bounded(&bar[kk & 1], uses[kk & 1] & 1u);
+                flag_error(st, ERR_TIMEOUT);
+            }
+            return;
         }
 #pragma unroll
-        for (int q = 0; q < EX_ROWS; ++q) {
+        for (int q = 0; q < 4; ++q) {
+#pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const float ob = __shfl_xor_sync(0xffffffffu, best[q], o);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi[q], o);
@@ -417,16 +503,28 @@ __global__ void __launch_bounds__(EX_WARPS * 32)
                     bi[q] = oi;
                 }
             }
-        }
-        if (lane == 0) {
-            for (int q = 0; q < nr; ++q) {
-                const bool valid = bi[q] >= 0 && bi[q] < N;
-                if (!valid) flag_error(st, ERR_NONFINITE);   // only NaN rows compare false everywhere
-                assign[rows[q]] = valid ? bi[q] : 0;
-                e[rows[q]] = valid ? best[q] : 0.f;
+            if (lane == 0) {
+                rb[warp][q] = best[q];
+                ri[warp][q] = bi[q];
             }
         }
-        __syncwarp();
+        __syncthreads();
+        if (tid < nr) {
+            const int hw = (tid / 4) * (EX_SW / 32), q = tid % 4;   // first warp of the row's half
+            float bb = rb[hw][q];
+            int ii = ri[hw][q];
+            for (int w = hw + 1; w < hw + EX_SW / 32; ++w)
+                if (rb[w][q] < bb || (rb[w][q] == bb && ri[w][q] < ii)) {
+                    bb = rb[w][q];
+                    ii = ri[w][q];
+                }
+            const int row = flags[g * EX_R + tid];
+            const bool valid = ii >= 0 && ii < N;
+            if (!valid) flag_error(st, ERR_NONFINITE);   // only NaN rows compare false everywhere
+            assign[row] = valid ? ii : 0;
+            e[row] = valid ? bb : 0.f;
+        }
+        __syncthreads();
     }
 }
 
@@ -444,17 +542,15 @@ __global__ void k_decode(const int32_t *__restrict__ assign, int64_t M, int L,
 
 void launch_codebook_mean(const float *C, int N, int L, float *mu, cudaStream_t s)
 {
-    k_codebook_mean<<<1, 1024, 0, s>>>(C, N, L, mu);
+    k_codebook_mean<<<L, 256, 0, s>>>(C, N, L, mu);
 }
 
 void launch_prep(const float *C, int N_alloc, const int32_t *n_dev, int n_host, int L, int Lp,
                  const float *mu, float *Cp, float *kn, float *CT, int NP, DevState *st,
                  cudaStream_t s)
 {
-    const int threads = 256;
     const int total = round_up(N_alloc, BN);
-    k_prep<<<(total + threads - 1) / threads, threads, 0, s>>>(C, n_dev, n_host, L, Lp, mu, Cp, kn,
-                                                              CT, NP, st);
+    k_prep<<<total / PREP_TILE, 256, 0, s>>>(C, n_dev, n_host, L, Lp, mu, Cp, kn, CT, NP, st);
 }
 
 size_t assign_smem_bytes(int Lp) { return (size_t)(Lp * BM + 2 * (Lp + 1) * BN) * sizeof(float); }
@@ -471,16 +567,18 @@ void launch_assign(const float *X, int64_t M, int L, int Lp, const float *Cp, co
                                                               C, st, assign, e, flags);
 }
 
-void launch_exact(const float *X, int L, const float *CT, int NP, const int32_t *n_dev, int n_host,
+void launch_exact(const float *X, int L, int Lp, const float *CT, const int32_t *n_dev, int n_host,
                   DevState *st, const int32_t *flags, int32_t *assign, float *e, int64_t M,
                   cudaStream_t s)
 {
-    // Enough warps for every SM; each warp loops over groups of flagged rows.
-    int64_t groups = (M + EX_ROWS - 1) / EX_ROWS;
-    int64_t blocks = (groups + EX_WARPS - 1) / EX_WARPS;
-    if (blocks > 152 * 4) blocks = 152 * 4;
+    // CTAs loop over groups of EX_R flagged rows; at most 3 CTAs per SM (the
+    // count of flagged rows is only known on the device; spare CTAs exit).
+    const size_t smem = (size_t)2 * Lp * EX_SW * sizeof(float);
+    cudaFuncSetAttribute(k_assign_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int64_t groups = (M + EX_R - 1) / EX_R;
+    int64_t blocks = groups < 152 * 3 ? groups : 152 * 3;
     if (blocks < 1) blocks = 1;
-    k_assign_exact<<<(unsigned)blocks, EX_WARPS * 32, 0, s>>>(X, L, CT, NP, n_dev, n_host, st, flags,
+    k_assign_exact<<<(unsigned)blocks, EX_THREADS, smem, s>>>(X, L, Lp, CT, n_dev, n_host, st, flags,
                                                              assign, e);
 }
 

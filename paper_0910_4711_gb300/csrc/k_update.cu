@@ -147,10 +147,14 @@ __global__ void __launch_bounds__(HIST_THREADS)
 __global__ void k_ctl(const double *__restrict__ dpart, int CH, DevState *st, int mode, double theta,
                       int max_passes, int N_target, PassRecord *rec, int max_rec)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
     if (mode == MODE_TRAIN && st->finished) return;
+    // lane partials over chunks lane, lane + 32, ..., then a fixed shuffle tree
     double D = 0.0;
-    for (int c = 0; c < CH; ++c) D += dpart[c];
+    for (int c = threadIdx.x; c < CH; c += 32) D += dpart[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) D += __shfl_xor_sync(0xffffffffu, D, o);
+    if (threadIdx.x != 0) return;
     const int nflag = st->nflag;
     st->n_exact_last = nflag;
     st->nflag = 0;
@@ -356,17 +360,15 @@ __global__ void __launch_bounds__(256)
         const int64_t pe = (int64_t)off[n + 1] < p1 ? (int64_t)off[n + 1] : p1;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         int64_t pp = p + rs;
-        for (; pp + 3 * RPG < pe; pp += 4 * RPG) {
-            const int r0 = perm[pp], r1 = perm[pp + RPG], r2 = perm[pp + 2 * RPG],
-                      r3 = perm[pp + 3 * RPG];
-            const float4 v0 = __ldg(X4 + (int64_t)r0 * G + qd);
-            const float4 v1 = __ldg(X4 + (int64_t)r1 * G + qd);
-            const float4 v2 = __ldg(X4 + (int64_t)r2 * G + qd);
-            const float4 v3 = __ldg(X4 + (int64_t)r3 * G + qd);
-            add4(acc, v0);
-            add4(acc, v1);
-            add4(acc, v2);
-            add4(acc, v3);
+        for (; pp + 7 * RPG < pe; pp += 8 * RPG) {   // eight rows in flight per lane
+            int r[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) r[u] = perm[pp + u * RPG];
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldg(X4 + (int64_t)r[u] * G + qd);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) add4(acc, v[u]);
         }
         for (; pp < pe; pp += RPG) add4(acc, __ldg(X4 + (int64_t)perm[pp] * G + qd));
 #pragma unroll
@@ -437,7 +439,9 @@ __global__ void k_combine(const float *__restrict__ pieces, const int32_t *__res
     const int64_t q0 = a / S, q1 = (b - 1) / S;
     double s = 0.0;
     for (int64_t q = q0; q <= q1; ++q) s += (double)pieces[(size_t)(n + q) * L + l];
-    C_out[i] = (float)(s / (double)(b - a));
+    // FP32 division of the rounded sum (two roundings, ~1.2e-7 relative; FP64
+    // division is slow on this part)
+    C_out[i] = (float)s / (float)(b - a);
 }
 
 // ---------------------------------------------------------------- split

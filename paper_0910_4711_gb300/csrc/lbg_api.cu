@@ -56,9 +56,9 @@ Plan make_plan(int64_t M, int L, int N, int max_rec, bool host_X, bool need_assi
     if (p.R < 256) p.R = 256;
     p.CH = (int)((M + p.R - 1) / p.R);
     if (p.CH < 1) p.CH = 1;
-    // centroid pieces: one warp per S cell-sorted rows, aiming at >= 32 warps per SM
-    int64_t S = round_up64((M + 152 * 32 - 1) / (152 * 32), 32);
-    if (S < 256) S = 256;
+    // centroid pieces: one warp per S cell-sorted rows, aiming at >= 64 warps per SM
+    int64_t S = round_up64((M + 152 * 64 - 1) / (152 * 64), 32);
+    if (S < 128) S = 128;
     if (S > 4096) S = 4096;
     p.S = S;
     p.nq = (M + S - 1) / S;
@@ -230,7 +230,7 @@ void run_assign(const Call &c, const Plan &p, const float *X, const float *C, co
 void run_exact(const Call &c, const Plan &p, const float *X, const int32_t *n_dev, int n_host,
                DevState *st, int32_t *assign)
 {
-    launch_exact(X, p.L, c.at<float>(p.CT), p.NP, n_dev, n_host, st, c.at<int32_t>(p.flags), assign,
+    launch_exact(X, p.L, p.Lp, c.at<float>(p.CT), n_dev, n_host, st, c.at<int32_t>(p.flags), assign,
                  c.at<float>(p.e), p.M, c.s);
 }
 

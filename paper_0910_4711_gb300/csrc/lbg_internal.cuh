@@ -134,7 +134,7 @@ void launch_prep(const float *C, int N_alloc, const int32_t *n_dev, int n_host, 
 void launch_assign(const float *X, int64_t M, int L, int Lp, const float *Cp, const float *kn,
                    const int32_t *n_dev, int n_host, const float *mu, const float *C, DevState *st,
                    int32_t *assign, float *e, int32_t *flags, cudaStream_t s);
-void launch_exact(const float *X, int L, const float *CT, int NP, const int32_t *n_dev, int n_host,
+void launch_exact(const float *X, int L, int Lp, const float *CT, const int32_t *n_dev, int n_host,
                   DevState *st, const int32_t *flags, int32_t *assign, float *e, int64_t M,
                   cudaStream_t s);
 void launch_decode(const int32_t *assign, int64_t M, int L, const float *C, float *Xhat,

@@ -156,7 +156,7 @@ extern "C" lbg_status vq_encode_noalloc(const float *X, int64_t M, int32_t L, co
         const float *Xc = X + r0 * L;
         int32_t *ic = idx + r0;
         launch_assign(Xc, mc, L, Lp, Cp, kn, nullptr, N, mu, C, st, ic, e, flags, s);
-        launch_exact(Xc, L, CT, NA_NP, nullptr, N, st, flags, ic, e, mc, s);
+        launch_exact(Xc, L, Lp, CT, nullptr, N, st, flags, ic, e, mc, s);
         // distortion of the chunk: same chunking rule as the cached-workspace path
         int64_t ch = (mc + 1023) / 1024;
         if (ch > HIST_CHUNKS_MAX) ch = HIST_CHUNKS_MAX;
