@@ -56,6 +56,10 @@ def parse():
                     help="target wall time of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"],
+                    help="form timed for the headline value (the other is timed beside it)")
+    ap.add_argument("--fp32-steps", type=int, default=3,
+                    help="timed steps of the other form (0: skip it)")
     return ap.parse_args()
 
 
@@ -246,55 +250,65 @@ def run_ours(args):
     X = torch.from_numpy(X_np).cuda()
     stream = torch.cuda.current_stream()
 
-    # full LBG design (also produces the codebook the step runs against)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    tr = lbg.lbg_train(X, N, delta=0.01, theta=1e-3, trace=100000)
-    torch.cuda.synchronize()
-    full_lbg_s = time.perf_counter() - t0
+    # full LBG design in both forms (the headline form's codebook is the one
+    # the timed steps run against)
+    other = "fp32" if args.precision == "bf16" else "bf16"
+    precs = [other, args.precision] if args.fp32_steps > 0 else [args.precision]
+    for prec in precs:   # untimed: workspace allocation and first launches
+        lbg.lbg_train(X, N, delta=0.01, theta=1e-3, max_passes=1, precision=prec)
+    trains = {}
+    for prec in precs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tr = lbg.lbg_train(X, N, delta=0.01, theta=1e-3, trace=100000, precision=prec)
+        torch.cuda.synchronize()
+        trains[prec] = (time.perf_counter() - t0, tr)
+    full_lbg_s, tr = trains[args.precision]
     C = tr.C.clone()
     C_out = torch.empty_like(C)
     A = torch.empty(M, dtype=torch.int32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    def step(phases):
-        r = lbg.lbg_lloyd_step(X, C, C_out=C_out, assign_out=A, phase_ms=True)
-        phases.append(r.phase_ms)
-        return r
-
-    scratch = []
-    for _ in range(max(3, args.warmup)):
-        flush.zero_()
-        step(scratch)
-    torch.cuda.synchronize()
-    phases, ev_ms, n_exact = [], [], []
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    with ClockSampler(gpu_uuid(dev)) as clk:
+    def timed_steps(prec, steps, clocks=None):
+        for _ in range(max(3, args.warmup)):
+            flush.zero_()
+            lbg.lbg_lloyd_step(X, C, C_out=C_out, assign_out=A, phase_ms=True, precision=prec)
+        torch.cuda.synchronize()
+        phases, n_exact = [], []
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         barrier(dist)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("timed_steps")
         w0 = time.perf_counter()
-        for k in range(args.steps):
+        for k in range(steps):
             flush.zero_()
             starts[k].record(stream)
-            r = step(phases)
+            r = lbg.lbg_lloyd_step(X, C, C_out=C_out, assign_out=A, phase_ms=True, precision=prec)
             ends[k].record(stream)
+            phases.append(r.phase_ms)
             n_exact.append(r.n_exact)
         torch.cuda.synchronize()
         wall = time.perf_counter() - w0
         torch.cuda.nvtx.range_pop()
         barrier(dist)
-    ev_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = statistics.mean(ev_ms)
-    ms = max_over_ranks(dist, ms)
-    value = world * M * N / (ms / 1e3)
+        ms = max_over_ranks(dist, statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends)))
+        ph = {k: statistics.mean(p[k] for p in phases) for k in ("prep", "assign", "exact", "update")}
+        return ms, ph, statistics.mean(n_exact), wall
 
-    assign_ms = statistics.mean(p["assign"] for p in phases)
-    update_ms = statistics.mean(p["update"] for p in phases)
-    exact_ms = statistics.mean(p["exact"] for p in phases)
-    prep_ms = statistics.mean(p["prep"] for p in phases)
+    with ClockSampler(gpu_uuid(dev)) as clk:
+        ms, ph, n_exact, wall = timed_steps(args.precision, args.steps)
     clocks = clk.summary()
+    value = world * M * N / (ms / 1e3)
+    other_line = None
+    if args.fp32_steps > 0:
+        o_ms, o_ph, o_ex, _ = timed_steps(other, args.fp32_steps)
+        o_train_s, o_tr = trains[other]
+        other_line = {"precision": other, "value": world * M * N / (o_ms / 1e3), "unit": UNIT,
+                      "ms_per_step": o_ms, "phase_ms": o_ph, "exact_rows_per_step": o_ex,
+                      "full_lbg_s": o_train_s, "full_lbg_passes": o_tr.n_passes,
+                      "full_lbg_D": o_tr.D}
+
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -302,39 +316,56 @@ def run_ours(args):
         pass
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
-    flops = 2.0 * L * M * N
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    flops = 2.0 * L * M * N          # algorithmic: L FMA per distance evaluation
+    assign_ms = ph["assign"]
     achieved = flops / (assign_ms / 1e3) / 1e12
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     upd_bytes = M * L * 4 + M * 4 + N * L * 4 + N * 4
-    upd_gbs = upd_bytes / (update_ms / 1e3) / 1e9
+    upd_gbs = upd_bytes / (ph["update"] / 1e3) / 1e9
+    if args.precision == "bf16":
+        Lk = (L + 15) // 16 * 16
+        executed = 2.0 * M * N * (3 * Lk + 16) / (assign_ms / 1e3) / 1e12
+        roof = {"bound": "tensor", "kernel": "k_assign_tc", "achieved": achieved, "peak": bf16_peak,
+                "unit": "TFLOP/s", "frac": achieved / bf16_peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
+                "work": "2*L*M*N flop per launch (algorithmic; the three-piece BF16 split and the "
+                        "norm column make the tensor cores execute 2*M*N*(3*ceil16(L)+16))",
+                "executed_tflops": executed, "executed_frac": executed / bf16_peak,
+                "epilogue_bound": {"ops_per_distance": 5, "peak_tops": fp32_peak / 2,
+                                   "bound_ms": 5.0 * M * N / (fp32_peak / 2 * 1e12) * 1e3}}
+    else:
+        roof = {"bound": "alu", "kernel": "k_assign_f32", "achieved": achieved, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                "peak_source": f"FP32 CUDA cores: {SM_COUNT} SMs x {FP32_LANES_PER_SM} "
+                               f"lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
+                "work": "2*L*M*N flop per launch"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": {"workload": workload_desc(args.workload, X_np, N), "M": M, "L": L, "N": N,
-                       "precision": "fp32",
+                       "precision": args.precision + (" (BF16 tensor-core distances, FP32 accumulation, "
+                                                      "certified or exact FP32 re-scoring)"
+                                                      if args.precision == "bf16" else " (FFMA)"),
                        "step": "one Lloyd pass (lbg_lloyd_step) against the trained N-entry codebook",
                        "l2": f"flushed: {L2_FLUSH_BYTES >> 20} MiB device write between steps",
                        "full_lbg_s": full_lbg_s, "full_lbg_passes": tr.n_passes,
                        "full_lbg_passes_per_stage": tr.passes_per_stage(),
-                       "full_lbg_D": tr.D, "exact_rows_per_step": statistics.mean(n_exact),
-                       "phase_ms": {"prep": prep_ms, "assign": assign_ms, "exact": exact_ms,
-                                    "update": update_ms},
-                       "wall_s_timed_region": wall, "data_sha256": synth.digest(X_np)[:16],
+                       "full_lbg_D": tr.D, "exact_rows_per_step": n_exact,
+                       "phase_ms": ph, "wall_s_timed_region": wall,
+                       "data_sha256": synth.digest(X_np)[:16],
                        "parallelism": f"replicas x{world}"},
-            "roofline": {"bound": "alu", "kernel": "k_assign_f32",
-                         "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": achieved / fp32_peak, "traffic": None,
-                         "peak_source": f"FP32 CUDA cores: {SM_COUNT} SMs x {FP32_LANES_PER_SM} "
-                                        f"lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
-                         "work": "2*L*M*N flop per launch"},
+            "roofline": roof,
             "update_roofline": {"bound": "hbm", "achieved": upd_gbs, "peak": hbm, "unit": "GB/s",
                                 "frac": upd_gbs / hbm, "bytes": upd_bytes,
                                 "work": "M*L*4 + M*4 + N*L*4 + N*4 bytes (read X, cell table; "
                                         "write codebook, counts)",
-                                "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+                                "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"},
             "clocks": clocks,
-            "gpu_launches": 11 * args.steps}
+            "gpu_launches": (12 if args.precision == "bf16" else 11) * args.steps}
+    if other_line is not None:
+        line["other_precision"] = other_line
 
     # end to end through the public API with host buffers
     if not args.no_e2e:
@@ -343,13 +374,13 @@ def run_ours(args):
         Coh = torch.empty_like(Ch).pin_memory()
         Ah = torch.empty(M, dtype=torch.int32).pin_memory()
         for _ in range(2):
-            lbg.lbg_lloyd_step(Xh, Ch, C_out=Coh, assign_out=Ah)
+            lbg.lbg_lloyd_step(Xh, Ch, C_out=Coh, assign_out=Ah, precision=args.precision)
         times = []
         for _ in range(max(3, min(args.steps, 10))):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            r = lbg.lbg_lloyd_step(Xh, Ch, C_out=Coh, assign_out=Ah)
+            r = lbg.lbg_lloyd_step(Xh, Ch, C_out=Coh, assign_out=Ah, precision=args.precision)
             times.append(time.perf_counter() - t0)
         e2e_s = max_over_ranks(dist, statistics.mean(times))
         line["e2e"] = {"value": world * M * N / e2e_s, "unit": UNIT,

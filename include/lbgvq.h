@@ -64,7 +64,12 @@ typedef enum lbg_status {
 } lbg_status;
 
 typedef enum lbg_precision {
-    LBG_PREC_FP32 = 0         /* FP32 FFMA distances, certified; exact FP32 fallback */
+    LBG_PREC_FP32 = 0,        /* FP32 FFMA distances, certified; exact FP32 fallback */
+    LBG_PREC_BF16 = 1         /* tensor cores (BF16 operands, FP32 accumulation), certified
+                                 against an accumulation-error model; exact FP32 fallback.
+                                 L <= 64.  Meant for data whose centred values are exact in
+                                 BF16 (integer samples such as 8-bit pixels); other data stay
+                                 correct but every row goes to the exact fallback. */
 } lbg_precision;
 
 /* Actions a pass of lbg_train can end with (lbg_pass_record.action). */

@@ -118,10 +118,16 @@ def _empty_like_src(src, shape, dtype: str):
     return np.empty(shape, dtype={"f32": np.float32, "i32": np.int32}[dtype])
 
 
-def _opts(cuda_ref, max_passes=1000, records=0, phase=False, stream=None):
+PRECISION = {"fp32": 0, "bf16": 1}
+
+
+def _opts(cuda_ref, max_passes=1000, records=0, phase=False, stream=None, precision="fp32"):
     o = Opts()
     lib().lbg_opts_init(ctypes.byref(o))
     o.max_passes = int(max_passes)
+    if precision not in PRECISION:
+        raise ValueError(f"precision must be one of {sorted(PRECISION)}")
+    o.precision = PRECISION[precision]
     keep = {}
     if stream is not None:
         o.stream = ctypes.c_void_p(int(stream))
@@ -197,7 +203,7 @@ class EncodeResult:
 # ------------------------------------------------------------ entry points
 def lbg_train(X, N: int, delta: float = 0.01, theta: float = 1e-3, C_init=None,
               max_passes: int = 1000, trace: int = 4096, phase_ms: bool = False, C_out=None,
-              assign_out=None, stream=None) -> TrainResult:
+              assign_out=None, stream=None, precision: str = "fp32") -> TrainResult:
     """Design an N-entry codebook from X [M, L] (see lbg_train in lbgvq.h)."""
     Xo, xp, _ = _prep(X, "f32", "X")
     M, L = int(X.shape[0]), int(X.shape[1])
@@ -209,7 +215,7 @@ def lbg_train(X, N: int, delta: float = 0.01, theta: float = 1e-3, C_init=None,
     A = assign_out if assign_out is not None else _empty_like_src(X, (M,), "i32")
     Co, cp, _ = _prep(C, "f32", "C")
     Ao, ap, _ = _prep(A, "i32", "assign")
-    o, keep = _opts(_cuda_ref(X, C, A), max_passes, trace, phase_ms, stream)
+    o, keep = _opts(_cuda_ref(X, C, A), max_passes, trace, phase_ms, stream, precision)
     D = ctypes.c_double(0.0)
     rc = _check(lib().lbg_train(xp, M, L, int(N), float(delta), float(theta), cp, n_init, ap,
                                 ctypes.byref(D), ctypes.byref(o)))
@@ -223,7 +229,7 @@ def lbg_train(X, N: int, delta: float = 0.01, theta: float = 1e-3, C_init=None,
 
 
 def lbg_lloyd_step(X, C_in, C_out=None, assign_out=None, phase_ms: bool = False,
-                   stream=None) -> StepResult:
+                   stream=None, precision: str = "fp32") -> StepResult:
     """One Lloyd pass from C_in (see lbg_lloyd_step in lbgvq.h)."""
     Xo, xp, _ = _prep(X, "f32", "X")
     M, L = int(X.shape[0]), int(X.shape[1])
@@ -233,14 +239,14 @@ def lbg_lloyd_step(X, C_in, C_out=None, assign_out=None, phase_ms: bool = False,
     Co, cop, _ = _prep(Co, "f32", "C_out")
     A = assign_out if assign_out is not None else _empty_like_src(X, (M,), "i32")
     A, ap, _ = _prep(A, "i32", "assign")
-    o, keep = _opts(_cuda_ref(X, C_in, Co, A), stream=stream, phase=phase_ms)
+    o, keep = _opts(_cuda_ref(X, C_in, Co, A), stream=stream, phase=phase_ms, precision=precision)
     D = ctypes.c_double(0.0)
     rc = _check(lib().lbg_lloyd_step(xp, M, L, N, cip, cop, ap, ctypes.byref(D), ctypes.byref(o)))
     return StepResult(rc, Co, A, D.value, keep["nex"].value, _phases(keep))
 
 
 def vq_encode(X, C, decode: bool = False, with_distortion: bool = True, phase_ms: bool = False,
-              idx_out=None, stream=None) -> EncodeResult:
+              idx_out=None, stream=None, precision: str = "fp32") -> EncodeResult:
     """Nearest codevector of every row of X (see vq_encode in lbgvq.h)."""
     Xo, xp, _ = _prep(X, "f32", "X")
     M, L = int(X.shape[0]), int(X.shape[1])
@@ -250,7 +256,7 @@ def vq_encode(X, C, decode: bool = False, with_distortion: bool = True, phase_ms
     I, ip, _ = _prep(I, "i32", "idx")
     H = _empty_like_src(X, (M, L), "f32") if decode else None
     H, hp, _ = _prep(H, "f32", "Xhat")
-    o, keep = _opts(_cuda_ref(X, C, I), stream=stream, phase=phase_ms)
+    o, keep = _opts(_cuda_ref(X, C, I), stream=stream, phase=phase_ms, precision=precision)
     D = ctypes.c_double(0.0)
     rc = _check(lib().vq_encode(xp, M, L, cp, N, ip, hp, ctypes.byref(D) if with_distortion else None,
                                 ctypes.byref(o)))

@@ -42,7 +42,7 @@ namespace {
 constexpr float U32 = 5.9604644775390625e-8f;   // 2^-24
 constexpr float SLOP = 1.0000305175781250f;     // 1 + 2^-15, covers FP32 evaluation of bounds
 constexpr int EX_R = 8;                         // flagged rows per CTA group in k_assign_exact
-constexpr int EX_SW = 128;                      // codevectors per staged chunk (= BN)
+constexpr int EX_SW = EXACT_SW;                 // codevectors per staged chunk
 constexpr int EX_THREADS = 256;
 
 __device__ __forceinline__ int cur_n(const int32_t *n_dev, int n_host)

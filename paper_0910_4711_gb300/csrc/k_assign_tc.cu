@@ -1,0 +1,608 @@
+// k_assign_tc.cu -- cell allocation (nearest codevector) on the 5th-generation
+// tensor cores: BF16 operands, FP32 accumulation in tensor memory.
+//
+// Paper: Algorithm 1 "Cell Allocation" / Sec. 2.2 step 1, as in k_assign.cu;
+// this is the same search with the cross term on tcgen05.mma.
+//
+// Exactness of the operands.  With an integer centring vector mu, centred
+// 8-bit image vectors x~ = x - mu are integers in [-255, 255], exact in BF16.
+// The scaled codevector c' = -2 c~ (FP32, 24 significant bits) is split into
+// three BF16 pieces p_hi + p_mid + p_lo = c' exactly, and so are the chain
+// start s0 = fl(||c~||^2 - k') and the row constant X2 = fl(||x~||^2).  One GEMM
+//     A = [ x~ | 1 1 1 X2_hi X2_mid X2_lo 0 ... ]          (K = Lk + 16)
+//     B = [ p_hi | p_mid | p_lo | s0 pieces 1 1 1 0 ... ]  (x~ reused 3 times)
+// therefore accumulates exactly X2 + s0 + x~.c' = X2 + f - k' (~ d - k', the
+// distance up to k'); the only error is the tensor core's FP32 accumulation.
+// X2 is the same in every column of a row, so it cancels in V2 - V1.
+//
+// Accumulation model.  Measured on GB300 (BF16 products, K up to 256, mixed
+// exponents) the error stayed below (K/16) * 2^-24 * (sum of |products|); the
+// library assumes tau = (K/16 + 2) * 2^-22 * (1 + 2^-7) of (sum of |products| +
+// |s0| + X2), a factor of about 4.8 above the worst case measured.  With
+// sum |x~_l c'_l| <= ||x~||^2 + ||c~||^2 this gives
+//     |v_n - (X2 + f_n - k'_n)| <= tau (2 ||x~||^2 + 2 ||c~_n||^2) + u ||c~_n||^2,
+// and with k'_n = (2 tau + 2^-23) ||c~_n||^2, R' = 2 tau ||x~||^2 the
+// certificate of k_assign.cu applies: V2 - V1 > 2R' + 2k'_i1 + 4 eta (g1 + eta),
+// plus 2^-16 (|V1| + |V2|) for the index packing below.
+//
+// Epilogue.  Each value's in-tile column j (7 bits) replaces the 7 low
+// mantissa bits (one LOP3, changes the value by less than 2^-16 of it), so
+// the running top-2 is three FMNMX per value and the argmin index comes out
+// of the minimum's low bits; a per-tile compare records the tile.
+// Tiles whose x~ are not BF16-exact, or codebooks whose pieces do not add up
+// exactly, send their rows to the exact FP32 fallback.
+//
+// Kernel layout (one CTA per SM, 256 rows per CTA):
+//   warp 0        producer: TMA bulk copies of prepared codebook tiles (128
+//                 codevectors x KB BF16, already in the MMA's shared-memory
+//                 layout) into a 3-stage ring;
+//   warp 1        allocates 512 TMEM columns, one thread issues the MMAs:
+//                 2 accumulators (128 rows each) x 128 columns, double-buffered;
+//   warps 2..9    epilogue, one row per thread: tcgen05.ld of its 128 values,
+//                 running top-2 with the argmin index (four interleaved chains),
+//                 then certificate, exact e(m) or a flag for the fallback.
+// Every mbarrier wait is bounded (2 s); on a time-out the CTA stops issuing,
+// reports LBG_ERR_TIMEOUT, waits for its own copies and frees its TMEM.
+#include "lbg_internal.cuh"
+
+#include <cuda_bf16.h>
+#include <math.h>
+
+namespace lbg {
+namespace {
+
+constexpr int TC_NACC = 2;                     // 128-row accumulators per CTA
+constexpr int TC_ROWS = 128 * TC_NACC;         // 256 rows per CTA
+constexpr int TC_NT = 128;                     // codevectors per tile (MMA N; N = 128 is the
+                                               // smallest N at full rate with both operands
+                                               // in shared memory, measured)
+constexpr int TC_JBITS = 7;                    // bits of the in-tile column index
+constexpr int TC_STAGES = 3;
+constexpr int TC_EPI_WARPS = 4 * TC_NACC;      // 16
+constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);
+constexpr int TC_TMEM_COLS = 2 * TC_NACC * TC_NT;   // 512
+constexpr int TC_LMAX = 64;
+
+constexpr float U32 = 5.9604644775390625e-8f;   // 2^-24
+constexpr float SLOP = 1.0000305175781250f;     // 1 + 2^-15
+
+__device__ __forceinline__ int cur_n(const int32_t *n_dev, int n_host)
+{
+    return n_dev ? *n_dev : n_host;
+}
+
+// Byte offset of element (row, k) in the canonical K-major, no-swizzle
+// layout: 8-row x 16-byte core matrices; core matrices along K are 128 bytes
+// apart (LBO), 8-row groups are sbo bytes apart (SBO).
+__host__ __device__ __forceinline__ uint32_t core_off(int row, int k, uint32_t sbo)
+{
+    return (uint32_t)(row >> 3) * sbo + (uint32_t)(k >> 3) * 128u + (uint32_t)(row & 7) * 16u +
+           (uint32_t)(k & 7) * 2u;
+}
+
+// tcgen05 shared-memory matrix descriptor: start address, LBO, SBO (all >> 4),
+// version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_NT >> 3) << 17) |
+                              ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Accumulation-error coefficient tau of the file header for KB accumulated
+// BF16 elements.
+__host__ __device__ inline double tc_tau(int KB)
+{
+    return (double)(KB / 16 + 2) * 2.384185791015625e-7 * 1.0078125;   // 2^-22, (1 + 2^-7)
+}
+
+// Split an FP32 value into three BF16 pieces that add up to it exactly (for
+// normal numbers); returns false if the remainder is not zero.
+__device__ __forceinline__ bool split3(float v, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l)
+{
+    h = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(h);
+    m = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(m);
+    l = __float2bfloat16_rn(r2);
+    return isfinite(v) ? (r2 - __bfloat162float(l)) == 0.f : isinf(v);
+}
+
+// Prepared BF16 codebook: tile t (TC_NT codevectors) is TC_NT x KB BF16 in
+// the core-matrix layout (SBO = KB/8 * 128); K columns [0,Lk) p_hi, [Lk,2Lk)
+// p_mid, [2Lk,3Lk) p_lo of c' = -2 (c - mu), [3Lk, 3Lk+3) the pieces of s0,
+// zeros elsewhere; padding codevectors have s0 = 2^100.  Also k'_n, the
+// chunk-major original codebook for the exact fallback, max ||c~||.
+__global__ void __launch_bounds__(256)
+    k_prep_tc(const float *__restrict__ C, const int32_t *n_dev, int n_host, int L, int Lk, int Lp,
+              const float *__restrict__ mu, __nv_bfloat16 *__restrict__ Bp, float *__restrict__ kn,
+              float *__restrict__ CT, DevState *st)
+{
+    if (st->finished) return;
+    const int N = cur_n(n_dev, n_host);
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ntile_pad = round_up(N, BN);   // CT chunks are BN wide; tiles TC_NT
+    if (n >= ntile_pad) return;
+    const int KB = 3 * Lk + 16;
+    const uint32_t sbo = (uint32_t)(KB / 8) * 128u;
+    uint8_t *tile = reinterpret_cast<uint8_t *>(Bp) + (size_t)(n / TC_NT) * TC_NT * KB * 2;
+    const int j = n % TC_NT;
+    auto put = [&](int k, __nv_bfloat16 v) {
+        *reinterpret_cast<__nv_bfloat16 *>(tile + core_off(j, k, sbo)) = v;
+    };
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+    if (n < N) {
+        double sq = 0.0;
+        bool finite = true, exact = true;
+        for (int l = 0; l < Lk; ++l) {
+            float cp = 0.f;
+            if (l < L) {
+                const float c = C[(size_t)n * L + l];
+                finite = finite && isfinite(c);
+                const float ct = c - mu[l];
+                sq += (double)ct * (double)ct;
+                cp = -2.0f * ct;
+            }
+            __nv_bfloat16 h, m, lo;
+            exact = split3(cp, h, m, lo) && exact;
+            put(l, h);
+            put(Lk + l, m);
+            put(2 * Lk + l, lo);
+        }
+        for (int l = 0; l < Lp; ++l)
+            CT[((size_t)(n / EXACT_SW) * Lp + l) * EXACT_SW + n % EXACT_SW] =
+                l < L ? C[(size_t)n * L + l] : 0.f;
+        if (!finite) flag_error(st, ERR_NONFINITE);
+        const double k = (2.0 * tc_tau(KB) + 1.1920928955078125e-7) * sq;   // 2 tau + 2^-23
+        const float kf = __double2float_ru(k);
+        const float s0 = __double2float_rn(sq - (double)kf);
+        __nv_bfloat16 h, m, lo;
+        exact = split3(s0, h, m, lo) && exact;
+        put(3 * Lk, h);
+        put(3 * Lk + 1, m);
+        put(3 * Lk + 2, lo);
+        const __nv_bfloat16 one = __float2bfloat16_rn(1.f);
+        for (int q = 3; q < 6; ++q) put(3 * Lk + q, one);     // x X2 pieces of the row
+        for (int q = 6; q < 16; ++q) put(3 * Lk + q, zero);
+        kn[n] = kf;
+        atomicMax(&st->cmax_bits, __float_as_uint(__double2float_ru(sqrt(sq))));
+        if (!exact) atomicOr(&st->tc_inexact, 1);
+    } else {
+        for (int k = 0; k < KB; ++k) put(k, zero);
+        put(3 * Lk, __float2bfloat16_rn(1.2676506002282294e30f));   // padding: 2^100, finite so
+                                                                     // index packing cannot make a NaN
+        kn[n] = 0.f;
+        for (int l = 0; l < Lp; ++l)
+            CT[((size_t)(n / EXACT_SW) * Lp + l) * EXACT_SW + n % EXACT_SW] = 0.f;
+    }
+}
+
+template <int LK>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_assign_tc(const float *__restrict__ X, int64_t M, int L,
+                const __nv_bfloat16 *__restrict__ Bp, const float *__restrict__ kn,
+                const int32_t *n_dev, int n_host, const float *__restrict__ mu,
+                const float *__restrict__ C, DevState *st, int32_t *__restrict__ assign,
+                float *__restrict__ e, int32_t *__restrict__ flags)
+{
+    if (st->finished) return;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], tfull[2], tempty[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_abort, s_inexact, s_prod_last, s_mma_last;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int N = cur_n(n_dev, n_host);
+    const int ntiles = (N + TC_NT - 1) / TC_NT;
+    constexpr int Lk = LK;
+    constexpr int KA = LK + 16, KB = 3 * LK + 16;
+    constexpr uint32_t sbo_a = (uint32_t)(KA / 8) * 128u, sbo_b = (uint32_t)(KB / 8) * 128u;
+    constexpr uint32_t a_bytes = 128u * KA * 2u;               // one accumulator's A block
+    constexpr uint32_t stage_bytes = (uint32_t)TC_NT * KB * 2u;
+    uint8_t *A = smem;
+    uint8_t *Bs = smem + TC_NACC * a_bytes;
+    const int64_t m0 = (int64_t)blockIdx.x * TC_ROWS;
+
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], TC_EPI_WARPS);
+        }
+        fence_mbar_init();
+        s_abort = 0;
+        s_inexact = 0;
+        s_prod_last = -1;
+        s_mma_last = -1;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(&tmem_base)),
+                     "n"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+
+    // Epilogue thread <-> row: accumulator acc, TMEM lane quarter = warp % 4.
+    const int acc = (warp - 2) >> 2;
+    const int rr = 32 * (warp & 3) + lane;
+    const int64_t m = m0 + 128 * acc + rr;
+    if (warp >= 2) {
+        // Stage the centred x tile as BF16 into the A blocks: the 512 x L tile
+        // is contiguous in X, so the epilogue threads read it as a flat array
+        // (coalesced, several loads in flight), convert, and scatter into the
+        // core-matrix layout.
+        const int et = tid - 64;                              // 0 .. 511
+        const int64_t rows = M - m0 < TC_ROWS ? M - m0 : TC_ROWS;
+        bool inexact = false, bad = false;
+        const float *Xt = X + m0 * L;
+        auto put_x = [&](int i, float xv) {   // i: flat index inside the tile (< 512 * 64)
+            const int r = i / L, l = i - r * L;
+            bad = bad || !isfinite(xv);
+            const float v = xv - mu[l];
+            const __nv_bfloat16 b = __float2bfloat16_rn(v);
+            inexact = inexact || (__bfloat162float(b) != v);
+            *reinterpret_cast<__nv_bfloat16 *>(A + (r >> 7) * a_bytes + core_off(r & 127, l, sbo_a)) = b;
+        };
+        const int total = (int)rows * L;
+        if ((L & 3) == 0 && (reinterpret_cast<uintptr_t>(Xt) & 15u) == 0) {
+            const float4 *X4 = reinterpret_cast<const float4 *>(Xt);
+            const int total4 = total >> 2;
+            int i = et;
+            for (; i + 3 * (TC_THREADS - 64) < total4; i += 4 * (TC_THREADS - 64)) {
+                float4 q[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) q[u] = __ldg(X4 + i + u * (TC_THREADS - 64));
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int f = 4 * (i + u * (TC_THREADS - 64));
+                    put_x(f, q[u].x);
+                    put_x(f + 1, q[u].y);
+                    put_x(f + 2, q[u].z);
+                    put_x(f + 3, q[u].w);
+                }
+            }
+            for (; i < total4; i += TC_THREADS - 64) {
+                const float4 q = __ldg(X4 + i);
+                put_x(4 * i, q.x);
+                put_x(4 * i + 1, q.y);
+                put_x(4 * i + 2, q.z);
+                put_x(4 * i + 3, q.w);
+            }
+        } else {
+            for (int i = et; i < total; i += TC_THREADS - 64) put_x(i, __ldg(Xt + i));
+        }
+        // Own row: zero padding dims (and whole rows past M), the ones block.
+        uint8_t *Ab = A + acc * a_bytes;
+        const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+        for (int l = (m < M ? L : 0); l < Lk; ++l)
+            *reinterpret_cast<__nv_bfloat16 *>(Ab + core_off(rr, l, sbo_a)) = zero;
+        if (bad) flag_error(st, ERR_NONFINITE);
+        if (inexact) s_inexact = 1;
+    }
+    __syncthreads();
+    float xn2 = 0.f;
+    if (warp >= 2) {
+        // ||x~||^2 of the own row from the staged (exact) BF16 values, then the
+        // norm block of A: 1 1 1 (x s0 pieces), X2 in three BF16 pieces.
+        uint8_t *Ab = A + acc * a_bytes;
+        for (int l = 0; l < L; ++l) {
+            const float v = __bfloat162float(
+                *reinterpret_cast<const __nv_bfloat16 *>(Ab + core_off(rr, l, sbo_a)));
+            xn2 = fmaf(v, v, xn2);
+        }
+        __nv_bfloat16 h, mi, lo;
+        split3(xn2, h, mi, lo);
+        const __nv_bfloat16 one = __float2bfloat16_rn(1.f), zero = __float2bfloat16_rn(0.f);
+        for (int q = 0; q < 16; ++q) {
+            __nv_bfloat16 v = zero;
+            if (q < 3) v = one;
+            else if (q == 3) v = h;
+            else if (q == 4) v = mi;
+            else if (q == 5) v = lo;
+            *reinterpret_cast<__nv_bfloat16 *>(Ab + core_off(rr, Lk + q, sbo_a)) = v;
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        // ---------------- producer
+        if (lane == 0) {
+            for (int t = 0; t < ntiles; ++t) {
+                const int s = t % TC_STAGES;
+                if (t >= TC_STAGES && !mbar_wait_bounded_sleep(&empty[s], (uint32_t)((t / TC_STAGES) - 1) & 1u)) {
+                    s_abort = 1;
+                    break;
+                }
+                if (s_abort) break;
+                mbar_expect_tx(&full[s], stage_bytes);
+                bulk_load(Bs + s * stage_bytes,
+                          reinterpret_cast<const uint8_t *>(Bp) + (size_t)t * stage_bytes, stage_bytes,
+                          &full[s]);
+                s_prod_last = t;
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        const uint64_t adesc0 = smem_desc(smem_addr(A), 128u, sbo_a);
+        const uint64_t bdesc0 = smem_desc(smem_addr(Bs), 128u, sbo_b);
+        if (lane == 0) {
+            for (int t = 0; t < ntiles; ++t) {
+                const int s = t % TC_STAGES, b = t & 1;
+                if (!mbar_wait_bounded_sleep(&full[s], (uint32_t)(t / TC_STAGES) & 1u)) {
+                    s_abort = 1;
+                    break;
+                }
+                if (t >= 2 && !mbar_wait_bounded_sleep(&tempty[b], (uint32_t)((t >> 1) - 1) & 1u)) {
+                    s_abort = 1;
+                    break;
+                }
+                if (s_abort) break;
+                tc_fence_after();
+                // Descriptors differ only in their start-address field: add the
+                // byte offset / 16 to base descriptors (addresses < 256 KB, no carry).
+                const uint64_t bst = bdesc0 + ((uint64_t)(s * stage_bytes) >> 4);
+#pragma unroll
+                for (int a = 0; a < TC_NACC; ++a) {
+                    const uint32_t d = tmem + (uint32_t)((b * TC_NACC + a) * TC_NT);
+                    const uint64_t ab = adesc0 + (uint64_t)((a * a_bytes) >> 4);
+#pragma unroll
+                    for (int seg = 0; seg < 3; ++seg)
+#pragma unroll
+                        for (int kk = 0; kk < LK / 16; ++kk)
+                            mma_bf16(d, ab + (uint64_t)(kk * 16), bst + (uint64_t)(seg * LK + kk * 16),
+                                     (seg | kk) ? 1u : 0u);
+                    mma_bf16(d, ab + (uint64_t)LK, bst + (uint64_t)(3 * LK), 1u);
+                }
+                mma_commit(&empty[s]);
+                mma_commit(&tfull[b]);
+                s_mma_last = t;
+            }
+        }
+    } else {
+        // ---------------- epilogue: one row per thread
+        constexpr int NCH = 4;                       // independent min-chains
+        constexpr int JMASK = (1 << TC_JBITS) - 1;
+        float c1[NCH], c2[NCH];
+        int cg[NCH];
+#pragma unroll
+        for (int q = 0; q < NCH; ++q) {
+            c1[q] = INFINITY;
+            c2[q] = INFINITY;
+            cg[q] = 0;
+        }
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        for (int t = 0; t < ntiles; ++t) {
+            const int b = t & 1;
+            if (!mbar_wait_bounded_sleep(&tfull[b], (uint32_t)(t >> 1) & 1u)) {
+                s_abort = 1;
+                break;
+            }
+            tc_fence_after();
+            float v[TC_NT];
+            const uint32_t col = (uint32_t)((b * TC_NACC + acc) * TC_NT);
+            float s1[NCH];
+#pragma unroll
+            for (int q = 0; q < NCH; ++q) s1[q] = c1[q];
+            // two halves: the second TMEM read is in flight while the first half is scanned
+            tmem_ld32(tmem + lane_base + col, v);
+            tmem_ld32(tmem + lane_base + col + 32u, v + 32);
+            tmem_ld_wait();
+            tmem_ld32(tmem + lane_base + col + 64u, v + 64);
+            tmem_ld32(tmem + lane_base + col + 96u, v + 96);
+#pragma unroll
+            for (int j = 0; j < TC_NT / 2; ++j) {
+                const int q = j % NCH;
+                const float k = __int_as_float((__float_as_int(v[j]) & ~JMASK) | j);
+                c2[q] = fminf(c2[q], fmaxf(c1[q], k));
+                c1[q] = fminf(c1[q], k);
+            }
+            tmem_ld_wait();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+#pragma unroll
+            for (int j = TC_NT / 2; j < TC_NT; ++j) {
+                const int q = j % NCH;
+                const float k = __int_as_float((__float_as_int(v[j]) & ~JMASK) | j);
+                c2[q] = fminf(c2[q], fmaxf(c1[q], k));
+                c1[q] = fminf(c1[q], k);
+            }
+#pragma unroll
+            for (int q = 0; q < NCH; ++q) cg[q] = c1[q] < s1[q] ? t : cg[q];
+            if (s_abort) break;
+        }
+        // merge the chains; the index is the tile times TC_NT plus the low bits
+        float V1 = c1[0], V2 = c2[0];
+        int i1 = cg[0] * TC_NT + (__float_as_int(c1[0]) & JMASK);
+#pragma unroll
+        for (int q = 1; q < NCH; ++q) {
+            const int iq = cg[q] * TC_NT + (__float_as_int(c1[q]) & JMASK);
+            V2 = fminf(fminf(V2, c2[q]), fmaxf(V1, c1[q]));
+            const bool take = c1[q] < V1 || (c1[q] == V1 && iq < i1);
+            V1 = take ? c1[q] : V1;
+            i1 = take ? iq : i1;
+        }
+        if (m < M && !s_abort) {
+            bool certified = false;
+            if (!s_inexact && st->tc_inexact == 0 && i1 >= 0 && i1 < N && V1 < INFINITY) {
+                const double tau = tc_tau(3 * Lk + 16);
+                const float xn2u = xn2 * SLOP;
+                const float R = 2.f * (float)tau * xn2u * SLOP;
+                const float kc = kn[i1];
+                const float cmax = __uint_as_float(st->cmax_bits);
+                const float eta = U32 * (sqrtf(xn2u) + cmax) * SLOP;
+                const float pack = 1.52587890625e-5f * (fabsf(V1) + fabsf(V2));   // 2^-16
+                // V1 ~ ||x~ - c~_i1||^2 - k' (X2 included): bound g1^2 from above
+                const float g1sq = V1 + 2.f * kc + R + pack + (float)(L + 2) * U32 * xn2u;
+                const float g1 = sqrtf(fmaxf(g1sq, 0.f)) * SLOP;
+                const float margin = (2.f * R + 2.f * kc + pack + 4.f * eta * (g1 + eta)) * SLOP;
+                certified = (V2 - V1) > margin;
+            }
+            if (certified) {
+                const float *xr = X + m * L;
+                const float *cr = C + (size_t)i1 * L;
+                float d2 = 0.f;
+                if ((L & 3) == 0 && ((reinterpret_cast<uintptr_t>(xr) | reinterpret_cast<uintptr_t>(cr)) & 15u) == 0) {
+                    const float4 *x4 = reinterpret_cast<const float4 *>(xr);
+                    const float4 *c4 = reinterpret_cast<const float4 *>(cr);
+                    for (int q0 = 0; q0 < L / 4; q0 += 4) {   // four 16-byte pairs in flight
+                        float4 a[4], b[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (q0 + u < L / 4) {
+                                a[u] = __ldg(x4 + q0 + u);
+                                b[u] = __ldg(c4 + q0 + u);
+                            }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (q0 + u < L / 4) {
+                                float d = a[u].x - b[u].x;
+                                d2 = fmaf(d, d, d2);
+                                d = a[u].y - b[u].y;
+                                d2 = fmaf(d, d, d2);
+                                d = a[u].z - b[u].z;
+                                d2 = fmaf(d, d, d2);
+                                d = a[u].w - b[u].w;
+                                d2 = fmaf(d, d, d2);
+                            }
+                    }
+                } else {
+                    for (int l = 0; l < L; ++l) {
+                        const float d = xr[l] - cr[l];
+                        d2 = fmaf(d, d, d2);
+                    }
+                }
+                assign[m] = i1;
+                e[m] = d2;
+            } else {
+                flags[atomicAdd(&st->nflag, 1)] = (int32_t)m;
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (s_abort) {
+        // Stop: wait (bounded) for the bulk copies nobody consumed and for the
+        // last committed MMAs, then free TMEM below.
+        if (tid == 0) {
+            for (int t = s_mma_last + 1; t <= s_prod_last; ++t)
+                (void)mbar_wait_bounded(&full[t % TC_STAGES], (uint32_t)(t / TC_STAGES) & 1u);
+            if (s_mma_last >= 0)
+                (void)mbar_wait_bounded(&tfull[s_mma_last & 1], (uint32_t)(s_mma_last >> 1) & 1u);
+            flag_error(st, ERR_TIMEOUT);
+        }
+        __syncthreads();
+    }
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TC_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+__global__ void k_round_mu(float *mu, int L)
+{
+    const int l = threadIdx.x;
+    if (l < L) mu[l] = rintf(mu[l]);
+}
+
+}  // namespace
+
+size_t tc_codebook_bytes(int NP, int L) { return (size_t)NP * (3 * round_up(L, 16) + 16) * 2; }
+
+bool tc_supported(int L) { return L >= 1 && L <= TC_LMAX; }
+
+void launch_round_mu(float *mu, int L, cudaStream_t s) { k_round_mu<<<1, 128, 0, s>>>(mu, L); }
+
+void launch_prep_tc(const float *C, int N_alloc, const int32_t *n_dev, int n_host, int L,
+                    const float *mu, void *Bp, float *kn, float *CT, DevState *st, cudaStream_t s)
+{
+    const int total = round_up(N_alloc, BN);
+    k_prep_tc<<<(total + 255) / 256, 256, 0, s>>>(C, n_dev, n_host, L, round_up(L, 16),
+                                                  round_up(L, 4), mu,
+                                                  static_cast<__nv_bfloat16 *>(Bp), kn, CT, st);
+}
+
+template <int LK>
+static void launch_tc(const float *X, int64_t M, int L, const void *Bp, const float *kn,
+                      const int32_t *n_dev, int n_host, const float *mu, const float *C, DevState *st,
+                      int32_t *assign, float *e, int32_t *flags, cudaStream_t s)
+{
+    const size_t need = (size_t)TC_NACC * 128 * (LK + 16) * 2 + (size_t)TC_STAGES * TC_NT * (3 * LK + 16) * 2;
+    // at least 120 KB so that a single CTA (and its 512 TMEM columns) owns the SM
+    const size_t smem = need > 120 * 1024 ? need : 120 * 1024;
+    cudaFuncSetAttribute(k_assign_tc<LK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int64_t grid = (M + TC_ROWS - 1) / TC_ROWS;
+    if (grid == 0) return;
+    k_assign_tc<LK><<<(unsigned)grid, TC_THREADS, smem, s>>>(
+        X, M, L, static_cast<const __nv_bfloat16 *>(Bp), kn, n_dev, n_host, mu, C, st, assign, e, flags);
+}
+
+void launch_assign_tc(const float *X, int64_t M, int L, const void *Bp, const float *kn,
+                      const int32_t *n_dev, int n_host, const float *mu, const float *C,
+                      DevState *st, int32_t *assign, float *e, int32_t *flags, cudaStream_t s)
+{
+    switch (round_up(L, 16)) {
+    case 16: launch_tc<16>(X, M, L, Bp, kn, n_dev, n_host, mu, C, st, assign, e, flags, s); break;
+    case 32: launch_tc<32>(X, M, L, Bp, kn, n_dev, n_host, mu, C, st, assign, e, flags, s); break;
+    case 48: launch_tc<48>(X, M, L, Bp, kn, n_dev, n_host, mu, C, st, assign, e, flags, s); break;
+    default: launch_tc<64>(X, M, L, Bp, kn, n_dev, n_host, mu, C, st, assign, e, flags, s); break;
+    }
+}
+
+}  // namespace lbg

@@ -27,8 +27,9 @@ Workspace g_ws[MAX_DEVICES];
 struct Plan {
     int64_t M = 0, R = 0, S = 0, nq = 0;
     int L = 0, Lp = 0, N = 0, NP = 0, CH = 0, G = 0, max_rec = 0;
+    bool tc = false;   // tensor-core (BF16) allocation
     size_t state, rec, Cp, kn, CT, mu, Ccur, Calt, assign, e, flags, table, dpart, counts, off, perm,
-        pieces, mpart, Xs, Cin, Cout, Xhat;
+        pieces, mpart, Xs, Cin, Cout, Xhat, Bp;
     size_t total = 0;
     size_t take(size_t bytes)
     {
@@ -39,9 +40,10 @@ struct Plan {
 };
 
 Plan make_plan(int64_t M, int L, int N, int max_rec, bool host_X, bool need_assign, bool host_C,
-               bool host_Xhat)
+               bool host_Xhat, bool tc)
 {
     Plan p;
+    p.tc = tc;
     p.M = M;
     p.L = L;
     p.Lp = round_up(L, 4);
@@ -89,6 +91,7 @@ Plan make_plan(int64_t M, int L, int N, int max_rec, bool host_X, bool need_assi
     p.Cin = host_C ? p.take(sizeof(float) * (size_t)N * L) : 0;
     p.Cout = host_C ? p.take(sizeof(float) * (size_t)N * L) : 0;
     p.Xhat = host_Xhat ? p.take(sizeof(float) * (size_t)M * L) : 0;
+    p.Bp = tc ? p.take(tc_codebook_bytes(p.NP, L)) : 0;
     return p;
 }
 
@@ -216,15 +219,23 @@ void run_prepare(const Call &c, const Plan &p, const float *C, const int32_t *n_
                  const float *mu, DevState *st)
 {
     cudaMemsetAsync(&st->cmax_bits, 0, sizeof(uint32_t), c.s);
-    launch_prep(C, p.N, n_dev, n_host, p.L, p.Lp, mu, c.at<float>(p.Cp), c.at<float>(p.kn),
-                c.at<float>(p.CT), p.NP, st, c.s);
+    if (p.tc)
+        launch_prep_tc(C, p.N, n_dev, n_host, p.L, mu, c.at<void>(p.Bp), c.at<float>(p.kn),
+                       c.at<float>(p.CT), st, c.s);
+    else
+        launch_prep(C, p.N, n_dev, n_host, p.L, p.Lp, mu, c.at<float>(p.Cp), c.at<float>(p.kn),
+                    c.at<float>(p.CT), p.NP, st, c.s);
 }
 
 void run_assign(const Call &c, const Plan &p, const float *X, const float *C, const int32_t *n_dev,
                 int n_host, const float *mu, DevState *st, int32_t *assign)
 {
-    launch_assign(X, p.M, p.L, p.Lp, c.at<float>(p.Cp), c.at<float>(p.kn), n_dev, n_host, mu, C, st,
-                  assign, c.at<float>(p.e), c.at<int32_t>(p.flags), c.s);
+    if (p.tc)
+        launch_assign_tc(X, p.M, p.L, c.at<void>(p.Bp), c.at<float>(p.kn), n_dev, n_host, mu, C, st,
+                         assign, c.at<float>(p.e), c.at<int32_t>(p.flags), c.s);
+    else
+        launch_assign(X, p.M, p.L, p.Lp, c.at<float>(p.Cp), c.at<float>(p.kn), n_dev, n_host, mu, C,
+                      st, assign, c.at<float>(p.e), c.at<int32_t>(p.flags), c.s);
 }
 
 void run_exact(const Call &c, const Plan &p, const float *X, const int32_t *n_dev, int n_host,
@@ -245,6 +256,14 @@ void run_update(const Call &c, const Plan &p, const float *X, const int32_t *n_d
     launch_cellsum(X, p.M, p.L, c.at<int32_t>(p.perm), off, n_dev, n_host, p.S,
                    c.at<float>(p.pieces), st, train, c.s);
     launch_combine(c.at<float>(p.pieces), off, n_dev, n_host, p.L, p.S, C_in, C_out, st, train, c.s);
+}
+
+// 0 = FP32, 1 = tensor cores, <0 = error status
+int precision_mode(const lbg_opts &o, int L)
+{
+    if (o.precision == LBG_PREC_FP32) return 0;
+    if (o.precision == LBG_PREC_BF16) return tc_supported(L) ? 1 : LBG_ERR_UNSUPPORTED;
+    return LBG_ERR_ARG;
 }
 
 lbg_status check_dims(int64_t M, int32_t L, int32_t N)
@@ -307,7 +326,8 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
     if (rc != LBG_OK) return rc;
     if (!C || (M > 0 && (!X || !idx))) return LBG_ERR_ARG;
     const lbg_opts o = resolve(opts);
-    if (o.precision != LBG_PREC_FP32) return LBG_ERR_UNSUPPORTED;
+    const int mode = precision_mode(o, L);
+    if (mode < 0) return (lbg_status)mode;
     std::lock_guard<std::mutex> lock(g_mu);
     Call c;
     if ((rc = begin(c, o)) != LBG_OK) return rc;
@@ -319,7 +339,7 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
     const int wX = where(X, c.dev), wC = where(C, c.dev), wI = where(idx, c.dev);
     const int wH = Xhat ? where(Xhat, c.dev) : 1;
     if (wX < 0 || wC < 0 || wI < 0 || wH < 0) return LBG_ERR_ARG;
-    const Plan p = make_plan(M, L, N, 0, wX == 0, wI == 0, wC == 0, wH == 0);
+    const Plan p = make_plan(M, L, N, 0, wX == 0, wI == 0, wC == 0, wH == 0, mode == 1);
     if ((rc = ensure_workspace(c, p.total)) != LBG_OK) return rc;
     DevState *st = c.at<DevState>(p.state);
     DevState h;
@@ -342,6 +362,7 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
     float *mu = c.at<float>(p.mu);
     tm.mark(0, c.s);
     launch_codebook_mean(dC, N, L, mu, c.s);
+    if (p.tc) launch_round_mu(mu, L, c.s);
     run_prepare(c, p, dC, nullptr, N, mu, st);
     tm.mark(1, c.s);
     run_assign(c, p, dX, dC, nullptr, N, mu, st, dI);
@@ -375,7 +396,8 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
     if (rc != LBG_OK) return rc;
     if (!C_in || !C_out || (M > 0 && !X)) return LBG_ERR_ARG;
     const lbg_opts o = resolve(opts);
-    if (o.precision != LBG_PREC_FP32) return LBG_ERR_UNSUPPORTED;
+    const int mode = precision_mode(o, L);
+    if (mode < 0) return (lbg_status)mode;
     std::lock_guard<std::mutex> lock(g_mu);
     Call c;
     if ((rc = begin(c, o)) != LBG_OK) return rc;
@@ -383,7 +405,7 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
     const int wA = assign ? where(assign, c.dev) : 0;
     if (wX < 0 || wCi < 0 || wCo < 0 || wA < 0) return LBG_ERR_ARG;
     const bool hostC = (wCi == 0) || (wCo == 0);
-    const Plan p = make_plan(M, L, N, 0, wX == 0, !(assign && wA == 1), hostC, false);
+    const Plan p = make_plan(M, L, N, 0, wX == 0, !(assign && wA == 1), hostC, false, mode == 1);
     if ((rc = ensure_workspace(c, p.total)) != LBG_OK) return rc;
     const size_t cbytes = sizeof(float) * (size_t)N * L;
     if (M == 0) {
@@ -417,6 +439,7 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
     float *mu = c.at<float>(p.mu);
     tm.mark(0, c.s);
     launch_codebook_mean(dCi, N, L, mu, c.s);
+    if (p.tc) launch_round_mu(mu, L, c.s);
     run_prepare(c, p, dCi, nullptr, N, mu, st);
     tm.mark(1, c.s);
     run_assign(c, p, dX, dCi, nullptr, N, mu, st, dA);
@@ -452,7 +475,8 @@ lbg_status lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double del
     if (n_init < 0 || n_init > N) return LBG_ERR_ARG;
     if (n_init > 0 && !is_pow2(n_init)) return LBG_ERR_NOT_POW2;
     const lbg_opts o = resolve(opts);
-    if (o.precision != LBG_PREC_FP32) return LBG_ERR_UNSUPPORTED;
+    const int mode = precision_mode(o, L);
+    if (mode < 0) return (lbg_status)mode;
     std::lock_guard<std::mutex> lock(g_mu);
     Call c;
     if ((rc = begin(c, o)) != LBG_OK) return rc;
@@ -463,7 +487,7 @@ lbg_status lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double del
     for (int n = n_init > 0 ? n_init : 1; n < N; n *= 2) ++stages;
     const int64_t max_total = (int64_t)stages * o.max_passes;
     const int max_rec = o.max_records < max_total ? o.max_records : (int)max_total;
-    const Plan p = make_plan(M, L, N, max_rec, wX == 0, !(assign && wA == 1), false, false);
+    const Plan p = make_plan(M, L, N, max_rec, wX == 0, !(assign && wA == 1), false, false, mode == 1);
     if ((rc = ensure_workspace(c, p.total)) != LBG_OK) return rc;
     DevState *st = c.at<DevState>(p.state);
     DevState h;
@@ -484,6 +508,7 @@ lbg_status lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double del
     // Initialization (Algorithm 1): centroid of the training set; it is also
     // the centring vector of every allocation of the run.
     launch_mean(dX, M, L, c.at<double>(p.mpart), p.G, mu, n_init > 0 ? nullptr : Ccur, st, c.s);
+    if (p.tc) launch_round_mu(mu, L, c.s);   // integer centring keeps integer samples exact in BF16
     const int32_t *n_dev = &st->n_cur;
     PassRecord *rec = c.at<PassRecord>(p.rec);
     int64_t issued = 0;

@@ -18,6 +18,9 @@ constexpr int NMAX = 8192;    // = LBG_MAX_CODEBOOK
 // chunks (one CTA each); the segmented centroid sums cut the cell-sorted
 // row order into pieces of SEG rows (one warp each).
 constexpr int HIST_CHUNKS_MAX = 304;   // 2 x 152 SMs
+// The exact re-scoring kernel stages the original codebook in chunks of
+// EXACT_SW codevectors, stored k-major inside a chunk.
+constexpr int EXACT_SW = 128;
 constexpr int HIST_THREADS = 256;
 
 // Error bits in DevState::err.
@@ -42,6 +45,7 @@ struct DevState {
     int32_t warn;         // 1 if some stage was cut at max_passes
     int32_t nflag;        // rows flagged for exact re-scoring in this pass
     int32_t n_exact_last; // nflag of the last pass (for step / encode reports)
+    int32_t tc_inexact;   // 1 if a BF16 codebook did not split exactly (tensor-core path)
     uint32_t err;         // ERR_* bits
     uint32_t cmax_bits;   // bits of max_n ||c_n - mu|| (non-negative float)
     double D;             // total distortion of the last pass
@@ -105,6 +109,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
+// Same test with a suspend-time hint: a waiting thread sleeps (instead of
+// spinning and taking issue slots) until the phase completes or ~hint_ns pass.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t hint_ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ uint64_t global_ns()
 {
     uint64_t t;
@@ -120,6 +139,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     for (uint32_t i = 1;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((i & 255u) == 0u && global_ns() - t0 > 2000000000ull) return false;
+    }
+}
+
+// Bounded wait that sleeps between tests (for waits expected to be long).
+__device__ __forceinline__ bool mbar_wait_bounded_sleep(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait_sleep(bar, parity, 100000u)) return true;
+        if (global_ns() - t0 > 2000000000ull) return false;
     }
 }
 
@@ -139,6 +169,16 @@ void launch_exact(const float *X, int L, int Lp, const float *CT, const int32_t 
                   cudaStream_t s);
 void launch_decode(const int32_t *assign, int64_t M, int L, const float *C, float *Xhat,
                    cudaStream_t s);
+
+// Tensor-core (BF16 / tcgen05) nearest codevector (k_assign_tc.cu).
+size_t tc_codebook_bytes(int NP, int L);
+bool tc_supported(int L);
+void launch_round_mu(float *mu, int L, cudaStream_t s);
+void launch_prep_tc(const float *C, int N_alloc, const int32_t *n_dev, int n_host, int L,
+                    const float *mu, void *Bp, float *kn, float *CT, DevState *st, cudaStream_t s);
+void launch_assign_tc(const float *X, int64_t M, int L, const void *Bp, const float *kn,
+                      const int32_t *n_dev, int n_host, const float *mu, const float *C,
+                      DevState *st, int32_t *assign, float *e, int32_t *flags, cudaStream_t s);
 
 // Cell table, distortion and centroid update (k_update.cu).
 void launch_mean(const float *X, int64_t M, int L, double *part, int G, float *mu, float *C0,

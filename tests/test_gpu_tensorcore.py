@@ -1,0 +1,110 @@
+"""Tensor-core (BF16 operands, FP32 accumulation) nearest-codevector path vs the
+FP64 oracle and vs the FP32 path, through the C ABI (precision = LBG_PREC_BF16).
+
+Same parity rules as tests/test_gpu_parity.py.  On integer image data the
+BF16 path must give the oracle's assignments outside near-ties (it certifies
+every row or re-scores it exactly); on data that is not BF16-exact it must
+stay correct by sending every row to the exact fallback.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from _gpu_helpers import check_assign, check_codebook, check_D
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbg():
+    from paper_0910_4711_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_0910_4711_gb300 as m
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def image_data(seed, H, W, b):
+    from paper_0910_4711_gb300 import synth
+    return synth.blocks(synth.make_image(seed, H, W), b)
+
+
+def codebook_from(X, N, seed):
+    rng = np.random.default_rng(seed)
+    return (X[rng.choice(X.shape[0], N, replace=False)] +
+            rng.uniform(-0.5, 0.5, (N, X.shape[1]))).astype(np.float32)
+
+
+@pytest.mark.parametrize("H,b,N", [(256, 4, 256), (512, 8, 1000), (256, 8, 64), (512, 4, 4096),
+                                   (128, 4, 7)])
+def test_encode_bf16_matches_oracle(lbg, H, b, N):
+    X = image_data(H + N, H, H, b)
+    X = X[: X.shape[0] - 37]                      # ragged tail of the 512-row tiles
+    C = codebook_from(X, N, 1)
+    r = lbg.vq_encode(dev(X), dev(C), precision="bf16")
+    a_ref, e_ref, gap = oracle.assign(X, C.astype(np.float64))
+    check_assign(X, C, host(r.idx), a_ref, e_ref, gap)
+    check_D(r.D, float(e_ref.sum()))
+    assert r.n_exact < 0.05 * X.shape[0]          # integer data: almost every row certified
+
+
+def test_encode_bf16_equals_fp32(lbg):
+    X = image_data(5, 512, 512, 8)
+    C = codebook_from(X, 512, 2)
+    r16 = lbg.vq_encode(dev(X), dev(C), precision="bf16")
+    r32 = lbg.vq_encode(dev(X), dev(C), precision="fp32")
+    a_ref, e_ref, gap = oracle.assign(X, C.astype(np.float64))
+    diff = host(r16.idx) != host(r32.idx)
+    assert np.all(gap[diff] <= 1e-5)
+    check_D(r16.D, r32.D)
+
+
+def test_bf16_non_integer_data_falls_back_exactly(lbg):
+    rng = np.random.default_rng(9)
+    X = (rng.standard_normal((3000, 32)) * 3.3).astype(np.float32)
+    C = codebook_from(X, 100, 3)
+    r = lbg.vq_encode(dev(X), dev(C), precision="bf16")
+    a_ref, e_ref, gap = oracle.assign(X, C.astype(np.float64))
+    check_assign(X, C, host(r.idx), a_ref, e_ref, gap)
+    assert r.n_exact == X.shape[0]
+
+
+def test_bf16_rejects_large_dimension(lbg):
+    X = np.zeros((10, 128), np.float32)
+    with pytest.raises(lbg.LBGError) as ei:
+        lbg.vq_encode(dev(X), dev(X[:2]), precision="bf16")
+    assert ei.value.status == -7
+
+
+def test_lloyd_step_bf16_matches_oracle(lbg):
+    X = image_data(77, 512, 512, 8)
+    C = codebook_from(X, 512, 4)
+    r = lbg.lbg_lloyd_step(dev(X), dev(C), precision="bf16")
+    s = oracle.lloyd_step(X, C.astype(np.float64))
+    a = host(r.assign)
+    check_assign(X, C, a, s.a, s.e, s.gap)
+    check_D(r.D, s.D)
+    C_upd, _ = oracle.update(X, a, C.astype(np.float64))
+    check_codebook(host(r.C), C_upd)
+
+
+def test_train_bf16_matches_oracle(lbg):
+    X = image_data(1, 256, 256, 4)
+    r = lbg.lbg_train(dev(X), 64, delta=0.01, theta=1e-3, precision="bf16")
+    C = host(r.C)
+    a_ref, e_ref, gap = oracle.assign(X, C.astype(np.float64))
+    check_assign(X, C, host(r.assign), a_ref, e_ref, gap)
+    check_D(r.D, float(e_ref.sum()))
+    t = oracle.lbg_train(X, 64, 0.01, 1e-3)
+    if t.near_ties() == 0:
+        assert r.passes_per_stage() == t.passes_per_stage()
+        check_codebook(C, t.C)
