@@ -60,6 +60,8 @@ def parse():
                     help="form timed for the headline value (the other is timed beside it)")
     ap.add_argument("--fp32-steps", type=int, default=3,
                     help="timed steps of the other form (0: skip it)")
+    ap.add_argument("--no-grad", action="store_true",
+                    help="skip the differentiation leg (GMM, M=262144, L=32, N=512)")
     return ap.parse_args()
 
 
@@ -367,6 +369,12 @@ def run_ours(args):
     if other_line is not None:
         line["other_precision"] = other_line
 
+    # differentiation form: D(X, C) forward (nearest codevector) + backward at
+    # the fixed cell table, on Gaussian-mixture vectors (M=262144, L=32, 512
+    # components, sigma 0.1), codebook from LBG to N=512
+    if not args.no_grad:
+        line["differentiation"] = grad_leg(lbg, synth, torch, stream, flush, args, dist)
+
     # end to end through the public API with host buffers
     if not args.no_e2e:
         Xh = torch.from_numpy(X_np).pin_memory()
@@ -395,6 +403,41 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def grad_leg(lbg, synth, torch, stream, flush, args, dist):
+    Xg_np, _, _ = synth.gmm(4, 262144, L=32, K=512, sigma=0.1)
+    Mg, Lg = Xg_np.shape
+    Ng = 512
+    Xg = torch.from_numpy(Xg_np).cuda()
+    Cg = lbg.lbg_train(Xg, Ng, delta=0.01, theta=1e-3).C
+    idx = torch.empty(Mg, dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        lbg.vq_encode(Xg, Cg, idx_out=idx)
+        lbg.distortion_backward(Xg, Cg, idx)
+    fw, bw, bwph = [], [], []
+    for _ in range(max(3, args.steps)):
+        flush.zero_()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        lbg.vq_encode(Xg, Cg, idx_out=idx)
+        e1.record(stream)
+        D, dC, dX, ph = lbg.distortion_backward(Xg, Cg, idx, phase_ms=True)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        fw.append(e0.elapsed_time(e1))
+        bw.append(e1.elapsed_time(e2))
+    fwd = max_over_ranks(dist, statistics.mean(fw))
+    bwd = max_over_ranks(dist, statistics.mean(bw))
+    bytes_bwd = 3 * Mg * Lg * 4 + 2 * Mg * 4 + 2 * Ng * Lg * 4
+    return {"workload": "gmm262144_l32_n512: 262144 Gaussian-mixture vectors, L=32, 512 components "
+                        "(sigma 0.1, means U[0,1]^32), codebook from LBG to N=512",
+            "forward_ms": fwd, "backward_ms": bwd, "D": D,
+            "backward_gbs": bytes_bwd / (bwd / 1e3) / 1e9,
+            "backward_bytes": bytes_bwd,
+            "backward_work": "read X twice (dX pass, cell sums), write dX, read the cell table twice, "
+                             "read C, write dC: 3*M*L*4 + 2*M*4 + 2*N*L*4 bytes",
+            "forward_evals_per_s": Mg * Ng / (fwd / 1e3)}
 
 
 def main():

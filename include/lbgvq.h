@@ -164,6 +164,21 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
                      int32_t *idx, float *Xhat, double *D, const lbg_opts *opts);
 
 /*
+ * lbg_distortion_backward -- the distortion of Sec. 2.2, D = sum_m
+ * ||x_m - c_a(m)||^2, at a FIXED cell table a, and its gradients scaled by
+ * the upstream gradient gD (the differentiable form of the paper's
+ * distortion; the paper itself has no gradient):
+ *   dC[n] = 2 gD (count_n c_n - sum_{a(m)=n} x_m)      [N x L], nullable
+ *   dX[m] = 2 gD (x_m - c_a(m))                         [M x L], nullable
+ *   D     = the distortion at the fixed cell table      host out, nullable
+ *   X [M x L], C [N x L], assign [M] (values in [0, N)) as for the other calls.
+ * dC is deterministic (fixed-order cell sums, no float atomics).
+ */
+lbg_status lbg_distortion_backward(const float *X, int64_t M, int32_t L, const float *C, int32_t N,
+                                   const int32_t *assign, float gD, float *dC, float *dX, double *D,
+                                   const lbg_opts *opts);
+
+/*
  * vq_encode_noalloc -- vq_encode for callers that cannot allocate device
  * memory.  (The paper has no counterpart: it concerns how this library gets
  * its scratch, not the method.)

@@ -4,8 +4,8 @@ The computation runs in the CUDA library ``_lib/liblbgvq.so`` (C ABI in
 ``include/lbgvq.h``, kernels in ``csrc/``); this package only marshals
 arguments to it.  Build it with :func:`paper_0910_4711_gb300.build.build`.
 """
-from ._binding import (EXPORTS, LBGError, LIB_PATH, lbg_lloyd_step, lbg_train, lib,
-                       release_workspace, version, vq_encode)
+from ._binding import (EXPORTS, LBGError, LIB_PATH, distortion_backward, lbg_lloyd_step, lbg_train,
+                       lib, release_workspace, version, vq_encode)
 
-__all__ = ["lbg_train", "lbg_lloyd_step", "vq_encode", "release_workspace", "version", "lib",
-           "LBGError", "LIB_PATH", "EXPORTS"]
+__all__ = ["lbg_train", "lbg_lloyd_step", "vq_encode", "distortion_backward", "release_workspace",
+           "version", "lib", "LBGError", "LIB_PATH", "EXPORTS"]

@@ -26,7 +26,7 @@ STATUS = {0: "LBG_OK", 1: "LBG_WARN_MAXPASS", -1: "LBG_ERR_ARG", -2: "LBG_ERR_NO
 PHASES = ("prep", "assign", "exact", "update", "total")
 ACTIONS = ("update", "split", "finish")
 EXPORTS = ("lbg_opts_init", "lbg_train", "lbg_lloyd_step", "vq_encode", "lbg_status_string",
-           "lbg_release_workspace", "lbg_version")
+           "lbg_release_workspace", "lbg_version", "lbg_distortion_backward")
 
 
 class LBGError(RuntimeError):
@@ -71,6 +71,9 @@ def lib():
         L.lbg_lloyd_step.restype = ctypes.c_int
         L.vq_encode.argtypes = [P, i64, i32, P, i32, P, P, P, ctypes.POINTER(Opts)]
         L.vq_encode.restype = ctypes.c_int
+        L.lbg_distortion_backward.argtypes = [P, i64, i32, P, i32, P, ctypes.c_float, P, P, P,
+                                              ctypes.POINTER(Opts)]
+        L.lbg_distortion_backward.restype = ctypes.c_int
         L.lbg_status_string.argtypes = [ctypes.c_int]
         L.lbg_status_string.restype = ctypes.c_char_p
         L.lbg_release_workspace.argtypes = []
@@ -262,6 +265,26 @@ def vq_encode(X, C, decode: bool = False, with_distortion: bool = True, phase_ms
                                 ctypes.byref(o)))
     return EncodeResult(rc, I, H, D.value if with_distortion else float("nan"), keep["nex"].value,
                         _phases(keep))
+
+
+def distortion_backward(X, C, assign, grad_D: float = 1.0, want_dC: bool = True,
+                        want_dX: bool = True, phase_ms: bool = False, stream=None):
+    """D at the fixed cell table `assign` and its gradients (see lbg_distortion_backward in
+    lbgvq.h).  Returns (D, dC or None, dX or None, phase_ms)."""
+    Xo, xp, _ = _prep(X, "f32", "X")
+    M, L = int(X.shape[0]), int(X.shape[1])
+    N = int(C.shape[0])
+    Co, cp, _ = _prep(C, "f32", "C")
+    Ao, ap, _ = _prep(assign, "i32", "assign")
+    dC = _empty_like_src(C, (N, L), "f32") if want_dC else None
+    dX = _empty_like_src(X, (M, L), "f32") if want_dX else None
+    dC, dcp, _ = _prep(dC, "f32", "dC")
+    dX, dxp, _ = _prep(dX, "f32", "dX")
+    o, keep = _opts(_cuda_ref(X, C, assign), stream=stream, phase=phase_ms)
+    D = ctypes.c_double(0.0)
+    _check(lib().lbg_distortion_backward(xp, M, L, cp, N, ap, float(grad_D), dcp, dxp,
+                                         ctypes.byref(D), ctypes.byref(o)))
+    return D.value, dC, dX, _phases(keep)
 
 
 def release_workspace() -> None:

@@ -444,6 +444,57 @@ __global__ void k_combine(const float *__restrict__ pieces, const int32_t *__res
     C_out[i] = (float)s / (float)(b - a);
 }
 
+// ---------------------------------------------------------------- backward
+// Distortion at a fixed cell table, D = sum_m ||x_m - c_a(m)||^2, and its
+// gradients (the differentiable form of the paper's distortion).  One warp
+// per row group: G lanes read a row with float4 loads (L = 4G), lane sums in
+// index order within its float4, a fixed shuffle tree across the G lanes.
+//   e[m]  = ||x_m - c_a(m)||^2            (for D through k_hist / k_ctl)
+//   dX[m] = 2 gD (x_m - c_a(m))           (nullable)
+__global__ void __launch_bounds__(256) k_grad_x(const float *__restrict__ X, int64_t M, int L,
+                                                const float *__restrict__ C, int N,
+                                                const int32_t *__restrict__ assign, float gD,
+                                                float *__restrict__ e, float *__restrict__ dX,
+                                                DevState *st)
+{
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    int a = assign[m];
+    if (a < 0 || a >= N) {
+        flag_error(st, ERR_INTERNAL);
+        a = a < 0 ? 0 : N - 1;
+    }
+    const float *xr = X + m * L;
+    const float *cr = C + (int64_t)a * L;
+    float *gr = dX ? dX + m * L : nullptr;
+    const float g2 = 2.0f * gD;
+    float d2 = 0.f;
+    for (int l = 0; l < L; ++l) {
+        const float d = xr[l] - cr[l];
+        d2 = fmaf(d, d, d2);
+        if (gr) gr[l] = g2 * d;
+    }
+    e[m] = d2;
+}
+
+// dC_n = 2 gD (count_n c_n - sum_{a(m)=n} x_m): the cell sums come from the
+// same deterministic pieces as the centroid update (FP64 combine in order).
+__global__ void k_combine_grad(const float *__restrict__ pieces, const int32_t *__restrict__ off,
+                               int N, int L, int64_t S, const float *__restrict__ C, float gD,
+                               float *__restrict__ dC)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)N * L) return;
+    const int n = (int)(i / L), l = (int)(i - (int64_t)n * L);
+    const int64_t a = off[n], b = off[n + 1];
+    double s = 0.0;
+    if (b > a) {
+        const int64_t q0 = a / S, q1 = (b - 1) / S;
+        for (int64_t q = q0; q <= q1; ++q) s += (double)pieces[(size_t)(n + q) * L + l];
+    }
+    dC[i] = (float)(2.0 * (double)gD * ((double)(b - a) * (double)C[i] - s));
+}
+
 // ---------------------------------------------------------------- split
 // [c + delta], [c - delta] per centroid, interleaved, rounded once from FP64.
 __global__ void k_split(const float *__restrict__ C_cur, float *__restrict__ C_alt, int L,
@@ -557,6 +608,20 @@ void launch_combine(const float *pieces, const int32_t *off, const int32_t *n_de
     const int64_t total = (int64_t)n_host * L;
     k_combine<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(pieces, off, n_dev, n_host, L, S, C_in,
                                                              C_out, st, train ? 1 : 0);
+}
+
+void launch_grad_x(const float *X, int64_t M, int L, const float *C, int N, const int32_t *assign,
+                   float gD, float *e, float *dX, DevState *st, cudaStream_t s)
+{
+    if (M == 0) return;
+    k_grad_x<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(X, M, L, C, N, assign, gD, e, dX, st);
+}
+
+void launch_combine_grad(const float *pieces, const int32_t *off, int N, int L, int64_t S,
+                         const float *C, float gD, float *dC, cudaStream_t s)
+{
+    const int64_t total = (int64_t)N * L;
+    k_combine_grad<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(pieces, off, N, L, S, C, gD, dC);
 }
 
 void launch_split(const float *C_cur, float *C_alt, int N_alloc, int L, double delta, DevState *st,

@@ -463,6 +463,86 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
     return finish_status(h);
 }
 
+lbg_status lbg_distortion_backward(const float *X, int64_t M, int32_t L, const float *C, int32_t N,
+                                   const int32_t *assign, float gD, float *dC, float *dX, double *D,
+                                   const lbg_opts *opts)
+{
+    lbg_status rc = check_dims(M, L, N);
+    if (rc != LBG_OK) return rc;
+    if (!C || (M > 0 && (!X || !assign))) return LBG_ERR_ARG;
+    if (!isfinite(gD)) return LBG_ERR_ARG;
+    const lbg_opts o = resolve(opts);
+    std::lock_guard<std::mutex> lock(g_mu);
+    Call c;
+    if ((rc = begin(c, o)) != LBG_OK) return rc;
+    const int wX = M > 0 ? where(X, c.dev) : 1, wC = where(C, c.dev);
+    const int wA = M > 0 ? where(assign, c.dev) : 1;
+    const int wdC = dC ? where(dC, c.dev) : 1, wdX = dX ? where(dX, c.dev) : 1;
+    if (wX < 0 || wC < 0 || wA < 0 || wdC < 0 || wdX < 0) return LBG_ERR_ARG;
+    const bool hostC = wC == 0 || wdC == 0;
+    const Plan p = make_plan(M, L, N, 0, wX == 0, wA == 0, hostC, wdX == 0, false);
+    if ((rc = ensure_workspace(c, p.total)) != LBG_OK) return rc;
+    const size_t cbytes = sizeof(float) * (size_t)N * L;
+    DevState *st = c.at<DevState>(p.state);
+    DevState h;
+    init_state(h, N);
+    CK(cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, c.s));
+    const float *dXin = X;
+    if (M > 0 && wX == 0) {
+        CK(cudaMemcpyAsync(c.at<float>(p.Xs), X, sizeof(float) * M * L, cudaMemcpyHostToDevice, c.s));
+        dXin = c.at<float>(p.Xs);
+    }
+    const float *dCin = C;
+    if (wC == 0) {
+        CK(cudaMemcpyAsync(c.at<float>(p.Cin), C, cbytes, cudaMemcpyHostToDevice, c.s));
+        dCin = c.at<float>(p.Cin);
+    }
+    const int32_t *dA = assign;
+    if (M > 0 && wA == 0) {
+        CK(cudaMemcpyAsync(c.at<int32_t>(p.assign), assign, sizeof(int32_t) * M, cudaMemcpyHostToDevice,
+                           c.s));
+        dA = c.at<int32_t>(p.assign);
+    }
+    float *gX = dX ? (wdX ? dX : c.at<float>(p.Xhat)) : nullptr;
+    float *gC = dC ? (wdC ? dC : c.at<float>(p.Cout)) : nullptr;
+    Timer tm;
+    if ((rc = tm.init(o.phase_ms != nullptr)) != LBG_OK) return rc;
+    tm.mark(0, c.s);
+    tm.mark(1, c.s);
+    launch_grad_x(dXin, M, L, dCin, N, dA, gD, c.at<float>(p.e), gX, st, c.s);
+    tm.mark(2, c.s);
+    tm.mark(3, c.s);
+    if (M > 0) {
+        launch_hist(dA, c.at<float>(p.e), M, p.R, p.CH, nullptr, N, gC != nullptr, c.at<int32_t>(p.table),
+                    c.at<double>(p.dpart), st, false, c.s);
+        launch_ctl(c.at<double>(p.dpart), p.CH, st, MODE_STEP, 0.0, 1, N, nullptr, 0, c.s);
+    }
+    if (gC) {
+        if (M > 0) {
+            int32_t *table = c.at<int32_t>(p.table), *off = c.at<int32_t>(p.off);
+            launch_scan(table, p.CH, nullptr, N, c.at<int32_t>(p.counts), st, false, c.s);
+            launch_offsets(c.at<int32_t>(p.counts), nullptr, N, p.M, off, st, false, c.s);
+            launch_scatter(dA, p.M, p.R, p.CH, table, off, nullptr, N, c.at<int32_t>(p.perm), st, false,
+                           c.s);
+            launch_cellsum(dXin, p.M, p.L, c.at<int32_t>(p.perm), off, nullptr, N, p.S,
+                           c.at<float>(p.pieces), st, false, c.s);
+            launch_combine_grad(c.at<float>(p.pieces), off, N, L, p.S, dCin, gD, gC, c.s);
+        } else {
+            CK(cudaMemsetAsync(gC, 0, cbytes, c.s));
+        }
+    }
+    tm.mark(4, c.s);
+    CK(cudaGetLastError());
+    if (dC && wdC == 0) CK(cudaMemcpyAsync(dC, gC, cbytes, cudaMemcpyDeviceToHost, c.s));
+    if (dX && wdX == 0 && M > 0)
+        CK(cudaMemcpyAsync(dX, gX, sizeof(float) * M * L, cudaMemcpyDeviceToHost, c.s));
+    CK(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, c.s));
+    CK(cudaStreamSynchronize(c.s));
+    tm.report(o.phase_ms, true);
+    if (D) *D = M > 0 ? h.D : 0.0;
+    return finish_status(h);
+}
+
 lbg_status lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double delta, double theta,
                      float *C, int32_t n_init, int32_t *assign, double *D, const lbg_opts *opts)
 {

@@ -203,6 +203,10 @@ void launch_combine(const float *pieces, const int32_t *off, const int32_t *n_de
                     cudaStream_t s);
 void launch_split(const float *C_cur, float *C_alt, int N_alloc, int L, double delta, DevState *st,
                   cudaStream_t s);
+void launch_grad_x(const float *X, int64_t M, int L, const float *C, int N, const int32_t *assign,
+                   float gD, float *e, float *dX, DevState *st, cudaStream_t s);
+void launch_combine_grad(const float *pieces, const int32_t *off, int N, int L, int64_t S,
+                         const float *C, float gD, float *dC, cudaStream_t s);
 void launch_advance(const float *C_alt, float *C_cur, int N_alloc, int L, DevState *st,
                     cudaStream_t s);
 
