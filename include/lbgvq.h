@@ -103,6 +103,15 @@ typedef struct lbg_opts {
     int32_t *n_records;         /* host: number of passes run (may exceed capacity), or NULL */
     float *phase_ms;            /* host float[LBG_NUM_PHASES]: device time per phase, or NULL */
     int32_t *n_exact;           /* host: rows re-scored exactly (step / encode), or NULL */
+    int32_t split_multiplicative; /* 0 (default, the paper): c + delta, c - delta;
+                                     1: c (1 + delta), c (1 - delta) (lbg_train) */
+    int32_t reseed_empty;       /* 0 (default): an empty cell keeps its codevector;
+                                   1: after each update, every empty cell (in index order)
+                                   takes c_b + delta from the largest cell b, which moves to
+                                   c_b - delta (lbg_train, lbg_lloyd_step; uses delta_reseed
+                                   in lbg_lloyd_step) */
+    double delta_reseed;        /* offset for reseed_empty in lbg_lloyd_step (lbg_train uses
+                                   its delta) */
 } lbg_opts;
 
 /* Fill *opts with the defaults (FP32, 1000 passes, default stream, no trace). */

@@ -68,6 +68,8 @@ def _load():
         lib.oracle_max_threads.restype = ctypes.c_int
         lib.oracle_mean.argtypes = [P, i64, i32, P]
         lib.oracle_split.argtypes = [P, i32, i32, f64, P]
+        lib.oracle_split_mode.argtypes = [P, i32, i32, f64, i32, P]
+        lib.oracle_reseed.argtypes = [P, P, i32, i32, f64]
         lib.oracle_assign.argtypes = [P, i64, i32, P, i32, P, P, P, i32]
         lib.oracle_sum.argtypes = [P, i64]
         lib.oracle_sum.restype = f64
@@ -76,8 +78,8 @@ def _load():
         lib.oracle_distortion_fixed.argtypes = [P, i64, i32, P, P]
         lib.oracle_distortion_fixed.restype = f64
         lib.oracle_grad.argtypes = [P, i64, i32, P, i32, P, P, P]
-        lib.oracle_lbg_train.argtypes = [P, i64, i32, i32, f64, f64, i32, i32, P, i32, P, P,
-                                         P, P, P, P, P, f64, i32, P]
+        lib.oracle_lbg_train.argtypes = [P, i64, i32, i32, f64, f64, i32, i32, i32, i32, P, i32,
+                                         P, P, P, P, P, P, P, f64, i32, P]
         _lib = lib
         return lib
 
@@ -118,12 +120,22 @@ def mean(X) -> np.ndarray:
     return out
 
 
-def split(C, delta: float) -> np.ndarray:
-    """[2n, L]: row 2i = c_i + delta, row 2i+1 = c_i - delta."""
+def split(C, delta: float, multiplicative: bool = False) -> np.ndarray:
+    """[2n, L]: row 2i = c_i + delta, row 2i+1 = c_i - delta (or c_i (1 +- delta))."""
     C = _c(C)
     out = np.empty((2 * C.shape[0], C.shape[1]), np.float64)
-    _check(_load().oracle_split(_ptr(C), C.shape[0], C.shape[1], float(delta), _ptr(out)), "split")
+    _check(_load().oracle_split_mode(_ptr(C), C.shape[0], C.shape[1], float(delta),
+                                     int(bool(multiplicative)), _ptr(out)), "split")
     return out
+
+
+def reseed(C, counts, delta: float):
+    """Variant V2 (see lbg_oracle.c): (C', counts') with the empty cells re-seeded."""
+    C = _c(C).copy()
+    counts = np.ascontiguousarray(counts, dtype=np.int64).copy()
+    _check(_load().oracle_reseed(_ptr(C), _ptr(counts), C.shape[0], C.shape[1], float(delta)),
+           "reseed")
+    return C, counts
 
 
 def assign(X, C, nthreads: int = 0):
@@ -223,7 +235,8 @@ class Train:
 
 def lbg_train(X, N: int, delta: float, theta: float, max_passes: int = 1000,
               nthreads: int = 0, trace_cap: int = 100000, C_init=None,
-              near_tol: float = 1e-5) -> Train:
+              near_tol: float = 1e-5, split_multiplicative: bool = False,
+              reseed_empty: bool = False) -> Train:
     """The whole LBG design up to N codevectors, from the centroid of X or,
     if C_init ([n_init, L]) is given, from that initial alphabet (Sec. 2.2)."""
     X = _x(X)
@@ -239,7 +252,8 @@ def lbg_train(X, N: int, delta: float, theta: float, max_passes: int = 1000,
     rnear = np.empty(trace_cap, np.int32)
     cnt = ctypes.c_int32()
     rc = _load().oracle_lbg_train(_ptr(X), M, L, int(N), float(delta), float(theta),
-                                  int(max_passes), int(nthreads), _ptr(Ci), n_init, _ptr(C),
+                                  int(max_passes), int(nthreads), int(bool(split_multiplicative)),
+                                  int(bool(reseed_empty)), _ptr(Ci), n_init, _ptr(C),
                                   _ptr(a),
                                   ctypes.byref(D), _ptr(rn), _ptr(rp), _ptr(rD), _ptr(rnear),
                                   float(near_tol), trace_cap, ctypes.byref(cnt))

@@ -41,6 +41,13 @@
  *   R11 a stage that reaches max_passes assignments without meeting the
  *       test is ended there (status LBG oracle WARN_MAXPASS = 1) and
  *       training continues with the next split.
+ * Opt-in variants (not the paper's defaults):
+ *   V1 multiplicative split: child 2i = c_i (1 + delta), 2i+1 = c_i (1 - delta).
+ *   V2 empty-cell re-seeding after an update: for every empty cell e in
+ *      increasing index order, take the cell b with the largest count (lowest
+ *      index on ties), set c_e = c_b + delta and c_b = c_b - delta (every
+ *      component), and let e take half of b's count (floor) and b keep the
+ *      rest, so that the next empty cell may pick another cell.
  */
 #include <math.h>
 #include <stdint.h>
@@ -94,14 +101,42 @@ int oracle_mean(const float *X, int64_t M, int32_t L, double *c_out)
 /* Codebook splitting (Algorithm 1; Sec. 3.2 "Codebook Splitting"): every
  * centroid c_i of the n-entry codebook C becomes two codevectors,
  * C2[2i] = c_i + delta and C2[2i+1] = c_i - delta (readings R5, R6). */
-int oracle_split(const double *C, int32_t n, int32_t L, double delta, double *C2)
+int oracle_split_mode(const double *C, int32_t n, int32_t L, double delta, int32_t mult, double *C2)
 {
     if (!C || !C2 || n < 1 || L < 1) return ORACLE_ERR_ARG;
     for (int32_t i = 0; i < n; ++i)
         for (int32_t l = 0; l < L; ++l) {
-            C2[(2 * (int64_t)i) * L + l] = C[(int64_t)i * L + l] + delta;
-            C2[(2 * (int64_t)i + 1) * L + l] = C[(int64_t)i * L + l] - delta;
+            const double c = C[(int64_t)i * L + l];
+            C2[(2 * (int64_t)i) * L + l] = mult ? c * (1.0 + delta) : c + delta;
+            C2[(2 * (int64_t)i + 1) * L + l] = mult ? c * (1.0 - delta) : c - delta;
         }
+    return ORACLE_OK;
+}
+
+int oracle_split(const double *C, int32_t n, int32_t L, double delta, double *C2)
+{
+    return oracle_split_mode(C, n, L, delta, 0, C2);
+}
+
+/* Variant V2: re-seed the empty cells of an updated codebook C (in place)
+ * from the largest cells; counts [N] are the cell sizes (updated in place). */
+int oracle_reseed(double *C, int64_t *counts, int32_t N, int32_t L, double delta)
+{
+    if (!C || !counts || N < 1 || L < 1) return ORACLE_ERR_ARG;
+    for (int32_t e = 0; e < N; ++e) {
+        if (counts[e] != 0) continue;
+        int32_t b = 0;
+        for (int32_t n = 1; n < N; ++n)
+            if (counts[n] > counts[b]) b = n;
+        if (counts[b] < 2) break;   /* nothing left to split */
+        for (int32_t l = 0; l < L; ++l) {
+            const double c = C[(int64_t)b * L + l];
+            C[(int64_t)e * L + l] = c + delta;
+            C[(int64_t)b * L + l] = c - delta;
+        }
+        counts[e] = counts[b] / 2;
+        counts[b] -= counts[e];
+    }
     return ORACLE_OK;
 }
 
@@ -280,8 +315,8 @@ static int is_pow2(int32_t n) { return n > 0 && (n & (n - 1)) == 0; }
  * receives the number of passes run (which may exceed rec_cap).  Returns 0,
  * 1 (WARN_MAXPASS) or a negative error. */
 int oracle_lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double delta,
-                     double theta, int32_t max_passes, int32_t nthreads,
-                     const double *C_init, int32_t n_init, double *C_out,
+                     double theta, int32_t max_passes, int32_t nthreads, int32_t split_mult,
+                     int32_t reseed, const double *C_init, int32_t n_init, double *C_out,
                      int32_t *a_out, double *D_out, int32_t *rec_n, int32_t *rec_pass,
                      double *rec_D, int32_t *rec_near, double near_tol, int32_t rec_cap,
                      int32_t *rec_count)
@@ -297,11 +332,13 @@ int oracle_lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double del
     double *Cn = (double *)malloc((size_t)N * L * sizeof(double));
     double *e = (double *)malloc((size_t)M * sizeof(double));
     double *gap = rec_near ? (double *)malloc((size_t)M * sizeof(double)) : NULL;
-    if (!C || !Cn || !e || (rec_near && !gap)) {
+    int64_t *cnt = (int64_t *)malloc((size_t)N * sizeof(int64_t));
+    if (!C || !Cn || !e || !cnt || (rec_near && !gap)) {
         free(C);
         free(Cn);
         free(e);
         free(gap);
+        free(cnt);
         return ORACLE_ERR_NOMEM;
     }
     int status = ORACLE_OK;
@@ -335,12 +372,13 @@ int oracle_lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double del
                 status = ORACLE_WARN_MAXPASS;
                 break;
             }
-            oracle_update(X, M, L, a_out, n, C, Cn, NULL);
+            oracle_update(X, M, L, a_out, n, C, Cn, cnt);
+            if (reseed) oracle_reseed(Cn, cnt, n, L, delta);
             memcpy(C, Cn, (size_t)n * L * sizeof(double));
             D_prev = D;
         }
         if (n == N) break;
-        oracle_split(C, n, L, delta, Cn);
+        oracle_split_mode(C, n, L, delta, split_mult, Cn);
         n *= 2;
         memcpy(C, Cn, (size_t)n * L * sizeof(double));
     }
@@ -351,5 +389,6 @@ int oracle_lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double del
     free(Cn);
     free(e);
     free(gap);
+    free(cnt);
     return status;
 }

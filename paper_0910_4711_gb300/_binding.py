@@ -45,7 +45,9 @@ class Opts(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("records", ctypes.POINTER(PassRecord)),
                 ("max_records", ctypes.c_int32), ("n_records", ctypes.POINTER(ctypes.c_int32)),
                 ("phase_ms", ctypes.POINTER(ctypes.c_float)),
-                ("n_exact", ctypes.POINTER(ctypes.c_int32))]
+                ("n_exact", ctypes.POINTER(ctypes.c_int32)),
+                ("split_multiplicative", ctypes.c_int32), ("reseed_empty", ctypes.c_int32),
+                ("delta_reseed", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -124,10 +126,14 @@ def _empty_like_src(src, shape, dtype: str):
 PRECISION = {"fp32": 0, "bf16": 1}
 
 
-def _opts(cuda_ref, max_passes=1000, records=0, phase=False, stream=None, precision="fp32"):
+def _opts(cuda_ref, max_passes=1000, records=0, phase=False, stream=None, precision="fp32",
+          split_multiplicative=False, reseed_empty=False, delta_reseed=0.0):
     o = Opts()
     lib().lbg_opts_init(ctypes.byref(o))
     o.max_passes = int(max_passes)
+    o.split_multiplicative = int(bool(split_multiplicative))
+    o.reseed_empty = int(bool(reseed_empty))
+    o.delta_reseed = float(delta_reseed)
     if precision not in PRECISION:
         raise ValueError(f"precision must be one of {sorted(PRECISION)}")
     o.precision = PRECISION[precision]
@@ -206,7 +212,8 @@ class EncodeResult:
 # ------------------------------------------------------------ entry points
 def lbg_train(X, N: int, delta: float = 0.01, theta: float = 1e-3, C_init=None,
               max_passes: int = 1000, trace: int = 4096, phase_ms: bool = False, C_out=None,
-              assign_out=None, stream=None, precision: str = "fp32") -> TrainResult:
+              assign_out=None, stream=None, precision: str = "fp32",
+              split_multiplicative: bool = False, reseed_empty: bool = False) -> TrainResult:
     """Design an N-entry codebook from X [M, L] (see lbg_train in lbgvq.h)."""
     Xo, xp, _ = _prep(X, "f32", "X")
     M, L = int(X.shape[0]), int(X.shape[1])
@@ -218,7 +225,8 @@ def lbg_train(X, N: int, delta: float = 0.01, theta: float = 1e-3, C_init=None,
     A = assign_out if assign_out is not None else _empty_like_src(X, (M,), "i32")
     Co, cp, _ = _prep(C, "f32", "C")
     Ao, ap, _ = _prep(A, "i32", "assign")
-    o, keep = _opts(_cuda_ref(X, C, A), max_passes, trace, phase_ms, stream, precision)
+    o, keep = _opts(_cuda_ref(X, C, A), max_passes, trace, phase_ms, stream, precision,
+                    split_multiplicative, reseed_empty)
     D = ctypes.c_double(0.0)
     rc = _check(lib().lbg_train(xp, M, L, int(N), float(delta), float(theta), cp, n_init, ap,
                                 ctypes.byref(D), ctypes.byref(o)))
@@ -232,7 +240,8 @@ def lbg_train(X, N: int, delta: float = 0.01, theta: float = 1e-3, C_init=None,
 
 
 def lbg_lloyd_step(X, C_in, C_out=None, assign_out=None, phase_ms: bool = False,
-                   stream=None, precision: str = "fp32") -> StepResult:
+                   stream=None, precision: str = "fp32", reseed_empty: bool = False,
+                   delta_reseed: float = 0.01) -> StepResult:
     """One Lloyd pass from C_in (see lbg_lloyd_step in lbgvq.h)."""
     Xo, xp, _ = _prep(X, "f32", "X")
     M, L = int(X.shape[0]), int(X.shape[1])
@@ -242,7 +251,8 @@ def lbg_lloyd_step(X, C_in, C_out=None, assign_out=None, phase_ms: bool = False,
     Co, cop, _ = _prep(Co, "f32", "C_out")
     A = assign_out if assign_out is not None else _empty_like_src(X, (M,), "i32")
     A, ap, _ = _prep(A, "i32", "assign")
-    o, keep = _opts(_cuda_ref(X, C_in, Co, A), stream=stream, phase=phase_ms, precision=precision)
+    o, keep = _opts(_cuda_ref(X, C_in, Co, A), stream=stream, phase=phase_ms, precision=precision,
+                    reseed_empty=reseed_empty, delta_reseed=delta_reseed)
     D = ctypes.c_double(0.0)
     rc = _check(lib().lbg_lloyd_step(xp, M, L, N, cip, cop, ap, ctypes.byref(D), ctypes.byref(o)))
     return StepResult(rc, Co, A, D.value, keep["nex"].value, _phases(keep))

@@ -496,9 +496,10 @@ __global__ void k_combine_grad(const float *__restrict__ pieces, const int32_t *
 }
 
 // ---------------------------------------------------------------- split
-// [c + delta], [c - delta] per centroid, interleaved, rounded once from FP64.
+// [c + delta], [c - delta] per centroid (or c (1 + delta), c (1 - delta) when
+// mult), interleaved, rounded once from FP64.
 __global__ void k_split(const float *__restrict__ C_cur, float *__restrict__ C_alt, int L,
-                        double delta, DevState *st)
+                        double delta, int mult, DevState *st)
 {
     if (st->finished || st->action != ACT_SPLIT) return;
     const int n = st->n_cur;
@@ -506,8 +507,71 @@ __global__ void k_split(const float *__restrict__ C_cur, float *__restrict__ C_a
     if (i >= (int64_t)n * L) return;
     const int64_t c = i / L, l = i - c * L;
     const double v = (double)C_cur[i];
-    C_alt[(2 * c) * L + l] = (float)(v + delta);
-    C_alt[(2 * c + 1) * L + l] = (float)(v - delta);
+    C_alt[(2 * c) * L + l] = (float)(mult ? v * (1.0 + delta) : v + delta);
+    C_alt[(2 * c + 1) * L + l] = (float)(mult ? v * (1.0 - delta) : v - delta);
+}
+
+// Empty-cell re-seeding (opt-in variant) after an update: every empty cell e,
+// in increasing index order, takes c_b + delta from the cell b with the
+// largest count (lowest index on ties), c_b becomes c_b - delta, and e takes
+// half of b's count.  One CTA: integer counts in shared memory, a fixed-order
+// argmax per empty cell.
+__global__ void __launch_bounds__(1024) k_reseed(const int32_t *__restrict__ off,
+                                                 const int32_t *n_dev, int n_host, int L,
+                                                 double delta, float *__restrict__ C, DevState *st,
+                                                 int train)
+{
+    if (skip_update(st, train)) return;
+    extern __shared__ int cnt[];
+    __shared__ int wbest[32], wcount[32];
+    __shared__ int s_b;
+    const int N = cur_n(n_dev, n_host);
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    for (int n = t; n < N; n += 1024) cnt[n] = off[n + 1] - off[n];
+    __syncthreads();
+    for (int e = 0; e < N; ++e) {
+        if (cnt[e] != 0) continue;   // uniform: every thread reads the same shared value
+        int bi = 0x7fffffff, bc = -1;
+        for (int n = t; n < N; n += 1024)
+            if (cnt[n] > bc) {
+                bc = cnt[n];
+                bi = n;
+            }
+        for (int o = 16; o > 0; o >>= 1) {
+            const int oc = __shfl_xor_sync(0xffffffffu, bc, o), oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (oc > bc || (oc == bc && oi < bi)) {
+                bc = oc;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            wbest[w] = bi;
+            wcount[w] = bc;
+        }
+        __syncthreads();
+        if (t == 0) {
+            int b = wbest[0], c = wcount[0];
+            for (int q = 1; q < 32; ++q)
+                if (wcount[q] > c || (wcount[q] == c && wbest[q] < b)) {
+                    c = wcount[q];
+                    b = wbest[q];
+                }
+            s_b = c >= 2 ? b : -1;
+        }
+        __syncthreads();
+        const int b = s_b;
+        if (b < 0) break;
+        for (int l = t; l < L; l += 1024) {
+            const double c = (double)C[(int64_t)b * L + l];
+            C[(int64_t)e * L + l] = (float)(c + delta);
+            C[(int64_t)b * L + l] = (float)(c - delta);
+        }
+        if (t == 0) {
+            cnt[e] = cnt[b] / 2;
+            cnt[b] -= cnt[e];
+        }
+        __syncthreads();
+    }
 }
 
 __global__ void k_copy_split(const float *__restrict__ C_alt, float *__restrict__ C_cur, int L,
@@ -624,11 +688,19 @@ void launch_combine_grad(const float *pieces, const int32_t *off, int N, int L, 
     k_combine_grad<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(pieces, off, N, L, S, C, gD, dC);
 }
 
-void launch_split(const float *C_cur, float *C_alt, int N_alloc, int L, double delta, DevState *st,
-                  cudaStream_t s)
+void launch_split(const float *C_cur, float *C_alt, int N_alloc, int L, double delta, bool mult,
+                  DevState *st, cudaStream_t s)
 {
     const int64_t total = (int64_t)(N_alloc / 2 > 0 ? N_alloc / 2 : 1) * L;
-    k_split<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(C_cur, C_alt, L, delta, st);
+    k_split<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(C_cur, C_alt, L, delta, mult ? 1 : 0, st);
+}
+
+void launch_reseed(const int32_t *off, const int32_t *n_dev, int n_host, int L, double delta,
+                   float *C, DevState *st, bool train, cudaStream_t s)
+{
+    const size_t smem = (size_t)n_host * sizeof(int);
+    cudaFuncSetAttribute(k_reseed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_reseed<<<1, 1024, smem, s>>>(off, n_dev, n_host, L, delta, C, st, train ? 1 : 0);
 }
 
 void launch_advance(const float *C_alt, float *C_cur, int N_alloc, int L, DevState *st,

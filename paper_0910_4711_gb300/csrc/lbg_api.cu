@@ -450,6 +450,7 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
                 c.at<double>(p.dpart), st, false, c.s);
     launch_ctl(c.at<double>(p.dpart), p.CH, st, MODE_STEP, 0.0, 1, N, nullptr, 0, c.s);
     run_update(c, p, dX, nullptr, N, st, dA, dCi, dCo, false);
+    if (o.reseed_empty) launch_reseed(c.at<int32_t>(p.off), nullptr, N, L, o.delta_reseed, dCo, st, false, c.s);
     tm.mark(4, c.s);
     CK(cudaGetLastError());
     if (hostC) CK(cudaMemcpyAsync(C_out, dCo, cbytes, cudaMemcpyDefault, c.s));
@@ -606,7 +607,9 @@ lbg_status lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double del
             launch_ctl(c.at<double>(p.dpart), p.CH, st, MODE_TRAIN, theta, o.max_passes, N, rec,
                        max_rec, c.s);
             run_update(c, p, dX, n_dev, N, st, dA, Ccur, Ccur, true);
-            launch_split(Ccur, Calt, N, L, delta, st, c.s);
+            if (o.reseed_empty)
+                launch_reseed(c.at<int32_t>(p.off), n_dev, N, L, delta, Ccur, st, true, c.s);
+            launch_split(Ccur, Calt, N, L, delta, o.split_multiplicative != 0, st, c.s);
             launch_advance(Calt, Ccur, N, L, st, c.s);
         }
         if (cudaGetLastError() != cudaSuccess) {

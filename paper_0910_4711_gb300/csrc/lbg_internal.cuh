@@ -201,8 +201,10 @@ void launch_cellsum(const float *X, int64_t M, int L, const int32_t *perm, const
 void launch_combine(const float *pieces, const int32_t *off, const int32_t *n_dev, int n_host,
                     int L, int64_t S, const float *C_in, float *C_out, DevState *st, bool train,
                     cudaStream_t s);
-void launch_split(const float *C_cur, float *C_alt, int N_alloc, int L, double delta, DevState *st,
-                  cudaStream_t s);
+void launch_split(const float *C_cur, float *C_alt, int N_alloc, int L, double delta, bool mult,
+                  DevState *st, cudaStream_t s);
+void launch_reseed(const int32_t *off, const int32_t *n_dev, int n_host, int L, double delta,
+                   float *C, DevState *st, bool train, cudaStream_t s);
 void launch_grad_x(const float *X, int64_t M, int L, const float *C, int N, const int32_t *assign,
                    float gD, float *e, float *dX, DevState *st, cudaStream_t s);
 void launch_combine_grad(const float *pieces, const int32_t *off, int N, int L, int64_t S,

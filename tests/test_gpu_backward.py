@@ -112,7 +112,7 @@ def test_autograd_function(lbg, gmm_problem):
     # one gradient step on C lowers D (descent direction of the distortion)
     with torch.no_grad():
         C2 = C - 1e-6 * dC
-    assert float(distortion(Xd, C2)) < float(D)
+    assert float(distortion(Xd, C2)) < float(D.detach())
 
 
 def test_backward_empty_rows(lbg):

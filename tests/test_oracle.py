@@ -219,6 +219,31 @@ def test_initial_alphabet_resume():
     assert full.passes_per_stage() == [2, 3]
 
 
+def test_multiplicative_split_values_and_closed_form():
+    """Variant V1: c (1 + delta), c (1 - delta); on the uniform scalar quantizer
+    over 1..2^k the children are symmetric around c, so the closed form of the
+    additive split holds unchanged."""
+    S = oracle.split(np.array([[2.0, -4.0]]), 0.5, multiplicative=True)
+    np.testing.assert_array_equal(S, [[3.0, -6.0], [1.0, -2.0]])
+    M, N = 64, 8
+    X = (np.arange(M, dtype=np.float32) + 1)[:, None]
+    t = oracle.lbg_train(X, N, 0.01, 1e-3, split_multiplicative=True)
+    w = M // N
+    mids = np.array([(c * w + (c + 1) * w - 1) / 2.0 + 1 for c in range(N)])[::-1]
+    np.testing.assert_array_equal(t.C[:, 0], mids)
+    assert t.passes_per_stage() == [2, 3, 3, 3]
+
+
+def test_reseed_empty_cells_hand_example():
+    """Variant V2 by hand: counts [2, 4, 0, 0] -> cell 2 takes from cell 1
+    (largest): c2 = c1 + d, c1 = c1 - d, counts [2, 2, 2, 0]; cell 3 then takes
+    from cell 0 (largest, lowest index): c3 = c0 + d, c0 = c0 - d."""
+    C = np.array([[0.0, 1.0], [10.0, 10.0], [7.0, 7.0], [8.0, 8.0]])
+    C2, cnt = oracle.reseed(C, [2, 4, 0, 0], 0.5)
+    np.testing.assert_array_equal(C2, [[-0.5, 0.5], [9.5, 9.5], [10.5, 10.5], [0.5, 1.5]])
+    np.testing.assert_array_equal(cnt, [1, 2, 2, 1])
+
+
 def test_arguments_rejected():
     X = np.zeros((4, 2), np.float32)
     with pytest.raises(ValueError):
