@@ -173,6 +173,30 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
                      int32_t *idx, float *Xhat, double *D, const lbg_opts *opts);
 
 /*
+ * lbg_train_batched -- S independent LBG designs (Sec. 2.2 + Algorithm 1, as
+ * lbg_train) of uneven sizes, advanced together: every Lloyd pass of all
+ * problems is one captured sequence of launches, the nearest-codevector
+ * search one persistent launch over (problem, row tile) work items.
+ *
+ *   S        number of problems, >= 1.
+ *   X        rows of all problems concatenated in problem order, [sum M_s x L]
+ *            (device or host).
+ *   row_off  HOST int64 [S + 1]: problem s owns rows [row_off[s], row_off[s+1]),
+ *            M_s = row_off[s+1] - row_off[s] >= 1.
+ *   N        HOST int32 [S]: codebook sizes, powers of 2 <= LBG_MAX_CODEBOOK.
+ *   C        [sum N_s x L] out: codebooks concatenated in problem order.
+ *   assign   [sum M_s] out, nullable: each problem's cell table (indices local
+ *            to its codebook).
+ *   D        HOST [S] out, nullable: each problem's final distortion.
+ * opts: stream, max_passes, split_multiplicative are honoured; precision must
+ * be LBG_PREC_FP32; n_records receives the largest pass count of a problem.
+ * Per problem the results are those lbg_train would give.
+ */
+lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, int32_t L,
+                             const int32_t *N, double delta, double theta, float *C,
+                             int32_t *assign, double *D, const lbg_opts *opts);
+
+/*
  * lbg_distortion_backward -- the distortion of Sec. 2.2, D = sum_m
  * ||x_m - c_a(m)||^2, at a FIXED cell table a, and its gradients scaled by
  * the upstream gradient gD (the differentiable form of the paper's

@@ -26,7 +26,7 @@ STATUS = {0: "LBG_OK", 1: "LBG_WARN_MAXPASS", -1: "LBG_ERR_ARG", -2: "LBG_ERR_NO
 PHASES = ("prep", "assign", "exact", "update", "total")
 ACTIONS = ("update", "split", "finish")
 EXPORTS = ("lbg_opts_init", "lbg_train", "lbg_lloyd_step", "vq_encode", "lbg_status_string",
-           "lbg_release_workspace", "lbg_version", "lbg_distortion_backward")
+           "lbg_release_workspace", "lbg_version", "lbg_distortion_backward", "lbg_train_batched")
 
 
 class LBGError(RuntimeError):
@@ -76,6 +76,8 @@ def lib():
         L.lbg_distortion_backward.argtypes = [P, i64, i32, P, i32, P, ctypes.c_float, P, P, P,
                                               ctypes.POINTER(Opts)]
         L.lbg_distortion_backward.restype = ctypes.c_int
+        L.lbg_train_batched.argtypes = [i32, P, P, i32, P, f64, f64, P, P, P, ctypes.POINTER(Opts)]
+        L.lbg_train_batched.restype = ctypes.c_int
         L.lbg_status_string.argtypes = [ctypes.c_int]
         L.lbg_status_string.restype = ctypes.c_char_p
         L.lbg_release_workspace.argtypes = []
@@ -295,6 +297,48 @@ def distortion_backward(X, C, assign, grad_D: float = 1.0, want_dC: bool = True,
     _check(lib().lbg_distortion_backward(xp, M, L, cp, N, ap, float(grad_D), dcp, dxp,
                                          ctypes.byref(D), ctypes.byref(o)))
     return D.value, dC, dX, _phases(keep)
+
+
+@dataclass
+class BatchedResult:
+    status: int
+    C: object            # [sum N_s, L] codebooks concatenated
+    assign: object       # [sum M_s] local cell indices
+    D: list
+    code_off: list       # codebook s is C[code_off[s]:code_off[s+1]]
+    max_passes_run: int
+    phase_ms: dict | None
+
+    def codebook(self, s):
+        return self.C[self.code_off[s]:self.code_off[s + 1]]
+
+
+def lbg_train_batched(X, row_off, N, delta: float = 0.01, theta: float = 1e-3,
+                      max_passes: int = 1000, phase_ms: bool = False, stream=None,
+                      split_multiplicative: bool = False) -> BatchedResult:
+    """S independent LBG designs at once (see lbg_train_batched in lbgvq.h).  X holds the rows
+    of all problems concatenated; row_off (S+1 offsets) and N (S sizes) are Python sequences."""
+    Xo, xp, _ = _prep(X, "f32", "X")
+    L = int(X.shape[1])
+    S = len(N)
+    ro = np.ascontiguousarray(row_off, dtype=np.int64)
+    Nn = np.ascontiguousarray(N, dtype=np.int32)
+    if ro.shape[0] != S + 1:
+        raise ValueError("row_off must have len(N) + 1 entries")
+    code_off = [0]
+    for n in Nn.tolist():
+        code_off.append(code_off[-1] + n)
+    C = _empty_like_src(X, (code_off[-1], L), "f32")
+    A = _empty_like_src(X, (int(ro[-1]),), "i32")
+    Co, cp, _ = _prep(C, "f32", "C")
+    Ao, ap, _ = _prep(A, "i32", "assign")
+    D = np.zeros(S, np.float64)
+    o, keep = _opts(_cuda_ref(X, C), max_passes, 0, phase_ms, stream, "fp32", split_multiplicative)
+    nrec = ctypes.c_int32(0)
+    o.n_records = ctypes.pointer(nrec)
+    rc = _check(lib().lbg_train_batched(S, xp, ro.ctypes.data, L, Nn.ctypes.data, float(delta),
+                                        float(theta), cp, ap, D.ctypes.data, ctypes.byref(o)))
+    return BatchedResult(rc, C, A, D.tolist(), code_off, nrec.value, _phases(keep))
 
 
 def release_workspace() -> None:

@@ -79,18 +79,16 @@ __global__ void __launch_bounds__(256) k_codebook_mean(const float *__restrict__
 // stores.
 constexpr int PREP_TILE = 32;
 
-__global__ void __launch_bounds__(256)
-    k_prep(const float *__restrict__ C, const int32_t *n_dev, int n_host, int L, int Lp,
-           const float *__restrict__ mu, float *__restrict__ Cp, float *__restrict__ kn,
-           float *__restrict__ CT, int NP, DevState *st)
+__device__ __forceinline__ void body_prep(const float *__restrict__ C, int N, int L, int Lp,
+                                          const float *__restrict__ mu, float *__restrict__ Cp,
+                                          float *__restrict__ kn, float *__restrict__ CT,
+                                          DevState *st, int blk)
 {
-    if (st->finished) return;
     __shared__ float orig[PREP_TILE][LMAX + 1];
     __shared__ float cen[PREP_TILE][LMAX + 1];
     __shared__ double sqs[PREP_TILE];
-    const int N = cur_n(n_dev, n_host);
     const int npad = round_up(N, BN);
-    const int n0 = blockIdx.x * PREP_TILE;
+    const int n0 = blk * PREP_TILE;
     if (n0 >= npad) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     bool finite = true;
@@ -144,39 +142,50 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-__device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
-
-// Nearest codevector of BM rows per CTA (see the file header).
-__global__ void __launch_bounds__(ASSIGN_THREADS, 2)
-    k_assign_f32(const float *__restrict__ X, int64_t M, int L, int Lp, const float *__restrict__ Cp,
-                 const float *__restrict__ kn, const int32_t *n_dev, int n_host,
-                 const float *__restrict__ mu, const float *__restrict__ C, DevState *st,
-                 int32_t *__restrict__ assign, float *__restrict__ e, int32_t *__restrict__ flags)
+__global__ void __launch_bounds__(256)
+    k_prep(const float *__restrict__ C, const int32_t *n_dev, int n_host, int L, int Lp,
+           const float *__restrict__ mu, float *__restrict__ Cp, float *__restrict__ kn,
+           float *__restrict__ CT, int NP, DevState *st)
 {
     if (st->finished) return;
-    extern __shared__ __align__(128) float smem[];
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ int s_abort;
-    __shared__ float rec_v1[2][BM], rec_v2[2][BM];
-    __shared__ int rec_id[2][BM];
+    (void)NP;
+    body_prep(C, cur_n(n_dev, n_host), L, Lp, mu, Cp, kn, CT, st, blockIdx.x);
+}
 
+__device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+
+// Shared state of an assignment CTA (static shared memory of the kernel).
+struct AssignSmem {
+    uint64_t bar[2];
+    int abort;
+    float rec_v1[2][BM], rec_v2[2][BM];
+    int rec_id[2][BM];
+};
+
+// Nearest codevector of the BM rows starting at m0 (see the file header).
+// The two chunk barriers persist across calls of one CTA: use0/use1 count
+// their completed phases.  Returns false (after reporting) if a bulk copy
+// timed out; every thread of the CTA returns the same value.
+__device__ __forceinline__ bool assign_f32_tile(
+    const float *__restrict__ X, int64_t M, int L, int Lp, const float *__restrict__ Cp,
+    const float *__restrict__ kn, int N, const float *__restrict__ mu, const float *__restrict__ C,
+    DevState *st, int32_t *__restrict__ assign, float *__restrict__ e, int32_t *__restrict__ flags,
+    int64_t m0, float *smem, AssignSmem &sh, uint32_t &use0, uint32_t &use1)
+{
+    uint64_t *bar = sh.bar;
+    auto &rec_v1 = sh.rec_v1;
+    auto &rec_v2 = sh.rec_v2;
+    auto &rec_id = sh.rec_id;
     const int tid = threadIdx.x;
-    const int N = cur_n(n_dev, n_host);
     const int nchunk = (N + BN - 1) / BN;
     const int chunk_floats = (Lp + 1) * BN;
     const uint32_t chunk_bytes = (uint32_t)chunk_floats * 4u;
     float *xs = smem;                       // [Lp][BM]
     float *cbuf0 = xs + Lp * BM;            // [Lp + 1][BN]
     float *cbuf1 = cbuf0 + chunk_floats;
-    const int64_t m0 = (int64_t)blockIdx.x * BM;
+    const uint32_t base0 = use0, base1 = use1;
+    auto parity = [&](int k) -> uint32_t { return ((k & 1 ? base1 : base0) + (uint32_t)(k >> 1)) & 1u; };
 
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-        s_abort = 0;
-    }
-    __syncthreads();
     if (tid == 0) {
         for (int k = 0; k < 2 && k < nchunk; ++k) {
             mbar_expect_tx(&bar[k], chunk_bytes);
@@ -219,8 +228,8 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 2)
     for (int k = 0; k < nchunk; ++k) {
         const int b = k & 1;
         const float *cb = b ? cbuf1 : cbuf0;
-        const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)(k >> 1) & 1u);
-        if (!ok) s_abort = 1;
+        const bool ok = mbar_wait_bounded(&bar[b], parity(k));
+        if (!ok) sh.abort = 1;
         if (ok) {
             float acc[8][8];
             {
@@ -259,7 +268,7 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 2)
             }
         }
         __syncthreads();
-        if (s_abort) {
+        if (sh.abort) {
             k_stop = k;
             break;
         }
@@ -274,11 +283,13 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 2)
         // still in flight, report, and leave the rows unwritten.
         if (tid == 0) {
             for (int kk = k_stop; kk < nchunk && kk < k_stop + 2; ++kk)
-                (void)mbar_wait_bounded(&bar[kk & 1], (uint32_t)(kk >> 1) & 1u);
+                (void)mbar_wait_bounded(&bar[kk & 1], parity(kk));
             flag_error(st, ERR_TIMEOUT);
         }
-        return;
+        return false;
     }
+    use0 = base0 + (uint32_t)((nchunk + 1) >> 1);
+    use1 = base1 + (uint32_t)(nchunk >> 1);
 
     // Merge the 8 lanes that share rows (lx = 0..7), then the two warps (wc).
 #pragma unroll
@@ -303,10 +314,9 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 2)
         }
     }
     __syncthreads();
-    if (tid >= BM) return;
     const int r = tid;
     const int64_t m = m0 + r;
-    if (m >= M) return;
+    if (tid >= BM || m >= M) return true;
     float V1, V2;
     int ID;
     {
@@ -383,6 +393,62 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 2)
     } else {
         flags[atomicAdd(&st->nflag, 1)] = (int32_t)m;
     }
+    return true;
+}
+
+__global__ void __launch_bounds__(ASSIGN_THREADS, 2)
+    k_assign_f32(const float *__restrict__ X, int64_t M, int L, int Lp, const float *__restrict__ Cp,
+                 const float *__restrict__ kn, const int32_t *n_dev, int n_host,
+                 const float *__restrict__ mu, const float *__restrict__ C, DevState *st,
+                 int32_t *__restrict__ assign, float *__restrict__ e, int32_t *__restrict__ flags)
+{
+    if (st->finished) return;
+    extern __shared__ __align__(128) float smem[];
+    __shared__ AssignSmem sh;
+    if (threadIdx.x == 0) {
+        mbar_init(&sh.bar[0], 1);
+        mbar_init(&sh.bar[1], 1);
+        fence_mbar_init();
+        sh.abort = 0;
+    }
+    __syncthreads();
+    uint32_t u0 = 0, u1 = 0;
+    (void)assign_f32_tile(X, M, L, Lp, Cp, kn, cur_n(n_dev, n_host), mu, C, st, assign, e, flags,
+                          (int64_t)blockIdx.x * BM, smem, sh, u0, u1);
+}
+
+// Batched problems: a persistent CTA takes (problem, row tile) work items from
+// a global counter until all are done; finished problems are skipped.
+__global__ void __launch_bounds__(ASSIGN_THREADS, 2)
+    kb_assign_f32(const BatchSet *__restrict__ sets, int S, const int64_t *__restrict__ pre_tiles,
+                  int64_t total, int L, int Lp, int *counter)
+{
+    extern __shared__ __align__(128) float smem[];
+    __shared__ AssignSmem sh;
+    __shared__ int64_t s_item;
+    if (threadIdx.x == 0) {
+        mbar_init(&sh.bar[0], 1);
+        mbar_init(&sh.bar[1], 1);
+        fence_mbar_init();
+        sh.abort = 0;
+    }
+    __syncthreads();
+    uint32_t u0 = 0, u1 = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(counter, 1);
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= total) break;
+        const int s = find_set64(pre_tiles, S, item);
+        const BatchSet &q = sets[s];
+        if (!q.st->finished) {
+            const int64_t tile = item - pre_tiles[s];
+            if (!assign_f32_tile(q.X, q.M, L, Lp, q.Cp, q.kn, q.st->n_cur, q.mu, q.C, q.st, q.assign,
+                                 q.e, q.flags, tile * BM, smem, sh, u0, u1))
+                break;
+        }
+        __syncthreads();   // all reads of this item's shared data before the next item
+    }
 }
 
 // Exact FP32 direct-form re-scoring of the rows k_assign_f32 could not
@@ -394,37 +460,33 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 2)
 // t % EX_SW of each chunk against rows 4 * (t / EX_SW) .. + 3.  The
 // (distance, index) minimum is reduced in a fixed order (shuffles, then the
 // warps of a row half in order).
-__global__ void __launch_bounds__(EX_THREADS)
-    k_assign_exact(const float *__restrict__ X, int L, int Lp, const float *__restrict__ CT,
-                   const int32_t *n_dev, int n_host, DevState *st, const int32_t *__restrict__ flags,
-                   int32_t *__restrict__ assign, float *__restrict__ e)
+struct ExactSmem {
+    float xs[LMAX][EX_R];
+    uint64_t bar[2];
+    int abort;
+    float rb[EX_THREADS / 32][4];
+    int ri[EX_THREADS / 32][4];
+};
+
+// Re-scores flagged group g (EX_R rows) of one problem; uses[] count the
+// completed phases of the two chunk barriers across calls of one CTA.
+// Returns false after a time-out (reported); uniform across the CTA.
+__device__ __forceinline__ bool exact_group(const float *__restrict__ X, int L, int Lp,
+                                            const float *__restrict__ CT, int N, DevState *st,
+                                            const int32_t *__restrict__ flags, int nflag,
+                                            int32_t *__restrict__ assign, float *__restrict__ e,
+                                            int g, float *cbuf, ExactSmem &sh, uint32_t *uses)
 {
-    if (st->finished) return;
-    const int nflag = st->nflag;
-    if (nflag == 0) return;
-    extern __shared__ __align__(128) float cbuf[];   // [2][Lp][EX_SW]
-    __shared__ __align__(16) float xs[LMAX][EX_R];
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ int s_abort;
-    __shared__ float rb[EX_THREADS / 32][4];
-    __shared__ int ri[EX_THREADS / 32][4];
-    const int N = cur_n(n_dev, n_host);
+    auto &xs = sh.xs;
+    uint64_t *bar = sh.bar;
+    auto &rb = sh.rb;
+    auto &ri = sh.ri;
     const int nchunk = (N + EX_SW - 1) / EX_SW;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int j = tid % EX_SW, half = tid / EX_SW;
     const uint32_t chunk_floats = (uint32_t)Lp * EX_SW;
     const uint32_t chunk_bytes = chunk_floats * 4u;
-    const int ngroups = (nflag + EX_R - 1) / EX_R;
-    if ((int)blockIdx.x >= ngroups) return;
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-        s_abort = 0;
-    }
-    __syncthreads();
-    uint32_t uses[2] = {0u, 0u};   // completed phases of each buffer's barrier
-    for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    {
         const int nr = min(EX_R, nflag - g * EX_R);
         for (int i = tid; i < EX_R * L; i += EX_THREADS) {
             const int r = i % EX_R, l = i / EX_R;
@@ -448,7 +510,7 @@ __global__ void __launch_bounds__(EX_THREADS)
             const int b = k & 1;
             const bool ok = mbar_wait_bounded(&bar[b], uses[b] & 1u);
             uses[b] += 1u;
-            if (!ok) s_abort = 1;
+            if (!ok) sh.abort = 1;
             const float *cb = cbuf + b * chunk_floats;
             const int n = k * EX_SW + j;
             if (ok && n < N) {
@@ -474,7 +536,7 @@ __global__ void __launch_bounds__(EX_THREADS)
                     }
             }
             __syncthreads();
-            if (s_abort) {
+            if (sh.abort) {
                 k_stop = k;
                 break;
             }
@@ -490,7 +552,7 @@ __global__ void __launch_bounds__(EX_THREADS)
                     (void)mbar_wait_bounded(&bar[kk & 1], uses[kk & 1] & 1u);
                 flag_error(st, ERR_TIMEOUT);
             }
-            return;
+            return false;
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -526,6 +588,87 @@ __global__ void __launch_bounds__(EX_THREADS)
         }
         __syncthreads();
     }
+    return true;
+}
+
+__device__ __forceinline__ void exact_init(ExactSmem &sh)
+{
+    if (threadIdx.x == 0) {
+        mbar_init(&sh.bar[0], 1);
+        mbar_init(&sh.bar[1], 1);
+        fence_mbar_init();
+        sh.abort = 0;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(EX_THREADS)
+    k_assign_exact(const float *__restrict__ X, int L, int Lp, const float *__restrict__ CT,
+                   const int32_t *n_dev, int n_host, DevState *st, const int32_t *__restrict__ flags,
+                   int32_t *__restrict__ assign, float *__restrict__ e)
+{
+    if (st->finished) return;
+    const int nflag = st->nflag;
+    const int ngroups = (nflag + EX_R - 1) / EX_R;
+    if ((int)blockIdx.x >= ngroups) return;
+    extern __shared__ __align__(128) float cbuf[];   // [2][Lp][EX_SW]
+    __shared__ __align__(16) ExactSmem sh;
+    exact_init(sh);
+    uint32_t uses[2] = {0u, 0u};
+    const int N = cur_n(n_dev, n_host);
+    for (int g = blockIdx.x; g < ngroups; g += gridDim.x)
+        if (!exact_group(X, L, Lp, CT, N, st, flags, nflag, assign, e, g, cbuf, sh, uses)) return;
+}
+
+// Batched problems: the flagged groups of all problems form one work list
+// (problem order, then group order); a persistent grid strides through it.
+__global__ void __launch_bounds__(EX_THREADS)
+    kb_assign_exact(const BatchSet *__restrict__ sets, int S, int L, int Lp)
+{
+    extern __shared__ __align__(128) float cbuf[];
+    __shared__ __align__(16) ExactSmem sh;
+    __shared__ int s_total;
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int s = 0; s < S; ++s)
+            if (!sets[s].st->finished) t += (sets[s].st->nflag + EX_R - 1) / EX_R;
+        s_total = t;
+    }
+    __syncthreads();
+    const int total = s_total;
+    if ((int)blockIdx.x >= total) return;
+    exact_init(sh);
+    uint32_t uses[2] = {0u, 0u};
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        int s = 0, g = item;
+        for (; s < S; ++s) {
+            if (sets[s].st->finished) continue;
+            const int ng = (sets[s].st->nflag + EX_R - 1) / EX_R;
+            if (g < ng) break;
+            g -= ng;
+        }
+        const BatchSet &q = sets[s];
+        if (!exact_group(q.X, L, Lp, q.CT, q.st->n_cur, q.st, q.flags, q.st->nflag, q.assign, q.e, g,
+                         cbuf, sh, uses))
+            return;
+    }
+}
+
+__global__ void __launch_bounds__(256) kb_prep(const BatchSet *__restrict__ sets, int S,
+                                               const int32_t *__restrict__ pre, int L, int Lp)
+{
+    const int s = find_set(pre, S, blockIdx.x);
+    const int b = blockIdx.x - pre[s];
+    const BatchSet &q = sets[s];
+    if (q.st->finished) return;
+    body_prep(q.C, q.st->n_cur, L, Lp, q.mu, q.Cp, q.kn, q.CT, q.st, b);
+}
+
+__global__ void kb_reset(const BatchSet *__restrict__ sets, int S, int *counter)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s == 0) *counter = 0;
+    if (s < S) sets[s].st->cmax_bits = 0u;
 }
 
 __global__ void k_decode(const int32_t *__restrict__ assign, int64_t M, int L,
@@ -580,6 +723,40 @@ void launch_exact(const float *X, int L, int Lp, const float *CT, const int32_t 
     if (blocks < 1) blocks = 1;
     k_assign_exact<<<(unsigned)blocks, EX_THREADS, smem, s>>>(X, L, Lp, CT, n_dev, n_host, st, flags,
                                                              assign, e);
+}
+
+void launch_b_prep(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int L, int Lp,
+                   cudaStream_t s)
+{
+    kb_prep<<<total_blocks, 256, 0, s>>>(sets, S, pre, L, Lp);
+}
+
+void launch_b_assign(const BatchSet *sets, int S, const int64_t *pre_tiles, int64_t total_tiles,
+                     int L, int Lp, int *counter, cudaStream_t s)
+{
+    // reset the work counter and the per-problem codebook norms first (kb_reset
+    // runs before kb_prep in the pass; see lbg_train_batched)
+    const size_t smem = assign_smem_bytes(Lp);
+    cudaFuncSetAttribute(kb_assign_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int64_t grid = 152 * 2;
+    if (grid > total_tiles) grid = total_tiles;
+    if (grid < 1) return;
+    kb_assign_f32<<<(unsigned)grid, ASSIGN_THREADS, smem, s>>>(sets, S, pre_tiles, total_tiles, L, Lp,
+                                                              counter);
+}
+
+void launch_b_reset(const BatchSet *sets, int S, int *counter, cudaStream_t s)
+{
+    kb_reset<<<(S + 255) / 256, 256, 0, s>>>(sets, S, counter);
+}
+
+void launch_b_exact(const BatchSet *sets, int S, int L, int Lp, int max_ngroups, cudaStream_t s)
+{
+    const size_t smem = (size_t)2 * Lp * EX_SW * sizeof(float);
+    cudaFuncSetAttribute(kb_assign_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int grid = max_ngroups < 152 * 3 ? max_ngroups : 152 * 3;
+    if (grid < 1) grid = 1;
+    kb_assign_exact<<<grid, EX_THREADS, smem, s>>>(sets, S, L, Lp);
 }
 
 void launch_decode(const int32_t *assign, int64_t M, int L, const float *C, float *Xhat,

@@ -41,15 +41,16 @@ __device__ __forceinline__ bool skip_update(const DevState *st, int train)
 // ---------------------------------------------------------------- mean
 // Column sums of X per CTA over a contiguous row range: FP32 runs of 8 rows
 // accumulated in FP64, then a fixed-order reduction.  part[b*L + l].
-__global__ void __launch_bounds__(256) k_mean_part(const float *__restrict__ X, int64_t M, int L,
-                                                   double *__restrict__ part, DevState *st)
+__device__ __forceinline__ void body_mean_part(const float *__restrict__ X, int64_t M, int L,
+                                               double *__restrict__ part, DevState *st, int blk,
+                                               int nblk)
 {
     __shared__ double red[256];
     const int per = 256 / L;   // rows in parallel
     const int t = threadIdx.x;
     const int l = t % L, rr = t / L;
-    const int64_t R = (M + gridDim.x - 1) / gridDim.x;
-    const int64_t m0 = (int64_t)blockIdx.x * R, m1 = m0 + R < M ? m0 + R : M;
+    const int64_t R = (M + nblk - 1) / nblk;
+    const int64_t m0 = (int64_t)blk * R, m1 = m0 + R < M ? m0 + R : M;
     double acc = 0.0;
     bool bad = false;
     if (rr < per) {
@@ -73,8 +74,14 @@ __global__ void __launch_bounds__(256) k_mean_part(const float *__restrict__ X, 
     if (t < L) {
         double s = 0.0;
         for (int q = 0; q < per; ++q) s += red[q * L + t];
-        part[(size_t)blockIdx.x * L + t] = s;
+        part[(size_t)blk * L + t] = s;
     }
+}
+
+__global__ void __launch_bounds__(256) k_mean_part(const float *__restrict__ X, int64_t M, int L,
+                                                   double *__restrict__ part, DevState *st)
+{
+    body_mean_part(X, M, L, part, st, blockIdx.x, gridDim.x);
 }
 
 // mu = C0 = fl32(sum of the partials in block order / M).
@@ -93,17 +100,15 @@ __global__ void k_mean_final(const double *__restrict__ part, int G, int64_t M, 
 // ---------------------------------------------------------------- hist
 // CTA per chunk of R rows: cell counts of the chunk -> table[chunk][n]
 // (stride n_cur) and the chunk's distortion partial -> dpart[chunk].
-__global__ void __launch_bounds__(HIST_THREADS)
-    k_hist(const int32_t *__restrict__ assign, const float *__restrict__ e, int64_t M, int64_t R,
-           const int32_t *n_dev, int n_host, int do_hist, int32_t *__restrict__ table,
-           double *__restrict__ dpart, DevState *st, int train)
+__device__ __forceinline__ void body_hist(const int32_t *__restrict__ assign,
+                                          const float *__restrict__ e, int64_t M, int64_t R, int N,
+                                          int do_hist, int32_t *__restrict__ table,
+                                          double *__restrict__ dpart, DevState *st, int blk)
 {
-    if (train && st->finished) return;
     extern __shared__ int h[];
     __shared__ double red[HIST_THREADS];
-    const int N = cur_n(n_dev, n_host);
     const int tid = threadIdx.x;
-    const int64_t m0 = (int64_t)blockIdx.x * R, m1 = m0 + R < M ? m0 + R : M;
+    const int64_t m0 = (int64_t)blk * R, m1 = m0 + R < M ? m0 + R : M;
     if (do_hist)
         for (int n = tid; n < N; n += HIST_THREADS) h[n] = 0;
     __syncthreads();
@@ -135,19 +140,29 @@ __global__ void __launch_bounds__(HIST_THREADS)
         if (tid < s) red[tid] += red[tid + s];
         __syncthreads();
     }
-    if (tid == 0) dpart[blockIdx.x] = red[0];
+    if (tid == 0) dpart[blk] = red[0];
     if (do_hist)
-        for (int n = tid; n < N; n += HIST_THREADS) table[(size_t)blockIdx.x * N + n] = h[n];
+        for (int n = tid; n < N; n += HIST_THREADS) table[(size_t)blk * N + n] = h[n];
+}
+
+__global__ void __launch_bounds__(HIST_THREADS)
+    k_hist(const int32_t *__restrict__ assign, const float *__restrict__ e, int64_t M, int64_t R,
+           const int32_t *n_dev, int n_host, int do_hist, int32_t *__restrict__ table,
+           double *__restrict__ dpart, DevState *st, int train)
+{
+    if (train && st->finished) return;
+    body_hist(assign, e, M, R, cur_n(n_dev, n_host), do_hist, table, dpart, st, blockIdx.x);
 }
 
 // ---------------------------------------------------------------- control
 // D = sum of the chunk partials in chunk order.  In MODE_TRAIN also the
 // stop test of Sec. 2.2 with the readings of the library: the stage ends if
 // D == 0 or (D_prev - D)/D <= theta, or when it has run max_passes passes.
-__global__ void k_ctl(const double *__restrict__ dpart, int CH, DevState *st, int mode, double theta,
-                      int max_passes, int N_target, PassRecord *rec, int max_rec)
+__device__ __forceinline__ void body_ctl(const double *__restrict__ dpart, int CH, DevState *st,
+                                         int mode, double theta, int max_passes, int N_target,
+                                         PassRecord *rec, int max_rec)
 {
-    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    if (threadIdx.x >= 32) return;
     if (mode == MODE_TRAIN && st->finished) return;
     // lane partials over chunks lane, lane + 32, ..., then a fixed shuffle tree
     double D = 0.0;
@@ -186,19 +201,23 @@ __global__ void k_ctl(const double *__restrict__ dpart, int CH, DevState *st, in
     }
 }
 
+__global__ void k_ctl(const double *__restrict__ dpart, int CH, DevState *st, int mode, double theta,
+                      int max_passes, int N_target, PassRecord *rec, int max_rec)
+{
+    if (blockIdx.x != 0) return;
+    body_ctl(dpart, CH, st, mode, theta, max_passes, N_target, rec, max_rec);
+}
+
 // ---------------------------------------------------------------- scan
 // CTA of 1024 threads per 32 cells: lane = cell, warp w covers a range of
 // chunks.  table[c][n] becomes the exclusive prefix over c; counts[n] = total.
-__global__ void __launch_bounds__(1024) k_scan(int32_t *__restrict__ table, int CH,
-                                               const int32_t *n_dev, int n_host,
-                                               int32_t *__restrict__ counts, DevState *st, int train)
+__device__ __forceinline__ void body_scan(int32_t *__restrict__ table, int CH, int N,
+                                          int32_t *__restrict__ counts, int blk)
 {
-    if (skip_update(st, train)) return;
-    const int N = cur_n(n_dev, n_host);
-    if ((int)blockIdx.x * 32 >= N) return;
+    if (blk * 32 >= N) return;
     __shared__ int part[32][33];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int n = blockIdx.x * 32 + lane;
+    const int n = blk * 32 + lane;
     const int per = (CH + 31) / 32;
     const int c0 = w * per, c1 = c0 + per < CH ? c0 + per : CH;
     int s = 0;
@@ -225,14 +244,19 @@ __global__ void __launch_bounds__(1024) k_scan(int32_t *__restrict__ table, int 
         }
 }
 
-// One CTA: off[n] = sum_{n' < n} counts[n'], off[N] = total.
-__global__ void __launch_bounds__(1024) k_offsets(const int32_t *__restrict__ counts,
-                                                  const int32_t *n_dev, int n_host,
-                                                  int32_t *__restrict__ off, DevState *st, int train)
+__global__ void __launch_bounds__(1024) k_scan(int32_t *__restrict__ table, int CH,
+                                               const int32_t *n_dev, int n_host,
+                                               int32_t *__restrict__ counts, DevState *st, int train)
 {
     if (skip_update(st, train)) return;
+    body_scan(table, CH, cur_n(n_dev, n_host), counts, blockIdx.x);
+}
+
+// One CTA: off[n] = sum_{n' < n} counts[n'], off[N] = total.
+__device__ __forceinline__ void body_offsets(const int32_t *__restrict__ counts, int N,
+                                             int32_t *__restrict__ off)
+{
     __shared__ int wsum[32];
-    const int N = cur_n(n_dev, n_host);
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int per = (N + 1023) / 1024;
     const int a = t * per, b = a + per < N ? a + per : N;
@@ -262,6 +286,14 @@ __global__ void __launch_bounds__(1024) k_offsets(const int32_t *__restrict__ co
     if (t == 1023) off[N] = run;
 }
 
+__global__ void __launch_bounds__(1024) k_offsets(const int32_t *__restrict__ counts,
+                                                  const int32_t *n_dev, int n_host,
+                                                  int32_t *__restrict__ off, DevState *st, int train)
+{
+    if (skip_update(st, train)) return;
+    body_offsets(counts, cur_n(n_dev, n_host), off);
+}
+
 // ---------------------------------------------------------------- scatter
 // CTA per chunk (same chunks as k_hist).  Rows are taken in rounds of 256 in
 // index order; inside a round a row's slot is
@@ -269,20 +301,17 @@ __global__ void __launch_bounds__(1024) k_offsets(const int32_t *__restrict__ co
 //   equal cells in its warp, __match_any_sync),
 // which is the stable counting-sort position.  run[] starts at the cell
 // offset plus the chunk's exclusive prefix.  Integer atomics only.
-__global__ void __launch_bounds__(256) k_scatter(const int32_t *__restrict__ assign, int64_t M,
-                                                 int64_t R, const int32_t *__restrict__ table,
-                                                 const int32_t *__restrict__ off,
-                                                 const int32_t *n_dev, int n_host,
-                                                 int32_t *__restrict__ perm, DevState *st, int train)
+__device__ __forceinline__ void body_scatter(const int32_t *__restrict__ assign, int64_t M,
+                                             int64_t R, const int32_t *__restrict__ table,
+                                             const int32_t *__restrict__ off, int N,
+                                             int32_t *__restrict__ perm, int blk)
 {
-    if (skip_update(st, train)) return;
     extern __shared__ int sm[];
-    const int N = cur_n(n_dev, n_host);
     int *run = sm;                                                   // [N]
     unsigned char *wcnt = reinterpret_cast<unsigned char *>(sm + N);  // [8][N]
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    const int64_t m0 = (int64_t)blockIdx.x * R, m1 = m0 + R < M ? m0 + R : M;
-    for (int n = tid; n < N; n += 256) run[n] = off[n] + table[(size_t)blockIdx.x * N + n];
+    const int64_t m0 = (int64_t)blk * R, m1 = m0 + R < M ? m0 + R : M;
+    for (int n = tid; n < N; n += 256) run[n] = off[n] + table[(size_t)blk * N + n];
     for (int i = tid; i < 2 * N; i += 256) reinterpret_cast<int *>(wcnt)[i] = 0;
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
@@ -309,6 +338,16 @@ __global__ void __launch_bounds__(256) k_scatter(const int32_t *__restrict__ ass
         }
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(256) k_scatter(const int32_t *__restrict__ assign, int64_t M,
+                                                 int64_t R, const int32_t *__restrict__ table,
+                                                 const int32_t *__restrict__ off,
+                                                 const int32_t *n_dev, int n_host,
+                                                 int32_t *__restrict__ perm, DevState *st, int train)
+{
+    if (skip_update(st, train)) return;
+    body_scatter(assign, M, R, table, off, cur_n(n_dev, n_host), perm, blockIdx.x);
 }
 
 // ---------------------------------------------------------------- cellsum
@@ -338,16 +377,14 @@ __device__ __forceinline__ void add4(float4 &a, const float4 &b)
 // row with float4 loads (L = 4G), 32/G rows per step, four steps in flight.
 // Piece (cell n, warp q) -> pieces[(n + q) * L ...] (unique slot per piece).
 template <int G>
-__global__ void __launch_bounds__(256)
-    k_cellsum_v4(const float *__restrict__ X, int64_t M, const int32_t *__restrict__ perm,
-                 const int32_t *__restrict__ off, const int32_t *n_dev, int n_host, int64_t S,
-                 float *__restrict__ pieces, DevState *st, int train)
+__device__ __forceinline__ void body_cellsum_v4(const float *__restrict__ X, int64_t M,
+                                                const int32_t *__restrict__ perm,
+                                                const int32_t *__restrict__ off, int N, int64_t S,
+                                                float *__restrict__ pieces, int blk)
 {
-    if (skip_update(st, train)) return;
     constexpr int RPG = 32 / G;
     constexpr int L = 4 * G;
-    const int N = cur_n(n_dev, n_host);
-    const int64_t q = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int64_t q = (int64_t)blk * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const int64_t p0 = q * S;
     if (p0 >= M) return;
@@ -384,15 +421,23 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// Any L: lanes own dims l = lane, lane + 32, ...; rows in order.
+template <int G>
 __global__ void __launch_bounds__(256)
-    k_cellsum_any(const float *__restrict__ X, int64_t M, int L, const int32_t *__restrict__ perm,
-                  const int32_t *__restrict__ off, const int32_t *n_dev, int n_host, int64_t S,
-                  float *__restrict__ pieces, DevState *st, int train)
+    k_cellsum_v4(const float *__restrict__ X, int64_t M, const int32_t *__restrict__ perm,
+                 const int32_t *__restrict__ off, const int32_t *n_dev, int n_host, int64_t S,
+                 float *__restrict__ pieces, DevState *st, int train)
 {
     if (skip_update(st, train)) return;
-    const int N = cur_n(n_dev, n_host);
-    const int64_t q = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    body_cellsum_v4<G>(X, M, perm, off, cur_n(n_dev, n_host), S, pieces, blockIdx.x);
+}
+
+// Any L: lanes own dims l = lane, lane + 32, ...; rows in order.
+__device__ __forceinline__ void body_cellsum_any(const float *__restrict__ X, int64_t M, int L,
+                                                 const int32_t *__restrict__ perm,
+                                                 const int32_t *__restrict__ off, int N, int64_t S,
+                                                 float *__restrict__ pieces, int blk)
+{
+    const int64_t q = (int64_t)blk * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const int64_t p0 = q * S;
     if (p0 >= M) return;
@@ -420,15 +465,22 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// c_n = (sum of its pieces, in piece order, in FP64) / count_n; an empty
-// cell copies C_in (may alias C_out).
-__global__ void k_combine(const float *__restrict__ pieces, const int32_t *__restrict__ off,
-                          const int32_t *n_dev, int n_host, int L, int64_t S, const float *C_in,
-                          float *C_out, DevState *st, int train)
+__global__ void __launch_bounds__(256)
+    k_cellsum_any(const float *__restrict__ X, int64_t M, int L, const int32_t *__restrict__ perm,
+                  const int32_t *__restrict__ off, const int32_t *n_dev, int n_host, int64_t S,
+                  float *__restrict__ pieces, DevState *st, int train)
 {
     if (skip_update(st, train)) return;
-    const int N = cur_n(n_dev, n_host);
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    body_cellsum_any(X, M, L, perm, off, cur_n(n_dev, n_host), S, pieces, blockIdx.x);
+}
+
+// c_n = (sum of its pieces, in piece order, in FP64) / count_n; an empty
+// cell copies C_in (may alias C_out).
+__device__ __forceinline__ void body_combine(const float *__restrict__ pieces,
+                                             const int32_t *__restrict__ off, int N, int L, int64_t S,
+                                             const float *C_in, float *C_out, int blk)
+{
+    const int64_t i = (int64_t)blk * blockDim.x + threadIdx.x;
     if (i >= (int64_t)N * L) return;
     const int n = (int)(i / L), l = (int)(i - (int64_t)n * L);
     const int64_t a = off[n], b = off[n + 1];
@@ -442,6 +494,14 @@ __global__ void k_combine(const float *__restrict__ pieces, const int32_t *__res
     // FP32 division of the rounded sum (two roundings, ~1.2e-7 relative; FP64
     // division is slow on this part)
     C_out[i] = (float)s / (float)(b - a);
+}
+
+__global__ void k_combine(const float *__restrict__ pieces, const int32_t *__restrict__ off,
+                          const int32_t *n_dev, int n_host, int L, int64_t S, const float *C_in,
+                          float *C_out, DevState *st, int train)
+{
+    if (skip_update(st, train)) return;
+    body_combine(pieces, off, cur_n(n_dev, n_host), L, S, C_in, C_out, blockIdx.x);
 }
 
 // ---------------------------------------------------------------- backward
@@ -498,17 +558,23 @@ __global__ void k_combine_grad(const float *__restrict__ pieces, const int32_t *
 // ---------------------------------------------------------------- split
 // [c + delta], [c - delta] per centroid (or c (1 + delta), c (1 - delta) when
 // mult), interleaved, rounded once from FP64.
-__global__ void k_split(const float *__restrict__ C_cur, float *__restrict__ C_alt, int L,
-                        double delta, int mult, DevState *st)
+__device__ __forceinline__ void body_split(const float *__restrict__ C_cur, float *__restrict__ C_alt,
+                                           int L, double delta, int mult, DevState *st, int blk)
 {
     if (st->finished || st->action != ACT_SPLIT) return;
     const int n = st->n_cur;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = (int64_t)blk * blockDim.x + threadIdx.x;
     if (i >= (int64_t)n * L) return;
     const int64_t c = i / L, l = i - c * L;
     const double v = (double)C_cur[i];
     C_alt[(2 * c) * L + l] = (float)(mult ? v * (1.0 + delta) : v + delta);
     C_alt[(2 * c + 1) * L + l] = (float)(mult ? v * (1.0 - delta) : v - delta);
+}
+
+__global__ void k_split(const float *__restrict__ C_cur, float *__restrict__ C_alt, int L,
+                        double delta, int mult, DevState *st)
+{
+    body_split(C_cur, C_alt, L, delta, mult, st, blockIdx.x);
 }
 
 // Empty-cell re-seeding (opt-in variant) after an update: every empty cell e,
@@ -574,17 +640,24 @@ __global__ void __launch_bounds__(1024) k_reseed(const int32_t *__restrict__ off
     }
 }
 
+__device__ __forceinline__ void body_copy_split(const float *__restrict__ C_alt,
+                                                float *__restrict__ C_cur, int L, DevState *st,
+                                                int blk)
+{
+    if (st->finished || st->action != ACT_SPLIT) return;
+    const int64_t i = (int64_t)blk * blockDim.x + threadIdx.x;
+    if (i < 2 * (int64_t)st->n_cur * L) C_cur[i] = C_alt[i];
+}
+
 __global__ void k_copy_split(const float *__restrict__ C_alt, float *__restrict__ C_cur, int L,
                              DevState *st)
 {
-    if (st->finished || st->action != ACT_SPLIT) return;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < 2 * (int64_t)st->n_cur * L) C_cur[i] = C_alt[i];
+    body_copy_split(C_alt, C_cur, L, st, blockIdx.x);
 }
 
 // End of a training pass: a split doubles the stage size and resets the
 // stage (D_prev = +inf, reading of the library); a finish ends training.
-__global__ void k_stage(DevState *st)
+__device__ __forceinline__ void body_stage(DevState *st)
 {
     if (threadIdx.x != 0 || st->finished) return;
     if (st->action == ACT_SPLIT) {
@@ -595,6 +668,137 @@ __global__ void k_stage(DevState *st)
         st->finished = 1;
     }
 }
+
+__global__ void k_stage(DevState *st) { body_stage(st); }
+
+// ---------------------------------------------------------------- batched
+// One launch per step for every problem of a batched call: block b serves
+// problem s = find_set(pre, S, b), local block b - pre[s]; problems that
+// have finished training (or whose step is skipped) return at once.
+__device__ __forceinline__ int set_of(const int32_t *pre, int S, int &local)
+{
+    const int s = find_set(pre, S, blockIdx.x);
+    local = blockIdx.x - pre[s];
+    return s;
+}
+
+__global__ void __launch_bounds__(256) kb_mean(const BatchSet *__restrict__ sets, int S,
+                                               const int32_t *__restrict__ pre, int L)
+{
+    int b;
+    const int s = set_of(pre, S, b);
+    const BatchSet &q = sets[s];
+    body_mean_part(q.X, q.M, L, q.mpart, q.st, b, q.G);
+}
+
+__global__ void kb_mean_final(const BatchSet *__restrict__ sets, int L)
+{
+    const BatchSet &q = sets[blockIdx.x];
+    const int l = threadIdx.x;
+    if (l >= L) return;
+    double acc = 0.0;
+    for (int b = 0; b < q.G; ++b) acc += q.mpart[(size_t)b * L + l];
+    const float c = (float)(acc / (double)q.M);
+    q.mu[l] = c;
+    q.C[l] = c;
+}
+
+__global__ void __launch_bounds__(HIST_THREADS) kb_hist(const BatchSet *__restrict__ sets, int S,
+                                                        const int32_t *__restrict__ pre)
+{
+    int b;
+    const int s = set_of(pre, S, b);
+    const BatchSet &q = sets[s];
+    if (q.st->finished) return;
+    body_hist(q.assign, q.e, q.M, q.R, q.st->n_cur, 1, q.table, q.dpart, q.st, b);
+}
+
+__global__ void kb_ctl(const BatchSet *__restrict__ sets, double theta, int max_passes)
+{
+    const BatchSet &q = sets[blockIdx.x];
+    if (q.st->finished) return;
+    body_ctl(q.dpart, q.CH, q.st, MODE_TRAIN, theta, max_passes, q.N, nullptr, 0);
+}
+
+__global__ void __launch_bounds__(1024) kb_scan(const BatchSet *__restrict__ sets, int S,
+                                                const int32_t *__restrict__ pre)
+{
+    int b;
+    const int s = set_of(pre, S, b);
+    const BatchSet &q = sets[s];
+    if (skip_update(q.st, 1)) return;
+    body_scan(q.table, q.CH, q.st->n_cur, q.counts, b);
+}
+
+__global__ void __launch_bounds__(1024) kb_offsets(const BatchSet *__restrict__ sets)
+{
+    const BatchSet &q = sets[blockIdx.x];
+    if (skip_update(q.st, 1)) return;
+    body_offsets(q.counts, q.st->n_cur, q.off);
+}
+
+__global__ void __launch_bounds__(256) kb_scatter(const BatchSet *__restrict__ sets, int S,
+                                                  const int32_t *__restrict__ pre)
+{
+    int b;
+    const int s = set_of(pre, S, b);
+    const BatchSet &q = sets[s];
+    if (skip_update(q.st, 1)) return;
+    body_scatter(q.assign, q.M, q.R, q.table, q.off, q.st->n_cur, q.perm, b);
+}
+
+template <int G>
+__global__ void __launch_bounds__(256) kb_cellsum_v4(const BatchSet *__restrict__ sets, int S,
+                                                     const int32_t *__restrict__ pre)
+{
+    int b;
+    const int s = set_of(pre, S, b);
+    const BatchSet &q = sets[s];
+    if (skip_update(q.st, 1)) return;
+    body_cellsum_v4<G>(q.X, q.M, q.perm, q.off, q.st->n_cur, q.S, q.pieces, b);
+}
+
+__global__ void __launch_bounds__(256) kb_cellsum_any(const BatchSet *__restrict__ sets, int S,
+                                                      const int32_t *__restrict__ pre, int L)
+{
+    int b;
+    const int s = set_of(pre, S, b);
+    const BatchSet &q = sets[s];
+    if (skip_update(q.st, 1)) return;
+    body_cellsum_any(q.X, q.M, L, q.perm, q.off, q.st->n_cur, q.S, q.pieces, b);
+}
+
+__global__ void kb_combine(const BatchSet *__restrict__ sets, int S, const int32_t *__restrict__ pre,
+                           int L)
+{
+    int b;
+    const int s = set_of(pre, S, b);
+    const BatchSet &q = sets[s];
+    if (skip_update(q.st, 1)) return;
+    const int N = q.st->n_cur;
+    if ((int64_t)b * blockDim.x >= (int64_t)N * L) return;
+    body_combine(q.pieces, q.off, N, L, q.S, q.C, q.C, b);
+}
+
+__global__ void kb_split(const BatchSet *__restrict__ sets, int S, const int32_t *__restrict__ pre,
+                         int L, double delta, int mult)
+{
+    int b;
+    const int s = set_of(pre, S, b);
+    const BatchSet &q = sets[s];
+    body_split(q.C, q.Calt, L, delta, mult, q.st, b);
+}
+
+__global__ void kb_copy_split(const BatchSet *__restrict__ sets, int S,
+                              const int32_t *__restrict__ pre, int L)
+{
+    int b;
+    const int s = set_of(pre, S, b);
+    const BatchSet &q = sets[s];
+    body_copy_split(q.Calt, q.C, L, q.st, b);
+}
+
+__global__ void kb_stage(const BatchSet *__restrict__ sets) { body_stage(sets[blockIdx.x].st); }
 
 }  // namespace
 
@@ -672,6 +876,77 @@ void launch_combine(const float *pieces, const int32_t *off, const int32_t *n_de
     const int64_t total = (int64_t)n_host * L;
     k_combine<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(pieces, off, n_dev, n_host, L, S, C_in,
                                                              C_out, st, train ? 1 : 0);
+}
+
+void launch_b_mean(const BatchSet *sets, int S, const int32_t *pre_mean, int total_blocks, int L,
+                   cudaStream_t s)
+{
+    kb_mean<<<total_blocks, 256, 0, s>>>(sets, S, pre_mean, L);
+    kb_mean_final<<<S, 128, 0, s>>>(sets, L);
+}
+
+void launch_b_hist(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int NMAXB,
+                   cudaStream_t s)
+{
+    const size_t smem = (size_t)NMAXB * sizeof(int);
+    cudaFuncSetAttribute(kb_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kb_hist<<<total_blocks, HIST_THREADS, smem, s>>>(sets, S, pre);
+}
+
+void launch_b_ctl(const BatchSet *sets, int S, double theta, int max_passes, cudaStream_t s)
+{
+    kb_ctl<<<S, 32, 0, s>>>(sets, theta, max_passes);
+}
+
+void launch_b_scan(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, cudaStream_t s)
+{
+    kb_scan<<<total_blocks, 1024, 0, s>>>(sets, S, pre);
+}
+
+void launch_b_offsets(const BatchSet *sets, int S, cudaStream_t s)
+{
+    kb_offsets<<<S, 1024, 0, s>>>(sets);
+}
+
+void launch_b_scatter(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int NMAXB,
+                      cudaStream_t s)
+{
+    const size_t smem = (size_t)NMAXB * (sizeof(int) + 8);
+    cudaFuncSetAttribute(kb_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kb_scatter<<<total_blocks, 256, smem, s>>>(sets, S, pre);
+}
+
+void launch_b_cellsum(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int L,
+                      bool vec, cudaStream_t s)
+{
+    switch (vec ? L : 0) {
+    case 4: kb_cellsum_v4<1><<<total_blocks, 256, 0, s>>>(sets, S, pre); break;
+    case 8: kb_cellsum_v4<2><<<total_blocks, 256, 0, s>>>(sets, S, pre); break;
+    case 16: kb_cellsum_v4<4><<<total_blocks, 256, 0, s>>>(sets, S, pre); break;
+    case 32: kb_cellsum_v4<8><<<total_blocks, 256, 0, s>>>(sets, S, pre); break;
+    case 64: kb_cellsum_v4<16><<<total_blocks, 256, 0, s>>>(sets, S, pre); break;
+    case 128: kb_cellsum_v4<32><<<total_blocks, 256, 0, s>>>(sets, S, pre); break;
+    default: kb_cellsum_any<<<total_blocks, 256, 0, s>>>(sets, S, pre, L);
+    }
+}
+
+void launch_b_combine(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int L,
+                      cudaStream_t s)
+{
+    kb_combine<<<total_blocks, 256, 0, s>>>(sets, S, pre, L);
+}
+
+void launch_b_split(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int L,
+                    double delta, bool mult, cudaStream_t s)
+{
+    kb_split<<<total_blocks, 256, 0, s>>>(sets, S, pre, L, delta, mult ? 1 : 0);
+}
+
+void launch_b_advance(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int L,
+                      cudaStream_t s)
+{
+    kb_copy_split<<<total_blocks, 256, 0, s>>>(sets, S, pre, L);
+    kb_stage<<<S, 32, 0, s>>>(sets);
 }
 
 void launch_grad_x(const float *X, int64_t M, int L, const float *C, int N, const int32_t *assign,

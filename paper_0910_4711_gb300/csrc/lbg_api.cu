@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 
 using namespace lbg;
 
@@ -265,6 +266,60 @@ int precision_mode(const lbg_opts &o, int L)
     if (o.precision == LBG_PREC_BF16) return tc_supported(L) ? 1 : LBG_ERR_UNSUPPORTED;
     return LBG_ERR_ARG;
 }
+
+// One training pass recorded into a CUDA graph and replayed: many small
+// kernels per pass are then issued with one launch.  Capture uses a private
+// stream (the caller's may be the legacy default stream, which cannot be
+// captured); if capture is not possible the pass is launched directly.
+struct GraphPass {
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev = nullptr;
+    template <class F>
+    void build(cudaStream_t user, F &&issue)
+    {
+        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return;
+        }
+        // warm the kernels' attributes outside capture, in stream order
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return;
+        }
+        issue(cap);
+        if (cudaStreamEndCapture(cap, &graph) != cudaSuccess || !graph ||
+            cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+            (void)cudaGetLastError();
+            if (graph) cudaGraphDestroy(graph);
+            graph = nullptr;
+            exec = nullptr;
+        }
+        (void)user;
+    }
+    template <class F>
+    void run(cudaStream_t user, F &&issue)
+    {
+        if (!exec) {
+            issue(user);
+            return;
+        }
+        cudaEventRecord(ev, user);
+        cudaStreamWaitEvent(cap, ev, 0);
+        cudaGraphLaunch(exec, cap);
+        cudaEventRecord(ev, cap);
+        cudaStreamWaitEvent(user, ev, 0);
+    }
+    ~GraphPass()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (ev) cudaEventDestroy(ev);
+        if (cap) cudaStreamDestroy(cap);
+    }
+};
 
 lbg_status check_dims(int64_t M, int32_t L, int32_t N)
 {
@@ -542,6 +597,215 @@ lbg_status lbg_distortion_backward(const float *X, int64_t M, int32_t L, const f
     tm.report(o.phase_ms, true);
     if (D) *D = M > 0 ? h.D : 0.0;
     return finish_status(h);
+}
+
+lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, int32_t L,
+                             const int32_t *N, double delta, double theta, float *C,
+                             int32_t *assign, double *D, const lbg_opts *opts)
+{
+    if (S < 1 || !X || !row_off || !N || !C) return LBG_ERR_ARG;
+    if (L < 1 || L > LBG_MAX_DIM) return LBG_ERR_ARG;
+    if (!(delta >= 0.0) || !(theta >= 0.0) || !isfinite(delta) || !isfinite(theta))
+        return LBG_ERR_ARG;
+    if (row_off[0] != 0) return LBG_ERR_ARG;
+    int64_t Mtot = 0, Ntot = 0;
+    int NMAXB = 1;
+    for (int s = 0; s < S; ++s) {
+        const int64_t Ms = row_off[s + 1] - row_off[s];
+        if (Ms < 1 || Ms > INT32_MAX) return LBG_ERR_ARG;
+        if (N[s] < 1 || N[s] > LBG_MAX_CODEBOOK) return LBG_ERR_ARG;
+        if (!is_pow2(N[s])) return LBG_ERR_NOT_POW2;
+        Mtot += Ms;
+        Ntot += N[s];
+        NMAXB = N[s] > NMAXB ? N[s] : NMAXB;
+    }
+    const lbg_opts o = resolve(opts);
+    if (o.precision != LBG_PREC_FP32) return LBG_ERR_UNSUPPORTED;
+    lbg_status rc;
+    std::lock_guard<std::mutex> lock(g_mu);
+    Call c;
+    if ((rc = begin(c, o)) != LBG_OK) return rc;
+    const int wX = where(X, c.dev), wC = where(C, c.dev), wA = assign ? where(assign, c.dev) : 0;
+    if (wX < 0 || wC < 0 || wA < 0) return LBG_ERR_ARG;
+    const int Lp = round_up(L, 4);
+
+    // ---- workspace: one plan per problem, laid out one after another
+    struct Sub {
+        Plan p;
+        size_t base;
+    };
+    std::vector<Sub> sub(S);
+    size_t total = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = total;
+        total += (bytes + 255) / 256 * 256;
+        return at;
+    };
+    const size_t o_sets = take(sizeof(BatchSet) * S);
+    const size_t o_pre = take(sizeof(int32_t) * (size_t)(S + 1) * 8);
+    const size_t o_tiles = take(sizeof(int64_t) * (size_t)(S + 1));
+    const size_t o_counter = take(sizeof(int) * 4);
+    const size_t o_X = wX == 0 ? take(sizeof(float) * (size_t)Mtot * L) : 0;
+    const size_t o_C = wC == 0 ? take(sizeof(float) * (size_t)Ntot * L) : 0;
+    const size_t o_A = take(sizeof(int32_t) * (size_t)Mtot);
+    for (int s = 0; s < S; ++s) {
+        const int64_t Ms = row_off[s + 1] - row_off[s];
+        sub[s].p = make_plan(Ms, L, N[s], 0, false, true, false, false, false);
+        sub[s].base = take(sub[s].p.total);
+    }
+    if ((rc = ensure_workspace(c, total)) != LBG_OK) return rc;
+    char *ws = c.ws;
+    const float *dX = X;
+    if (wX == 0) {
+        CK(cudaMemcpyAsync(ws + o_X, X, sizeof(float) * Mtot * L, cudaMemcpyHostToDevice, c.s));
+        dX = reinterpret_cast<const float *>(ws + o_X);
+    }
+    float *dC = wC ? C : reinterpret_cast<float *>(ws + o_C);
+    int32_t *dA = (assign && wA == 1) ? assign : reinterpret_cast<int32_t *>(ws + o_A);
+
+    // ---- descriptors, states, block maps
+    std::vector<BatchSet> hs(S);
+    std::vector<int32_t> pre(8 * (S + 1), 0);
+    std::vector<int64_t> tiles(S + 1, 0);
+    int32_t *P[8];
+    for (int k = 0; k < 8; ++k) P[k] = pre.data() + k * (S + 1);
+    std::vector<DevState> st0(S);
+    int64_t coff = 0;
+    for (int s = 0; s < S; ++s) {
+        const Plan &p = sub[s].p;
+        char *b = ws + sub[s].base;
+        BatchSet &q = hs[s];
+        q.X = dX + row_off[s] * L;
+        q.M = p.M;
+        q.N = p.N;
+        q.NP = p.NP;
+        q.CH = p.CH;
+        q.G = p.G;
+        q.R = p.R;
+        q.S = p.S;
+        q.C = dC + coff * L;
+        q.Calt = reinterpret_cast<float *>(b + p.Calt);
+        q.Cp = reinterpret_cast<float *>(b + p.Cp);
+        q.kn = reinterpret_cast<float *>(b + p.kn);
+        q.CT = reinterpret_cast<float *>(b + p.CT);
+        q.mu = reinterpret_cast<float *>(b + p.mu);
+        q.st = reinterpret_cast<DevState *>(b + p.state);
+        q.assign = dA + row_off[s];
+        q.flags = reinterpret_cast<int32_t *>(b + p.flags);
+        q.table = reinterpret_cast<int32_t *>(b + p.table);
+        q.counts = reinterpret_cast<int32_t *>(b + p.counts);
+        q.off = reinterpret_cast<int32_t *>(b + p.off);
+        q.perm = reinterpret_cast<int32_t *>(b + p.perm);
+        q.e = reinterpret_cast<float *>(b + p.e);
+        q.pieces = reinterpret_cast<float *>(b + p.pieces);
+        q.dpart = reinterpret_cast<double *>(b + p.dpart);
+        q.mpart = reinterpret_cast<double *>(b + p.mpart);
+        coff += N[s];
+        init_state(st0[s], 1);
+        // blocks per problem of each batched launch
+        const int64_t nq = p.nq;
+        const int cnt[8] = {p.CH,
+                            (N[s] + 31) / 32,
+                            p.NP / 32,
+                            (int)((nq + 7) / 8),
+                            (int)(((int64_t)N[s] * L + 255) / 256),
+                            (int)(((int64_t)(N[s] / 2 > 0 ? N[s] / 2 : 1) * L + 255) / 256),
+                            (int)(((int64_t)N[s] * L + 255) / 256),
+                            p.G};
+        for (int k = 0; k < 8; ++k) P[k][s + 1] = P[k][s] + cnt[k];
+        tiles[s + 1] = tiles[s] + (p.M + BM - 1) / BM;
+    }
+    for (int s = 0; s < S; ++s)
+        CK(cudaMemcpyAsync(hs[s].st, &st0[s], sizeof(DevState), cudaMemcpyHostToDevice, c.s));
+    BatchSet *dsets = reinterpret_cast<BatchSet *>(ws + o_sets);
+    int32_t *dpre = reinterpret_cast<int32_t *>(ws + o_pre);
+    int64_t *dtiles = reinterpret_cast<int64_t *>(ws + o_tiles);
+    int *counter = reinterpret_cast<int *>(ws + o_counter);
+    CK(cudaMemcpyAsync(dsets, hs.data(), sizeof(BatchSet) * S, cudaMemcpyHostToDevice, c.s));
+    CK(cudaMemcpyAsync(dpre, pre.data(), sizeof(int32_t) * pre.size(), cudaMemcpyHostToDevice, c.s));
+    CK(cudaMemcpyAsync(dtiles, tiles.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, c.s));
+    const int32_t *dP[8];
+    for (int k = 0; k < 8; ++k) dP[k] = dpre + k * (S + 1);
+    int max_groups = 0;
+    for (int s = 0; s < S; ++s) max_groups += (int)((sub[s].p.M + 7) / 8);
+    const bool vec = (reinterpret_cast<uintptr_t>(dX) & 15u) == 0;
+    Timer tm;
+    if ((rc = tm.init(o.phase_ms != nullptr)) != LBG_OK) return rc;
+    tm.mark(0, c.s);
+    launch_b_mean(dsets, S, dP[7], P[7][S], L, c.s);
+
+    // ---- one batched pass, recorded once into a graph and replayed
+    auto pass = [&](cudaStream_t st) {
+        launch_b_reset(dsets, S, counter, st);
+        launch_b_prep(dsets, S, dP[2], P[2][S], L, Lp, st);
+        launch_b_assign(dsets, S, dtiles, tiles[S], L, Lp, counter, st);
+        launch_b_exact(dsets, S, L, Lp, max_groups, st);
+        launch_b_hist(dsets, S, dP[0], P[0][S], NMAXB, st);
+        launch_b_ctl(dsets, S, theta, o.max_passes, st);
+        launch_b_scan(dsets, S, dP[1], P[1][S], st);
+        launch_b_offsets(dsets, S, st);
+        launch_b_scatter(dsets, S, dP[0], P[0][S], NMAXB, st);
+        launch_b_cellsum(dsets, S, dP[3], P[3][S], L, vec, st);
+        launch_b_combine(dsets, S, dP[4], P[4][S], L, st);
+        launch_b_split(dsets, S, dP[5], P[5][S], L, delta, o.split_multiplicative != 0, st);
+        launch_b_advance(dsets, S, dP[6], P[6][S], L, st);
+    };
+    int stages = 1;
+    for (int s = 0; s < S; ++s) {
+        int k = 1;
+        for (int n = 1; n < N[s]; n *= 2) ++k;
+        stages = k > stages ? k : stages;
+    }
+    const int64_t max_total = (int64_t)stages * o.max_passes;
+    GraphPass gp;
+    gp.build(c.s, pass);   // falls back to direct launches if capture is not possible
+    std::vector<DevState> hst(S);
+    lbg_status out = LBG_OK;
+    int64_t issued = 0;
+    int batch = 2;
+    for (;;) {
+        for (int b = 0; b < batch && issued < max_total; ++b, ++issued) gp.run(c.s, pass);
+        if (cudaGetLastError() != cudaSuccess) {
+            out = LBG_ERR_CUDA;
+            break;
+        }
+        bool all = true;
+        uint32_t err = 0;
+        for (int s = 0; s < S; ++s)
+            if (cudaMemcpyAsync(&hst[s], hs[s].st, sizeof(DevState), cudaMemcpyDeviceToHost, c.s) !=
+                cudaSuccess)
+                out = LBG_ERR_CUDA;
+        if (cudaStreamSynchronize(c.s) != cudaSuccess) out = LBG_ERR_CUDA;
+        if (out != LBG_OK) {
+            (void)cudaGetLastError();
+            break;
+        }
+        for (int s = 0; s < S; ++s) {
+            all = all && hst[s].finished;
+            err |= hst[s].err;
+        }
+        if (all || err || issued >= max_total) break;
+        if (batch < 32) batch *= 2;
+    }
+    tm.mark(4, c.s);
+    if (out != LBG_OK) return out;
+    if (wC == 0) CK(cudaMemcpyAsync(C, dC, sizeof(float) * Ntot * L, cudaMemcpyDeviceToHost, c.s));
+    if (assign && wA == 0)
+        CK(cudaMemcpyAsync(assign, dA, sizeof(int32_t) * Mtot, cudaMemcpyDeviceToHost, c.s));
+    CK(cudaStreamSynchronize(c.s));
+    tm.report(o.phase_ms, false);
+    DevState agg;
+    init_state(agg, 0);
+    int maxp = 0;
+    for (int s = 0; s < S; ++s) {
+        if (D) D[s] = hst[s].D;
+        agg.err |= hst[s].err;
+        agg.warn |= hst[s].warn;
+        maxp = hst[s].total > maxp ? hst[s].total : maxp;
+        if (!hst[s].finished && !hst[s].err) return LBG_ERR_CUDA;
+    }
+    if (o.n_records) *o.n_records = maxp;
+    return finish_status(agg);
 }
 
 lbg_status lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double delta, double theta,

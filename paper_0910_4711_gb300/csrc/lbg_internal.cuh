@@ -58,6 +58,59 @@ struct PassRecord {
     double D;
 };
 
+// One problem of a batched call (device-resident descriptor; every pointer
+// is that problem's own region of the batched workspace).
+struct BatchSet {
+    const float *X;        // [M x L] rows of this problem
+    int64_t M;
+    int N;                 // final codebook size (allocated cells)
+    int NP;                // N rounded up to BN
+    int CH;                // histogram / scatter chunks
+    int G;                 // blocks of the initial mean
+    int64_t R;             // rows per chunk
+    int64_t S;             // rows per segmented-sum piece
+    float *C, *Calt;       // [N x L] current codebook, split scratch
+    float *Cp, *kn, *CT;   // prepared codebook
+    float *mu;             // [Lp] centring vector
+    DevState *st;
+    int32_t *assign, *flags, *table, *counts, *off, *perm;
+    float *e, *pieces;
+    double *dpart, *mpart;
+};
+
+// Prefix arrays (device, S + 1 entries each) mapping the blocks of a batched
+// launch to problems: block b belongs to problem s with pre[s] <= b < pre[s+1].
+struct BatchMaps {
+    const int32_t *hist, *scan, *prep, *cellsum, *combine, *split, *copy, *mean, *exact_unused;
+    const int64_t *tiles;  // assign work items: row tiles of BM rows
+};
+
+__host__ __device__ inline int find_set(const int32_t *pre, int S, int64_t b)
+{
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((int64_t)pre[mid] <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__host__ __device__ inline int find_set64(const int64_t *pre, int S, int64_t b)
+{
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
 __host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 __host__ __device__ inline int64_t round_up64(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
@@ -205,6 +258,31 @@ void launch_split(const float *C_cur, float *C_alt, int N_alloc, int L, double d
                   DevState *st, cudaStream_t s);
 void launch_reseed(const int32_t *off, const int32_t *n_dev, int n_host, int L, double delta,
                    float *C, DevState *st, bool train, cudaStream_t s);
+// Batched problems (k_update.cu / k_assign.cu): one launch per step for all problems.
+void launch_b_mean(const BatchSet *sets, int S, const int32_t *pre_mean, int total_blocks, int L,
+                   cudaStream_t s);
+void launch_b_hist(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int NMAXB,
+                   cudaStream_t s);
+void launch_b_ctl(const BatchSet *sets, int S, double theta, int max_passes, cudaStream_t s);
+void launch_b_scan(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, cudaStream_t s);
+void launch_b_offsets(const BatchSet *sets, int S, cudaStream_t s);
+void launch_b_scatter(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int NMAXB,
+                      cudaStream_t s);
+void launch_b_cellsum(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int L,
+                      bool vec, cudaStream_t s);
+void launch_b_combine(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int L,
+                      cudaStream_t s);
+void launch_b_split(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int L,
+                    double delta, bool mult, cudaStream_t s);
+void launch_b_advance(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int L,
+                      cudaStream_t s);
+void launch_b_prep(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int L, int Lp,
+                   cudaStream_t s);
+void launch_b_assign(const BatchSet *sets, int S, const int64_t *pre_tiles, int64_t total_tiles,
+                     int L, int Lp, int *counter, cudaStream_t s);
+void launch_b_exact(const BatchSet *sets, int S, int L, int Lp, int max_ngroups, cudaStream_t s);
+void launch_b_reset(const BatchSet *sets, int S, int *counter, cudaStream_t s);
+
 void launch_grad_x(const float *X, int64_t M, int L, const float *C, int N, const int32_t *assign,
                    float gD, float *e, float *dX, DevState *st, cudaStream_t s);
 void launch_combine_grad(const float *pieces, const int32_t *off, int N, int L, int64_t S,

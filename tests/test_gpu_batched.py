@@ -1,0 +1,69 @@
+"""Batched ragged LBG (many independent problems advanced together) vs one
+lbg_train per problem (bitwise: the batched launches run the same per-problem
+arithmetic) and vs the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from _gpu_helpers import check_assign, check_D
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbg():
+    from paper_0910_4711_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_0910_4711_gb300 as m
+    return m
+
+
+def ragged_sets(seed, sizes, Ns):
+    from paper_0910_4711_gb300 import synth
+    parts = []
+    for k, M in enumerate(sizes):
+        X = synth.blocks(synth.make_image(seed + k, 512, 512), 4)
+        parts.append(X[:M])
+    row_off = np.concatenate([[0], np.cumsum([p.shape[0] for p in parts])])
+    return parts, np.concatenate(parts), row_off, list(Ns)
+
+
+def test_batched_equals_single_problem_runs(lbg):
+    parts, Xc, row_off, Ns = ragged_sets(40, [500, 16384, 3000, 12345, 777, 9000],
+                                         [4, 256, 64, 128, 16, 32])
+    r = lbg.lbg_train_batched(torch.from_numpy(Xc).cuda(), row_off, Ns)
+    assert r.status == 0
+    for s, (X, N) in enumerate(zip(parts, Ns)):
+        single = lbg.lbg_train(torch.from_numpy(X).cuda(), N, 0.01, 1e-3)
+        assert torch.equal(r.codebook(s), single.C), s
+        a = r.assign[row_off[s]:row_off[s + 1]]
+        assert torch.equal(a, single.assign), s
+        assert r.D[s] == single.D, s
+
+
+def test_batched_matches_oracle(lbg):
+    parts, Xc, row_off, Ns = ragged_sets(60, [2048, 5000, 1500], [64, 128, 8])
+    r = lbg.lbg_train_batched(torch.from_numpy(Xc).cuda(), row_off, Ns)
+    for s, X in enumerate(parts):
+        C = r.codebook(s).cpu().numpy()
+        a_ref, e_ref, gap = oracle.assign(X, C.astype(np.float64))
+        check_assign(X, C, r.assign[row_off[s]:row_off[s + 1]].cpu().numpy(), a_ref, e_ref, gap)
+        check_D(r.D[s], float(e_ref.sum()))
+
+
+def test_batched_host_buffers_and_single_problem(lbg):
+    parts, Xc, row_off, Ns = ragged_sets(70, [3000], [32])
+    rd = lbg.lbg_train_batched(torch.from_numpy(Xc).cuda(), row_off, Ns)
+    rh = lbg.lbg_train_batched(Xc, row_off, Ns)
+    np.testing.assert_array_equal(rd.C.cpu().numpy(), rh.C)
+    assert rd.D == rh.D
+
+
+def test_batched_rejects_bad_sizes(lbg):
+    X = np.zeros((10, 16), np.float32)
+    with pytest.raises(lbg.LBGError):
+        lbg.lbg_train_batched(X, [0, 5, 10], [4, 3])       # 3 not a power of 2
+    with pytest.raises(lbg.LBGError):
+        lbg.lbg_train_batched(X, [0, 0, 10], [4, 4])       # empty problem
