@@ -62,6 +62,12 @@ def parse():
                     help="timed steps of the other form (0: skip it)")
     ap.add_argument("--no-grad", action="store_true",
                     help="skip the differentiation leg (GMM, M=262144, L=32, N=512)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched leg (64 ragged problems, L=16)")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the full-LBG timing of the 512x512 image workload")
+    ap.add_argument("--large", action="store_true",
+                    help="add the 64-image leg: LBG to N=4096 on 16.7M vectors + encode of 16.7M more")
     return ap.parse_args()
 
 
@@ -375,6 +381,13 @@ def run_ours(args):
     if not args.no_grad:
         line["differentiation"] = grad_leg(lbg, synth, torch, stream, flush, args, dist)
 
+    if not args.no_batched:
+        line["batched"] = batched_leg(lbg, synth, torch)
+    if not args.no_small:
+        line["small_full_lbg"] = small_leg(lbg, synth, torch)
+    if args.large:
+        line["large"] = large_leg(lbg, synth, torch)
+
     # end to end through the public API with host buffers
     if not args.no_e2e:
         Xh = torch.from_numpy(X_np).pin_memory()
@@ -438,6 +451,85 @@ def grad_leg(lbg, synth, torch, stream, flush, args, dist):
             "backward_work": "read X twice (dX pass, cell sums), write dX, read the cell table twice, "
                              "read C, write dC: 3*M*L*4 + 2*M*4 + 2*N*L*4 bytes",
             "forward_evals_per_s": Mg * Ng / (fwd / 1e3)}
+
+
+def small_leg(lbg, synth, torch):
+    """Full LBG design on one 512x512 image, 4x4 blocks (M=16384, L=16, N=256)."""
+    X_np, N = synth.workload("img512_b4_n256")
+    X = torch.from_numpy(X_np).cuda()
+    out = {"workload": workload_desc("img512_b4_n256", X_np, N)}
+    for prec in ("fp32", "bf16"):
+        lbg.lbg_train(X, N, 0.01, 1e-3, precision=prec)   # warm
+        ts = []
+        for _ in range(5):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = lbg.lbg_train(X, N, 0.01, 1e-3, precision=prec)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        out[prec] = {"full_lbg_ms": 1e3 * statistics.median(ts), "passes": r.n_passes, "D": r.D}
+    return out
+
+
+def batched_leg(lbg, synth, torch):
+    """64 ragged problems: M_s log-uniform in [4096, 262144], N_s in {64..1024}, L=16 (4x4
+    blocks of each problem's own 2048x2048 image); the whole batched design vs one lbg_train
+    per problem on the same GPU."""
+    spec = synth.batched_sets(3000)
+    parts = [synth.blocks(synth.make_image(seed, 2048, 2048), 4)[:M] for seed, M, _ in spec]
+    Ns = [n for _, _, n in spec]
+    row_off = np.concatenate([[0], np.cumsum([p.shape[0] for p in parts])])
+    X = torch.from_numpy(np.concatenate(parts)).cuda()
+    lbg.lbg_train_batched(X, row_off, Ns, max_passes=1)   # warm: workspace, graph capture
+    ts = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = lbg.lbg_train_batched(X, row_off, Ns)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    Xs = [X[row_off[s]:row_off[s + 1]] for s in range(len(Ns))]
+    for s in range(len(Ns)):   # warm the single-problem path
+        lbg.lbg_train(Xs[s], Ns[s], 0.01, 1e-3, max_passes=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq_passes = 0
+    for s in range(len(Ns)):
+        seq_passes = max(seq_passes, lbg.lbg_train(Xs[s], Ns[s], 0.01, 1e-3).n_passes)
+    torch.cuda.synchronize()
+    seq = time.perf_counter() - t0
+    bt = statistics.median(ts)
+    return {"workload": f"64 problems, sum M = {int(row_off[-1])}, L = 16, N in {{64..1024}}",
+            "batched_s": bt, "sequential_s": seq, "speedup": seq / bt,
+            "max_passes": r.max_passes_run, "passes_per_s": r.max_passes_run / bt}
+
+
+def large_leg(lbg, synth, torch):
+    """64 2048x2048 images, 4x4 blocks: LBG to N=4096 on 16.7M vectors, then encode 16.7M more;
+    BF16 vs FP32."""
+    X_np, N = synth.workload("img2048x64_b4_n4096")
+    X = torch.from_numpy(X_np).cuda()
+    del X_np
+    Y = torch.from_numpy(synth.image_blocks(range(5101, 5165), 2048, 2048, 4)).cuda()
+    out = {"workload": "img2048x64_b4_n4096 train (M=16777216, L=16, N=4096) + encode of 16777216 "
+                       "more vectors (seeds 5101..5164)"}
+    for prec in ("bf16", "fp32"):
+        lbg.lbg_train(X, N, 0.01, 1e-3, max_passes=1, precision=prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = lbg.lbg_train(X, N, 0.01, 1e-3, precision=prec)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        idx = torch.empty(Y.shape[0], dtype=torch.int32, device="cuda")
+        lbg.vq_encode(Y, r.C, idx_out=idx, precision=prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        enc = lbg.vq_encode(Y, r.C, idx_out=idx, precision=prec, phase_ms=True)
+        torch.cuda.synchronize()
+        t_enc = time.perf_counter() - t0
+        out[prec] = {"full_lbg_s": t_train, "passes": r.n_passes, "D": r.D, "encode_s": t_enc,
+                     "encode_evals_per_s": Y.shape[0] * N / t_enc, "encode_phase_ms": enc.phase_ms}
+    return out
 
 
 def main():

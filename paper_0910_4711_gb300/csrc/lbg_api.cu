@@ -861,21 +861,26 @@ lbg_status lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double del
     DevState *hs = nullptr;
     CK(cudaMallocHost(&hs, sizeof(DevState)));
     lbg_status out = LBG_OK;
+    auto pass = [&](cudaStream_t sst) {
+        Call cs = c;
+        cs.s = sst;
+        run_prepare(cs, p, Ccur, n_dev, N, mu, st);
+        run_assign(cs, p, dX, Ccur, n_dev, N, mu, st, dA);
+        run_exact(cs, p, dX, n_dev, N, st, dA);
+        launch_hist(dA, cs.at<float>(p.e), M, p.R, p.CH, n_dev, N, true, cs.at<int32_t>(p.table),
+                    cs.at<double>(p.dpart), st, true, sst);
+        launch_ctl(cs.at<double>(p.dpart), p.CH, st, MODE_TRAIN, theta, o.max_passes, N, rec,
+                   max_rec, sst);
+        run_update(cs, p, dX, n_dev, N, st, dA, Ccur, Ccur, true);
+        if (o.reseed_empty)
+            launch_reseed(cs.at<int32_t>(p.off), n_dev, N, L, delta, Ccur, st, true, sst);
+        launch_split(Ccur, Calt, N, L, delta, o.split_multiplicative != 0, st, sst);
+        launch_advance(Calt, Ccur, N, L, st, sst);
+    };
+    GraphPass gp;
+    gp.build(c.s, pass);
     for (;;) {
-        for (int b = 0; b < batch && issued < max_total; ++b, ++issued) {
-            run_prepare(c, p, Ccur, n_dev, N, mu, st);
-            run_assign(c, p, dX, Ccur, n_dev, N, mu, st, dA);
-            run_exact(c, p, dX, n_dev, N, st, dA);
-            launch_hist(dA, c.at<float>(p.e), M, p.R, p.CH, n_dev, N, true, c.at<int32_t>(p.table),
-                        c.at<double>(p.dpart), st, true, c.s);
-            launch_ctl(c.at<double>(p.dpart), p.CH, st, MODE_TRAIN, theta, o.max_passes, N, rec,
-                       max_rec, c.s);
-            run_update(c, p, dX, n_dev, N, st, dA, Ccur, Ccur, true);
-            if (o.reseed_empty)
-                launch_reseed(c.at<int32_t>(p.off), n_dev, N, L, delta, Ccur, st, true, c.s);
-            launch_split(Ccur, Calt, N, L, delta, o.split_multiplicative != 0, st, c.s);
-            launch_advance(Calt, Ccur, N, L, st, c.s);
-        }
+        for (int b = 0; b < batch && issued < max_total; ++b, ++issued) gp.run(c.s, pass);
         if (cudaGetLastError() != cudaSuccess) {
             out = LBG_ERR_CUDA;
             break;
