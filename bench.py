@@ -79,14 +79,16 @@ def workload_desc(name, X, N):
 
 
 # ------------------------------------------------------------------ distributed
-def dist_setup(n):
+def dist_setup(n, backend="nccl"):
+    """Join the process group torchrun set up (one replica per GPU); (0, 1, None) alone."""
     if n <= 1 or "RANK" not in os.environ:
         return 0, 1, None
     import torch
     import torch.distributed as dist
     rank, world = int(os.environ["RANK"]), int(os.environ["WORLD_SIZE"])
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
-    dist.init_process_group("nccl")
+    if backend == "nccl":
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
+    dist.init_process_group(backend)
     return rank, world, dist
 
 
@@ -99,9 +101,16 @@ def max_over_ranks(dist, v):
     if dist is None:
         return v
     import torch
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(world, units_per_rank, seconds):
+    """Whole-job rate of `world` replicas that each process `units_per_rank` units, timed by the
+    slowest rank (`seconds` is already the max over ranks)."""
+    return world * units_per_rank / seconds
 
 
 # ------------------------------------------------------------------ clocks
@@ -116,27 +125,93 @@ def gpu_uuid(dev):
         return vis.split(",")[dev] if vis else str(dev)
 
 
+class NvmlClocks:
+    """Reads SM clock, max SM clock, power and clock-event reasons of one GPU
+    through NVML's public C API (libnvidia-ml, shipped with the driver).  Read
+    only: nothing here changes a GPU setting."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, uuid):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML handle for " + uuid)
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sample(self):
+        ct = self.ct
+        sm, mx, mw, rs = ct.c_uint(), ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(sm))        # NVML_CLOCK_SM
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ct.byref(mx))
+        self.lib.nvmlDeviceGetPowerUsage(self.h, ct.byref(mw))
+        self.reasons_fn(self.h, ct.byref(rs))
+        return sm.value, mx.value, mw.value / 1e3, rs.value
+
+    def close(self):
+        self.lib.nvmlShutdown()
+
+
 class ClockSampler:
+    """Samples the GPU's clocks while the timed region runs: NVML from a thread
+    every ~2 ms (so a region of a few ms still gets samples), else nvidia-smi
+    at its 200 ms minimum interval."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
-        self.path = tempfile.mktemp(suffix=".csv")
-        self.gpu = gpu_index
+    def __init__(self, gpu_uuid):
+        self.gpu = gpu_uuid
         self.p = None
+        self.nvml = None
+        self.rows = []
+        self.source = None
+
+    def _loop(self):
+        while not self.stop:
+            try:
+                self.rows.append(self.nvml.sample())
+            except Exception:
+                return
+            time.sleep(0.002)
 
     def __enter__(self):
+        import threading
+        try:
+            self.nvml = NvmlClocks(self.gpu)
+            self.stop = False
+            self.rows.append(self.nvml.sample())
+            self.th = threading.Thread(target=self._loop, daemon=True)
+            self.th.start()
+            self.source = "nvml"
+            return self
+        except Exception:
+            self.nvml = None
+        self.path = tempfile.mktemp(suffix=".csv")
         try:
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}",
                                        f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
                                        "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+            self.source = "nvidia-smi"
         except OSError:
             self.p = None
         return self
 
     def __exit__(self, *a):
+        if self.nvml is not None:
+            self.stop = True
+            self.th.join(timeout=5)
+            try:
+                self.rows.append(self.nvml.sample())
+                self.nvml.close()
+            except Exception:
+                pass
         if self.p is not None:
             self.p.terminate()
             try:
@@ -146,6 +221,15 @@ class ClockSampler:
             self.f.close()
 
     def summary(self):
+        if self.nvml is not None:
+            if not self.rows:
+                return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+            reasons = sorted({name for r in self.rows for bit, name in NvmlClocks.REASONS.items()
+                              if r[3] & bit})
+            return {"sm_mhz": statistics.median(r[0] for r in self.rows),
+                    "sm_max_mhz": max(r[1] for r in self.rows),
+                    "power_w_median": statistics.median(r[2] for r in self.rows),
+                    "samples": len(self.rows), "source": "nvml", "reasons": reasons}
         if self.p is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         rows = []
@@ -164,7 +248,7 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in rows for k in range(4) if r[2 + k] == "Active"})
         return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "samples": len(rows), "reasons": reasons}
+                "samples": len(rows), "source": "nvidia-smi", "reasons": reasons}
 
 
 # ------------------------------------------------------------------ cpu baseline
@@ -307,12 +391,12 @@ def run_ours(args):
     with ClockSampler(gpu_uuid(dev)) as clk:
         ms, ph, n_exact, wall = timed_steps(args.precision, args.steps)
     clocks = clk.summary()
-    value = world * M * N / (ms / 1e3)
+    value = job_throughput(world, M * N, ms / 1e3)
     other_line = None
     if args.fp32_steps > 0:
         o_ms, o_ph, o_ex, _ = timed_steps(other, args.fp32_steps)
         o_train_s, o_tr = trains[other]
-        other_line = {"precision": other, "value": world * M * N / (o_ms / 1e3), "unit": UNIT,
+        other_line = {"precision": other, "value": job_throughput(world, M * N, o_ms / 1e3), "unit": UNIT,
                       "ms_per_step": o_ms, "phase_ms": o_ph, "exact_rows_per_step": o_ex,
                       "full_lbg_s": o_train_s, "full_lbg_passes": o_tr.n_passes,
                       "full_lbg_D": o_tr.D}
@@ -404,7 +488,7 @@ def run_ours(args):
             r = lbg.lbg_lloyd_step(Xh, Ch, C_out=Coh, assign_out=Ah, precision=args.precision)
             times.append(time.perf_counter() - t0)
         e2e_s = max_over_ranks(dist, statistics.mean(times))
-        line["e2e"] = {"value": world * M * N / e2e_s, "unit": UNIT,
+        line["e2e"] = {"value": job_throughput(world, M * N, e2e_s), "unit": UNIT,
                        "h2d_bytes_per_step": M * L * 4 + N * L * 4,
                        "d2h_bytes_per_step": N * L * 4 + M * 4 + 8,
                        "ms_per_step": 1e3 * e2e_s}

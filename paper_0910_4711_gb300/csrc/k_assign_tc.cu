@@ -23,12 +23,20 @@
 //     |v_n - (X2 + f_n - k'_n)| <= tau (2 ||x~||^2 + 2 ||c~_n||^2) + u ||c~_n||^2,
 // and with k'_n = (2 tau + 2^-23) ||c~_n||^2, R' = 2 tau ||x~||^2 the
 // certificate of k_assign.cu applies: V2 - V1 > 2R' + 2k'_i1 + 4 eta (g1 + eta),
-// plus 2^-16 (|V1| + |V2|) for the index packing below.
+// plus 2^-18 (|V1| + |V2|) + 2^-23 (|V1| + 2|V2|) for the epilogue below.
 //
-// Epilogue.  Each value's in-tile column j (7 bits) replaces the 7 low
-// mantissa bits (one LOP3, changes the value by less than 2^-16 of it), so
-// the running top-2 is three FMNMX per value and the argmin index comes out
-// of the minimum's low bits; a per-tile compare records the tile.
+// Epilogue.  Each thread owns one row and one half (64 columns) of every
+// tile, taken as 32 column pairs (a, b).  lo = min(a, b) gets the pair index
+// (5 bits) in its low mantissa bits (one LOP3; the value moves by less than
+// 2^-18 of it); hi = (a + b) - lo is formed on the otherwise idle FMA pipe
+// (within 2^-23 (|V1| + 2|hi|) of max(a, b)); then c2 = min(c2, max(c1, lo),
+// hi) (three-input min) and c1 = min(c1, lo).  That is five ALU operations
+// per pair for the running top-2 of values with the index of the best pair;
+// a per-tile compare records the tile, and the two halves of a row are
+// merged through shared memory at the end.  Which member of the best pair is
+// the minimum is decided from the exact FP32 distances of both, when they
+// differ by more than the direct form's rounding bound (else the row goes to
+// the fallback); a certified row keeps that distance as e(m).
 // Tiles whose x~ are not BF16-exact, or codebooks whose pieces do not add up
 // exactly, send their rows to the exact FP32 fallback.
 //
@@ -38,9 +46,11 @@
 //                 layout) into a 3-stage ring;
 //   warp 1        allocates 512 TMEM columns, one thread issues the MMAs:
 //                 2 accumulators (128 rows each) x 128 columns, double-buffered;
-//   warps 2..9    epilogue, one row per thread: tcgen05.ld of its 128 values,
-//                 running top-2 with the argmin index (four interleaved chains),
-//                 then certificate, exact e(m) or a flag for the fallback.
+//   warps 2..17   epilogue, one (row, column half) per thread: tcgen05.ld of
+//                 its 64 values per tile, running top-2 with the argmin index
+//                 (four interleaved chains); after the last tile the half-0
+//                 thread of each row merges both halves and runs the
+//                 certificate, the exact e(m) or a flag for the fallback.
 // Every mbarrier wait is bounded (2 s); on a time-out the CTA stops issuing,
 // reports LBG_ERR_TIMEOUT, waits for its own copies and frees its TMEM.
 #include "lbg_internal.cuh"
@@ -56,9 +66,14 @@ constexpr int TC_ROWS = 128 * TC_NACC;         // 256 rows per CTA
 constexpr int TC_NT = 128;                     // codevectors per tile (MMA N; N = 128 is the
                                                // smallest N at full rate with both operands
                                                // in shared memory, measured)
-constexpr int TC_JBITS = 7;                    // bits of the in-tile column index
+constexpr int TC_HALF = TC_NT / 2;             // columns per epilogue thread per tile
+constexpr int TC_PAIRS = TC_HALF / 2;          // column pairs per epilogue thread per tile
+constexpr int TC_JBITS = 5;                    // bits of the in-half pair index
+constexpr float TC_PACK = 3.814697265625e-6f;  // 2^(TC_JBITS - 23): packing changes a value
+                                               // by less than this fraction of it
+constexpr float TC_HIERR = 1.1920928955078125e-7f;   // 2^-23: bound of the FMA-pipe pair maximum
 constexpr int TC_STAGES = 3;
-constexpr int TC_EPI_WARPS = 4 * TC_NACC;      // 16
+constexpr int TC_EPI_WARPS = 8 * TC_NACC;      // 16: (accumulator, lane quarter, half)
 constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);
 constexpr int TC_TMEM_COLS = 2 * TC_NACC * TC_NT;   // 512
 constexpr int TC_LMAX = 64;
@@ -131,6 +146,45 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
         : "r"(taddr));
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// One epilogue step for the column pair P = (2P, 2P+1) of the thread's half:
+// lo = min(a, b) carries the pair index in its JBITS low mantissa bits (one
+// LOP3; `keymask` = ~(2^JBITS - 1) comes in as a kernel argument so that the
+// mask stays in a register and the immediate is the index); hi = (a + b) - lo
+// runs on the FMA pipe (within 2^-24 (|lo| + 2|hi|) of max(a, b)); then the
+// running top-2 of chain P % 4.
+template <int P>
+struct PairSteps {
+    __device__ __forceinline__ static void run(const float *v, float *c1, float *c2, int keymask)
+    {
+        PairSteps<P - 1>::run(v, c1, c2, keymask);
+        constexpr int j = P - 1, q = j & 3;
+        const float a = v[2 * j], b = v[2 * j + 1];
+        const float lo = fminf(a, b);
+        const float hi = __fsub_rn(__fadd_rn(a, b), lo);
+        int kb;
+        asm("lop3.b32 %0, %1, %2, %3, 0xEA;" : "=r"(kb) : "r"(__float_as_int(lo)), "r"(keymask), "n"(j));
+        const float k = __int_as_float(kb);
+        c2[q] = fmin3(c2[q], fmaxf(c1[q], k), hi);
+        c1[q] = fminf(c1[q], k);
+    }
+};
+template <>
+struct PairSteps<0> {
+    __device__ __forceinline__ static void run(const float *, float *, float *, int) {}
+};
+
+__device__ __forceinline__ void named_sync(int id, int threads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -229,13 +283,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const __nv_bfloat16 *__restrict__ Bp, const float *__restrict__ kn,
                 const int32_t *n_dev, int n_host, const float *__restrict__ mu,
                 const float *__restrict__ C, DevState *st, int32_t *__restrict__ assign,
-                float *__restrict__ e, int32_t *__restrict__ flags)
+                float *__restrict__ e, int32_t *__restrict__ flags, int keymask)
 {
     if (st->finished) return;
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base;
     __shared__ int s_abort, s_inexact, s_prod_last, s_mma_last;
+    __shared__ float s_v1[2][TC_ROWS], s_v2[2][TC_ROWS], s_d[2][TC_ROWS], s_k[2][TC_ROWS];
+    __shared__ int s_i1[2][TC_ROWS];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int N = cur_n(n_dev, n_host);
@@ -272,25 +328,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
 
-    // Epilogue thread <-> row: accumulator acc, TMEM lane quarter = warp % 4.
-    const int acc = (warp - 2) >> 2;
+    // Epilogue thread <-> (row, column half): TMEM lane quarter = warp % 4
+    // (the quarter a warp may read), accumulator acc, half of the tile's columns.
+    const int acc = ((warp - 2) >> 2) & 1;
+    const int half = (warp - 2) >> 3;
     const int rr = 32 * (warp & 3) + lane;
     const int64_t m = m0 + 128 * acc + rr;
     if (warp >= 2) {
-        // Stage the centred x tile as BF16 into the A blocks: the 512 x L tile
-        // is contiguous in X, so the epilogue threads read it as a flat array
-        // (coalesced, several loads in flight), convert, and scatter into the
-        // core-matrix layout.
-        const int et = tid - 64;                              // 0 .. 511
+        // Stage the centred x tile as BF16 into the A blocks: the TC_ROWS x L
+        // tile is contiguous in X, so the epilogue threads read it as a flat
+        // array (coalesced, eight 16-byte loads in flight per thread), convert,
+        // and scatter into the core-matrix layout.  A tile is usable only if
+        // every x~ = x - mu is exact in FP32 (TwoSum error zero) and in BF16.
+        constexpr int ST = TC_THREADS - 64;                   // 512 staging threads
+        const int et = tid - 64;
         const int64_t rows = M - m0 < TC_ROWS ? M - m0 : TC_ROWS;
         bool inexact = false, bad = false;
         const float *Xt = X + m0 * L;
-        auto put_x = [&](int i, float xv) {   // i: flat index inside the tile (< 512 * 64)
+        auto put_x = [&](int i, float xv) {   // i: flat index inside the tile
             const int r = i / L, l = i - r * L;
             bad = bad || !isfinite(xv);
-            const float v = xv - mu[l];
+            const float ml = __ldg(mu + l);
+            const float v = __fsub_rn(xv, ml);
+            const float bb = __fsub_rn(v, xv);
+            const float err = __fadd_rn(__fsub_rn(xv, __fsub_rn(v, bb)), __fsub_rn(-ml, bb));
             const __nv_bfloat16 b = __float2bfloat16_rn(v);
-            inexact = inexact || (__bfloat162float(b) != v);
+            inexact = inexact || err != 0.f || (__bfloat162float(b) != v);
             *reinterpret_cast<__nv_bfloat16 *>(A + (r >> 7) * a_bytes + core_off(r & 127, l, sbo_a)) = b;
         };
         const int total = (int)rows * L;
@@ -298,20 +361,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const float4 *X4 = reinterpret_cast<const float4 *>(Xt);
             const int total4 = total >> 2;
             int i = et;
-            for (; i + 3 * (TC_THREADS - 64) < total4; i += 4 * (TC_THREADS - 64)) {
-                float4 q[4];
+            for (; i + 7 * ST < total4; i += 8 * ST) {
+                float4 q[8];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) q[u] = __ldg(X4 + i + u * (TC_THREADS - 64));
+                for (int u = 0; u < 8; ++u) q[u] = __ldg(X4 + i + u * ST);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int f = 4 * (i + u * (TC_THREADS - 64));
+                for (int u = 0; u < 8; ++u) {
+                    const int f = 4 * (i + u * ST);
                     put_x(f, q[u].x);
                     put_x(f + 1, q[u].y);
                     put_x(f + 2, q[u].z);
                     put_x(f + 3, q[u].w);
                 }
             }
-            for (; i < total4; i += TC_THREADS - 64) {
+            for (; i < total4; i += ST) {
                 const float4 q = __ldg(X4 + i);
                 put_x(4 * i, q.x);
                 put_x(4 * i + 1, q.y);
@@ -319,44 +382,54 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 put_x(4 * i + 3, q.w);
             }
         } else {
-            for (int i = et; i < total; i += TC_THREADS - 64) put_x(i, __ldg(Xt + i));
+            for (int i = et; i < total; i += ST) put_x(i, __ldg(Xt + i));
         }
-        // Own row: zero padding dims (and whole rows past M), the ones block.
+        // Own row (half-0 thread): zero padding dims (and whole rows past M).
         uint8_t *Ab = A + acc * a_bytes;
         const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
-        for (int l = (m < M ? L : 0); l < Lk; ++l)
-            *reinterpret_cast<__nv_bfloat16 *>(Ab + core_off(rr, l, sbo_a)) = zero;
+        if (half == 0)
+            for (int l = (m < M ? L : 0); l < Lk; ++l)
+                *reinterpret_cast<__nv_bfloat16 *>(Ab + core_off(rr, l, sbo_a)) = zero;
         if (bad) flag_error(st, ERR_NONFINITE);
         if (inexact) s_inexact = 1;
     }
     __syncthreads();
     float xn2 = 0.f;
-    if (warp >= 2) {
-        // ||x~||^2 of the own row from the staged (exact) BF16 values, then the
-        // norm block of A: 1 1 1 (x s0 pieces), X2 in three BF16 pieces.
+    if (warp >= 2 && half == 0) {
+        // ||x~||^2 of the own row from the staged (exact) BF16 values, eight
+        // per 16-byte read of a core-matrix row, then the norm block of A:
+        // 1 1 1 (x s0 pieces), X2 in three BF16 pieces, zeros.
         uint8_t *Ab = A + acc * a_bytes;
-        for (int l = 0; l < L; ++l) {
-            const float v = __bfloat162float(
-                *reinterpret_cast<const __nv_bfloat16 *>(Ab + core_off(rr, l, sbo_a)));
-            xn2 = fmaf(v, v, xn2);
+#pragma unroll
+        for (int g = 0; g < Lk / 8; ++g) {
+            const uint4 w = *reinterpret_cast<const uint4 *>(Ab + core_off(rr, 8 * g, sbo_a));
+            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const float v0 = __uint_as_float(ws[h] << 16), v1 = __uint_as_float(ws[h] & 0xFFFF0000u);
+                xn2 = fmaf(v0, v0, xn2);
+                xn2 = fmaf(v1, v1, xn2);
+            }
         }
         __nv_bfloat16 h, mi, lo;
         split3(xn2, h, mi, lo);
-        const __nv_bfloat16 one = __float2bfloat16_rn(1.f), zero = __float2bfloat16_rn(0.f);
-        for (int q = 0; q < 16; ++q) {
-            __nv_bfloat16 v = zero;
-            if (q < 3) v = one;
-            else if (q == 3) v = h;
-            else if (q == 4) v = mi;
-            else if (q == 5) v = lo;
-            *reinterpret_cast<__nv_bfloat16 *>(Ab + core_off(rr, Lk + q, sbo_a)) = v;
-        }
+        const uint32_t one = __bfloat16_as_ushort(__float2bfloat16_rn(1.f));
+        uint4 nb;
+        nb.x = one | (one << 16);
+        nb.y = one | ((uint32_t)__bfloat16_as_ushort(h) << 16);
+        nb.z = (uint32_t)__bfloat16_as_ushort(mi) | ((uint32_t)__bfloat16_as_ushort(lo) << 16);
+        nb.w = 0u;
+        *reinterpret_cast<uint4 *>(Ab + core_off(rr, Lk, sbo_a)) = nb;
+        *reinterpret_cast<uint4 *>(Ab + core_off(rr, Lk + 8, sbo_a)) = make_uint4(0u, 0u, 0u, 0u);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
+    // codebook state written by the preparation kernel (constant here)
+    const bool tc_exact_cb = st->tc_inexact == 0;
+    const float cmax = __uint_as_float(st->cmax_bits);
 
     if (warp == 0) {
         // ---------------- producer
@@ -413,7 +486,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
         }
     } else {
-        // ---------------- epilogue: one row per thread
+        // ---------------- epilogue: one (row, column half) per thread
         constexpr int NCH = 4;                       // independent min-chains
         constexpr int JMASK = (1 << TC_JBITS) - 1;
         float c1[NCH], c2[NCH];
@@ -427,110 +500,165 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
         for (int t = 0; t < ntiles; ++t) {
             const int b = t & 1;
-            if (!mbar_wait_bounded_sleep(&tfull[b], (uint32_t)(t >> 1) & 1u)) {
+            if (!mbar_wait_bounded(&tfull[b], (uint32_t)(t >> 1) & 1u)) {
                 s_abort = 1;
                 break;
             }
             tc_fence_after();
-            float v[TC_NT];
-            const uint32_t col = (uint32_t)((b * TC_NACC + acc) * TC_NT);
-            float s1[NCH];
-#pragma unroll
-            for (int q = 0; q < NCH; ++q) s1[q] = c1[q];
-            // two halves: the second TMEM read is in flight while the first half is scanned
+            float v[TC_HALF];
+            const uint32_t col = (uint32_t)((b * TC_NACC + acc) * TC_NT + half * TC_HALF);
             tmem_ld32(tmem + lane_base + col, v);
             tmem_ld32(tmem + lane_base + col + 32u, v + 32);
             tmem_ld_wait();
-            tmem_ld32(tmem + lane_base + col + 64u, v + 64);
-            tmem_ld32(tmem + lane_base + col + 96u, v + 96);
-#pragma unroll
-            for (int j = 0; j < TC_NT / 2; ++j) {
-                const int q = j % NCH;
-                const float k = __int_as_float((__float_as_int(v[j]) & ~JMASK) | j);
-                c2[q] = fminf(c2[q], fmaxf(c1[q], k));
-                c1[q] = fminf(c1[q], k);
-            }
-            tmem_ld_wait();
+            // the values are in registers: hand the accumulator back to the MMA
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[b]);
+            float s1[NCH];
 #pragma unroll
-            for (int j = TC_NT / 2; j < TC_NT; ++j) {
-                const int q = j % NCH;
-                const float k = __int_as_float((__float_as_int(v[j]) & ~JMASK) | j);
-                c2[q] = fminf(c2[q], fmaxf(c1[q], k));
-                c1[q] = fminf(c1[q], k);
-            }
+            for (int q = 0; q < NCH; ++q) s1[q] = c1[q];
+            PairSteps<TC_PAIRS>::run(v, c1, c2, keymask);
 #pragma unroll
             for (int q = 0; q < NCH; ++q) cg[q] = c1[q] < s1[q] ? t : cg[q];
             if (s_abort) break;
         }
-        // merge the chains; the index is the tile times TC_NT plus the low bits
+        // merge the chains; i1 is the first column of the minimum's pair:
+        // tile * TC_NT + half * TC_HALF + 2 * (the low bits)
         float V1 = c1[0], V2 = c2[0];
-        int i1 = cg[0] * TC_NT + (__float_as_int(c1[0]) & JMASK);
+        int i1 = cg[0] * TC_NT + half * TC_HALF + 2 * (__float_as_int(c1[0]) & JMASK);
 #pragma unroll
         for (int q = 1; q < NCH; ++q) {
-            const int iq = cg[q] * TC_NT + (__float_as_int(c1[q]) & JMASK);
+            const int iq = cg[q] * TC_NT + half * TC_HALF + 2 * (__float_as_int(c1[q]) & JMASK);
             V2 = fminf(fminf(V2, c2[q]), fmaxf(V1, c1[q]));
             const bool take = c1[q] < V1 || (c1[q] == V1 && iq < i1);
             V1 = take ? c1[q] : V1;
             i1 = take ? iq : i1;
         }
-        if (m < M && !s_abort) {
-            bool certified = false;
-            if (!s_inexact && st->tc_inexact == 0 && i1 >= 0 && i1 < N && V1 < INFINITY) {
-                const double tau = tc_tau(3 * Lk + 16);
-                const float xn2u = xn2 * SLOP;
-                const float R = 2.f * (float)tau * xn2u * SLOP;
-                const float kc = kn[i1];
-                const float cmax = __uint_as_float(st->cmax_bits);
-                const float eta = U32 * (sqrtf(xn2u) + cmax) * SLOP;
-                const float pack = 1.52587890625e-5f * (fabsf(V1) + fabsf(V2));   // 2^-16
-                // V1 ~ ||x~ - c~_i1||^2 - k' (X2 included): bound g1^2 from above
-                const float g1sq = V1 + 2.f * kc + R + pack + (float)(L + 2) * U32 * xn2u;
-                const float g1 = sqrtf(fmaxf(g1sq, 0.f)) * SLOP;
-                const float margin = (2.f * R + 2.f * kc + pack + 4.f * eta * (g1 + eta)) * SLOP;
-                certified = (V2 - V1) > margin;
+        // The two halves of a row exchange their top-2 and merge them in the
+        // same fixed order, so both threads hold the same result.
+        const int crow = 128 * acc + rr;
+        s_v1[half][crow] = V1;
+        s_v2[half][crow] = V2;
+        s_i1[half][crow] = i1;
+        named_sync(1, 32 * TC_EPI_WARPS);
+        {
+            const float A1 = s_v1[0][crow], A2 = s_v2[0][crow], B1 = s_v1[1][crow], B2 = s_v2[1][crow];
+            const int ai = s_i1[0][crow], bi = s_i1[1][crow];
+            V2 = fminf(fminf(A2, B2), fmaxf(A1, B1));
+            const bool take = B1 < A1 || (B1 == A1 && bi < ai);
+            V1 = take ? B1 : A1;
+            i1 = take ? bi : ai;
+        }
+        // The minimum is one of the pair (i1, i1 + 1).  Each half computes the
+        // exact FP32 distance of one member.  With L a multiple of 4 the warp
+        // does it cooperatively: a half-warp per row, a float4 of x and of the
+        // codevector per lane (coalesced reads of X and C), each lane sums its
+        // four terms (x_l - c_l)^2 in order, and a butterfly over the 16 lanes
+        // of each half-warp reduces the 16 rows' partial sums at once (a fixed
+        // tree: 15 shuffles per lane); the owner lane of each row takes its sum.
+        const bool usable = m < M && !s_abort && !s_inexact && tc_exact_cb && i1 >= 0 && i1 < N &&
+                            V1 < INFINITY;
+        const int cand = i1 + half;
+        const int ccand = (usable && cand < N) ? cand : -1;
+        const float kc = ccand >= 0 ? __ldg(kn + ccand) : 0.f;
+        float dc = INFINITY;
+        if ((L & 3) == 0 && ((reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(X)) & 15u) == 0) {
+            const int rq = lane & 15, sub = lane >> 4;
+            const int64_t mrow0 = m0 + 128 * acc + 32 * (warp & 3);   // row of lane 0
+            float p[16];
+#pragma unroll
+            for (int bt = 0; bt < 2; ++bt) {                          // two batches of 8 rows
+                int crs[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) crs[k] = __shfl_sync(0xffffffffu, ccand, 2 * (8 * bt + k) + sub);
+                float4 c4[8], x4[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const bool on = crs[k] >= 0 && 4 * rq < L;
+                    const int64_t mr = mrow0 + 2 * (8 * bt + k) + sub;
+                    c4[k] = on ? __ldg(reinterpret_cast<const float4 *>(C + (size_t)crs[k] * L) + rq)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+                    x4[k] = on ? __ldg(reinterpret_cast<const float4 *>(X + mr * L) + rq)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    float d = __fsub_rn(x4[k].x, c4[k].x);
+                    float q = d * d;
+                    d = __fsub_rn(x4[k].y, c4[k].y);
+                    q = fmaf(d, d, q);
+                    d = __fsub_rn(x4[k].z, c4[k].z);
+                    q = fmaf(d, d, q);
+                    d = __fsub_rn(x4[k].w, c4[k].w);
+                    p[8 * bt + k] = fmaf(d, d, q);
+                }
             }
-            if (certified) {
-                const float *xr = X + m * L;
-                const float *cr = C + (size_t)i1 * L;
-                float d2 = 0.f;
-                if ((L & 3) == 0 && ((reinterpret_cast<uintptr_t>(xr) | reinterpret_cast<uintptr_t>(cr)) & 15u) == 0) {
-                    const float4 *x4 = reinterpret_cast<const float4 *>(xr);
-                    const float4 *c4 = reinterpret_cast<const float4 *>(cr);
-                    for (int q0 = 0; q0 < L / 4; q0 += 4) {   // four 16-byte pairs in flight
-                        float4 a[4], b[4];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            if (q0 + u < L / 4) {
-                                a[u] = __ldg(x4 + q0 + u);
-                                b[u] = __ldg(c4 + q0 + u);
-                            }
+            for (int lvl = 8; lvl >= 1; lvl >>= 1) {
+                const bool up = (rq & lvl) != 0;
 #pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            if (q0 + u < L / 4) {
-                                float d = a[u].x - b[u].x;
-                                d2 = fmaf(d, d, d2);
-                                d = a[u].y - b[u].y;
-                                d2 = fmaf(d, d, d2);
-                                d = a[u].z - b[u].z;
-                                d2 = fmaf(d, d, d2);
-                                d = a[u].w - b[u].w;
-                                d2 = fmaf(d, d, d2);
-                            }
-                    }
-                } else {
-                    for (int l = 0; l < L; ++l) {
-                        const float d = xr[l] - cr[l];
-                        d2 = fmaf(d, d, d2);
+                for (int i = 0; i < lvl; ++i) {
+                    const float send = up ? p[i] : p[i + lvl];
+                    const float keep = up ? p[i + lvl] : p[i];
+                    p[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, lvl));
+                }
+            }
+            // lane (sub, rq) now holds the sum of row 2 rq + sub
+            const float got = __shfl_sync(0xffffffffu, p[0], (lane & 1) * 16 + (lane >> 1));
+            if (ccand >= 0) dc = got;
+        } else if (ccand >= 0) {
+            const float *xr = X + m * L;
+            const float *cr = C + (size_t)ccand * L;
+            float d2 = 0.f;
+            for (int l = 0; l < L; ++l) {
+                const float d = __fsub_rn(__ldg(xr + l), __ldg(cr + l));
+                d2 = fmaf(d, d, d2);
+            }
+            dc = d2;
+        }
+        s_d[half][crow] = dc;
+        s_k[half][crow] = kc;
+        named_sync(2, 32 * TC_EPI_WARPS);
+        if (half == 0 && m < M && !s_abort) {
+            // the smaller distance is taken when the two differ by more than the
+            // rounding bound of the FP32 sum, |fl(d2) - d2| <= (L + 2) u d2 for
+            // any order of the L terms (kept as (L + 4) u); else the row is not
+            // certified
+            bool certified = false;
+            if (usable) {
+                float da = s_d[0][crow], ka = s_k[0][crow];
+                const float db = s_d[1][crow], kb = s_k[1][crow];
+                int ii = i1;
+                bool sure = true;
+                if (i1 + 1 < N) {
+                    const float tol = (float)(L + 4) * U32 * (da + db) * SLOP;
+                    if (db < da - tol) {
+                        ii = i1 + 1;
+                        da = db;
+                        ka = kb;
+                    } else if (!(da < db - tol)) {
+                        sure = false;
                     }
                 }
-                assign[m] = i1;
-                e[m] = d2;
-            } else {
-                flags[atomicAdd(&st->nflag, 1)] = (int32_t)m;
+                if (sure) {
+                    const double tau = tc_tau(3 * Lk + 16);
+                    const float xn2u = xn2 * SLOP;
+                    const float R = 2.f * (float)tau * xn2u * SLOP;
+                    const float eta = U32 * (sqrtf(xn2u) + cmax) * SLOP;
+                    // index packing of the pair minima, FMA-pipe pair maxima
+                    const float pack = TC_PACK * (fabsf(V1) + fabsf(V2)) + TC_HIERR * (fabsf(V1) + 2.f * fabsf(V2));
+                    // V1 ~ ||x~ - c~_ii||^2 - k' (X2 included): bound g1^2 from above
+                    const float g1sq = V1 + 2.f * ka + R + pack + (float)(L + 2) * U32 * xn2u;
+                    const float g1 = sqrtf(fmaxf(g1sq, 0.f)) * SLOP;
+                    const float margin = (2.f * R + 2.f * ka + pack + 4.f * eta * (g1 + eta)) * SLOP;
+                    certified = (V2 - V1) > margin;
+                }
+                if (certified) {
+                    assign[m] = ii;
+                    e[m] = da;
+                }
             }
+            if (!certified) flags[atomicAdd(&st->nflag, 1)] = (int32_t)m;
         }
     }
 
@@ -590,7 +718,8 @@ static void launch_tc(const float *X, int64_t M, int L, const void *Bp, const fl
     const int64_t grid = (M + TC_ROWS - 1) / TC_ROWS;
     if (grid == 0) return;
     k_assign_tc<LK><<<(unsigned)grid, TC_THREADS, smem, s>>>(
-        X, M, L, static_cast<const __nv_bfloat16 *>(Bp), kn, n_dev, n_host, mu, C, st, assign, e, flags);
+        X, M, L, static_cast<const __nv_bfloat16 *>(Bp), kn, n_dev, n_host, mu, C, st, assign, e, flags,
+        ~((1 << TC_JBITS) - 1));
 }
 
 void launch_assign_tc(const float *X, int64_t M, int L, const void *Bp, const float *kn,

@@ -1,0 +1,72 @@
+"""bench.py's multi-rank path on CPU: two `gloo` ranks stand in for two GPUs.
+
+The hot path does not shard (each rank runs an independent replica of the
+whole LBG design on its own data), so the only cross-rank steps are the
+barrier around the timed region and the max over ranks of the step time; the
+job's value is world x per-rank units / that max.  The reference arm runs on
+rank 0 only; the other ranks exit at once.
+"""
+import json
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank),
+                      MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import bench
+    r, w, dist = bench.dist_setup(world, backend="gloo")
+    assert (r, w) == (rank, world) and dist is not None
+    bench.barrier(dist)
+    # rank k "measured" a step of (3 + k) ms; every rank must see the slowest one
+    ms = bench.max_over_ranks(dist, 3.0 + rank)
+    value = bench.job_throughput(w, 1000 * 64, ms / 1e3)
+    bench.barrier(dist)
+
+    class Args:
+        workload = "img512_b4_n256"
+        gpus = world
+        steps = 1
+        warmup = 0
+
+    ref_rc = bench.run_reference(Args) if rank != 0 else None
+    with open(os.path.join(out_dir, f"rank{rank}.json"), "w") as f:
+        json.dump({"ms": ms, "value": value, "ref_rc": ref_rc}, f)
+    dist.destroy_process_group()
+
+
+def test_two_rank_replicas_aggregate(tmp_path):
+    world = 2
+    mp.start_processes(_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world,
+                       join=True, start_method="spawn")
+    res = [json.load(open(tmp_path / f"rank{r}.json")) for r in range(world)]
+    for r in res:
+        assert r["ms"] == pytest.approx(4.0)            # max over ranks, not the local time
+        assert r["value"] == pytest.approx(2 * 64000 / 4e-3)
+    assert res[1]["ref_rc"] == 0                        # non-zero ranks skip the reference arm
+
+
+def test_single_process_needs_no_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    saved = os.environ.pop("RANK", None)
+    try:
+        assert bench.dist_setup(1) == (0, 1, None)
+        assert bench.max_over_ranks(None, 2.5) == 2.5
+        assert bench.job_throughput(1, 10, 2.0) == 5.0
+    finally:
+        if saved is not None:
+            os.environ["RANK"] = saved
