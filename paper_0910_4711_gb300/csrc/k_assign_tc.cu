@@ -41,16 +41,24 @@
 // exactly, send their rows to the exact FP32 fallback.
 //
 // Kernel layout (one CTA per SM, 256 rows per CTA):
+//   prologue      the epilogue warps stage the x tile (coalesced) as centred
+//                 BF16 rows in shared memory, then each thread writes its half
+//                 of its row's A operand (x~ and the norm block) into tensor
+//                 memory with tcgen05.st: the MMAs read A from TMEM and only B
+//                 from shared memory, which leaves shared-memory bandwidth for
+//                 the codebook stream;
 //   warp 0        producer: TMA bulk copies of prepared codebook tiles (128
 //                 codevectors x KB BF16, already in the MMA's shared-memory
 //                 layout) into a 3-stage ring;
-//   warp 1        allocates 512 TMEM columns, one thread issues the MMAs:
-//                 2 accumulators (128 rows each) x 128 columns, double-buffered;
+//   warp 1        allocates 512 TMEM columns, one thread issues the MMAs: job
+//                 j = 2 t + a (tile t, accumulator a of 128 rows) accumulates
+//                 into slot j % 3 of a ring of three 128-column accumulators;
 //   warps 2..17   epilogue, one (row, column half) per thread: tcgen05.ld of
-//                 its 64 values per tile, running top-2 with the argmin index
-//                 (four interleaved chains); after the last tile the half-0
-//                 thread of each row merges both halves and runs the
-//                 certificate, the exact e(m) or a flag for the fallback.
+//                 its 64 values per job, running top-2 with the pair index
+//                 (four interleaved chains); after the last tile the two halves
+//                 of each row merge, compute the exact distances of the best
+//                 pair's two codevectors, and the half-0 thread runs the
+//                 certificate, writes the index and e(m) or flags the row.
 // Every mbarrier wait is bounded (2 s); on a time-out the CTA stops issuing,
 // reports LBG_ERR_TIMEOUT, waits for its own copies and frees its TMEM.
 #include "lbg_internal.cuh"
@@ -75,7 +83,9 @@ constexpr float TC_HIERR = 1.1920928955078125e-7f;   // 2^-23: bound of the FMA-
 constexpr int TC_STAGES = 3;
 constexpr int TC_EPI_WARPS = 8 * TC_NACC;      // 16: (accumulator, lane quarter, half)
 constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);
-constexpr int TC_TMEM_COLS = 2 * TC_NACC * TC_NT;   // 512
+constexpr int TC_SLOTS = 3;                    // accumulator ring: (tile, accumulator) jobs
+constexpr int TC_A_COL = TC_SLOTS * TC_NT;     // TMEM column of the A operand (x~ rows)
+constexpr int TC_TMEM_COLS = 512;              // 3 x 128 accumulator columns + 2 x (L + 16)/2
 constexpr int TC_LMAX = 64;
 
 constexpr float U32 = 5.9604644775390625e-8f;   // 2^-24
@@ -107,22 +117,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 // N >> 3 at bit 17, M >> 4 at bit 24.
 constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_NT >> 3) << 17) |
                               ((uint32_t)(128 >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     smem_addr(bar))
-                 : "memory");
-}
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
@@ -188,6 +182,84 @@ __device__ __forceinline__ void named_sync(int id, int threads)
 }
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Store n consecutive 32-bit columns of the warp's 32 lanes (n = 4, 8, 16).
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t *r)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(r[0]), "r"(r[1]),
+                 "r"(r[2]), "r"(r[3])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t *r)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *r)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+                     taddr),
+                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+                 "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+                 : "memory");
+}
+template <int NW>
+__device__ __forceinline__ void tmem_st_words(uint32_t taddr, const uint32_t *r)
+{
+    int c = 0;
+    if (NW - c >= 16) { tmem_st16(taddr + c, r + c); c += 16; }
+    if (NW - c >= 8) { tmem_st8(taddr + c, r + c); c += 8; }
+    if (NW - c >= 4) { tmem_st4(taddr + c, r + c); c += 4; }
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// tcgen05.mma, kind::f16, with the A operand in tensor memory (row = lane,
+// two BF16 of K per 32-bit column) and B in shared memory, and tcgen05.commit,
+// each issued by one elected lane of a converged warp (the whole warp runs the
+// issue loop, so its addresses stay warp-uniform).
+__device__ __forceinline__ void mma_bf16_ta_elect(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p, e;\n\telect.sync _|e, 0xffffffff;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(TC_IDESC), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit_elect(uint64_t *bar)
+{
+    asm volatile(
+        "{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(smem_addr(bar))
+        : "memory");
+}
+
+// The A words of one half of a row (half H of the K = LK + 16 elements, two
+// BF16 per word): centred x~ from the staged row (zero past L and for rows
+// past M), and the running sum of squares of those x~ in order.  Half 1 also
+// holds the norm block, filled in later.
+template <int LK, int H>
+__device__ __forceinline__ void a_words(const __nv_bfloat16 *xrow, int L, bool live, uint32_t *wv, float &part)
+{
+    constexpr int KA = LK + 16, HK = KA / 2, E0 = H * HK;
+    constexpr int XE = H == 0 ? HK : LK - HK;          // x~ elements in this half
+#pragma unroll
+    for (int w = 0; w < HK / 2; ++w) wv[w] = 0u;
+#pragma unroll
+    for (int g = 0; g < XE / 8; ++g) {
+        const uint4 q = live ? *reinterpret_cast<const uint4 *>(xrow + E0 + 8 * g) : make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t qs[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int e0 = E0 + 8 * g + 2 * j;
+            const uint32_t lo = e0 < L ? (qs[j] & 0xFFFFu) : 0u, hi = e0 + 1 < L ? (qs[j] >> 16) : 0u;
+            wv[4 * g + j] = lo | (hi << 16);
+            const float a = __uint_as_float(lo << 16), b = __uint_as_float(hi << 16);
+            part = fmaf(a, a, part);
+            part = fmaf(b, b, part);
+        }
+    }
+}
 
 // Accumulation-error coefficient tau of the file header for KB accumulated
 // BF16 elements.
@@ -287,9 +359,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 {
     if (st->finished) return;
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], tfull[2], tempty[2];
+    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], tfull[TC_SLOTS], tempty[TC_SLOTS];
     __shared__ uint32_t tmem_base;
-    __shared__ int s_abort, s_inexact, s_prod_last, s_mma_last;
+    __shared__ int s_abort, s_inexact, s_prod_last, s_mma_tile, s_mma_job;
     __shared__ float s_v1[2][TC_ROWS], s_v2[2][TC_ROWS], s_d[2][TC_ROWS], s_k[2][TC_ROWS];
     __shared__ int s_i1[2][TC_ROWS];
 
@@ -298,11 +370,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int ntiles = (N + TC_NT - 1) / TC_NT;
     constexpr int Lk = LK;
     constexpr int KA = LK + 16, KB = 3 * LK + 16;
-    constexpr uint32_t sbo_a = (uint32_t)(KA / 8) * 128u, sbo_b = (uint32_t)(KB / 8) * 128u;
-    constexpr uint32_t a_bytes = 128u * KA * 2u;               // one accumulator's A block
+    constexpr int XSTR = LK + 8;                               // staged row stride (BF16), padded
+    constexpr uint32_t sbo_b = (uint32_t)(KB / 8) * 128u;
+    constexpr uint32_t xs_bytes = (uint32_t)TC_ROWS * XSTR * 2u;
     constexpr uint32_t stage_bytes = (uint32_t)TC_NT * KB * 2u;
-    uint8_t *A = smem;
-    uint8_t *Bs = smem + TC_NACC * a_bytes;
+    __nv_bfloat16 *XS = reinterpret_cast<__nv_bfloat16 *>(smem);
+    uint8_t *Bs = smem + xs_bytes;
     const int64_t m0 = (int64_t)blockIdx.x * TC_ROWS;
 
     if (tid == 0) {
@@ -310,15 +383,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < TC_SLOTS; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], TC_EPI_WARPS);
+            mbar_init(&tempty[b], TC_EPI_WARPS / TC_NACC);
         }
         fence_mbar_init();
         s_abort = 0;
         s_inexact = 0;
         s_prod_last = -1;
-        s_mma_last = -1;
+        s_mma_tile = -1;
+        s_mma_job = -1;
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -329,18 +403,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 
     // Epilogue thread <-> (row, column half): TMEM lane quarter = warp % 4
-    // (the quarter a warp may read), accumulator acc, half of the tile's columns.
+    // (the quarter a warp may access), accumulator acc, half of the columns.
     const int acc = ((warp - 2) >> 2) & 1;
     const int half = (warp - 2) >> 3;
     const int rr = 32 * (warp & 3) + lane;
     const int64_t m = m0 + 128 * acc + rr;
-    if (warp >= 2) {
-        // Stage the centred x tile as BF16 into the A blocks: the TC_ROWS x L
-        // tile is contiguous in X, so the epilogue threads read it as a flat
-        // array (coalesced, eight 16-byte loads in flight per thread), convert,
-        // and scatter into the core-matrix layout.  A tile is usable only if
-        // every x~ = x - mu is exact in FP32 (TwoSum error zero) and in BF16.
-        constexpr int ST = TC_THREADS - 64;                   // 512 staging threads
+    const int crow = 128 * acc + rr;
+    const bool epi = warp >= 2 && warp < 2 + TC_EPI_WARPS;
+    if (epi) {
+        // Stage the centred x tile as BF16 rows in shared memory: the TC_ROWS x
+        // L tile is contiguous in X, so the epilogue threads read it as a flat
+        // array (coalesced, eight 16-byte loads in flight per thread).  A tile
+        // is usable only if every x~ = x - mu is exact in FP32 (TwoSum error
+        // zero) and in BF16.
+        constexpr int ST = 32 * TC_EPI_WARPS;                 // 512 staging threads
         const int et = tid - 64;
         const int64_t rows = M - m0 < TC_ROWS ? M - m0 : TC_ROWS;
         bool inexact = false, bad = false;
@@ -354,7 +430,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const float err = __fadd_rn(__fsub_rn(xv, __fsub_rn(v, bb)), __fsub_rn(-ml, bb));
             const __nv_bfloat16 b = __float2bfloat16_rn(v);
             inexact = inexact || err != 0.f || (__bfloat162float(b) != v);
-            *reinterpret_cast<__nv_bfloat16 *>(A + (r >> 7) * a_bytes + core_off(r & 127, l, sbo_a)) = b;
+            XS[r * XSTR + l] = b;
         };
         const int total = (int)rows * L;
         if ((L & 3) == 0 && (reinterpret_cast<uintptr_t>(Xt) & 15u) == 0) {
@@ -384,45 +460,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         } else {
             for (int i = et; i < total; i += ST) put_x(i, __ldg(Xt + i));
         }
-        // Own row (half-0 thread): zero padding dims (and whole rows past M).
-        uint8_t *Ab = A + acc * a_bytes;
-        const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
-        if (half == 0)
-            for (int l = (m < M ? L : 0); l < Lk; ++l)
-                *reinterpret_cast<__nv_bfloat16 *>(Ab + core_off(rr, l, sbo_a)) = zero;
         if (bad) flag_error(st, ERR_NONFINITE);
         if (inexact) s_inexact = 1;
     }
-    __syncthreads();
-    float xn2 = 0.f;
-    if (warp >= 2 && half == 0) {
-        // ||x~||^2 of the own row from the staged (exact) BF16 values, eight
-        // per 16-byte read of a core-matrix row, then the norm block of A:
-        // 1 1 1 (x s0 pieces), X2 in three BF16 pieces, zeros.
-        uint8_t *Ab = A + acc * a_bytes;
-#pragma unroll
-        for (int g = 0; g < Lk / 8; ++g) {
-            const uint4 w = *reinterpret_cast<const uint4 *>(Ab + core_off(rr, 8 * g, sbo_a));
-            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const float v0 = __uint_as_float(ws[h] << 16), v1 = __uint_as_float(ws[h] & 0xFFFF0000u);
-                xn2 = fmaf(v0, v0, xn2);
-                xn2 = fmaf(v1, v1, xn2);
-            }
-        }
-        __nv_bfloat16 h, mi, lo;
-        split3(xn2, h, mi, lo);
-        const uint32_t one = __bfloat16_as_ushort(__float2bfloat16_rn(1.f));
-        uint4 nb;
-        nb.x = one | (one << 16);
-        nb.y = one | ((uint32_t)__bfloat16_as_ushort(h) << 16);
-        nb.z = (uint32_t)__bfloat16_as_ushort(mi) | ((uint32_t)__bfloat16_as_ushort(lo) << 16);
-        nb.w = 0u;
-        *reinterpret_cast<uint4 *>(Ab + core_off(rr, Lk, sbo_a)) = nb;
-        *reinterpret_cast<uint4 *>(Ab + core_off(rr, Lk + 8, sbo_a)) = make_uint4(0u, 0u, 0u, 0u);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -430,6 +470,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // codebook state written by the preparation kernel (constant here)
     const bool tc_exact_cb = st->tc_inexact == 0;
     const float cmax = __uint_as_float(st->cmax_bits);
+
+    float xn2 = 0.f;
+    if (epi) {
+        // The A operand in tensor memory: each thread writes its half of its
+        // row's K = Lk + 16 BF16 (two per column): x~ (zero past L and for
+        // rows past M), then in half 1 the norm block 1 1 1 (x s0 pieces),
+        // X2 = ||x~||^2 in three BF16 pieces, zeros.  ||x~||^2 is half 0's sum
+        // of squares plus half 1's, in that order.
+        constexpr int NW = KA / 4;                               // words per half
+        uint32_t wv[NW];
+        float part = 0.f;
+        const __nv_bfloat16 *xrow = XS + (size_t)crow * XSTR;
+        if (half == 0) a_words<LK, 0>(xrow, L, m < M, wv, part);
+        else a_words<LK, 1>(xrow, L, m < M, wv, part);
+        s_d[half][crow] = part;
+        named_sync(1, 32 * TC_EPI_WARPS);
+        xn2 = __fadd_rn(s_d[0][crow], s_d[1][crow]);
+        if (half == 1) {
+            __nv_bfloat16 h, mi, lo;
+            split3(xn2, h, mi, lo);
+            const uint32_t one = __bfloat16_as_ushort(__float2bfloat16_rn(1.f));
+            constexpr int w0 = (LK - KA / 2) / 2;                // first norm-block word
+            wv[w0] = one | (one << 16);
+            wv[w0 + 1] = one | ((uint32_t)__bfloat16_as_ushort(h) << 16);
+            wv[w0 + 2] = (uint32_t)__bfloat16_as_ushort(mi) | ((uint32_t)__bfloat16_as_ushort(lo) << 16);
+        }
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        tmem_st_words<NW>(tmem + lane_base + (uint32_t)(TC_A_COL + acc * (KA / 2) + half * NW), wv);
+        tmem_st_wait();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
 
     if (warp == 0) {
         // ---------------- producer
@@ -449,43 +522,52 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
         }
     } else if (warp == 1) {
-        // ---------------- MMA issuer
-        const uint64_t adesc0 = smem_desc(smem_addr(A), 128u, sbo_a);
+        // ---------------- MMA issuer: job j = 2 t + a (tile t, accumulator a)
+        // goes to slot j % 3 of the ring.  The issue of an MMA returns about
+        // when the tensor pipe takes it, so the issuer's own instructions sit
+        // on the tensor pipe's critical path: the whole warp runs the loop
+        // (warp-uniform addresses; waits suspend instead of spinning) and one
+        // elected lane issues each MMA and commit.
         const uint64_t bdesc0 = smem_desc(smem_addr(Bs), 128u, sbo_b);
-        if (lane == 0) {
-            for (int t = 0; t < ntiles; ++t) {
-                const int s = t % TC_STAGES, b = t & 1;
-                if (!mbar_wait_bounded_sleep(&full[s], (uint32_t)(t / TC_STAGES) & 1u)) {
-                    s_abort = 1;
-                    break;
-                }
-                if (t >= 2 && !mbar_wait_bounded_sleep(&tempty[b], (uint32_t)((t >> 1) - 1) & 1u)) {
-                    s_abort = 1;
-                    break;
-                }
-                if (s_abort) break;
-                tc_fence_after();
-                // Descriptors differ only in their start-address field: add the
-                // byte offset / 16 to base descriptors (addresses < 256 KB, no carry).
-                const uint64_t bst = bdesc0 + ((uint64_t)(s * stage_bytes) >> 4);
-#pragma unroll
-                for (int a = 0; a < TC_NACC; ++a) {
-                    const uint32_t d = tmem + (uint32_t)((b * TC_NACC + a) * TC_NT);
-                    const uint64_t ab = adesc0 + (uint64_t)((a * a_bytes) >> 4);
-#pragma unroll
-                    for (int seg = 0; seg < 3; ++seg)
-#pragma unroll
-                        for (int kk = 0; kk < LK / 16; ++kk)
-                            mma_bf16(d, ab + (uint64_t)(kk * 16), bst + (uint64_t)(seg * LK + kk * 16),
-                                     (seg | kk) ? 1u : 0u);
-                    mma_bf16(d, ab + (uint64_t)LK, bst + (uint64_t)(3 * LK), 1u);
-                }
-                mma_commit(&empty[s]);
-                mma_commit(&tfull[b]);
-                s_mma_last = t;
+        bool ok = true;
+        for (int t = 0; t < ntiles && ok; ++t) {
+            const int s = t % TC_STAGES;
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded_sleep(&full[s], (uint32_t)(t / TC_STAGES) & 1u))) {
+                ok = false;
+                break;
             }
+            // Descriptors differ only in their start-address field: add the
+            // byte offset / 16 to the base descriptor (addresses < 256 KB, no carry).
+            const uint64_t bst = bdesc0 + ((uint64_t)(s * stage_bytes) >> 4);
+#pragma unroll
+            for (int a = 0; a < TC_NACC; ++a) {
+                const int j = 2 * t + a, slot = j % TC_SLOTS;
+                if ((j >= TC_SLOTS &&
+                     !__all_sync(0xffffffffu, mbar_wait_bounded_sleep(&tempty[slot], (uint32_t)((j / TC_SLOTS) - 1) & 1u))) ||
+                    s_abort) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(slot * TC_NT);
+                const uint32_t at = tmem + (uint32_t)(TC_A_COL + a * (KA / 2));
+#pragma unroll
+                for (int seg = 0; seg < 3; ++seg)
+#pragma unroll
+                    for (int kk = 0; kk < LK / 16; ++kk)
+                        mma_bf16_ta_elect(d, at + (uint32_t)(8 * kk), bst + (uint64_t)(seg * LK + kk * 16),
+                                          (seg | kk) ? 1u : 0u);
+                mma_bf16_ta_elect(d, at + (uint32_t)(LK / 2), bst + (uint64_t)(3 * LK), 1u);
+                mma_commit_elect(&tfull[slot]);
+                if (lane == 0) s_mma_job = j;
+            }
+            if (!ok) break;
+            mma_commit_elect(&empty[s]);
+            if (lane == 0) s_mma_tile = t;
         }
-    } else {
+        if (!ok && lane == 0) s_abort = 1;
+        __syncwarp();
+    } else if (epi) {
         // ---------------- epilogue: one (row, column half) per thread
         constexpr int NCH = 4;                       // independent min-chains
         constexpr int JMASK = (1 << TC_JBITS) - 1;
@@ -499,21 +581,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
         for (int t = 0; t < ntiles; ++t) {
-            const int b = t & 1;
-            if (!mbar_wait_bounded(&tfull[b], (uint32_t)(t >> 1) & 1u)) {
+            const int j = 2 * t + acc, slot = j % TC_SLOTS;
+            if (!mbar_wait_bounded_sleep(&tfull[slot], (uint32_t)(j / TC_SLOTS) & 1u)) {
                 s_abort = 1;
                 break;
             }
             tc_fence_after();
             float v[TC_HALF];
-            const uint32_t col = (uint32_t)((b * TC_NACC + acc) * TC_NT + half * TC_HALF);
+            const uint32_t col = (uint32_t)(slot * TC_NT + half * TC_HALF);
             tmem_ld32(tmem + lane_base + col, v);
             tmem_ld32(tmem + lane_base + col + 32u, v + 32);
             tmem_ld_wait();
             // the values are in registers: hand the accumulator back to the MMA
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[b]);
+            if (lane == 0) mbar_arrive(&tempty[slot]);
             float s1[NCH];
 #pragma unroll
             for (int q = 0; q < NCH; ++q) s1[q] = c1[q];
@@ -536,7 +618,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         // The two halves of a row exchange their top-2 and merge them in the
         // same fixed order, so both threads hold the same result.
-        const int crow = 128 * acc + rr;
         s_v1[half][crow] = V1;
         s_v2[half][crow] = V2;
         s_i1[half][crow] = i1;
@@ -668,10 +749,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // Stop: wait (bounded) for the bulk copies nobody consumed and for the
         // last committed MMAs, then free TMEM below.
         if (tid == 0) {
-            for (int t = s_mma_last + 1; t <= s_prod_last; ++t)
+            for (int t = s_mma_tile + 1; t <= s_prod_last; ++t)
                 (void)mbar_wait_bounded(&full[t % TC_STAGES], (uint32_t)(t / TC_STAGES) & 1u);
-            if (s_mma_last >= 0)
-                (void)mbar_wait_bounded(&tfull[s_mma_last & 1], (uint32_t)(s_mma_last >> 1) & 1u);
+            if (s_mma_job >= 0)
+                (void)mbar_wait_bounded(&tfull[s_mma_job % TC_SLOTS], (uint32_t)(s_mma_job / TC_SLOTS) & 1u);
             flag_error(st, ERR_TIMEOUT);
         }
         __syncthreads();
@@ -711,7 +792,7 @@ static void launch_tc(const float *X, int64_t M, int L, const void *Bp, const fl
                       const int32_t *n_dev, int n_host, const float *mu, const float *C, DevState *st,
                       int32_t *assign, float *e, int32_t *flags, cudaStream_t s)
 {
-    const size_t need = (size_t)TC_NACC * 128 * (LK + 16) * 2 + (size_t)TC_STAGES * TC_NT * (3 * LK + 16) * 2;
+    const size_t need = (size_t)TC_ROWS * (LK + 8) * 2 + (size_t)TC_STAGES * TC_NT * (3 * LK + 16) * 2;
     // at least 120 KB so that a single CTA (and its 512 TMEM columns) owns the SM
     const size_t smem = need > 120 * 1024 ? need : 120 * 1024;
     cudaFuncSetAttribute(k_assign_tc<LK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
