@@ -117,8 +117,9 @@ __device__ __forceinline__ void body_prep(const float *__restrict__ C, int N, in
         if (lane == 0) sqs[j] = sq;
     }
     __syncthreads();
-    if (tid < PREP_TILE) {
+    if (tid < PREP_TILE) {   // warp 0: one codevector per lane
         const int n = n0 + tid;
+        uint32_t cbits = 0u;
         float *blk = Cp + (size_t)(n / BN) * (Lp + 1) * BN;
         if (n < N) {
             const double sq = sqs[tid];
@@ -126,11 +127,14 @@ __device__ __forceinline__ void body_prep(const float *__restrict__ C, int N, in
             const float kf = __double2float_ru(k);
             blk[n % BN] = __double2float_rn(sq - (double)kf);
             kn[n] = kf;
-            atomicMax(&st->cmax_bits, __float_as_uint(__double2float_ru(sqrt(sq))));
+            cbits = __float_as_uint(__fsqrt_ru(__double2float_ru(sq)));   // >= ||c~_n||
         } else if (n < npad) {
             blk[n % BN] = INFINITY;
             kn[n] = 0.f;
         }
+        // max ||c~_n|| of the tile (bits of non-negative floats order as integers): one atomic per CTA
+        cbits = __reduce_max_sync(0xffffffffu, cbits);
+        if (tid == 0 && cbits) atomicMax(&st->cmax_bits, cbits);
     }
     for (int i = tid; i < Lp * PREP_TILE; i += 256) {
         const int l = i / PREP_TILE, j = i % PREP_TILE;
@@ -620,6 +624,213 @@ __global__ void __launch_bounds__(EX_THREADS)
         if (!exact_group(X, L, Lp, CT, N, st, flags, nflag, assign, e, g, cbuf, sh, uses)) return;
 }
 
+// Exact re-scoring with the codebook split across CTAs.  A work item is
+// (group of XS_R flagged rows, slice of the codebook chunks); the number of
+// slices is chosen on the device from the flagged count so that about
+// XS_ITEMS items exist (few flagged rows would otherwise leave most SMs idle,
+// and every CTA would stream the whole codebook).  Thread t scores
+// codevector t % EX_SW of each chunk against rows 16 (t / EX_SW) .. + 15,
+// d = sum_l (x_l - c_l)^2 in index order as above.  With one slice the group
+// is finished in place; with more, each item writes its per-row (d, index)
+// minima and the last item of the group (atomic count) merges them in slice
+// order, so ties keep the lowest index and the result does not depend on
+// which CTA finishes last.
+constexpr int XS_R = 32;
+constexpr int XS_HALF = XS_R / 2;
+constexpr int XS_ITEMS = 2 * 152;   // two resident CTAs per SM: one wave
+
+struct ExactSplitSmem {
+    float xs[LMAX][XS_R];
+    uint64_t bar[2];
+    int abort, last;
+    float rb[EX_THREADS / 32][XS_HALF];
+    int ri[EX_THREADS / 32][XS_HALF];
+    float rowb[XS_R];
+    int rowi[XS_R];
+};
+
+__global__ void __launch_bounds__(EX_THREADS)
+    k_assign_exact_split(const float *__restrict__ X, int L, int Lp, const float *__restrict__ CT,
+                         const int32_t *n_dev, int n_host, DevState *st, const int32_t *__restrict__ flags,
+                         int32_t *__restrict__ assign, float *__restrict__ e, float *__restrict__ part_d,
+                         int32_t *__restrict__ part_i, int32_t *__restrict__ cnt)
+{
+    if (st->finished) return;
+    const int nflag = st->nflag;
+    const int groups = (nflag + XS_R - 1) / XS_R;
+    if (groups == 0) return;
+    const int N = cur_n(n_dev, n_host);
+    const int nchunk = (N + EX_SW - 1) / EX_SW;
+    int nsplit = XS_ITEMS / groups;
+    nsplit = nsplit < 1 ? 1 : (nsplit > nchunk ? nchunk : nsplit);
+    const int cps = (nchunk + nsplit - 1) / nsplit;
+    nsplit = (nchunk + cps - 1) / cps;
+    const int items = groups * nsplit;
+    if ((int)blockIdx.x >= items) return;
+
+    extern __shared__ __align__(128) float cbuf[];   // [2][Lp][EX_SW]
+    __shared__ __align__(16) ExactSplitSmem sh;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int j = tid % EX_SW, h = tid / EX_SW;
+    const uint32_t chunk_floats = (uint32_t)Lp * EX_SW;
+    const uint32_t chunk_bytes = chunk_floats * 4u;
+    if (tid == 0) {
+        mbar_init(&sh.bar[0], 1);
+        mbar_init(&sh.bar[1], 1);
+        fence_mbar_init();
+        sh.abort = 0;
+    }
+    __syncthreads();
+    uint32_t uses[2] = {0u, 0u};
+    for (int w = blockIdx.x; w < items; w += gridDim.x) {
+        const int g = w / nsplit, sp = w % nsplit;
+        const int k0 = sp * cps, k1 = min(nchunk, k0 + cps);
+        const int nr = min(XS_R, nflag - g * XS_R);
+        if (tid == 0)   // the first two chunks are in flight while the rows are staged
+            for (int k = k0; k < k0 + 2 && k < k1; ++k) {
+                mbar_expect_tx(&sh.bar[(k - k0) & 1], chunk_bytes);
+                bulk_load(cbuf + ((k - k0) & 1) * chunk_floats, CT + (size_t)k * chunk_floats, chunk_bytes,
+                          &sh.bar[(k - k0) & 1]);
+            }
+        for (int r = warp; r < XS_R; r += EX_THREADS / 32) {   // a warp per row: coalesced
+            const float *xr = r < nr ? X + (int64_t)flags[g * XS_R + r] * L : nullptr;
+            for (int l = lane; l < L; l += 32) sh.xs[l][r] = xr ? xr[l] : 0.f;
+        }
+        __syncthreads();
+        float best[XS_HALF];
+        int bi[XS_HALF];
+#pragma unroll
+        for (int q = 0; q < XS_HALF; ++q) {
+            best[q] = INFINITY;
+            bi[q] = 0x7fffffff;
+        }
+        int k_stop = k1;
+        for (int k = k0; k < k1; ++k) {
+            const int b = (k - k0) & 1;
+            const bool ok = mbar_wait_bounded(&sh.bar[b], uses[b] & 1u);
+            uses[b] += 1u;
+            if (!ok) sh.abort = 1;
+            const float *cb = cbuf + b * chunk_floats;
+            const int n = k * EX_SW + j;
+            if (ok && n < N) {
+                float d2[XS_HALF];
+#pragma unroll
+                for (int q = 0; q < XS_HALF; ++q) d2[q] = 0.f;
+#pragma unroll 2
+                for (int l = 0; l < L; ++l) {
+                    const float c = cb[l * EX_SW + j];
+#pragma unroll
+                    for (int q4 = 0; q4 < XS_HALF / 4; ++q4) {
+                        const float4 x4 = lds4(&sh.xs[l][h * XS_HALF + 4 * q4]);
+                        float d = x4.x - c;
+                        d2[4 * q4] = fmaf(d, d, d2[4 * q4]);
+                        d = x4.y - c;
+                        d2[4 * q4 + 1] = fmaf(d, d, d2[4 * q4 + 1]);
+                        d = x4.z - c;
+                        d2[4 * q4 + 2] = fmaf(d, d, d2[4 * q4 + 2]);
+                        d = x4.w - c;
+                        d2[4 * q4 + 3] = fmaf(d, d, d2[4 * q4 + 3]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < XS_HALF; ++q)
+                    if (d2[q] < best[q]) {
+                        best[q] = d2[q];
+                        bi[q] = n;
+                    }
+            }
+            __syncthreads();
+            if (sh.abort) {
+                k_stop = k;
+                break;
+            }
+            if (tid == 0 && k + 2 < k1) {
+                mbar_expect_tx(&sh.bar[b], chunk_bytes);
+                bulk_load(cbuf + b * chunk_floats, CT + (size_t)(k + 2) * chunk_floats, chunk_bytes,
+                          &sh.bar[b]);
+            }
+        }
+        if (k_stop < k1) {
+            if (tid == 0) {
+                for (int kk = k_stop + 1; kk < k1 && kk < k_stop + 2; ++kk)
+                    (void)mbar_wait_bounded(&sh.bar[(kk - k0) & 1], uses[(kk - k0) & 1] & 1u);
+                flag_error(st, ERR_TIMEOUT);
+            }
+            return;
+        }
+        // per-row minimum: shuffles inside a warp, then the 4 warps of a half in order
+#pragma unroll
+        for (int q = 0; q < XS_HALF; ++q) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best[q], o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi[q], o);
+                if (ob < best[q] || (ob == best[q] && oi < bi[q])) {
+                    best[q] = ob;
+                    bi[q] = oi;
+                }
+            }
+            if (lane == 0) {
+                sh.rb[warp][q] = best[q];
+                sh.ri[warp][q] = bi[q];
+            }
+        }
+        __syncthreads();
+        if (tid < XS_R) {
+            const int hh = tid / XS_HALF, q = tid % XS_HALF, w0 = hh * (EX_SW / 32);
+            float bb = sh.rb[w0][q];
+            int ii = sh.ri[w0][q];
+            for (int ww = w0 + 1; ww < w0 + EX_SW / 32; ++ww)
+                if (sh.rb[ww][q] < bb || (sh.rb[ww][q] == bb && sh.ri[ww][q] < ii)) {
+                    bb = sh.rb[ww][q];
+                    ii = sh.ri[ww][q];
+                }
+            sh.rowb[tid] = bb;
+            sh.rowi[tid] = ii;
+            if (nsplit > 1) {
+                part_d[(size_t)w * XS_R + tid] = bb;
+                part_i[(size_t)w * XS_R + tid] = ii;
+            }
+        }
+        bool fin = nsplit == 1;
+        if (nsplit > 1) {
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) sh.last = atomicAdd(&cnt[g], 1) == nsplit - 1;
+            __syncthreads();
+            fin = sh.last != 0;
+            if (fin) {
+                __threadfence();
+                if (tid < nr) {
+                    float bb = __ldcg(part_d + (size_t)(g * nsplit) * XS_R + tid);
+                    int ii = __ldcg(part_i + (size_t)(g * nsplit) * XS_R + tid);
+                    for (int q = 1; q < nsplit; ++q) {
+                        const float ob = __ldcg(part_d + (size_t)(g * nsplit + q) * XS_R + tid);
+                        const int oi = __ldcg(part_i + (size_t)(g * nsplit + q) * XS_R + tid);
+                        if (ob < bb || (ob == bb && oi < ii)) {
+                            bb = ob;
+                            ii = oi;
+                        }
+                    }
+                    sh.rowb[tid] = bb;
+                    sh.rowi[tid] = ii;
+                }
+                if (tid == 0) cnt[g] = 0;
+            }
+        }
+        if (fin && tid < nr) {
+            const float bb = sh.rowb[tid];
+            const int ii = sh.rowi[tid];
+            const int row = flags[g * XS_R + tid];
+            const bool valid = ii >= 0 && ii < N;
+            if (!valid) flag_error(st, ERR_NONFINITE);   // only NaN rows compare false everywhere
+            assign[row] = valid ? ii : 0;
+            e[row] = valid ? bb : 0.f;
+        }
+        __syncthreads();
+    }
+}
+
 // Batched problems: the flagged groups of all problems form one work list
 // (problem order, then group order); a persistent grid strides through it.
 __global__ void __launch_bounds__(EX_THREADS)
@@ -723,6 +934,23 @@ void launch_exact(const float *X, int L, int Lp, const float *CT, const int32_t 
     if (blocks < 1) blocks = 1;
     k_assign_exact<<<(unsigned)blocks, EX_THREADS, smem, s>>>(X, L, Lp, CT, n_dev, n_host, st, flags,
                                                              assign, e);
+}
+
+int exact_split_items() { return XS_ITEMS; }
+int exact_split_rows() { return XS_R; }
+
+void launch_exact_split(const float *X, int L, int Lp, const float *CT, const int32_t *n_dev, int n_host,
+                        DevState *st, const int32_t *flags, int32_t *assign, float *e, float *part_d,
+                        int32_t *part_i, int32_t *cnt, int64_t M, cudaStream_t s)
+{
+    const size_t smem = (size_t)2 * Lp * EX_SW * sizeof(float);
+    cudaFuncSetAttribute(k_assign_exact_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int64_t blocks = (M + XS_R - 1) / XS_R;
+    if (blocks < XS_ITEMS) blocks = blocks * 16 < XS_ITEMS ? blocks * 16 : XS_ITEMS;
+    if (blocks > XS_ITEMS) blocks = XS_ITEMS;
+    if (blocks < 1) blocks = 1;
+    k_assign_exact_split<<<(unsigned)blocks, EX_THREADS, smem, s>>>(X, L, Lp, CT, n_dev, n_host, st, flags,
+                                                                   assign, e, part_d, part_i, cnt);
 }
 
 void launch_b_prep(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int L, int Lp,

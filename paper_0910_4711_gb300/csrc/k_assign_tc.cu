@@ -285,67 +285,128 @@ __device__ __forceinline__ bool split3(float v, __nv_bfloat16 &h, __nv_bfloat16 
 // p_mid, [2Lk,3Lk) p_lo of c' = -2 (c - mu), [3Lk, 3Lk+3) the pieces of s0,
 // zeros elsewhere; padding codevectors have s0 = 2^100.  Also k'_n, the
 // chunk-major original codebook for the exact fallback, max ||c~||.
+constexpr int PT_N = 32;   // codevectors per preparation CTA
+
+template <int LK>
 __global__ void __launch_bounds__(256)
-    k_prep_tc(const float *__restrict__ C, const int32_t *n_dev, int n_host, int L, int Lk, int Lp,
+    k_prep_tc(const float *__restrict__ C, const int32_t *n_dev, int n_host, int L, int Lp,
               const float *__restrict__ mu, __nv_bfloat16 *__restrict__ Bp, float *__restrict__ kn,
               float *__restrict__ CT, DevState *st)
 {
     if (st->finished) return;
     const int N = cur_n(n_dev, n_host);
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    const int ntile_pad = round_up(N, BN);   // CT chunks are BN wide; tiles TC_NT
-    if (n >= ntile_pad) return;
-    const int KB = 3 * Lk + 16;
-    const uint32_t sbo = (uint32_t)(KB / 8) * 128u;
-    uint8_t *tile = reinterpret_cast<uint8_t *>(Bp) + (size_t)(n / TC_NT) * TC_NT * KB * 2;
-    const int j = n % TC_NT;
-    auto put = [&](int k, __nv_bfloat16 v) {
-        *reinterpret_cast<__nv_bfloat16 *>(tile + core_off(j, k, sbo)) = v;
-    };
-    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
-    if (n < N) {
+    const int n0 = blockIdx.x * PT_N;
+    if (n0 >= round_up(N, BN)) return;   // CT chunks are BN wide; tiles TC_NT
+    constexpr int KB = 3 * LK + 16;
+    constexpr uint32_t sbo = (uint32_t)(KB / 8) * 128u;
+    __shared__ float cs[PT_N][LK + 1];   // codevectors as given (0 past L / N)
+    __shared__ float ct[PT_N][LK + 1];   // centred c~ = c - mu
+    __shared__ float s0s[PT_N];
+    __shared__ double sqs[PT_N];
+    __shared__ int s_bad, s_inexact;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        s_bad = 0;
+        s_inexact = 0;
+    }
+    __syncthreads();
+    // this CTA's block of C is contiguous: read it coalesced
+    for (int i = tid; i < PT_N * L; i += blockDim.x) {
+        const int r = i / L, l = i - r * L, n = n0 + r;
+        const float c = n < N ? C[(size_t)n0 * L + i] : 0.f;
+        if (!isfinite(c)) s_bad = 1;
+        cs[r][l] = c;
+        ct[r][l] = n < N ? c - mu[l] : 0.f;
+    }
+    for (int i = tid; i < PT_N * (LK - L); i += blockDim.x) {
+        const int r = i / (LK - L), l = L + i % (LK - L);
+        cs[r][l] = 0.f;
+        ct[r][l] = 0.f;
+    }
+    __syncthreads();
+    // ||c~||^2 in FP64: warp w sums codevectors w, w + 8, ... over its lanes
+    // (fixed shuffle tree), then k'_n and the chain start s0
+    for (int r = warp; r < PT_N; r += blockDim.x / 32) {
         double sq = 0.0;
-        bool finite = true, exact = true;
-        for (int l = 0; l < Lk; ++l) {
-            float cp = 0.f;
-            if (l < L) {
-                const float c = C[(size_t)n * L + l];
-                finite = finite && isfinite(c);
-                const float ct = c - mu[l];
-                sq += (double)ct * (double)ct;
-                cp = -2.0f * ct;
-            }
-            __nv_bfloat16 h, m, lo;
-            exact = split3(cp, h, m, lo) && exact;
-            put(l, h);
-            put(Lk + l, m);
-            put(2 * Lk + l, lo);
+        for (int l = lane; l < L; l += 32) sq = fma((double)ct[r][l], (double)ct[r][l], sq);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (lane == 0) sqs[r] = sq;
+    }
+    __syncthreads();
+    if (tid < PT_N) {   // warp 0: one codevector per lane
+        const int n = n0 + tid;
+        uint32_t cbits = 0u;
+        if (n < N) {
+            const double sq = sqs[tid];
+            const double k = (2.0 * tc_tau(KB) + 1.1920928955078125e-7) * sq;   // 2 tau + 2^-23
+            const float kf = __double2float_ru(k);
+            s0s[tid] = __double2float_rn(sq - (double)kf);
+            kn[n] = kf;
+            cbits = __float_as_uint(__fsqrt_ru(__double2float_ru(sq)));   // >= ||c~_n||
+        } else {
+            s0s[tid] = 1.2676506002282294e30f;   // padding: 2^100, finite so index packing cannot make a NaN
+            kn[n] = 0.f;
         }
-        for (int l = 0; l < Lp; ++l)
-            CT[((size_t)(n / EXACT_SW) * Lp + l) * EXACT_SW + n % EXACT_SW] =
-                l < L ? C[(size_t)n * L + l] : 0.f;
-        if (!finite) flag_error(st, ERR_NONFINITE);
-        const double k = (2.0 * tc_tau(KB) + 1.1920928955078125e-7) * sq;   // 2 tau + 2^-23
-        const float kf = __double2float_ru(k);
-        const float s0 = __double2float_rn(sq - (double)kf);
-        __nv_bfloat16 h, m, lo;
-        exact = split3(s0, h, m, lo) && exact;
-        put(3 * Lk, h);
-        put(3 * Lk + 1, m);
-        put(3 * Lk + 2, lo);
-        const __nv_bfloat16 one = __float2bfloat16_rn(1.f);
-        for (int q = 3; q < 6; ++q) put(3 * Lk + q, one);     // x X2 pieces of the row
-        for (int q = 6; q < 16; ++q) put(3 * Lk + q, zero);
-        kn[n] = kf;
-        atomicMax(&st->cmax_bits, __float_as_uint(__double2float_ru(sqrt(sq))));
-        if (!exact) atomicOr(&st->tc_inexact, 1);
-    } else {
-        for (int k = 0; k < KB; ++k) put(k, zero);
-        put(3 * Lk, __float2bfloat16_rn(1.2676506002282294e30f));   // padding: 2^100, finite so
-                                                                     // index packing cannot make a NaN
-        kn[n] = 0.f;
-        for (int l = 0; l < Lp; ++l)
-            CT[((size_t)(n / EXACT_SW) * Lp + l) * EXACT_SW + n % EXACT_SW] = 0.f;
+        // max ||c~_n|| of the block (bits of non-negative floats order as integers): one atomic per CTA
+        cbits = __reduce_max_sync(0xffffffffu, cbits);
+        if (tid == 0 && cbits) atomicMax(&st->cmax_bits, cbits);
+    }
+    __syncthreads();
+    // B rows: K in [0, LK) p_hi of c' = -2 c~, [LK, 2LK) p_mid, [2LK, 3LK) p_lo,
+    // then the s0 pieces, three ones (x the row's X2 pieces), zeros.  A unit is
+    // (codevector, 8 dims): each value is split once and its three pieces go
+    // out as three 16-byte core-matrix rows.
+    uint8_t *tile = reinterpret_cast<uint8_t *>(Bp) + (size_t)(n0 / TC_NT) * TC_NT * KB * 2;
+    const int rt = n0 % TC_NT;
+    constexpr int G8 = LK / 8;
+    bool inexact = false;
+    for (int u = tid; u < PT_N * G8; u += blockDim.x) {
+        const int r = u / G8, l0 = 8 * (u - r * G8);
+        uint32_t w[3][4];
+#pragma unroll
+        for (int e2 = 0; e2 < 4; ++e2) {
+            __nv_bfloat16 h0, m0, o0, h1, m1, o1;
+            inexact |= !split3(-2.0f * ct[r][l0 + 2 * e2], h0, m0, o0);
+            inexact |= !split3(-2.0f * ct[r][l0 + 2 * e2 + 1], h1, m1, o1);
+            w[0][e2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            w[1][e2] = (uint32_t)__bfloat16_as_ushort(m0) | ((uint32_t)__bfloat16_as_ushort(m1) << 16);
+            w[2][e2] = (uint32_t)__bfloat16_as_ushort(o0) | ((uint32_t)__bfloat16_as_ushort(o1) << 16);
+        }
+#pragma unroll
+        for (int pc = 0; pc < 3; ++pc)
+            *reinterpret_cast<uint4 *>(tile + core_off(rt + r, pc * LK + l0, sbo)) =
+                make_uint4(w[pc][0], w[pc][1], w[pc][2], w[pc][3]);
+    }
+    if (tid < PT_N) {   // the norm block of each codevector: two 16-byte rows
+        const int r = tid;
+        const bool real = n0 + r < N;
+        __nv_bfloat16 h, m, o;
+        const bool ex = split3(s0s[r], h, m, o);
+        if (real) inexact |= !ex;
+        const uint32_t one = __bfloat16_as_ushort(__float2bfloat16_rn(1.f));
+        uint4 nb;
+        if (real) {
+            nb.x = (uint32_t)__bfloat16_as_ushort(h) | ((uint32_t)__bfloat16_as_ushort(m) << 16);
+            nb.y = (uint32_t)__bfloat16_as_ushort(o) | (one << 16);
+            nb.z = one | (one << 16);
+            nb.w = 0u;
+        } else {
+            nb = make_uint4((uint32_t)__bfloat16_as_ushort(h), 0u, 0u, 0u);
+        }
+        *reinterpret_cast<uint4 *>(tile + core_off(rt + r, 3 * LK, sbo)) = nb;
+        *reinterpret_cast<uint4 *>(tile + core_off(rt + r, 3 * LK + 8, sbo)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (inexact) s_inexact = 1;
+    // FP32 codebook for the exact fallback, chunk-major (coalesced along n)
+    for (int i = tid; i < PT_N * Lp; i += blockDim.x) {
+        const int l = i / PT_N, r = i - l * PT_N, n = n0 + r;
+        CT[((size_t)(n / EXACT_SW) * Lp + l) * EXACT_SW + n % EXACT_SW] = l < L ? cs[r][l] : 0.f;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (s_bad) flag_error(st, ERR_NONFINITE);
+        if (s_inexact) atomicOr(&st->tc_inexact, 1);
     }
 }
 
@@ -781,10 +842,15 @@ void launch_round_mu(float *mu, int L, cudaStream_t s) { k_round_mu<<<1, 128, 0,
 void launch_prep_tc(const float *C, int N_alloc, const int32_t *n_dev, int n_host, int L,
                     const float *mu, void *Bp, float *kn, float *CT, DevState *st, cudaStream_t s)
 {
-    const int total = round_up(N_alloc, BN);
-    k_prep_tc<<<(total + 255) / 256, 256, 0, s>>>(C, n_dev, n_host, L, round_up(L, 16),
-                                                  round_up(L, 4), mu,
-                                                  static_cast<__nv_bfloat16 *>(Bp), kn, CT, st);
+    const int blocks = round_up(N_alloc, BN) / PT_N;
+    __nv_bfloat16 *B = static_cast<__nv_bfloat16 *>(Bp);
+    const int Lp = round_up(L, 4);
+    switch (round_up(L, 16)) {
+    case 16: k_prep_tc<16><<<blocks, 256, 0, s>>>(C, n_dev, n_host, L, Lp, mu, B, kn, CT, st); break;
+    case 32: k_prep_tc<32><<<blocks, 256, 0, s>>>(C, n_dev, n_host, L, Lp, mu, B, kn, CT, st); break;
+    case 48: k_prep_tc<48><<<blocks, 256, 0, s>>>(C, n_dev, n_host, L, Lp, mu, B, kn, CT, st); break;
+    default: k_prep_tc<64><<<blocks, 256, 0, s>>>(C, n_dev, n_host, L, Lp, mu, B, kn, CT, st); break;
+    }
 }
 
 template <int LK>

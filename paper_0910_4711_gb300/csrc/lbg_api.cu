@@ -30,7 +30,7 @@ struct Plan {
     int L = 0, Lp = 0, N = 0, NP = 0, CH = 0, G = 0, max_rec = 0;
     bool tc = false;   // tensor-core (BF16) allocation
     size_t state, rec, Cp, kn, CT, mu, Ccur, Calt, assign, e, flags, table, dpart, counts, off, perm,
-        pieces, mpart, Xs, Cin, Cout, Xhat, Bp;
+        pieces, mpart, Xs, Cin, Cout, Xhat, Bp, xpart_d, xpart_i, xcnt;
     size_t total = 0;
     size_t take(size_t bytes)
     {
@@ -93,6 +93,9 @@ Plan make_plan(int64_t M, int L, int N, int max_rec, bool host_X, bool need_assi
     p.Cout = host_C ? p.take(sizeof(float) * (size_t)N * L) : 0;
     p.Xhat = host_Xhat ? p.take(sizeof(float) * (size_t)M * L) : 0;
     p.Bp = tc ? p.take(tc_codebook_bytes(p.NP, L)) : 0;
+    p.xpart_d = p.take(sizeof(float) * (size_t)exact_split_items() * exact_split_rows());
+    p.xpart_i = p.take(sizeof(int32_t) * (size_t)exact_split_items() * exact_split_rows());
+    p.xcnt = p.take(sizeof(int32_t) * (size_t)exact_split_items());
     return p;
 }
 
@@ -242,8 +245,10 @@ void run_assign(const Call &c, const Plan &p, const float *X, const float *C, co
 void run_exact(const Call &c, const Plan &p, const float *X, const int32_t *n_dev, int n_host,
                DevState *st, int32_t *assign)
 {
-    launch_exact(X, p.L, p.Lp, c.at<float>(p.CT), n_dev, n_host, st, c.at<int32_t>(p.flags), assign,
-                 c.at<float>(p.e), p.M, c.s);
+    cudaMemsetAsync(c.at<int32_t>(p.xcnt), 0, sizeof(int32_t) * (size_t)exact_split_items(), c.s);
+    launch_exact_split(X, p.L, p.Lp, c.at<float>(p.CT), n_dev, n_host, st, c.at<int32_t>(p.flags), assign,
+                       c.at<float>(p.e), c.at<float>(p.xpart_d), c.at<int32_t>(p.xpart_i),
+                       c.at<int32_t>(p.xcnt), p.M, c.s);
 }
 
 void run_update(const Call &c, const Plan &p, const float *X, const int32_t *n_dev, int n_host,
