@@ -564,7 +564,8 @@ def batched_leg(lbg, synth, torch):
     Ns = [n for _, _, n in spec]
     row_off = np.concatenate([[0], np.cumsum([p.shape[0] for p in parts])])
     X = torch.from_numpy(np.concatenate(parts)).cuda()
-    lbg.lbg_train_batched(X, row_off, Ns, max_passes=1)   # warm: workspace, graph capture
+    # warm: workspace, graph capture, and the tile autotuner's calibration of this bucket
+    tune = lbg.lbg_train_batched(X, row_off, Ns, max_passes=1).tune
     ts = []
     for _ in range(3):
         torch.cuda.synchronize()
@@ -585,7 +586,9 @@ def batched_leg(lbg, synth, torch):
     bt = statistics.median(ts)
     return {"workload": f"64 problems, sum M = {int(row_off[-1])}, L = 16, N in {{64..1024}}",
             "batched_s": bt, "sequential_s": seq, "speedup": seq / bt,
-            "max_passes": r.max_passes_run, "passes_per_s": r.max_passes_run / bt}
+            "max_passes": r.max_passes_run, "passes_per_s": r.max_passes_run / bt,
+            "assign_tile": {"chosen": {"tile_rows": r.tune["tile_rows"], "ctas_per_sm": r.tune["ctas_per_sm"]},
+                            "calibration": tune["candidates"]}}
 
 
 def large_leg(lbg, synth, torch):

@@ -94,6 +94,19 @@ typedef struct lbg_pass_record {
     double D;          /* total distortion of the pass */
 } lbg_pass_record;
 
+/* Tile choice of lbg_train_batched's persistent nearest-codevector launch and
+ * the calibration behind it (see lbg_opts.autotune). */
+typedef struct lbg_tune_report {
+    int32_t tile_rows;            /* training rows per work item: 64 or 128 */
+    int32_t ctas_per_sm;          /* resident CTAs per SM of the persistent grid */
+    int32_t from_cache;           /* 1: chosen by an earlier calibration of the same bucket */
+    int32_t n_candidates;         /* candidates timed by this call (0 if none ran) */
+    int32_t cand_tile_rows[8];
+    int32_t cand_ctas_per_sm[8];
+    float cand_ms[8];             /* device time of one batched assignment of all problems at
+                                     their final codebook sizes, per candidate (best of 2) */
+} lbg_tune_report;
+
 typedef struct lbg_opts {
     int32_t precision;          /* lbg_precision; default LBG_PREC_FP32 */
     int32_t max_passes;         /* per stage (lbg_train); <= 0 means 1000 */
@@ -112,9 +125,19 @@ typedef struct lbg_opts {
                                    in lbg_lloyd_step) */
     double delta_reseed;        /* offset for reseed_empty in lbg_lloyd_step (lbg_train uses
                                    its delta) */
+    int32_t autotune;           /* lbg_train_batched: 1 (default) picks the tile of the batched
+                                   nearest-codevector launch by timing the candidates (64 or 128
+                                   rows per work item x resident CTAs per SM) once per bucket
+                                   (L, largest N, total M) and device, then reuses the choice;
+                                   0: 128 rows, 2 CTAs per SM.  Results do not depend on it. */
+    int32_t tile_rows;          /* lbg_train_batched: force 64 or 128 rows (0: autotune) */
+    int32_t ctas_per_sm;        /* lbg_train_batched: force 1, 2 or 4 (0: autotune; 4 needs
+                                   64-row tiles) */
+    lbg_tune_report *tune_report; /* host out for lbg_train_batched, or NULL */
 } lbg_opts;
 
-/* Fill *opts with the defaults (FP32, 1000 passes, default stream, no trace). */
+/* Fill *opts with the defaults (FP32, 1000 passes, default stream, no trace,
+ * autotuned batched tiles). */
 void lbg_opts_init(lbg_opts *opts);
 
 /*

@@ -40,6 +40,21 @@ class PassRecord(ctypes.Structure):
                 ("n_exact", ctypes.c_int32), ("D", ctypes.c_double)]
 
 
+class TuneReport(ctypes.Structure):
+    _fields_ = [("tile_rows", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("from_cache", ctypes.c_int32), ("n_candidates", ctypes.c_int32),
+                ("cand_tile_rows", ctypes.c_int32 * 8), ("cand_ctas_per_sm", ctypes.c_int32 * 8),
+                ("cand_ms", ctypes.c_float * 8)]
+
+    def as_dict(self):
+        n = self.n_candidates
+        return {"tile_rows": self.tile_rows, "ctas_per_sm": self.ctas_per_sm,
+                "from_cache": bool(self.from_cache),
+                "candidates": [{"tile_rows": self.cand_tile_rows[k],
+                                "ctas_per_sm": self.cand_ctas_per_sm[k], "ms": self.cand_ms[k]}
+                               for k in range(n)]}
+
+
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_passes", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("records", ctypes.POINTER(PassRecord)),
@@ -47,7 +62,9 @@ class Opts(ctypes.Structure):
                 ("phase_ms", ctypes.POINTER(ctypes.c_float)),
                 ("n_exact", ctypes.POINTER(ctypes.c_int32)),
                 ("split_multiplicative", ctypes.c_int32), ("reseed_empty", ctypes.c_int32),
-                ("delta_reseed", ctypes.c_double)]
+                ("delta_reseed", ctypes.c_double), ("autotune", ctypes.c_int32),
+                ("tile_rows", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("tune_report", ctypes.POINTER(TuneReport))]
 
 
 _lock = threading.Lock()
@@ -308,6 +325,7 @@ class BatchedResult:
     code_off: list       # codebook s is C[code_off[s]:code_off[s+1]]
     max_passes_run: int
     phase_ms: dict | None
+    tune: dict | None = None   # tile of the batched assignment and its calibration
 
     def codebook(self, s):
         return self.C[self.code_off[s]:self.code_off[s + 1]]
@@ -315,9 +333,12 @@ class BatchedResult:
 
 def lbg_train_batched(X, row_off, N, delta: float = 0.01, theta: float = 1e-3,
                       max_passes: int = 1000, phase_ms: bool = False, stream=None,
-                      split_multiplicative: bool = False) -> BatchedResult:
+                      split_multiplicative: bool = False, autotune: bool = True,
+                      tile_rows: int = 0, ctas_per_sm: int = 0) -> BatchedResult:
     """S independent LBG designs at once (see lbg_train_batched in lbgvq.h).  X holds the rows
-    of all problems concatenated; row_off (S+1 offsets) and N (S sizes) are Python sequences."""
+    of all problems concatenated; row_off (S+1 offsets) and N (S sizes) are Python sequences.
+    The tile of the batched nearest-codevector launch is autotuned (or forced with tile_rows /
+    ctas_per_sm); the choice is in the result's ``tune``."""
     Xo, xp, _ = _prep(X, "f32", "X")
     L = int(X.shape[1])
     S = len(N)
@@ -336,9 +357,14 @@ def lbg_train_batched(X, row_off, N, delta: float = 0.01, theta: float = 1e-3,
     o, keep = _opts(_cuda_ref(X, C), max_passes, 0, phase_ms, stream, "fp32", split_multiplicative)
     nrec = ctypes.c_int32(0)
     o.n_records = ctypes.pointer(nrec)
+    o.autotune = int(bool(autotune))
+    o.tile_rows = int(tile_rows)
+    o.ctas_per_sm = int(ctas_per_sm)
+    rep = TuneReport()
+    o.tune_report = ctypes.pointer(rep)
     rc = _check(lib().lbg_train_batched(S, xp, ro.ctypes.data, L, Nn.ctypes.data, float(delta),
                                         float(theta), cp, ap, D.ctypes.data, ctypes.byref(o)))
-    return BatchedResult(rc, C, A, D.tolist(), code_off, nrec.value, _phases(keep))
+    return BatchedResult(rc, C, A, D.tolist(), code_off, nrec.value, _phases(keep), rep.as_dict())
 
 
 def release_workspace() -> None:

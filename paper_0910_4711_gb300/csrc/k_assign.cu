@@ -159,22 +159,27 @@ __global__ void __launch_bounds__(256)
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 
 // Shared state of an assignment CTA (static shared memory of the kernel).
-struct AssignSmem {
+template <int TBM>
+struct AssignSmemT {
     uint64_t bar[2];
     int abort;
-    float rec_v1[2][BM], rec_v2[2][BM];
-    int rec_id[2][BM];
+    float rec_v1[2][TBM], rec_v2[2][TBM];
+    int rec_id[2][TBM];
 };
+using AssignSmem = AssignSmemT<BM>;
 
-// Nearest codevector of the BM rows starting at m0 (see the file header).
+// Nearest codevector of the TBM rows starting at m0 (see the file header);
+// 2 TBM threads: warps are 4x8 thread grids of 8x8 (row, codevector) tiles,
+// TBM / 32 warp rows x 2 warp columns.
 // The two chunk barriers persist across calls of one CTA: use0/use1 count
 // their completed phases.  Returns false (after reporting) if a bulk copy
 // timed out; every thread of the CTA returns the same value.
-__device__ __forceinline__ bool assign_f32_tile(
+template <int TBM>
+__device__ __forceinline__ bool assign_f32_tile_t(
     const float *__restrict__ X, int64_t M, int L, int Lp, const float *__restrict__ Cp,
     const float *__restrict__ kn, int N, const float *__restrict__ mu, const float *__restrict__ C,
     DevState *st, int32_t *__restrict__ assign, float *__restrict__ e, int32_t *__restrict__ flags,
-    int64_t m0, float *smem, AssignSmem &sh, uint32_t &use0, uint32_t &use1)
+    int64_t m0, float *smem, AssignSmemT<TBM> &sh, uint32_t &use0, uint32_t &use1)
 {
     uint64_t *bar = sh.bar;
     auto &rec_v1 = sh.rec_v1;
@@ -184,8 +189,8 @@ __device__ __forceinline__ bool assign_f32_tile(
     const int nchunk = (N + BN - 1) / BN;
     const int chunk_floats = (Lp + 1) * BN;
     const uint32_t chunk_bytes = (uint32_t)chunk_floats * 4u;
-    float *xs = smem;                       // [Lp][BM]
-    float *cbuf0 = xs + Lp * BM;            // [Lp + 1][BN]
+    float *xs = smem;                       // [Lp][TBM]
+    float *cbuf0 = xs + Lp * TBM;            // [Lp + 1][BN]
     float *cbuf1 = cbuf0 + chunk_floats;
     const uint32_t base0 = use0, base1 = use1;
     auto parity = [&](int k) -> uint32_t { return ((k & 1 ? base1 : base0) + (uint32_t)(k >> 1)) & 1u; };
@@ -199,8 +204,8 @@ __device__ __forceinline__ bool assign_f32_tile(
 
     // Stage the centred x tile, transposed: xs[l][r] (zero outside M x L).
     bool bad = false;
-    for (int i = tid; i < BM * Lp; i += ASSIGN_THREADS) {
-        const int r = i % BM, l = i / BM;
+    for (int i = tid; i < TBM * Lp; i += (2 * TBM)) {
+        const int r = i % TBM, l = i / TBM;
         const int64_t m = m0 + r;
         float v = 0.f;
         if (m < M && l < L) {
@@ -208,7 +213,7 @@ __device__ __forceinline__ bool assign_f32_tile(
             bad = bad || !isfinite(xv);
             v = xv - mu[l];
         }
-        xs[l * BM + r] = v;
+        xs[l * TBM + r] = v;
     }
     if (bad) flag_error(st, ERR_NONFINITE);
 
@@ -250,7 +255,7 @@ __device__ __forceinline__ bool assign_f32_tile(
             }
 #pragma unroll 4
             for (int l = 1; l < Lp; ++l) {
-                const float4 xa = lds4(&xs[l * BM + rA]), xb = lds4(&xs[l * BM + rA + 16]);
+                const float4 xa = lds4(&xs[l * TBM + rA]), xb = lds4(&xs[l * TBM + rA + 16]);
                 const float4 ca = lds4(&cb[(1 + l) * BN + cA]), cc = lds4(&cb[(1 + l) * BN + cA + 32]);
                 const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
                 const float cv[8] = {ca.x, ca.y, ca.z, ca.w, cc.x, cc.y, cc.z, cc.w};
@@ -320,7 +325,7 @@ __device__ __forceinline__ bool assign_f32_tile(
     __syncthreads();
     const int r = tid;
     const int64_t m = m0 + r;
-    if (tid >= BM || m >= M) return true;
+    if (tid >= TBM || m >= M) return true;
     float V1, V2;
     int ID;
     {
@@ -355,7 +360,7 @@ __device__ __forceinline__ bool assign_f32_tile(
     for (int l = 1; l < Lp; ++l) {
         const float4 c0 = __ldg(reinterpret_cast<const float4 *>(blk + (1 + l) * BN + nl));
         const float4 c1 = __ldg(reinterpret_cast<const float4 *>(blk + (1 + l) * BN + nl + 32));
-        const float x = xs[l * BM + r];
+        const float x = xs[l * TBM + r];
         s[0] = fmaf(x, c0.x, s[0]);
         s[1] = fmaf(x, c0.y, s[1]);
         s[2] = fmaf(x, c0.z, s[2]);
@@ -373,7 +378,7 @@ __device__ __forceinline__ bool assign_f32_tile(
     bool certified = false;
     if (i1 >= 0 && i1 < N && V1 < INFINITY) {
         float xn2 = 0.f;
-        for (int l = 0; l < L; ++l) xn2 = fmaf(xs[l * BM + r], xs[l * BM + r], xn2);
+        for (int l = 0; l < L; ++l) xn2 = fmaf(xs[l * TBM + r], xs[l * TBM + r], xn2);
         const float xn2u = xn2 * SLOP;
         const float R = (float)(L + 2) * U32 * xn2u * SLOP;
         const float kc = kn[i1];
@@ -417,18 +422,19 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 2)
     }
     __syncthreads();
     uint32_t u0 = 0, u1 = 0;
-    (void)assign_f32_tile(X, M, L, Lp, Cp, kn, cur_n(n_dev, n_host), mu, C, st, assign, e, flags,
-                          (int64_t)blockIdx.x * BM, smem, sh, u0, u1);
+    (void)assign_f32_tile_t<BM>(X, M, L, Lp, Cp, kn, cur_n(n_dev, n_host), mu, C, st, assign, e, flags,
+                                (int64_t)blockIdx.x * BM, smem, sh, u0, u1);
 }
 
 // Batched problems: a persistent CTA takes (problem, row tile) work items from
 // a global counter until all are done; finished problems are skipped.
-__global__ void __launch_bounds__(ASSIGN_THREADS, 2)
+template <int TBM>
+__global__ void __launch_bounds__(2 * TBM, TBM == 128 ? 2 : 4)
     kb_assign_f32(const BatchSet *__restrict__ sets, int S, const int64_t *__restrict__ pre_tiles,
                   int64_t total, int L, int Lp, int *counter)
 {
     extern __shared__ __align__(128) float smem[];
-    __shared__ AssignSmem sh;
+    __shared__ AssignSmemT<TBM> sh;
     __shared__ int64_t s_item;
     if (threadIdx.x == 0) {
         mbar_init(&sh.bar[0], 1);
@@ -447,8 +453,8 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 2)
         const BatchSet &q = sets[s];
         if (!q.st->finished) {
             const int64_t tile = item - pre_tiles[s];
-            if (!assign_f32_tile(q.X, q.M, L, Lp, q.Cp, q.kn, q.st->n_cur, q.mu, q.C, q.st, q.assign,
-                                 q.e, q.flags, tile * BM, smem, sh, u0, u1))
+            if (!assign_f32_tile_t<TBM>(q.X, q.M, L, Lp, q.Cp, q.kn, q.st->n_cur, q.mu, q.C, q.st,
+                                        q.assign, q.e, q.flags, tile * TBM, smem, sh, u0, u1))
                 break;
         }
         __syncthreads();   // all reads of this item's shared data before the next item
@@ -960,17 +966,22 @@ void launch_b_prep(const BatchSet *sets, int S, const int32_t *pre, int total_bl
 }
 
 void launch_b_assign(const BatchSet *sets, int S, const int64_t *pre_tiles, int64_t total_tiles,
-                     int L, int Lp, int *counter, cudaStream_t s)
+                     int L, int Lp, int *counter, int tile_rows, int ctas_per_sm, cudaStream_t s)
 {
-    // reset the work counter and the per-problem codebook norms first (kb_reset
-    // runs before kb_prep in the pass; see lbg_train_batched)
-    const size_t smem = assign_smem_bytes(Lp);
-    cudaFuncSetAttribute(kb_assign_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int64_t grid = 152 * 2;
+    // the work counter and the per-problem codebook norms are reset by
+    // kb_reset, which runs before kb_prep in the pass (see lbg_train_batched)
+    int64_t grid = 152 * (int64_t)ctas_per_sm;
     if (grid > total_tiles) grid = total_tiles;
     if (grid < 1) return;
-    kb_assign_f32<<<(unsigned)grid, ASSIGN_THREADS, smem, s>>>(sets, S, pre_tiles, total_tiles, L, Lp,
-                                                              counter);
+    if (tile_rows == 64) {
+        const size_t smem = (size_t)(Lp * 64 + 2 * (Lp + 1) * BN) * sizeof(float);
+        cudaFuncSetAttribute(kb_assign_f32<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kb_assign_f32<64><<<(unsigned)grid, 128, smem, s>>>(sets, S, pre_tiles, total_tiles, L, Lp, counter);
+    } else {
+        const size_t smem = assign_smem_bytes(Lp);
+        cudaFuncSetAttribute(kb_assign_f32<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kb_assign_f32<128><<<(unsigned)grid, 256, smem, s>>>(sets, S, pre_tiles, total_tiles, L, Lp, counter);
+    }
 }
 
 void launch_b_reset(const BatchSet *sets, int S, int *counter, cudaStream_t s)

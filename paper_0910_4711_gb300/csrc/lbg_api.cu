@@ -7,6 +7,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <array>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -344,6 +346,7 @@ void lbg_opts_init(lbg_opts *o)
     memset(o, 0, sizeof(*o));
     o->precision = LBG_PREC_FP32;
     o->max_passes = 1000;
+    o->autotune = 1;
 }
 
 int32_t lbg_version(void) { return 1; }
@@ -604,6 +607,86 @@ lbg_status lbg_distortion_backward(const float *X, int64_t M, int32_t L, const f
     return finish_status(h);
 }
 
+// ---- autotuner of the batched nearest-codevector launch
+// Candidates: rows per work item x resident CTAs per SM.  A bucket (device, L,
+// log2 of the largest N, log2 of the total rows) is calibrated once: every
+// problem gets a full-size provisional codebook (its first rows, cyclically),
+// the batched preparation runs, and one batched assignment per candidate is
+// timed with CUDA events (best of two); the fastest is cached.  The choice
+// changes only the speed: every row is computed the same way in each tile.
+static std::map<std::array<int, 4>, std::pair<int, int>> g_tune;
+static const int kTuneRows[4] = {128, 128, 64, 64};
+static const int kTuneCtas[4] = {2, 1, 4, 2};
+
+int ilog2_ceil(int64_t v)
+{
+    int k = 0;
+    while (((int64_t)1 << k) < v) ++k;
+    return k;
+}
+
+lbg_status calibrate_batched(const Call &c, int S, const std::vector<BatchSet> &hs, const BatchSet *dsets,
+                             const int32_t *const *dP, int32_t *const *P, const int64_t *dtiles,
+                             const int64_t *dtiles64, const std::vector<int64_t> &tiles,
+                             const std::vector<int64_t> &tiles64, int *counter, const int32_t *N,
+                             const int64_t *row_off, const float *dX, int L, int Lp, int &best_rows,
+                             int &best_ctas, lbg_tune_report &rep)
+{
+    // data means (the centring of the preparation), then provisional codebooks
+    launch_b_mean(dsets, S, dP[7], P[7][S], L, c.s);
+    for (int s = 0; s < S; ++s) {
+        const int64_t Ms = row_off[s + 1] - row_off[s];
+        for (int64_t n = 0; n < N[s]; n += Ms) {
+            const int64_t rows = (int64_t)N[s] - n < Ms ? (int64_t)N[s] - n : Ms;
+            CK(cudaMemcpyAsync(hs[s].C + n * L, dX + row_off[s] * L, sizeof(float) * rows * L,
+                               cudaMemcpyDeviceToDevice, c.s));
+        }
+    }
+    std::vector<DevState> cal(S);
+    for (int s = 0; s < S; ++s) init_state(cal[s], N[s]);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return LBG_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return LBG_ERR_CUDA;
+    }
+    lbg_status rc = LBG_OK;
+    float best = INFINITY;
+    rep.n_candidates = 4;
+    for (int k = 0; k < 4 && rc == LBG_OK; ++k) {
+        const int rows = kTuneRows[k], ctas = kTuneCtas[k];
+        float t_best = INFINITY;
+        for (int r = 0; r < 2 && rc == LBG_OK; ++r) {
+            for (int s = 0; s < S; ++s)
+                if (cudaMemcpyAsync(hs[s].st, &cal[s], sizeof(DevState), cudaMemcpyHostToDevice, c.s) !=
+                    cudaSuccess)
+                    rc = LBG_ERR_CUDA;
+            launch_b_reset(dsets, S, counter, c.s);
+            launch_b_prep(dsets, S, dP[2], P[2][S], L, Lp, c.s);
+            cudaEventRecord(e0, c.s);
+            launch_b_assign(dsets, S, rows == 64 ? dtiles64 : dtiles, rows == 64 ? tiles64[S] : tiles[S], L, Lp,
+                            counter, rows, ctas, c.s);
+            cudaEventRecord(e1, c.s);
+            float ms = 0.f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                rc = LBG_ERR_CUDA;
+            t_best = ms < t_best ? ms : t_best;
+        }
+        rep.cand_tile_rows[k] = rows;
+        rep.cand_ctas_per_sm[k] = ctas;
+        rep.cand_ms[k] = t_best;
+        if (t_best < best) {
+            best = t_best;
+            best_rows = rows;
+            best_ctas = ctas;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == LBG_OK && cudaGetLastError() != cudaSuccess) rc = LBG_ERR_CUDA;
+    return rc;
+}
+
 lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, int32_t L,
                              const int32_t *N, double delta, double theta, float *C,
                              int32_t *assign, double *D, const lbg_opts *opts)
@@ -626,6 +709,10 @@ lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, 
     }
     const lbg_opts o = resolve(opts);
     if (o.precision != LBG_PREC_FP32) return LBG_ERR_UNSUPPORTED;
+    if (o.tile_rows != 0 && o.tile_rows != 64 && o.tile_rows != 128) return LBG_ERR_ARG;
+    if (o.ctas_per_sm != 0 && o.ctas_per_sm != 1 && o.ctas_per_sm != 2 && o.ctas_per_sm != 4)
+        return LBG_ERR_ARG;
+    if (o.ctas_per_sm == 4 && o.tile_rows != 64) return LBG_ERR_ARG;
     lbg_status rc;
     std::lock_guard<std::mutex> lock(g_mu);
     Call c;
@@ -649,6 +736,7 @@ lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, 
     const size_t o_sets = take(sizeof(BatchSet) * S);
     const size_t o_pre = take(sizeof(int32_t) * (size_t)(S + 1) * 8);
     const size_t o_tiles = take(sizeof(int64_t) * (size_t)(S + 1));
+    const size_t o_tiles64 = take(sizeof(int64_t) * (size_t)(S + 1));
     const size_t o_counter = take(sizeof(int) * 4);
     const size_t o_X = wX == 0 ? take(sizeof(float) * (size_t)Mtot * L) : 0;
     const size_t o_C = wC == 0 ? take(sizeof(float) * (size_t)Ntot * L) : 0;
@@ -671,7 +759,7 @@ lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, 
     // ---- descriptors, states, block maps
     std::vector<BatchSet> hs(S);
     std::vector<int32_t> pre(8 * (S + 1), 0);
-    std::vector<int64_t> tiles(S + 1, 0);
+    std::vector<int64_t> tiles(S + 1, 0), tiles64(S + 1, 0);
     int32_t *P[8];
     for (int k = 0; k < 8; ++k) P[k] = pre.data() + k * (S + 1);
     std::vector<DevState> st0(S);
@@ -719,21 +807,54 @@ lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, 
                             p.G};
         for (int k = 0; k < 8; ++k) P[k][s + 1] = P[k][s] + cnt[k];
         tiles[s + 1] = tiles[s] + (p.M + BM - 1) / BM;
+        tiles64[s + 1] = tiles64[s] + (p.M + 63) / 64;
     }
     for (int s = 0; s < S; ++s)
         CK(cudaMemcpyAsync(hs[s].st, &st0[s], sizeof(DevState), cudaMemcpyHostToDevice, c.s));
     BatchSet *dsets = reinterpret_cast<BatchSet *>(ws + o_sets);
     int32_t *dpre = reinterpret_cast<int32_t *>(ws + o_pre);
     int64_t *dtiles = reinterpret_cast<int64_t *>(ws + o_tiles);
+    int64_t *dtiles64 = reinterpret_cast<int64_t *>(ws + o_tiles64);
     int *counter = reinterpret_cast<int *>(ws + o_counter);
     CK(cudaMemcpyAsync(dsets, hs.data(), sizeof(BatchSet) * S, cudaMemcpyHostToDevice, c.s));
     CK(cudaMemcpyAsync(dpre, pre.data(), sizeof(int32_t) * pre.size(), cudaMemcpyHostToDevice, c.s));
     CK(cudaMemcpyAsync(dtiles, tiles.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, c.s));
+    CK(cudaMemcpyAsync(dtiles64, tiles64.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, c.s));
     const int32_t *dP[8];
     for (int k = 0; k < 8; ++k) dP[k] = dpre + k * (S + 1);
     int max_groups = 0;
     for (int s = 0; s < S; ++s) max_groups += (int)((sub[s].p.M + 7) / 8);
     const bool vec = (reinterpret_cast<uintptr_t>(dX) & 15u) == 0;
+
+    // ---- tile of the batched nearest-codevector launch (lbg_opts.autotune)
+    int tile_rows = 128, ctas = 2;
+    lbg_tune_report report;
+    memset(&report, 0, sizeof(report));
+    if (o.tile_rows != 0 || o.ctas_per_sm != 0) {
+        tile_rows = o.tile_rows != 0 ? o.tile_rows : 128;
+        ctas = o.ctas_per_sm != 0 ? o.ctas_per_sm : (tile_rows == 64 ? 4 : 2);
+    } else if (o.autotune) {
+        const std::array<int, 4> key = {c.dev, L, ilog2_ceil(NMAXB), ilog2_ceil((int64_t)Mtot)};
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            tile_rows = it->second.first;
+            ctas = it->second.second;
+            report.from_cache = 1;
+        } else if ((rc = calibrate_batched(c, S, hs, dsets, dP, P, dtiles, dtiles64, tiles, tiles64, counter,
+                                           N, row_off, dX, L, Lp, tile_rows, ctas, report)) != LBG_OK) {
+            return rc;
+        } else {
+            g_tune[key] = {tile_rows, ctas};
+            // the calibration ran passes on scratch states: start from the initial ones
+            for (int s = 0; s < S; ++s)
+                CK(cudaMemcpyAsync(hs[s].st, &st0[s], sizeof(DevState), cudaMemcpyHostToDevice, c.s));
+        }
+    }
+    report.tile_rows = tile_rows;
+    report.ctas_per_sm = ctas;
+    if (o.tune_report) *o.tune_report = report;
+    const int64_t *dtiles_use = tile_rows == 64 ? dtiles64 : dtiles;
+    const int64_t ntiles_use = tile_rows == 64 ? tiles64[S] : tiles[S];
     Timer tm;
     if ((rc = tm.init(o.phase_ms != nullptr)) != LBG_OK) return rc;
     tm.mark(0, c.s);
@@ -743,7 +864,7 @@ lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, 
     auto pass = [&](cudaStream_t st) {
         launch_b_reset(dsets, S, counter, st);
         launch_b_prep(dsets, S, dP[2], P[2][S], L, Lp, st);
-        launch_b_assign(dsets, S, dtiles, tiles[S], L, Lp, counter, st);
+        launch_b_assign(dsets, S, dtiles_use, ntiles_use, L, Lp, counter, tile_rows, ctas, st);
         launch_b_exact(dsets, S, L, Lp, max_groups, st);
         launch_b_hist(dsets, S, dP[0], P[0][S], NMAXB, st);
         launch_b_ctl(dsets, S, theta, o.max_passes, st);

@@ -286,8 +286,11 @@ void launch_b_advance(const BatchSet *sets, int S, const int32_t *pre, int total
                       cudaStream_t s);
 void launch_b_prep(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int L, int Lp,
                    cudaStream_t s);
+// Persistent batched nearest-codevector launch over (problem, row tile) work
+// items; tile_rows 64 or 128 (pre_tiles counts tiles of that height), grid =
+// 152 x ctas_per_sm CTAs.
 void launch_b_assign(const BatchSet *sets, int S, const int64_t *pre_tiles, int64_t total_tiles,
-                     int L, int Lp, int *counter, cudaStream_t s);
+                     int L, int Lp, int *counter, int tile_rows, int ctas_per_sm, cudaStream_t s);
 void launch_b_exact(const BatchSet *sets, int S, int L, int Lp, int max_ngroups, cudaStream_t s);
 void launch_b_reset(const BatchSet *sets, int S, int *counter, cudaStream_t s);
 

@@ -71,3 +71,20 @@ def test_step_and_encode_reject_bad_arguments(lib):
     # null codebook through the raw ABI
     assert lib.vq_encode(None, 8, 4, None, 2, None, None, None, None) == -1
     assert lib.lbg_lloyd_step(None, 8, 4, 2, None, None, None, None, None) == -1
+
+
+def test_opts_defaults(lib):
+    from paper_0910_4711_gb300 import _binding
+    o = _binding.Opts()
+    lib.lbg_opts_init(ctypes.byref(o))
+    assert o.precision == 0 and o.max_passes == 1000
+    assert o.autotune == 1 and o.tile_rows == 0 and o.ctas_per_sm == 0
+    assert not o.tune_report and not o.records and not o.phase_ms
+
+
+def test_batched_rejects_bad_tile_options(lib):
+    X = np.zeros((256, 16), np.float32)
+    ro, N = [0, 256], [4]
+    assert _err(lbgvq.lbg_train_batched, X, ro, N, 0.01, 1e-3, 1000, False, None, False, True, 96) == -1
+    assert _err(lbgvq.lbg_train_batched, X, ro, N, 0.01, 1e-3, 1000, False, None, False, True, 64, 3) == -1
+    assert _err(lbgvq.lbg_train_batched, X, ro, N, 0.01, 1e-3, 1000, False, None, False, True, 128, 4) == -1

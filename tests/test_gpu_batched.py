@@ -67,3 +67,34 @@ def test_batched_rejects_bad_sizes(lbg):
         lbg.lbg_train_batched(X, [0, 5, 10], [4, 3])       # 3 not a power of 2
     with pytest.raises(lbg.LBGError):
         lbg.lbg_train_batched(X, [0, 0, 10], [4, 4])       # empty problem
+
+
+def test_tile_choice_does_not_change_results(lbg):
+    """Every candidate tile of the batched assignment (rows per work item x CTAs
+    per SM) gives the same bits as the fixed default and as the autotuned run."""
+    parts, Xc, row_off, Ns = ragged_sets(70, [4096, 20000, 777, 9000], [64, 512, 16, 128])
+    Xd = torch.from_numpy(Xc).cuda()
+    ref = lbg.lbg_train_batched(Xd, row_off, Ns, autotune=False)
+    assert ref.tune["tile_rows"] == 128 and ref.tune["ctas_per_sm"] == 2
+    for rows, ctas in ((128, 1), (128, 2), (64, 2), (64, 4)):
+        r = lbg.lbg_train_batched(Xd, row_off, Ns, tile_rows=rows, ctas_per_sm=ctas)
+        assert (r.tune["tile_rows"], r.tune["ctas_per_sm"]) == (rows, ctas)
+        assert torch.equal(r.C, ref.C) and torch.equal(r.assign, ref.assign) and r.D == ref.D, (rows, ctas)
+    tuned = lbg.lbg_train_batched(Xd, row_off, Ns)
+    assert torch.equal(tuned.C, ref.C) and torch.equal(tuned.assign, ref.assign) and tuned.D == ref.D
+
+
+def test_autotune_report_and_cache(lbg):
+    parts, Xc, row_off, Ns = ragged_sets(90, [3000, 5000, 7000], [32, 64, 1024])
+    Xd = torch.from_numpy(Xc).cuda()
+    first = lbg.lbg_train_batched(Xd, row_off, Ns)
+    t = first.tune
+    if not t["from_cache"]:                  # a calibration ran in this call
+        c = t["candidates"]
+        assert len(c) == 4 and all(x["ms"] > 0 for x in c)
+        best = min(c, key=lambda x: x["ms"])
+        assert (t["tile_rows"], t["ctas_per_sm"]) == (best["tile_rows"], best["ctas_per_sm"])
+    again = lbg.lbg_train_batched(Xd, row_off, Ns)
+    assert again.tune["from_cache"] and again.tune["candidates"] == []
+    assert (again.tune["tile_rows"], again.tune["ctas_per_sm"]) == (t["tile_rows"], t["ctas_per_sm"])
+    assert torch.equal(again.C, first.C) and again.D == first.D
