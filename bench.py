@@ -78,6 +78,42 @@ def workload_desc(name, X, N):
     return f"{name}: {w}, M={X.shape[0]}, L={X.shape[1]}, N={N}, delta=0.01, theta=1e-3"
 
 
+# ------------------------------------------------------------------ measured traffic
+# DRAM bytes per launch of the roofline kernel come from a committed ncu summary
+# (profiles/), valid only while the kernel's sources are unchanged since that
+# capture: the summary records a digest of them.
+TRAFFIC = {("bf16", "img2048x8_b8_n4096"): ("k_assign_tc_img2048x8_b8_n4096_full.md",
+                                             ("k_assign_tc.cu", "lbg_internal.cuh"))}
+
+
+def source_digest(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_0910_4711_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(precision, workload):
+    """(bytes per launch or None, summary file, current source digest)."""
+    import re
+    entry = TRAFFIC.get((precision, workload))
+    if entry is None:
+        return None, None, None
+    summary, files = entry
+    digest = source_digest(files)
+    try:
+        text = open(os.path.join(ROOT, "profiles", summary)).read()
+    except OSError:
+        return None, summary, digest
+    m_d = re.search(r"source digest: `([0-9a-f]+)`", text)
+    m_b = re.search(r"dram bytes per launch: `([0-9,]+)`", text)
+    if m_d and m_b and m_d.group(1) == digest:
+        return int(m_b.group(1).replace(",", "")), summary, digest
+    return None, summary, digest
+
+
 # ------------------------------------------------------------------ distributed
 def dist_setup(n, backend="nccl"):
     """Join the process group torchrun set up (one replica per GPU); (0, 1, None) alone."""
@@ -271,11 +307,17 @@ def cpu_baseline(X, C, seconds, seed=0):
     oracle.lloyd_step(S, Cd)
     t = time.perf_counter() - t0
     evals = S.shape[0] * Cd.shape[0]
+    # the same pass on one host thread, on 1/16 of that sample
+    S1 = S[: max(256, S.shape[0] // 16)]
+    t0 = time.perf_counter()
+    oracle.lloyd_step(S1, Cd, nthreads=1)
+    t_1 = time.perf_counter() - t0
     return {"value": evals / t, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "seconds": t,
+            "seconds": t, "value_1thread": S1.shape[0] * Cd.shape[0] / t_1,
             "sample": (f"one FP64 oracle Lloyd pass (allocation, distortion, updation) over "
                        f"{S.shape[0]} random rows of the same X against the same N={Cd.shape[0]} "
-                       f"codebook")}
+                       f"codebook on all host threads (OpenMP static row split); value_1thread: "
+                       f"the first {S1.shape[0]} of those rows on one thread")}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -415,11 +457,16 @@ def run_ours(args):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     upd_bytes = M * L * 4 + M * 4 + N * L * 4 + N * 4
     upd_gbs = upd_bytes / (ph["update"] / 1e3) / 1e9
+    traffic, t_summary, t_digest = measured_traffic(args.precision, args.workload)
     if args.precision == "bf16":
         Lk = (L + 15) // 16 * 16
         executed = 2.0 * M * N * (3 * Lk + 16) / (assign_ms / 1e3) / 1e12
         roof = {"bound": "tensor", "kernel": "k_assign_tc", "achieved": achieved, "peak": bf16_peak,
-                "unit": "TFLOP/s", "frac": achieved / bf16_peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / bf16_peak, "traffic": traffic,
+                "traffic_source": (f"profiles/{t_summary} (ncu dram__bytes_read.sum + dram__bytes_write.sum "
+                                   f"per launch; kernel source digest {t_digest})"
+                                   if traffic is not None else
+                                   f"null: no capture of the current kernel sources (digest {t_digest})"),
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
                 "work": "2*L*M*N flop per launch (algorithmic; the three-piece BF16 split and the "
                         "norm column make the tensor cores execute 2*M*N*(3*ceil16(L)+16))",
@@ -468,7 +515,7 @@ def run_ours(args):
     if not args.no_batched:
         line["batched"] = batched_leg(lbg, synth, torch)
     if not args.no_small:
-        line["small_full_lbg"] = small_leg(lbg, synth, torch)
+        line["small_full_lbg"] = small_leg(lbg, synth, torch, with_oracle=not args.no_cpu_baseline)
     if args.large:
         line["large"] = large_leg(lbg, synth, torch)
 
@@ -537,7 +584,7 @@ def grad_leg(lbg, synth, torch, stream, flush, args, dist):
             "forward_evals_per_s": Mg * Ng / (fwd / 1e3)}
 
 
-def small_leg(lbg, synth, torch):
+def small_leg(lbg, synth, torch, with_oracle=True):
     """Full LBG design on one 512x512 image, 4x4 blocks (M=16384, L=16, N=256)."""
     X_np, N = synth.workload("img512_b4_n256")
     X = torch.from_numpy(X_np).cuda()
@@ -552,6 +599,14 @@ def small_leg(lbg, synth, torch):
             torch.cuda.synchronize()
             ts.append(time.perf_counter() - t0)
         out[prec] = {"full_lbg_ms": 1e3 * statistics.median(ts), "passes": r.n_passes, "D": r.D}
+    if with_oracle:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        o = oracle.lbg_train(X_np, N, 0.01, 1e-3)
+        out["oracle_full_lbg"] = {"seconds": time.perf_counter() - t0, "passes": int(len(o.trace_D)),
+                                  "D": float(o.D), "cores": oracle.max_threads(),
+                                  "kind": "FP64 oracle LBG on the host (same data, delta, theta)"}
     return out
 
 
