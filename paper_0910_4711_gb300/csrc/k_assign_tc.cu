@@ -410,6 +410,274 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// ---------------------------------------------------------------- shared parts
+// Static shared state of the assignment kernels.
+struct TcSmem {
+    uint64_t full[3], empty[3], tfull[TC_SLOTS], tempty[TC_SLOTS], xfull, xempty, aready;
+    uint32_t tmem_base;
+    int abort, inexact, prod_last, mma_tile, mma_job, x_issued, x_done;
+    float v1[2][TC_ROWS], v2[2][TC_ROWS], d[2][TC_ROWS], k[2][TC_ROWS];
+    int i1[2][TC_ROWS];
+};
+
+__device__ __forceinline__ bool named_sync_or(int id, int threads, bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(threads)
+        : "memory");
+    return r != 0;
+}
+
+// One centred x value into the staged BF16 rows; flags non-finite input and
+// values for which x~ = x - mu is not exact in FP32 (TwoSum error) or BF16.
+__device__ __forceinline__ void tc_put_x(__nv_bfloat16 *XS, int xstr, int i, int L, float xv,
+                                         const float *__restrict__ mu, bool &bad, bool &inexact)
+{
+    const int r = i / L, l = i - r * L;
+    bad = bad || !isfinite(xv);
+    const float ml = __ldg(mu + l);
+    const float v = __fsub_rn(xv, ml);
+    const float bb = __fsub_rn(v, xv);
+    const float err = __fadd_rn(__fsub_rn(xv, __fsub_rn(v, bb)), __fsub_rn(-ml, bb));
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    inexact = inexact || err != 0.f || (__bfloat162float(b) != v);
+    XS[r * xstr + l] = b;
+}
+
+// The A operand in tensor memory: each epilogue thread writes its half of its
+// row's K = LK + 16 BF16 (two per column): x~ (zero past L and for rows past
+// M), then in half 1 the norm block 1 1 1 (x s0 pieces), X2 = ||x~||^2 in
+// three BF16 pieces, zeros.  ||x~||^2 is half 0's sum of squares plus half 1's
+// in that order.  Returns ||x~||^2 of the thread's row; the caller fences and
+// synchronises before the MMAs read A.
+template <int LK>
+__device__ __forceinline__ float tc_write_a(const __nv_bfloat16 *XS, int L, bool live, int crow, int half,
+                                            int acc, int warp, uint32_t tmem, TcSmem &sh)
+{
+    constexpr int KA = LK + 16, NW = KA / 4, XSTR = LK + 8;
+    uint32_t wv[NW];
+    float part = 0.f;
+    const __nv_bfloat16 *xrow = XS + (size_t)crow * XSTR;
+    if (half == 0) a_words<LK, 0>(xrow, L, live, wv, part);
+    else a_words<LK, 1>(xrow, L, live, wv, part);
+    sh.d[half][crow] = part;
+    named_sync(1, 32 * TC_EPI_WARPS);
+    const float xn2 = __fadd_rn(sh.d[0][crow], sh.d[1][crow]);
+    if (half == 1) {
+        __nv_bfloat16 h, mi, lo;
+        split3(xn2, h, mi, lo);
+        const uint32_t one = __bfloat16_as_ushort(__float2bfloat16_rn(1.f));
+        constexpr int w0 = (LK - KA / 2) / 2;   // first norm-block word
+        wv[w0] = one | (one << 16);
+        wv[w0 + 1] = one | ((uint32_t)__bfloat16_as_ushort(h) << 16);
+        wv[w0 + 2] = (uint32_t)__bfloat16_as_ushort(mi) | ((uint32_t)__bfloat16_as_ushort(lo) << 16);
+    }
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    tmem_st_words<NW>(tmem + lane_base + (uint32_t)(TC_A_COL + acc * (KA / 2) + half * NW), wv);
+    tmem_st_wait();
+    return xn2;
+}
+
+// The epilogue of one row tile: for each codebook tile t, job j0 + 2t + acc
+// (accumulator slot (j0 + 2t + acc) % 3); the thread's 64 values per job go
+// through the pair top-2; returns the merged (V1, V2, pair index) of the
+// thread's half.  Stops at a time-out (sh.abort set).
+__device__ __forceinline__ void tc_jobs(TcSmem &sh, uint32_t tmem, int warp, int lane, int acc, int half,
+                                        int ntiles, int j0, int keymask, float &V1, float &V2, int &i1)
+{
+    constexpr int NCH = 4;   // independent min-chains
+    constexpr int JMASK = (1 << TC_JBITS) - 1;
+    float c1[NCH], c2[NCH];
+    int cg[NCH];
+#pragma unroll
+    for (int q = 0; q < NCH; ++q) {
+        c1[q] = INFINITY;
+        c2[q] = INFINITY;
+        cg[q] = 0;
+    }
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    for (int t = 0; t < ntiles; ++t) {
+        if (sh.abort) break;
+        const int j = j0 + 2 * t + acc, slot = j % TC_SLOTS;
+        if (!mbar_wait_bounded_sleep(&sh.tfull[slot], (uint32_t)(j / TC_SLOTS) & 1u)) {
+            sh.abort = 1;
+            break;
+        }
+        tc_fence_after();
+        float v[TC_HALF];
+        const uint32_t col = (uint32_t)(slot * TC_NT + half * TC_HALF);
+        tmem_ld32(tmem + lane_base + col, v);
+        tmem_ld32(tmem + lane_base + col + 32u, v + 32);
+        tmem_ld_wait();
+        // the values are in registers: hand the accumulator back to the MMA
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh.tempty[slot]);
+        float s1[NCH];
+#pragma unroll
+        for (int q = 0; q < NCH; ++q) s1[q] = c1[q];
+        PairSteps<TC_PAIRS>::run(v, c1, c2, keymask);
+#pragma unroll
+        for (int q = 0; q < NCH; ++q) cg[q] = c1[q] < s1[q] ? t : cg[q];
+    }
+    // merge the chains; i1 is the first column of the minimum's pair:
+    // tile * TC_NT + half * TC_HALF + 2 * (the low bits)
+    V1 = c1[0];
+    V2 = c2[0];
+    i1 = cg[0] * TC_NT + half * TC_HALF + 2 * (__float_as_int(c1[0]) & JMASK);
+#pragma unroll
+    for (int q = 1; q < NCH; ++q) {
+        const int iq = cg[q] * TC_NT + half * TC_HALF + 2 * (__float_as_int(c1[q]) & JMASK);
+        V2 = fminf(fminf(V2, c2[q]), fmaxf(V1, c1[q]));
+        const bool take = c1[q] < V1 || (c1[q] == V1 && iq < i1);
+        V1 = take ? c1[q] : V1;
+        i1 = take ? iq : i1;
+    }
+}
+
+// The end of a row tile (all 16 epilogue warps; uses named barriers 1 and 2):
+// the two halves of a row merge their top-2 in a fixed order; the minimum is
+// one of the pair (i1, i1 + 1), and each half computes the exact FP32
+// distance of one member.  With L a multiple of 4 the warp does it
+// cooperatively: a half-warp per row, a float4 of x and of the codevector per
+// lane (coalesced reads of X and C), each lane sums its four terms
+// (x_l - c_l)^2 in order, and a butterfly over the 16 lanes of each half-warp
+// reduces the 16 rows' partial sums at once (a fixed tree: 15 shuffles per
+// lane); the owner lane of each row takes its sum.  The half-0 thread then
+// takes the smaller distance when the two differ by more than the rounding
+// bound of the FP32 sum, runs the certificate, and writes a(m), e(m) or flags
+// the row.  `usable` = the tile's x~ and the codebook split are exact.
+template <int LK>
+__device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc, int half, int rr,
+                                        int64_t m0, const float *__restrict__ X, int64_t M, int L, int N,
+                                        const float *__restrict__ C, const float *__restrict__ kn, float xn2,
+                                        bool usable_tile, float cmax, float V1, float V2, int i1, DevState *st,
+                                        int32_t *__restrict__ assign, float *__restrict__ e,
+                                        int32_t *__restrict__ flags)
+{
+    const int crow = 128 * acc + rr;
+    const int64_t m = m0 + crow;
+    sh.v1[half][crow] = V1;
+    sh.v2[half][crow] = V2;
+    sh.i1[half][crow] = i1;
+    named_sync(1, 32 * TC_EPI_WARPS);
+    {
+        const float A1 = sh.v1[0][crow], A2 = sh.v2[0][crow], B1 = sh.v1[1][crow], B2 = sh.v2[1][crow];
+        const int ai = sh.i1[0][crow], bi = sh.i1[1][crow];
+        V2 = fminf(fminf(A2, B2), fmaxf(A1, B1));
+        const bool take = B1 < A1 || (B1 == A1 && bi < ai);
+        V1 = take ? B1 : A1;
+        i1 = take ? bi : ai;
+    }
+    const bool usable = m < M && !sh.abort && usable_tile && i1 >= 0 && i1 < N && V1 < INFINITY;
+    const int cand = i1 + half;
+    const int ccand = (usable && cand < N) ? cand : -1;
+    const float kc = ccand >= 0 ? __ldg(kn + ccand) : 0.f;
+    float dc = INFINITY;
+    if ((L & 3) == 0 && ((reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(X)) & 15u) == 0) {
+        const int rq = lane & 15, sub = lane >> 4;
+        const int64_t mrow0 = m0 + 128 * acc + 32 * (warp & 3);   // row of lane 0
+        float p[16];
+#pragma unroll
+        for (int bt = 0; bt < 2; ++bt) {   // two batches of 8 rows
+            int crs[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) crs[k] = __shfl_sync(0xffffffffu, ccand, 2 * (8 * bt + k) + sub);
+            float4 c4[8], x4[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const bool on = crs[k] >= 0 && 4 * rq < L;
+                const int64_t mr = mrow0 + 2 * (8 * bt + k) + sub;
+                c4[k] = on ? __ldg(reinterpret_cast<const float4 *>(C + (size_t)crs[k] * L) + rq)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+                x4[k] = on ? __ldg(reinterpret_cast<const float4 *>(X + mr * L) + rq)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                float d = __fsub_rn(x4[k].x, c4[k].x);
+                float q = d * d;
+                d = __fsub_rn(x4[k].y, c4[k].y);
+                q = fmaf(d, d, q);
+                d = __fsub_rn(x4[k].z, c4[k].z);
+                q = fmaf(d, d, q);
+                d = __fsub_rn(x4[k].w, c4[k].w);
+                p[8 * bt + k] = fmaf(d, d, q);
+            }
+        }
+#pragma unroll
+        for (int lvl = 8; lvl >= 1; lvl >>= 1) {
+            const bool up = (rq & lvl) != 0;
+#pragma unroll
+            for (int i = 0; i < lvl; ++i) {
+                const float send = up ? p[i] : p[i + lvl];
+                const float keep = up ? p[i + lvl] : p[i];
+                p[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, lvl));
+            }
+        }
+        // lane (sub, rq) now holds the sum of row 2 rq + sub
+        const float got = __shfl_sync(0xffffffffu, p[0], (lane & 1) * 16 + (lane >> 1));
+        if (ccand >= 0) dc = got;
+    } else if (ccand >= 0) {
+        const float *xr = X + m * L;
+        const float *cr = C + (size_t)ccand * L;
+        float d2 = 0.f;
+        for (int l = 0; l < L; ++l) {
+            const float d = __fsub_rn(__ldg(xr + l), __ldg(cr + l));
+            d2 = fmaf(d, d, d2);
+        }
+        dc = d2;
+    }
+    sh.d[half][crow] = dc;
+    sh.k[half][crow] = kc;
+    named_sync(2, 32 * TC_EPI_WARPS);
+    if (half == 0 && m < M && !sh.abort) {
+        // the smaller distance is taken when the two differ by more than the
+        // rounding bound of the FP32 sum, |fl(d2) - d2| <= (L + 2) u d2 for any
+        // order of the L terms (kept as (L + 4) u); else the row is not certified
+        bool certified = false;
+        if (usable) {
+            float da = sh.d[0][crow], ka = sh.k[0][crow];
+            const float db = sh.d[1][crow], kb = sh.k[1][crow];
+            int ii = i1;
+            bool sure = true;
+            if (i1 + 1 < N) {
+                const float tol = (float)(L + 4) * U32 * (da + db) * SLOP;
+                if (db < da - tol) {
+                    ii = i1 + 1;
+                    da = db;
+                    ka = kb;
+                } else if (!(da < db - tol)) {
+                    sure = false;
+                }
+            }
+            if (sure) {
+                const double tau = tc_tau(3 * LK + 16);
+                const float xn2u = xn2 * SLOP;
+                const float R = 2.f * (float)tau * xn2u * SLOP;
+                const float eta = U32 * (sqrtf(xn2u) + cmax) * SLOP;
+                // index packing of the pair minima, FMA-pipe pair maxima
+                const float pack = TC_PACK * (fabsf(V1) + fabsf(V2)) + TC_HIERR * (fabsf(V1) + 2.f * fabsf(V2));
+                // V1 ~ ||x~ - c~_ii||^2 - k' (X2 included): bound g1^2 from above
+                const float g1sq = V1 + 2.f * ka + R + pack + (float)(L + 2) * U32 * xn2u;
+                const float g1 = sqrtf(fmaxf(g1sq, 0.f)) * SLOP;
+                const float margin = (2.f * R + 2.f * ka + pack + 4.f * eta * (g1 + eta)) * SLOP;
+                certified = (V2 - V1) > margin;
+            }
+            if (certified) {
+                assign[m] = ii;
+                e[m] = da;
+            }
+        }
+        if (!certified) flags[atomicAdd(&st->nflag, 1)] = (int32_t)m;
+    }
+}
+
+// ---------------------------------------------------------------- one CTA per row tile
 template <int LK>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_assign_tc(const float *__restrict__ X, int64_t M, int L,
@@ -420,17 +688,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 {
     if (st->finished) return;
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], tfull[TC_SLOTS], tempty[TC_SLOTS];
-    __shared__ uint32_t tmem_base;
-    __shared__ int s_abort, s_inexact, s_prod_last, s_mma_tile, s_mma_job;
-    __shared__ float s_v1[2][TC_ROWS], s_v2[2][TC_ROWS], s_d[2][TC_ROWS], s_k[2][TC_ROWS];
-    __shared__ int s_i1[2][TC_ROWS];
+    __shared__ TcSmem sh;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int N = cur_n(n_dev, n_host);
     const int ntiles = (N + TC_NT - 1) / TC_NT;
-    constexpr int Lk = LK;
-    constexpr int KA = LK + 16, KB = 3 * LK + 16;
+    constexpr int KB = 3 * LK + 16;
     constexpr int XSTR = LK + 8;                               // staged row stride (BF16), padded
     constexpr uint32_t sbo_b = (uint32_t)(KB / 8) * 128u;
     constexpr uint32_t xs_bytes = (uint32_t)TC_ROWS * XSTR * 2u;
@@ -441,23 +704,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&sh.full[s], 1);
+            mbar_init(&sh.empty[s], 1);
         }
         for (int b = 0; b < TC_SLOTS; ++b) {
-            mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], TC_EPI_WARPS / TC_NACC);
+            mbar_init(&sh.tfull[b], 1);
+            mbar_init(&sh.tempty[b], TC_EPI_WARPS / TC_NACC);
         }
         fence_mbar_init();
-        s_abort = 0;
-        s_inexact = 0;
-        s_prod_last = -1;
-        s_mma_tile = -1;
-        s_mma_job = -1;
+        sh.abort = 0;
+        sh.inexact = 0;
+        sh.prod_last = -1;
+        sh.mma_tile = -1;
+        sh.mma_job = -1;
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_addr(&tmem_base)),
+                         smem_addr(&sh.tmem_base)),
                      "n"(TC_TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -474,25 +737,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (epi) {
         // Stage the centred x tile as BF16 rows in shared memory: the TC_ROWS x
         // L tile is contiguous in X, so the epilogue threads read it as a flat
-        // array (coalesced, eight 16-byte loads in flight per thread).  A tile
-        // is usable only if every x~ = x - mu is exact in FP32 (TwoSum error
-        // zero) and in BF16.
+        // array (coalesced, eight 16-byte loads in flight per thread).
         constexpr int ST = 32 * TC_EPI_WARPS;                 // 512 staging threads
         const int et = tid - 64;
         const int64_t rows = M - m0 < TC_ROWS ? M - m0 : TC_ROWS;
         bool inexact = false, bad = false;
         const float *Xt = X + m0 * L;
-        auto put_x = [&](int i, float xv) {   // i: flat index inside the tile
-            const int r = i / L, l = i - r * L;
-            bad = bad || !isfinite(xv);
-            const float ml = __ldg(mu + l);
-            const float v = __fsub_rn(xv, ml);
-            const float bb = __fsub_rn(v, xv);
-            const float err = __fadd_rn(__fsub_rn(xv, __fsub_rn(v, bb)), __fsub_rn(-ml, bb));
-            const __nv_bfloat16 b = __float2bfloat16_rn(v);
-            inexact = inexact || err != 0.f || (__bfloat162float(b) != v);
-            XS[r * XSTR + l] = b;
-        };
         const int total = (int)rows * L;
         if ((L & 3) == 0 && (reinterpret_cast<uintptr_t>(Xt) & 15u) == 0) {
             const float4 *X4 = reinterpret_cast<const float4 *>(Xt);
@@ -505,62 +755,35 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int f = 4 * (i + u * ST);
-                    put_x(f, q[u].x);
-                    put_x(f + 1, q[u].y);
-                    put_x(f + 2, q[u].z);
-                    put_x(f + 3, q[u].w);
+                    tc_put_x(XS, XSTR, f, L, q[u].x, mu, bad, inexact);
+                    tc_put_x(XS, XSTR, f + 1, L, q[u].y, mu, bad, inexact);
+                    tc_put_x(XS, XSTR, f + 2, L, q[u].z, mu, bad, inexact);
+                    tc_put_x(XS, XSTR, f + 3, L, q[u].w, mu, bad, inexact);
                 }
             }
             for (; i < total4; i += ST) {
                 const float4 q = __ldg(X4 + i);
-                put_x(4 * i, q.x);
-                put_x(4 * i + 1, q.y);
-                put_x(4 * i + 2, q.z);
-                put_x(4 * i + 3, q.w);
+                tc_put_x(XS, XSTR, 4 * i, L, q.x, mu, bad, inexact);
+                tc_put_x(XS, XSTR, 4 * i + 1, L, q.y, mu, bad, inexact);
+                tc_put_x(XS, XSTR, 4 * i + 2, L, q.z, mu, bad, inexact);
+                tc_put_x(XS, XSTR, 4 * i + 3, L, q.w, mu, bad, inexact);
             }
         } else {
-            for (int i = et; i < total; i += ST) put_x(i, __ldg(Xt + i));
+            for (int i = et; i < total; i += ST) tc_put_x(XS, XSTR, i, L, __ldg(Xt + i), mu, bad, inexact);
         }
         if (bad) flag_error(st, ERR_NONFINITE);
-        if (inexact) s_inexact = 1;
+        if (inexact) sh.inexact = 1;
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = tmem_base;
+    const uint32_t tmem = sh.tmem_base;
     // codebook state written by the preparation kernel (constant here)
     const bool tc_exact_cb = st->tc_inexact == 0;
     const float cmax = __uint_as_float(st->cmax_bits);
 
     float xn2 = 0.f;
-    if (epi) {
-        // The A operand in tensor memory: each thread writes its half of its
-        // row's K = Lk + 16 BF16 (two per column): x~ (zero past L and for
-        // rows past M), then in half 1 the norm block 1 1 1 (x s0 pieces),
-        // X2 = ||x~||^2 in three BF16 pieces, zeros.  ||x~||^2 is half 0's sum
-        // of squares plus half 1's, in that order.
-        constexpr int NW = KA / 4;                               // words per half
-        uint32_t wv[NW];
-        float part = 0.f;
-        const __nv_bfloat16 *xrow = XS + (size_t)crow * XSTR;
-        if (half == 0) a_words<LK, 0>(xrow, L, m < M, wv, part);
-        else a_words<LK, 1>(xrow, L, m < M, wv, part);
-        s_d[half][crow] = part;
-        named_sync(1, 32 * TC_EPI_WARPS);
-        xn2 = __fadd_rn(s_d[0][crow], s_d[1][crow]);
-        if (half == 1) {
-            __nv_bfloat16 h, mi, lo;
-            split3(xn2, h, mi, lo);
-            const uint32_t one = __bfloat16_as_ushort(__float2bfloat16_rn(1.f));
-            constexpr int w0 = (LK - KA / 2) / 2;                // first norm-block word
-            wv[w0] = one | (one << 16);
-            wv[w0 + 1] = one | ((uint32_t)__bfloat16_as_ushort(h) << 16);
-            wv[w0 + 2] = (uint32_t)__bfloat16_as_ushort(mi) | ((uint32_t)__bfloat16_as_ushort(lo) << 16);
-        }
-        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-        tmem_st_words<NW>(tmem + lane_base + (uint32_t)(TC_A_COL + acc * (KA / 2) + half * NW), wv);
-        tmem_st_wait();
-    }
+    if (epi) xn2 = tc_write_a<LK>(XS, L, m < M, crow, half, acc, warp, tmem, sh);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -570,16 +793,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {
             for (int t = 0; t < ntiles; ++t) {
                 const int s = t % TC_STAGES;
-                if (t >= TC_STAGES && !mbar_wait_bounded_sleep(&empty[s], (uint32_t)((t / TC_STAGES) - 1) & 1u)) {
-                    s_abort = 1;
+                if (t >= TC_STAGES && !mbar_wait_bounded_sleep(&sh.empty[s], (uint32_t)((t / TC_STAGES) - 1) & 1u)) {
+                    sh.abort = 1;
                     break;
                 }
-                if (s_abort) break;
-                mbar_expect_tx(&full[s], stage_bytes);
+                if (sh.abort) break;
+                mbar_expect_tx(&sh.full[s], stage_bytes);
                 bulk_load(Bs + s * stage_bytes,
                           reinterpret_cast<const uint8_t *>(Bp) + (size_t)t * stage_bytes, stage_bytes,
-                          &full[s]);
-                s_prod_last = t;
+                          &sh.full[s]);
+                sh.prod_last = t;
             }
         }
     } else if (warp == 1) {
@@ -593,7 +816,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         bool ok = true;
         for (int t = 0; t < ntiles && ok; ++t) {
             const int s = t % TC_STAGES;
-            if (!__all_sync(0xffffffffu, mbar_wait_bounded_sleep(&full[s], (uint32_t)(t / TC_STAGES) & 1u))) {
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded_sleep(&sh.full[s], (uint32_t)(t / TC_STAGES) & 1u))) {
                 ok = false;
                 break;
             }
@@ -604,14 +827,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int a = 0; a < TC_NACC; ++a) {
                 const int j = 2 * t + a, slot = j % TC_SLOTS;
                 if ((j >= TC_SLOTS &&
-                     !__all_sync(0xffffffffu, mbar_wait_bounded_sleep(&tempty[slot], (uint32_t)((j / TC_SLOTS) - 1) & 1u))) ||
-                    s_abort) {
+                     !__all_sync(0xffffffffu, mbar_wait_bounded_sleep(&sh.tempty[slot], (uint32_t)((j / TC_SLOTS) - 1) & 1u))) ||
+                    sh.abort) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(slot * TC_NT);
-                const uint32_t at = tmem + (uint32_t)(TC_A_COL + a * (KA / 2));
+                const uint32_t at = tmem + (uint32_t)(TC_A_COL + a * ((LK + 16) / 2));
 #pragma unroll
                 for (int seg = 0; seg < 3; ++seg)
 #pragma unroll
@@ -619,201 +842,273 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         mma_bf16_ta_elect(d, at + (uint32_t)(8 * kk), bst + (uint64_t)(seg * LK + kk * 16),
                                           (seg | kk) ? 1u : 0u);
                 mma_bf16_ta_elect(d, at + (uint32_t)(LK / 2), bst + (uint64_t)(3 * LK), 1u);
-                mma_commit_elect(&tfull[slot]);
-                if (lane == 0) s_mma_job = j;
+                mma_commit_elect(&sh.tfull[slot]);
+                if (lane == 0) sh.mma_job = j;
             }
             if (!ok) break;
-            mma_commit_elect(&empty[s]);
-            if (lane == 0) s_mma_tile = t;
+            mma_commit_elect(&sh.empty[s]);
+            if (lane == 0) sh.mma_tile = t;
         }
-        if (!ok && lane == 0) s_abort = 1;
+        if (!ok && lane == 0) sh.abort = 1;
         __syncwarp();
     } else if (epi) {
         // ---------------- epilogue: one (row, column half) per thread
-        constexpr int NCH = 4;                       // independent min-chains
-        constexpr int JMASK = (1 << TC_JBITS) - 1;
-        float c1[NCH], c2[NCH];
-        int cg[NCH];
-#pragma unroll
-        for (int q = 0; q < NCH; ++q) {
-            c1[q] = INFINITY;
-            c2[q] = INFINITY;
-            cg[q] = 0;
+        float V1, V2;
+        int i1;
+        tc_jobs(sh, tmem, warp, lane, acc, half, ntiles, 0, keymask, V1, V2, i1);
+        tc_tail<LK>(sh, warp, lane, acc, half, rr, m0, X, M, L, N, C, kn, xn2, !sh.inexact && tc_exact_cb,
+                    cmax, V1, V2, i1, st, assign, e, flags);
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (sh.abort) {
+        // Stop: wait (bounded) for the bulk copies nobody consumed and for the
+        // last committed MMAs, then free TMEM below.
+        if (tid == 0) {
+            for (int t = sh.mma_tile + 1; t <= sh.prod_last; ++t)
+                (void)mbar_wait_bounded(&sh.full[t % TC_STAGES], (uint32_t)(t / TC_STAGES) & 1u);
+            if (sh.mma_job >= 0)
+                (void)mbar_wait_bounded(&sh.tfull[sh.mma_job % TC_SLOTS], (uint32_t)(sh.mma_job / TC_SLOTS) & 1u);
+            flag_error(st, ERR_TIMEOUT);
         }
-        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-        for (int t = 0; t < ntiles; ++t) {
-            const int j = 2 * t + acc, slot = j % TC_SLOTS;
-            if (!mbar_wait_bounded_sleep(&tfull[slot], (uint32_t)(j / TC_SLOTS) & 1u)) {
-                s_abort = 1;
-                break;
-            }
-            tc_fence_after();
-            float v[TC_HALF];
-            const uint32_t col = (uint32_t)(slot * TC_NT + half * TC_HALF);
-            tmem_ld32(tmem + lane_base + col, v);
-            tmem_ld32(tmem + lane_base + col + 32u, v + 32);
-            tmem_ld_wait();
-            // the values are in registers: hand the accumulator back to the MMA
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[slot]);
-            float s1[NCH];
-#pragma unroll
-            for (int q = 0; q < NCH; ++q) s1[q] = c1[q];
-            PairSteps<TC_PAIRS>::run(v, c1, c2, keymask);
-#pragma unroll
-            for (int q = 0; q < NCH; ++q) cg[q] = c1[q] < s1[q] ? t : cg[q];
-            if (s_abort) break;
+        __syncthreads();
+    }
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TC_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ---------------------------------------------------------------- persistent
+// One CTA per SM loops over the row tiles blockIdx.x, + gridDim.x, ...  The
+// producer also streams each next x tile (one TMA bulk copy of its TC_ROWS x L
+// floats) into a shared FP32 buffer while the current tile's MMAs run; at a
+// tile boundary the epilogue warps convert it (centring, exactness checks) and
+// write the next A operand into tensor memory as soon as the previous tile's
+// MMAs are done (they have consumed its last jobs), and only then finish the
+// previous tile (merge, exact pair distances, certificate), so the tensor pipe
+// starts the next tile while that tail runs.  Codebook tiles stream through
+// a 2-stage ring (the x buffer takes the third stage's space); job and tile
+// counters run across row tiles, so the barriers' phases continue.
+// Needs L % 4 == 0 and a 16-byte aligned X (the launcher checks).
+constexpr int TC_PSTAGES = 2;
+
+template <int LK>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_assign_tc_p(const float *__restrict__ X, int64_t M, int L,
+                  const __nv_bfloat16 *__restrict__ Bp, const float *__restrict__ kn,
+                  const int32_t *n_dev, int n_host, const float *__restrict__ mu,
+                  const float *__restrict__ C, DevState *st, int32_t *__restrict__ assign,
+                  float *__restrict__ e, int32_t *__restrict__ flags, int keymask)
+{
+    if (st->finished) return;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ TcSmem sh;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int N = cur_n(n_dev, n_host);
+    const int ntiles = (N + TC_NT - 1) / TC_NT;
+    const int64_t nrt = (M + TC_ROWS - 1) / TC_ROWS;   // row tiles
+    const int K = (int)((nrt - (int64_t)blockIdx.x + gridDim.x - 1) / gridDim.x);   // this CTA's
+    constexpr int KB = 3 * LK + 16;
+    constexpr int XSTR = LK + 8;
+    constexpr uint32_t sbo_b = (uint32_t)(KB / 8) * 128u;
+    constexpr uint32_t stage_bytes = (uint32_t)TC_NT * KB * 2u;
+    constexpr uint32_t xs_bytes = (uint32_t)TC_ROWS * XSTR * 2u;
+    uint8_t *Bs = smem;
+    __nv_bfloat16 *XS = reinterpret_cast<__nv_bfloat16 *>(smem + TC_PSTAGES * stage_bytes);
+    float *XF = reinterpret_cast<float *>(smem + TC_PSTAGES * stage_bytes + xs_bytes);
+    auto tile_m0 = [&](int k) -> int64_t { return ((int64_t)blockIdx.x + (int64_t)k * gridDim.x) * TC_ROWS; };
+    auto tile_rows = [&](int k) -> int64_t {
+        const int64_t r = M - tile_m0(k);
+        return r < TC_ROWS ? r : TC_ROWS;
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < TC_PSTAGES; ++s) {
+            mbar_init(&sh.full[s], 1);
+            mbar_init(&sh.empty[s], 1);
         }
-        // merge the chains; i1 is the first column of the minimum's pair:
-        // tile * TC_NT + half * TC_HALF + 2 * (the low bits)
-        float V1 = c1[0], V2 = c2[0];
-        int i1 = cg[0] * TC_NT + half * TC_HALF + 2 * (__float_as_int(c1[0]) & JMASK);
-#pragma unroll
-        for (int q = 1; q < NCH; ++q) {
-            const int iq = cg[q] * TC_NT + half * TC_HALF + 2 * (__float_as_int(c1[q]) & JMASK);
-            V2 = fminf(fminf(V2, c2[q]), fmaxf(V1, c1[q]));
-            const bool take = c1[q] < V1 || (c1[q] == V1 && iq < i1);
-            V1 = take ? c1[q] : V1;
-            i1 = take ? iq : i1;
+        for (int b = 0; b < TC_SLOTS; ++b) {
+            mbar_init(&sh.tfull[b], 1);
+            mbar_init(&sh.tempty[b], TC_EPI_WARPS / TC_NACC);
         }
-        // The two halves of a row exchange their top-2 and merge them in the
-        // same fixed order, so both threads hold the same result.
-        s_v1[half][crow] = V1;
-        s_v2[half][crow] = V2;
-        s_i1[half][crow] = i1;
-        named_sync(1, 32 * TC_EPI_WARPS);
-        {
-            const float A1 = s_v1[0][crow], A2 = s_v2[0][crow], B1 = s_v1[1][crow], B2 = s_v2[1][crow];
-            const int ai = s_i1[0][crow], bi = s_i1[1][crow];
-            V2 = fminf(fminf(A2, B2), fmaxf(A1, B1));
-            const bool take = B1 < A1 || (B1 == A1 && bi < ai);
-            V1 = take ? B1 : A1;
-            i1 = take ? bi : ai;
-        }
-        // The minimum is one of the pair (i1, i1 + 1).  Each half computes the
-        // exact FP32 distance of one member.  With L a multiple of 4 the warp
-        // does it cooperatively: a half-warp per row, a float4 of x and of the
-        // codevector per lane (coalesced reads of X and C), each lane sums its
-        // four terms (x_l - c_l)^2 in order, and a butterfly over the 16 lanes
-        // of each half-warp reduces the 16 rows' partial sums at once (a fixed
-        // tree: 15 shuffles per lane); the owner lane of each row takes its sum.
-        const bool usable = m < M && !s_abort && !s_inexact && tc_exact_cb && i1 >= 0 && i1 < N &&
-                            V1 < INFINITY;
-        const int cand = i1 + half;
-        const int ccand = (usable && cand < N) ? cand : -1;
-        const float kc = ccand >= 0 ? __ldg(kn + ccand) : 0.f;
-        float dc = INFINITY;
-        if ((L & 3) == 0 && ((reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(X)) & 15u) == 0) {
-            const int rq = lane & 15, sub = lane >> 4;
-            const int64_t mrow0 = m0 + 128 * acc + 32 * (warp & 3);   // row of lane 0
-            float p[16];
-#pragma unroll
-            for (int bt = 0; bt < 2; ++bt) {                          // two batches of 8 rows
-                int crs[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) crs[k] = __shfl_sync(0xffffffffu, ccand, 2 * (8 * bt + k) + sub);
-                float4 c4[8], x4[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const bool on = crs[k] >= 0 && 4 * rq < L;
-                    const int64_t mr = mrow0 + 2 * (8 * bt + k) + sub;
-                    c4[k] = on ? __ldg(reinterpret_cast<const float4 *>(C + (size_t)crs[k] * L) + rq)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
-                    x4[k] = on ? __ldg(reinterpret_cast<const float4 *>(X + mr * L) + rq)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    float d = __fsub_rn(x4[k].x, c4[k].x);
-                    float q = d * d;
-                    d = __fsub_rn(x4[k].y, c4[k].y);
-                    q = fmaf(d, d, q);
-                    d = __fsub_rn(x4[k].z, c4[k].z);
-                    q = fmaf(d, d, q);
-                    d = __fsub_rn(x4[k].w, c4[k].w);
-                    p[8 * bt + k] = fmaf(d, d, q);
-                }
-            }
-#pragma unroll
-            for (int lvl = 8; lvl >= 1; lvl >>= 1) {
-                const bool up = (rq & lvl) != 0;
-#pragma unroll
-                for (int i = 0; i < lvl; ++i) {
-                    const float send = up ? p[i] : p[i + lvl];
-                    const float keep = up ? p[i + lvl] : p[i];
-                    p[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, lvl));
-                }
-            }
-            // lane (sub, rq) now holds the sum of row 2 rq + sub
-            const float got = __shfl_sync(0xffffffffu, p[0], (lane & 1) * 16 + (lane >> 1));
-            if (ccand >= 0) dc = got;
-        } else if (ccand >= 0) {
-            const float *xr = X + m * L;
-            const float *cr = C + (size_t)ccand * L;
-            float d2 = 0.f;
-            for (int l = 0; l < L; ++l) {
-                const float d = __fsub_rn(__ldg(xr + l), __ldg(cr + l));
-                d2 = fmaf(d, d, d2);
-            }
-            dc = d2;
-        }
-        s_d[half][crow] = dc;
-        s_k[half][crow] = kc;
-        named_sync(2, 32 * TC_EPI_WARPS);
-        if (half == 0 && m < M && !s_abort) {
-            // the smaller distance is taken when the two differ by more than the
-            // rounding bound of the FP32 sum, |fl(d2) - d2| <= (L + 2) u d2 for
-            // any order of the L terms (kept as (L + 4) u); else the row is not
-            // certified
-            bool certified = false;
-            if (usable) {
-                float da = s_d[0][crow], ka = s_k[0][crow];
-                const float db = s_d[1][crow], kb = s_k[1][crow];
-                int ii = i1;
-                bool sure = true;
-                if (i1 + 1 < N) {
-                    const float tol = (float)(L + 4) * U32 * (da + db) * SLOP;
-                    if (db < da - tol) {
-                        ii = i1 + 1;
-                        da = db;
-                        ka = kb;
-                    } else if (!(da < db - tol)) {
-                        sure = false;
+        mbar_init(&sh.xfull, 1);
+        mbar_init(&sh.xempty, 1);
+        mbar_init(&sh.aready, 1);
+        fence_mbar_init();
+        sh.abort = 0;
+        sh.prod_last = -1;
+        sh.mma_tile = -1;
+        sh.mma_job = -1;
+        sh.x_issued = -1;
+        sh.x_done = -1;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(&sh.tmem_base)),
+                     "n"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh.tmem_base;
+    const bool tc_exact_cb = st->tc_inexact == 0;
+    const float cmax = __uint_as_float(st->cmax_bits);
+    const int acc = ((warp - 2) >> 2) & 1;
+    const int half = (warp - 2) >> 3;
+    const int rr = 32 * (warp & 3) + lane;
+    const int crow = 128 * acc + rr;
+    const bool epi = warp >= 2 && warp < 2 + TC_EPI_WARPS;
+
+    if (warp == 0) {
+        // ---------------- producer: x tiles and codebook tiles
+        if (lane == 0 && K > 0) {
+            auto load_x = [&](int k) {
+                const uint32_t bytes = (uint32_t)(tile_rows(k) * L * 4);
+                mbar_expect_tx(&sh.xfull, bytes);
+                bulk_load(XF, X + tile_m0(k) * L, bytes, &sh.xfull);
+                sh.x_issued = k;
+            };
+            load_x(0);
+            for (int k = 0; k < K && !sh.abort; ++k) {
+                for (int t = 0; t < ntiles; ++t) {
+                    const int G = k * ntiles + t, s = G % TC_PSTAGES;
+                    if (G >= TC_PSTAGES &&
+                        !mbar_wait_bounded_sleep(&sh.empty[s], (uint32_t)((G / TC_PSTAGES) - 1) & 1u)) {
+                        sh.abort = 1;
+                        break;
+                    }
+                    if (sh.abort) break;
+                    mbar_expect_tx(&sh.full[s], stage_bytes);
+                    bulk_load(Bs + s * stage_bytes,
+                              reinterpret_cast<const uint8_t *>(Bp) + (size_t)t * stage_bytes, stage_bytes,
+                              &sh.full[s]);
+                    sh.prod_last = G;
+                    if (t == 0 && k + 1 < K) {
+                        // the next x tile once this one has been converted
+                        if (!mbar_wait_bounded_sleep(&sh.xempty, (uint32_t)k & 1u)) {
+                            sh.abort = 1;
+                            break;
+                        }
+                        load_x(k + 1);
                     }
                 }
-                if (sure) {
-                    const double tau = tc_tau(3 * Lk + 16);
-                    const float xn2u = xn2 * SLOP;
-                    const float R = 2.f * (float)tau * xn2u * SLOP;
-                    const float eta = U32 * (sqrtf(xn2u) + cmax) * SLOP;
-                    // index packing of the pair minima, FMA-pipe pair maxima
-                    const float pack = TC_PACK * (fabsf(V1) + fabsf(V2)) + TC_HIERR * (fabsf(V1) + 2.f * fabsf(V2));
-                    // V1 ~ ||x~ - c~_ii||^2 - k' (X2 included): bound g1^2 from above
-                    const float g1sq = V1 + 2.f * ka + R + pack + (float)(L + 2) * U32 * xn2u;
-                    const float g1 = sqrtf(fmaxf(g1sq, 0.f)) * SLOP;
-                    const float margin = (2.f * R + 2.f * ka + pack + 4.f * eta * (g1 + eta)) * SLOP;
-                    certified = (V2 - V1) > margin;
-                }
-                if (certified) {
-                    assign[m] = ii;
-                    e[m] = da;
-                }
             }
-            if (!certified) flags[atomicAdd(&st->nflag, 1)] = (int32_t)m;
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (as in k_assign_tc), per row tile after
+        // its A operand is in tensor memory
+        const uint64_t bdesc0 = smem_desc(smem_addr(Bs), 128u, sbo_b);
+        bool ok = true;
+        for (int k = 0; k < K && ok; ++k) {
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded_sleep(&sh.aready, (uint32_t)k & 1u)) || sh.abort) {
+                ok = false;
+                break;
+            }
+            for (int t = 0; t < ntiles && ok; ++t) {
+                const int G = k * ntiles + t, s = G % TC_PSTAGES;
+                if (!__all_sync(0xffffffffu, mbar_wait_bounded_sleep(&sh.full[s], (uint32_t)(G / TC_PSTAGES) & 1u))) {
+                    ok = false;
+                    break;
+                }
+                const uint64_t bst = bdesc0 + ((uint64_t)(s * stage_bytes) >> 4);
+#pragma unroll
+                for (int a = 0; a < TC_NACC; ++a) {
+                    const int j = 2 * G + a, slot = j % TC_SLOTS;
+                    if ((j >= TC_SLOTS &&
+                         !__all_sync(0xffffffffu, mbar_wait_bounded_sleep(&sh.tempty[slot], (uint32_t)((j / TC_SLOTS) - 1) & 1u))) ||
+                        sh.abort) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tmem + (uint32_t)(slot * TC_NT);
+                    const uint32_t at = tmem + (uint32_t)(TC_A_COL + a * ((LK + 16) / 2));
+#pragma unroll
+                    for (int seg = 0; seg < 3; ++seg)
+#pragma unroll
+                        for (int kk = 0; kk < LK / 16; ++kk)
+                            mma_bf16_ta_elect(d, at + (uint32_t)(8 * kk), bst + (uint64_t)(seg * LK + kk * 16),
+                                              (seg | kk) ? 1u : 0u);
+                    mma_bf16_ta_elect(d, at + (uint32_t)(LK / 2), bst + (uint64_t)(3 * LK), 1u);
+                    mma_commit_elect(&sh.tfull[slot]);
+                    if (lane == 0) sh.mma_job = j;
+                }
+                if (!ok) break;
+                mma_commit_elect(&sh.empty[s]);
+                if (lane == 0) sh.mma_tile = G;
+            }
+        }
+        if (!ok && lane == 0) sh.abort = 1;
+        __syncwarp();
+    } else if (epi) {
+        // ---------------- epilogue warps.  Every warp passes the same named
+        // barriers in the same order for every k, also after a time-out (work
+        // is skipped, barriers are not).
+        constexpr int ST = 32 * TC_EPI_WARPS;
+        const int et = tid - 64;
+        float pV1 = INFINITY, pV2 = INFINITY, pxn2 = 0.f;
+        int pi1 = -1;
+        bool pusable = false;
+        for (int k = 0; k <= K; ++k) {
+            float xn2 = 0.f;
+            bool tile_exact = false;
+            if (k < K) {
+                // convert the x tile (it is in XF) into centred BF16 rows
+                bool inexact = false, bad = false;
+                if (!sh.abort && !mbar_wait_bounded_sleep(&sh.xfull, (uint32_t)k & 1u)) sh.abort = 1;
+                if (!sh.abort) {
+                    const int total4 = (int)(tile_rows(k) * L) >> 2;
+                    const float4 *X4 = reinterpret_cast<const float4 *>(XF);
+                    for (int i = et; i < total4; i += ST) {
+                        const float4 q = X4[i];
+                        tc_put_x(XS, XSTR, 4 * i, L, q.x, mu, bad, inexact);
+                        tc_put_x(XS, XSTR, 4 * i + 1, L, q.y, mu, bad, inexact);
+                        tc_put_x(XS, XSTR, 4 * i + 2, L, q.z, mu, bad, inexact);
+                        tc_put_x(XS, XSTR, 4 * i + 3, L, q.w, mu, bad, inexact);
+                    }
+                }
+                if (bad) flag_error(st, ERR_NONFINITE);
+                tile_exact = !named_sync_or(1, 32 * TC_EPI_WARPS, inexact);
+                if (tid == 64) {
+                    mbar_arrive(&sh.xempty);   // XF may take the next x tile
+                    sh.x_done = k;
+                }
+                // all 16 warps consumed the previous tile's last jobs, so its
+                // MMAs are done and A may be rewritten
+                xn2 = tc_write_a<LK>(XS, L, tile_m0(k) + crow < M, crow, half, acc, warp, tmem, sh);
+                tc_fence_before();
+                named_sync(1, 32 * TC_EPI_WARPS);
+                if (tid == 64) mbar_arrive(&sh.aready);
+            }
+            if (k >= 1)
+                tc_tail<LK>(sh, warp, lane, acc, half, rr, tile_m0(k - 1), X, M, L, N, C, kn, pxn2, pusable,
+                            cmax, pV1, pV2, pi1, st, assign, e, flags);
+            if (k < K) {
+                tc_jobs(sh, tmem, warp, lane, acc, half, ntiles, 2 * k * ntiles, keymask, pV1, pV2, pi1);
+                pxn2 = xn2;
+                pusable = tile_exact && tc_exact_cb;
+            }
         }
     }
 
     tc_fence_before();
     __syncthreads();
-    if (s_abort) {
-        // Stop: wait (bounded) for the bulk copies nobody consumed and for the
-        // last committed MMAs, then free TMEM below.
+    if (sh.abort) {
+        // Stop: wait (bounded) for the copies nobody consumed and for the last
+        // committed MMAs, then free TMEM below.
         if (tid == 0) {
-            for (int t = s_mma_tile + 1; t <= s_prod_last; ++t)
-                (void)mbar_wait_bounded(&full[t % TC_STAGES], (uint32_t)(t / TC_STAGES) & 1u);
-            if (s_mma_job >= 0)
-                (void)mbar_wait_bounded(&tfull[s_mma_job % TC_SLOTS], (uint32_t)(s_mma_job / TC_SLOTS) & 1u);
+            for (int G = sh.mma_tile + 1; G <= sh.prod_last; ++G)
+                (void)mbar_wait_bounded(&sh.full[G % TC_PSTAGES], (uint32_t)(G / TC_PSTAGES) & 1u);
+            for (int k = sh.x_done + 1; k <= sh.x_issued; ++k)
+                (void)mbar_wait_bounded(&sh.xfull, (uint32_t)k & 1u);
+            if (sh.mma_job >= 0)
+                (void)mbar_wait_bounded(&sh.tfull[sh.mma_job % TC_SLOTS], (uint32_t)(sh.mma_job / TC_SLOTS) & 1u);
             flag_error(st, ERR_TIMEOUT);
         }
         __syncthreads();
@@ -858,15 +1153,28 @@ static void launch_tc(const float *X, int64_t M, int L, const void *Bp, const fl
                       const int32_t *n_dev, int n_host, const float *mu, const float *C, DevState *st,
                       int32_t *assign, float *e, int32_t *flags, cudaStream_t s)
 {
+    const int64_t grid = (M + TC_ROWS - 1) / TC_ROWS;
+    if (grid == 0) return;
+    const int keymask = ~((1 << TC_JBITS) - 1);
+    const __nv_bfloat16 *B = static_cast<const __nv_bfloat16 *>(Bp);
+    if ((L & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) {
+        // persistent: 2 codebook stages + staged BF16 rows + the FP32 x tile
+        const size_t need = (size_t)TC_PSTAGES * TC_NT * (3 * LK + 16) * 2 + (size_t)TC_ROWS * (LK + 8) * 2 +
+                            (size_t)TC_ROWS * LK * 4;
+        // at least 120 KB so that a single CTA (and its 512 TMEM columns) owns the SM
+        const size_t smem = need > 120 * 1024 ? need : 120 * 1024;
+        cudaFuncSetAttribute(k_assign_tc_p<LK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int64_t g = grid < 152 ? grid : 152;
+        k_assign_tc_p<LK><<<(unsigned)g, TC_THREADS, smem, s>>>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign,
+                                                               e, flags, keymask);
+        return;
+    }
     const size_t need = (size_t)TC_ROWS * (LK + 8) * 2 + (size_t)TC_STAGES * TC_NT * (3 * LK + 16) * 2;
     // at least 120 KB so that a single CTA (and its 512 TMEM columns) owns the SM
     const size_t smem = need > 120 * 1024 ? need : 120 * 1024;
     cudaFuncSetAttribute(k_assign_tc<LK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int64_t grid = (M + TC_ROWS - 1) / TC_ROWS;
-    if (grid == 0) return;
-    k_assign_tc<LK><<<(unsigned)grid, TC_THREADS, smem, s>>>(
-        X, M, L, static_cast<const __nv_bfloat16 *>(Bp), kn, n_dev, n_host, mu, C, st, assign, e, flags,
-        ~((1 << TC_JBITS) - 1));
+    k_assign_tc<LK><<<(unsigned)grid, TC_THREADS, smem, s>>>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign,
+                                                             e, flags, keymask);
 }
 
 void launch_assign_tc(const float *X, int64_t M, int L, const void *Bp, const float *kn,
