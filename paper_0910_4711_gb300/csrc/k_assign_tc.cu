@@ -485,9 +485,16 @@ __device__ __forceinline__ float tc_write_a(const __nv_bfloat16 *XS, int L, bool
 // The epilogue of one row tile: for each codebook tile t, job j0 + 2t + acc
 // (accumulator slot (j0 + 2t + acc) % 3); the thread's 64 values per job go
 // through the pair top-2; returns the merged (V1, V2, pair index) of the
-// thread's half.  Stops at a time-out (sh.abort set).
+// thread's half.  hook(t) runs after job t in every epilogue warp (it may use
+// named barriers: after a time-out, sh.abort, the jobs are skipped but the
+// hooks still run).
+struct NoHook {
+    __device__ __forceinline__ void operator()(int) const {}
+};
+template <class Hook = NoHook>
 __device__ __forceinline__ void tc_jobs(TcSmem &sh, uint32_t tmem, int warp, int lane, int acc, int half,
-                                        int ntiles, int j0, int keymask, float &V1, float &V2, int &i1)
+                                        int ntiles, int j0, int keymask, float &V1, float &V2, int &i1,
+                                        const Hook &hook = Hook())
 {
     constexpr int NCH = 4;   // independent min-chains
     constexpr int JMASK = (1 << TC_JBITS) - 1;
@@ -501,11 +508,11 @@ __device__ __forceinline__ void tc_jobs(TcSmem &sh, uint32_t tmem, int warp, int
     }
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
     for (int t = 0; t < ntiles; ++t) {
-        if (sh.abort) break;
         const int j = j0 + 2 * t + acc, slot = j % TC_SLOTS;
-        if (!mbar_wait_bounded_sleep(&sh.tfull[slot], (uint32_t)(j / TC_SLOTS) & 1u)) {
+        if (sh.abort || !mbar_wait_bounded_sleep(&sh.tfull[slot], (uint32_t)(j / TC_SLOTS) & 1u)) {
             sh.abort = 1;
-            break;
+            hook(t);
+            continue;
         }
         tc_fence_after();
         float v[TC_HALF];
@@ -523,6 +530,7 @@ __device__ __forceinline__ void tc_jobs(TcSmem &sh, uint32_t tmem, int warp, int
         PairSteps<TC_PAIRS>::run(v, c1, c2, keymask);
 #pragma unroll
         for (int q = 0; q < NCH; ++q) cg[q] = c1[q] < s1[q] ? t : cg[q];
+        hook(t);
     }
     // merge the chains; i1 is the first column of the minimum's pair:
     // tile * TC_NT + half * TC_HALF + 2 * (the low bits)
@@ -968,13 +976,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 0) {
         // ---------------- producer: x tiles and codebook tiles
         if (lane == 0 && K > 0) {
-            auto load_x = [&](int k) {
-                const uint32_t bytes = (uint32_t)(tile_rows(k) * L * 4);
+            // x tile kx into XF once x tile kx - 1 has been converted; never after
+            // a time-out (sh.x_issued counts the copies for the drain below)
+            auto load_x = [&](int kx) -> bool {
+                if (kx < 1 || kx >= K || kx <= sh.x_issued) return true;
+                if (!mbar_wait_bounded_sleep(&sh.xempty, (uint32_t)(kx - 1) & 1u) || sh.abort) {
+                    sh.abort = 1;
+                    return false;
+                }
+                const uint32_t bytes = (uint32_t)(tile_rows(kx) * L * 4);
                 mbar_expect_tx(&sh.xfull, bytes);
-                bulk_load(XF, X + tile_m0(k) * L, bytes, &sh.xfull);
-                sh.x_issued = k;
+                bulk_load(XF, X + tile_m0(kx) * L, bytes, &sh.xfull);
+                sh.x_issued = kx;
+                return true;
             };
-            load_x(0);
+            {   // x tile 0
+                const uint32_t bytes = (uint32_t)(tile_rows(0) * L * 4);
+                mbar_expect_tx(&sh.xfull, bytes);
+                bulk_load(XF, X + tile_m0(0) * L, bytes, &sh.xfull);
+                sh.x_issued = 0;
+            }
             for (int k = 0; k < K && !sh.abort; ++k) {
                 for (int t = 0; t < ntiles; ++t) {
                     const int G = k * ntiles + t, s = G % TC_PSTAGES;
@@ -989,14 +1010,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                               reinterpret_cast<const uint8_t *>(Bp) + (size_t)t * stage_bytes, stage_bytes,
                               &sh.full[s]);
                     sh.prod_last = G;
-                    if (t == 0 && k + 1 < K) {
-                        // the next x tile once this one has been converted
-                        if (!mbar_wait_bounded_sleep(&sh.xempty, (uint32_t)k & 1u)) {
-                            sh.abort = 1;
-                            break;
-                        }
-                        load_x(k + 1);
-                    }
+                    // x tile k + 1 as soon as x tile k has been converted (at tile k's
+                    // boundary); it lands during tile k's MMAs
+                    if (t == 0 && !load_x(k + 1)) break;
                 }
             }
         }
@@ -1051,36 +1067,79 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // barriers in the same order for every k, also after a time-out (work
         // is skipped, barriers are not).
         constexpr int ST = 32 * TC_EPI_WARPS;
+        constexpr int NCHUNK = 1;   // the x tile is converted in one piece at the boundary
         const int et = tid - 64;
         float pV1 = INFINITY, pV2 = INFINITY, pxn2 = 0.f;
         int pi1 = -1;
-        bool pusable = false;
+        bool pusable = false, next_exact = false;
+        bool cv_bad = false, cv_inexact = false;
+        // Convert piece c (of NCHUNK) of x tile kk from XF into centred BF16
+        // rows in XS; the last piece publishes the tile's exactness and frees XF.
+        auto convert = [&](int kk, int c) {
+            if (c == 0) {
+                cv_bad = false;
+                cv_inexact = false;
+                if (!sh.abort) {
+                    if (!mbar_wait_bounded_sleep(&sh.xfull, (uint32_t)kk & 1u)) sh.abort = 1;
+                    else if (tid == 64) sh.x_done = kk;   // xfull phases observed: 0 .. kk
+                }
+            }
+            if (!sh.abort) {
+                const int total4 = (int)(tile_rows(kk) * L) >> 2;
+                const int per = (total4 + NCHUNK - 1) / NCHUNK;
+                const int lo = c * per, hi = min(total4, lo + per);
+                const float4 *X4 = reinterpret_cast<const float4 *>(XF);
+                if ((4 * ST) % L == 0) {
+                    // L divides 4 ST: a thread's four columns are the same in every
+                    // round, so mu is read once and rows advance by 4 ST / L
+                    const int i0 = lo + et;
+                    const int l0 = (4 * i0) % L, dr = 4 * ST / L;
+                    const float4 m4 = make_float4(__ldg(mu + l0), __ldg(mu + l0 + 1), __ldg(mu + l0 + 2),
+                                                  __ldg(mu + l0 + 3));
+                    int r = (4 * i0) / L;
+                    for (int i = i0; i < hi; i += ST, r += dr) {
+                        const float4 q = X4[i];
+                        const float xv[4] = {q.x, q.y, q.z, q.w};
+                        const float mv[4] = {m4.x, m4.y, m4.z, m4.w};
+                        uint32_t bits[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            cv_bad = cv_bad || !isfinite(xv[u]);
+                            const float v = __fsub_rn(xv[u], mv[u]);
+                            const float bb = __fsub_rn(v, xv[u]);
+                            const float err = __fadd_rn(__fsub_rn(xv[u], __fsub_rn(v, bb)), __fsub_rn(-mv[u], bb));
+                            const __nv_bfloat16 b = __float2bfloat16_rn(v);
+                            cv_inexact = cv_inexact || err != 0.f || (__bfloat162float(b) != v);
+                            bits[u] = __bfloat16_as_ushort(b);
+                        }
+                        *reinterpret_cast<uint2 *>(XS + r * XSTR + l0) =
+                            make_uint2(bits[0] | (bits[1] << 16), bits[2] | (bits[3] << 16));
+                    }
+                } else {
+                    for (int i = lo + et; i < hi; i += ST) {
+                        const float4 q = X4[i];
+                        tc_put_x(XS, XSTR, 4 * i, L, q.x, mu, cv_bad, cv_inexact);
+                        tc_put_x(XS, XSTR, 4 * i + 1, L, q.y, mu, cv_bad, cv_inexact);
+                        tc_put_x(XS, XSTR, 4 * i + 2, L, q.z, mu, cv_bad, cv_inexact);
+                        tc_put_x(XS, XSTR, 4 * i + 3, L, q.w, mu, cv_bad, cv_inexact);
+                    }
+                }
+            }
+            if (c == NCHUNK - 1) {
+                if (cv_bad) flag_error(st, ERR_NONFINITE);
+                next_exact = !named_sync_or(1, 32 * TC_EPI_WARPS, cv_inexact);
+                if (tid == 64 && !sh.abort) mbar_arrive(&sh.xempty);   // XF may take the next x tile
+            }
+        };
         for (int k = 0; k <= K; ++k) {
             float xn2 = 0.f;
             bool tile_exact = false;
             if (k < K) {
-                // convert the x tile (it is in XF) into centred BF16 rows
-                bool inexact = false, bad = false;
-                if (!sh.abort && !mbar_wait_bounded_sleep(&sh.xfull, (uint32_t)k & 1u)) sh.abort = 1;
-                if (!sh.abort) {
-                    const int total4 = (int)(tile_rows(k) * L) >> 2;
-                    const float4 *X4 = reinterpret_cast<const float4 *>(XF);
-                    for (int i = et; i < total4; i += ST) {
-                        const float4 q = X4[i];
-                        tc_put_x(XS, XSTR, 4 * i, L, q.x, mu, bad, inexact);
-                        tc_put_x(XS, XSTR, 4 * i + 1, L, q.y, mu, bad, inexact);
-                        tc_put_x(XS, XSTR, 4 * i + 2, L, q.z, mu, bad, inexact);
-                        tc_put_x(XS, XSTR, 4 * i + 3, L, q.w, mu, bad, inexact);
-                    }
-                }
-                if (bad) flag_error(st, ERR_NONFINITE);
-                tile_exact = !named_sync_or(1, 32 * TC_EPI_WARPS, inexact);
-                if (tid == 64) {
-                    mbar_arrive(&sh.xempty);   // XF may take the next x tile
-                    sh.x_done = k;
-                }
-                // all 16 warps consumed the previous tile's last jobs, so its
-                // MMAs are done and A may be rewritten
+                // convert x tile k (it is in XF) into centred BF16 rows; then, all 16
+                // warps having consumed the previous tile's last jobs (before the
+                // conversion's named barrier), its MMAs are done and A may be rewritten
+                for (int c = 0; c < NCHUNK; ++c) convert(k, c);
+                tile_exact = next_exact;
                 xn2 = tc_write_a<LK>(XS, L, tile_m0(k) + crow < M, crow, half, acc, warp, tmem, sh);
                 tc_fence_before();
                 named_sync(1, 32 * TC_EPI_WARPS);
@@ -1105,6 +1164,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (tid == 0) {
             for (int G = sh.mma_tile + 1; G <= sh.prod_last; ++G)
                 (void)mbar_wait_bounded(&sh.full[G % TC_PSTAGES], (uint32_t)(G / TC_PSTAGES) & 1u);
+            // x copies are issued in tile order and complete xfull's phases in
+            // that order: wait for every issued copy past the last phase observed
             for (int k = sh.x_done + 1; k <= sh.x_issued; ++k)
                 (void)mbar_wait_bounded(&sh.xfull, (uint32_t)k & 1u);
             if (sh.mma_job >= 0)
