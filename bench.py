@@ -7,7 +7,11 @@ splitting to N = 4096 (delta = 0.01, theta = 1e-3).
 A *step* is one Lloyd pass through the C ABI (``lbg_lloyd_step``): cell
 allocation of all M rows against the trained N = 4096 codebook, integration
 of the distortion, cell table and centroid update -- every kernel of the hot
-path.  ``value`` = M * N distance evaluations / device time per step.
+path.  ``value`` = M * N distance evaluations / device time per step, the
+steps enqueued back to back (the call's asynchronous form: its graph is
+replayed and D, n_exact and the status land in a device buffer).
+``phase_ms`` and the roofline's kernel time come from as many directly
+launched steps right after the timed ones (per-phase CUDA events).
 
 Other legs in the same run:
 * full LBG design time (``lbg_train`` from the centroid to N = 4096);
@@ -404,11 +408,16 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def timed_steps(prec, steps, clocks=None):
+        """`steps` passes enqueued back to back (replayed graphs, each reporting
+        D / n_exact / status into a device buffer, no host wait in between), L2
+        flushed before each; then as many directly launched passes with
+        per-phase CUDA events (same inputs, same flush) for the phase breakdown
+        and the nearest-codevector kernel's time."""
+        buf = lbg.step_result_buffer()
         for _ in range(max(3, args.warmup)):
             flush.zero_()
-            lbg.lbg_lloyd_step(X, C, C_out=C_out, assign_out=A, phase_ms=True, precision=prec)
+            lbg.lbg_lloyd_step(X, C, C_out=C_out, assign_out=A, precision=prec, result_out=buf)
         torch.cuda.synchronize()
-        phases, n_exact = [], []
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         barrier(dist)
@@ -418,17 +427,24 @@ def run_ours(args):
         for k in range(steps):
             flush.zero_()
             starts[k].record(stream)
-            r = lbg.lbg_lloyd_step(X, C, C_out=C_out, assign_out=A, phase_ms=True, precision=prec)
+            lbg.lbg_lloyd_step(X, C, C_out=C_out, assign_out=A, precision=prec, result_out=buf)
             ends[k].record(stream)
-            phases.append(r.phase_ms)
-            n_exact.append(r.n_exact)
         torch.cuda.synchronize()
         wall = time.perf_counter() - w0
         torch.cuda.nvtx.range_pop()
         barrier(dist)
         ms = max_over_ranks(dist, statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends)))
-        ph = {k: statistics.mean(p[k] for p in phases) for k in ("prep", "assign", "exact", "update")}
-        return ms, ph, statistics.mean(n_exact), wall
+        _, n_exact, status = lbg.read_step_result(buf)
+        if status != 0:
+            raise RuntimeError(f"device status {status} in the timed passes")
+        phases = []
+        for _ in range(steps):
+            flush.zero_()
+            phases.append(lbg.lbg_lloyd_step(X, C, C_out=C_out, assign_out=A, phase_ms=True,
+                                             precision=prec).phase_ms)
+        ph = {k: statistics.mean(p[k] for p in phases)
+              for k in ("prep", "assign", "exact", "update", "total")}
+        return ms, ph, n_exact, wall
 
     with ClockSampler(gpu_uuid(dev)) as clk:
         ms, ph, n_exact, wall = timed_steps(args.precision, args.steps)
@@ -502,7 +518,7 @@ def run_ours(args):
                                         "write codebook, counts)",
                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"},
             "clocks": clocks,
-            "gpu_launches": (12 if args.precision == "bf16" else 11) * args.steps}
+            "gpu_launches": (14 if args.precision == "bf16" else 13) * args.steps}
     if other_line is not None:
         line["other_precision"] = other_line
 

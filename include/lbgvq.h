@@ -107,6 +107,15 @@ typedef struct lbg_tune_report {
                                      their final codebook sizes, per candidate (best of 2) */
 } lbg_tune_report;
 
+/* Device-side report of an enqueued lbg_lloyd_step / vq_encode (see
+ * lbg_opts.result_dev).  Written by the last launch of the call. */
+typedef struct lbg_step_result {
+    double D;                     /* sum of the minimum squared distances */
+    int32_t n_exact;              /* rows re-scored exactly */
+    int32_t status;               /* lbg_status of the device work: LBG_OK,
+                                     LBG_ERR_NONFINITE, LBG_ERR_TIMEOUT or LBG_ERR_CUDA */
+} lbg_step_result;
+
 typedef struct lbg_opts {
     int32_t precision;          /* lbg_precision; default LBG_PREC_FP32 */
     int32_t max_passes;         /* per stage (lbg_train); <= 0 means 1000 */
@@ -134,10 +143,19 @@ typedef struct lbg_opts {
     int32_t ctas_per_sm;        /* lbg_train_batched: force 1, 2 or 4 (0: autotune; 4 needs
                                    64-row tiles) */
     lbg_tune_report *tune_report; /* host out for lbg_train_batched, or NULL */
+    lbg_step_result *result_dev;  /* lbg_lloyd_step / vq_encode: DEVICE out, or NULL.  Non-NULL
+                                     makes the call asynchronous: it validates, enqueues the
+                                     pass on `stream` and returns without waiting; *result_dev
+                                     receives D, n_exact and the device status when the stream
+                                     reaches the end of the pass.  Every array must then be
+                                     device memory of the current device, and the host outs
+                                     (D, n_exact, phase_ms) must be NULL (else LBG_ERR_ARG).
+                                     Later calls of this library on any stream of the device
+                                     wait for the enqueued pass before touching its scratch. */
 } lbg_opts;
 
 /* Fill *opts with the defaults (FP32, 1000 passes, default stream, no trace,
- * autotuned batched tiles). */
+ * autotuned batched tiles, synchronous calls). */
 void lbg_opts_init(lbg_opts *opts);
 
 /*
@@ -177,6 +195,10 @@ lbg_status lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double del
  *          May alias C_in.
  *   assign [M] out, nullable: nearest codevector of every row under C_in.
  *   D      host out, nullable: sum of the minimum distances under C_in.
+ * The device work of a call depends only on its device pointers, sizes and
+ * options; it is recorded once into a CUDA graph under that key and replayed
+ * by later calls with the same key (phase_ms calls launch directly, so that
+ * the phases can be timed).  With opts->result_dev the call only enqueues.
  */
 lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N,
                           const float *C_in, float *C_out, int32_t *assign, double *D,
@@ -191,6 +213,8 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N,
  *   idx   [M] out: index of the nearest codevector.
  *   Xhat  [M x L] out, nullable: the decoded vectors C[idx[m]].
  *   D     host out, nullable: sum of the squared distances.
+ * Replayed from a recorded CUDA graph and optionally asynchronous, as
+ * lbg_lloyd_step (with opts->result_dev, D is always computed).
  */
 lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32_t N,
                      int32_t *idx, float *Xhat, double *D, const lbg_opts *opts);

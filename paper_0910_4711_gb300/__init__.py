@@ -5,8 +5,9 @@ The computation runs in the CUDA library ``_lib/liblbgvq.so`` (C ABI in
 arguments to it.  Build it with :func:`paper_0910_4711_gb300.build.build`.
 """
 from ._binding import (EXPORTS, LBGError, LIB_PATH, distortion_backward, lbg_lloyd_step, lbg_train,
-                       lbg_train_batched, lib, release_workspace, version, vq_encode)
+                       lbg_train_batched, lib, read_step_result, release_workspace, step_result_buffer,
+                       version, vq_encode)
 
 __all__ = ["lbg_train", "lbg_train_batched", "lbg_lloyd_step", "vq_encode", "distortion_backward",
-           "release_workspace",
+           "release_workspace", "step_result_buffer", "read_step_result",
            "version", "lib", "LBGError", "LIB_PATH", "EXPORTS"]

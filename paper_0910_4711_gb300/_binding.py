@@ -64,7 +64,28 @@ class Opts(ctypes.Structure):
                 ("split_multiplicative", ctypes.c_int32), ("reseed_empty", ctypes.c_int32),
                 ("delta_reseed", ctypes.c_double), ("autotune", ctypes.c_int32),
                 ("tile_rows", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("tune_report", ctypes.POINTER(TuneReport))]
+                ("tune_report", ctypes.POINTER(TuneReport)),
+                ("result_dev", ctypes.c_void_p)]
+
+
+STEP_RESULT_BYTES = 16   # lbg_step_result: double D, int32 n_exact, int32 status
+
+
+def step_result_buffer(device=None):
+    """A zeroed device buffer for an asynchronous step / encode report
+    (lbg_step_result, 16 bytes)."""
+    import torch
+    return torch.zeros(STEP_RESULT_BYTES, dtype=torch.uint8,
+                       device=device if device is not None else "cuda")
+
+
+def read_step_result(buf):
+    """(D, n_exact, status) of a report written by an asynchronous call (waits
+    for the stream that wrote it, through the device-to-host copy)."""
+    raw = np.ascontiguousarray(buf.detach().cpu().numpy()).view(np.uint8)[:STEP_RESULT_BYTES]
+    D = float(raw[:8].view(np.float64)[0])
+    n_exact, status = (int(v) for v in raw[8:16].view(np.int32))
+    return D, n_exact, status
 
 
 _lock = threading.Lock()
@@ -146,7 +167,7 @@ PRECISION = {"fp32": 0, "bf16": 1}
 
 
 def _opts(cuda_ref, max_passes=1000, records=0, phase=False, stream=None, precision="fp32",
-          split_multiplicative=False, reseed_empty=False, delta_reseed=0.0):
+          split_multiplicative=False, reseed_empty=False, delta_reseed=0.0, result=None):
     o = Opts()
     lib().lbg_opts_init(ctypes.byref(o))
     o.max_passes = int(max_passes)
@@ -171,8 +192,15 @@ def _opts(cuda_ref, max_passes=1000, records=0, phase=False, stream=None, precis
     if phase:
         keep["ph"] = (ctypes.c_float * 5)()
         o.phase_ms = ctypes.cast(keep["ph"], ctypes.POINTER(ctypes.c_float))
-    keep["nex"] = ctypes.c_int32(0)
-    o.n_exact = ctypes.pointer(keep["nex"])
+    keep["nex"] = ctypes.c_int32(-1)
+    if result is not None:
+        if not (_is_torch(result) and result.is_cuda and result.is_contiguous()
+                and result.numel() * result.element_size() >= STEP_RESULT_BYTES):
+            raise ValueError("result must be a contiguous CUDA tensor of >= 16 bytes "
+                             "(see step_result_buffer)")
+        o.result_dev = ctypes.c_void_p(result.data_ptr())
+    else:
+        o.n_exact = ctypes.pointer(keep["nex"])
     return o, keep
 
 
@@ -213,9 +241,10 @@ class StepResult:
     status: int
     C: object
     assign: object
-    D: float
-    n_exact: int
+    D: float            # nan for an asynchronous call (read its report instead)
+    n_exact: int        # -1 for an asynchronous call
     phase_ms: dict | None
+    result: object = None   # the device report buffer of an asynchronous call
 
 
 @dataclass
@@ -223,9 +252,10 @@ class EncodeResult:
     status: int
     idx: object
     Xhat: object
-    D: float
-    n_exact: int
+    D: float            # nan for an asynchronous call or with_distortion=False
+    n_exact: int        # -1 for an asynchronous call
     phase_ms: dict | None
+    result: object = None   # the device report buffer of an asynchronous call
 
 
 # ------------------------------------------------------------ entry points
@@ -260,8 +290,10 @@ def lbg_train(X, N: int, delta: float = 0.01, theta: float = 1e-3, C_init=None,
 
 def lbg_lloyd_step(X, C_in, C_out=None, assign_out=None, phase_ms: bool = False,
                    stream=None, precision: str = "fp32", reseed_empty: bool = False,
-                   delta_reseed: float = 0.01) -> StepResult:
-    """One Lloyd pass from C_in (see lbg_lloyd_step in lbgvq.h)."""
+                   delta_reseed: float = 0.01, result_out=None) -> StepResult:
+    """One Lloyd pass from C_in (see lbg_lloyd_step in lbgvq.h).  With result_out (a
+    step_result_buffer) the pass is only enqueued on the stream: D, n_exact and the
+    device status land in result_out (read_step_result)."""
     Xo, xp, _ = _prep(X, "f32", "X")
     M, L = int(X.shape[0]), int(X.shape[1])
     N = int(C_in.shape[0])
@@ -271,15 +303,19 @@ def lbg_lloyd_step(X, C_in, C_out=None, assign_out=None, phase_ms: bool = False,
     A = assign_out if assign_out is not None else _empty_like_src(X, (M,), "i32")
     A, ap, _ = _prep(A, "i32", "assign")
     o, keep = _opts(_cuda_ref(X, C_in, Co, A), stream=stream, phase=phase_ms, precision=precision,
-                    reseed_empty=reseed_empty, delta_reseed=delta_reseed)
+                    reseed_empty=reseed_empty, delta_reseed=delta_reseed, result=result_out)
+    if result_out is not None:
+        rc = _check(lib().lbg_lloyd_step(xp, M, L, N, cip, cop, ap, None, ctypes.byref(o)))
+        return StepResult(rc, Co, A, float("nan"), -1, None, result_out)
     D = ctypes.c_double(0.0)
     rc = _check(lib().lbg_lloyd_step(xp, M, L, N, cip, cop, ap, ctypes.byref(D), ctypes.byref(o)))
     return StepResult(rc, Co, A, D.value, keep["nex"].value, _phases(keep))
 
 
 def vq_encode(X, C, decode: bool = False, with_distortion: bool = True, phase_ms: bool = False,
-              idx_out=None, stream=None, precision: str = "fp32") -> EncodeResult:
-    """Nearest codevector of every row of X (see vq_encode in lbgvq.h)."""
+              idx_out=None, stream=None, precision: str = "fp32", result_out=None) -> EncodeResult:
+    """Nearest codevector of every row of X (see vq_encode in lbgvq.h).  With result_out
+    (a step_result_buffer) the call is only enqueued, as for lbg_lloyd_step."""
     Xo, xp, _ = _prep(X, "f32", "X")
     M, L = int(X.shape[0]), int(X.shape[1])
     N = int(C.shape[0])
@@ -288,7 +324,11 @@ def vq_encode(X, C, decode: bool = False, with_distortion: bool = True, phase_ms
     I, ip, _ = _prep(I, "i32", "idx")
     H = _empty_like_src(X, (M, L), "f32") if decode else None
     H, hp, _ = _prep(H, "f32", "Xhat")
-    o, keep = _opts(_cuda_ref(X, C, I), stream=stream, phase=phase_ms, precision=precision)
+    o, keep = _opts(_cuda_ref(X, C, I), stream=stream, phase=phase_ms, precision=precision,
+                    result=result_out)
+    if result_out is not None:
+        rc = _check(lib().vq_encode(xp, M, L, cp, N, ip, hp, None, ctypes.byref(o)))
+        return EncodeResult(rc, I, H, float("nan"), -1, None, result_out)
     D = ctypes.c_double(0.0)
     rc = _check(lib().vq_encode(xp, M, L, cp, N, ip, hp, ctypes.byref(D) if with_distortion else None,
                                 ctypes.byref(o)))

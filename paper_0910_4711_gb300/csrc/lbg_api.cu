@@ -25,6 +25,11 @@ struct Workspace {
 
 std::mutex g_mu;
 Workspace g_ws[MAX_DEVICES];
+// Recorded at the end of every asynchronous call's device work; every call
+// makes its stream wait for it before touching the workspace.
+cudaEvent_t g_ws_done[MAX_DEVICES];
+
+void seq_clear(int dev);
 
 // Byte offsets of the scratch arrays of one call inside the workspace.
 struct Plan {
@@ -126,6 +131,7 @@ lbg_status ensure_workspace(Call &c, size_t bytes)
     if (w.bytes < bytes) {
         if (w.base) {
             CK(cudaDeviceSynchronize());
+            seq_clear(c.dev);
             cudaFree(w.base);
             w.base = nullptr;
             w.bytes = 0;
@@ -172,6 +178,15 @@ lbg_status begin(Call &c, const lbg_opts &o)
     CK(cudaGetDevice(&c.dev));
     if (c.dev < 0 || c.dev >= MAX_DEVICES) return LBG_ERR_UNSUPPORTED;
     c.s = static_cast<cudaStream_t>(o.stream);
+    if (g_ws_done[c.dev]) CK(cudaStreamWaitEvent(c.s, g_ws_done[c.dev], 0));
+    return LBG_OK;
+}
+
+// Marks the workspace busy until the work enqueued so far on c.s is done.
+lbg_status end_async(const Call &c)
+{
+    if (!g_ws_done[c.dev]) CK(cudaEventCreateWithFlags(&g_ws_done[c.dev], cudaEventDisableTiming));
+    CK(cudaEventRecord(g_ws_done[c.dev], c.s));
     return LBG_OK;
 }
 
@@ -218,6 +233,30 @@ void init_state(DevState &h, int n_cur)
     memset(&h, 0, sizeof(h));
     h.n_cur = n_cur;
     h.D_prev = INFINITY;
+}
+
+// Device-side start of a step / encode: the initial DevState (as init_state).
+__global__ void k_state_init(DevState *st, int n_cur)
+{
+    DevState h = {};
+    h.n_cur = n_cur;
+    h.D_prev = INFINITY;
+    *st = h;
+}
+
+// Device-side report of an asynchronous step / encode (finish_status without
+// the max_passes warning, which only lbg_train raises).
+__global__ void k_step_report(const DevState *st, lbg_step_result *r, int use_last)
+{
+    const uint32_t err = st->err;
+    lbg_step_result o;
+    o.D = st->D;
+    o.n_exact = use_last ? st->n_exact_last : st->nflag;
+    o.status = (err & ERR_NONFINITE)  ? LBG_ERR_NONFINITE
+               : (err & ERR_TIMEOUT)  ? LBG_ERR_TIMEOUT
+               : (err & ERR_INTERNAL) ? LBG_ERR_CUDA
+                                      : LBG_OK;
+    *r = o;
 }
 
 // Prepared codebook + one allocation (cell table of C under X) -> assign, e.
@@ -328,6 +367,106 @@ struct GraphPass {
     }
 };
 
+// Replayed device sequences of lbg_lloyd_step / vq_encode.  Everything such
+// a call launches follows from the device pointers it touches, its sizes and
+// its options, so the sequence is recorded once into a graph under that key
+// and later calls with the same key launch the graph on their own stream.
+struct SeqKey {
+    int dev, op, mode, flags;   // op: 0 step, 1 encode; flags: bit 0 reseed, 1 D, 2 decode
+    int64_t M;
+    int L, N;
+    size_t total;               // workspace plan size (fixes every scratch offset)
+    double dres;
+    const void *X, *C, *Co, *A, *H, *res, *ws;
+    bool operator==(const SeqKey &k) const
+    {
+        return dev == k.dev && op == k.op && mode == k.mode && flags == k.flags && M == k.M &&
+               L == k.L && N == k.N && total == k.total && dres == k.dres && X == k.X && C == k.C &&
+               Co == k.Co && A == k.A && H == k.H && res == k.res && ws == k.ws;
+    }
+};
+
+struct SeqGraph {
+    SeqKey key;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t used = 0;
+};
+
+constexpr size_t SEQ_CACHE_MAX = 32;
+std::vector<SeqGraph> g_seq;
+uint64_t g_seq_clock = 0;
+cudaStream_t g_cap[MAX_DEVICES];
+
+// Destroys the cached graphs of device `dev` (all devices if dev < 0); the
+// caller has made sure none of them is still running.
+void seq_clear(int dev)
+{
+    for (size_t i = 0; i < g_seq.size();) {
+        if (dev < 0 || g_seq[i].key.dev == dev) {
+            cudaGraphExecDestroy(g_seq[i].exec);
+            g_seq[i] = g_seq.back();
+            g_seq.pop_back();
+        } else {
+            ++i;
+        }
+    }
+}
+
+// Launches the sequence of `key` on c.s: from the cache, else recorded now
+// (on a private capturing stream: c.s may be the legacy stream), else issued
+// directly when recording is not possible.
+template <class F>
+lbg_status seq_run(const Call &c, const SeqKey &key, F &&issue)
+{
+    SeqGraph *hit = nullptr;
+    for (auto &g : g_seq)
+        if (g.key == key) hit = &g;
+    if (!hit) {
+        if (!g_cap[c.dev] && cudaStreamCreateWithFlags(&g_cap[c.dev], cudaStreamNonBlocking) != cudaSuccess) {
+            (void)cudaGetLastError();
+            issue(c.s);
+            CK(cudaGetLastError());
+            return LBG_OK;
+        }
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        if (cudaStreamBeginCapture(g_cap[c.dev], cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+            issue(g_cap[c.dev]);
+            if (cudaStreamEndCapture(g_cap[c.dev], &graph) != cudaSuccess || !graph ||
+                cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+                exec = nullptr;
+        }
+        if (graph) cudaGraphDestroy(graph);
+        (void)cudaGetLastError();
+        if (!exec) {
+            issue(c.s);
+            CK(cudaGetLastError());
+            return LBG_OK;
+        }
+        if (g_seq.size() >= SEQ_CACHE_MAX) {
+            // evict the least recently used graph once every launch of it is done
+            size_t old = 0;
+            for (size_t i = 1; i < g_seq.size(); ++i)
+                if (g_seq[i].used < g_seq[old].used) old = i;
+            CK(cudaSetDevice(g_seq[old].key.dev));
+            const lbg_status rc = cudaDeviceSynchronize() == cudaSuccess ? LBG_OK : LBG_ERR_CUDA;
+            CK(cudaSetDevice(c.dev));
+            if (rc != LBG_OK) {
+                cudaGraphExecDestroy(exec);
+                return rc;
+            }
+            cudaGraphExecDestroy(g_seq[old].exec);
+            g_seq[old] = g_seq.back();
+            g_seq.pop_back();
+        }
+        g_seq.push_back(SeqGraph{key, exec, 0});
+        hit = &g_seq.back();
+    }
+    hit->used = ++g_seq_clock;
+    CK(cudaGraphLaunch(hit->exec, c.s));
+    return LBG_OK;
+}
+
 lbg_status check_dims(int64_t M, int32_t L, int32_t N)
 {
     if (M < 0 || M > INT32_MAX) return LBG_ERR_ARG;
@@ -375,6 +514,7 @@ lbg_status lbg_release_workspace(void)
     if (dev < 0 || dev >= MAX_DEVICES) return LBG_ERR_UNSUPPORTED;
     if (g_ws[dev].base) {
         CK(cudaDeviceSynchronize());
+        seq_clear(dev);
         cudaFree(g_ws[dev].base);
         g_ws[dev].base = nullptr;
         g_ws[dev].bytes = 0;
@@ -391,23 +531,25 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
     const lbg_opts o = resolve(opts);
     const int mode = precision_mode(o, L);
     if (mode < 0) return (lbg_status)mode;
+    lbg_step_result *res = o.result_dev;
+    if (res && (D || o.n_exact || o.phase_ms)) return LBG_ERR_ARG;
     std::lock_guard<std::mutex> lock(g_mu);
     Call c;
     if ((rc = begin(c, o)) != LBG_OK) return rc;
+    if (res && where(res, c.dev) != 1) return LBG_ERR_ARG;
     if (M == 0) {
         if (D) *D = 0.0;
         if (o.n_exact) *o.n_exact = 0;
+        if (res) CK(cudaMemsetAsync(res, 0, sizeof(*res), c.s));   // D = 0, n_exact = 0, LBG_OK
         return LBG_OK;
     }
     const int wX = where(X, c.dev), wC = where(C, c.dev), wI = where(idx, c.dev);
     const int wH = Xhat ? where(Xhat, c.dev) : 1;
     if (wX < 0 || wC < 0 || wI < 0 || wH < 0) return LBG_ERR_ARG;
+    if (res && (wX != 1 || wC != 1 || wI != 1 || wH != 1)) return LBG_ERR_ARG;
     const Plan p = make_plan(M, L, N, 0, wX == 0, wI == 0, wC == 0, wH == 0, mode == 1);
     if ((rc = ensure_workspace(c, p.total)) != LBG_OK) return rc;
     DevState *st = c.at<DevState>(p.state);
-    DevState h;
-    init_state(h, N);
-    CK(cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, c.s));
     const float *dX = X;
     const float *dC = C;
     if (wX == 0) {
@@ -420,30 +562,46 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
         dC = c.at<float>(p.Cin);
     }
     int32_t *dI = wI ? idx : c.at<int32_t>(p.assign);
+    float *dH = Xhat ? (wH ? Xhat : c.at<float>(p.Xhat)) : nullptr;
+    const bool wantD = D || res;
     Timer tm;
     if ((rc = tm.init(o.phase_ms != nullptr)) != LBG_OK) return rc;
     float *mu = c.at<float>(p.mu);
-    tm.mark(0, c.s);
-    launch_codebook_mean(dC, N, L, mu, c.s);
-    if (p.tc) launch_round_mu(mu, L, c.s);
-    run_prepare(c, p, dC, nullptr, N, mu, st);
-    tm.mark(1, c.s);
-    run_assign(c, p, dX, dC, nullptr, N, mu, st, dI);
-    tm.mark(2, c.s);
-    run_exact(c, p, dX, nullptr, N, st, dI);
-    tm.mark(3, c.s);
-    if (D) {
-        launch_hist(dI, c.at<float>(p.e), M, p.R, p.CH, nullptr, N, false, nullptr,
-                    c.at<double>(p.dpart), st, false, c.s);
-        launch_ctl(c.at<double>(p.dpart), p.CH, st, MODE_STEP, 0.0, 1, N, nullptr, 0, c.s);
+    auto issue = [&](cudaStream_t s) {
+        Call k = c;
+        k.s = s;
+        k_state_init<<<1, 1, 0, s>>>(st, N);
+        tm.mark(0, s);
+        launch_codebook_mean(dC, N, L, mu, s);
+        if (p.tc) launch_round_mu(mu, L, s);
+        run_prepare(k, p, dC, nullptr, N, mu, st);
+        tm.mark(1, s);
+        run_assign(k, p, dX, dC, nullptr, N, mu, st, dI);
+        tm.mark(2, s);
+        run_exact(k, p, dX, nullptr, N, st, dI);
+        tm.mark(3, s);
+        if (wantD) {
+            launch_hist(dI, k.at<float>(p.e), M, p.R, p.CH, nullptr, N, false, nullptr,
+                        k.at<double>(p.dpart), st, false, s);
+            launch_ctl(k.at<double>(p.dpart), p.CH, st, MODE_STEP, 0.0, 1, N, nullptr, 0, s);
+        }
+        if (dH) launch_decode(dI, M, L, dC, dH, s);
+        if (res) k_step_report<<<1, 1, 0, s>>>(st, res, 1);
+        tm.mark(4, s);
+    };
+    if (o.phase_ms) {
+        issue(c.s);
+        CK(cudaGetLastError());
+    } else {
+        const SeqKey key{c.dev, 1, mode, (wantD ? 2 : 0) | (dH ? 4 : 0), M, L, N, p.total, 0.0,
+                         dX, dC, nullptr, dI, dH, res, c.ws};
+        if ((rc = seq_run(c, key, issue)) != LBG_OK) return rc;
     }
-    if (Xhat) launch_decode(dI, M, L, dC, wH ? Xhat : c.at<float>(p.Xhat), c.s);
-    tm.mark(4, c.s);
-    CK(cudaGetLastError());
+    if (res) return end_async(c);
     if (wI == 0) CK(cudaMemcpyAsync(idx, dI, sizeof(int32_t) * M, cudaMemcpyDeviceToHost, c.s));
     if (Xhat && wH == 0)
-        CK(cudaMemcpyAsync(Xhat, c.at<float>(p.Xhat), sizeof(float) * M * L, cudaMemcpyDeviceToHost,
-                           c.s));
+        CK(cudaMemcpyAsync(Xhat, dH, sizeof(float) * M * L, cudaMemcpyDeviceToHost, c.s));
+    DevState h;
     CK(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, c.s));
     CK(cudaStreamSynchronize(c.s));
     tm.report(o.phase_ms, true);
@@ -461,18 +619,27 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
     const lbg_opts o = resolve(opts);
     const int mode = precision_mode(o, L);
     if (mode < 0) return (lbg_status)mode;
+    lbg_step_result *res = o.result_dev;
+    if (res && (D || o.n_exact || o.phase_ms)) return LBG_ERR_ARG;
     std::lock_guard<std::mutex> lock(g_mu);
     Call c;
     if ((rc = begin(c, o)) != LBG_OK) return rc;
     const int wX = M > 0 ? where(X, c.dev) : 1, wCi = where(C_in, c.dev), wCo = where(C_out, c.dev);
     const int wA = assign ? where(assign, c.dev) : 0;
     if (wX < 0 || wCi < 0 || wCo < 0 || wA < 0) return LBG_ERR_ARG;
+    if (res && (wX != 1 || wCi != 1 || wCo != 1 || (assign && wA != 1) || where(res, c.dev) != 1))
+        return LBG_ERR_ARG;
     const bool hostC = (wCi == 0) || (wCo == 0);
-    const Plan p = make_plan(M, L, N, 0, wX == 0, !(assign && wA == 1), hostC, false, mode == 1);
+    const bool wsA = !(assign && wA == 1);
+    const Plan p = make_plan(M, L, N, 0, wX == 0, wsA, hostC, false, mode == 1);
     if ((rc = ensure_workspace(c, p.total)) != LBG_OK) return rc;
     const size_t cbytes = sizeof(float) * (size_t)N * L;
     if (M == 0) {
         if (C_out != C_in) CK(cudaMemcpyAsync(C_out, C_in, cbytes, cudaMemcpyDefault, c.s));
+        if (res) {
+            CK(cudaMemsetAsync(res, 0, sizeof(*res), c.s));   // D = 0, n_exact = 0, LBG_OK
+            return end_async(c);
+        }
         CK(cudaStreamSynchronize(c.s));
         if (D) *D = 0.0;
         if (o.n_exact) *o.n_exact = 0;
@@ -481,9 +648,6 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
         return LBG_OK;
     }
     DevState *st = c.at<DevState>(p.state);
-    DevState h;
-    init_state(h, N);
-    CK(cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, c.s));
     const float *dX = X;
     if (wX == 0) {
         CK(cudaMemcpyAsync(c.at<float>(p.Xs), X, sizeof(float) * M * L, cudaMemcpyHostToDevice, c.s));
@@ -496,29 +660,45 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
         dCi = c.at<float>(p.Cin);
         dCo = c.at<float>(p.Cout);
     }
-    int32_t *dA = (assign && wA == 1) ? assign : c.at<int32_t>(p.assign);
+    int32_t *dA = wsA ? c.at<int32_t>(p.assign) : assign;
     Timer tm;
     if ((rc = tm.init(o.phase_ms != nullptr)) != LBG_OK) return rc;
     float *mu = c.at<float>(p.mu);
-    tm.mark(0, c.s);
-    launch_codebook_mean(dCi, N, L, mu, c.s);
-    if (p.tc) launch_round_mu(mu, L, c.s);
-    run_prepare(c, p, dCi, nullptr, N, mu, st);
-    tm.mark(1, c.s);
-    run_assign(c, p, dX, dCi, nullptr, N, mu, st, dA);
-    tm.mark(2, c.s);
-    run_exact(c, p, dX, nullptr, N, st, dA);
-    tm.mark(3, c.s);
-    launch_hist(dA, c.at<float>(p.e), M, p.R, p.CH, nullptr, N, true, c.at<int32_t>(p.table),
-                c.at<double>(p.dpart), st, false, c.s);
-    launch_ctl(c.at<double>(p.dpart), p.CH, st, MODE_STEP, 0.0, 1, N, nullptr, 0, c.s);
-    run_update(c, p, dX, nullptr, N, st, dA, dCi, dCo, false);
-    if (o.reseed_empty) launch_reseed(c.at<int32_t>(p.off), nullptr, N, L, o.delta_reseed, dCo, st, false, c.s);
-    tm.mark(4, c.s);
-    CK(cudaGetLastError());
+    auto issue = [&](cudaStream_t s) {
+        Call k = c;
+        k.s = s;
+        k_state_init<<<1, 1, 0, s>>>(st, N);
+        tm.mark(0, s);
+        launch_codebook_mean(dCi, N, L, mu, s);
+        if (p.tc) launch_round_mu(mu, L, s);
+        run_prepare(k, p, dCi, nullptr, N, mu, st);
+        tm.mark(1, s);
+        run_assign(k, p, dX, dCi, nullptr, N, mu, st, dA);
+        tm.mark(2, s);
+        run_exact(k, p, dX, nullptr, N, st, dA);
+        tm.mark(3, s);
+        launch_hist(dA, k.at<float>(p.e), M, p.R, p.CH, nullptr, N, true, k.at<int32_t>(p.table),
+                    k.at<double>(p.dpart), st, false, s);
+        launch_ctl(k.at<double>(p.dpart), p.CH, st, MODE_STEP, 0.0, 1, N, nullptr, 0, s);
+        run_update(k, p, dX, nullptr, N, st, dA, dCi, dCo, false);
+        if (o.reseed_empty)
+            launch_reseed(k.at<int32_t>(p.off), nullptr, N, L, o.delta_reseed, dCo, st, false, s);
+        if (res) k_step_report<<<1, 1, 0, s>>>(st, res, 1);
+        tm.mark(4, s);
+    };
+    if (o.phase_ms) {
+        issue(c.s);
+        CK(cudaGetLastError());
+    } else {
+        const SeqKey key{c.dev, 0, mode, o.reseed_empty ? 1 : 0, M, L, N, p.total,
+                         o.reseed_empty ? o.delta_reseed : 0.0, dX, dCi, dCo, dA, nullptr, res, c.ws};
+        if ((rc = seq_run(c, key, issue)) != LBG_OK) return rc;
+    }
+    if (res) return end_async(c);
     if (hostC) CK(cudaMemcpyAsync(C_out, dCo, cbytes, cudaMemcpyDefault, c.s));
     if (assign && wA == 0)
         CK(cudaMemcpyAsync(assign, dA, sizeof(int32_t) * M, cudaMemcpyDeviceToHost, c.s));
+    DevState h;
     CK(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, c.s));
     CK(cudaStreamSynchronize(c.s));
     tm.report(o.phase_ms, true);

@@ -88,3 +88,42 @@ def test_batched_rejects_bad_tile_options(lib):
     assert _err(lbgvq.lbg_train_batched, X, ro, N, 0.01, 1e-3, 1000, False, None, False, True, 96) == -1
     assert _err(lbgvq.lbg_train_batched, X, ro, N, 0.01, 1e-3, 1000, False, None, False, True, 64, 3) == -1
     assert _err(lbgvq.lbg_train_batched, X, ro, N, 0.01, 1e-3, 1000, False, None, False, True, 128, 4) == -1
+
+
+def test_struct_layout_matches_header(tmp_path):
+    """The binding's ctypes mirrors have the C compiler's sizes and offsets."""
+    import subprocess
+    from paper_0910_4711_gb300 import _binding
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "lbgvq.h"\n'
+        "int main(void) {\n"
+        '  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(lbg_opts), offsetof(lbg_opts, tune_report),\n'
+        "         offsetof(lbg_opts, result_dev), sizeof(lbg_step_result),\n"
+        "         offsetof(lbg_step_result, n_exact), offsetof(lbg_step_result, status));\n"
+        "  return 0; }\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    O = _binding.Opts
+    assert got[:3] == [ctypes.sizeof(O), O.tune_report.offset, O.result_dev.offset]
+    assert got[3:] == [_binding.STEP_RESULT_BYTES, 8, 12]
+
+
+def test_async_calls_reject_host_outs(lib):
+    """An asynchronous step / encode (result_dev set) refuses host outputs before
+    any device work."""
+    from paper_0910_4711_gb300 import _binding
+    o = _binding.Opts()
+    lib.lbg_opts_init(ctypes.byref(o))
+    assert not o.result_dev
+    fake = ctypes.c_void_p(0x1000)   # never dereferenced: the call returns first
+    o.result_dev = fake
+    D = ctypes.c_double(0.0)
+    assert lib.lbg_lloyd_step(fake, 8, 4, 2, fake, fake, None, ctypes.byref(D), ctypes.byref(o)) == -1
+    assert lib.vq_encode(fake, 8, 4, fake, 2, fake, None, ctypes.byref(D), ctypes.byref(o)) == -1
+    n = ctypes.c_int32(0)
+    o.n_exact = ctypes.pointer(n)
+    assert lib.lbg_lloyd_step(fake, 8, 4, 2, fake, fake, None, None, ctypes.byref(o)) == -1
