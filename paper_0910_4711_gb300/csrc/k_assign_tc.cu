@@ -23,12 +23,12 @@
 //     |v_n - (X2 + f_n - k'_n)| <= tau (2 ||x~||^2 + 2 ||c~_n||^2) + u ||c~_n||^2,
 // and with k'_n = (2 tau + 2^-23) ||c~_n||^2, R' = 2 tau ||x~||^2 the
 // certificate of k_assign.cu applies: V2 - V1 > 2R' + 2k'_i1 + 4 eta (g1 + eta),
-// plus 2^-18 (|V1| + |V2|) + 2^-23 (|V1| + 2|V2|) for the epilogue below.
+// plus 2^-17 (|V1| + |V2|) + 2^-23 (|V1| + 2|V2|) for the epilogue below.
 //
-// Epilogue.  Each thread owns one row and one half (64 columns) of every
-// tile, taken as 32 column pairs (a, b).  lo = min(a, b) gets the pair index
-// (5 bits) in its low mantissa bits (one LOP3; the value moves by less than
-// 2^-18 of it); hi = (a + b) - lo is formed on the otherwise idle FMA pipe
+// Epilogue.  Each thread owns one row and one half (72 columns) of every
+// tile, taken as 36 column pairs (a, b).  lo = min(a, b) gets the pair index
+// (6 bits) in its low mantissa bits (one LOP3; the value moves by less than
+// 2^-17 of it); hi = (a + b) - lo is formed on the otherwise idle FMA pipe
 // (within 2^-23 (|V1| + 2|hi|) of max(a, b)); then c2 = min(c2, max(c1, lo),
 // hi) (three-input min) and c1 = min(c1, lo).  That is five ALU operations
 // per pair for the running top-2 of values with the index of the best pair;
@@ -47,14 +47,14 @@
 //                 memory with tcgen05.st: the MMAs read A from TMEM and only B
 //                 from shared memory, which leaves shared-memory bandwidth for
 //                 the codebook stream;
-//   warp 0        producer: TMA bulk copies of prepared codebook tiles (128
+//   warp 0        producer: TMA bulk copies of prepared codebook tiles (144
 //                 codevectors x KB BF16, already in the MMA's shared-memory
 //                 layout) into a 3-stage ring;
 //   warp 1        allocates 512 TMEM columns, one thread issues the MMAs: job
 //                 j = 2 t + a (tile t, accumulator a of 128 rows) accumulates
-//                 into slot j % 3 of a ring of three 128-column accumulators;
+//                 into slot j % 3 of a ring of three 144-column accumulators;
 //   warps 2..17   epilogue, one (row, column half) per thread: tcgen05.ld of
-//                 its 64 values per job, running top-2 with the pair index
+//                 its 72 values per job, running top-2 with the pair index
 //                 (four interleaved chains); after the last tile the two halves
 //                 of each row merge, compute the exact distances of the best
 //                 pair's two codevectors, and the half-0 thread runs the
@@ -71,13 +71,17 @@ namespace {
 
 constexpr int TC_NACC = 2;                     // 128-row accumulators per CTA
 constexpr int TC_ROWS = 128 * TC_NACC;         // 256 rows per CTA
-constexpr int TC_NT = 128;                     // codevectors per tile (MMA N; N = 128 is the
-                                               // smallest N at full rate with both operands
-                                               // in shared memory, measured)
+constexpr int TC_NT = 144;                     // codevectors per tile (MMA N): 3 accumulator
+                                               // slots of 144 columns and A fill the 512 TMEM
+                                               // columns; wider MMAs need fewer issues per flop,
+                                               // which keeps the single issuing thread ahead of
+                                               // the tensor pipe while its SM sub-partition also
+                                               // runs epilogue warps (N = 128 issued about one
+                                               // MMA per 86 cycles for 64 cycles of work)
 constexpr int TC_HALF = TC_NT / 2;             // columns per epilogue thread per tile
 constexpr int TC_PAIRS = TC_HALF / 2;          // column pairs per epilogue thread per tile
-constexpr int TC_JBITS = 5;                    // bits of the in-half pair index
-constexpr float TC_PACK = 3.814697265625e-6f;  // 2^(TC_JBITS - 23): packing changes a value
+constexpr int TC_JBITS = 6;                    // bits of the in-half pair index (36 pairs)
+constexpr float TC_PACK = 7.62939453125e-6f;   // 2^(TC_JBITS - 23): packing changes a value
                                                // by less than this fraction of it
 constexpr float TC_HIERR = 1.1920928955078125e-7f;   // 2^-23: bound of the FMA-pipe pair maximum
 constexpr int TC_STAGES = 3;
@@ -85,8 +89,10 @@ constexpr int TC_EPI_WARPS = 8 * TC_NACC;      // 16: (accumulator, lane quarter
 constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);
 constexpr int TC_SLOTS = 3;                    // accumulator ring: (tile, accumulator) jobs
 constexpr int TC_A_COL = TC_SLOTS * TC_NT;     // TMEM column of the A operand (x~ rows)
-constexpr int TC_TMEM_COLS = 512;              // 3 x 128 accumulator columns + 2 x (L + 16)/2
+constexpr int TC_TMEM_COLS = 512;              // 3 x 144 accumulator columns + 2 x (L + 16)/2
 constexpr int TC_LMAX = 64;
+static_assert(TC_A_COL + 2 * ((TC_LMAX + 16) / 2) <= TC_TMEM_COLS, "accumulators + A exceed TMEM");
+static_assert(TC_HALF == 72 && TC_PAIRS <= (1 << TC_JBITS), "epilogue loads 64 + 8 columns");
 
 constexpr float U32 = 5.9604644775390625e-8f;   // 2^-24
 constexpr float SLOP = 1.0000305175781250f;     // 1 + 2^-15
@@ -140,6 +146,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
         : "r"(taddr));
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v)
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 __device__ __forceinline__ float fmin3(float a, float b, float c)
@@ -234,12 +251,29 @@ __device__ __forceinline__ void mma_commit_elect(uint64_t *bar)
         : "memory");
 }
 
+// Staged BF16 x~ rows in shared memory.  Rows of LK < 64 elements are padded
+// by 8 (16 bytes) so that a thread per row reads 16-byte chunks without bank
+// conflicts; 64-element rows (128 bytes) are not padded but have their eight
+// 16-byte chunks permuted by the row (chunk c at c ^ (row & 7)), which does
+// the same in less space.
+template <int LK>
+struct XsRow {
+    static constexpr int STR = LK == 64 ? 64 : LK + 8;   // BF16 per staged row
+};
+template <int LK>
+__device__ __forceinline__ int xs_at(int r, int l)
+{
+    if (LK == 64) return r * 64 + ((((l >> 3) ^ (r & 7)) << 3) | (l & 7));
+    return r * XsRow<LK>::STR + l;
+}
+
 // The A words of one half of a row (half H of the K = LK + 16 elements, two
 // BF16 per word): centred x~ from the staged row (zero past L and for rows
 // past M), and the running sum of squares of those x~ in order.  Half 1 also
 // holds the norm block, filled in later.
 template <int LK, int H>
-__device__ __forceinline__ void a_words(const __nv_bfloat16 *xrow, int L, bool live, uint32_t *wv, float &part)
+__device__ __forceinline__ void a_words(const __nv_bfloat16 *XS, int crow, int L, bool live, uint32_t *wv,
+                                        float &part)
 {
     constexpr int KA = LK + 16, HK = KA / 2, E0 = H * HK;
     constexpr int XE = H == 0 ? HK : LK - HK;          // x~ elements in this half
@@ -247,7 +281,8 @@ __device__ __forceinline__ void a_words(const __nv_bfloat16 *xrow, int L, bool l
     for (int w = 0; w < HK / 2; ++w) wv[w] = 0u;
 #pragma unroll
     for (int g = 0; g < XE / 8; ++g) {
-        const uint4 q = live ? *reinterpret_cast<const uint4 *>(xrow + E0 + 8 * g) : make_uint4(0u, 0u, 0u, 0u);
+        const uint4 q = live ? *reinterpret_cast<const uint4 *>(XS + xs_at<LK>(crow, E0 + 8 * g))
+                             : make_uint4(0u, 0u, 0u, 0u);
         const uint32_t qs[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -280,12 +315,22 @@ __device__ __forceinline__ bool split3(float v, __nv_bfloat16 &h, __nv_bfloat16 
     return isfinite(v) ? (r2 - __bfloat162float(l)) == 0.f : isinf(v);
 }
 
-// Prepared BF16 codebook: tile t (TC_NT codevectors) is TC_NT x KB BF16 in
-// the core-matrix layout (SBO = KB/8 * 128); K columns [0,Lk) p_hi, [Lk,2Lk)
-// p_mid, [2Lk,3Lk) p_lo of c' = -2 (c - mu), [3Lk, 3Lk+3) the pieces of s0,
-// zeros elsewhere; padding codevectors have s0 = 2^100.  Also k'_n, the
-// chunk-major original codebook for the exact fallback, max ||c~||.
+// Prepared BF16 codebook: codevector rows x KB BF16 in the core-matrix layout
+// (8-row groups SBO = KB/8 * 128 bytes apart), so that tile t (TC_NT rows) is
+// the contiguous block at t * TC_NT * KB * 2 bytes; K columns [0,Lk) p_hi,
+// [Lk,2Lk) p_mid, [2Lk,3Lk) p_lo of c' = -2 (c - mu), [3Lk, 3Lk+3) the pieces
+// of s0, zeros elsewhere; padding codevectors (up to whole tiles) have
+// s0 = 2^100.  Also k'_n, the chunk-major original codebook for the exact
+// fallback (both BN-padded), max ||c~||.
 constexpr int PT_N = 32;   // codevectors per preparation CTA
+
+// Rows of the prepared codebook for N codevectors: whole tiles and whole BN
+// chunks, in whole preparation CTAs.
+__host__ __device__ inline int tc_prep_rows(int N)
+{
+    const int t = round_up(N, TC_NT), b = round_up(N, BN);
+    return round_up(t > b ? t : b, PT_N);
+}
 
 template <int LK>
 __global__ void __launch_bounds__(256)
@@ -296,7 +341,8 @@ __global__ void __launch_bounds__(256)
     if (st->finished) return;
     const int N = cur_n(n_dev, n_host);
     const int n0 = blockIdx.x * PT_N;
-    if (n0 >= round_up(N, BN)) return;   // CT chunks are BN wide; tiles TC_NT
+    if (n0 >= tc_prep_rows(N)) return;
+    const int NPk = round_up(N, BN);      // k'_n and CT entries (BN-padded)
     constexpr int KB = 3 * LK + 16;
     constexpr uint32_t sbo = (uint32_t)(KB / 8) * 128u;
     __shared__ float cs[PT_N][LK + 1];   // codevectors as given (0 past L / N)
@@ -346,7 +392,7 @@ __global__ void __launch_bounds__(256)
             cbits = __float_as_uint(__fsqrt_ru(__double2float_ru(sq)));   // >= ||c~_n||
         } else {
             s0s[tid] = 1.2676506002282294e30f;   // padding: 2^100, finite so index packing cannot make a NaN
-            kn[n] = 0.f;
+            if (n < NPk) kn[n] = 0.f;
         }
         // max ||c~_n|| of the block (bits of non-negative floats order as integers): one atomic per CTA
         cbits = __reduce_max_sync(0xffffffffu, cbits);
@@ -357,8 +403,8 @@ __global__ void __launch_bounds__(256)
     // then the s0 pieces, three ones (x the row's X2 pieces), zeros.  A unit is
     // (codevector, 8 dims): each value is split once and its three pieces go
     // out as three 16-byte core-matrix rows.
-    uint8_t *tile = reinterpret_cast<uint8_t *>(Bp) + (size_t)(n0 / TC_NT) * TC_NT * KB * 2;
-    const int rt = n0 % TC_NT;
+    uint8_t *tile = reinterpret_cast<uint8_t *>(Bp);
+    const int rt = n0;
     constexpr int G8 = LK / 8;
     bool inexact = false;
     for (int u = tid; u < PT_N * G8; u += blockDim.x) {
@@ -399,10 +445,11 @@ __global__ void __launch_bounds__(256)
     }
     if (inexact) s_inexact = 1;
     // FP32 codebook for the exact fallback, chunk-major (coalesced along n)
-    for (int i = tid; i < PT_N * Lp; i += blockDim.x) {
-        const int l = i / PT_N, r = i - l * PT_N, n = n0 + r;
-        CT[((size_t)(n / EXACT_SW) * Lp + l) * EXACT_SW + n % EXACT_SW] = l < L ? cs[r][l] : 0.f;
-    }
+    if (n0 < NPk)
+        for (int i = tid; i < PT_N * Lp; i += blockDim.x) {
+            const int l = i / PT_N, r = i - l * PT_N, n = n0 + r;
+            CT[((size_t)(n / EXACT_SW) * Lp + l) * EXACT_SW + n % EXACT_SW] = l < L ? cs[r][l] : 0.f;
+        }
     __syncthreads();
     if (tid == 0) {
         if (s_bad) flag_error(st, ERR_NONFINITE);
@@ -434,7 +481,8 @@ __device__ __forceinline__ bool named_sync_or(int id, int threads, bool v)
 
 // One centred x value into the staged BF16 rows; flags non-finite input and
 // values for which x~ = x - mu is not exact in FP32 (TwoSum error) or BF16.
-__device__ __forceinline__ void tc_put_x(__nv_bfloat16 *XS, int xstr, int i, int L, float xv,
+template <int LK>
+__device__ __forceinline__ void tc_put_x(__nv_bfloat16 *XS, int i, int L, float xv,
                                          const float *__restrict__ mu, bool &bad, bool &inexact)
 {
     const int r = i / L, l = i - r * L;
@@ -445,7 +493,7 @@ __device__ __forceinline__ void tc_put_x(__nv_bfloat16 *XS, int xstr, int i, int
     const float err = __fadd_rn(__fsub_rn(xv, __fsub_rn(v, bb)), __fsub_rn(-ml, bb));
     const __nv_bfloat16 b = __float2bfloat16_rn(v);
     inexact = inexact || err != 0.f || (__bfloat162float(b) != v);
-    XS[r * xstr + l] = b;
+    XS[xs_at<LK>(r, l)] = b;
 }
 
 // The A operand in tensor memory: each epilogue thread writes its half of its
@@ -458,12 +506,11 @@ template <int LK>
 __device__ __forceinline__ float tc_write_a(const __nv_bfloat16 *XS, int L, bool live, int crow, int half,
                                             int acc, int warp, uint32_t tmem, TcSmem &sh)
 {
-    constexpr int KA = LK + 16, NW = KA / 4, XSTR = LK + 8;
+    constexpr int KA = LK + 16, NW = KA / 4;
     uint32_t wv[NW];
     float part = 0.f;
-    const __nv_bfloat16 *xrow = XS + (size_t)crow * XSTR;
-    if (half == 0) a_words<LK, 0>(xrow, L, live, wv, part);
-    else a_words<LK, 1>(xrow, L, live, wv, part);
+    if (half == 0) a_words<LK, 0>(XS, crow, L, live, wv, part);
+    else a_words<LK, 1>(XS, crow, L, live, wv, part);
     sh.d[half][crow] = part;
     named_sync(1, 32 * TC_EPI_WARPS);
     const float xn2 = __fadd_rn(sh.d[0][crow], sh.d[1][crow]);
@@ -483,7 +530,7 @@ __device__ __forceinline__ float tc_write_a(const __nv_bfloat16 *XS, int L, bool
 }
 
 // The epilogue of one row tile: for each codebook tile t, job j0 + 2t + acc
-// (accumulator slot (j0 + 2t + acc) % 3); the thread's 64 values per job go
+// (accumulator slot (j0 + 2t + acc) % 3); the thread's 72 values per job go
 // through the pair top-2; returns the merged (V1, V2, pair index) of the
 // thread's half.  hook(t) runs after job t in every epilogue warp (it may use
 // named barriers: after a time-out, sh.abort, the jobs are skipped but the
@@ -519,6 +566,7 @@ __device__ __forceinline__ void tc_jobs(TcSmem &sh, uint32_t tmem, int warp, int
         const uint32_t col = (uint32_t)(slot * TC_NT + half * TC_HALF);
         tmem_ld32(tmem + lane_base + col, v);
         tmem_ld32(tmem + lane_base + col + 32u, v + 32);
+        tmem_ld8(tmem + lane_base + col + 64u, v + 64);
         tmem_ld_wait();
         // the values are in registers: hand the accumulator back to the MMA
         tc_fence_before();
@@ -702,7 +750,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int N = cur_n(n_dev, n_host);
     const int ntiles = (N + TC_NT - 1) / TC_NT;
     constexpr int KB = 3 * LK + 16;
-    constexpr int XSTR = LK + 8;                               // staged row stride (BF16), padded
+    constexpr int XSTR = XsRow<LK>::STR;                       // staged row stride (BF16)
     constexpr uint32_t sbo_b = (uint32_t)(KB / 8) * 128u;
     constexpr uint32_t xs_bytes = (uint32_t)TC_ROWS * XSTR * 2u;
     constexpr uint32_t stage_bytes = (uint32_t)TC_NT * KB * 2u;
@@ -763,21 +811,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int f = 4 * (i + u * ST);
-                    tc_put_x(XS, XSTR, f, L, q[u].x, mu, bad, inexact);
-                    tc_put_x(XS, XSTR, f + 1, L, q[u].y, mu, bad, inexact);
-                    tc_put_x(XS, XSTR, f + 2, L, q[u].z, mu, bad, inexact);
-                    tc_put_x(XS, XSTR, f + 3, L, q[u].w, mu, bad, inexact);
+                    tc_put_x<LK>(XS, f, L, q[u].x, mu, bad, inexact);
+                    tc_put_x<LK>(XS, f + 1, L, q[u].y, mu, bad, inexact);
+                    tc_put_x<LK>(XS, f + 2, L, q[u].z, mu, bad, inexact);
+                    tc_put_x<LK>(XS, f + 3, L, q[u].w, mu, bad, inexact);
                 }
             }
             for (; i < total4; i += ST) {
                 const float4 q = __ldg(X4 + i);
-                tc_put_x(XS, XSTR, 4 * i, L, q.x, mu, bad, inexact);
-                tc_put_x(XS, XSTR, 4 * i + 1, L, q.y, mu, bad, inexact);
-                tc_put_x(XS, XSTR, 4 * i + 2, L, q.z, mu, bad, inexact);
-                tc_put_x(XS, XSTR, 4 * i + 3, L, q.w, mu, bad, inexact);
+                tc_put_x<LK>(XS, 4 * i, L, q.x, mu, bad, inexact);
+                tc_put_x<LK>(XS, 4 * i + 1, L, q.y, mu, bad, inexact);
+                tc_put_x<LK>(XS, 4 * i + 2, L, q.z, mu, bad, inexact);
+                tc_put_x<LK>(XS, 4 * i + 3, L, q.w, mu, bad, inexact);
             }
         } else {
-            for (int i = et; i < total; i += ST) tc_put_x(XS, XSTR, i, L, __ldg(Xt + i), mu, bad, inexact);
+            for (int i = et; i < total; i += ST) tc_put_x<LK>(XS, i, L, __ldg(Xt + i), mu, bad, inexact);
         }
         if (bad) flag_error(st, ERR_NONFINITE);
         if (inexact) sh.inexact = 1;
@@ -921,7 +969,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int64_t nrt = (M + TC_ROWS - 1) / TC_ROWS;   // row tiles
     const int K = (int)((nrt - (int64_t)blockIdx.x + gridDim.x - 1) / gridDim.x);   // this CTA's
     constexpr int KB = 3 * LK + 16;
-    constexpr int XSTR = LK + 8;
+    constexpr int XSTR = XsRow<LK>::STR;
     constexpr uint32_t sbo_b = (uint32_t)(KB / 8) * 128u;
     constexpr uint32_t stage_bytes = (uint32_t)TC_NT * KB * 2u;
     constexpr uint32_t xs_bytes = (uint32_t)TC_ROWS * XSTR * 2u;
@@ -1112,16 +1160,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             cv_inexact = cv_inexact || err != 0.f || (__bfloat162float(b) != v);
                             bits[u] = __bfloat16_as_ushort(b);
                         }
-                        *reinterpret_cast<uint2 *>(XS + r * XSTR + l0) =
+                        *reinterpret_cast<uint2 *>(XS + xs_at<LK>(r, l0)) =
                             make_uint2(bits[0] | (bits[1] << 16), bits[2] | (bits[3] << 16));
                     }
                 } else {
                     for (int i = lo + et; i < hi; i += ST) {
                         const float4 q = X4[i];
-                        tc_put_x(XS, XSTR, 4 * i, L, q.x, mu, cv_bad, cv_inexact);
-                        tc_put_x(XS, XSTR, 4 * i + 1, L, q.y, mu, cv_bad, cv_inexact);
-                        tc_put_x(XS, XSTR, 4 * i + 2, L, q.z, mu, cv_bad, cv_inexact);
-                        tc_put_x(XS, XSTR, 4 * i + 3, L, q.w, mu, cv_bad, cv_inexact);
+                        tc_put_x<LK>(XS, 4 * i, L, q.x, mu, cv_bad, cv_inexact);
+                        tc_put_x<LK>(XS, 4 * i + 1, L, q.y, mu, cv_bad, cv_inexact);
+                        tc_put_x<LK>(XS, 4 * i + 2, L, q.z, mu, cv_bad, cv_inexact);
+                        tc_put_x<LK>(XS, 4 * i + 3, L, q.w, mu, cv_bad, cv_inexact);
                     }
                 }
             }
@@ -1189,7 +1237,7 @@ __global__ void k_round_mu(float *mu, int L)
 
 }  // namespace
 
-size_t tc_codebook_bytes(int NP, int L) { return (size_t)NP * (3 * round_up(L, 16) + 16) * 2; }
+size_t tc_codebook_bytes(int NP, int L) { return (size_t)tc_prep_rows(NP) * (3 * round_up(L, 16) + 16) * 2; }
 
 bool tc_supported(int L) { return L >= 1 && L <= TC_LMAX; }
 
@@ -1198,7 +1246,7 @@ void launch_round_mu(float *mu, int L, cudaStream_t s) { k_round_mu<<<1, 128, 0,
 void launch_prep_tc(const float *C, int N_alloc, const int32_t *n_dev, int n_host, int L,
                     const float *mu, void *Bp, float *kn, float *CT, DevState *st, cudaStream_t s)
 {
-    const int blocks = round_up(N_alloc, BN) / PT_N;
+    const int blocks = tc_prep_rows(N_alloc) / PT_N;
     __nv_bfloat16 *B = static_cast<__nv_bfloat16 *>(Bp);
     const int Lp = round_up(L, 4);
     switch (round_up(L, 16)) {
@@ -1220,7 +1268,7 @@ static void launch_tc(const float *X, int64_t M, int L, const void *Bp, const fl
     const __nv_bfloat16 *B = static_cast<const __nv_bfloat16 *>(Bp);
     if ((L & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) {
         // persistent: 2 codebook stages + staged BF16 rows + the FP32 x tile
-        const size_t need = (size_t)TC_PSTAGES * TC_NT * (3 * LK + 16) * 2 + (size_t)TC_ROWS * (LK + 8) * 2 +
+        const size_t need = (size_t)TC_PSTAGES * TC_NT * (3 * LK + 16) * 2 + (size_t)TC_ROWS * XsRow<LK>::STR * 2 +
                             (size_t)TC_ROWS * LK * 4;
         // at least 120 KB so that a single CTA (and its 512 TMEM columns) owns the SM
         const size_t smem = need > 120 * 1024 ? need : 120 * 1024;
@@ -1230,7 +1278,7 @@ static void launch_tc(const float *X, int64_t M, int L, const void *Bp, const fl
                                                                e, flags, keymask);
         return;
     }
-    const size_t need = (size_t)TC_ROWS * (LK + 8) * 2 + (size_t)TC_STAGES * TC_NT * (3 * LK + 16) * 2;
+    const size_t need = (size_t)TC_ROWS * XsRow<LK>::STR * 2 + (size_t)TC_STAGES * TC_NT * (3 * LK + 16) * 2;
     // at least 120 KB so that a single CTA (and its 512 TMEM columns) owns the SM
     const size_t smem = need > 120 * 1024 ? need : 120 * 1024;
     cudaFuncSetAttribute(k_assign_tc<LK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
