@@ -4,26 +4,32 @@
 // Paper: Algorithm 1 "Cell Allocation" / Sec. 2.2 step 1, as in k_assign.cu;
 // this is the same search with the cross term on tcgen05.mma.
 //
-// Exactness of the operands.  With an integer centring vector mu, centred
-// 8-bit image vectors x~ = x - mu are integers in [-255, 255], exact in BF16.
-// The scaled codevector c' = -2 c~ (FP32, 24 significant bits) is split into
-// three BF16 pieces p_hi + p_mid + p_lo = c' exactly, and so are the chain
-// start s0 = fl(||c~||^2 - k') and the row constant X2 = fl(||x~||^2).  One GEMM
-//     A = [ x~ | 1 1 1 X2_hi X2_mid X2_lo 0 ... ]          (K = Lk + 16)
-//     B = [ p_hi | p_mid | p_lo | s0 pieces 1 1 1 0 ... ]  (x~ reused 3 times)
-// therefore accumulates exactly X2 + s0 + x~.c' = X2 + f - k' (~ d - k', the
-// distance up to k'); the only error is the tensor core's FP32 accumulation.
-// X2 is the same in every column of a row, so it cancels in V2 - V1.
+// Operands.  With an integer centring vector mu, centred 8-bit image vectors
+// x~ = x - mu are integers in [-255, 255], exact in BF16.  The scaled
+// codevector c' = -2 c~ (FP32) is split into two BF16 pieces p_hi + p_mid with
+// an FP32-exact remainder r = c' - p_hi - p_mid (|r| <= 2^-16 |c'|); the chain
+// start s0 = fl(||c~||^2 - k') and the row constant X2 = fl(||x~||^2) are split
+// exactly into three pieces each.  One GEMM
+//     A = [ x~ | 1 1 1 X2_hi X2_mid X2_lo 0 ... ]      (K = Lk + 16)
+//     B = [ p_hi | p_mid | s0 pieces 1 1 1 0 ... ]     (x~ reused twice)
+// therefore accumulates X2 + s0 + x~.c' - x~.r = X2 + f - k' - x~.r (~ d - k',
+// the distance up to k'), with |x~.r_n| <= ||x~|| rho, rho = max_n ||r_n||
+// (measured by the preparation kernel), besides the tensor core's FP32
+// accumulation error.  X2 is the same in every column of a row, so it cancels
+// in V2 - V1.  (A third piece would make x~.c' exact at 3/2 the MMAs and
+// codebook bytes; on the image workloads the remainder term certifies all
+// but a few tenths of a percent of the rows.)
 //
 // Accumulation model.  Measured on GB300 (BF16 products, K up to 256, mixed
 // exponents) the error stayed below (K/16) * 2^-24 * (sum of |products|); the
 // library assumes tau = (K/16 + 2) * 2^-22 * (1 + 2^-7) of (sum of |products| +
 // |s0| + X2), a factor of about 4.8 above the worst case measured.  With
 // sum |x~_l c'_l| <= ||x~||^2 + ||c~||^2 this gives
-//     |v_n - (X2 + f_n - k'_n)| <= tau (2 ||x~||^2 + 2 ||c~_n||^2) + u ||c~_n||^2,
-// and with k'_n = (2 tau + 2^-23) ||c~_n||^2, R' = 2 tau ||x~||^2 the
-// certificate of k_assign.cu applies: V2 - V1 > 2R' + 2k'_i1 + 4 eta (g1 + eta),
-// plus 2^-17 (|V1| + |V2|) + 2^-23 (|V1| + 2|V2|) for the epilogue below.
+//     |v_n - (X2 + f_n - k'_n)| <= tau (2 ||x~||^2 + 2 ||c~_n||^2) + u ||c~_n||^2 + E,
+// E = ||x~|| rho, and with k'_n = (2 tau + 2^-23) ||c~_n||^2, R' = 2 tau ||x~||^2
+// the certificate of k_assign.cu applies: V2 - V1 > 2R' + 2k'_i1 + 2E +
+// 4 eta (g1 + eta), plus 2^-17 (|V1| + |V2|) + 2^-23 (|V1| + 2|V2|) for the
+// epilogue below.
 //
 // Epilogue.  Each thread owns one row and one half (72 columns) of every
 // tile, taken as 36 column pairs (a, b).  lo = min(a, b) gets the pair index
@@ -91,6 +97,7 @@ constexpr int TC_SLOTS = 3;                    // accumulator ring: (tile, accum
 constexpr int TC_A_COL = TC_SLOTS * TC_NT;     // TMEM column of the A operand (x~ rows)
 constexpr int TC_TMEM_COLS = 512;              // 3 x 144 accumulator columns + 2 x (L + 16)/2
 constexpr int TC_LMAX = 64;
+constexpr int TC_PIECES = 2;                   // BF16 pieces of c' in B (K blocks of x~ . c')
 static_assert(TC_A_COL + 2 * ((TC_LMAX + 16) / 2) <= TC_TMEM_COLS, "accumulators + A exceed TMEM");
 static_assert(TC_HALF == 72 && TC_PAIRS <= (1 << TC_JBITS), "epilogue loads 64 + 8 columns");
 
@@ -303,6 +310,20 @@ __host__ __device__ inline double tc_tau(int KB)
     return (double)(KB / 16 + 2) * 2.384185791015625e-7 * 1.0078125;   // 2^-22, (1 + 2^-7)
 }
 
+// K of one B row: the pieces of c' (LK each) and the 16-element norm block.
+__host__ __device__ constexpr int tc_kb(int LK) { return TC_PIECES * LK + 16; }
+
+// Split an FP32 value into two BF16 pieces h + m; returns the remainder
+// v - h - m, which is exact in FP32 (each subtraction is; |v - h - m| <= 2^-16 |v|
+// for normal numbers), NaN or Inf for non-finite v.
+__device__ __forceinline__ float split2(float v, __nv_bfloat16 &h, __nv_bfloat16 &m)
+{
+    h = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(h);
+    m = __float2bfloat16_rn(r1);
+    return r1 - __bfloat162float(m);
+}
+
 // Split an FP32 value into three BF16 pieces that add up to it exactly (for
 // normal numbers); returns false if the remainder is not zero.
 __device__ __forceinline__ bool split3(float v, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l)
@@ -318,10 +339,10 @@ __device__ __forceinline__ bool split3(float v, __nv_bfloat16 &h, __nv_bfloat16 
 // Prepared BF16 codebook: codevector rows x KB BF16 in the core-matrix layout
 // (8-row groups SBO = KB/8 * 128 bytes apart), so that tile t (TC_NT rows) is
 // the contiguous block at t * TC_NT * KB * 2 bytes; K columns [0,Lk) p_hi,
-// [Lk,2Lk) p_mid, [2Lk,3Lk) p_lo of c' = -2 (c - mu), [3Lk, 3Lk+3) the pieces
-// of s0, zeros elsewhere; padding codevectors (up to whole tiles) have
+// [Lk,2Lk) p_mid of c' = -2 (c - mu), [2Lk, 2Lk+3) the pieces of s0, three
+// ones, zeros elsewhere; padding codevectors (up to whole tiles) have
 // s0 = 2^100.  Also k'_n, the chunk-major original codebook for the exact
-// fallback (both BN-padded), max ||c~||.
+// fallback (both BN-padded), max ||c~|| and max ||c' - p_hi - p_mid||.
 constexpr int PT_N = 32;   // codevectors per preparation CTA
 
 // Rows of the prepared codebook for N codevectors: whole tiles and whole BN
@@ -343,7 +364,7 @@ __global__ void __launch_bounds__(256)
     const int n0 = blockIdx.x * PT_N;
     if (n0 >= tc_prep_rows(N)) return;
     const int NPk = round_up(N, BN);      // k'_n and CT entries (BN-padded)
-    constexpr int KB = 3 * LK + 16;
+    constexpr int KB = tc_kb(LK);
     constexpr uint32_t sbo = (uint32_t)(KB / 8) * 128u;
     __shared__ float cs[PT_N][LK + 1];   // codevectors as given (0 past L / N)
     __shared__ float ct[PT_N][LK + 1];   // centred c~ = c - mu
@@ -399,28 +420,34 @@ __global__ void __launch_bounds__(256)
         if (tid == 0 && cbits) atomicMax(&st->cmax_bits, cbits);
     }
     __syncthreads();
-    // B rows: K in [0, LK) p_hi of c' = -2 c~, [LK, 2LK) p_mid, [2LK, 3LK) p_lo,
-    // then the s0 pieces, three ones (x the row's X2 pieces), zeros.  A unit is
-    // (codevector, 8 dims): each value is split once and its three pieces go
-    // out as three 16-byte core-matrix rows.
+    // B rows: K in [0, LK) p_hi of c' = -2 c~, [LK, 2LK) p_mid, then the s0
+    // pieces, three ones (x the row's X2 pieces), zeros.  A unit is (codevector,
+    // 8 dims): each value is split once and its two pieces go out as two
+    // 16-byte core-matrix rows; the squared remainders c' - p_hi - p_mid of the
+    // unit (exact in FP32, summed in FP64 in a fixed order) go to rsq.
     uint8_t *tile = reinterpret_cast<uint8_t *>(Bp);
     const int rt = n0;
     constexpr int G8 = LK / 8;
+    __shared__ double rsq[PT_N][G8];
     bool inexact = false;
     for (int u = tid; u < PT_N * G8; u += blockDim.x) {
-        const int r = u / G8, l0 = 8 * (u - r * G8);
-        uint32_t w[3][4];
+        const int r = u / G8, g = u - r * G8, l0 = 8 * g;
+        uint32_t w[TC_PIECES][4];
+        double q = 0.0;
 #pragma unroll
         for (int e2 = 0; e2 < 4; ++e2) {
-            __nv_bfloat16 h0, m0, o0, h1, m1, o1;
-            inexact |= !split3(-2.0f * ct[r][l0 + 2 * e2], h0, m0, o0);
-            inexact |= !split3(-2.0f * ct[r][l0 + 2 * e2 + 1], h1, m1, o1);
+            __nv_bfloat16 h0, m0, h1, m1;
+            const float r0 = split2(-2.0f * ct[r][l0 + 2 * e2], h0, m0);
+            const float r1 = split2(-2.0f * ct[r][l0 + 2 * e2 + 1], h1, m1);
+            inexact |= !isfinite(r0) || !isfinite(r1);
+            q = fma((double)r0, (double)r0, q);
+            q = fma((double)r1, (double)r1, q);
             w[0][e2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
             w[1][e2] = (uint32_t)__bfloat16_as_ushort(m0) | ((uint32_t)__bfloat16_as_ushort(m1) << 16);
-            w[2][e2] = (uint32_t)__bfloat16_as_ushort(o0) | ((uint32_t)__bfloat16_as_ushort(o1) << 16);
         }
+        rsq[r][g] = q;
 #pragma unroll
-        for (int pc = 0; pc < 3; ++pc)
+        for (int pc = 0; pc < TC_PIECES; ++pc)
             *reinterpret_cast<uint4 *>(tile + core_off(rt + r, pc * LK + l0, sbo)) =
                 make_uint4(w[pc][0], w[pc][1], w[pc][2], w[pc][3]);
     }
@@ -440,8 +467,8 @@ __global__ void __launch_bounds__(256)
         } else {
             nb = make_uint4((uint32_t)__bfloat16_as_ushort(h), 0u, 0u, 0u);
         }
-        *reinterpret_cast<uint4 *>(tile + core_off(rt + r, 3 * LK, sbo)) = nb;
-        *reinterpret_cast<uint4 *>(tile + core_off(rt + r, 3 * LK + 8, sbo)) = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(tile + core_off(rt + r, TC_PIECES * LK, sbo)) = nb;
+        *reinterpret_cast<uint4 *>(tile + core_off(rt + r, TC_PIECES * LK + 8, sbo)) = make_uint4(0u, 0u, 0u, 0u);
     }
     if (inexact) s_inexact = 1;
     // FP32 codebook for the exact fallback, chunk-major (coalesced along n)
@@ -451,6 +478,14 @@ __global__ void __launch_bounds__(256)
             CT[((size_t)(n / EXACT_SW) * Lp + l) * EXACT_SW + n % EXACT_SW] = l < L ? cs[r][l] : 0.f;
         }
     __syncthreads();
+    if (tid < PT_N) {   // warp 0: ||c'_n - p_hi - p_mid|| rounded up, max of the block, one atomic
+        double q = 0.0;
+#pragma unroll
+        for (int g = 0; g < G8; ++g) q += rsq[tid][g];
+        uint32_t rbits = __float_as_uint(__double2float_ru(sqrt(q)));
+        rbits = __reduce_max_sync(0xffffffffu, rbits);
+        if (tid == 0 && rbits) atomicMax(&st->rho_bits, rbits);
+    }
     if (tid == 0) {
         if (s_bad) flag_error(st, ERR_NONFINITE);
         if (s_inexact) atomicOr(&st->tc_inexact, 1);
@@ -463,8 +498,15 @@ struct TcSmem {
     uint64_t full[3], empty[3], tfull[TC_SLOTS], tempty[TC_SLOTS], xfull, xempty, aready;
     uint32_t tmem_base;
     int abort, inexact, prod_last, mma_tile, mma_job, x_issued, x_done;
-    float v1[2][TC_ROWS], v2[2][TC_ROWS], d[2][TC_ROWS], k[2][TC_ROWS];
-    int i1[2][TC_ROWS];
+    union {   // the tail's two uses are separated by a named barrier
+        struct {
+            float v1[2][TC_ROWS], v2[2][TC_ROWS];   // the halves' top-2 (tail merge)
+            int i1[2][TC_ROWS];
+        } m;
+        struct {
+            float d[2][TC_ROWS], k[2][TC_ROWS];     // exact distances (tail); ||x~||^2 halves (A write)
+        } r;
+    };
 };
 
 __device__ __forceinline__ bool named_sync_or(int id, int threads, bool v)
@@ -511,9 +553,9 @@ __device__ __forceinline__ float tc_write_a(const __nv_bfloat16 *XS, int L, bool
     float part = 0.f;
     if (half == 0) a_words<LK, 0>(XS, crow, L, live, wv, part);
     else a_words<LK, 1>(XS, crow, L, live, wv, part);
-    sh.d[half][crow] = part;
+    sh.r.d[half][crow] = part;
     named_sync(1, 32 * TC_EPI_WARPS);
-    const float xn2 = __fadd_rn(sh.d[0][crow], sh.d[1][crow]);
+    const float xn2 = __fadd_rn(sh.r.d[0][crow], sh.r.d[1][crow]);
     if (half == 1) {
         __nv_bfloat16 h, mi, lo;
         split3(xn2, h, mi, lo);
@@ -611,24 +653,26 @@ template <int LK>
 __device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc, int half, int rr,
                                         int64_t m0, const float *__restrict__ X, int64_t M, int L, int N,
                                         const float *__restrict__ C, const float *__restrict__ kn, float xn2,
-                                        bool usable_tile, float cmax, float V1, float V2, int i1, DevState *st,
+                                        bool usable_tile, float cmax, float rho, float V1, float V2, int i1,
+                                        DevState *st,
                                         int32_t *__restrict__ assign, float *__restrict__ e,
                                         int32_t *__restrict__ flags)
 {
     const int crow = 128 * acc + rr;
     const int64_t m = m0 + crow;
-    sh.v1[half][crow] = V1;
-    sh.v2[half][crow] = V2;
-    sh.i1[half][crow] = i1;
+    sh.m.v1[half][crow] = V1;
+    sh.m.v2[half][crow] = V2;
+    sh.m.i1[half][crow] = i1;
     named_sync(1, 32 * TC_EPI_WARPS);
     {
-        const float A1 = sh.v1[0][crow], A2 = sh.v2[0][crow], B1 = sh.v1[1][crow], B2 = sh.v2[1][crow];
-        const int ai = sh.i1[0][crow], bi = sh.i1[1][crow];
+        const float A1 = sh.m.v1[0][crow], A2 = sh.m.v2[0][crow], B1 = sh.m.v1[1][crow], B2 = sh.m.v2[1][crow];
+        const int ai = sh.m.i1[0][crow], bi = sh.m.i1[1][crow];
         V2 = fminf(fminf(A2, B2), fmaxf(A1, B1));
         const bool take = B1 < A1 || (B1 == A1 && bi < ai);
         V1 = take ? B1 : A1;
         i1 = take ? bi : ai;
     }
+    named_sync(2, 32 * TC_EPI_WARPS);   // merge inputs read: sh.r may now overwrite sh.m
     const bool usable = m < M && !sh.abort && usable_tile && i1 >= 0 && i1 < N && V1 < INFINITY;
     const int cand = i1 + half;
     const int ccand = (usable && cand < N) ? cand : -1;
@@ -688,8 +732,8 @@ __device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc,
         }
         dc = d2;
     }
-    sh.d[half][crow] = dc;
-    sh.k[half][crow] = kc;
+    sh.r.d[half][crow] = dc;
+    sh.r.k[half][crow] = kc;
     named_sync(2, 32 * TC_EPI_WARPS);
     if (half == 0 && m < M && !sh.abort) {
         // the smaller distance is taken when the two differ by more than the
@@ -697,8 +741,8 @@ __device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc,
         // order of the L terms (kept as (L + 4) u); else the row is not certified
         bool certified = false;
         if (usable) {
-            float da = sh.d[0][crow], ka = sh.k[0][crow];
-            const float db = sh.d[1][crow], kb = sh.k[1][crow];
+            float da = sh.r.d[0][crow], ka = sh.r.k[0][crow];
+            const float db = sh.r.d[1][crow], kb = sh.r.k[1][crow];
             int ii = i1;
             bool sure = true;
             if (i1 + 1 < N) {
@@ -712,16 +756,19 @@ __device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc,
                 }
             }
             if (sure) {
-                const double tau = tc_tau(3 * LK + 16);
+                const double tau = tc_tau(tc_kb(LK));
                 const float xn2u = xn2 * SLOP;
                 const float R = 2.f * (float)tau * xn2u * SLOP;
                 const float eta = U32 * (sqrtf(xn2u) + cmax) * SLOP;
                 // index packing of the pair minima, FMA-pipe pair maxima
                 const float pack = TC_PACK * (fabsf(V1) + fabsf(V2)) + TC_HIERR * (fabsf(V1) + 2.f * fabsf(V2));
+                // the MMA sums x~ . (p_hi + p_mid) and misses x~ . r_n, r_n = c'_n - p_hi - p_mid:
+                // |x~ . r_n| <= ||x~|| rho for every n (Cauchy-Schwarz)
+                const float E = sqrtf(xn2u) * rho * SLOP;
                 // V1 ~ ||x~ - c~_ii||^2 - k' (X2 included): bound g1^2 from above
-                const float g1sq = V1 + 2.f * ka + R + pack + (float)(L + 2) * U32 * xn2u;
+                const float g1sq = V1 + 2.f * ka + R + pack + E + (float)(L + 2) * U32 * xn2u;
                 const float g1 = sqrtf(fmaxf(g1sq, 0.f)) * SLOP;
-                const float margin = (2.f * R + 2.f * ka + pack + 4.f * eta * (g1 + eta)) * SLOP;
+                const float margin = (2.f * R + 2.f * ka + pack + 2.f * E + 4.f * eta * (g1 + eta)) * SLOP;
                 certified = (V2 - V1) > margin;
             }
             if (certified) {
@@ -749,7 +796,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int N = cur_n(n_dev, n_host);
     const int ntiles = (N + TC_NT - 1) / TC_NT;
-    constexpr int KB = 3 * LK + 16;
+    constexpr int KB = tc_kb(LK);
     constexpr int XSTR = XsRow<LK>::STR;                       // staged row stride (BF16)
     constexpr uint32_t sbo_b = (uint32_t)(KB / 8) * 128u;
     constexpr uint32_t xs_bytes = (uint32_t)TC_ROWS * XSTR * 2u;
@@ -837,6 +884,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // codebook state written by the preparation kernel (constant here)
     const bool tc_exact_cb = st->tc_inexact == 0;
     const float cmax = __uint_as_float(st->cmax_bits);
+    const float rho = __uint_as_float(st->rho_bits);
 
     float xn2 = 0.f;
     if (epi) xn2 = tc_write_a<LK>(XS, L, m < M, crow, half, acc, warp, tmem, sh);
@@ -892,12 +940,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const uint32_t d = tmem + (uint32_t)(slot * TC_NT);
                 const uint32_t at = tmem + (uint32_t)(TC_A_COL + a * ((LK + 16) / 2));
 #pragma unroll
-                for (int seg = 0; seg < 3; ++seg)
+                for (int seg = 0; seg < TC_PIECES; ++seg)
 #pragma unroll
                     for (int kk = 0; kk < LK / 16; ++kk)
                         mma_bf16_ta_elect(d, at + (uint32_t)(8 * kk), bst + (uint64_t)(seg * LK + kk * 16),
                                           (seg | kk) ? 1u : 0u);
-                mma_bf16_ta_elect(d, at + (uint32_t)(LK / 2), bst + (uint64_t)(3 * LK), 1u);
+                mma_bf16_ta_elect(d, at + (uint32_t)(LK / 2), bst + (uint64_t)(TC_PIECES * LK), 1u);
                 mma_commit_elect(&sh.tfull[slot]);
                 if (lane == 0) sh.mma_job = j;
             }
@@ -913,7 +961,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         int i1;
         tc_jobs(sh, tmem, warp, lane, acc, half, ntiles, 0, keymask, V1, V2, i1);
         tc_tail<LK>(sh, warp, lane, acc, half, rr, m0, X, M, L, N, C, kn, xn2, !sh.inexact && tc_exact_cb,
-                    cmax, V1, V2, i1, st, assign, e, flags);
+                    cmax, rho, V1, V2, i1, st, assign, e, flags);
     }
 
     tc_fence_before();
@@ -946,7 +994,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // MMAs are done (they have consumed its last jobs), and only then finish the
 // previous tile (merge, exact pair distances, certificate), so the tensor pipe
 // starts the next tile while that tail runs.  Codebook tiles stream through
-// a 2-stage ring (the x buffer takes the third stage's space); job and tile
+// a 2-stage ring (a third stage fits but measured no faster: the copies are
+// limited by the SM's bandwidth from L2, not by their latency); job and tile
 // counters run across row tiles, so the barriers' phases continue.
 // Needs L % 4 == 0 and a 16-byte aligned X (the launcher checks).
 constexpr int TC_PSTAGES = 2;
@@ -968,7 +1017,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int ntiles = (N + TC_NT - 1) / TC_NT;
     const int64_t nrt = (M + TC_ROWS - 1) / TC_ROWS;   // row tiles
     const int K = (int)((nrt - (int64_t)blockIdx.x + gridDim.x - 1) / gridDim.x);   // this CTA's
-    constexpr int KB = 3 * LK + 16;
+    constexpr int KB = tc_kb(LK);
     constexpr int XSTR = XsRow<LK>::STR;
     constexpr uint32_t sbo_b = (uint32_t)(KB / 8) * 128u;
     constexpr uint32_t stage_bytes = (uint32_t)TC_NT * KB * 2u;
@@ -1015,6 +1064,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t tmem = sh.tmem_base;
     const bool tc_exact_cb = st->tc_inexact == 0;
     const float cmax = __uint_as_float(st->cmax_bits);
+    const float rho = __uint_as_float(st->rho_bits);
     const int acc = ((warp - 2) >> 2) & 1;
     const int half = (warp - 2) >> 3;
     const int rr = 32 * (warp & 3) + lane;
@@ -1094,12 +1144,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const uint32_t d = tmem + (uint32_t)(slot * TC_NT);
                     const uint32_t at = tmem + (uint32_t)(TC_A_COL + a * ((LK + 16) / 2));
 #pragma unroll
-                    for (int seg = 0; seg < 3; ++seg)
+                    for (int seg = 0; seg < TC_PIECES; ++seg)
 #pragma unroll
                         for (int kk = 0; kk < LK / 16; ++kk)
                             mma_bf16_ta_elect(d, at + (uint32_t)(8 * kk), bst + (uint64_t)(seg * LK + kk * 16),
                                               (seg | kk) ? 1u : 0u);
-                    mma_bf16_ta_elect(d, at + (uint32_t)(LK / 2), bst + (uint64_t)(3 * LK), 1u);
+                    mma_bf16_ta_elect(d, at + (uint32_t)(LK / 2), bst + (uint64_t)(TC_PIECES * LK), 1u);
                     mma_commit_elect(&sh.tfull[slot]);
                     if (lane == 0) sh.mma_job = j;
                 }
@@ -1195,7 +1245,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             if (k >= 1)
                 tc_tail<LK>(sh, warp, lane, acc, half, rr, tile_m0(k - 1), X, M, L, N, C, kn, pxn2, pusable,
-                            cmax, pV1, pV2, pi1, st, assign, e, flags);
+                            cmax, rho, pV1, pV2, pi1, st, assign, e, flags);
             if (k < K) {
                 tc_jobs(sh, tmem, warp, lane, acc, half, ntiles, 2 * k * ntiles, keymask, pV1, pV2, pi1);
                 pxn2 = xn2;
@@ -1237,7 +1287,7 @@ __global__ void k_round_mu(float *mu, int L)
 
 }  // namespace
 
-size_t tc_codebook_bytes(int NP, int L) { return (size_t)tc_prep_rows(NP) * (3 * round_up(L, 16) + 16) * 2; }
+size_t tc_codebook_bytes(int NP, int L) { return (size_t)tc_prep_rows(NP) * tc_kb(round_up(L, 16)) * 2; }
 
 bool tc_supported(int L) { return L >= 1 && L <= TC_LMAX; }
 
@@ -1268,7 +1318,7 @@ static void launch_tc(const float *X, int64_t M, int L, const void *Bp, const fl
     const __nv_bfloat16 *B = static_cast<const __nv_bfloat16 *>(Bp);
     if ((L & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) {
         // persistent: 2 codebook stages + staged BF16 rows + the FP32 x tile
-        const size_t need = (size_t)TC_PSTAGES * TC_NT * (3 * LK + 16) * 2 + (size_t)TC_ROWS * XsRow<LK>::STR * 2 +
+        const size_t need = (size_t)TC_PSTAGES * TC_NT * tc_kb(LK) * 2 + (size_t)TC_ROWS * XsRow<LK>::STR * 2 +
                             (size_t)TC_ROWS * LK * 4;
         // at least 120 KB so that a single CTA (and its 512 TMEM columns) owns the SM
         const size_t smem = need > 120 * 1024 ? need : 120 * 1024;
@@ -1278,7 +1328,7 @@ static void launch_tc(const float *X, int64_t M, int L, const void *Bp, const fl
                                                                e, flags, keymask);
         return;
     }
-    const size_t need = (size_t)TC_ROWS * XsRow<LK>::STR * 2 + (size_t)TC_STAGES * TC_NT * (3 * LK + 16) * 2;
+    const size_t need = (size_t)TC_ROWS * XsRow<LK>::STR * 2 + (size_t)TC_STAGES * TC_NT * tc_kb(LK) * 2;
     // at least 120 KB so that a single CTA (and its 512 TMEM columns) owns the SM
     const size_t smem = need > 120 * 1024 ? need : 120 * 1024;
     cudaFuncSetAttribute(k_assign_tc<LK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

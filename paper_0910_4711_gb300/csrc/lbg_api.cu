@@ -263,7 +263,7 @@ __global__ void k_step_report(const DevState *st, lbg_step_result *r, int use_la
 void run_prepare(const Call &c, const Plan &p, const float *C, const int32_t *n_dev, int n_host,
                  const float *mu, DevState *st)
 {
-    cudaMemsetAsync(&st->cmax_bits, 0, sizeof(uint32_t), c.s);
+    cudaMemsetAsync(&st->cmax_bits, 0, 2 * sizeof(uint32_t), c.s);   // cmax_bits, rho_bits
     if (p.tc)
         launch_prep_tc(C, p.N, n_dev, n_host, p.L, mu, c.at<void>(p.Bp), c.at<float>(p.kn),
                        c.at<float>(p.CT), st, c.s);

@@ -48,6 +48,7 @@ struct DevState {
     int32_t tc_inexact;   // 1 if a BF16 codebook did not split exactly (tensor-core path)
     uint32_t err;         // ERR_* bits
     uint32_t cmax_bits;   // bits of max_n ||c_n - mu|| (non-negative float)
+    uint32_t rho_bits;    // bits of max_n ||c'_n - (its BF16 pieces)|| (tensor-core path)
     double D;             // total distortion of the last pass
     double D_prev;        // distortion of the previous pass of the stage
 };
