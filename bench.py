@@ -476,7 +476,8 @@ def run_ours(args):
     traffic, t_summary, t_digest = measured_traffic(args.precision, args.workload)
     if args.precision == "bf16":
         Lk = (L + 15) // 16 * 16
-        executed = 2.0 * M * N * (3 * Lk + 16) / (assign_ms / 1e3) / 1e12
+        Nt = (N + 143) // 144 * 144      # whole 144-codevector tiles
+        executed = 2.0 * M * Nt * (2 * Lk + 16) / (assign_ms / 1e3) / 1e12
         roof = {"bound": "tensor", "kernel": "k_assign_tc", "achieved": achieved, "peak": bf16_peak,
                 "unit": "TFLOP/s", "frac": achieved / bf16_peak, "traffic": traffic,
                 "traffic_source": (f"profiles/{t_summary} (ncu dram__bytes_read.sum + dram__bytes_write.sum "
@@ -484,8 +485,9 @@ def run_ours(args):
                                    if traffic is not None else
                                    f"null: no capture of the current kernel sources (digest {t_digest})"),
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
-                "work": "2*L*M*N flop per launch (algorithmic; the three-piece BF16 split and the "
-                        "norm column make the tensor cores execute 2*M*N*(3*ceil16(L)+16))",
+                "work": "2*L*M*N flop per launch (algorithmic; the two-piece BF16 split of the codevectors, "
+                        "the norm column and whole 144-codevector tiles make the tensor cores execute "
+                        "2*M*ceil144(N)*(2*ceil16(L)+16))",
                 "executed_tflops": executed, "executed_frac": executed / bf16_peak,
                 "epilogue_bound": {"ops_per_distance": 5, "peak_tops": fp32_peak / 2,
                                    "bound_ms": 5.0 * M * N / (fp32_peak / 2 * 1e12) * 1e3}}
