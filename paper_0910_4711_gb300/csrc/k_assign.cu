@@ -158,6 +158,20 @@ __global__ void __launch_bounds__(256)
 
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 
+// Two rows at once on the packed FP32 pipe: (da, db) += ((xa, xb) - (c, c))^2,
+// each lane rounded exactly as the scalar __fsub_rn / fmaf pair would be.
+__device__ __forceinline__ void sqdiff2(float xa, float xb, uint64_t cc, float &da, float &db)
+{
+    asm("{\n\t.reg .b64 x, d, a;\n\t"
+        "mov.b64 x, {%2, %3};\n\t"
+        "sub.rn.f32x2 d, x, %4;\n\t"
+        "mov.b64 a, {%0, %1};\n\t"
+        "fma.rn.f32x2 a, d, d, a;\n\t"
+        "mov.b64 {%0, %1}, a;\n\t}"
+        : "+f"(da), "+f"(db)
+        : "f"(xa), "f"(xb), "l"(cc));
+}
+
 // Shared state of an assignment CTA (static shared memory of the kernel).
 template <int TBM>
 struct AssignSmemT {
@@ -725,17 +739,13 @@ __global__ void __launch_bounds__(EX_THREADS)
 #pragma unroll 2
                 for (int l = 0; l < L; ++l) {
                     const float c = cb[l * EX_SW + j];
+                    uint64_t cc;
+                    asm("mov.b64 %0, {%1, %1};" : "=l"(cc) : "f"(c));
 #pragma unroll
                     for (int q4 = 0; q4 < XS_HALF / 4; ++q4) {
                         const float4 x4 = lds4(&sh.xs[l][h * XS_HALF + 4 * q4]);
-                        float d = x4.x - c;
-                        d2[4 * q4] = fmaf(d, d, d2[4 * q4]);
-                        d = x4.y - c;
-                        d2[4 * q4 + 1] = fmaf(d, d, d2[4 * q4 + 1]);
-                        d = x4.z - c;
-                        d2[4 * q4 + 2] = fmaf(d, d, d2[4 * q4 + 2]);
-                        d = x4.w - c;
-                        d2[4 * q4 + 3] = fmaf(d, d, d2[4 * q4 + 3]);
+                        sqdiff2(x4.x, x4.y, cc, d2[4 * q4], d2[4 * q4 + 1]);
+                        sqdiff2(x4.z, x4.w, cc, d2[4 * q4 + 2], d2[4 * q4 + 3]);
                     }
                 }
 #pragma unroll
