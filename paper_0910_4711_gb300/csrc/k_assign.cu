@@ -68,6 +68,35 @@ __global__ void __launch_bounds__(256) k_codebook_mean(const float *__restrict__
     if (t == 0) mu[l] = part[0] / (float)N;
 }
 
+// Start of a Lloyd step / encode in one launch: the codebook mean mu (CTA l sums
+// column l as k_codebook_mean does), rounded to integers for the tensor-core
+// form, and the initial device state (CTA 0; st may be null).
+__global__ void __launch_bounds__(256) k_begin(const float *__restrict__ C, int N, int L,
+                                               float *__restrict__ mu, int round_mu, DevState *st,
+                                               int n_cur)
+{
+    __shared__ float part[256];
+    const int l = blockIdx.x, t = threadIdx.x;
+    float s = 0.f;
+    for (int n = t; n < N; n += 256) s += C[(size_t)n * L + l];
+    part[t] = s;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (t < h) part[t] += part[t + h];
+        __syncthreads();
+    }
+    if (t == 0) {
+        const float m = part[0] / (float)N;
+        mu[l] = round_mu ? rintf(m) : m;
+        if (l == 0 && st) {
+            DevState h0 = {};
+            h0.n_cur = n_cur;
+            h0.D_prev = INFINITY;
+            *st = h0;
+        }
+    }
+}
+
 // Prepared codebook, chunk-major: chunk k holds (Lp + 1) x BN floats; row 0
 // is the chain start s0_n = fl(||c~_n||^2 - k_n) (+inf for padding), rows
 // 1..Lp are -2 c~_{n,l} (0 for l >= L or padding).  Also writes k_n, the
@@ -909,6 +938,11 @@ __global__ void k_decode(const int32_t *__restrict__ assign, int64_t M, int L,
 }
 
 }  // namespace
+
+void launch_begin(const float *C, int N, int L, float *mu, bool round_mu, DevState *st, cudaStream_t s)
+{
+    k_begin<<<L, 256, 0, s>>>(C, N, L, mu, round_mu ? 1 : 0, st, N);
+}
 
 void launch_codebook_mean(const float *C, int N, int L, float *mu, cudaStream_t s)
 {

@@ -235,15 +235,6 @@ void init_state(DevState &h, int n_cur)
     h.D_prev = INFINITY;
 }
 
-// Device-side start of a step / encode: the initial DevState (as init_state).
-__global__ void k_state_init(DevState *st, int n_cur)
-{
-    DevState h = {};
-    h.n_cur = n_cur;
-    h.D_prev = INFINITY;
-    *st = h;
-}
-
 // Device-side report of an asynchronous step / encode (finish_status without
 // the max_passes warning, which only lbg_train raises).
 __global__ void k_step_report(const DevState *st, lbg_step_result *r, int use_last)
@@ -261,9 +252,9 @@ __global__ void k_step_report(const DevState *st, lbg_step_result *r, int use_la
 
 // Prepared codebook + one allocation (cell table of C under X) -> assign, e.
 void run_prepare(const Call &c, const Plan &p, const float *C, const int32_t *n_dev, int n_host,
-                 const float *mu, DevState *st)
+                 const float *mu, DevState *st, bool zero_bounds = true)
 {
-    cudaMemsetAsync(&st->cmax_bits, 0, 2 * sizeof(uint32_t), c.s);   // cmax_bits, rho_bits
+    if (zero_bounds) cudaMemsetAsync(&st->cmax_bits, 0, 2 * sizeof(uint32_t), c.s);   // cmax_bits, rho_bits
     if (p.tc)
         launch_prep_tc(C, p.N, n_dev, n_host, p.L, mu, c.at<void>(p.Bp), c.at<float>(p.kn),
                        c.at<float>(p.CT), st, c.s);
@@ -570,11 +561,9 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
     auto issue = [&](cudaStream_t s) {
         Call k = c;
         k.s = s;
-        k_state_init<<<1, 1, 0, s>>>(st, N);
         tm.mark(0, s);
-        launch_codebook_mean(dC, N, L, mu, s);
-        if (p.tc) launch_round_mu(mu, L, s);
-        run_prepare(k, p, dC, nullptr, N, mu, st);
+        launch_begin(dC, N, L, mu, p.tc, st, s);   // also the initial state (cmax, rho zero)
+        run_prepare(k, p, dC, nullptr, N, mu, st, false);
         tm.mark(1, s);
         run_assign(k, p, dX, dC, nullptr, N, mu, st, dI);
         tm.mark(2, s);
@@ -667,11 +656,9 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
     auto issue = [&](cudaStream_t s) {
         Call k = c;
         k.s = s;
-        k_state_init<<<1, 1, 0, s>>>(st, N);
         tm.mark(0, s);
-        launch_codebook_mean(dCi, N, L, mu, s);
-        if (p.tc) launch_round_mu(mu, L, s);
-        run_prepare(k, p, dCi, nullptr, N, mu, st);
+        launch_begin(dCi, N, L, mu, p.tc, st, s);   // also the initial state (cmax, rho zero)
+        run_prepare(k, p, dCi, nullptr, N, mu, st, false);
         tm.mark(1, s);
         run_assign(k, p, dX, dCi, nullptr, N, mu, st, dA);
         tm.mark(2, s);

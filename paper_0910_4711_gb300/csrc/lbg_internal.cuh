@@ -212,6 +212,9 @@ __device__ __forceinline__ void flag_error(DevState *st, uint32_t bits) { atomic
 // ------------------------------------------------------------ launchers
 // Codebook preparation (k_assign.cu).
 void launch_codebook_mean(const float *C, int N, int L, float *mu, cudaStream_t s);
+// mean (rounded to integers if round_mu) and, if st, the initial DevState of a
+// step / encode with N codevectors, in one launch.
+void launch_begin(const float *C, int N, int L, float *mu, bool round_mu, DevState *st, cudaStream_t s);
 void launch_prep(const float *C, int N_alloc, const int32_t *n_dev, int n_host, int L, int Lp,
                  const float *mu, float *Cp, float *kn, float *CT, int NP, DevState *st,
                  cudaStream_t s);
