@@ -98,6 +98,9 @@ constexpr int TC_A_COL = TC_SLOTS * TC_NT;     // TMEM column of the A operand (
 constexpr int TC_TMEM_COLS = 512;              // 3 x 144 accumulator columns + 2 x (L + 16)/2
 constexpr int TC_LMAX = 64;
 constexpr int TC_PIECES = 2;                   // BF16 pieces of c' in B (K blocks of x~ . c')
+constexpr int TC_NCH = 2;                      // independent min-chains of the epilogue (the other
+                                               // epilogue warps of the sub-partition hide the
+                                               // chains' latency; fewer chains, less bookkeeping)
 static_assert(TC_A_COL + 2 * ((TC_LMAX + 16) / 2) <= TC_TMEM_COLS, "accumulators + A exceed TMEM");
 static_assert(TC_HALF == 72 && TC_PAIRS <= (1 << TC_JBITS), "epilogue loads 64 + 8 columns");
 
@@ -184,7 +187,7 @@ struct PairSteps {
     __device__ __forceinline__ static void run(const float *v, float *c1, float *c2, int keymask)
     {
         PairSteps<P - 1>::run(v, c1, c2, keymask);
-        constexpr int j = P - 1, q = j & 3;
+        constexpr int j = P - 1, q = j % TC_NCH;
         const float a = v[2 * j], b = v[2 * j + 1];
         const float lo = fminf(a, b);
         const float hi = __fsub_rn(__fadd_rn(a, b), lo);
@@ -277,8 +280,8 @@ __device__ __forceinline__ int xs_at(int r, int l)
 // The A words of one half of a row (half H of the K = LK + 16 elements, two
 // BF16 per word): centred x~ from the staged row (zero past L and for rows
 // past M), and the running sum of squares of those x~ in order.  Half 1 also
-// holds the norm block, filled in later.
-template <int LK, int H>
+// holds the norm block, filled in later.  FULL: L == LK, nothing to mask.
+template <int LK, int H, bool FULL>
 __device__ __forceinline__ void a_words(const __nv_bfloat16 *XS, int crow, int L, bool live, uint32_t *wv,
                                         float &part)
 {
@@ -294,7 +297,8 @@ __device__ __forceinline__ void a_words(const __nv_bfloat16 *XS, int crow, int L
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int e0 = E0 + 8 * g + 2 * j;
-            const uint32_t lo = e0 < L ? (qs[j] & 0xFFFFu) : 0u, hi = e0 + 1 < L ? (qs[j] >> 16) : 0u;
+            const uint32_t lo = (FULL || e0 < L) ? (qs[j] & 0xFFFFu) : 0u;
+            const uint32_t hi = (FULL || e0 + 1 < L) ? (qs[j] >> 16) : 0u;
             wv[4 * g + j] = lo | (hi << 16);
             const float a = __uint_as_float(lo << 16), b = __uint_as_float(hi << 16);
             part = fmaf(a, a, part);
@@ -544,15 +548,15 @@ __device__ __forceinline__ void tc_put_x(__nv_bfloat16 *XS, int i, int L, float 
 // three BF16 pieces, zeros.  ||x~||^2 is half 0's sum of squares plus half 1's
 // in that order.  Returns ||x~||^2 of the thread's row; the caller fences and
 // synchronises before the MMAs read A.
-template <int LK>
+template <int LK, bool FULL>
 __device__ __forceinline__ float tc_write_a(const __nv_bfloat16 *XS, int L, bool live, int crow, int half,
                                             int acc, int warp, uint32_t tmem, TcSmem &sh)
 {
     constexpr int KA = LK + 16, NW = KA / 4;
     uint32_t wv[NW];
     float part = 0.f;
-    if (half == 0) a_words<LK, 0>(XS, crow, L, live, wv, part);
-    else a_words<LK, 1>(XS, crow, L, live, wv, part);
+    if (half == 0) a_words<LK, 0, FULL>(XS, crow, L, live, wv, part);
+    else a_words<LK, 1, FULL>(XS, crow, L, live, wv, part);
     sh.r.d[half][crow] = part;
     named_sync(1, 32 * TC_EPI_WARPS);
     const float xn2 = __fadd_rn(sh.r.d[0][crow], sh.r.d[1][crow]);
@@ -585,7 +589,7 @@ __device__ __forceinline__ void tc_jobs(TcSmem &sh, uint32_t tmem, int warp, int
                                         int ntiles, int j0, int keymask, float &V1, float &V2, int &i1,
                                         const Hook &hook = Hook())
 {
-    constexpr int NCH = 4;   // independent min-chains
+    constexpr int NCH = TC_NCH;
     constexpr int JMASK = (1 << TC_JBITS) - 1;
     float c1[NCH], c2[NCH];
     int cg[NCH];
@@ -596,9 +600,18 @@ __device__ __forceinline__ void tc_jobs(TcSmem &sh, uint32_t tmem, int warp, int
         cg[q] = 0;
     }
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    // job j = j0 + 2 t + acc: slot j % 3 and the parity of j / 3, stepped by j += 2
+    int slot = (j0 + acc) % TC_SLOTS;
+    uint32_t par = (uint32_t)((j0 + acc) / TC_SLOTS) & 1u;
     for (int t = 0; t < ntiles; ++t) {
-        const int j = j0 + 2 * t + acc, slot = j % TC_SLOTS;
-        if (sh.abort || !mbar_wait_bounded_sleep(&sh.tfull[slot], (uint32_t)(j / TC_SLOTS) & 1u)) {
+        if (t > 0) {
+            slot += 2;
+            if (slot >= TC_SLOTS) {
+                slot -= TC_SLOTS;
+                par ^= 1u;
+            }
+        }
+        if (sh.abort || !mbar_wait_bounded_sleep(&sh.tfull[slot], par)) {
             sh.abort = 1;
             hook(t);
             continue;
@@ -887,7 +900,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const float rho = __uint_as_float(st->rho_bits);
 
     float xn2 = 0.f;
-    if (epi) xn2 = tc_write_a<LK>(XS, L, m < M, crow, half, acc, warp, tmem, sh);
+    if (epi)
+        xn2 = L == LK ? tc_write_a<LK, true>(XS, L, m < M, crow, half, acc, warp, tmem, sh)
+                      : tc_write_a<LK, false>(XS, L, m < M, crow, half, acc, warp, tmem, sh);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -1238,7 +1253,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 // conversion's named barrier), its MMAs are done and A may be rewritten
                 for (int c = 0; c < NCHUNK; ++c) convert(k, c);
                 tile_exact = next_exact;
-                xn2 = tc_write_a<LK>(XS, L, tile_m0(k) + crow < M, crow, half, acc, warp, tmem, sh);
+                xn2 = L == LK ? tc_write_a<LK, true>(XS, L, tile_m0(k) + crow < M, crow, half, acc, warp, tmem, sh)
+                              : tc_write_a<LK, false>(XS, L, tile_m0(k) + crow < M, crow, half, acc, warp, tmem, sh);
                 tc_fence_before();
                 named_sync(1, 32 * TC_EPI_WARPS);
                 if (tid == 64) mbar_arrive(&sh.aready);
