@@ -452,7 +452,8 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 2)
     k_assign_f32(const float *__restrict__ X, int64_t M, int L, int Lp, const float *__restrict__ Cp,
                  const float *__restrict__ kn, const int32_t *n_dev, int n_host,
                  const float *__restrict__ mu, const float *__restrict__ C, DevState *st,
-                 int32_t *__restrict__ assign, float *__restrict__ e, int32_t *__restrict__ flags)
+                 int32_t *__restrict__ assign, float *__restrict__ e, int32_t *__restrict__ flags,
+                 int64_t m_lo)
 {
     if (st->finished) return;
     extern __shared__ __align__(128) float smem[];
@@ -466,7 +467,7 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 2)
     __syncthreads();
     uint32_t u0 = 0, u1 = 0;
     (void)assign_f32_tile_t<BM>(X, M, L, Lp, Cp, kn, cur_n(n_dev, n_host), mu, C, st, assign, e, flags,
-                                (int64_t)blockIdx.x * BM, smem, sh, u0, u1);
+                                m_lo + (int64_t)blockIdx.x * BM, smem, sh, u0, u1);
 }
 
 // Batched problems: a persistent CTA takes (problem, row tile) work items from
@@ -961,14 +962,14 @@ size_t assign_smem_bytes(int Lp) { return (size_t)(Lp * BM + 2 * (Lp + 1) * BN) 
 
 void launch_assign(const float *X, int64_t M, int L, int Lp, const float *Cp, const float *kn,
                    const int32_t *n_dev, int n_host, const float *mu, const float *C, DevState *st,
-                   int32_t *assign, float *e, int32_t *flags, cudaStream_t s)
+                   int32_t *assign, float *e, int32_t *flags, cudaStream_t s, int64_t m_lo)
 {
     const size_t smem = assign_smem_bytes(Lp);
     cudaFuncSetAttribute(k_assign_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int64_t grid = (M + BM - 1) / BM;
-    if (grid == 0) return;
+    const int64_t grid = (M - m_lo + BM - 1) / BM;
+    if (grid <= 0) return;
     k_assign_f32<<<(unsigned)grid, ASSIGN_THREADS, smem, s>>>(X, M, L, Lp, Cp, kn, n_dev, n_host, mu,
-                                                              C, st, assign, e, flags);
+                                                              C, st, assign, e, flags, m_lo);
 }
 
 void launch_exact(const float *X, int L, int Lp, const float *CT, const int32_t *n_dev, int n_host,

@@ -800,7 +800,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const __nv_bfloat16 *__restrict__ Bp, const float *__restrict__ kn,
                 const int32_t *n_dev, int n_host, const float *__restrict__ mu,
                 const float *__restrict__ C, DevState *st, int32_t *__restrict__ assign,
-                float *__restrict__ e, int32_t *__restrict__ flags, int keymask)
+                float *__restrict__ e, int32_t *__restrict__ flags, int keymask,
+                int64_t m_lo)
 {
     if (st->finished) return;
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -816,7 +817,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     constexpr uint32_t stage_bytes = (uint32_t)TC_NT * KB * 2u;
     __nv_bfloat16 *XS = reinterpret_cast<__nv_bfloat16 *>(smem);
     uint8_t *Bs = smem + xs_bytes;
-    const int64_t m0 = (int64_t)blockIdx.x * TC_ROWS;
+    const int64_t m0 = m_lo + (int64_t)blockIdx.x * TC_ROWS;
 
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
@@ -1021,7 +1022,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                   const __nv_bfloat16 *__restrict__ Bp, const float *__restrict__ kn,
                   const int32_t *n_dev, int n_host, const float *__restrict__ mu,
                   const float *__restrict__ C, DevState *st, int32_t *__restrict__ assign,
-                  float *__restrict__ e, int32_t *__restrict__ flags, int keymask)
+                  float *__restrict__ e, int32_t *__restrict__ flags, int keymask,
+                  int64_t m_lo)
 {
     if (st->finished) return;
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -1030,7 +1032,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int N = cur_n(n_dev, n_host);
     const int ntiles = (N + TC_NT - 1) / TC_NT;
-    const int64_t nrt = (M + TC_ROWS - 1) / TC_ROWS;   // row tiles
+    const int64_t nrt = (M - m_lo + TC_ROWS - 1) / TC_ROWS;   // row tiles of rows [m_lo, M)
     const int K = (int)((nrt - (int64_t)blockIdx.x + gridDim.x - 1) / gridDim.x);   // this CTA's
     constexpr int KB = tc_kb(LK);
     constexpr int XSTR = XsRow<LK>::STR;
@@ -1040,7 +1042,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint8_t *Bs = smem;
     __nv_bfloat16 *XS = reinterpret_cast<__nv_bfloat16 *>(smem + TC_PSTAGES * stage_bytes);
     float *XF = reinterpret_cast<float *>(smem + TC_PSTAGES * stage_bytes + xs_bytes);
-    auto tile_m0 = [&](int k) -> int64_t { return ((int64_t)blockIdx.x + (int64_t)k * gridDim.x) * TC_ROWS; };
+    auto tile_m0 = [&](int k) -> int64_t {
+        return m_lo + ((int64_t)blockIdx.x + (int64_t)k * gridDim.x) * TC_ROWS;
+    };
     auto tile_rows = [&](int k) -> int64_t {
         const int64_t r = M - tile_m0(k);
         return r < TC_ROWS ? r : TC_ROWS;
@@ -1326,10 +1330,10 @@ void launch_prep_tc(const float *C, int N_alloc, const int32_t *n_dev, int n_hos
 template <int LK>
 static void launch_tc(const float *X, int64_t M, int L, const void *Bp, const float *kn,
                       const int32_t *n_dev, int n_host, const float *mu, const float *C, DevState *st,
-                      int32_t *assign, float *e, int32_t *flags, cudaStream_t s)
+                      int32_t *assign, float *e, int32_t *flags, cudaStream_t s, int64_t m_lo)
 {
-    const int64_t grid = (M + TC_ROWS - 1) / TC_ROWS;
-    if (grid == 0) return;
+    const int64_t grid = (M - m_lo + TC_ROWS - 1) / TC_ROWS;
+    if (grid <= 0) return;
     const int keymask = ~((1 << TC_JBITS) - 1);
     const __nv_bfloat16 *B = static_cast<const __nv_bfloat16 *>(Bp);
     if ((L & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) {
@@ -1341,7 +1345,7 @@ static void launch_tc(const float *X, int64_t M, int L, const void *Bp, const fl
         cudaFuncSetAttribute(k_assign_tc_p<LK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         const int64_t g = grid < 152 ? grid : 152;
         k_assign_tc_p<LK><<<(unsigned)g, TC_THREADS, smem, s>>>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign,
-                                                               e, flags, keymask);
+                                                               e, flags, keymask, m_lo);
         return;
     }
     const size_t need = (size_t)TC_ROWS * XsRow<LK>::STR * 2 + (size_t)TC_STAGES * TC_NT * tc_kb(LK) * 2;
@@ -1349,18 +1353,19 @@ static void launch_tc(const float *X, int64_t M, int L, const void *Bp, const fl
     const size_t smem = need > 120 * 1024 ? need : 120 * 1024;
     cudaFuncSetAttribute(k_assign_tc<LK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_assign_tc<LK><<<(unsigned)grid, TC_THREADS, smem, s>>>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign,
-                                                             e, flags, keymask);
+                                                             e, flags, keymask, m_lo);
 }
 
 void launch_assign_tc(const float *X, int64_t M, int L, const void *Bp, const float *kn,
                       const int32_t *n_dev, int n_host, const float *mu, const float *C,
-                      DevState *st, int32_t *assign, float *e, int32_t *flags, cudaStream_t s)
+                      DevState *st, int32_t *assign, float *e, int32_t *flags, cudaStream_t s,
+                      int64_t m_lo)
 {
     switch (round_up(L, 16)) {
-    case 16: launch_tc<16>(X, M, L, Bp, kn, n_dev, n_host, mu, C, st, assign, e, flags, s); break;
-    case 32: launch_tc<32>(X, M, L, Bp, kn, n_dev, n_host, mu, C, st, assign, e, flags, s); break;
-    case 48: launch_tc<48>(X, M, L, Bp, kn, n_dev, n_host, mu, C, st, assign, e, flags, s); break;
-    default: launch_tc<64>(X, M, L, Bp, kn, n_dev, n_host, mu, C, st, assign, e, flags, s); break;
+    case 16: launch_tc<16>(X, M, L, Bp, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo); break;
+    case 32: launch_tc<32>(X, M, L, Bp, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo); break;
+    case 48: launch_tc<48>(X, M, L, Bp, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo); break;
+    default: launch_tc<64>(X, M, L, Bp, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo); break;
     }
 }
 

@@ -10,6 +10,7 @@
 #include <array>
 #include <map>
 #include <mutex>
+#include <algorithm>
 #include <vector>
 
 using namespace lbg;
@@ -263,15 +264,62 @@ void run_prepare(const Call &c, const Plan &p, const float *C, const int32_t *n_
                     c.at<float>(p.CT), p.NP, st, c.s);
 }
 
+// Nearest codevector of rows [m_lo, m_hi) (default: all rows).
 void run_assign(const Call &c, const Plan &p, const float *X, const float *C, const int32_t *n_dev,
-                int n_host, const float *mu, DevState *st, int32_t *assign)
+                int n_host, const float *mu, DevState *st, int32_t *assign, int64_t m_lo = 0,
+                int64_t m_hi = -1)
 {
+    const int64_t M = m_hi < 0 ? p.M : m_hi;
     if (p.tc)
-        launch_assign_tc(X, p.M, p.L, c.at<void>(p.Bp), c.at<float>(p.kn), n_dev, n_host, mu, C, st,
-                         assign, c.at<float>(p.e), c.at<int32_t>(p.flags), c.s);
+        launch_assign_tc(X, M, p.L, c.at<void>(p.Bp), c.at<float>(p.kn), n_dev, n_host, mu, C, st,
+                         assign, c.at<float>(p.e), c.at<int32_t>(p.flags), c.s, m_lo);
     else
-        launch_assign(X, p.M, p.L, p.Lp, c.at<float>(p.Cp), c.at<float>(p.kn), n_dev, n_host, mu, C,
-                      st, assign, c.at<float>(p.e), c.at<int32_t>(p.flags), c.s);
+        launch_assign(X, M, p.L, p.Lp, c.at<float>(p.Cp), c.at<float>(p.kn), n_dev, n_host, mu, C,
+                      st, assign, c.at<float>(p.e), c.at<int32_t>(p.flags), c.s, m_lo);
+}
+
+// Host-resident X: its rows go to the device staging buffer Xs in HOST_CHUNKS
+// pieces on a copy stream, and the nearest-codevector search of each piece
+// starts as soon as it has landed, so that the host-to-device copy (the
+// larger cost of a step from host memory) overlaps the search.  Returns false
+// if a CUDA call failed.
+constexpr int HOST_CHUNKS = 8;
+cudaStream_t g_copy[MAX_DEVICES];
+cudaEvent_t g_copy_ev[MAX_DEVICES][HOST_CHUNKS + 1];
+
+// The copies may start once everything issued so far on c.s (earlier users of
+// Xs) is done: called at the start of the call's device work, so that they
+// overlap the codebook preparation too.
+bool host_copy_begin(const Call &c)
+{
+    const int d = c.dev;
+    if (!g_copy[d]) {
+        if (cudaStreamCreateWithFlags(&g_copy[d], cudaStreamNonBlocking) != cudaSuccess) return false;
+        for (auto &e : g_copy_ev[d])
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
+    }
+    return cudaEventRecord(g_copy_ev[d][HOST_CHUNKS], c.s) == cudaSuccess &&
+           cudaStreamWaitEvent(g_copy[d], g_copy_ev[d][HOST_CHUNKS], 0) == cudaSuccess;
+}
+
+bool run_assign_host(const Call &c, const Plan &p, const float *hostX, float *Xs, const float *C,
+                     const int32_t *n_dev, int n_host, const float *mu, DevState *st, int32_t *assign)
+{
+    const int d = c.dev;
+    // pieces in whole 256-row tiles
+    const int64_t tiles = (p.M + 255) / 256;
+    for (int k = 0; k < HOST_CHUNKS; ++k) {
+        const int64_t r0 = std::min<int64_t>(p.M, tiles * k / HOST_CHUNKS * 256);
+        const int64_t r1 = std::min<int64_t>(p.M, tiles * (k + 1) / HOST_CHUNKS * 256);
+        if (r1 <= r0) continue;
+        const size_t off = (size_t)r0 * p.L, bytes = sizeof(float) * (size_t)(r1 - r0) * p.L;
+        if (cudaMemcpyAsync(Xs + off, hostX + off, bytes, cudaMemcpyHostToDevice, g_copy[d]) != cudaSuccess ||
+            cudaEventRecord(g_copy_ev[d][k], g_copy[d]) != cudaSuccess ||
+            cudaStreamWaitEvent(c.s, g_copy_ev[d][k], 0) != cudaSuccess)
+            return false;
+        run_assign(c, p, Xs, C, n_dev, n_host, mu, st, assign, r0, r1);
+    }
+    return true;
 }
 
 void run_exact(const Call &c, const Plan &p, const float *X, const int32_t *n_dev, int n_host,
@@ -541,12 +589,9 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
     const Plan p = make_plan(M, L, N, 0, wX == 0, wI == 0, wC == 0, wH == 0, mode == 1);
     if ((rc = ensure_workspace(c, p.total)) != LBG_OK) return rc;
     DevState *st = c.at<DevState>(p.state);
-    const float *dX = X;
+    // host X: copied piece by piece inside the assignment step (run_assign_host)
+    const float *dX = wX == 0 ? c.at<float>(p.Xs) : X;
     const float *dC = C;
-    if (wX == 0) {
-        CK(cudaMemcpyAsync(c.at<float>(p.Xs), X, sizeof(float) * M * L, cudaMemcpyHostToDevice, c.s));
-        dX = c.at<float>(p.Xs);
-    }
     if (wC == 0) {
         CK(cudaMemcpyAsync(c.at<float>(p.Cin), C, sizeof(float) * (size_t)N * L,
                            cudaMemcpyHostToDevice, c.s));
@@ -555,17 +600,23 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
     int32_t *dI = wI ? idx : c.at<int32_t>(p.assign);
     float *dH = Xhat ? (wH ? Xhat : c.at<float>(p.Xhat)) : nullptr;
     const bool wantD = D || res;
+    bool host_ok = true;
     Timer tm;
     if ((rc = tm.init(o.phase_ms != nullptr)) != LBG_OK) return rc;
     float *mu = c.at<float>(p.mu);
     auto issue = [&](cudaStream_t s) {
         Call k = c;
         k.s = s;
+        if (wX == 0 && !host_copy_begin(k)) host_ok = false;
         tm.mark(0, s);
         launch_begin(dC, N, L, mu, p.tc, st, s);   // also the initial state (cmax, rho zero)
         run_prepare(k, p, dC, nullptr, N, mu, st, false);
         tm.mark(1, s);
-        run_assign(k, p, dX, dC, nullptr, N, mu, st, dI);
+        if (wX == 0) {
+            if (!run_assign_host(k, p, X, c.at<float>(p.Xs), dC, nullptr, N, mu, st, dI)) host_ok = false;
+        } else {
+            run_assign(k, p, dX, dC, nullptr, N, mu, st, dI);
+        }
         tm.mark(2, s);
         run_exact(k, p, dX, nullptr, N, st, dI);
         tm.mark(3, s);
@@ -578,8 +629,9 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
         if (res) k_step_report<<<1, 1, 0, s>>>(st, res, 1);
         tm.mark(4, s);
     };
-    if (o.phase_ms) {
+    if (o.phase_ms || wX == 0) {   // direct: timed phases, or the pieces of a host X
         issue(c.s);
+        if (!host_ok) return LBG_ERR_CUDA;
         CK(cudaGetLastError());
     } else {
         const SeqKey key{c.dev, 1, mode, (wantD ? 2 : 0) | (dH ? 4 : 0), M, L, N, p.total, 0.0,
@@ -637,11 +689,8 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
         return LBG_OK;
     }
     DevState *st = c.at<DevState>(p.state);
-    const float *dX = X;
-    if (wX == 0) {
-        CK(cudaMemcpyAsync(c.at<float>(p.Xs), X, sizeof(float) * M * L, cudaMemcpyHostToDevice, c.s));
-        dX = c.at<float>(p.Xs);
-    }
+    // host X: copied piece by piece inside the assignment step (run_assign_host)
+    const float *dX = wX == 0 ? c.at<float>(p.Xs) : X;
     const float *dCi = C_in;
     float *dCo = C_out;
     if (hostC) {
@@ -650,17 +699,23 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
         dCo = c.at<float>(p.Cout);
     }
     int32_t *dA = wsA ? c.at<int32_t>(p.assign) : assign;
+    bool host_ok = true;
     Timer tm;
     if ((rc = tm.init(o.phase_ms != nullptr)) != LBG_OK) return rc;
     float *mu = c.at<float>(p.mu);
     auto issue = [&](cudaStream_t s) {
         Call k = c;
         k.s = s;
+        if (wX == 0 && !host_copy_begin(k)) host_ok = false;
         tm.mark(0, s);
         launch_begin(dCi, N, L, mu, p.tc, st, s);   // also the initial state (cmax, rho zero)
         run_prepare(k, p, dCi, nullptr, N, mu, st, false);
         tm.mark(1, s);
-        run_assign(k, p, dX, dCi, nullptr, N, mu, st, dA);
+        if (wX == 0) {
+            if (!run_assign_host(k, p, X, c.at<float>(p.Xs), dCi, nullptr, N, mu, st, dA)) host_ok = false;
+        } else {
+            run_assign(k, p, dX, dCi, nullptr, N, mu, st, dA);
+        }
         tm.mark(2, s);
         run_exact(k, p, dX, nullptr, N, st, dA);
         tm.mark(3, s);
@@ -673,8 +728,9 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
         if (res) k_step_report<<<1, 1, 0, s>>>(st, res, 1);
         tm.mark(4, s);
     };
-    if (o.phase_ms) {
+    if (o.phase_ms || wX == 0) {   // direct: timed phases, or the pieces of a host X
         issue(c.s);
+        if (!host_ok) return LBG_ERR_CUDA;
         CK(cudaGetLastError());
     } else {
         const SeqKey key{c.dev, 0, mode, o.reseed_empty ? 1 : 0, M, L, N, p.total,

@@ -218,9 +218,11 @@ void launch_begin(const float *C, int N, int L, float *mu, bool round_mu, DevSta
 void launch_prep(const float *C, int N_alloc, const int32_t *n_dev, int n_host, int L, int Lp,
                  const float *mu, float *Cp, float *kn, float *CT, int NP, DevState *st,
                  cudaStream_t s);
+// Nearest codevector of rows [m_lo, M) of X (row indices, assign, e and flags
+// stay global).
 void launch_assign(const float *X, int64_t M, int L, int Lp, const float *Cp, const float *kn,
                    const int32_t *n_dev, int n_host, const float *mu, const float *C, DevState *st,
-                   int32_t *assign, float *e, int32_t *flags, cudaStream_t s);
+                   int32_t *assign, float *e, int32_t *flags, cudaStream_t s, int64_t m_lo = 0);
 void launch_exact(const float *X, int L, int Lp, const float *CT, const int32_t *n_dev, int n_host,
                   DevState *st, const int32_t *flags, int32_t *assign, float *e, int64_t M,
                   cudaStream_t s);
@@ -243,7 +245,7 @@ void launch_prep_tc(const float *C, int N_alloc, const int32_t *n_dev, int n_hos
                     const float *mu, void *Bp, float *kn, float *CT, DevState *st, cudaStream_t s);
 void launch_assign_tc(const float *X, int64_t M, int L, const void *Bp, const float *kn,
                       const int32_t *n_dev, int n_host, const float *mu, const float *C,
-                      DevState *st, int32_t *assign, float *e, int32_t *flags, cudaStream_t s);
+                      DevState *st, int32_t *assign, float *e, int32_t *flags, cudaStream_t s, int64_t m_lo = 0);
 
 // Cell table, distortion and centroid update (k_update.cu).
 void launch_mean(const float *X, int64_t M, int L, double *part, int G, float *mu, float *C0,
