@@ -278,12 +278,16 @@ void run_assign(const Call &c, const Plan &p, const float *X, const float *C, co
                       st, assign, c.at<float>(p.e), c.at<int32_t>(p.flags), c.s, m_lo);
 }
 
-// Host-resident X: its rows go to the device staging buffer Xs in HOST_CHUNKS
-// pieces on a copy stream, and the nearest-codevector search of each piece
-// starts as soon as it has landed, so that the host-to-device copy (the
-// larger cost of a step from host memory) overlaps the search.  Returns false
-// if a CUDA call failed.
-constexpr int HOST_CHUNKS = 8;
+// Host-resident X: its rows go to the device staging buffer Xs in pieces on a
+// copy stream, and the nearest-codevector search of each piece starts as soon
+// as it has landed, so that the host-to-device copy (the larger cost of a step
+// from host memory) overlaps the search.  A piece is one wave of the search
+// (152 SMs x 256 rows; the FP32 kernel's wave, 2 x 152 x 128 rows, is the
+// same), so that each piece's search keeps pace with the next piece's copy
+// (measured ~210 GB/s host-to-device); at most HOST_CHUNKS pieces.  Returns
+// false if a CUDA call failed.
+constexpr int HOST_CHUNKS = 32;
+constexpr int64_t HOST_PIECE_ROWS = 152 * 256;
 cudaStream_t g_copy[MAX_DEVICES];
 cudaEvent_t g_copy_ev[MAX_DEVICES][HOST_CHUNKS + 1];
 
@@ -308,9 +312,11 @@ bool run_assign_host(const Call &c, const Plan &p, const float *hostX, float *Xs
     const int d = c.dev;
     // pieces in whole 256-row tiles
     const int64_t tiles = (p.M + 255) / 256;
-    for (int k = 0; k < HOST_CHUNKS; ++k) {
-        const int64_t r0 = std::min<int64_t>(p.M, tiles * k / HOST_CHUNKS * 256);
-        const int64_t r1 = std::min<int64_t>(p.M, tiles * (k + 1) / HOST_CHUNKS * 256);
+    int64_t np = (p.M + HOST_PIECE_ROWS - 1) / HOST_PIECE_ROWS;
+    if (np > HOST_CHUNKS) np = HOST_CHUNKS;
+    for (int k = 0; k < np; ++k) {
+        const int64_t r0 = std::min<int64_t>(p.M, tiles * k / np * 256);
+        const int64_t r1 = std::min<int64_t>(p.M, tiles * (k + 1) / np * 256);
         if (r1 <= r0) continue;
         const size_t off = (size_t)r0 * p.L, bytes = sizeof(float) * (size_t)(r1 - r0) * p.L;
         if (cudaMemcpyAsync(Xs + off, hostX + off, bytes, cudaMemcpyHostToDevice, g_copy[d]) != cudaSuccess ||
