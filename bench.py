@@ -520,7 +520,7 @@ def run_ours(args):
                                         "write codebook, counts)",
                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"},
             "clocks": clocks,
-            "gpu_launches": 12 * args.steps}
+            "gpu_launches": 10 * args.steps}
     if other_line is not None:
         line["other_precision"] = other_line
 

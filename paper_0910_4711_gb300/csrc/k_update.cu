@@ -294,6 +294,42 @@ __global__ void __launch_bounds__(1024) k_offsets(const int32_t *__restrict__ co
     body_offsets(counts, cur_n(n_dev, n_host), off);
 }
 
+// ---------------------------------------------------------------- fused (step forms)
+// The last CTA to finish (a counter in the state; __threadfence before it, so
+// that every CTA's partials are visible to it) runs the second kernel's body
+// and resets the counter.
+__device__ __forceinline__ bool last_cta(DevState *st)
+{
+    __shared__ int is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(&st->done_ctr, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    return true;
+}
+
+__global__ void __launch_bounds__(HIST_THREADS)
+    k_hist_ctl(const int32_t *__restrict__ assign, const float *__restrict__ e, int64_t M, int64_t R,
+               int N, int do_hist, int32_t *__restrict__ table, double *__restrict__ dpart, DevState *st)
+{
+    body_hist(assign, e, M, R, N, do_hist, table, dpart, st, blockIdx.x);
+    if (!last_cta(st)) return;
+    if (threadIdx.x == 0) st->done_ctr = 0u;
+    body_ctl(dpart, gridDim.x, st, MODE_STEP, 0.0, 1, N, nullptr, 0);
+}
+
+__global__ void __launch_bounds__(1024)
+    k_scan_offsets(int32_t *__restrict__ table, int CH, int N, int32_t *__restrict__ counts,
+                   int32_t *__restrict__ off, DevState *st)
+{
+    if ((int)blockIdx.x * 32 < N) body_scan(table, CH, N, counts, blockIdx.x);
+    if (!last_cta(st)) return;
+    if (threadIdx.x == 0) st->done_ctr = 0u;
+    body_offsets(counts, N, off);
+}
+
 // ---------------------------------------------------------------- scatter
 // CTA per chunk (same chunks as k_hist).  Rows are taken in rounds of 256 in
 // index order; inside a round a row's slot is
@@ -823,6 +859,20 @@ void launch_ctl(const double *dpart, int CH, DevState *st, int mode, double thet
                 int N_target, PassRecord *records, int max_records, cudaStream_t s)
 {
     k_ctl<<<1, 32, 0, s>>>(dpart, CH, st, mode, theta, max_passes, N_target, records, max_records);
+}
+
+void launch_hist_ctl(const int32_t *assign, const float *e, int64_t M, int64_t R, int CH, int N,
+                     bool do_hist, int32_t *table, double *dpart, DevState *st, cudaStream_t s)
+{
+    const size_t smem = do_hist ? (size_t)N * sizeof(int) : 0;
+    cudaFuncSetAttribute(k_hist_ctl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_hist_ctl<<<CH, HIST_THREADS, smem, s>>>(assign, e, M, R, N, do_hist ? 1 : 0, table, dpart, st);
+}
+
+void launch_scan_offsets(int32_t *table, int CH, int N, int32_t *counts, int32_t *off, DevState *st,
+                         cudaStream_t s)
+{
+    k_scan_offsets<<<(N + 31) / 32, 1024, 0, s>>>(table, CH, N, counts, off, st);
 }
 
 void launch_scan(int32_t *table, int CH, const int32_t *n_dev, int n_host, int32_t *counts,

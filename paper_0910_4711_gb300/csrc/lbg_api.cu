@@ -341,8 +341,12 @@ void run_update(const Call &c, const Plan &p, const float *X, const int32_t *n_d
                 DevState *st, const int32_t *assign, const float *C_in, float *C_out, bool train)
 {
     int32_t *table = c.at<int32_t>(p.table), *off = c.at<int32_t>(p.off);
-    launch_scan(table, p.CH, n_dev, n_host, c.at<int32_t>(p.counts), st, train, c.s);
-    launch_offsets(c.at<int32_t>(p.counts), n_dev, n_host, p.M, off, st, train, c.s);
+    if (!train && !n_dev) {
+        launch_scan_offsets(table, p.CH, n_host, c.at<int32_t>(p.counts), off, st, c.s);
+    } else {
+        launch_scan(table, p.CH, n_dev, n_host, c.at<int32_t>(p.counts), st, train, c.s);
+        launch_offsets(c.at<int32_t>(p.counts), n_dev, n_host, p.M, off, st, train, c.s);
+    }
     launch_scatter(assign, p.M, p.R, p.CH, table, off, n_dev, n_host, c.at<int32_t>(p.perm), st,
                    train, c.s);
     launch_cellsum(X, p.M, p.L, c.at<int32_t>(p.perm), off, n_dev, n_host, p.S,
@@ -626,11 +630,7 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
         tm.mark(2, s);
         run_exact(k, p, dX, nullptr, N, st, dI);
         tm.mark(3, s);
-        if (wantD) {
-            launch_hist(dI, k.at<float>(p.e), M, p.R, p.CH, nullptr, N, false, nullptr,
-                        k.at<double>(p.dpart), st, false, s);
-            launch_ctl(k.at<double>(p.dpart), p.CH, st, MODE_STEP, 0.0, 1, N, nullptr, 0, s);
-        }
+        if (wantD) launch_hist_ctl(dI, k.at<float>(p.e), M, p.R, p.CH, N, false, nullptr, k.at<double>(p.dpart), st, s);
         if (dH) launch_decode(dI, M, L, dC, dH, s);
         if (res) k_step_report<<<1, 1, 0, s>>>(st, res, 1);
         tm.mark(4, s);
@@ -725,9 +725,8 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
         tm.mark(2, s);
         run_exact(k, p, dX, nullptr, N, st, dA);
         tm.mark(3, s);
-        launch_hist(dA, k.at<float>(p.e), M, p.R, p.CH, nullptr, N, true, k.at<int32_t>(p.table),
-                    k.at<double>(p.dpart), st, false, s);
-        launch_ctl(k.at<double>(p.dpart), p.CH, st, MODE_STEP, 0.0, 1, N, nullptr, 0, s);
+        launch_hist_ctl(dA, k.at<float>(p.e), M, p.R, p.CH, N, true, k.at<int32_t>(p.table),
+                        k.at<double>(p.dpart), st, s);
         run_update(k, p, dX, nullptr, N, st, dA, dCi, dCo, false);
         if (o.reseed_empty)
             launch_reseed(k.at<int32_t>(p.off), nullptr, N, L, o.delta_reseed, dCo, st, false, s);
@@ -806,15 +805,13 @@ lbg_status lbg_distortion_backward(const float *X, int64_t M, int32_t L, const f
     tm.mark(2, c.s);
     tm.mark(3, c.s);
     if (M > 0) {
-        launch_hist(dA, c.at<float>(p.e), M, p.R, p.CH, nullptr, N, gC != nullptr, c.at<int32_t>(p.table),
-                    c.at<double>(p.dpart), st, false, c.s);
-        launch_ctl(c.at<double>(p.dpart), p.CH, st, MODE_STEP, 0.0, 1, N, nullptr, 0, c.s);
+        launch_hist_ctl(dA, c.at<float>(p.e), M, p.R, p.CH, N, gC != nullptr, c.at<int32_t>(p.table),
+                        c.at<double>(p.dpart), st, c.s);
     }
     if (gC) {
         if (M > 0) {
             int32_t *table = c.at<int32_t>(p.table), *off = c.at<int32_t>(p.off);
-            launch_scan(table, p.CH, nullptr, N, c.at<int32_t>(p.counts), st, false, c.s);
-            launch_offsets(c.at<int32_t>(p.counts), nullptr, N, p.M, off, st, false, c.s);
+            launch_scan_offsets(table, p.CH, N, c.at<int32_t>(p.counts), off, st, c.s);
             launch_scatter(dA, p.M, p.R, p.CH, table, off, nullptr, N, c.at<int32_t>(p.perm), st, false,
                            c.s);
             launch_cellsum(dXin, p.M, p.L, c.at<int32_t>(p.perm), off, nullptr, N, p.S,

@@ -49,6 +49,7 @@ struct DevState {
     uint32_t err;         // ERR_* bits
     uint32_t cmax_bits;   // bits of max_n ||c_n - mu|| (non-negative float)
     uint32_t rho_bits;    // bits of max_n ||c'_n - (its BF16 pieces)|| (tensor-core path)
+    uint32_t done_ctr;    // CTAs done in a fused kernel (its last CTA finishes and resets it)
     double D;             // total distortion of the last pass
     double D_prev;        // distortion of the previous pass of the stage
 };
@@ -253,6 +254,12 @@ void launch_mean(const float *X, int64_t M, int L, double *part, int G, float *m
 void launch_hist(const int32_t *assign, const float *e, int64_t M, int64_t R, int CH,
                  const int32_t *n_dev, int n_host, bool do_hist, int32_t *table, double *dpart,
                  DevState *st, bool train, cudaStream_t s);
+// Step / encode / backward forms (MODE_STEP, N on the host): k_hist + k_ctl and
+// k_scan + k_offsets, each pair in one launch whose last CTA does the second part.
+void launch_hist_ctl(const int32_t *assign, const float *e, int64_t M, int64_t R, int CH, int N,
+                     bool do_hist, int32_t *table, double *dpart, DevState *st, cudaStream_t s);
+void launch_scan_offsets(int32_t *table, int CH, int N, int32_t *counts, int32_t *off, DevState *st,
+                         cudaStream_t s);
 void launch_ctl(const double *dpart, int CH, DevState *st, int mode, double theta, int max_passes,
                 int N_target, PassRecord *records, int max_records, cudaStream_t s);
 void launch_scan(int32_t *table, int CH, const int32_t *n_dev, int n_host, int32_t *counts,
