@@ -253,6 +253,36 @@ __device__ __forceinline__ void mma_bf16_ta_elect(uint32_t d_tmem, uint32_t a_tm
         "r"(a_tmem), "l"(bdesc), "r"(TC_IDESC), "r"(acc)
         : "memory");
 }
+// One whole job of the L = 64 form (K = 2 x 64 + 16: nine MMAs, the x~ K-blocks
+// kk = 0..3 against both pieces of c', then the norm block) and its commit in one
+// instruction sequence (addresses formed by adds inside it, one election): the
+// issuing warp shares its SM sub-partition with ALU-bound epilogue warps and gets
+// few issue slots, so the fewer instructions per MMA the better.
+__device__ __forceinline__ void job9_elect(uint32_t d, uint32_t a0, uint64_t b0, uint32_t bar)
+{
+    asm volatile(
+        "{\n\t.reg .pred e, pf, pt;\n\t.reg .b32 a1, a2, a3, a4;\n\t"
+        ".reg .b64 b1, b2, b3, b4, b5, b6, b7, b8;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.ne.b32 pf, %4, %4;\n\t"
+        "setp.eq.b32 pt, %4, %4;\n\t"
+        "add.u32 a1, %1, 8;\n\tadd.u32 a2, %1, 16;\n\tadd.u32 a3, %1, 24;\n\tadd.u32 a4, %1, 32;\n\t"
+        "add.s64 b1, %2, 16;\n\tadd.s64 b2, %2, 32;\n\tadd.s64 b3, %2, 48;\n\tadd.s64 b4, %2, 64;\n\t"
+        "add.s64 b5, %2, 80;\n\tadd.s64 b6, %2, 96;\n\tadd.s64 b7, %2, 112;\n\tadd.s64 b8, %2, 128;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, pf;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a1], b1, %3, pt;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a2], b2, %3, pt;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a3], b3, %3, pt;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], b4, %3, pt;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a1], b5, %3, pt;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a2], b6, %3, pt;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a3], b7, %3, pt;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a4], b8, %3, pt;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%5];\n\t}" ::"r"(d),
+        "r"(a0), "l"(b0), "r"(TC_IDESC), "r"(0), "r"(bar)
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_commit_elect(uint64_t *bar)
 {
     asm volatile(
@@ -669,7 +699,7 @@ __device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc,
                                         bool usable_tile, float cmax, float rho, float V1, float V2, int i1,
                                         DevState *st,
                                         int32_t *__restrict__ assign, float *__restrict__ e,
-                                        int32_t *__restrict__ flags)
+                                        int32_t *__restrict__ flags, int64_t flag_base)
 {
     const int crow = 128 * acc + rr;
     const int64_t m = m0 + crow;
@@ -789,7 +819,7 @@ __device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc,
                 e[m] = da;
             }
         }
-        if (!certified) flags[atomicAdd(&st->nflag, 1)] = (int32_t)m;
+        if (!certified) flags[atomicAdd(&st->nflag, 1)] = (int32_t)(flag_base + m);
     }
 }
 
@@ -801,7 +831,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int32_t *n_dev, int n_host, const float *__restrict__ mu,
                 const float *__restrict__ C, DevState *st, int32_t *__restrict__ assign,
                 float *__restrict__ e, int32_t *__restrict__ flags, int keymask,
-                int64_t m_lo)
+                int64_t flag_base)
 {
     if (st->finished) return;
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -817,7 +847,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     constexpr uint32_t stage_bytes = (uint32_t)TC_NT * KB * 2u;
     __nv_bfloat16 *XS = reinterpret_cast<__nv_bfloat16 *>(smem);
     uint8_t *Bs = smem + xs_bytes;
-    const int64_t m0 = m_lo + (int64_t)blockIdx.x * TC_ROWS;
+    const int64_t m0 = (int64_t)blockIdx.x * TC_ROWS;
 
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
@@ -977,7 +1007,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         int i1;
         tc_jobs(sh, tmem, warp, lane, acc, half, ntiles, 0, keymask, V1, V2, i1);
         tc_tail<LK>(sh, warp, lane, acc, half, rr, m0, X, M, L, N, C, kn, xn2, !sh.inexact && tc_exact_cb,
-                    cmax, rho, V1, V2, i1, st, assign, e, flags);
+                    cmax, rho, V1, V2, i1, st, assign, e, flags, flag_base);
     }
 
     tc_fence_before();
@@ -1023,7 +1053,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                   const int32_t *n_dev, int n_host, const float *__restrict__ mu,
                   const float *__restrict__ C, DevState *st, int32_t *__restrict__ assign,
                   float *__restrict__ e, int32_t *__restrict__ flags, int keymask,
-                  int64_t m_lo)
+                  int64_t flag_base)
 {
     if (st->finished) return;
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -1032,7 +1062,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int N = cur_n(n_dev, n_host);
     const int ntiles = (N + TC_NT - 1) / TC_NT;
-    const int64_t nrt = (M - m_lo + TC_ROWS - 1) / TC_ROWS;   // row tiles of rows [m_lo, M)
+    const int64_t nrt = (M + TC_ROWS - 1) / TC_ROWS;   // row tiles
     const int K = (int)((nrt - (int64_t)blockIdx.x + gridDim.x - 1) / gridDim.x);   // this CTA's
     constexpr int KB = tc_kb(LK);
     constexpr int XSTR = XsRow<LK>::STR;
@@ -1043,7 +1073,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __nv_bfloat16 *XS = reinterpret_cast<__nv_bfloat16 *>(smem + TC_PSTAGES * stage_bytes);
     float *XF = reinterpret_cast<float *>(smem + TC_PSTAGES * stage_bytes + xs_bytes);
     auto tile_m0 = [&](int k) -> int64_t {
-        return m_lo + ((int64_t)blockIdx.x + (int64_t)k * gridDim.x) * TC_ROWS;
+        return ((int64_t)blockIdx.x + (int64_t)k * gridDim.x) * TC_ROWS;
     };
     auto tile_rows = [&](int k) -> int64_t {
         const int64_t r = M - tile_m0(k);
@@ -1137,6 +1167,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ---------------- MMA issuer (as in k_assign_tc), per row tile after
         // its A operand is in tensor memory
         const uint64_t bdesc0 = smem_desc(smem_addr(Bs), 128u, sbo_b);
+        // L = 64 with two pieces: a job is one instruction sequence (job9_elect)
+        constexpr bool JOB9 = LK == 64 && TC_PIECES == 2;
         bool ok = true;
         for (int k = 0; k < K && ok; ++k) {
             if (!__all_sync(0xffffffffu, mbar_wait_bounded_sleep(&sh.aready, (uint32_t)k & 1u)) || sh.abort) {
@@ -1161,15 +1193,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                     tc_fence_after();
                     const uint32_t d = tmem + (uint32_t)(slot * TC_NT);
-                    const uint32_t at = tmem + (uint32_t)(TC_A_COL + a * ((LK + 16) / 2));
+                    if (JOB9) {
+                        job9_elect(d, tmem + (uint32_t)(TC_A_COL + a * ((LK + 16) / 2)), bst,
+                                   smem_addr(&sh.tfull[slot]));
+                    } else {
+                        const uint32_t at = tmem + (uint32_t)(TC_A_COL + a * ((LK + 16) / 2));
 #pragma unroll
-                    for (int seg = 0; seg < TC_PIECES; ++seg)
+                        for (int seg = 0; seg < TC_PIECES; ++seg)
 #pragma unroll
-                        for (int kk = 0; kk < LK / 16; ++kk)
-                            mma_bf16_ta_elect(d, at + (uint32_t)(8 * kk), bst + (uint64_t)(seg * LK + kk * 16),
-                                              (seg | kk) ? 1u : 0u);
-                    mma_bf16_ta_elect(d, at + (uint32_t)(LK / 2), bst + (uint64_t)(TC_PIECES * LK), 1u);
-                    mma_commit_elect(&sh.tfull[slot]);
+                            for (int kk = 0; kk < LK / 16; ++kk)
+                                mma_bf16_ta_elect(d, at + (uint32_t)(8 * kk),
+                                                  bst + (uint64_t)(seg * LK + kk * 16), (seg | kk) ? 1u : 0u);
+                        mma_bf16_ta_elect(d, at + (uint32_t)(LK / 2), bst + (uint64_t)(TC_PIECES * LK), 1u);
+                        mma_commit_elect(&sh.tfull[slot]);
+                    }
                     if (lane == 0) sh.mma_job = j;
                 }
                 if (!ok) break;
@@ -1265,7 +1302,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             if (k >= 1)
                 tc_tail<LK>(sh, warp, lane, acc, half, rr, tile_m0(k - 1), X, M, L, N, C, kn, pxn2, pusable,
-                            cmax, rho, pV1, pV2, pi1, st, assign, e, flags);
+                            cmax, rho, pV1, pV2, pi1, st, assign, e, flags, flag_base);
             if (k < K) {
                 tc_jobs(sh, tmem, warp, lane, acc, half, ntiles, 2 * k * ntiles, keymask, pV1, pV2, pi1);
                 pxn2 = xn2;
@@ -1332,7 +1369,13 @@ static void launch_tc(const float *X, int64_t M, int L, const void *Bp, const fl
                       const int32_t *n_dev, int n_host, const float *mu, const float *C, DevState *st,
                       int32_t *assign, float *e, int32_t *flags, cudaStream_t s, int64_t m_lo)
 {
-    const int64_t grid = (M - m_lo + TC_ROWS - 1) / TC_ROWS;
+    // rows [m_lo, M): the kernels see them as rows [0, M - m_lo) of offset arrays and add
+    // m_lo back only to the flag list entries (global row numbers)
+    X += m_lo * L;
+    assign += m_lo;
+    e += m_lo;
+    M -= m_lo;
+    const int64_t grid = (M + TC_ROWS - 1) / TC_ROWS;
     if (grid <= 0) return;
     const int keymask = ~((1 << TC_JBITS) - 1);
     const __nv_bfloat16 *B = static_cast<const __nv_bfloat16 *>(Bp);
