@@ -1170,23 +1170,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // L = 64 with two pieces: a job is one instruction sequence (job9_elect)
         constexpr bool JOB9 = LK == 64 && TC_PIECES == 2;
         bool ok = true;
+        // job j: accumulator slot j % 3 and the parity of j / 3; codebook tile G: stage
+        // G % TC_PSTAGES and the parity of G / TC_PSTAGES, all stepped (no divisions);
+        // the last committed job and tile are published once, at the end
+        int j = 0, slot = 0, G = 0, s = 0, last_job = -1, last_tile = -1;
+        uint32_t jpar = 0u, gpar = 0u;
         for (int k = 0; k < K && ok; ++k) {
             if (!__all_sync(0xffffffffu, mbar_wait_bounded_sleep(&sh.aready, (uint32_t)k & 1u)) || sh.abort) {
                 ok = false;
                 break;
             }
             for (int t = 0; t < ntiles && ok; ++t) {
-                const int G = k * ntiles + t, s = G % TC_PSTAGES;
-                if (!__all_sync(0xffffffffu, mbar_wait_bounded_sleep(&sh.full[s], (uint32_t)(G / TC_PSTAGES) & 1u))) {
+                if (!__all_sync(0xffffffffu, mbar_wait_bounded_sleep(&sh.full[s], gpar))) {
                     ok = false;
                     break;
                 }
                 const uint64_t bst = bdesc0 + ((uint64_t)(s * stage_bytes) >> 4);
 #pragma unroll
                 for (int a = 0; a < TC_NACC; ++a) {
-                    const int j = 2 * G + a, slot = j % TC_SLOTS;
-                    if ((j >= TC_SLOTS &&
-                         !__all_sync(0xffffffffu, mbar_wait_bounded_sleep(&sh.tempty[slot], (uint32_t)((j / TC_SLOTS) - 1) & 1u))) ||
+                    if ((j >= TC_SLOTS && !__all_sync(0xffffffffu, mbar_wait_bounded_sleep(&sh.tempty[slot], jpar ^ 1u))) ||
                         sh.abort) {
                         ok = false;
                         break;
@@ -1207,12 +1209,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         mma_bf16_ta_elect(d, at + (uint32_t)(LK / 2), bst + (uint64_t)(TC_PIECES * LK), 1u);
                         mma_commit_elect(&sh.tfull[slot]);
                     }
-                    if (lane == 0) sh.mma_job = j;
+                    last_job = j++;
+                    if (++slot == TC_SLOTS) {
+                        slot = 0;
+                        jpar ^= 1u;
+                    }
                 }
                 if (!ok) break;
                 mma_commit_elect(&sh.empty[s]);
-                if (lane == 0) sh.mma_tile = G;
+                last_tile = G++;
+                if (++s == TC_PSTAGES) {
+                    s = 0;
+                    gpar ^= 1u;
+                }
             }
+        }
+        if (lane == 0) {
+            sh.mma_job = last_job;
+            sh.mma_tile = last_tile;
         }
         if (!ok && lane == 0) sh.abort = 1;
         __syncwarp();
