@@ -147,3 +147,21 @@ def test_graph_cache_eviction_keeps_results(lbg):
             assert r.D == want.D
     for Co in outs:
         assert np.array_equal(host(Co), host(want.C))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_host_input_pieces_match_device_input(lbg, precision):
+    """A host-resident X is copied and searched piece by piece (one search wave per
+    piece); the step and the encode must give the device-input call's results bit
+    for bit, for a size with several pieces and a ragged last one."""
+    X, C = workload(17, 120000, 4, 512)
+    X = np.ascontiguousarray(X[: 120000 - 77])
+    Xd, Cd = torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda()
+    dev_step = lbg.lbg_lloyd_step(Xd, Cd, precision=precision)
+    host_step = lbg.lbg_lloyd_step(torch.from_numpy(X).pin_memory(), torch.from_numpy(C), precision=precision)
+    assert np.array_equal(host(host_step.assign), host(dev_step.assign))
+    assert np.array_equal(host(host_step.C), host(dev_step.C))
+    assert host_step.D == dev_step.D and host_step.n_exact == dev_step.n_exact
+    dev_enc = lbg.vq_encode(Xd, Cd, precision=precision)
+    host_enc = lbg.vq_encode(X, C, precision=precision)            # pageable host memory
+    assert np.array_equal(host(host_enc.idx), host(dev_enc.idx)) and host_enc.D == dev_enc.D
