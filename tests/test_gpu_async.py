@@ -154,8 +154,12 @@ def test_host_input_pieces_match_device_input(lbg, precision):
     """A host-resident X is copied and searched piece by piece (one search wave per
     piece); the step and the encode must give the device-input call's results bit
     for bit, for a size with several pieces and a ragged last one."""
-    X, C = workload(17, 120000, 4, 512)
-    X = np.ascontiguousarray(X[: 120000 - 77])
+    from paper_0910_4711_gb300 import synth
+    X = np.ascontiguousarray(synth.blocks(synth.make_image(17, 1024, 2048), 4)[: 100000 - 77], np.float32)
+    rng = np.random.default_rng(17)
+    C = np.ascontiguousarray(X[rng.choice(X.shape[0], 512, replace=False)] + rng.uniform(-0.5, 0.5, (512, 16)),
+                             np.float32)
+    assert X.shape[0] > 2 * 152 * 256      # three pieces, the last one ragged
     Xd, Cd = torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda()
     dev_step = lbg.lbg_lloyd_step(Xd, Cd, precision=precision)
     host_step = lbg.lbg_lloyd_step(torch.from_numpy(X).pin_memory(), torch.from_numpy(C), precision=precision)
