@@ -27,7 +27,7 @@ def lbg():
 
 
 def host(t):
-    return t.detach().cpu().numpy()
+    return t.detach().cpu().numpy() if hasattr(t, "detach") else np.asarray(t)
 
 
 def workload(seed, M, b, N):
