@@ -674,20 +674,25 @@ __global__ void __launch_bounds__(EX_THREADS)
         if (!exact_group(X, L, Lp, CT, N, st, flags, nflag, assign, e, g, cbuf, sh, uses)) return;
 }
 
-// Exact re-scoring with the codebook split across CTAs.  A work item is
-// (group of XS_R flagged rows, slice of the codebook chunks); the number of
-// slices is chosen on the device from the flagged count so that about
-// XS_ITEMS items exist (few flagged rows would otherwise leave most SMs idle,
-// and every CTA would stream the whole codebook).  Thread t scores
-// codevector t % EX_SW of each chunk against rows 16 (t / EX_SW) .. + 15,
-// d = sum_l (x_l - c_l)^2 in index order as above.  With one slice the group
-// is finished in place; with more, each item writes its per-row (d, index)
-// minima and the last item of the group (atomic count) merges them in slice
-// order, so ties keep the lowest index and the result does not depend on
-// which CTA finishes last.
+// Exact re-scoring spread evenly over the CTAs.  The work is U = groups x
+// nchunk units (a group of XS_R flagged rows against one chunk of EX_SW
+// codevectors), ordered group-major; CTA b takes the contiguous units
+// [b U / G, (b + 1) U / G) of G = min(launched CTAs, U), so every CTA streams about
+// the same number of chunks whatever the flagged count (the count is known
+// only on the device).  Thread t scores codevector t % EX_SW of each chunk
+// against rows 16 (t / EX_SW) .. + 15, d = sum_l (x_l - c_l)^2 in index order
+// (terms beyond L are (0 - 0)^2 and leave the sum unchanged), with the
+// operands of dimension l + 1 loaded while dimension l is scored.  A CTA keeps
+// its rows and running minima while consecutive units share a group.  A group
+// that lies in one CTA is finished in place; a group cut by CTA boundaries has
+// one segment per CTA it touches: each writes its per-row (d, index) minima to
+// its slot (0 for the CTA's first group, 1 for its last), and the last
+// segment to arrive (atomic count on the group's first CTA, reset by itself)
+// merges them in CTA order, i.e. in codevector order, so ties keep the lowest
+// index and the result does not depend on which CTA finishes last.
 constexpr int XS_R = 32;
 constexpr int XS_HALF = XS_R / 2;
-constexpr int XS_ITEMS = 2 * 152;   // two resident CTAs per SM: one wave
+constexpr int XS_CTAS = 2 * 152;   // two resident CTAs per SM: one wave
 
 struct ExactSplitSmem {
     float xs[LMAX][XS_R];
@@ -698,6 +703,24 @@ struct ExactSplitSmem {
     float rowb[XS_R];
     int rowi[XS_R];
 };
+
+// first unit of CTA b; the CTA that takes unit u (the largest b with
+// first unit <= u, which is never an empty CTA)
+__device__ __forceinline__ int64_t xs_first_unit(int64_t b, int64_t U, int G) { return b * U / G; }
+__device__ __forceinline__ int xs_cta_of(int64_t u, int64_t U, int G) { return (int)(((u + 1) * G - 1) / U); }
+
+// d[q] += (x_q - c)^2 for the 16 rows of a thread at one dimension, two rows
+// per packed instruction
+__device__ __forceinline__ void xs_step(float (&d2)[XS_HALF], const float4 (&x)[4], float c)
+{
+    uint64_t cc;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(cc) : "f"(c));
+#pragma unroll
+    for (int q4 = 0; q4 < 4; ++q4) {
+        sqdiff2(x[q4].x, x[q4].y, cc, d2[4 * q4], d2[4 * q4 + 1]);
+        sqdiff2(x[q4].z, x[q4].w, cc, d2[4 * q4 + 2], d2[4 * q4 + 3]);
+    }
+}
 
 __global__ void __launch_bounds__(EX_THREADS)
     k_assign_exact_split(const float *__restrict__ X, int L, int Lp, const float *__restrict__ CT,
@@ -711,12 +734,11 @@ __global__ void __launch_bounds__(EX_THREADS)
     if (groups == 0) return;
     const int N = cur_n(n_dev, n_host);
     const int nchunk = (N + EX_SW - 1) / EX_SW;
-    int nsplit = XS_ITEMS / groups;
-    nsplit = nsplit < 1 ? 1 : (nsplit > nchunk ? nchunk : nsplit);
-    const int cps = (nchunk + nsplit - 1) / nsplit;
-    nsplit = (nchunk + cps - 1) / cps;
-    const int items = groups * nsplit;
-    if ((int)blockIdx.x >= items) return;
+    const int64_t U = (int64_t)groups * nchunk;
+    const int G = (int)min((int64_t)gridDim.x, U), b = (int)blockIdx.x;   // G <= U: no CTA is empty
+    if (b >= G) return;
+    const int64_t u0 = xs_first_unit(b, U, G), u1 = xs_first_unit(b + 1, U, G);
+    const int g_first = (int)(u0 / nchunk);
 
     extern __shared__ __align__(128) float cbuf[];   // [2][Lp][EX_SW]
     __shared__ __align__(16) ExactSplitSmem sh;
@@ -729,151 +751,160 @@ __global__ void __launch_bounds__(EX_THREADS)
         mbar_init(&sh.bar[1], 1);
         fence_mbar_init();
         sh.abort = 0;
+        for (int64_t u = u0; u < u0 + 2 && u < u1; ++u) {   // in flight while the rows are staged
+            const int bb = (int)(u - u0) & 1;
+            mbar_expect_tx(&sh.bar[bb], chunk_bytes);
+            bulk_load(cbuf + bb * chunk_floats, CT + (size_t)(u % nchunk) * chunk_floats, chunk_bytes,
+                      &sh.bar[bb]);
+        }
     }
-    __syncthreads();
     uint32_t uses[2] = {0u, 0u};
-    for (int w = blockIdx.x; w < items; w += gridDim.x) {
-        const int g = w / nsplit, sp = w % nsplit;
-        const int k0 = sp * cps, k1 = min(nchunk, k0 + cps);
-        const int nr = min(XS_R, nflag - g * XS_R);
-        if (tid == 0)   // the first two chunks are in flight while the rows are staged
-            for (int k = k0; k < k0 + 2 && k < k1; ++k) {
-                mbar_expect_tx(&sh.bar[(k - k0) & 1], chunk_bytes);
-                bulk_load(cbuf + ((k - k0) & 1) * chunk_floats, CT + (size_t)k * chunk_floats, chunk_bytes,
-                          &sh.bar[(k - k0) & 1]);
-            }
-        for (int r = warp; r < XS_R; r += EX_THREADS / 32) {   // a warp per row: coalesced
-            const float *xr = r < nr ? X + (int64_t)flags[g * XS_R + r] * L : nullptr;
-            for (int l = lane; l < L; l += 32) sh.xs[l][r] = xr ? xr[l] : 0.f;
-        }
-        __syncthreads();
-        float best[XS_HALF];
-        int bi[XS_HALF];
+    float best[XS_HALF];
+    int bi[XS_HALF];
+    int g = -1, nr = 0;
+    for (int64_t u = u0;; ++u) {
+        const int gu = u < u1 ? (int)(u / nchunk) : -1;
+        if (gu != g) {
+            if (g >= 0) {
+                // ---- the segment of group g in this CTA is done: per-row minima ----
 #pragma unroll
-        for (int q = 0; q < XS_HALF; ++q) {
-            best[q] = INFINITY;
-            bi[q] = 0x7fffffff;
-        }
-        int k_stop = k1;
-        for (int k = k0; k < k1; ++k) {
-            const int b = (k - k0) & 1;
-            const bool ok = mbar_wait_bounded(&sh.bar[b], uses[b] & 1u);
-            uses[b] += 1u;
-            if (!ok) sh.abort = 1;
-            const float *cb = cbuf + b * chunk_floats;
-            const int n = k * EX_SW + j;
-            if (ok && n < N) {
-                float d2[XS_HALF];
+                for (int q = 0; q < XS_HALF; ++q) {
 #pragma unroll
-                for (int q = 0; q < XS_HALF; ++q) d2[q] = 0.f;
-#pragma unroll 2
-                for (int l = 0; l < L; ++l) {
-                    const float c = cb[l * EX_SW + j];
-                    uint64_t cc;
-                    asm("mov.b64 %0, {%1, %1};" : "=l"(cc) : "f"(c));
-#pragma unroll
-                    for (int q4 = 0; q4 < XS_HALF / 4; ++q4) {
-                        const float4 x4 = lds4(&sh.xs[l][h * XS_HALF + 4 * q4]);
-                        sqdiff2(x4.x, x4.y, cc, d2[4 * q4], d2[4 * q4 + 1]);
-                        sqdiff2(x4.z, x4.w, cc, d2[4 * q4 + 2], d2[4 * q4 + 3]);
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const float ob = __shfl_xor_sync(0xffffffffu, best[q], o);
+                        const int oi = __shfl_xor_sync(0xffffffffu, bi[q], o);
+                        if (ob < best[q] || (ob == best[q] && oi < bi[q])) {
+                            best[q] = ob;
+                            bi[q] = oi;
+                        }
+                    }
+                    if (lane == 0) {
+                        sh.rb[warp][q] = best[q];
+                        sh.ri[warp][q] = bi[q];
                     }
                 }
-#pragma unroll
-                for (int q = 0; q < XS_HALF; ++q)
-                    if (d2[q] < best[q]) {
-                        best[q] = d2[q];
-                        bi[q] = n;
+                __syncthreads();
+                const int fb = xs_cta_of((int64_t)g * nchunk, U, G);
+                const int lb = xs_cta_of((int64_t)(g + 1) * nchunk - 1, U, G);
+                const int slot = g == g_first ? 0 : 1;
+                if (tid < XS_R) {
+                    const int hh = tid / XS_HALF, q = tid % XS_HALF, w0 = hh * (EX_SW / 32);
+                    float bb = sh.rb[w0][q];
+                    int ii = sh.ri[w0][q];
+                    for (int ww = w0 + 1; ww < w0 + EX_SW / 32; ++ww)
+                        if (sh.rb[ww][q] < bb || (sh.rb[ww][q] == bb && sh.ri[ww][q] < ii)) {
+                            bb = sh.rb[ww][q];
+                            ii = sh.ri[ww][q];
+                        }
+                    sh.rowb[tid] = bb;
+                    sh.rowi[tid] = ii;
+                    if (fb != lb) {
+                        part_d[((size_t)b * 2 + slot) * XS_R + tid] = bb;
+                        part_i[((size_t)b * 2 + slot) * XS_R + tid] = ii;
                     }
+                }
+                bool fin = fb == lb;
+                if (!fin) {
+                    __threadfence();
+                    __syncthreads();
+                    if (tid == 0) sh.last = atomicAdd(&cnt[fb], 1) == lb - fb;
+                    __syncthreads();
+                    fin = sh.last != 0;
+                    if (fin) {
+                        __threadfence();
+                        if (tid < nr) {   // segments in CTA order = codevector order
+                            float bb = INFINITY;
+                            int ii = 0x7fffffff;
+                            for (int c = fb; c <= lb; ++c) {
+                                const int s = (int)(xs_first_unit(c, U, G) / nchunk) == g ? 0 : 1;
+                                const float ob = __ldcg(part_d + ((size_t)c * 2 + s) * XS_R + tid);
+                                const int oi = __ldcg(part_i + ((size_t)c * 2 + s) * XS_R + tid);
+                                if (ob < bb || (ob == bb && oi < ii)) {
+                                    bb = ob;
+                                    ii = oi;
+                                }
+                            }
+                            sh.rowb[tid] = bb;
+                            sh.rowi[tid] = ii;
+                        }
+                        if (tid == 0) cnt[fb] = 0;
+                    }
+                }
+                if (fin && tid < nr) {
+                    const float bb = sh.rowb[tid];
+                    const int ii = sh.rowi[tid];
+                    const int row = flags[g * XS_R + tid];
+                    const bool valid = ii >= 0 && ii < N;
+                    if (!valid) flag_error(st, ERR_NONFINITE);   // only NaN rows compare false everywhere
+                    assign[row] = valid ? ii : 0;
+                    e[row] = valid ? bb : 0.f;
+                }
+                __syncthreads();   // rb/ri/rowb and xs are reused
+            }
+            if (gu < 0) break;
+            // ---- stage the rows of group gu (a warp per row: coalesced), zero beyond L ----
+            g = gu;
+            nr = min(XS_R, nflag - g * XS_R);
+            for (int r = warp; r < XS_R; r += EX_THREADS / 32) {
+                const float *xr = r < nr ? X + (int64_t)flags[g * XS_R + r] * L : nullptr;
+                for (int l = lane; l < Lp; l += 32) sh.xs[l][r] = xr && l < L ? xr[l] : 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < XS_HALF; ++q) {
+                best[q] = INFINITY;
+                bi[q] = 0x7fffffff;
             }
             __syncthreads();
-            if (sh.abort) {
-                k_stop = k;
-                break;
-            }
-            if (tid == 0 && k + 2 < k1) {
-                mbar_expect_tx(&sh.bar[b], chunk_bytes);
-                bulk_load(cbuf + b * chunk_floats, CT + (size_t)(k + 2) * chunk_floats, chunk_bytes,
-                          &sh.bar[b]);
-            }
         }
-        if (k_stop < k1) {
+        // ---- unit u: chunk u % nchunk against the staged rows ----
+        const int bsel = (int)(u - u0) & 1;
+        const bool ok = mbar_wait_bounded(&sh.bar[bsel], uses[bsel] & 1u);
+        uses[bsel] += 1u;
+        if (!ok) sh.abort = 1;
+        const int n = (int)(u % nchunk) * EX_SW + j;
+        if (ok && n < N) {
+            const float *cq = cbuf + bsel * chunk_floats + j;
+            const float *xq = &sh.xs[0][h * XS_HALF];
+            float d2[XS_HALF];
+#pragma unroll
+            for (int q = 0; q < XS_HALF; ++q) d2[q] = 0.f;
+            float4 xa[4], xb[4];
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4) xa[q4] = lds4(xq + 4 * q4);
+            float ca = cq[0];
+            for (int l = 0; l < Lp; l += 2) {   // Lp is a multiple of 4
+#pragma unroll
+                for (int q4 = 0; q4 < 4; ++q4) xb[q4] = lds4(xq + (l + 1) * XS_R + 4 * q4);
+                const float cb2 = cq[(l + 1) * EX_SW];
+                xs_step(d2, xa, ca);
+                if (l + 2 < Lp) {
+#pragma unroll
+                    for (int q4 = 0; q4 < 4; ++q4) xa[q4] = lds4(xq + (l + 2) * XS_R + 4 * q4);
+                    ca = cq[(l + 2) * EX_SW];
+                }
+                xs_step(d2, xb, cb2);
+            }
+#pragma unroll
+            for (int q = 0; q < XS_HALF; ++q)
+                if (d2[q] < best[q]) {
+                    best[q] = d2[q];
+                    bi[q] = n;
+                }
+        }
+        __syncthreads();
+        if (sh.abort) {
             if (tid == 0) {
-                for (int kk = k_stop + 1; kk < k1 && kk < k_stop + 2; ++kk)
-                    (void)mbar_wait_bounded(&sh.bar[(kk - k0) & 1], uses[(kk - k0) & 1] & 1u);
+                if (u + 1 < u1)
+                    (void)mbar_wait_bounded(&sh.bar[bsel ^ 1], uses[bsel ^ 1] & 1u);
                 flag_error(st, ERR_TIMEOUT);
             }
             return;
         }
-        // per-row minimum: shuffles inside a warp, then the 4 warps of a half in order
-#pragma unroll
-        for (int q = 0; q < XS_HALF; ++q) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ob = __shfl_xor_sync(0xffffffffu, best[q], o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi[q], o);
-                if (ob < best[q] || (ob == best[q] && oi < bi[q])) {
-                    best[q] = ob;
-                    bi[q] = oi;
-                }
-            }
-            if (lane == 0) {
-                sh.rb[warp][q] = best[q];
-                sh.ri[warp][q] = bi[q];
-            }
+        if (tid == 0 && u + 2 < u1) {
+            mbar_expect_tx(&sh.bar[bsel], chunk_bytes);
+            bulk_load(cbuf + bsel * chunk_floats, CT + (size_t)((u + 2) % nchunk) * chunk_floats, chunk_bytes,
+                      &sh.bar[bsel]);
         }
-        __syncthreads();
-        if (tid < XS_R) {
-            const int hh = tid / XS_HALF, q = tid % XS_HALF, w0 = hh * (EX_SW / 32);
-            float bb = sh.rb[w0][q];
-            int ii = sh.ri[w0][q];
-            for (int ww = w0 + 1; ww < w0 + EX_SW / 32; ++ww)
-                if (sh.rb[ww][q] < bb || (sh.rb[ww][q] == bb && sh.ri[ww][q] < ii)) {
-                    bb = sh.rb[ww][q];
-                    ii = sh.ri[ww][q];
-                }
-            sh.rowb[tid] = bb;
-            sh.rowi[tid] = ii;
-            if (nsplit > 1) {
-                part_d[(size_t)w * XS_R + tid] = bb;
-                part_i[(size_t)w * XS_R + tid] = ii;
-            }
-        }
-        bool fin = nsplit == 1;
-        if (nsplit > 1) {
-            __threadfence();
-            __syncthreads();
-            if (tid == 0) sh.last = atomicAdd(&cnt[g], 1) == nsplit - 1;
-            __syncthreads();
-            fin = sh.last != 0;
-            if (fin) {
-                __threadfence();
-                if (tid < nr) {
-                    float bb = __ldcg(part_d + (size_t)(g * nsplit) * XS_R + tid);
-                    int ii = __ldcg(part_i + (size_t)(g * nsplit) * XS_R + tid);
-                    for (int q = 1; q < nsplit; ++q) {
-                        const float ob = __ldcg(part_d + (size_t)(g * nsplit + q) * XS_R + tid);
-                        const int oi = __ldcg(part_i + (size_t)(g * nsplit + q) * XS_R + tid);
-                        if (ob < bb || (ob == bb && oi < ii)) {
-                            bb = ob;
-                            ii = oi;
-                        }
-                    }
-                    sh.rowb[tid] = bb;
-                    sh.rowi[tid] = ii;
-                }
-                if (tid == 0) cnt[g] = 0;
-            }
-        }
-        if (fin && tid < nr) {
-            const float bb = sh.rowb[tid];
-            const int ii = sh.rowi[tid];
-            const int row = flags[g * XS_R + tid];
-            const bool valid = ii >= 0 && ii < N;
-            if (!valid) flag_error(st, ERR_NONFINITE);   // only NaN rows compare false everywhere
-            assign[row] = valid ? ii : 0;
-            e[row] = valid ? bb : 0.f;
-        }
-        __syncthreads();
     }
 }
 
@@ -987,7 +1018,7 @@ void launch_exact(const float *X, int L, int Lp, const float *CT, const int32_t 
                                                              assign, e);
 }
 
-int exact_split_items() { return XS_ITEMS; }
+int exact_split_ctas() { return XS_CTAS; }
 int exact_split_rows() { return XS_R; }
 
 void launch_exact_split(const float *X, int L, int Lp, const float *CT, const int32_t *n_dev, int n_host,
@@ -996,9 +1027,10 @@ void launch_exact_split(const float *X, int L, int Lp, const float *CT, const in
 {
     const size_t smem = (size_t)2 * Lp * EX_SW * sizeof(float);
     cudaFuncSetAttribute(k_assign_exact_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the flagged count is known only on the device: up to one wave, at least 16 CTAs per
+    // possible group of rows when M is small (CTAs beyond the units exit at once)
     int64_t blocks = (M + XS_R - 1) / XS_R;
-    if (blocks < XS_ITEMS) blocks = blocks * 16 < XS_ITEMS ? blocks * 16 : XS_ITEMS;
-    if (blocks > XS_ITEMS) blocks = XS_ITEMS;
+    blocks = blocks * 16 < XS_CTAS ? blocks * 16 : XS_CTAS;
     if (blocks < 1) blocks = 1;
     k_assign_exact_split<<<(unsigned)blocks, EX_THREADS, smem, s>>>(X, L, Lp, CT, n_dev, n_host, st, flags,
                                                                    assign, e, part_d, part_i, cnt);

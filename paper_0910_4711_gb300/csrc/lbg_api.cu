@@ -101,9 +101,9 @@ Plan make_plan(int64_t M, int L, int N, int max_rec, bool host_X, bool need_assi
     p.Cout = host_C ? p.take(sizeof(float) * (size_t)N * L) : 0;
     p.Xhat = host_Xhat ? p.take(sizeof(float) * (size_t)M * L) : 0;
     p.Bp = tc ? p.take(tc_codebook_bytes(p.NP, L)) : 0;
-    p.xpart_d = p.take(sizeof(float) * (size_t)exact_split_items() * exact_split_rows());
-    p.xpart_i = p.take(sizeof(int32_t) * (size_t)exact_split_items() * exact_split_rows());
-    p.xcnt = p.take(sizeof(int32_t) * (size_t)exact_split_items());
+    p.xpart_d = p.take(sizeof(float) * 2 * (size_t)exact_split_ctas() * exact_split_rows());
+    p.xpart_i = p.take(sizeof(int32_t) * 2 * (size_t)exact_split_ctas() * exact_split_rows());
+    p.xcnt = p.take(sizeof(int32_t) * (size_t)exact_split_ctas());
     return p;
 }
 
@@ -331,7 +331,7 @@ bool run_assign_host(const Call &c, const Plan &p, const float *hostX, float *Xs
 void run_exact(const Call &c, const Plan &p, const float *X, const int32_t *n_dev, int n_host,
                DevState *st, int32_t *assign)
 {
-    cudaMemsetAsync(c.at<int32_t>(p.xcnt), 0, sizeof(int32_t) * (size_t)exact_split_items(), c.s);
+    cudaMemsetAsync(c.at<int32_t>(p.xcnt), 0, sizeof(int32_t) * (size_t)exact_split_ctas(), c.s);
     launch_exact_split(X, p.L, p.Lp, c.at<float>(p.CT), n_dev, n_host, st, c.at<int32_t>(p.flags), assign,
                        c.at<float>(p.e), c.at<float>(p.xpart_d), c.at<int32_t>(p.xpart_i),
                        c.at<int32_t>(p.xcnt), p.M, c.s);

@@ -227,10 +227,10 @@ void launch_assign(const float *X, int64_t M, int L, int Lp, const float *Cp, co
 void launch_exact(const float *X, int L, int Lp, const float *CT, const int32_t *n_dev, int n_host,
                   DevState *st, const int32_t *flags, int32_t *assign, float *e, int64_t M,
                   cudaStream_t s);
-// Exact re-scoring with the codebook split across CTAs (XS_ITEMS work items at
-// most, so exact_split_items() x exact_split_rows() partial minima and
-// exact_split_items() group counters of scratch, the counters zero on entry).
-int exact_split_items();
+// Exact re-scoring with the flagged rows' work spread over at most
+// exact_split_ctas() CTAs: scratch of 2 x exact_split_ctas() x exact_split_rows()
+// partial minima and exact_split_ctas() group counters, the counters zero on entry.
+int exact_split_ctas();
 int exact_split_rows();
 void launch_exact_split(const float *X, int L, int Lp, const float *CT, const int32_t *n_dev, int n_host,
                         DevState *st, const int32_t *flags, int32_t *assign, float *e, float *part_d,

@@ -78,6 +78,26 @@ def test_bf16_non_integer_data_falls_back_exactly(lbg):
     assert r.n_exact == X.shape[0]
 
 
+@pytest.mark.parametrize("M,N,L", [(64, 4096, 16), (20000, 1024, 16), (3001, 512, 64), (33, 129, 5)])
+def test_exact_fallback_spread_over_ctas(lbg, M, N, L):
+    """Every row re-scored exactly, at sizes where a group of 32 flagged rows is cut across
+    many CTAs (its per-CTA minima merged), across two, or held whole by one, with a ragged
+    last group and chunk.  A codebook that repeats its first half must give the first half's
+    result bit for bit: equal FP32 distances in different CTAs keep the lowest index."""
+    rng = np.random.default_rng(M + N + L)
+    X = (rng.standard_normal((M, L)) * 3.3).astype(np.float32)
+    C = (rng.standard_normal((N, L)) * 3.3).astype(np.float32)
+    r = lbg.vq_encode(dev(X), dev(C), precision="bf16")
+    assert r.n_exact == M
+    a_ref, e_ref, gap = oracle.assign(X, C.astype(np.float64))
+    check_assign(X, C, host(r.idx), a_ref, e_ref, gap)
+    check_D(r.D, float(e_ref.sum()))
+    H = C[: N // 2]
+    half = lbg.vq_encode(dev(X), dev(H), precision="bf16")
+    dup = lbg.vq_encode(dev(X), dev(np.concatenate([H, H])), precision="bf16")
+    assert np.array_equal(host(dup.idx), host(half.idx)) and dup.D == half.D
+
+
 def test_bf16_rejects_large_dimension(lbg):
     X = np.zeros((10, 128), np.float32)
     with pytest.raises(lbg.LBGError) as ei:
