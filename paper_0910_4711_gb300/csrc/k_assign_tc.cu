@@ -29,7 +29,16 @@
 // E = ||x~|| rho, and with k'_n = (2 tau + 2^-23) ||c~_n||^2, R' = 2 tau ||x~||^2
 // the certificate of k_assign.cu applies: V2 - V1 > 2R' + 2k'_i1 + 2E +
 // 4 eta (g1 + eta), plus 2^-17 (|V1| + |V2|) + 2^-23 (|V1| + 2|V2|) for the
-// epilogue below.
+// epilogue below.  A second certificate needs no bound on the winner's
+// approximation.  With X2 + f_n = ||x~ - c~_n||^2 + (X2 - ||x~||^2) and
+// k'_n >= 2 tau ||c~_n||^2 + u ||c~_n||^2, the bound gives
+//     ||x~ - c~_n||^2 >= v_n - R' - E - |X2 - ||x~||^2|,
+// and every codevector outside the best pair has v_n >= V2 (V2 is the second
+// smallest value), so ||x - c_n||^2 >= (sqrt(V2 - R' - E - P - (L+2) u ||x~||^2)
+// - eta)^2, P the epilogue term above.  The chosen member's FP32 direct-form
+// distance d gives ||x - c_ii||^2 <= d (1 + (L+4) u); when the lower bound
+// exceeds that, ii is the exact argmin.  A row is certified when either
+// certificate holds.
 //
 // Epilogue.  Each thread owns one row and one half (72 columns) of every
 // tile, taken as 36 column pairs (a, b).  lo = min(a, b) gets the pair index
@@ -90,6 +99,7 @@ constexpr int TC_JBITS = 6;                    // bits of the in-half pair index
 constexpr float TC_PACK = 7.62939453125e-6f;   // 2^(TC_JBITS - 23): packing changes a value
                                                // by less than this fraction of it
 constexpr float TC_HIERR = 1.1920928955078125e-7f;   // 2^-23: bound of the FMA-pipe pair maximum
+constexpr float TC_EVAL = 9.5367431640625e-7f;   // 2^-20: FP32 evaluation of the second certificate
 constexpr int TC_STAGES = 3;
 constexpr int TC_EPI_WARPS = 8 * TC_NACC;      // 16: (accumulator, lane quarter, half)
 constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);
@@ -808,11 +818,21 @@ __device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc,
                 // the MMA sums x~ . (p_hi + p_mid) and misses x~ . r_n, r_n = c'_n - p_hi - p_mid:
                 // |x~ . r_n| <= ||x~|| rho for every n (Cauchy-Schwarz)
                 const float E = sqrtf(xn2u) * rho * SLOP;
+                // |fl(||x~||^2) - ||x~||^2|: X2 as the MMA saw it
+                const float xerr = (float)(L + 2) * U32 * xn2u;
                 // V1 ~ ||x~ - c~_ii||^2 - k' (X2 included): bound g1^2 from above
-                const float g1sq = V1 + 2.f * ka + R + pack + E + (float)(L + 2) * U32 * xn2u;
+                const float g1sq = V1 + 2.f * ka + R + pack + E + xerr;
                 const float g1 = sqrtf(fmaxf(g1sq, 0.f)) * SLOP;
                 const float margin = (2.f * R + 2.f * ka + pack + 2.f * E + 4.f * eta * (g1 + eta)) * SLOP;
                 certified = (V2 - V1) > margin;
+                if (!certified) {
+                    // second certificate: every codevector outside the pair has
+                    // ||x - c_n||^2 >= (sqrt(V2 - R - E - pack - xerr) - eta)^2, which must
+                    // exceed the winner's direct-form distance rounded up
+                    const float lb = V2 - (R + E + pack + xerr) * SLOP;
+                    const float ub = da * (1.f + (float)(L + 4) * U32) * SLOP;
+                    certified = lb > 0.f && (lb - 2.f * eta * sqrtf(lb) * SLOP) * (1.f - TC_EVAL) > ub * (1.f + TC_EVAL);
+                }
             }
             if (certified) {
                 assign[m] = ii;
