@@ -805,24 +805,32 @@ __global__ void __launch_bounds__(EX_THREADS)
                 }
                 bool fin = fb == lb;
                 if (!fin) {
-                    __threadfence();
+                    if (tid < XS_R) __threadfence();   // the partial minima written above
                     __syncthreads();
                     if (tid == 0) sh.last = atomicAdd(&cnt[fb], 1) == lb - fb;
                     __syncthreads();
                     fin = sh.last != 0;
                     if (fin) {
-                        __threadfence();
-                        if (tid < nr) {   // segments in CTA order = codevector order
+                        if (tid < nr) {   // segments in CTA order = codevector order, 8 loads in flight
+                            __threadfence();
                             float bb = INFINITY;
                             int ii = 0x7fffffff;
-                            for (int c = fb; c <= lb; ++c) {
-                                const int s = (int)(xs_first_unit(c, U, G) / nchunk) == g ? 0 : 1;
-                                const float ob = __ldcg(part_d + ((size_t)c * 2 + s) * XS_R + tid);
-                                const int oi = __ldcg(part_i + ((size_t)c * 2 + s) * XS_R + tid);
-                                if (ob < bb || (ob == bb && oi < ii)) {
-                                    bb = ob;
-                                    ii = oi;
+                            for (int c0 = fb; c0 <= lb; c0 += 8) {
+                                float ob[8];
+                                int oi[8];
+#pragma unroll
+                                for (int k = 0; k < 8; ++k) {
+                                    const int c = c0 + k;
+                                    const int s = c <= lb && (int)(xs_first_unit(c, U, G) / nchunk) != g ? 1 : 0;
+                                    ob[k] = c <= lb ? __ldcg(part_d + ((size_t)c * 2 + s) * XS_R + tid) : INFINITY;
+                                    oi[k] = c <= lb ? __ldcg(part_i + ((size_t)c * 2 + s) * XS_R + tid) : 0x7fffffff;
                                 }
+#pragma unroll
+                                for (int k = 0; k < 8; ++k)
+                                    if (ob[k] < bb || (ob[k] == bb && oi[k] < ii)) {
+                                        bb = ob[k];
+                                        ii = oi[k];
+                                    }
                             }
                             sh.rowb[tid] = bb;
                             sh.rowi[tid] = ii;
@@ -842,12 +850,28 @@ __global__ void __launch_bounds__(EX_THREADS)
                 __syncthreads();   // rb/ri/rowb and xs are reused
             }
             if (gu < 0) break;
-            // ---- stage the rows of group gu (a warp per row: coalesced), zero beyond L ----
+            // ---- stage the rows of group gu, zero beyond L: lane r reads the r-th flag, then
+            // each warp loads its rows (coalesced) with every load in flight before the stores ----
             g = gu;
             nr = min(XS_R, nflag - g * XS_R);
-            for (int r = warp; r < XS_R; r += EX_THREADS / 32) {
-                const float *xr = r < nr ? X + (int64_t)flags[g * XS_R + r] * L : nullptr;
-                for (int l = lane; l < Lp; l += 32) sh.xs[l][r] = xr && l < L ? xr[l] : 0.f;
+            {
+                constexpr int RPW = XS_R / (EX_THREADS / 32), VPL = LMAX / 32;
+                const int frow = lane < nr ? flags[g * XS_R + lane] : -1;
+                float v[RPW][VPL];
+#pragma unroll
+                for (int k = 0; k < RPW; ++k) {
+                    const int row = __shfl_sync(0xffffffffu, frow, warp + k * (EX_THREADS / 32));
+#pragma unroll
+                    for (int i = 0; i < VPL; ++i) {
+                        const int l = lane + 32 * i;
+                        v[k][i] = row >= 0 && l < L ? X[(int64_t)row * L + l] : 0.f;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < RPW; ++k)
+#pragma unroll
+                    for (int i = 0; i < VPL; ++i)
+                        if (lane + 32 * i < Lp) sh.xs[lane + 32 * i][warp + k * (EX_THREADS / 32)] = v[k][i];
             }
 #pragma unroll
             for (int q = 0; q < XS_HALF; ++q) {
