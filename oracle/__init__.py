@@ -39,22 +39,33 @@ _lib = None
 OK, WARN_MAXPASS = 0, 1
 
 
-def build(force: bool = False) -> str:
-    """Compile ``lbg_oracle.c`` into ``_lib/liblbgoracle.so`` with gcc.
+#: Environment variable naming another compiled copy of the oracle to load
+#: instead of ``_lib/liblbgoracle.so`` (the mutation test of the pins loads
+#: copies of ``lbg_oracle.c`` with planted mistakes through it).
+LIBRARY_ENV = "LBG_ORACLE_LIBRARY"
+
+
+def compile_source(src: str, out: str) -> str:
+    """Compile one C source of the oracle into the shared library ``out``.
 
     ``-ffp-contract=off`` keeps a*b+c unfused so x86 and aarch64 give the
     same bits; OpenMP parallelises only the independent rows of the cell
     allocation.
     """
+    tmp = out + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
+           src, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile ``lbg_oracle.c`` into ``_lib/liblbgoracle.so`` (if out of date)."""
     os.makedirs(_LIBDIR, exist_ok=True)
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
-    tmp = _LIB + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
-           _SRC, "-o", tmp, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    return compile_source(_SRC, _LIB)
 
 
 def _load():
@@ -62,7 +73,7 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        lib = ctypes.CDLL(build())
+        lib = ctypes.CDLL(os.environ.get(LIBRARY_ENV) or build())
         P = ctypes.c_void_p
         i64, i32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
         lib.oracle_max_threads.restype = ctypes.c_int

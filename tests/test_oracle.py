@@ -157,6 +157,10 @@ def test_identical_vectors_zero_distortion():
     assert np.all(t.a == 2)
     assert t.passes_per_stage() == [1, 2, 1]
     np.testing.assert_array_equal(t.trace_D, [0.0, 10 * 2 * d * d, 0.0, 0.0])
+    # a near-tie is a gap <= the tolerance: right after the first split every
+    # row is equally far from both children (gap exactly 0), and nowhere else
+    t0 = oracle.lbg_train(X, 4, delta=d, theta=1e-3, near_tol=0.0)
+    assert t0.trace_near.tolist() == [0, 10, 0, 0]
 
 
 def test_separated_blobs_end_at_blob_means():
@@ -234,6 +238,31 @@ def test_multiplicative_split_values_and_closed_form():
     assert t.passes_per_stage() == [2, 3, 3, 3]
 
 
+def test_variants_in_training_zero_mean_hand_example():
+    """X = {-3, -1, 1, 3} (mean 0), N = 2, delta = 0.5, worked by hand.
+    Paper split (additive): children 0.5, -0.5 -> cells {1, 3}, {-3, -1}:
+    D 20, 20 | 13, 4, 4, ending at C = [2, -2].
+    Multiplicative split (V1): 0 (1 +- delta) = 0 twice, every row ties and
+    goes to child 0, child 1 stays empty and keeps 0: D 20, 20 | 20, 20.
+    V1 with re-seeding (V2): after the first update child 1 takes 0 + delta
+    and child 0 becomes 0 - delta, each with 2 rows: D 20, 20 | 20, 13, 4, 4,
+    ending at C = [-2, 2]."""
+    X = np.array([-3, -1, 1, 3], np.float32)[:, None]
+    add = oracle.lbg_train(X, 2, 0.5, 1e-3)
+    np.testing.assert_array_equal(add.trace_D, [20, 20, 13, 4, 4])
+    np.testing.assert_array_equal(add.C[:, 0], [2, -2])
+    assert add.a.tolist() == [1, 1, 0, 0] and add.D == 4
+    mult = oracle.lbg_train(X, 2, 0.5, 1e-3, split_multiplicative=True)
+    np.testing.assert_array_equal(mult.trace_D, [20, 20, 20, 20])
+    np.testing.assert_array_equal(mult.C[:, 0], [0, 0])
+    assert mult.a.tolist() == [0, 0, 0, 0] and mult.D == 20
+    both = oracle.lbg_train(X, 2, 0.5, 1e-3, split_multiplicative=True, reseed_empty=True)
+    np.testing.assert_array_equal(both.trace_D, [20, 20, 20, 13, 4, 4])
+    np.testing.assert_array_equal(both.C[:, 0], [-2, 2])
+    assert both.a.tolist() == [0, 0, 1, 1] and both.D == 4
+    assert both.passes_per_stage() == [2, 4]
+
+
 def test_reseed_empty_cells_hand_example():
     """Variant V2 by hand: counts [2, 4, 0, 0] -> cell 2 takes from cell 1
     (largest): c2 = c1 + d, c1 = c1 - d, counts [2, 2, 2, 0]; cell 3 then takes
@@ -242,6 +271,12 @@ def test_reseed_empty_cells_hand_example():
     C2, cnt = oracle.reseed(C, [2, 4, 0, 0], 0.5)
     np.testing.assert_array_equal(C2, [[-0.5, 0.5], [9.5, 9.5], [10.5, 10.5], [0.5, 1.5]])
     np.testing.assert_array_equal(cnt, [1, 2, 2, 1])
+    # odd count: the empty cell takes floor(5 / 2) = 2, the donor keeps 3 and so
+    # is still the largest when cell 2 is re-seeded: c2 = c0' + d, c0 = c0' - d
+    C = np.array([[1.0, 2.0], [9.0, 9.0], [4.0, 4.0]])
+    C2, cnt = oracle.reseed(C, [5, 0, 0], 0.5)
+    np.testing.assert_array_equal(C2, [[0.0, 1.0], [1.5, 2.5], [1.0, 2.0]])
+    np.testing.assert_array_equal(cnt, [2, 2, 1])
 
 
 def test_arguments_rejected():
