@@ -70,3 +70,25 @@ def test_reseed_train_matches_oracle(lbg):
         assert r.passes_per_stage() == t.passes_per_stage()
         check_codebook(C, t.C)
         check_D(r.D, t.D)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_zero_mean_variants_hand_example(lbg, precision):
+    """X = {-3, -1, 1, 3}, N = 2, delta = 0.5, worked by hand (the oracle's pin
+    of the same case): the additive split ends at [2, -2]; the multiplicative
+    split of the zero mean gives two equal codevectors, every row ties and goes
+    to the lowest index, and the empty cell keeps 0; re-seeding then splits the
+    full cell and ends at [-2, 2]."""
+    X = np.array([-3, -1, 1, 3], np.float32)[:, None]
+    cases = [  # (multiplicative, reseed, D per pass, final C, final cell table, D)
+        (False, False, [20, 20, 13, 4, 4], [2, -2], [1, 1, 0, 0], 4.0),
+        (True, False, [20, 20, 20, 20], [0, 0], [0, 0, 0, 0], 20.0),
+        (True, True, [20, 20, 20, 13, 4, 4], [-2, 2], [0, 0, 1, 1], 4.0),
+    ]
+    for mult, reseed, trace_D, C, a, D in cases:
+        r = lbg.lbg_train(dev(X), 2, 0.5, 1e-3, split_multiplicative=mult, reseed_empty=reseed,
+                          precision=precision)
+        assert [rec["D"] for rec in r.records] == trace_D, (mult, reseed)
+        np.testing.assert_array_equal(r.C.cpu().numpy()[:, 0], C)
+        assert r.assign.cpu().numpy().tolist() == a
+        assert r.D == D
