@@ -1,0 +1,373 @@
+"""The two certificates of the BF16 tensor-core nearest-codevector search,
+checked on the CPU under the library's accumulation model.
+
+The tensor-core search (Alg. 1 "Cell Allocation" with the cross term on
+tcgen05 MMAs) works with an integer centring vector mu, integer rows
+x~ = x - mu (8-bit image samples), and codevectors c~ = fl32(c - mu) whose
+scaled value c' = -2 c~ is split into two BF16 pieces p_hi + p_mid with the
+exact remainder r = c' - p_hi - p_mid.  One MMA row accumulates
+
+    G_n = X2 + s0_n + x~ . (p_hi + p_mid),   X2 = ||x~||^2,
+    s0_n = fl32(||c~||^2 - k'_n),  k'_n = fl32_up((2 tau + 2^-23) ||c~||^2),
+
+and the library assumes the FP32 accumulation error stays within
+tau * (sum_l |x~_l c'_l| + |s0_n| + X2), tau = (K/16 + 2) 2^-22 (1 + 2^-7),
+K = 2 ceil16(L) + 16.  These tests take that model at its worst: the
+accumulator value of the exact winner is pushed to the top of its interval
+and every other value to the bottom.  The epilogue is then emulated in FP32
+as the kernel runs it (pairs of columns, the pair index packed into the low
+mantissa bits of the pair minimum, the pair maximum as (a + b) - min, running
+top-2 per chain, merges), the two members of the best pair get FP32 direct
+distances at the worst end of their rounding bound, and both certificates are
+evaluated in exact arithmetic.  A row either of them accepts must have the
+exact (rational) argmin of the original FP32 values.  This checks the
+algebra of the certificates under the model; the measured accumulation
+error behind the model, and the kernel itself, are checked on the GPU.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+U = Fraction(1, 2 ** 24)
+NT, HALF, JBITS = 144, 72, 6        # codevectors per tile, per half, bits of the pair index
+PACK = Fraction(1, 2 ** 17)         # packing moves a pair minimum by less than this fraction
+HIERR = Fraction(1, 2 ** 23)        # pair maximum (a + b) - min within this of (|V1| + 2|V2|)
+
+
+def round_bits(x: Fraction, p: int, up: bool = False) -> Fraction:
+    """x rounded to p significant bits (nearest even, or toward +inf)."""
+    if x == 0:
+        return Fraction(0)
+    a = abs(x)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    while Fraction(2) ** e > a:
+        e -= 1
+    while Fraction(2) ** (e + 1) <= a:
+        e += 1
+    unit = Fraction(2) ** (e - p + 1)
+    q, r = divmod(a, unit)
+    q = int(q)
+    if up:
+        if r and x > 0:
+            q += 1
+        if r and x < 0:
+            pass
+    else:
+        half = unit / 2
+        if r > half or (r == half and q & 1):
+            q += 1
+    return (q * unit) if x > 0 else -(q * unit)
+
+
+def f32(x: Fraction, up: bool = False) -> Fraction:
+    return round_bits(Fraction(x), 24, up)
+
+
+def bf16(x: Fraction) -> Fraction:
+    return round_bits(Fraction(x), 8)
+
+
+def sqrt_up(x: Fraction) -> Fraction:
+    return Fraction(math.sqrt(float(x)) * (1 + 2 ** -50)) if x > 0 else Fraction(0)
+
+
+def test_rounding_helpers():
+    assert f32(Fraction(2 ** 24 + 1)) == 2 ** 24
+    assert f32(Fraction(2 ** 24 + 3)) == 2 ** 24 + 4
+    assert f32(Fraction(2 ** 24 + 1), up=True) == 2 ** 24 + 2
+    assert bf16(Fraction(257)) == 256 and bf16(Fraction(259)) == 260
+    rng = np.random.default_rng(0)
+    vals = rng.standard_normal(500) * 10.0 ** rng.integers(-6, 6, 500)
+    for v in vals:
+        assert f32(Fraction(float(v))) == Fraction(float(np.float32(v)))
+    v32 = vals.astype(np.float32)
+    for a, b in zip(v32, bf16_rne(v32)):
+        assert Fraction(float(b)) == bf16(Fraction(float(a)))
+    ties = np.array([257.0, 259.0, -257.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8], np.float32)
+    np.testing.assert_array_equal(bf16_rne(ties), [256.0, 260.0, -256.0, 1.0, 1.0 + 2.0 ** -6])
+
+
+def _f32bits_key(lo: np.float32, j: int) -> np.float32:
+    b = np.array([lo], np.float32).view(np.uint32)
+    b = (b & np.uint32(~((1 << JBITS) - 1) & 0xFFFFFFFF)) | np.uint32(j)
+    return b.view(np.float32)[0]
+
+
+def _epilogue(v):
+    """Top-2 of the kernel's epilogue over one row's FP32 accumulator values v
+    (length a multiple of NT): (V1, V2, i1), i1 the first column of the best pair."""
+    nt = len(v) // NT
+    halves = []
+    for h in range(2):
+        c1, c2, cg = [np.float32(np.inf)] * 2, [np.float32(np.inf)] * 2, [0, 0]
+        for t in range(nt):
+            s1 = list(c1)
+            for j in range(HALF // 2):
+                q = j % 2
+                a, b = v[t * NT + h * HALF + 2 * j], v[t * NT + h * HALF + 2 * j + 1]
+                lo = np.minimum(a, b)
+                hi = np.float32(np.float32(a + b) - lo)
+                k = _f32bits_key(lo, j)
+                c2[q] = min(c2[q], max(c1[q], k), hi)
+                c1[q] = min(c1[q], k)
+            for q in range(2):
+                if c1[q] < s1[q]:
+                    cg[q] = t
+        jm = (1 << JBITS) - 1
+        V1, V2 = c1[0], c2[0]
+        i1 = cg[0] * NT + h * HALF + 2 * (int(np.array([c1[0]]).view(np.uint32)[0]) & jm)
+        iq = cg[1] * NT + h * HALF + 2 * (int(np.array([c1[1]]).view(np.uint32)[0]) & jm)
+        V2 = min(min(V2, c2[1]), max(V1, c1[1]))
+        if c1[1] < V1 or (c1[1] == V1 and iq < i1):
+            V1, i1 = c1[1], iq
+        halves.append((V1, V2, i1))
+    (A1, A2, ai), (B1, B2, bi) = halves
+    V2 = min(min(A2, B2), max(A1, B1))
+    if B1 < A1 or (B1 == A1 and bi < ai):
+        return B1, V2, bi
+    return A1, V2, ai
+
+
+def bf16_rne(a):
+    """float32 array rounded to BF16 (nearest even), returned as float32."""
+    b = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
+
+
+def _ints(arrays):
+    """Exact integer images of float arrays under one common scale:
+    (list of object arrays of Python ints, S) with a == ints * 2**-S."""
+    S = 0
+    for a in arrays:
+        f = np.asarray(a, np.float64)
+        nz = f[f != 0]
+        if nz.size:
+            S = max(S, int(53 - np.frexp(nz)[1].min()))
+    out = []
+    for a in arrays:
+        f = np.asarray(a, np.float64) * 2.0 ** S
+        out.append(np.array([int(v) for v in f.ravel()], dtype=object).reshape(f.shape))
+    return out, S
+
+
+def _epilogue_worst(v, best):
+    """The epilogue's top-2 in exact arithmetic with its two rounding effects at
+    their worst: a pair minimum moved by its packing (at most 63 units in the
+    last place of an FP32 value, < 2^-17 of it) and a pair maximum by the FP32
+    rounding of (a + b) - min (2^-24 (|min| + 2 |max|)); up for the exact
+    winner's pair, down for every other pair.  Returns (V1, V2, i1)."""
+    c1 = c2 = None
+    i1 = -1
+    for p in range(len(v) // 2):
+        a, b = v[2 * p], v[2 * p + 1]
+        lo, mx = min(a, b), max(a, b)
+        s = 1 if best in (2 * p, 2 * p + 1) else -1
+        k = lo + s * Fraction(63, 2 ** 23) * abs(lo)
+        hi = mx + s * Fraction(1, 2 ** 24) * (abs(lo) + 2 * abs(mx))
+        if c1 is None:
+            c1, c2, i1 = k, hi, 2 * p
+            continue
+        c2 = min(c2, max(c1, k), hi)
+        if k < c1:
+            c1, i1 = k, 2 * p
+    return c1, c2, i1
+
+
+def certify(x, C, mu, N, adversarial=True, worst=False):
+    """Run one row through the model and the two certificates.  With
+    worst=True every bounded quantity is at the end of its bound that favours
+    a wrong answer (see test_bf16_certificates_sound_at_every_bound).
+    Returns (accepted, chosen index, exact argmin)."""
+    L = len(x)
+    Lk = -(-L // 16) * 16
+    K = 2 * Lk + 16
+    tau = Fraction(K // 16 + 2, 2 ** 22) * Fraction(129, 128)
+    x = np.asarray(x, np.float32)
+    C = np.asarray(C, np.float32)
+    mu = np.asarray(mu, np.float32)
+    xt = (x - mu).astype(np.float64)
+    assert np.all(xt == np.rint(xt))
+    xt = np.array([int(v) for v in xt], dtype=object)
+    X2 = int((xt * xt).sum())
+    assert X2 < 2 ** 24          # exact in FP32 for these data
+    # exact squared distances of the original FP32 values
+    (xi, ci), Sd = _ints([x, C])
+    diff = ci - xi[None, :]
+    exact = [Fraction(int(v), 1 << (2 * Sd)) for v in (diff * diff).sum(1)]
+    best = min(range(N), key=lambda n: (exact[n], n))
+    # operands: c~ = fl32(c - mu), c' = -2 c~ = p_hi + p_mid + r (each step exact in FP32)
+    ct = (C - mu[None, :]).astype(np.float32)
+    cp = (np.float32(-2.0) * ct).astype(np.float32)
+    ph = bf16_rne(cp)
+    r1 = (cp - ph).astype(np.float32)
+    pm = bf16_rne(r1)
+    r = (r1 - pm).astype(np.float32)
+    (cti, cpi, phi, pmi, ri, r1i), S = _ints([ct, cp, ph, pm, r, r1])
+    assert np.all(cpi == phi + r1i) and np.all(r1i == pmi + ri)
+    sq_exact = [Fraction(int(v), 1 << (2 * S)) for v in (cti * cti).sum(1)]
+    # k'_n rounded up and s0_n rounded to nearest from the FP64 norm, as the preparation does
+    s0 = np.empty(N, np.float32)
+    kp = []
+    for n in range(N):
+        sq = float(sq_exact[n])
+        k64 = (2.0 * float(tau) + 2.0 ** -23) * sq
+        kf = np.float32(k64)
+        if float(kf) < k64:
+            kf = np.nextafter(kf, np.float32(np.inf))
+        kp.append(Fraction(float(kf)))
+        s0[n] = np.float32(sq - float(kf))
+    (s0i,), S0 = _ints([s0])
+    scale = 1 << S
+    dot = (phi + pmi) @ xt                         # x~ . (p_hi + p_mid), scaled by 2**S
+    adot = np.abs(cpi) @ np.abs(xt)                # sum_l |x~_l c'_l|, scaled by 2**S
+    rnorm = [sqrt_up(Fraction(int(v), scale * scale)) for v in (ri * ri).sum(1)]
+    rho = max(rnorm)
+    cmax = max(sqrt_up(q) for q in sq_exact)
+    E = sqrt_up(Fraction(X2)) * rho
+    dotc = cpi @ xt                                # x~ . c', scaled by 2**S
+    v = []
+    for n in range(N):
+        s0n = Fraction(int(s0i[n]), 1 << S0)
+        up = (n == best) == adversarial
+        if worst:   # the missed term -x~.r_n anywhere in [-E, E]
+            G = X2 + s0n + Fraction(int(dotc[n]), scale) + (E if up else -E)
+        else:
+            G = X2 + s0n + Fraction(int(dot[n]), scale)
+        Sn = Fraction(int(adot[n]), scale) + abs(s0n) + X2
+        e = tau * Sn if up else -tau * Sn
+        if worst:
+            v.append(G + e)
+            continue
+        target = G + e
+        # an FP32 value inside the model's interval: round toward G
+        val = f32(target, up=True) if e < 0 else -f32(-target, up=True)
+        v.append(np.float32(float(val)))
+    if worst:
+        V1, V2, i1 = _epilogue_worst(v, best)
+    else:
+        npad = -(-N // NT) * NT
+        v += [np.float32(2.0 ** 100)] * (npad - N)
+        V1, V2, i1 = _epilogue(v)
+        V1, V2 = Fraction(float(V1)), Fraction(float(V2))
+
+    # FP32 direct-form distances of the pair, at the worst end of their bound
+    def direct(n):
+        d = exact[n]
+        return d * (1 + (L + 2) * U) if (n == best) == adversarial else d * (1 - (L + 2) * U)
+
+    da = direct(i1)
+    ii, ka = i1, kp[i1]
+    if i1 + 1 < N:
+        db = direct(i1 + 1)
+        tol = (L + 4) * U * (da + db)
+        if db < da - tol:
+            ii, da, ka = i1 + 1, db, kp[i1 + 1]
+        elif not (da < db - tol):
+            return False, ii, best
+    R = 2 * tau * X2
+    eta = U * (sqrt_up(Fraction(X2)) + cmax)
+    pack = PACK * (abs(V1) + abs(V2)) + HIERR * (abs(V1) + 2 * abs(V2))
+    xerr = (L + 2) * U * X2
+    g1 = sqrt_up(V1 + 2 * ka + R + pack + E + xerr)
+    margin = 2 * R + 2 * ka + pack + 2 * E + 4 * eta * (g1 + eta)
+    if V2 - V1 > margin:
+        return True, ii, best
+    lb = V2 - (R + E + pack + xerr)
+    ub = da * (1 + (L + 4) * U)
+    if lb > 0 and lb - 2 * eta * sqrt_up(lb) > ub:
+        return True, ii, best
+    return False, ii, best
+
+
+def _rows(rng, L, N, spread, trials, family="near"):
+    """Integer rows, and codebooks holding a near-tie pair for each row: c0
+    near the row ("near"; mu = the rounded codebook mean) or near 2 mu - x
+    ("mirror"; mu = the row moved by up to 40 per component, so that
+    c~0 = -x~ and the bound sum |x~ c'| <= ||x~||^2 + ||c~||^2 behind the
+    accumulation error is tight), c1 its reflection across a hyperplane through
+    the row moved by eps (0 in a quarter of the cases), placed in the same
+    column pair, in different pairs of one half, or in different halves."""
+    for trial in range(trials):
+        x = rng.integers(0, 256, L).astype(np.float32)
+        if family == "mirror":
+            mu = (x + rng.integers(-40, 41, L)).astype(np.float32)
+            c0 = (2 * mu - x + spread * rng.standard_normal(L)).astype(np.float32)
+        else:
+            c0 = (x + spread * rng.standard_normal(L)).astype(np.float32)
+        w = rng.standard_normal(L)
+        w /= np.linalg.norm(w)
+        d = c0.astype(np.float64) - x
+        c1 = x + d - 2 * np.dot(d, w) * w
+        eps = 0.0 if trial % 4 == 0 else spread * 10 ** rng.uniform(-7, 0)
+        dv = rng.standard_normal(L)
+        c1 = (c1 + eps * dv / np.linalg.norm(dv)).astype(np.float32)
+        if family == "mirror":
+            r0 = float(np.linalg.norm(d))
+            C = (x + 2 * r0 / np.sqrt(L) * rng.choice([-1, 1], (N, L))
+                 + rng.standard_normal((N, L))).astype(np.float32)
+        else:
+            C = (x + spread * (2.5 + rng.standard_normal((N, L)))).astype(np.float32)
+        where = trial % 3
+        p0 = 2 * int(rng.integers(0, N // 2))
+        p1 = {0: p0 + 1, 1: (p0 + 6) % N, 2: (p0 + HALF + 3) % N}[where]
+        C[p0], C[p1] = (c0, c1) if trial % 2 else (c1, c0)
+        if family != "mirror":
+            mu = np.rint(C.mean(0)).astype(np.float32)
+        yield x, C, mu
+
+
+@pytest.mark.parametrize("L,spread,family", [(16, 20.0, "near"), (16, 2.0, "near"),
+                                              (64, 20.0, "near"), (64, 2.0, "near"),
+                                              (16, 0.5, "mirror"), (64, 0.5, "mirror")])
+def test_bf16_certificates_sound_at_the_model_bound(L, spread, family):
+    rng = np.random.default_rng(L + int(spread))
+    N = NT
+    trials = 60 if L == 64 else 120
+    accepted = 0
+    for x, C, mu in _rows(rng, L, N, spread, trials, family):
+        ok, ii, best = certify(x, C, mu, N)
+        if ok:
+            accepted += 1
+            assert ii == best, (ii, best)
+    assert accepted > 0
+
+
+@pytest.mark.parametrize("L,spread,family", [(16, 20.0, "near"), (16, 2.0, "near"),
+                                              (64, 20.0, "near"), (64, 2.0, "near"),
+                                              (16, 0.5, "mirror"), (64, 0.5, "mirror")])
+def test_bf16_certificates_sound_at_every_bound(L, spread, family):
+    """The proof uses each error only through its bound, so it must hold with
+    every error at the end of its bound that favours a wrong answer: the
+    accumulation error (model), the missed term x~.r_n anywhere in
+    [-||x~|| rho, ||x~|| rho], the packed pair minimum, the FMA-pipe pair
+    maximum and the direct-form distances of the pair.  With all of them at
+    their worst, no wrong row is accepted; and a certificate missing any one of
+    its terms, or with one of them halved, does accept a wrong row in one of
+    these cases."""
+    rng = np.random.default_rng(100 + L + int(spread))
+    N = NT
+    trials = 60 if L == 64 else 120
+    accepted = 0
+    for x, C, mu in _rows(rng, L, N, spread, trials, family):
+        ok, ii, best = certify(x, C, mu, N, worst=True)
+        if ok:
+            accepted += 1
+            assert ii == best, (ii, best)
+    assert accepted > 0
+
+
+def test_bf16_certificates_accept_clear_winners():
+    """With the accumulation error at the model's worst, a row next to one
+    codevector of a spread codebook is still accepted."""
+    rng = np.random.default_rng(5)
+    L, N = 16, NT
+    base = rng.integers(0, 256, L).astype(np.float32)
+    C = (base + 40 * rng.standard_normal((N, L))).astype(np.float32)
+    mu = np.rint(C.mean(0)).astype(np.float32)
+    for n in rng.choice(N, 20, replace=False):
+        x = np.clip(np.rint(C[n] + rng.standard_normal(L)), 0, 255).astype(np.float32)
+        ok, ii, best = certify(x, C, mu, N)
+        assert ok and ii == best == n
