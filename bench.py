@@ -18,9 +18,16 @@ Other legs in the same run:
 * ``e2e``: the same step through the C ABI with HOST buffers (pinned), the
   host->device copy of X and C and the device->host read of C, the cell
   table and D inside the timed region;
-* ``roofline``: the nearest-codevector kernel, FP32 FFMA work 2*L*M*N per
-  launch over its CUDA-event time, against the FP32 CUDA-core peak
-  152 SMs x 128 FP32 lanes x 2 flop x max SM clock;
+* ``roofline``: the nearest-codevector kernel of the timed precision,
+  algorithmic work 2*L*M*N flop per launch over its CUDA-event time, against
+  the measured BF16 tensor peak (burst) for the BF16 form (default) or the
+  FP32 CUDA-core peak 152 SMs x 128 FP32 lanes x 2 flop x max SM clock for
+  the FP32 form; ``traffic`` = the ncu DRAM bytes per launch recorded under
+  profiles/ while the kernel sources keep the digest recorded there;
+* ``update_roofline``: cell table and update, algorithmic bytes over their
+  time, against the measured HBM copy peak;
+* ``other_precision`` (the other form's step and full LBG), ``differentiation``,
+  ``batched``, ``small_full_lbg`` and, with ``--large``, ``large``;
 * ``cpu_baseline``: the FP64 oracle's Lloyd pass on a bounded row sample on
   the host cores.
 ``--impl reference`` times only the oracle (the baseline arm).
