@@ -55,7 +55,8 @@
 // Tiles whose x~ are not BF16-exact, or codebooks whose pieces do not add up
 // exactly, send their rows to the exact FP32 fallback.
 //
-// Kernel layout (one CTA per SM, 256 rows per CTA):
+// Kernel layout (256 rows per CTA; k_assign_tc takes one row tile per CTA,
+// k_assign_tc_p walks the row tiles with one CTA per SM):
 //   prologue      the epilogue warps stage the x tile (coalesced) as centred
 //                 BF16 rows in shared memory, then each thread writes its half
 //                 of its row's A operand (x~ and the norm block) into tensor
@@ -64,13 +65,13 @@
 //                 the codebook stream;
 //   warp 0        producer: TMA bulk copies of prepared codebook tiles (144
 //                 codevectors x KB BF16, already in the MMA's shared-memory
-//                 layout) into a 3-stage ring;
+//                 layout) into a ring of 3 stages (2 in k_assign_tc_p);
 //   warp 1        allocates 512 TMEM columns, one thread issues the MMAs: job
 //                 j = 2 t + a (tile t, accumulator a of 128 rows) accumulates
 //                 into slot j % 3 of a ring of three 144-column accumulators;
 //   warps 2..17   epilogue, one (row, column half) per thread: tcgen05.ld of
 //                 its 72 values per job, running top-2 with the pair index
-//                 (four interleaved chains); after the last tile the two halves
+//                 (two interleaved chains); after the last tile the two halves
 //                 of each row merge, compute the exact distances of the best
 //                 pair's two codevectors, and the half-0 thread runs the
 //                 certificate, writes the index and e(m) or flags the row.
