@@ -19,7 +19,8 @@
 //     the one winning 8-codevector group bit-identically;
 //   * a rigorous rounding-error bound certifies the minimum; rows it cannot
 //     certify (about 0.2% on image blocks) are re-scored exactly in FP32
-//     direct form by k_assign_exact.
+//     direct form by k_assign_exact_split (k_assign_exact in the batched and
+//     no-allocation paths).
 //
 // Certification.  Let x~ = fl(x - mu), c~_n = fl(c_n - mu), u = 2^-24 and
 //   k_n = 2 (L+2) u ||c~_n||^2,  R = (L+2) u ||x~||^2.
