@@ -127,3 +127,20 @@ def test_async_calls_reject_host_outs(lib):
     n = ctypes.c_int32(0)
     o.n_exact = ctypes.pointer(n)
     assert lib.lbg_lloyd_step(fake, 8, 4, 2, fake, fake, None, None, ctypes.byref(o)) == -1
+
+
+def test_binding_rejects_bad_arrays(lib):
+    """The binding only marshals: a wrong dtype, a non-contiguous array or an
+    unknown precision is refused before the library is called."""
+    import torch
+    X = np.zeros((8, 4), np.float32)
+    with pytest.raises(TypeError):
+        lbgvq.lbg_train(X.astype(np.float64), 4)
+    with pytest.raises(TypeError):
+        lbgvq.vq_encode(np.asfortranarray(np.zeros((8, 4), np.float32)), X[:2])
+    with pytest.raises(TypeError):
+        lbgvq.vq_encode(torch.zeros((8, 4), dtype=torch.float64), torch.zeros((2, 4)))
+    with pytest.raises(ValueError):
+        lbgvq.vq_encode(torch.zeros((4, 8)).t(), torch.zeros((2, 4)))
+    with pytest.raises(ValueError):
+        lbgvq.lbg_lloyd_step(X, X[:2], precision="fp16")
