@@ -277,6 +277,11 @@ def test_reseed_empty_cells_hand_example():
     C2, cnt = oracle.reseed(C, [5, 0, 0], 0.5)
     np.testing.assert_array_equal(C2, [[0.0, 1.0], [1.5, 2.5], [1.0, 2.0]])
     np.testing.assert_array_equal(cnt, [2, 2, 1])
+    # a largest cell of one row has nothing to give: the empty cells stay as they are
+    C = np.array([[1.0, 2.0], [9.0, 9.0], [4.0, 4.0]])
+    C2, cnt = oracle.reseed(C, [1, 0, 1], 0.5)
+    np.testing.assert_array_equal(C2, C)
+    np.testing.assert_array_equal(cnt, [1, 0, 1])
 
 
 def test_arguments_rejected():

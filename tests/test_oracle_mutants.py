@@ -82,6 +82,12 @@ MUTANTS = {
                                 "for (int64_t m = 1; m < M; ++m) {\n        const float *x = X")],
     "update_counts_doubled": [("        cnt[n] += 1;\n        for (int32_t l = 0; l < L; ++l) sum[",
                                "        cnt[n] += 2;\n        for (int32_t l = 0; l < L; ++l) sum[")],
+    "mean_not_zeroed": [("for (int32_t l = 0; l < L; ++l) c_out[l] = 0.0;",
+                         "for (int32_t l = 0; l < L; ++l) c_out[l] += 0.0;")],
+    "update_keeps_singleton_cells": [("C_out[i] = cnt[n] > 0 ?", "C_out[i] = cnt[n] > 1 ?")],
+    "second_best_not_shifted": [("                d2 = d1;\n", "")],
+    "d_prev_not_updated": [("            D_prev = D;\n", "")],
+    "reseed_splits_singletons": [("if (counts[b] < 2) break;", "if (counts[b] < 1) break;")],
     # gradient at a fixed cell table
     "grad_c_wrong_sign": [("gC[i] = 2.0 * ((double)cnt[n] * C[i] + gC[i]);",
                            "gC[i] = 2.0 * ((double)cnt[n] * C[i] - gC[i]);")],
