@@ -88,6 +88,11 @@ MUTANTS = {
     "second_best_not_shifted": [("                d2 = d1;\n", "")],
     "d_prev_not_updated": [("            D_prev = D;\n", "")],
     "reseed_splits_singletons": [("if (counts[b] < 2) break;", "if (counts[b] < 1) break;")],
+    "distance_accumulates_in_fp32": [("{\n    double s = 0.0;\n    for (int32_t l = 0; l < L; ++l) {\n        double d =",
+                                      "{\n    float s = 0.0f;\n    for (int32_t l = 0; l < L; ++l) {\n        double d =")],
+    "update_reads_column_major": [("sum[(int64_t)n * L + l] += (double)X[m * L + l];",
+                                   "sum[(int64_t)n * L + l] += (double)X[m + (int64_t)l * M];")],
+    "pass_counter_starts_at_1": [("for (int32_t pass = 0;; ++pass)", "for (int32_t pass = 1;; ++pass)")],
     # gradient at a fixed cell table
     "grad_c_wrong_sign": [("gC[i] = 2.0 * ((double)cnt[n] * C[i] + gC[i]);",
                            "gC[i] = 2.0 * ((double)cnt[n] * C[i] - gC[i]);")],
