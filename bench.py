@@ -160,6 +160,19 @@ def job_throughput(world, units_per_rank, seconds):
     return world * units_per_rank / seconds
 
 
+def estimated_full_lbg_s(passes_per_stage, M, evals_per_s):
+    """Estimated time of a whole LBG design on the CPU oracle: stage s (codebook
+    size 2**s) ran passes_per_stage[s] passes, each costing M * 2**s distance
+    evaluations at the oracle's measured rate.  An estimate (the oracle's full
+    design at this size would take hours): the update's share, which does not
+    grow with the codebook size, is not counted."""
+    n, total = 1, 0.0
+    for p in passes_per_stage:
+        total += p * M * n / evals_per_s
+        n *= 2
+    return total
+
+
 # ------------------------------------------------------------------ clocks
 def gpu_uuid(dev):
     """nvidia-smi id of the CUDA device `dev` (its UUID; the box may list other GPUs)."""
@@ -567,6 +580,13 @@ def run_ours(args):
 
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(X_np, tr.C.cpu().numpy(), args.cpu_seconds)
+        try:
+            cb = line["cpu_baseline"]
+            cb["full_lbg_estimated_s"] = estimated_full_lbg_s(tr.passes_per_stage(), M, cb["value"])
+            cb["full_lbg_estimate"] = ("estimated, not run: the GPU design's passes per stage x "
+                                       "M x stage size evaluations at the oracle's measured rate")
+        except Exception as exc:   # an estimate must never cost the measured line
+            line["cpu_baseline"]["full_lbg_estimate"] = f"not computed: {exc!r}"
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

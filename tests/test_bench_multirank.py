@@ -70,3 +70,11 @@ def test_single_process_needs_no_group():
     finally:
         if saved is not None:
             os.environ["RANK"] = saved
+
+
+def test_estimated_full_lbg_time():
+    """Stage s of a design (codebook size 2**s) costs passes x M x 2**s evaluations."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.estimated_full_lbg_s([2, 3, 3], 100, 1000.0) == pytest.approx(2.0)
+    assert bench.estimated_full_lbg_s([], 100, 1000.0) == 0.0
