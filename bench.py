@@ -484,6 +484,8 @@ def run_ours(args):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
+    # without the measured file: the fallback peaks of an earlier GB300 measurement
+    of = "of measured" if peaks else "of fallback (MEASURED_PEAKS.json absent)"
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
     bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
@@ -504,7 +506,7 @@ def run_ours(args):
                                    f"per launch; kernel source digest {t_digest})"
                                    if traffic is not None else
                                    f"null: no capture of the current kernel sources (digest {t_digest})"),
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
+                "peak_source": f"MEASURED_PEAKS.json bf16_tflops (burst), {of}",
                 "work": "2*L*M*N flop per launch (algorithmic; the two-piece BF16 split of the codevectors, "
                         "the norm column and whole 144-codevector tiles make the tensor cores execute "
                         "2*M*ceil144(N)*(2*ceil16(L)+16))",
@@ -538,7 +540,7 @@ def run_ours(args):
                                 "frac": upd_gbs / hbm, "bytes": upd_bytes,
                                 "work": "M*L*4 + M*4 + N*L*4 + N*4 bytes (read X, cell table; "
                                         "write codebook, counts)",
-                                "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"},
+                                "peak_source": f"MEASURED_PEAKS.json hbm_gbs, {of}"},
             "clocks": clocks,
             "gpu_launches": 10 * args.steps}
     if other_line is not None:
