@@ -636,6 +636,7 @@ def small_leg(lbg, synth, torch, with_oracle=True):
     X_np, N = synth.workload("img512_b4_n256")
     X = torch.from_numpy(X_np).cuda()
     out = {"workload": workload_desc("img512_b4_n256", X_np, N)}
+    runs = {}
     for prec in ("fp32", "bf16"):
         lbg.lbg_train(X, N, 0.01, 1e-3, precision=prec)   # warm
         ts = []
@@ -646,6 +647,7 @@ def small_leg(lbg, synth, torch, with_oracle=True):
             torch.cuda.synchronize()
             ts.append(time.perf_counter() - t0)
         out[prec] = {"full_lbg_ms": 1e3 * statistics.median(ts), "passes": r.n_passes, "D": r.D}
+        runs[prec] = r
     if with_oracle:
         import oracle
         oracle.build()
@@ -654,6 +656,18 @@ def small_leg(lbg, synth, torch, with_oracle=True):
         out["oracle_full_lbg"] = {"seconds": time.perf_counter() - t0, "passes": int(len(o.trace_D)),
                                   "D": float(o.D), "cores": oracle.max_threads(),
                                   "kind": "FP64 oracle LBG on the host (same data, delta, theta)"}
+        # whole-run comparison (meaningful when the oracle's run met no near-tie row)
+        try:
+            den = np.maximum(np.abs(o.C).max(1), 1.0)
+            for prec, r in runs.items():
+                Cg = r.C.cpu().numpy().astype(np.float64)
+                out[prec]["vs_oracle"] = {
+                    "near_tie_rows_in_oracle_run": o.near_ties(),
+                    "same_passes_per_stage": r.passes_per_stage() == o.passes_per_stage(),
+                    "D_rel_diff": abs(r.D - o.D) / o.D,
+                    "codebook_max_rel_diff": float((np.abs(Cg - o.C).max(1) / den).max())}
+        except Exception as exc:   # a report must never cost the measured line
+            out["vs_oracle_error"] = repr(exc)
     return out
 
 

@@ -78,3 +78,64 @@ def test_estimated_full_lbg_time():
     import bench
     assert bench.estimated_full_lbg_s([2, 3, 3], 100, 1000.0) == pytest.approx(2.0)
     assert bench.estimated_full_lbg_s([], 100, 1000.0) == 0.0
+
+
+def test_small_leg_reports_whole_run_comparison():
+    """The small leg's comparison with the oracle's whole run, driven here by a
+    stand-in for the library (the oracle itself, codebook returned in FP32) so
+    that the report code runs without a GPU."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from paper_0910_4711_gb300 import synth
+
+    class T:                       # the few tensor methods small_leg uses
+        def __init__(self, a):
+            self.a = a
+
+        def cuda(self):
+            return self
+
+        def cpu(self):
+            return self
+
+        def numpy(self):
+            return self.a
+
+    class FakeTorch:
+        from_numpy = T
+
+        class cuda:
+            @staticmethod
+            def synchronize():
+                pass
+
+    class FakeLib:
+        @staticmethod
+        def lbg_train(X, N, delta, theta, precision="fp32"):
+            t = oracle.lbg_train(X.a, N, delta, theta)
+
+            class R:
+                C = T(t.C.astype(np.float32))
+                D = t.D
+                n_passes = len(t.trace_D)
+
+                @staticmethod
+                def passes_per_stage():
+                    return t.passes_per_stage()
+            return R
+
+    class FakeSynth:
+        @staticmethod
+        def workload(name):
+            return synth.blocks(synth.make_image(1, 64, 64), 4), 16
+
+    out = bench.small_leg(FakeLib, FakeSynth, FakeTorch, with_oracle=True)
+    assert "vs_oracle_error" not in out, out.get("vs_oracle_error")
+    for prec in ("fp32", "bf16"):
+        v = out[prec]["vs_oracle"]
+        assert v["same_passes_per_stage"] is True
+        assert v["D_rel_diff"] == 0.0
+        assert v["codebook_max_rel_diff"] < 1e-6
+        assert isinstance(v["near_tie_rows_in_oracle_run"], int)
