@@ -176,11 +176,15 @@ def _epilogue_worst(v, best):
     return c1, c2, i1
 
 
-def certify(x, C, mu, N, adversarial=True, worst=False):
+def certify(x, C, mu, N, adversarial=True, worst=False, weights=None):
     """Run one row through the model and the two certificates.  With
     worst=True every bounded quantity is at the end of its bound that favours
     a wrong answer (see test_bf16_certificates_sound_at_every_bound).
-    Returns (accepted, chosen index, exact argmin)."""
+    `weights` (keys m_R, m_k, m_pack, m_E, lb_R, lb_E, lb_pack) scale terms of
+    the first certificate's margin and of the second one's lower bound, to show
+    that each is needed.  Returns (accepted, chosen index, exact argmin)."""
+    wt = {k: Fraction(1) for k in ("m_R", "m_k", "m_pack", "m_E", "lb_R", "lb_E", "lb_pack")}
+    wt.update({k: Fraction(v) for k, v in (weights or {}).items()})
     L = len(x)
     Lk = -(-L // 16) * 16
     K = 2 * Lk + 16
@@ -272,10 +276,11 @@ def certify(x, C, mu, N, adversarial=True, worst=False):
     pack = PACK * (abs(V1) + abs(V2)) + HIERR * (abs(V1) + 2 * abs(V2))
     xerr = (L + 2) * U * X2
     g1 = sqrt_up(V1 + 2 * ka + R + pack + E + xerr)
-    margin = 2 * R + 2 * ka + pack + 2 * E + 4 * eta * (g1 + eta)
+    margin = (wt["m_R"] * 2 * R + wt["m_k"] * 2 * ka + wt["m_pack"] * pack + wt["m_E"] * 2 * E
+              + 4 * eta * (g1 + eta))
     if V2 - V1 > margin:
         return True, ii, best
-    lb = V2 - (R + E + pack + xerr)
+    lb = V2 - (wt["lb_R"] * R + wt["lb_E"] * E + wt["lb_pack"] * pack + xerr)
     ub = da * (1 + (L + 4) * U)
     if lb > 0 and lb - 2 * eta * sqrt_up(lb) > ub:
         return True, ii, best
@@ -344,9 +349,8 @@ def test_bf16_certificates_sound_at_every_bound(L, spread, family):
     accumulation error (model), the missed term x~.r_n anywhere in
     [-||x~|| rho, ||x~|| rho], the packed pair minimum, the FMA-pipe pair
     maximum and the direct-form distances of the pair.  With all of them at
-    their worst, no wrong row is accepted; and a certificate missing any one of
-    its terms, or with one of them halved, does accept a wrong row in one of
-    these cases."""
+    their worst, no wrong row is accepted (and the next test shows that the
+    terms are needed)."""
     rng = np.random.default_rng(100 + L + int(spread))
     N = NT
     trials = 60 if L == 64 else 120
@@ -357,6 +361,27 @@ def test_bf16_certificates_sound_at_every_bound(L, spread, family):
             accepted += 1
             assert ii == best, (ii, best)
     assert accepted > 0
+
+
+@pytest.mark.parametrize("weights", [{"m_R": 0}, {"m_R": 0.5}, {"m_k": 0}, {"m_k": 0.5},
+                                     {"m_pack": 0}, {"m_pack": 0.5}, {"m_E": 0}, {"m_E": 0.5},
+                                     {"lb_R": 0}, {"lb_E": 0}, {"lb_E": 0.5}, {"lb_pack": 0}])
+def test_bf16_certificate_terms_are_needed(weights):
+    """With every error at its worst (as above), dropping or halving one term of
+    the first certificate's margin, or dropping one of the second's lower bound,
+    lets a wrong row through in one of the row families.  (Not shown this way:
+    the eta terms, never binding here since x~ is exact for integer mu; halving
+    R' in the second certificate, whose packing term leaves that much slack.)"""
+    params = [(16, 20.0, "near"), (16, 2.0, "near"), (64, 20.0, "near"), (64, 2.0, "near"),
+              (16, 0.5, "mirror"), (64, 0.5, "mirror")]
+    for L, spread, family in params:
+        rng = np.random.default_rng(100 + L + int(spread))
+        trials = 60 if L == 64 else 120
+        for x, C, mu in _rows(rng, L, NT, spread, trials, family):
+            ok, ii, best = certify(x, C, mu, NT, worst=True, weights=weights)
+            if ok and ii != best:
+                return
+    pytest.fail(f"weights {weights}: no wrong row accepted")
 
 
 def test_bf16_certificates_accept_clear_winners():

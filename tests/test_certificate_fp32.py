@@ -216,11 +216,13 @@ def test_certified_rows_are_exact_on_near_ties(family):
     assert accepted > 0 and refused > 0
 
 
-def _worst_case_margin_check(x, C, mu, L):
+def _worst_case_margin_check(x, C, mu, L, weights=(1, 1, 1)):
     """Worst case allowed by the bound: every v_n anywhere in
     [f_n - 2k_n - R, f_n + R].  The adversary pushes the exact winner b up and
-    every other codevector down; the certificate must then refuse, or name b.
-    Returns True when the certificate accepted."""
+    every other codevector down.  Returns "refused", "right" (accepted, names
+    the exact argmin) or "wrong" (accepted another codevector).  `weights`
+    scale the margin's three terms (2R, 2k, the eta term) to show that each is
+    needed."""
     (xt,), ct = centred([x], C, mu)
     xq = [Fraction(v) for v in xt]
     xn2 = sum(v * v for v in xq)
@@ -241,27 +243,24 @@ def _worst_case_margin_check(x, C, mu, L):
     eta = U * Fraction(math.sqrt(float(xn2)) * (1 + 2 ** -50) + cmax * (1 + 2 ** -50))
     g1 = Fraction(math.sqrt(float(sum((a - Fraction(t)) ** 2 for a, t in zip(xq, ct[i1]))))
                   * (1 + 2 ** -50))
-    margin = 2 * R + 2 * v[i1][1] + 4 * eta * (g1 + eta)
+    wR, wk, we = (Fraction(w) for w in weights)
+    margin = wR * 2 * R + wk * 2 * v[i1][1] + we * 4 * eta * (g1 + eta)
     if V2 - V1 > margin:
-        assert i1 == b and exact[b] < min(e for n, e in enumerate(exact) if n != b)
-        return True
-    return False
+        ok = i1 == b and exact[b] < min(e for n, e in enumerate(exact) if n != b)
+        return "right" if ok else "wrong"
+    return "refused"
 
 
-@pytest.mark.parametrize("family", ["pair_near_row", "pair_far_row_at_mu", "mu_far_from_row"])
-def test_certificate_sound_at_the_bound(family):
-    """Near-tie pairs as above, with every computed value at the worst end of
-    the proven interval: no wrong row may be accepted, and rows with a clear
-    enough gap still are.  Unlike random rounding, this adversary uses the
-    whole error budget: a margin without any one of its terms (2R, 2k, the
-    eta term), or with 2R or 2k halved, accepts a wrong row in one of the
-    families.  (The eta term is the difference between the centred and the
-    original order; on the exact reflections of eps = 0 the two disagree.)"""
+FAMILIES = ["pair_near_row", "pair_far_row_at_mu", "mu_far_from_row"]
+
+
+def _near_tie_rows(family, trials=300):
+    """Near-tie pairs: c0 around the row, c1 its reflection across a hyperplane
+    through the row moved by eps, three farther codevectors; mu by family."""
     rng = np.random.default_rng(3)
     L = 8
     spread = {"pair_near_row": 20.0, "pair_far_row_at_mu": 1000.0, "mu_far_from_row": 20.0}[family]
-    accepted = 0
-    for trial in range(300):
+    for trial in range(trials):
         x = (128 + 40 * rng.standard_normal(L)).astype(np.float32)
         c0 = (x + spread * rng.standard_normal(L)).astype(np.float32)
         w = rng.standard_normal(L)
@@ -279,8 +278,31 @@ def test_certificate_sound_at_the_bound(family):
             mu = (x + 1e-3 * rng.standard_normal(L)).astype(np.float32)
         else:
             mu = (x - 2000 + 100 * rng.standard_normal(L)).astype(np.float32)
-        accepted += _worst_case_margin_check(x, C, mu, L)
-    assert accepted > 0
+        yield x, C, mu, L
+
+
+@pytest.mark.parametrize("family", FAMILIES)
+def test_certificate_sound_at_the_bound(family):
+    """Near-tie pairs as above, with every computed value at the worst end of
+    the proven interval: no wrong row may be accepted, and rows with a clear
+    enough gap still are."""
+    outcomes = [_worst_case_margin_check(x, C, mu, L) for x, C, mu, L in _near_tie_rows(family)]
+    assert "wrong" not in outcomes
+    assert "right" in outcomes
+
+
+@pytest.mark.parametrize("weights", [(0, 1, 1), (1, 0, 1), (1, 1, 0), (0.5, 1, 1), (1, 0.5, 1)])
+def test_each_margin_term_is_needed(weights):
+    """Unlike random rounding, the adversary above uses the whole error budget:
+    a margin without one of its terms (2R, 2k, the eta term), or with 2R or 2k
+    halved, accepts a wrong row in one of the families.  (The eta term covers
+    the difference between the centred and the original order; on the exact
+    reflections of eps = 0 the two disagree.)"""
+    for family in FAMILIES:
+        for x, C, mu, L in _near_tie_rows(family):
+            if _worst_case_margin_check(x, C, mu, L, weights) == "wrong":
+                return
+    pytest.fail(f"margin weights {weights}: no wrong row accepted")
 
 
 def test_certificate_accepts_clear_winners():
