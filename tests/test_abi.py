@@ -144,3 +144,19 @@ def test_binding_rejects_bad_arrays(lib):
         lbgvq.vq_encode(torch.zeros((4, 8)).t(), torch.zeros((2, 4)))
     with pytest.raises(ValueError):
         lbgvq.lbg_lloyd_step(X, X[:2], precision="fp16")
+
+
+@pytest.mark.parametrize("compiler,std,ext", [("gcc", "-std=c99", "c"), ("g++", "-std=c++11", "cpp")])
+def test_header_compiles_cleanly(tmp_path, compiler, std, ext):
+    """include/lbgvq.h is usable from plain C and from C++ without warnings
+    (extern "C" linkage, no C++-only or compiler-specific constructs)."""
+    import subprocess
+    src = tmp_path / f"use.{ext}"
+    src.write_text('#include "lbgvq.h"\n'
+                   "int main(void) {\n"
+                   "  lbg_opts o;\n"
+                   "  lbg_opts_init(&o);\n"
+                   "  return (int)o.precision + (int)sizeof(lbg_step_result) - 16;\n"
+                   "}\n")
+    subprocess.run([compiler, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                    "-I", os.path.join(ROOT, "include"), str(src)], check=True)
