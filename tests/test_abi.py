@@ -160,3 +160,29 @@ def test_header_compiles_cleanly(tmp_path, compiler, std, ext):
                    "}\n")
     subprocess.run([compiler, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
                     "-I", os.path.join(ROOT, "include"), str(src)], check=True)
+
+
+def test_plain_c_program_links_and_calls(lib, tmp_path):
+    """A C program links liblbgvq directly (no Python) and calls the ABI: the
+    version, a status string, and calls that the library rejects before any
+    device work (N not a power of 2, a null codebook)."""
+    import subprocess
+    libdir = os.path.dirname(lbgvq.LIB_PATH)
+    src = tmp_path / "client.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <string.h>\n#include "lbgvq.h"\n'
+        "int main(void) {\n"
+        "  float X[8 * 4] = {0}, C[3 * 4];\n"
+        "  int32_t idx[8];\n"
+        "  if (lbg_version() != 1) return 1;\n"
+        '  if (strcmp(lbg_status_string(LBG_ERR_NOT_POW2), "codebook size is not a power of 2")) return 2;\n'
+        "  if (lbg_train(X, 8, 4, 3, 0.01, 1e-3, C, 0, NULL, NULL, NULL) != LBG_ERR_NOT_POW2) return 3;\n"
+        "  if (vq_encode(X, 8, 4, NULL, 2, idx, NULL, NULL, NULL) != LBG_ERR_ARG) return 4;\n"
+        '  printf("ok\\n");\n'
+        "  return 0;\n"
+        "}\n")
+    exe = tmp_path / "client"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                    "-L", libdir, "-llbgvq", f"-Wl,-rpath,{libdir}"], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", (out.returncode, out.stderr)
