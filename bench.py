@@ -382,7 +382,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": workload_desc(args.workload, X, N), "rows_per_step": rows},
+            "config": {"workload": workload_desc(args.workload, X, N), "M": int(X.shape[0]),
+                       "L": int(X.shape[1]), "N": int(N), "rows_per_step": rows},
             "cpu_baseline": {"kind": "oracle", "cores": oracle.max_threads(), "sample": sample,
                              "value": value, "unit": UNIT},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
