@@ -139,3 +139,15 @@ def test_small_leg_reports_whole_run_comparison():
         assert v["D_rel_diff"] == 0.0
         assert v["codebook_max_rel_diff"] < 1e-6
         assert isinstance(v["near_tie_rows_in_oracle_run"], int)
+
+
+def test_throttle_rule():
+    """Hardware and thermal slowdowns call for a re-measurement; the power cap does not."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.throttled({"reasons": ["hw_thermal_slowdown"]})
+    assert bench.throttled({"reasons": ["sw_power_cap", "sw_thermal_slowdown"]})
+    assert not bench.throttled({"reasons": ["sw_power_cap"]})
+    assert not bench.throttled({"reasons": []})
+    assert not bench.throttled({"sm_mhz": None, "reasons": ["no samples"]})
+    assert not bench.throttled(None)
