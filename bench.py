@@ -20,16 +20,24 @@ Other legs in the same run:
   table and D inside the timed region;
 * ``roofline``: the nearest-codevector kernel of the timed precision,
   algorithmic work 2*L*M*N flop per launch over its CUDA-event time, against
-  the measured BF16 tensor peak (burst) for the BF16 form (default) or the
-  FP32 CUDA-core peak 152 SMs x 128 FP32 lanes x 2 flop x max SM clock for
-  the FP32 form; ``traffic`` = the ncu DRAM bytes per launch recorded under
-  profiles/ while the kernel sources keep the digest recorded there;
+  the measured BF16 tensor peak (burst) for the BF16 form (default) or, for
+  the FP32 form, the FP32 FMA peak measured in this run by the library's
+  FFMA kernel (``fp32_peak``, with the device's SM count); ``traffic`` = the
+  ncu DRAM bytes per launch recorded under profiles/ while the kernel
+  sources keep the digest recorded there;
 * ``update_roofline``: cell table and update, algorithmic bytes over their
   time, against the measured HBM copy peak;
-* ``other_precision`` (the other form's step and full LBG), ``differentiation``,
-  ``batched``, ``small_full_lbg`` and, with ``--large``, ``large``;
+* ``other_precision`` (the other form's step and full LBG), ``step_after_split``
+  (the step against the codebook right after the last split, the least
+  converged one of the design), ``differentiation`` (with the FP64 oracle's
+  full LBG on the same Gaussian-mixture data), ``batched``, ``small_full_lbg``
+  (with the pass-by-pass comparison of each precision's design with the
+  oracle) and ``large`` (64 images, 4x4 blocks: LBG on 16.8M vectors and
+  encode of 16.8M more, with the oracle's sampled encode rate);
 * ``cpu_baseline``: the FP64 oracle's Lloyd pass on a bounded row sample on
   the host cores.
+``ms_per_step`` is the median of the timed steps; ``gpu_launches`` is the
+library's own count of the kernels it launched in the timed region.
 ``--impl reference`` times only the oracle (the baseline arm).
 With ``--gpus N`` (under torchrun) every rank runs an independent replica.
 """
@@ -51,8 +59,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "vector·codevector distance evals/s per Lloyd pass; full LBG time, bf16 vs fp32"
 UNIT = "evals/s"
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -77,8 +83,10 @@ def parse():
                     help="skip the batched leg (64 ragged problems, L=16)")
     ap.add_argument("--no-small", action="store_true",
                     help="skip the full-LBG timing of the 512x512 image workload")
-    ap.add_argument("--large", action="store_true",
-                    help="add the 64-image leg: LBG to N=4096 on 16.7M vectors + encode of 16.7M more")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 64-image leg: LBG to N=4096 on 16.7M vectors + encode of 16.7M more")
+    ap.add_argument("--no-after-split", action="store_true",
+                    help="skip the step against the codebook right after the last split")
     return ap.parse_args()
 
 
@@ -392,7 +400,10 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": workload_desc(args.workload, X, N), "M": int(X.shape[0]),
-                       "L": int(X.shape[1]), "N": int(N), "rows_per_step": rows},
+                       "L": int(X.shape[1]), "N": int(N), "rows_per_step": rows,
+                       "codebook": f"N={N} seeded rows of X (untrained: the trained codebook needs the GPU)",
+                       "sample": "each step is one Lloyd pass over rows_per_step consecutive rows of X "
+                                 "(a bounded sample of the workload; value scales it to M*N evals/s)"},
             "cpu_baseline": {"kind": "oracle", "cores": oracle.max_threads(), "sample": sample,
                              "value": value, "unit": UNIT},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -415,8 +426,13 @@ def run_ours(args):
 
     X_np, N = synth.workload(args.workload)
     M, L = X_np.shape
+    # inputs of the 64-image leg, generated on the host cores in worker processes started
+    # now, before the first GPU call (their pool is spawned, never forked)
+    large_future = None if args.no_large else start_large_inputs()
     X = torch.from_numpy(X_np).cuda()
     stream = torch.cuda.current_stream()
+    # the FP32 FMA peak of this device, measured (the FP32 form's roofline denominator)
+    fp32_tflops, n_sms = lbg.measure_fp32_peak(stream.cuda_stream)
 
     # full LBG design in both forms (the headline form's codebook is the one
     # the timed steps run against)
@@ -453,6 +469,7 @@ def run_ours(args):
         barrier(dist)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("timed_steps")
+        l0 = lbg.launch_count()
         w0 = time.perf_counter()
         for k in range(steps):
             flush.zero_()
@@ -461,9 +478,12 @@ def run_ours(args):
             ends[k].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - w0
+        launches = lbg.launch_count() - l0
         torch.cuda.nvtx.range_pop()
         barrier(dist)
-        ms = max_over_ranks(dist, statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends)))
+        per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        ms = max_over_ranks(dist, statistics.median(per))
+        ms_mean = max_over_ranks(dist, statistics.mean(per))
         _, n_exact, status = lbg.read_step_result(buf)
         if status != 0:
             raise RuntimeError(f"device status {status} in the timed passes")
@@ -472,24 +492,27 @@ def run_ours(args):
             flush.zero_()
             phases.append(lbg.lbg_lloyd_step(X, C, C_out=C_out, assign_out=A, phase_ms=True,
                                              precision=prec).phase_ms)
-        ph = {k: statistics.mean(p[k] for p in phases)
+        ph = {k: statistics.median(p[k] for p in phases)
               for k in ("prep", "assign", "exact", "update", "total")}
-        return ms, ph, n_exact, wall
+        return {"ms": ms, "ms_mean": ms_mean, "ph": ph, "n_exact": n_exact, "wall": wall,
+                "launches": launches, "per_step_ms": per}
 
     with ClockSampler(gpu_uuid(dev)) as clk:
-        ms, ph, n_exact, wall = timed_steps(args.precision, args.steps)
+        t = timed_steps(args.precision, args.steps)
     clocks = clk.summary()
     # a slowdown on any rank: every rank times the steps once more (same barriers)
     if max_over_ranks(dist, 1.0 if throttled(clocks) else 0.0) > 0:
         first = clocks
         with ClockSampler(gpu_uuid(dev)) as clk:
-            ms, ph, n_exact, wall = timed_steps(args.precision, args.steps)
+            t = timed_steps(args.precision, args.steps)
         clocks = clk.summary()
         clocks["remeasured_after"] = first.get("reasons")
+    ms, ph, n_exact, wall = t["ms"], t["ph"], t["n_exact"], t["wall"]
     value = job_throughput(world, M * N, ms / 1e3)
     other_line = None
     if args.fp32_steps > 0:
-        o_ms, o_ph, o_ex, _ = timed_steps(other, args.fp32_steps)
+        ot = timed_steps(other, args.fp32_steps)
+        o_ms, o_ph, o_ex = ot["ms"], ot["ph"], ot["n_exact"]
         o_train_s, o_tr = trains[other]
         other_line = {"precision": other, "value": job_throughput(world, M * N, o_ms / 1e3), "unit": UNIT,
                       "ms_per_step": o_ms, "phase_ms": o_ph, "exact_rows_per_step": o_ex,
@@ -503,8 +526,7 @@ def run_ours(args):
         pass
     # without the measured file: the fallback peaks of an earlier GB300 measurement
     of = "of measured" if peaks else "of fallback (MEASURED_PEAKS.json absent)"
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+    fp32_peak = fp32_tflops                                   # measured in this run
     bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
     flops = 2.0 * L * M * N          # algorithmic: L FMA per distance evaluation
     assign_ms = ph["assign"]
@@ -533,12 +555,12 @@ def run_ours(args):
     else:
         roof = {"bound": "alu", "kernel": "k_assign_f32", "achieved": achieved, "peak": fp32_peak,
                 "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
-                "peak_source": f"FP32 CUDA cores: {SM_COUNT} SMs x {FP32_LANES_PER_SM} "
-                               f"lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
+                "peak_source": f"FP32 FMA peak measured in this run (lbg_measure_fp32_peak, {n_sms} SMs)",
                 "work": "2*L*M*N flop per launch"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "ms_per_step_mean": t["ms_mean"],
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": {"workload": workload_desc(args.workload, X_np, N), "M": M, "L": L, "N": N,
                        "precision": args.precision + (" (BF16 tensor-core distances, FP32 accumulation, "
@@ -550,6 +572,7 @@ def run_ours(args):
                        "full_lbg_passes_per_stage": tr.passes_per_stage(),
                        "full_lbg_D": tr.D, "exact_rows_per_step": n_exact,
                        "phase_ms": ph, "wall_s_timed_region": wall,
+                       "timing": "median of the timed steps' CUDA-event times (ms_per_step_mean: their mean)",
                        "data_sha256": synth.digest(X_np)[:16],
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,
@@ -559,22 +582,37 @@ def run_ours(args):
                                         "write codebook, counts)",
                                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs, {of}"},
             "clocks": clocks,
-            "gpu_launches": 10 * args.steps}
+            "fp32_peak": {"tflops": fp32_tflops, "sms": n_sms,
+                          "how": "lbg_measure_fp32_peak: independent FFMA chains on every SM, CUDA events"},
+            "gpu_launches": t["launches"],
+            "gpu_launches_source": "lbg_launch_count() difference over the timed region (kernels of "
+                                   "replayed graphs included)"}
     if other_line is not None:
         line["other_precision"] = other_line
+        if args.precision == "bf16":
+            f_ach = flops / (o_ph["assign"] / 1e3) / 1e12
+            other_line["roofline"] = {"bound": "alu", "kernel": "k_assign_f32", "achieved": f_ach,
+                                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": f_ach / fp32_peak,
+                                      "peak_source": "FP32 FMA peak measured in this run"}
+    if not args.no_after_split:
+        try:
+            line["step_after_split"] = after_split_leg(lbg, torch, X, N, args, flush, stream, dist)
+        except Exception as exc:   # a report must never cost the measured line
+            line["step_after_split"] = {"error": repr(exc)}
 
     # differentiation form: D(X, C) forward (nearest codevector) + backward at
     # the fixed cell table, on Gaussian-mixture vectors (M=262144, L=32, 512
     # components, sigma 0.1), codebook from LBG to N=512
     if not args.no_grad:
-        line["differentiation"] = grad_leg(lbg, synth, torch, stream, flush, args, dist)
+        line["differentiation"] = grad_leg(lbg, synth, torch, stream, flush, args, dist,
+                                           with_oracle=not args.no_cpu_baseline)
 
     if not args.no_batched:
         line["batched"] = batched_leg(lbg, synth, torch)
     if not args.no_small:
         line["small_full_lbg"] = small_leg(lbg, synth, torch, with_oracle=not args.no_cpu_baseline)
-    if args.large:
-        line["large"] = large_leg(lbg, synth, torch)
+    if large_future is not None:
+        line["large"] = large_leg(lbg, synth, torch, large_future, with_oracle=not args.no_cpu_baseline)
 
     # end to end through the public API with host buffers
     if not args.no_e2e:
@@ -613,12 +651,18 @@ def run_ours(args):
     return 0
 
 
-def grad_leg(lbg, synth, torch, stream, flush, args, dist):
+def grad_leg(lbg, synth, torch, stream, flush, args, dist, with_oracle=True):
     Xg_np, _, _ = synth.gmm(4, 262144, L=32, K=512, sigma=0.1)
     Mg, Lg = Xg_np.shape
     Ng = 512
     Xg = torch.from_numpy(Xg_np).cuda()
-    Cg = lbg.lbg_train(Xg, Ng, delta=0.01, theta=1e-3).C
+    lbg.lbg_train(Xg, Ng, delta=0.01, theta=1e-3, max_passes=1)   # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tr = lbg.lbg_train(Xg, Ng, delta=0.01, theta=1e-3)
+    torch.cuda.synchronize()
+    gpu_lbg_s = time.perf_counter() - t0
+    Cg = tr.C
     idx = torch.empty(Mg, dtype=torch.int32, device="cuda")
     for _ in range(3):
         lbg.vq_encode(Xg, Cg, idx_out=idx)
@@ -635,11 +679,26 @@ def grad_leg(lbg, synth, torch, stream, flush, args, dist):
         torch.cuda.synchronize()
         fw.append(e0.elapsed_time(e1))
         bw.append(e1.elapsed_time(e2))
-    fwd = max_over_ranks(dist, statistics.mean(fw))
-    bwd = max_over_ranks(dist, statistics.mean(bw))
+    fwd = max_over_ranks(dist, statistics.median(fw))
+    bwd = max_over_ranks(dist, statistics.median(bw))
     bytes_bwd = 3 * Mg * Lg * 4 + 2 * Mg * 4 + 2 * Ng * Lg * 4
+    full = {"gpu_fp32_s": gpu_lbg_s, "gpu_passes": tr.n_passes, "gpu_D": tr.D}
+    if with_oracle:
+        try:
+            import oracle
+            oracle.build()
+            t0 = time.perf_counter()
+            o = oracle.lbg_train(Xg_np, Ng, 0.01, 1e-3)
+            full["oracle_s"] = time.perf_counter() - t0
+            full["oracle_passes"] = int(len(o.trace_D))
+            full["oracle_D"] = float(o.D)
+            full["oracle_cores"] = oracle.max_threads()
+            full["oracle_kind"] = "FP64 oracle LBG to N=512 on the same data, all host threads"
+        except Exception as exc:   # a report must never cost the measured line
+            full["oracle_error"] = repr(exc)
     return {"workload": "gmm262144_l32_n512: 262144 Gaussian-mixture vectors, L=32, 512 components "
                         "(sigma 0.1, means U[0,1]^32), codebook from LBG to N=512",
+            "full_lbg": full,
             "forward_ms": fwd, "backward_ms": bwd, "D": D,
             "backward_gbs": bytes_bwd / (bwd / 1e3) / 1e9,
             "backward_bytes": bytes_bwd,
@@ -673,8 +732,10 @@ def small_leg(lbg, synth, torch, with_oracle=True):
         out["oracle_full_lbg"] = {"seconds": time.perf_counter() - t0, "passes": int(len(o.trace_D)),
                                   "D": float(o.D), "cores": oracle.max_threads(),
                                   "kind": "FP64 oracle LBG on the host (same data, delta, theta)"}
-        # whole-run comparison (meaningful when the oracle's run met no near-tie row)
+        # whole-run comparison (meaningful when the oracle's run met no near-tie row), and
+        # the pass-by-pass comparison: the oracle's step from every pass's own codebook
         try:
+            from oracle import trajectory
             den = np.maximum(np.abs(o.C).max(1), 1.0)
             for prec, r in runs.items():
                 Cg = r.C.cpu().numpy().astype(np.float64)
@@ -683,6 +744,12 @@ def small_leg(lbg, synth, torch, with_oracle=True):
                     "same_passes_per_stage": r.passes_per_stage() == o.passes_per_stage(),
                     "D_rel_diff": abs(r.D - o.D) / o.D,
                     "codebook_max_rel_diff": float((np.abs(Cg - o.C).max(1) / den).max())}
+                t = lbg.lbg_train(X, N, 0.01, 1e-3, precision=prec, trace=4096, trace_passes=4096)
+                rep = trajectory.compare(X_np, N, 0.01, 1e-3, t.records, t.pass_C.cpu().numpy(),
+                                         t.pass_assign.cpu().numpy(), t.C.cpu().numpy(),
+                                         t.assign.cpu().numpy(), t.D)
+                out[prec]["per_pass_vs_oracle"] = rep.summary()
+                out[prec]["pass_ms_median"] = statistics.median(rec["ms"] for rec in t.records)
         except Exception as exc:   # a report must never cost the measured line
             out["vs_oracle_error"] = repr(exc)
     return out
@@ -724,15 +791,40 @@ def batched_leg(lbg, synth, torch):
                             "calibration": tune["candidates"]}}
 
 
-def large_leg(lbg, synth, torch):
+def _large_part(seeds):
+    from paper_0910_4711_gb300 import synth
+    return synth.image_blocks(seeds, 2048, 2048, 4)
+
+
+def start_large_inputs():
+    """Start generating the 64-image leg's inputs (train seeds 5001..5064, encode seeds
+    5101..5164) in spawned worker processes; returns a callable giving (X, Y)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    n = max(1, min(16, os.cpu_count() or 1))
+    pool = cf.ProcessPoolExecutor(max_workers=n, mp_context=mp.get_context("spawn"))
+    groups = [list(range(a, a + 4)) for a in range(5001, 5065, 4)] + \
+             [list(range(a, a + 4)) for a in range(5101, 5165, 4)]
+    futs = [pool.submit(_large_part, g) for g in groups]
+
+    def result():
+        parts = [f.result() for f in futs]
+        pool.shutdown()
+        return np.concatenate(parts[:16]), np.concatenate(parts[16:])
+    return result
+
+
+def large_leg(lbg, synth, torch, inputs, with_oracle=True):
     """64 2048x2048 images, 4x4 blocks: LBG to N=4096 on 16.7M vectors, then encode 16.7M more;
-    BF16 vs FP32."""
-    X_np, N = synth.workload("img2048x64_b4_n4096")
+    BF16 vs FP32; beside it the FP64 oracle's encode rate on a row sample."""
+    X_np, Y_np = inputs()
+    N = 4096
     X = torch.from_numpy(X_np).cuda()
-    del X_np
-    Y = torch.from_numpy(synth.image_blocks(range(5101, 5165), 2048, 2048, 4)).cuda()
-    out = {"workload": "img2048x64_b4_n4096 train (M=16777216, L=16, N=4096) + encode of 16777216 "
-                       "more vectors (seeds 5101..5164)"}
+    Y = torch.from_numpy(Y_np).cuda()
+    out = {"workload": "img2048x64_b4_n4096 train (M=16777216, L=16, N=4096, seeds 5001..5064) + "
+                       "encode of 16777216 more vectors (seeds 5101..5164)",
+           "data_sha256": {"train": synth.digest(X_np)[:16], "encode": synth.digest(Y_np)[:16]}}
+    C_last = None
     for prec in ("bf16", "fp32"):
         lbg.lbg_train(X, N, 0.01, 1e-3, max_passes=1, precision=prec)
         torch.cuda.synchronize()
@@ -742,14 +834,67 @@ def large_leg(lbg, synth, torch):
         t_train = time.perf_counter() - t0
         idx = torch.empty(Y.shape[0], dtype=torch.int32, device="cuda")
         lbg.vq_encode(Y, r.C, idx_out=idx, precision=prec)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        enc = lbg.vq_encode(Y, r.C, idx_out=idx, precision=prec, phase_ms=True)
-        torch.cuda.synchronize()
-        t_enc = time.perf_counter() - t0
+        ts = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            enc = lbg.vq_encode(Y, r.C, idx_out=idx, precision=prec, phase_ms=True)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        t_enc = statistics.median(ts)
         out[prec] = {"full_lbg_s": t_train, "passes": r.n_passes, "D": r.D, "encode_s": t_enc,
-                     "encode_evals_per_s": Y.shape[0] * N / t_enc, "encode_phase_ms": enc.phase_ms}
+                     "encode_evals_per_s": Y.shape[0] * N / t_enc, "encode_phase_ms": enc.phase_ms,
+                     "encode_exact_rows": enc.n_exact}
+        C_last = r.C
+    if with_oracle:
+        try:
+            import oracle
+            oracle.build()
+            rng = np.random.default_rng(5)
+            C = C_last.cpu().numpy().astype(np.float64)
+            rows = 4096
+            while True:
+                S = np.ascontiguousarray(Y_np[np.sort(rng.choice(Y_np.shape[0], rows, replace=False))])
+                t0 = time.perf_counter()
+                oracle.assign(S, C)
+                t = time.perf_counter() - t0
+                if t > 3.0 or rows >= 1 << 20:
+                    break
+                rows *= 4
+            out["oracle_encode"] = {"evals_per_s": rows * N / t, "rows": rows, "seconds": t,
+                                    "cores": oracle.max_threads(), "kind": "FP64 oracle nearest "
+                                    "codevector of a random row sample of the encode set against the "
+                                    "FP32 design's codebook, all host threads"}
+        except Exception as exc:   # a report must never cost the measured line
+            out["oracle_encode"] = {"error": repr(exc)}
     return out
+
+
+def after_split_leg(lbg, torch, X, N, args, flush, stream, dist):
+    """The step against the codebook right after the design's last split (pass 0 of the
+    N-entry stage: every codevector has a twin at 2 delta, the least converged codebook and
+    the one with the most near-ties), in the headline precision."""
+    half = lbg.lbg_train(X, N // 2, 0.01, 1e-3, precision=args.precision).C
+    Cs = lbg.lbg_train(X, N, 0.01, 1e-3, C_init=half, max_passes=1, precision=args.precision).C
+    C_out = torch.empty_like(Cs)
+    A = torch.empty(X.shape[0], dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        flush.zero_()
+        lbg.lbg_lloyd_step(X, Cs, C_out=C_out, assign_out=A, precision=args.precision)
+    per, nex = [], None
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = lbg.lbg_lloyd_step(X, Cs, C_out=C_out, assign_out=A, precision=args.precision, phase_ms=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per.append(e0.elapsed_time(e1))
+        nex = r.n_exact
+    ms = max_over_ranks(dist, statistics.median(per))
+    return {"codebook": f"N={N}: the N/2 design split once (pass 0 of the last stage)",
+            "ms_per_step": ms, "value": X.shape[0] * N / (ms / 1e3), "unit": UNIT,
+            "exact_rows_per_step": nex, "phase_ms": r.phase_ms}
 
 
 def main():

@@ -92,6 +92,10 @@ typedef struct lbg_pass_record {
     int32_t action;    /* LBG_ACT_* taken after the stop test */
     int32_t n_exact;   /* rows re-scored exactly by the fallback kernel */
     double D;          /* total distortion of the pass */
+    int32_t n_empty;   /* cells (of stage_n) that no row chose in this pass */
+    float ms;          /* device time of the pass, from the start of its first
+                          kernel to the end of its last (%globaltimer, about
+                          1 us resolution) */
 } lbg_pass_record;
 
 /* Tile choice of lbg_train_batched's persistent nearest-codevector launch and
@@ -152,6 +156,27 @@ typedef struct lbg_opts {
                                      (D, n_exact, phase_ms) must be NULL (else LBG_ERR_ARG).
                                      Later calls of this library on any stream of the device
                                      wait for the enqueued pass before touching its scratch. */
+    float *trace_C;             /* lbg_train: DEVICE [trace_cap x N x L] or NULL.  Pass p (counted
+                                   over the whole run from 0, as the records) writes the codebook
+                                   its allocation used (the stage's stage_n rows; the rest of the
+                                   N x L slot is left as it was) to trace_C + p N L.  Passes
+                                   beyond trace_cap are not written. */
+    int32_t *trace_assign;      /* lbg_train: DEVICE [trace_cap x M] or NULL.  Pass p writes its
+                                   cell table (nearest codevector of every row under that
+                                   codebook) to trace_assign + p M. */
+    int32_t trace_cap;          /* passes trace_C / trace_assign hold */
+    int32_t test_expire_wait;   /* test hook, 0 in normal use.  Non-zero: in an FP32
+                                   lbg_lloyd_step / vq_encode, the first bounded wait of every CTA
+                                   of the nearest-codevector kernel gives up at once, as if its
+                                   codebook copy had not landed within the time limit.  Each CTA
+                                   then waits (bounded) for the copies it issued, writes no row and
+                                   reports; the call returns LBG_ERR_TIMEOUT.  Such calls are
+                                   launched directly, never recorded into a graph.  Ignored by the
+                                   other entry points and by LBG_PREC_BF16. */
+    const float *grad_scale_dev; /* lbg_distortion_backward: DEVICE float or NULL.  When set, the
+                                    upstream gradient is read from it on the device and the gD
+                                    argument is ignored (an autograd caller then needs no host
+                                    read of it); every array must be device memory. */
 } lbg_opts;
 
 /* Fill *opts with the defaults (FP32, 1000 passes, default stream, no trace,
@@ -252,7 +277,11 @@ lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, 
  *   dX[m] = 2 gD (x_m - c_a(m))                         [M x L], nullable
  *   D     = the distortion at the fixed cell table      host out, nullable
  *   X [M x L], C [N x L], assign [M] (values in [0, N)) as for the other calls.
- * dC is deterministic (fixed-order cell sums, no float atomics).
+ * dC is deterministic (fixed-order cell sums, no float atomics).  gD must be
+ * finite (LBG_ERR_ARG) unless opts->grad_scale_dev supplies it on the device.
+ * With opts->result_dev the call only enqueues, as lbg_lloyd_step: D and the
+ * device status land in *result_dev (D must then be NULL and every array
+ * device memory).
  */
 lbg_status lbg_distortion_backward(const float *X, int64_t M, int32_t L, const float *C, int32_t N,
                                    const int32_t *assign, float gD, float *dC, float *dX, double *D,
@@ -272,13 +301,18 @@ lbg_status lbg_distortion_backward(const float *X, int64_t M, int32_t L, const f
  * one calls no cudaMalloc, cudaFree or allocating library routine.
  *
  * Its scratch is one fixed 16 MiB __device__ array inside the library, held
- * on every GPU that loads the library until the process exits.  The first
- * call on a device looks up that array's device address (cudaGetSymbolAddress
- * with the device current); make that first call before any stream capture.
- * All calls share the array and each re-initialises what it needs, so calls
- * whose work overlaps on the GPU (other streams, other host threads) race.
+ * on every GPU that loads the library's device code until the process exits
+ * (that load, by the first call of the library on a device that uses these
+ * kernels, is when the array comes into being).  The first call on a device
+ * also looks up the array's device address (cudaGetSymbolAddress with the
+ * device current).  All calls share the array and each re-initialises what it
+ * needs, so calls whose work overlaps on the GPU (other streams, other host
+ * threads) race.  Every call reads its result back and synchronises its
+ * stream before it returns, so it cannot be called on a stream that is being
+ * captured into a CUDA graph.
  *
- *   X     [M x L] DEVICE array; M >= 0 (any size: processed in chunks).
+ *   X     [M x L] DEVICE array; 0 <= M <= INT32_MAX (LBG_ERR_ARG beyond;
+ *         rows are processed in chunks of 2^20).
  *   C     [N x L] DEVICE codebook.
  *   idx   [M] DEVICE out: nearest codevector (same rule as vq_encode).
  *   D     host out, nullable: sum of the squared distances.
@@ -295,7 +329,38 @@ const char *lbg_status_string(lbg_status s);
 /* Free the cached device scratch of the current device. */
 lbg_status lbg_release_workspace(void);
 
-/* Library ABI version (this header: 1). */
+/*
+ * lbg_set_workspace_limit -- cap, in bytes, on the cached device scratch of
+ * every device (0 = no cap, the default).  The cap is enforced where the
+ * scratch is allocated: a call that needs more than the cap behaves as if
+ * cudaMalloc had refused -- the cached scratch of the device is released (as
+ * for any growth) and the call returns LBG_ERR_NOMEM with its outputs
+ * untouched.  Lifting or raising the cap makes later calls succeed again.
+ * (A memory budget for the library's scratch; no counterpart in the paper.)
+ */
+lbg_status lbg_set_workspace_limit(size_t bytes);
+
+/*
+ * lbg_launch_count -- number of CUDA kernels this library has launched in
+ * this process (all devices): direct launches, plus the kernels of a
+ * recorded graph each time it is replayed.  Recording a graph launches
+ * nothing and is not counted.  A diagnostic for reports; no counterpart in
+ * the paper.
+ */
+int64_t lbg_launch_count(void);
+
+/*
+ * lbg_measure_fp32_peak -- the FP32 FMA throughput of the current device,
+ * measured: a kernel of independent FFMA chains on every SM (32 warps per SM,
+ * 8 chains per thread) is timed with CUDA events on `stream` after a warm-up
+ * launch.  *tflops = 2 flop per lane FMA / time (TFLOP/s, at whatever SM clock
+ * the device ran), *sms = the device's multiprocessor count (either out may be
+ * NULL).  The denominator of the FP32 nearest-codevector kernel's roofline;
+ * no counterpart in the paper.  Synchronises the stream.
+ */
+lbg_status lbg_measure_fp32_peak(void *stream, double *tflops, int32_t *sms);
+
+/* Library ABI version (this header: 2). */
 int32_t lbg_version(void);
 
 #ifdef __cplusplus

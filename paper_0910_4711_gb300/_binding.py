@@ -26,7 +26,9 @@ STATUS = {0: "LBG_OK", 1: "LBG_WARN_MAXPASS", -1: "LBG_ERR_ARG", -2: "LBG_ERR_NO
 PHASES = ("prep", "assign", "exact", "update", "total")
 ACTIONS = ("update", "split", "finish")
 EXPORTS = ("lbg_opts_init", "lbg_train", "lbg_lloyd_step", "vq_encode", "lbg_status_string",
-           "lbg_release_workspace", "lbg_version", "lbg_distortion_backward", "lbg_train_batched")
+           "lbg_release_workspace", "lbg_version", "lbg_distortion_backward", "lbg_train_batched",
+           "vq_encode_noalloc", "lbg_set_workspace_limit", "lbg_launch_count",
+           "lbg_measure_fp32_peak")
 
 
 class LBGError(RuntimeError):
@@ -37,7 +39,8 @@ class LBGError(RuntimeError):
 
 class PassRecord(ctypes.Structure):
     _fields_ = [("stage_n", ctypes.c_int32), ("pass_", ctypes.c_int32), ("action", ctypes.c_int32),
-                ("n_exact", ctypes.c_int32), ("D", ctypes.c_double)]
+                ("n_exact", ctypes.c_int32), ("D", ctypes.c_double), ("n_empty", ctypes.c_int32),
+                ("ms", ctypes.c_float)]
 
 
 class TuneReport(ctypes.Structure):
@@ -65,7 +68,10 @@ class Opts(ctypes.Structure):
                 ("delta_reseed", ctypes.c_double), ("autotune", ctypes.c_int32),
                 ("tile_rows", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("tune_report", ctypes.POINTER(TuneReport)),
-                ("result_dev", ctypes.c_void_p)]
+                ("result_dev", ctypes.c_void_p),
+                ("trace_C", ctypes.c_void_p), ("trace_assign", ctypes.c_void_p),
+                ("trace_cap", ctypes.c_int32), ("test_expire_wait", ctypes.c_int32),
+                ("grad_scale_dev", ctypes.c_void_p)]
 
 
 STEP_RESULT_BYTES = 16   # lbg_step_result: double D, int32 n_exact, int32 status
@@ -122,6 +128,15 @@ def lib():
         L.lbg_release_workspace.restype = ctypes.c_int
         L.lbg_version.argtypes = []
         L.lbg_version.restype = ctypes.c_int32
+        L.vq_encode_noalloc.argtypes = [P, i64, i32, P, i32, P, P, P]
+        L.vq_encode_noalloc.restype = ctypes.c_int
+        L.lbg_set_workspace_limit.argtypes = [ctypes.c_size_t]
+        L.lbg_set_workspace_limit.restype = ctypes.c_int
+        L.lbg_launch_count.argtypes = []
+        L.lbg_launch_count.restype = ctypes.c_int64
+        L.lbg_measure_fp32_peak.argtypes = [P, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_int32)]
+        L.lbg_measure_fp32_peak.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -167,10 +182,12 @@ PRECISION = {"fp32": 0, "bf16": 1}
 
 
 def _opts(cuda_ref, max_passes=1000, records=0, phase=False, stream=None, precision="fp32",
-          split_multiplicative=False, reseed_empty=False, delta_reseed=0.0, result=None):
+          split_multiplicative=False, reseed_empty=False, delta_reseed=0.0, result=None,
+          test_expire_wait=False):
     o = Opts()
     lib().lbg_opts_init(ctypes.byref(o))
     o.max_passes = int(max_passes)
+    o.test_expire_wait = int(bool(test_expire_wait))
     o.split_multiplicative = int(bool(split_multiplicative))
     o.reseed_empty = int(bool(reseed_empty))
     o.delta_reseed = float(delta_reseed)
@@ -226,6 +243,8 @@ class TrainResult:
     records: list
     n_passes: int
     phase_ms: dict | None
+    pass_C: object = None       # [passes, N, L] device: codebook each pass's allocation used
+    pass_assign: object = None  # [passes, M] device: each pass's cell table
 
     def passes_per_stage(self):
         out = []
@@ -262,8 +281,12 @@ class EncodeResult:
 def lbg_train(X, N: int, delta: float = 0.01, theta: float = 1e-3, C_init=None,
               max_passes: int = 1000, trace: int = 4096, phase_ms: bool = False, C_out=None,
               assign_out=None, stream=None, precision: str = "fp32",
-              split_multiplicative: bool = False, reseed_empty: bool = False) -> TrainResult:
-    """Design an N-entry codebook from X [M, L] (see lbg_train in lbgvq.h)."""
+              split_multiplicative: bool = False, reseed_empty: bool = False,
+              trace_passes: int = 0) -> TrainResult:
+    """Design an N-entry codebook from X [M, L] (see lbg_train in lbgvq.h).  With
+    trace_passes > 0 (X on a CUDA device) the codebook and the cell table of each of the first
+    trace_passes passes are kept on the device (result.pass_C, result.pass_assign, one entry
+    per pass run)."""
     Xo, xp, _ = _prep(X, "f32", "X")
     M, L = int(X.shape[0]), int(X.shape[1])
     C = C_out if C_out is not None else _empty_like_src(X, (N, L), "f32")
@@ -276,6 +299,15 @@ def lbg_train(X, N: int, delta: float = 0.01, theta: float = 1e-3, C_init=None,
     Ao, ap, _ = _prep(A, "i32", "assign")
     o, keep = _opts(_cuda_ref(X, C, A), max_passes, trace, phase_ms, stream, precision,
                     split_multiplicative, reseed_empty)
+    pC = pA = None
+    if trace_passes > 0:
+        ref = _cuda_ref(X)
+        if ref is None:
+            raise ValueError("trace_passes needs X on a CUDA device (the trace is device memory)")
+        import torch
+        pC = torch.zeros((trace_passes, N, L), dtype=torch.float32, device=ref.device)
+        pA = torch.full((trace_passes, M), -1, dtype=torch.int32, device=ref.device)
+        o.trace_C, o.trace_assign, o.trace_cap = pC.data_ptr(), pA.data_ptr(), int(trace_passes)
     D = ctypes.c_double(0.0)
     rc = _check(lib().lbg_train(xp, M, L, int(N), float(delta), float(theta), cp, n_init, ap,
                                 ctypes.byref(D), ctypes.byref(o)))
@@ -284,13 +316,17 @@ def lbg_train(X, N: int, delta: float = 0.01, theta: float = 1e-3, C_init=None,
         n = min(keep["nrec"].value, trace)
         for r in keep["rec"][:n]:
             recs.append({"stage_n": r.stage_n, "pass": r.pass_, "action": ACTIONS[r.action],
-                         "n_exact": r.n_exact, "D": r.D})
-    return TrainResult(rc, C, A, D.value, recs, keep["nrec"].value if trace else -1, _phases(keep))
+                         "n_exact": r.n_exact, "D": r.D, "n_empty": r.n_empty, "ms": r.ms})
+    n_passes = keep["nrec"].value if trace else -1
+    if pC is not None and n_passes >= 0:
+        pC, pA = pC[:n_passes], pA[:n_passes]
+    return TrainResult(rc, C, A, D.value, recs, n_passes, _phases(keep), pC, pA)
 
 
 def lbg_lloyd_step(X, C_in, C_out=None, assign_out=None, phase_ms: bool = False,
                    stream=None, precision: str = "fp32", reseed_empty: bool = False,
-                   delta_reseed: float = 0.01, result_out=None) -> StepResult:
+                   delta_reseed: float = 0.01, result_out=None,
+                   test_expire_wait: bool = False) -> StepResult:
     """One Lloyd pass from C_in (see lbg_lloyd_step in lbgvq.h).  With result_out (a
     step_result_buffer) the pass is only enqueued on the stream: D, n_exact and the
     device status land in result_out (read_step_result)."""
@@ -303,7 +339,8 @@ def lbg_lloyd_step(X, C_in, C_out=None, assign_out=None, phase_ms: bool = False,
     A = assign_out if assign_out is not None else _empty_like_src(X, (M,), "i32")
     A, ap, _ = _prep(A, "i32", "assign")
     o, keep = _opts(_cuda_ref(X, C_in, Co, A), stream=stream, phase=phase_ms, precision=precision,
-                    reseed_empty=reseed_empty, delta_reseed=delta_reseed, result=result_out)
+                    reseed_empty=reseed_empty, delta_reseed=delta_reseed, result=result_out,
+                    test_expire_wait=test_expire_wait)
     if result_out is not None:
         rc = _check(lib().lbg_lloyd_step(xp, M, L, N, cip, cop, ap, None, ctypes.byref(o)))
         return StepResult(rc, Co, A, float("nan"), -1, None, result_out)
@@ -313,7 +350,8 @@ def lbg_lloyd_step(X, C_in, C_out=None, assign_out=None, phase_ms: bool = False,
 
 
 def vq_encode(X, C, decode: bool = False, with_distortion: bool = True, phase_ms: bool = False,
-              idx_out=None, stream=None, precision: str = "fp32", result_out=None) -> EncodeResult:
+              idx_out=None, stream=None, precision: str = "fp32", result_out=None,
+              test_expire_wait: bool = False) -> EncodeResult:
     """Nearest codevector of every row of X (see vq_encode in lbgvq.h).  With result_out
     (a step_result_buffer) the call is only enqueued, as for lbg_lloyd_step."""
     Xo, xp, _ = _prep(X, "f32", "X")
@@ -325,7 +363,7 @@ def vq_encode(X, C, decode: bool = False, with_distortion: bool = True, phase_ms
     H = _empty_like_src(X, (M, L), "f32") if decode else None
     H, hp, _ = _prep(H, "f32", "Xhat")
     o, keep = _opts(_cuda_ref(X, C, I), stream=stream, phase=phase_ms, precision=precision,
-                    result=result_out)
+                    result=result_out, test_expire_wait=test_expire_wait)
     if result_out is not None:
         rc = _check(lib().vq_encode(xp, M, L, cp, N, ip, hp, None, ctypes.byref(o)))
         return EncodeResult(rc, I, H, float("nan"), -1, None, result_out)
@@ -337,9 +375,13 @@ def vq_encode(X, C, decode: bool = False, with_distortion: bool = True, phase_ms
 
 
 def distortion_backward(X, C, assign, grad_D: float = 1.0, want_dC: bool = True,
-                        want_dX: bool = True, phase_ms: bool = False, stream=None):
+                        want_dX: bool = True, phase_ms: bool = False, stream=None,
+                        grad_scale=None, result_out=None):
     """D at the fixed cell table `assign` and its gradients (see lbg_distortion_backward in
-    lbgvq.h).  Returns (D, dC or None, dX or None, phase_ms)."""
+    lbgvq.h).  Returns (D, dC or None, dX or None, phase_ms).  grad_scale: a one-element
+    float32 CUDA tensor holding the upstream gradient (read on the device; grad_D is then
+    ignored).  result_out (a step_result_buffer): the call is only enqueued, D lands there
+    (the returned D is nan)."""
     Xo, xp, _ = _prep(X, "f32", "X")
     M, L = int(X.shape[0]), int(X.shape[1])
     N = int(C.shape[0])
@@ -349,7 +391,17 @@ def distortion_backward(X, C, assign, grad_D: float = 1.0, want_dC: bool = True,
     dX = _empty_like_src(X, (M, L), "f32") if want_dX else None
     dC, dcp, _ = _prep(dC, "f32", "dC")
     dX, dxp, _ = _prep(dX, "f32", "dX")
-    o, keep = _opts(_cuda_ref(X, C, assign), stream=stream, phase=phase_ms)
+    o, keep = _opts(_cuda_ref(X, C, assign), stream=stream, phase=phase_ms, result=result_out)
+    if grad_scale is not None:
+        gs, gp, gcuda = _prep(grad_scale, "f32", "grad_scale")
+        if not gcuda:
+            raise ValueError("grad_scale must be a CUDA tensor")
+        o.grad_scale_dev = gp
+        grad_D = 0.0
+    if result_out is not None:
+        _check(lib().lbg_distortion_backward(xp, M, L, cp, N, ap, float(grad_D), dcp, dxp, None,
+                                             ctypes.byref(o)))
+        return float("nan"), dC, dX, None
     D = ctypes.c_double(0.0)
     _check(lib().lbg_distortion_backward(xp, M, L, cp, N, ap, float(grad_D), dcp, dxp,
                                          ctypes.byref(D), ctypes.byref(o)))
@@ -407,8 +459,48 @@ def lbg_train_batched(X, row_off, N, delta: float = 0.01, theta: float = 1e-3,
     return BatchedResult(rc, C, A, D.tolist(), code_off, nrec.value, _phases(keep), rep.as_dict())
 
 
+def vq_encode_noalloc(X, C, idx_out=None, with_distortion: bool = True, stream=None):
+    """(idx, D) of vq_encode_noalloc (see lbgvq.h): X, C and idx are CUDA tensors; the call
+    allocates no device memory (D is nan without with_distortion)."""
+    Xo, xp, xc = _prep(X, "f32", "X")
+    Co, cp, cc = _prep(C, "f32", "C")
+    if not (xc and cc):
+        raise ValueError("vq_encode_noalloc needs X and C on a CUDA device")
+    M, L, N = int(X.shape[0]), int(X.shape[1]), int(C.shape[0])
+    I = idx_out if idx_out is not None else _empty_like_src(X, (M,), "i32")
+    I, ip, _ = _prep(I, "i32", "idx")
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream(X.device).cuda_stream
+    D = ctypes.c_double(float("nan"))
+    _check(lib().vq_encode_noalloc(xp, M, L, cp, N, ip, ctypes.byref(D) if with_distortion else None,
+                                   ctypes.c_void_p(int(stream))))
+    return I, D.value
+
+
 def release_workspace() -> None:
     _check(lib().lbg_release_workspace())
+
+
+def set_workspace_limit(nbytes: int) -> None:
+    """Cap the library's cached device scratch at nbytes (0: no cap); see lbg_set_workspace_limit."""
+    _check(lib().lbg_set_workspace_limit(int(nbytes)))
+
+
+def launch_count() -> int:
+    """Kernels this library has launched in this process (graph replays included)."""
+    return int(lib().lbg_launch_count())
+
+
+def measure_fp32_peak(stream=None):
+    """(TFLOP/s of FP32 FMA measured on the current device, its SM count)."""
+    tf = ctypes.c_double(0.0)
+    sms = ctypes.c_int32(0)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(lib().lbg_measure_fp32_peak(ctypes.c_void_p(int(stream)), ctypes.byref(tf), ctypes.byref(sms)))
+    return tf.value, sms.value
 
 
 def version() -> int:

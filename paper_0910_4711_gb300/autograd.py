@@ -10,7 +10,9 @@ pass (lbg_distortion_backward):
 
 These are the true gradients wherever no vector sits on a tie between two
 codevectors (where D is not differentiable).  Both kernels run on the GPU;
-this module only marshals tensors.
+this module only marshals tensors.  For CUDA tensors neither pass waits for
+the device: D is a device scalar written by the forward call, and the
+upstream gradient is handed to the backward kernels as a device scalar.
 """
 from __future__ import annotations
 
@@ -26,16 +28,28 @@ class Distortion(torch.autograd.Function):
     def forward(ctx, X: torch.Tensor, C: torch.Tensor, precision: str = "fp32"):
         X = X.detach().contiguous()
         C = C.detach().contiguous()
-        enc = _binding.vq_encode(X, C, precision=precision)
+        if X.is_cuda and C.is_cuda:
+            buf = _binding.step_result_buffer(X.device)
+            enc = _binding.vq_encode(X, C, precision=precision, result_out=buf)
+            D = buf[:8].view(torch.float64).reshape(())       # written on the device
+        else:
+            enc = _binding.vq_encode(X, C, precision=precision)
+            D = torch.tensor(enc.D, dtype=torch.float64, device=X.device)
         ctx.save_for_backward(X, C, enc.idx)
-        return torch.tensor(enc.D, dtype=torch.float64, device=X.device)
+        return D
 
     @staticmethod
     def backward(ctx, grad_D):
         X, C, idx = ctx.saved_tensors
         need_x, need_c = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
-        _, dC, dX, _ = _binding.distortion_backward(X, C, idx, float(grad_D), want_dC=need_c,
-                                                    want_dX=need_x)
+        if X.is_cuda:
+            g = grad_D.detach().to(device=X.device, dtype=torch.float32).reshape(1).contiguous()
+            buf = _binding.step_result_buffer(X.device)
+            _, dC, dX, _ = _binding.distortion_backward(X, C, idx, want_dC=need_c, want_dX=need_x,
+                                                        grad_scale=g, result_out=buf)
+        else:
+            _, dC, dX, _ = _binding.distortion_backward(X, C, idx, float(grad_D), want_dC=need_c,
+                                                        want_dX=need_x)
         return dX, dC, None
 
 

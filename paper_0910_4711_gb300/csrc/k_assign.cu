@@ -217,13 +217,15 @@ using AssignSmem = AssignSmemT<BM>;
 // TBM / 32 warp rows x 2 warp columns.
 // The two chunk barriers persist across calls of one CTA: use0/use1 count
 // their completed phases.  Returns false (after reporting) if a bulk copy
-// timed out; every thread of the CTA returns the same value.
+// timed out; every thread of the CTA returns the same value.  `expire`
+// (a test hook) makes the first chunk wait give up at once, as a wait that
+// ran out of time would.
 template <int TBM>
 __device__ __forceinline__ bool assign_f32_tile_t(
     const float *__restrict__ X, int64_t M, int L, int Lp, const float *__restrict__ Cp,
     const float *__restrict__ kn, int N, const float *__restrict__ mu, const float *__restrict__ C,
     DevState *st, int32_t *__restrict__ assign, float *__restrict__ e, int32_t *__restrict__ flags,
-    int64_t m0, float *smem, AssignSmemT<TBM> &sh, uint32_t &use0, uint32_t &use1)
+    int64_t m0, float *smem, AssignSmemT<TBM> &sh, uint32_t &use0, uint32_t &use1, int expire = 0)
 {
     uint64_t *bar = sh.bar;
     auto &rec_v1 = sh.rec_v1;
@@ -281,7 +283,7 @@ __device__ __forceinline__ bool assign_f32_tile_t(
     for (int k = 0; k < nchunk; ++k) {
         const int b = k & 1;
         const float *cb = b ? cbuf1 : cbuf0;
-        const bool ok = mbar_wait_bounded(&bar[b], parity(k));
+        const bool ok = (expire && k == 0) ? false : mbar_wait_bounded(&bar[b], parity(k));
         if (!ok) sh.abort = 1;
         if (ok) {
             float acc[8][8];
@@ -454,7 +456,7 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 2)
                  const float *__restrict__ kn, const int32_t *n_dev, int n_host,
                  const float *__restrict__ mu, const float *__restrict__ C, DevState *st,
                  int32_t *__restrict__ assign, float *__restrict__ e, int32_t *__restrict__ flags,
-                 int64_t m_lo)
+                 int64_t m_lo, int expire)
 {
     if (st->finished) return;
     extern __shared__ __align__(128) float smem[];
@@ -468,7 +470,7 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 2)
     __syncthreads();
     uint32_t u0 = 0, u1 = 0;
     (void)assign_f32_tile_t<BM>(X, M, L, Lp, Cp, kn, cur_n(n_dev, n_host), mu, C, st, assign, e, flags,
-                                m_lo + (int64_t)blockIdx.x * BM, smem, sh, u0, u1);
+                                m_lo + (int64_t)blockIdx.x * BM, smem, sh, u0, u1, expire);
 }
 
 // Batched problems: a persistent CTA takes (problem, row tile) work items from
@@ -693,7 +695,8 @@ __global__ void __launch_bounds__(EX_THREADS)
 // index and the result does not depend on which CTA finishes last.
 constexpr int XS_R = 32;
 constexpr int XS_HALF = XS_R / 2;
-constexpr int XS_CTAS = 2 * 152;   // two resident CTAs per SM: one wave
+// two resident CTAs per SM: one wave
+int xs_ctas() { return 2 * num_sms(); }
 
 struct ExactSplitSmem {
     float xs[LMAX][XS_R];
@@ -998,12 +1001,12 @@ __global__ void k_decode(const int32_t *__restrict__ assign, int64_t M, int L,
 
 void launch_begin(const float *C, int N, int L, float *mu, bool round_mu, DevState *st, cudaStream_t s)
 {
-    k_begin<<<L, 256, 0, s>>>(C, N, L, mu, round_mu ? 1 : 0, st, N);
+    LBG_COUNTED k_begin<<<L, 256, 0, s>>>(C, N, L, mu, round_mu ? 1 : 0, st, N);
 }
 
 void launch_codebook_mean(const float *C, int N, int L, float *mu, cudaStream_t s)
 {
-    k_codebook_mean<<<L, 256, 0, s>>>(C, N, L, mu);
+    LBG_COUNTED k_codebook_mean<<<L, 256, 0, s>>>(C, N, L, mu);
 }
 
 void launch_prep(const float *C, int N_alloc, const int32_t *n_dev, int n_host, int L, int Lp,
@@ -1011,21 +1014,21 @@ void launch_prep(const float *C, int N_alloc, const int32_t *n_dev, int n_host, 
                  cudaStream_t s)
 {
     const int total = round_up(N_alloc, BN);
-    k_prep<<<total / PREP_TILE, 256, 0, s>>>(C, n_dev, n_host, L, Lp, mu, Cp, kn, CT, NP, st);
+    LBG_COUNTED k_prep<<<total / PREP_TILE, 256, 0, s>>>(C, n_dev, n_host, L, Lp, mu, Cp, kn, CT, NP, st);
 }
 
 size_t assign_smem_bytes(int Lp) { return (size_t)(Lp * BM + 2 * (Lp + 1) * BN) * sizeof(float); }
 
 void launch_assign(const float *X, int64_t M, int L, int Lp, const float *Cp, const float *kn,
                    const int32_t *n_dev, int n_host, const float *mu, const float *C, DevState *st,
-                   int32_t *assign, float *e, int32_t *flags, cudaStream_t s, int64_t m_lo)
+                   int32_t *assign, float *e, int32_t *flags, cudaStream_t s, int64_t m_lo, int expire)
 {
     const size_t smem = assign_smem_bytes(Lp);
     cudaFuncSetAttribute(k_assign_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int64_t grid = (M - m_lo + BM - 1) / BM;
     if (grid <= 0) return;
-    k_assign_f32<<<(unsigned)grid, ASSIGN_THREADS, smem, s>>>(X, M, L, Lp, Cp, kn, n_dev, n_host, mu,
-                                                              C, st, assign, e, flags, m_lo);
+    LBG_COUNTED k_assign_f32<<<(unsigned)grid, ASSIGN_THREADS, smem, s>>>(X, M, L, Lp, Cp, kn, n_dev, n_host, mu,
+                                                              C, st, assign, e, flags, m_lo, expire);
 }
 
 void launch_exact(const float *X, int L, int Lp, const float *CT, const int32_t *n_dev, int n_host,
@@ -1037,13 +1040,14 @@ void launch_exact(const float *X, int L, int Lp, const float *CT, const int32_t 
     const size_t smem = (size_t)2 * Lp * EX_SW * sizeof(float);
     cudaFuncSetAttribute(k_assign_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int64_t groups = (M + EX_R - 1) / EX_R;
-    int64_t blocks = groups < 152 * 3 ? groups : 152 * 3;
+    const int64_t cap = 3 * (int64_t)num_sms();
+    int64_t blocks = groups < cap ? groups : cap;
     if (blocks < 1) blocks = 1;
-    k_assign_exact<<<(unsigned)blocks, EX_THREADS, smem, s>>>(X, L, Lp, CT, n_dev, n_host, st, flags,
+    LBG_COUNTED k_assign_exact<<<(unsigned)blocks, EX_THREADS, smem, s>>>(X, L, Lp, CT, n_dev, n_host, st, flags,
                                                              assign, e);
 }
 
-int exact_split_ctas() { return XS_CTAS; }
+int exact_split_ctas() { return xs_ctas(); }
 int exact_split_rows() { return XS_R; }
 
 void launch_exact_split(const float *X, int L, int Lp, const float *CT, const int32_t *n_dev, int n_host,
@@ -1055,16 +1059,17 @@ void launch_exact_split(const float *X, int L, int Lp, const float *CT, const in
     // the flagged count is known only on the device: up to one wave, at least 16 CTAs per
     // possible group of rows when M is small (CTAs beyond the units exit at once)
     int64_t blocks = (M + XS_R - 1) / XS_R;
-    blocks = blocks * 16 < XS_CTAS ? blocks * 16 : XS_CTAS;
+    const int64_t wave = xs_ctas();
+    blocks = blocks * 16 < wave ? blocks * 16 : wave;
     if (blocks < 1) blocks = 1;
-    k_assign_exact_split<<<(unsigned)blocks, EX_THREADS, smem, s>>>(X, L, Lp, CT, n_dev, n_host, st, flags,
+    LBG_COUNTED k_assign_exact_split<<<(unsigned)blocks, EX_THREADS, smem, s>>>(X, L, Lp, CT, n_dev, n_host, st, flags,
                                                                    assign, e, part_d, part_i, cnt);
 }
 
 void launch_b_prep(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int L, int Lp,
                    cudaStream_t s)
 {
-    kb_prep<<<total_blocks, 256, 0, s>>>(sets, S, pre, L, Lp);
+    LBG_COUNTED kb_prep<<<total_blocks, 256, 0, s>>>(sets, S, pre, L, Lp);
 }
 
 void launch_b_assign(const BatchSet *sets, int S, const int64_t *pre_tiles, int64_t total_tiles,
@@ -1072,32 +1077,33 @@ void launch_b_assign(const BatchSet *sets, int S, const int64_t *pre_tiles, int6
 {
     // the work counter and the per-problem codebook norms are reset by
     // kb_reset, which runs before kb_prep in the pass (see lbg_train_batched)
-    int64_t grid = 152 * (int64_t)ctas_per_sm;
+    int64_t grid = num_sms() * (int64_t)ctas_per_sm;
     if (grid > total_tiles) grid = total_tiles;
     if (grid < 1) return;
     if (tile_rows == 64) {
         const size_t smem = (size_t)(Lp * 64 + 2 * (Lp + 1) * BN) * sizeof(float);
         cudaFuncSetAttribute(kb_assign_f32<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kb_assign_f32<64><<<(unsigned)grid, 128, smem, s>>>(sets, S, pre_tiles, total_tiles, L, Lp, counter);
+        LBG_COUNTED kb_assign_f32<64><<<(unsigned)grid, 128, smem, s>>>(sets, S, pre_tiles, total_tiles, L, Lp, counter);
     } else {
         const size_t smem = assign_smem_bytes(Lp);
         cudaFuncSetAttribute(kb_assign_f32<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kb_assign_f32<128><<<(unsigned)grid, 256, smem, s>>>(sets, S, pre_tiles, total_tiles, L, Lp, counter);
+        LBG_COUNTED kb_assign_f32<128><<<(unsigned)grid, 256, smem, s>>>(sets, S, pre_tiles, total_tiles, L, Lp, counter);
     }
 }
 
 void launch_b_reset(const BatchSet *sets, int S, int *counter, cudaStream_t s)
 {
-    kb_reset<<<(S + 255) / 256, 256, 0, s>>>(sets, S, counter);
+    LBG_COUNTED kb_reset<<<(S + 255) / 256, 256, 0, s>>>(sets, S, counter);
 }
 
 void launch_b_exact(const BatchSet *sets, int S, int L, int Lp, int max_ngroups, cudaStream_t s)
 {
     const size_t smem = (size_t)2 * Lp * EX_SW * sizeof(float);
     cudaFuncSetAttribute(kb_assign_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int grid = max_ngroups < 152 * 3 ? max_ngroups : 152 * 3;
+    const int cap = 3 * num_sms();
+    int grid = max_ngroups < cap ? max_ngroups : cap;
     if (grid < 1) grid = 1;
-    kb_assign_exact<<<grid, EX_THREADS, smem, s>>>(sets, S, L, Lp);
+    LBG_COUNTED kb_assign_exact<<<grid, EX_THREADS, smem, s>>>(sets, S, L, Lp);
 }
 
 void launch_decode(const int32_t *assign, int64_t M, int L, const float *C, float *Xhat,
@@ -1105,7 +1111,7 @@ void launch_decode(const int32_t *assign, int64_t M, int L, const float *C, floa
 {
     const int64_t total = M * L;
     if (total == 0) return;
-    k_decode<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(assign, M, L, C, Xhat);
+    LBG_COUNTED k_decode<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(assign, M, L, C, Xhat);
 }
 
 }  // namespace lbg

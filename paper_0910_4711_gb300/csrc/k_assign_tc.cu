@@ -1383,7 +1383,7 @@ size_t tc_codebook_bytes(int NP, int L) { return (size_t)tc_prep_rows(NP) * tc_k
 
 bool tc_supported(int L) { return L >= 1 && L <= TC_LMAX; }
 
-void launch_round_mu(float *mu, int L, cudaStream_t s) { k_round_mu<<<1, 128, 0, s>>>(mu, L); }
+void launch_round_mu(float *mu, int L, cudaStream_t s) { LBG_COUNTED k_round_mu<<<1, 128, 0, s>>>(mu, L); }
 
 void launch_prep_tc(const float *C, int N_alloc, const int32_t *n_dev, int n_host, int L,
                     const float *mu, void *Bp, float *kn, float *CT, DevState *st, cudaStream_t s)
@@ -1392,10 +1392,10 @@ void launch_prep_tc(const float *C, int N_alloc, const int32_t *n_dev, int n_hos
     __nv_bfloat16 *B = static_cast<__nv_bfloat16 *>(Bp);
     const int Lp = round_up(L, 4);
     switch (round_up(L, 16)) {
-    case 16: k_prep_tc<16><<<blocks, 256, 0, s>>>(C, n_dev, n_host, L, Lp, mu, B, kn, CT, st); break;
-    case 32: k_prep_tc<32><<<blocks, 256, 0, s>>>(C, n_dev, n_host, L, Lp, mu, B, kn, CT, st); break;
-    case 48: k_prep_tc<48><<<blocks, 256, 0, s>>>(C, n_dev, n_host, L, Lp, mu, B, kn, CT, st); break;
-    default: k_prep_tc<64><<<blocks, 256, 0, s>>>(C, n_dev, n_host, L, Lp, mu, B, kn, CT, st); break;
+    case 16: LBG_COUNTED k_prep_tc<16><<<blocks, 256, 0, s>>>(C, n_dev, n_host, L, Lp, mu, B, kn, CT, st); break;
+    case 32: LBG_COUNTED k_prep_tc<32><<<blocks, 256, 0, s>>>(C, n_dev, n_host, L, Lp, mu, B, kn, CT, st); break;
+    case 48: LBG_COUNTED k_prep_tc<48><<<blocks, 256, 0, s>>>(C, n_dev, n_host, L, Lp, mu, B, kn, CT, st); break;
+    default: LBG_COUNTED k_prep_tc<64><<<blocks, 256, 0, s>>>(C, n_dev, n_host, L, Lp, mu, B, kn, CT, st); break;
     }
 }
 
@@ -1421,8 +1421,8 @@ static void launch_tc(const float *X, int64_t M, int L, const void *Bp, const fl
         // at least 120 KB so that a single CTA (and its 512 TMEM columns) owns the SM
         const size_t smem = need > 120 * 1024 ? need : 120 * 1024;
         cudaFuncSetAttribute(k_assign_tc_p<LK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        const int64_t g = grid < 152 ? grid : 152;
-        k_assign_tc_p<LK><<<(unsigned)g, TC_THREADS, smem, s>>>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign,
+        const int64_t g = grid < num_sms() ? grid : num_sms();
+        LBG_COUNTED k_assign_tc_p<LK><<<(unsigned)g, TC_THREADS, smem, s>>>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign,
                                                                e, flags, keymask, m_lo);
         return;
     }
@@ -1430,7 +1430,7 @@ static void launch_tc(const float *X, int64_t M, int L, const void *Bp, const fl
     // at least 120 KB so that a single CTA (and its 512 TMEM columns) owns the SM
     const size_t smem = need > 120 * 1024 ? need : 120 * 1024;
     cudaFuncSetAttribute(k_assign_tc<LK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_assign_tc<LK><<<(unsigned)grid, TC_THREADS, smem, s>>>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign,
+    LBG_COUNTED k_assign_tc<LK><<<(unsigned)grid, TC_THREADS, smem, s>>>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign,
                                                              e, flags, keymask, m_lo);
 }
 

@@ -38,6 +38,14 @@ __device__ __forceinline__ bool skip_update(const DevState *st, int train)
     return train && (st->finished || st->action != ACT_UPDATE);
 }
 
+// The cell sizes and offsets (k_scan, k_offsets) are computed on every pass of
+// a training run, also on a pass that ends its stage: the pass trace reports
+// the empty cells of every allocation.
+__device__ __forceinline__ bool skip_counts(const DevState *st, int train)
+{
+    return train && st->finished;
+}
+
 // ---------------------------------------------------------------- mean
 // Column sums of X per CTA over a contiguous row range: FP32 runs of 8 rows
 // accumulated in FP64, then a fixed-order reduction.  part[b*L + l].
@@ -191,6 +199,8 @@ __device__ __forceinline__ void body_ctl(const double *__restrict__ dpart, int C
         r.action = act;
         r.n_exact = nflag;
         r.D = D;
+        r.n_empty = -1;   // filled in at the end of a traced pass
+        r.ms = 0.f;
         rec[st->total] = r;
     }
     st->total += 1;
@@ -248,7 +258,7 @@ __global__ void __launch_bounds__(1024) k_scan(int32_t *__restrict__ table, int 
                                                const int32_t *n_dev, int n_host,
                                                int32_t *__restrict__ counts, DevState *st, int train)
 {
-    if (skip_update(st, train)) return;
+    if (skip_counts(st, train)) return;
     body_scan(table, CH, cur_n(n_dev, n_host), counts, blockIdx.x);
 }
 
@@ -290,7 +300,7 @@ __global__ void __launch_bounds__(1024) k_offsets(const int32_t *__restrict__ co
                                                   const int32_t *n_dev, int n_host,
                                                   int32_t *__restrict__ off, DevState *st, int train)
 {
-    if (skip_update(st, train)) return;
+    if (skip_counts(st, train)) return;
     body_offsets(counts, cur_n(n_dev, n_host), off);
 }
 
@@ -550,6 +560,7 @@ __global__ void k_combine(const float *__restrict__ pieces, const int32_t *__res
 __global__ void __launch_bounds__(256) k_grad_x(const float *__restrict__ X, int64_t M, int L,
                                                 const float *__restrict__ C, int N,
                                                 const int32_t *__restrict__ assign, float gD,
+                                                const float *__restrict__ gD_dev,
                                                 float *__restrict__ e, float *__restrict__ dX,
                                                 DevState *st)
 {
@@ -563,7 +574,7 @@ __global__ void __launch_bounds__(256) k_grad_x(const float *__restrict__ X, int
     const float *xr = X + m * L;
     const float *cr = C + (int64_t)a * L;
     float *gr = dX ? dX + m * L : nullptr;
-    const float g2 = 2.0f * gD;
+    const float g2 = 2.0f * (gD_dev ? *gD_dev : gD);
     float d2 = 0.f;
     for (int l = 0; l < L; ++l) {
         const float d = xr[l] - cr[l];
@@ -577,8 +588,9 @@ __global__ void __launch_bounds__(256) k_grad_x(const float *__restrict__ X, int
 // same deterministic pieces as the centroid update (FP64 combine in order).
 __global__ void k_combine_grad(const float *__restrict__ pieces, const int32_t *__restrict__ off,
                                int N, int L, int64_t S, const float *__restrict__ C, float gD,
-                               float *__restrict__ dC)
+                               const float *__restrict__ gD_dev, float *__restrict__ dC)
 {
+    if (gD_dev) gD = *gD_dev;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)N * L) return;
     const int n = (int)(i / L), l = (int)(i - (int64_t)n * L);
@@ -706,6 +718,61 @@ __device__ __forceinline__ void body_stage(DevState *st)
 }
 
 __global__ void k_stage(DevState *st) { body_stage(st); }
+
+// ---------------------------------------------------------------- pass trace
+// Start of a pass of lbg_train with a trace: marks whether the pass runs (a
+// pass issued after training ended does not), stamps its start and copies the
+// codebook its allocation uses (the stage's n_cur rows) to trace slot
+// st->total (the pass's index over the run).
+__global__ void __launch_bounds__(256) k_trace_begin(DevState *st, const float *__restrict__ C, int N,
+                                                     int L, float *__restrict__ trace_C, int cap)
+{
+    const bool run = !st->finished;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->trace_on = run ? 1 : 0;
+        if (run) st->t_pass0 = global_ns();
+    }
+    if (!run || !trace_C) return;
+    const int slot = st->total;
+    if (slot >= cap) return;
+    const int64_t n = (int64_t)st->n_cur * L;
+    float *dst = trace_C + (int64_t)slot * N * L;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = C[i];
+}
+
+// End of a traced pass (its record is slot st->total - 1): the pass's cell
+// table to its trace slot; block 0 counts the stage's empty cells and writes
+// them and the pass's device time into the record.
+__global__ void __launch_bounds__(256) k_trace_end(DevState *st, const int32_t *__restrict__ assign,
+                                                   int64_t M, const int32_t *__restrict__ counts,
+                                                   PassRecord *rec, int max_rec,
+                                                   int32_t *__restrict__ trace_A, int cap)
+{
+    if (!st->trace_on) return;
+    const int slot = st->total - 1;
+    if (slot < 0) return;
+    if (trace_A && slot < cap) {
+        int32_t *dst = trace_A + (int64_t)slot * M;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x)
+            dst[i] = assign[i];
+    }
+    if (blockIdx.x != 0 || !rec || slot >= max_rec) return;
+    __shared__ int wsum[8];
+    const int n = rec[slot].stage_n;
+    int empty = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) empty += counts[i] == 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) empty += __shfl_xor_sync(0xffffffffu, empty, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = empty;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < 8; ++w) t += wsum[w];
+        rec[slot].n_empty = t;
+        rec[slot].ms = (float)((double)(global_ns() - st->t_pass0) * 1e-6);
+    }
+}
 
 // ---------------------------------------------------------------- batched
 // One launch per step for every problem of a batched call: block b serves
@@ -841,8 +908,8 @@ __global__ void kb_stage(const BatchSet *__restrict__ sets) { body_stage(sets[bl
 void launch_mean(const float *X, int64_t M, int L, double *part, int G, float *mu, float *C0,
                  DevState *st, cudaStream_t s)
 {
-    k_mean_part<<<G, 256, 0, s>>>(X, M, L, part, st);
-    k_mean_final<<<1, 128, 0, s>>>(part, G, M, L, mu, C0);
+    LBG_COUNTED k_mean_part<<<G, 256, 0, s>>>(X, M, L, part, st);
+    LBG_COUNTED k_mean_final<<<1, 128, 0, s>>>(part, G, M, L, mu, C0);
 }
 
 void launch_hist(const int32_t *assign, const float *e, int64_t M, int64_t R, int CH,
@@ -851,14 +918,14 @@ void launch_hist(const int32_t *assign, const float *e, int64_t M, int64_t R, in
 {
     const size_t smem = do_hist ? (size_t)n_host * sizeof(int) : 0;
     cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_hist<<<CH, HIST_THREADS, smem, s>>>(assign, e, M, R, n_dev, n_host, do_hist ? 1 : 0, table,
+    LBG_COUNTED k_hist<<<CH, HIST_THREADS, smem, s>>>(assign, e, M, R, n_dev, n_host, do_hist ? 1 : 0, table,
                                           dpart, st, train ? 1 : 0);
 }
 
 void launch_ctl(const double *dpart, int CH, DevState *st, int mode, double theta, int max_passes,
                 int N_target, PassRecord *records, int max_records, cudaStream_t s)
 {
-    k_ctl<<<1, 32, 0, s>>>(dpart, CH, st, mode, theta, max_passes, N_target, records, max_records);
+    LBG_COUNTED k_ctl<<<1, 32, 0, s>>>(dpart, CH, st, mode, theta, max_passes, N_target, records, max_records);
 }
 
 void launch_hist_ctl(const int32_t *assign, const float *e, int64_t M, int64_t R, int CH, int N,
@@ -866,26 +933,26 @@ void launch_hist_ctl(const int32_t *assign, const float *e, int64_t M, int64_t R
 {
     const size_t smem = do_hist ? (size_t)N * sizeof(int) : 0;
     cudaFuncSetAttribute(k_hist_ctl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_hist_ctl<<<CH, HIST_THREADS, smem, s>>>(assign, e, M, R, N, do_hist ? 1 : 0, table, dpart, st);
+    LBG_COUNTED k_hist_ctl<<<CH, HIST_THREADS, smem, s>>>(assign, e, M, R, N, do_hist ? 1 : 0, table, dpart, st);
 }
 
 void launch_scan_offsets(int32_t *table, int CH, int N, int32_t *counts, int32_t *off, DevState *st,
                          cudaStream_t s)
 {
-    k_scan_offsets<<<(N + 31) / 32, 1024, 0, s>>>(table, CH, N, counts, off, st);
+    LBG_COUNTED k_scan_offsets<<<(N + 31) / 32, 1024, 0, s>>>(table, CH, N, counts, off, st);
 }
 
 void launch_scan(int32_t *table, int CH, const int32_t *n_dev, int n_host, int32_t *counts,
                  DevState *st, bool train, cudaStream_t s)
 {
-    k_scan<<<(n_host + 31) / 32, 1024, 0, s>>>(table, CH, n_dev, n_host, counts, st, train ? 1 : 0);
+    LBG_COUNTED k_scan<<<(n_host + 31) / 32, 1024, 0, s>>>(table, CH, n_dev, n_host, counts, st, train ? 1 : 0);
 }
 
 void launch_offsets(const int32_t *counts, const int32_t *n_dev, int n_host, int64_t M,
                     int32_t *off, DevState *st, bool train, cudaStream_t s)
 {
     (void)M;
-    k_offsets<<<1, 1024, 0, s>>>(counts, n_dev, n_host, off, st, train ? 1 : 0);
+    LBG_COUNTED k_offsets<<<1, 1024, 0, s>>>(counts, n_dev, n_host, off, st, train ? 1 : 0);
 }
 
 void launch_scatter(const int32_t *assign, int64_t M, int64_t R, int CH, const int32_t *table,
@@ -894,7 +961,7 @@ void launch_scatter(const int32_t *assign, int64_t M, int64_t R, int CH, const i
 {
     const size_t smem = (size_t)n_host * (sizeof(int) + 8);
     cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_scatter<<<CH, 256, smem, s>>>(assign, M, R, table, off, n_dev, n_host, perm, st,
+    LBG_COUNTED k_scatter<<<CH, 256, smem, s>>>(assign, M, R, table, off, n_dev, n_host, perm, st,
                                     train ? 1 : 0);
 }
 
@@ -908,14 +975,14 @@ void launch_cellsum(const float *X, int64_t M, int L, const int32_t *perm, const
     const int t = train ? 1 : 0;
     const bool al = (reinterpret_cast<uintptr_t>(X) & 15u) == 0;
     switch (al ? L : 0) {
-    case 4: k_cellsum_v4<1><<<blocks, 256, 0, s>>>(X, M, perm, off, n_dev, n_host, S, pieces, st, t); break;
-    case 8: k_cellsum_v4<2><<<blocks, 256, 0, s>>>(X, M, perm, off, n_dev, n_host, S, pieces, st, t); break;
-    case 16: k_cellsum_v4<4><<<blocks, 256, 0, s>>>(X, M, perm, off, n_dev, n_host, S, pieces, st, t); break;
-    case 32: k_cellsum_v4<8><<<blocks, 256, 0, s>>>(X, M, perm, off, n_dev, n_host, S, pieces, st, t); break;
-    case 64: k_cellsum_v4<16><<<blocks, 256, 0, s>>>(X, M, perm, off, n_dev, n_host, S, pieces, st, t); break;
-    case 128: k_cellsum_v4<32><<<blocks, 256, 0, s>>>(X, M, perm, off, n_dev, n_host, S, pieces, st, t); break;
+    case 4: LBG_COUNTED k_cellsum_v4<1><<<blocks, 256, 0, s>>>(X, M, perm, off, n_dev, n_host, S, pieces, st, t); break;
+    case 8: LBG_COUNTED k_cellsum_v4<2><<<blocks, 256, 0, s>>>(X, M, perm, off, n_dev, n_host, S, pieces, st, t); break;
+    case 16: LBG_COUNTED k_cellsum_v4<4><<<blocks, 256, 0, s>>>(X, M, perm, off, n_dev, n_host, S, pieces, st, t); break;
+    case 32: LBG_COUNTED k_cellsum_v4<8><<<blocks, 256, 0, s>>>(X, M, perm, off, n_dev, n_host, S, pieces, st, t); break;
+    case 64: LBG_COUNTED k_cellsum_v4<16><<<blocks, 256, 0, s>>>(X, M, perm, off, n_dev, n_host, S, pieces, st, t); break;
+    case 128: LBG_COUNTED k_cellsum_v4<32><<<blocks, 256, 0, s>>>(X, M, perm, off, n_dev, n_host, S, pieces, st, t); break;
     default:
-        k_cellsum_any<<<blocks, 256, 0, s>>>(X, M, L, perm, off, n_dev, n_host, S, pieces, st, t);
+        LBG_COUNTED k_cellsum_any<<<blocks, 256, 0, s>>>(X, M, L, perm, off, n_dev, n_host, S, pieces, st, t);
     }
 }
 
@@ -924,15 +991,15 @@ void launch_combine(const float *pieces, const int32_t *off, const int32_t *n_de
                     cudaStream_t s)
 {
     const int64_t total = (int64_t)n_host * L;
-    k_combine<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(pieces, off, n_dev, n_host, L, S, C_in,
+    LBG_COUNTED k_combine<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(pieces, off, n_dev, n_host, L, S, C_in,
                                                              C_out, st, train ? 1 : 0);
 }
 
 void launch_b_mean(const BatchSet *sets, int S, const int32_t *pre_mean, int total_blocks, int L,
                    cudaStream_t s)
 {
-    kb_mean<<<total_blocks, 256, 0, s>>>(sets, S, pre_mean, L);
-    kb_mean_final<<<S, 128, 0, s>>>(sets, L);
+    LBG_COUNTED kb_mean<<<total_blocks, 256, 0, s>>>(sets, S, pre_mean, L);
+    LBG_COUNTED kb_mean_final<<<S, 128, 0, s>>>(sets, L);
 }
 
 void launch_b_hist(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int NMAXB,
@@ -940,22 +1007,22 @@ void launch_b_hist(const BatchSet *sets, int S, const int32_t *pre, int total_bl
 {
     const size_t smem = (size_t)NMAXB * sizeof(int);
     cudaFuncSetAttribute(kb_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kb_hist<<<total_blocks, HIST_THREADS, smem, s>>>(sets, S, pre);
+    LBG_COUNTED kb_hist<<<total_blocks, HIST_THREADS, smem, s>>>(sets, S, pre);
 }
 
 void launch_b_ctl(const BatchSet *sets, int S, double theta, int max_passes, cudaStream_t s)
 {
-    kb_ctl<<<S, 32, 0, s>>>(sets, theta, max_passes);
+    LBG_COUNTED kb_ctl<<<S, 32, 0, s>>>(sets, theta, max_passes);
 }
 
 void launch_b_scan(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, cudaStream_t s)
 {
-    kb_scan<<<total_blocks, 1024, 0, s>>>(sets, S, pre);
+    LBG_COUNTED kb_scan<<<total_blocks, 1024, 0, s>>>(sets, S, pre);
 }
 
 void launch_b_offsets(const BatchSet *sets, int S, cudaStream_t s)
 {
-    kb_offsets<<<S, 1024, 0, s>>>(sets);
+    LBG_COUNTED kb_offsets<<<S, 1024, 0, s>>>(sets);
 }
 
 void launch_b_scatter(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int NMAXB,
@@ -963,61 +1030,61 @@ void launch_b_scatter(const BatchSet *sets, int S, const int32_t *pre, int total
 {
     const size_t smem = (size_t)NMAXB * (sizeof(int) + 8);
     cudaFuncSetAttribute(kb_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kb_scatter<<<total_blocks, 256, smem, s>>>(sets, S, pre);
+    LBG_COUNTED kb_scatter<<<total_blocks, 256, smem, s>>>(sets, S, pre);
 }
 
 void launch_b_cellsum(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int L,
                       bool vec, cudaStream_t s)
 {
     switch (vec ? L : 0) {
-    case 4: kb_cellsum_v4<1><<<total_blocks, 256, 0, s>>>(sets, S, pre); break;
-    case 8: kb_cellsum_v4<2><<<total_blocks, 256, 0, s>>>(sets, S, pre); break;
-    case 16: kb_cellsum_v4<4><<<total_blocks, 256, 0, s>>>(sets, S, pre); break;
-    case 32: kb_cellsum_v4<8><<<total_blocks, 256, 0, s>>>(sets, S, pre); break;
-    case 64: kb_cellsum_v4<16><<<total_blocks, 256, 0, s>>>(sets, S, pre); break;
-    case 128: kb_cellsum_v4<32><<<total_blocks, 256, 0, s>>>(sets, S, pre); break;
-    default: kb_cellsum_any<<<total_blocks, 256, 0, s>>>(sets, S, pre, L);
+    case 4: LBG_COUNTED kb_cellsum_v4<1><<<total_blocks, 256, 0, s>>>(sets, S, pre); break;
+    case 8: LBG_COUNTED kb_cellsum_v4<2><<<total_blocks, 256, 0, s>>>(sets, S, pre); break;
+    case 16: LBG_COUNTED kb_cellsum_v4<4><<<total_blocks, 256, 0, s>>>(sets, S, pre); break;
+    case 32: LBG_COUNTED kb_cellsum_v4<8><<<total_blocks, 256, 0, s>>>(sets, S, pre); break;
+    case 64: LBG_COUNTED kb_cellsum_v4<16><<<total_blocks, 256, 0, s>>>(sets, S, pre); break;
+    case 128: LBG_COUNTED kb_cellsum_v4<32><<<total_blocks, 256, 0, s>>>(sets, S, pre); break;
+    default: LBG_COUNTED kb_cellsum_any<<<total_blocks, 256, 0, s>>>(sets, S, pre, L);
     }
 }
 
 void launch_b_combine(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int L,
                       cudaStream_t s)
 {
-    kb_combine<<<total_blocks, 256, 0, s>>>(sets, S, pre, L);
+    LBG_COUNTED kb_combine<<<total_blocks, 256, 0, s>>>(sets, S, pre, L);
 }
 
 void launch_b_split(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int L,
                     double delta, bool mult, cudaStream_t s)
 {
-    kb_split<<<total_blocks, 256, 0, s>>>(sets, S, pre, L, delta, mult ? 1 : 0);
+    LBG_COUNTED kb_split<<<total_blocks, 256, 0, s>>>(sets, S, pre, L, delta, mult ? 1 : 0);
 }
 
 void launch_b_advance(const BatchSet *sets, int S, const int32_t *pre, int total_blocks, int L,
                       cudaStream_t s)
 {
-    kb_copy_split<<<total_blocks, 256, 0, s>>>(sets, S, pre, L);
-    kb_stage<<<S, 32, 0, s>>>(sets);
+    LBG_COUNTED kb_copy_split<<<total_blocks, 256, 0, s>>>(sets, S, pre, L);
+    LBG_COUNTED kb_stage<<<S, 32, 0, s>>>(sets);
 }
 
 void launch_grad_x(const float *X, int64_t M, int L, const float *C, int N, const int32_t *assign,
-                   float gD, float *e, float *dX, DevState *st, cudaStream_t s)
+                   float gD, const float *gD_dev, float *e, float *dX, DevState *st, cudaStream_t s)
 {
     if (M == 0) return;
-    k_grad_x<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(X, M, L, C, N, assign, gD, e, dX, st);
+    LBG_COUNTED k_grad_x<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(X, M, L, C, N, assign, gD, gD_dev, e, dX, st);
 }
 
 void launch_combine_grad(const float *pieces, const int32_t *off, int N, int L, int64_t S,
-                         const float *C, float gD, float *dC, cudaStream_t s)
+                         const float *C, float gD, const float *gD_dev, float *dC, cudaStream_t s)
 {
     const int64_t total = (int64_t)N * L;
-    k_combine_grad<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(pieces, off, N, L, S, C, gD, dC);
+    LBG_COUNTED k_combine_grad<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(pieces, off, N, L, S, C, gD, gD_dev, dC);
 }
 
 void launch_split(const float *C_cur, float *C_alt, int N_alloc, int L, double delta, bool mult,
                   DevState *st, cudaStream_t s)
 {
     const int64_t total = (int64_t)(N_alloc / 2 > 0 ? N_alloc / 2 : 1) * L;
-    k_split<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(C_cur, C_alt, L, delta, mult ? 1 : 0, st);
+    LBG_COUNTED k_split<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(C_cur, C_alt, L, delta, mult ? 1 : 0, st);
 }
 
 void launch_reseed(const int32_t *off, const int32_t *n_dev, int n_host, int L, double delta,
@@ -1025,15 +1092,32 @@ void launch_reseed(const int32_t *off, const int32_t *n_dev, int n_host, int L, 
 {
     const size_t smem = (size_t)n_host * sizeof(int);
     cudaFuncSetAttribute(k_reseed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_reseed<<<1, 1024, smem, s>>>(off, n_dev, n_host, L, delta, C, st, train ? 1 : 0);
+    LBG_COUNTED k_reseed<<<1, 1024, smem, s>>>(off, n_dev, n_host, L, delta, C, st, train ? 1 : 0);
+}
+
+void launch_trace_begin(DevState *st, const float *C, int N, int L, float *trace_C, int cap,
+                        cudaStream_t s)
+{
+    int blocks = (int)(((int64_t)N * L + 1023) / 1024);
+    if (blocks < 1) blocks = 1;
+    LBG_COUNTED k_trace_begin<<<blocks, 256, 0, s>>>(st, C, N, L, trace_C, cap);
+}
+
+void launch_trace_end(DevState *st, const int32_t *assign, int64_t M, const int32_t *counts,
+                      PassRecord *rec, int max_rec, int32_t *trace_A, int cap, cudaStream_t s)
+{
+    int64_t blocks = trace_A ? (M + 1023) / 1024 : 1;
+    if (blocks > 2 * (int64_t)num_sms()) blocks = 2 * (int64_t)num_sms();
+    if (blocks < 1) blocks = 1;
+    LBG_COUNTED k_trace_end<<<(unsigned)blocks, 256, 0, s>>>(st, assign, M, counts, rec, max_rec, trace_A, cap);
 }
 
 void launch_advance(const float *C_alt, float *C_cur, int N_alloc, int L, DevState *st,
                     cudaStream_t s)
 {
     const int64_t total = (int64_t)N_alloc * L;
-    k_copy_split<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(C_alt, C_cur, L, st);
-    k_stage<<<1, 32, 0, s>>>(st);
+    LBG_COUNTED k_copy_split<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(C_alt, C_cur, L, st);
+    LBG_COUNTED k_stage<<<1, 32, 0, s>>>(st);
 }
 
 }  // namespace lbg

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <array>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <algorithm>
@@ -16,8 +17,34 @@
 using namespace lbg;
 
 namespace {
-
 constexpr int MAX_DEVICES = 64;
+std::atomic<int64_t> g_launches{0};
+std::atomic<int> g_sms[MAX_DEVICES];
+std::atomic<size_t> g_ws_limit{0};
+}  // namespace
+
+namespace lbg {
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int num_sms()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+        (void)cudaGetLastError();
+        return 1;
+    }
+    int n = g_sms[dev].load(std::memory_order_relaxed);
+    if (n > 0) return n;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+        (void)cudaGetLastError();
+        return 1;
+    }
+    g_sms[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
+}  // namespace lbg
+
+namespace {
 
 struct Workspace {
     void *base = nullptr;
@@ -61,20 +88,22 @@ Plan make_plan(int64_t M, int L, int N, int max_rec, bool host_X, bool need_assi
     p.max_rec = max_rec;
     // histogram / scatter chunks: <= HIST_CHUNKS_MAX CTAs of R rows (R a multiple of 256)
     int64_t ch = (M + 1023) / 1024;
-    if (ch > HIST_CHUNKS_MAX) ch = HIST_CHUNKS_MAX;
+    const int64_t ch_cap = std::min<int64_t>(HIST_CHUNKS_MAX, 2 * (int64_t)num_sms());
+    if (ch > ch_cap) ch = ch_cap;
     if (ch < 1) ch = 1;
     p.R = round_up64((M + ch - 1) / ch, 256);
     if (p.R < 256) p.R = 256;
     p.CH = (int)((M + p.R - 1) / p.R);
     if (p.CH < 1) p.CH = 1;
     // centroid pieces: one warp per S cell-sorted rows, aiming at >= 64 warps per SM
-    int64_t S = round_up64((M + 152 * 64 - 1) / (152 * 64), 32);
+    const int64_t warps = (int64_t)num_sms() * 64;
+    int64_t S = round_up64((M + warps - 1) / warps, 32);
     if (S < 128) S = 128;
     if (S > 4096) S = 4096;
     p.S = S;
     p.nq = (M + S - 1) / S;
     int64_t g = (M + 4095) / 4096;
-    if (g > 304) g = 304;
+    if (g > 2 * num_sms()) g = 2 * num_sms();
     if (g < 1) g = 1;
     p.G = (int)g;
 
@@ -138,6 +167,8 @@ lbg_status ensure_workspace(Call &c, size_t bytes)
             w.bytes = 0;
         }
         void *p = nullptr;
+        const size_t cap = g_ws_limit.load();
+        if (cap != 0 && bytes > cap) return LBG_ERR_NOMEM;   // as if cudaMalloc had refused
         if (cudaMalloc(&p, bytes) != cudaSuccess) {
             (void)cudaGetLastError();
             return LBG_ERR_NOMEM;
@@ -267,7 +298,7 @@ void run_prepare(const Call &c, const Plan &p, const float *C, const int32_t *n_
 // Nearest codevector of rows [m_lo, m_hi) (default: all rows).
 void run_assign(const Call &c, const Plan &p, const float *X, const float *C, const int32_t *n_dev,
                 int n_host, const float *mu, DevState *st, int32_t *assign, int64_t m_lo = 0,
-                int64_t m_hi = -1)
+                int64_t m_hi = -1, int expire = 0)
 {
     const int64_t M = m_hi < 0 ? p.M : m_hi;
     if (p.tc)
@@ -275,19 +306,19 @@ void run_assign(const Call &c, const Plan &p, const float *X, const float *C, co
                          assign, c.at<float>(p.e), c.at<int32_t>(p.flags), c.s, m_lo);
     else
         launch_assign(X, M, p.L, p.Lp, c.at<float>(p.Cp), c.at<float>(p.kn), n_dev, n_host, mu, C,
-                      st, assign, c.at<float>(p.e), c.at<int32_t>(p.flags), c.s, m_lo);
+                      st, assign, c.at<float>(p.e), c.at<int32_t>(p.flags), c.s, m_lo, expire);
 }
 
 // Host-resident X: its rows go to the device staging buffer Xs in pieces on a
 // copy stream, and the nearest-codevector search of each piece starts as soon
 // as it has landed, so that the host-to-device copy (the larger cost of a step
 // from host memory) overlaps the search.  A piece is one wave of the search
-// (152 SMs x 256 rows; the FP32 kernel's wave, 2 x 152 x 128 rows, is the
+// (SMs x 256 rows; the FP32 kernel's wave, 2 x SMs x 128 rows, is the
 // same), so that each piece's search keeps pace with the next piece's copy
 // (measured ~210 GB/s host-to-device); at most HOST_CHUNKS pieces.  Returns
 // false if a CUDA call failed.
 constexpr int HOST_CHUNKS = 32;
-constexpr int64_t HOST_PIECE_ROWS = 152 * 256;
+int64_t host_piece_rows() { return (int64_t)num_sms() * 256; }
 cudaStream_t g_copy[MAX_DEVICES];
 cudaEvent_t g_copy_ev[MAX_DEVICES][HOST_CHUNKS + 1];
 
@@ -307,12 +338,14 @@ bool host_copy_begin(const Call &c)
 }
 
 bool run_assign_host(const Call &c, const Plan &p, const float *hostX, float *Xs, const float *C,
-                     const int32_t *n_dev, int n_host, const float *mu, DevState *st, int32_t *assign)
+                     const int32_t *n_dev, int n_host, const float *mu, DevState *st, int32_t *assign,
+                     int expire = 0)
 {
     const int d = c.dev;
     // pieces in whole 256-row tiles
     const int64_t tiles = (p.M + 255) / 256;
-    int64_t np = (p.M + HOST_PIECE_ROWS - 1) / HOST_PIECE_ROWS;
+    const int64_t piece = host_piece_rows();
+    int64_t np = (p.M + piece - 1) / piece;
     if (np > HOST_CHUNKS) np = HOST_CHUNKS;
     for (int k = 0; k < np; ++k) {
         const int64_t r0 = std::min<int64_t>(p.M, tiles * k / np * 256);
@@ -323,7 +356,7 @@ bool run_assign_host(const Call &c, const Plan &p, const float *hostX, float *Xs
             cudaEventRecord(g_copy_ev[d][k], g_copy[d]) != cudaSuccess ||
             cudaStreamWaitEvent(c.s, g_copy_ev[d][k], 0) != cudaSuccess)
             return false;
-        run_assign(c, p, Xs, C, n_dev, n_host, mu, st, assign, r0, r1);
+        run_assign(c, p, Xs, C, n_dev, n_host, mu, st, assign, r0, r1, expire);
     }
     return true;
 }
@@ -371,6 +404,7 @@ struct GraphPass {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev = nullptr;
+    int64_t kernels = 0;   // kernels recorded into the graph (counted per replay)
     template <class F>
     void build(cudaStream_t user, F &&issue)
     {
@@ -384,7 +418,10 @@ struct GraphPass {
             (void)cudaGetLastError();
             return;
         }
+        const int64_t before = g_launches.load();
         issue(cap);
+        kernels = g_launches.load() - before;
+        g_launches.fetch_sub(kernels);   // recording launches nothing
         if (cudaStreamEndCapture(cap, &graph) != cudaSuccess || !graph ||
             cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
             (void)cudaGetLastError();
@@ -404,6 +441,7 @@ struct GraphPass {
         cudaEventRecord(ev, user);
         cudaStreamWaitEvent(cap, ev, 0);
         cudaGraphLaunch(exec, cap);
+        g_launches.fetch_add(kernels);
         cudaEventRecord(ev, cap);
         cudaStreamWaitEvent(user, ev, 0);
     }
@@ -439,6 +477,7 @@ struct SeqGraph {
     SeqKey key;
     cudaGraphExec_t exec = nullptr;
     uint64_t used = 0;
+    int64_t kernels = 0;   // kernels recorded into the graph (counted per replay)
 };
 
 constexpr size_t SEQ_CACHE_MAX = 32;
@@ -479,8 +518,12 @@ lbg_status seq_run(const Call &c, const SeqKey &key, F &&issue)
         }
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
+        int64_t kernels = 0;
         if (cudaStreamBeginCapture(g_cap[c.dev], cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+            const int64_t before = g_launches.load();
             issue(g_cap[c.dev]);
+            kernels = g_launches.load() - before;
+            g_launches.fetch_sub(kernels);   // recording launches nothing
             if (cudaStreamEndCapture(g_cap[c.dev], &graph) != cudaSuccess || !graph ||
                 cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
                 exec = nullptr;
@@ -508,11 +551,12 @@ lbg_status seq_run(const Call &c, const SeqKey &key, F &&issue)
             g_seq[old] = g_seq.back();
             g_seq.pop_back();
         }
-        g_seq.push_back(SeqGraph{key, exec, 0});
+        g_seq.push_back(SeqGraph{key, exec, 0, kernels});
         hit = &g_seq.back();
     }
     hit->used = ++g_seq_clock;
     CK(cudaGraphLaunch(hit->exec, c.s));
+    g_launches.fetch_add(hit->kernels);
     return LBG_OK;
 }
 
@@ -537,7 +581,15 @@ void lbg_opts_init(lbg_opts *o)
     o->autotune = 1;
 }
 
-int32_t lbg_version(void) { return 1; }
+int32_t lbg_version(void) { return 2; }
+
+lbg_status lbg_set_workspace_limit(size_t bytes)
+{
+    g_ws_limit.store(bytes);
+    return LBG_OK;
+}
+
+int64_t lbg_launch_count(void) { return g_launches.load(); }
 
 const char *lbg_status_string(lbg_status s)
 {
@@ -623,19 +675,20 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
         run_prepare(k, p, dC, nullptr, N, mu, st, false);
         tm.mark(1, s);
         if (wX == 0) {
-            if (!run_assign_host(k, p, X, c.at<float>(p.Xs), dC, nullptr, N, mu, st, dI)) host_ok = false;
+            if (!run_assign_host(k, p, X, c.at<float>(p.Xs), dC, nullptr, N, mu, st, dI, o.test_expire_wait))
+                host_ok = false;
         } else {
-            run_assign(k, p, dX, dC, nullptr, N, mu, st, dI);
+            run_assign(k, p, dX, dC, nullptr, N, mu, st, dI, 0, -1, o.test_expire_wait);
         }
         tm.mark(2, s);
         run_exact(k, p, dX, nullptr, N, st, dI);
         tm.mark(3, s);
         if (wantD) launch_hist_ctl(dI, k.at<float>(p.e), M, p.R, p.CH, N, false, nullptr, k.at<double>(p.dpart), st, s);
         if (dH) launch_decode(dI, M, L, dC, dH, s);
-        if (res) k_step_report<<<1, 1, 0, s>>>(st, res, 1);
+        if (res) LBG_COUNTED k_step_report<<<1, 1, 0, s>>>(st, res, 1);
         tm.mark(4, s);
     };
-    if (o.phase_ms || wX == 0) {   // direct: timed phases, or the pieces of a host X
+    if (o.phase_ms || wX == 0 || o.test_expire_wait) {   // direct: timed phases, host X pieces, test hook
         issue(c.s);
         if (!host_ok) return LBG_ERR_CUDA;
         CK(cudaGetLastError());
@@ -718,9 +771,10 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
         run_prepare(k, p, dCi, nullptr, N, mu, st, false);
         tm.mark(1, s);
         if (wX == 0) {
-            if (!run_assign_host(k, p, X, c.at<float>(p.Xs), dCi, nullptr, N, mu, st, dA)) host_ok = false;
+            if (!run_assign_host(k, p, X, c.at<float>(p.Xs), dCi, nullptr, N, mu, st, dA, o.test_expire_wait))
+                host_ok = false;
         } else {
-            run_assign(k, p, dX, dCi, nullptr, N, mu, st, dA);
+            run_assign(k, p, dX, dCi, nullptr, N, mu, st, dA, 0, -1, o.test_expire_wait);
         }
         tm.mark(2, s);
         run_exact(k, p, dX, nullptr, N, st, dA);
@@ -730,10 +784,10 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
         run_update(k, p, dX, nullptr, N, st, dA, dCi, dCo, false);
         if (o.reseed_empty)
             launch_reseed(k.at<int32_t>(p.off), nullptr, N, L, o.delta_reseed, dCo, st, false, s);
-        if (res) k_step_report<<<1, 1, 0, s>>>(st, res, 1);
+        if (res) LBG_COUNTED k_step_report<<<1, 1, 0, s>>>(st, res, 1);
         tm.mark(4, s);
     };
-    if (o.phase_ms || wX == 0) {   // direct: timed phases, or the pieces of a host X
+    if (o.phase_ms || wX == 0 || o.test_expire_wait) {   // direct: timed phases, host X pieces, test hook
         issue(c.s);
         if (!host_ok) return LBG_ERR_CUDA;
         CK(cudaGetLastError());
@@ -762,8 +816,11 @@ lbg_status lbg_distortion_backward(const float *X, int64_t M, int32_t L, const f
     lbg_status rc = check_dims(M, L, N);
     if (rc != LBG_OK) return rc;
     if (!C || (M > 0 && (!X || !assign))) return LBG_ERR_ARG;
-    if (!isfinite(gD)) return LBG_ERR_ARG;
     const lbg_opts o = resolve(opts);
+    const float *gdev = o.grad_scale_dev;
+    lbg_step_result *res = o.result_dev;
+    if (!gdev && !isfinite(gD)) return LBG_ERR_ARG;
+    if (res && (D || o.phase_ms)) return LBG_ERR_ARG;
     std::lock_guard<std::mutex> lock(g_mu);
     Call c;
     if ((rc = begin(c, o)) != LBG_OK) return rc;
@@ -771,14 +828,16 @@ lbg_status lbg_distortion_backward(const float *X, int64_t M, int32_t L, const f
     const int wA = M > 0 ? where(assign, c.dev) : 1;
     const int wdC = dC ? where(dC, c.dev) : 1, wdX = dX ? where(dX, c.dev) : 1;
     if (wX < 0 || wC < 0 || wA < 0 || wdC < 0 || wdX < 0) return LBG_ERR_ARG;
+    if ((gdev || res) && (wX != 1 || wC != 1 || wA != 1 || wdC != 1 || wdX != 1 ||
+                          (gdev && where(gdev, c.dev) != 1) || (res && where(res, c.dev) != 1)))
+        return LBG_ERR_ARG;
     const bool hostC = wC == 0 || wdC == 0;
     const Plan p = make_plan(M, L, N, 0, wX == 0, wA == 0, hostC, wdX == 0, false);
     if ((rc = ensure_workspace(c, p.total)) != LBG_OK) return rc;
     const size_t cbytes = sizeof(float) * (size_t)N * L;
     DevState *st = c.at<DevState>(p.state);
     DevState h;
-    init_state(h, N);
-    CK(cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, c.s));
+    CK(cudaMemsetAsync(st, 0, sizeof(DevState), c.s));   // no host memory: stays asynchronous
     const float *dXin = X;
     if (M > 0 && wX == 0) {
         CK(cudaMemcpyAsync(c.at<float>(p.Xs), X, sizeof(float) * M * L, cudaMemcpyHostToDevice, c.s));
@@ -801,7 +860,7 @@ lbg_status lbg_distortion_backward(const float *X, int64_t M, int32_t L, const f
     if ((rc = tm.init(o.phase_ms != nullptr)) != LBG_OK) return rc;
     tm.mark(0, c.s);
     tm.mark(1, c.s);
-    launch_grad_x(dXin, M, L, dCin, N, dA, gD, c.at<float>(p.e), gX, st, c.s);
+    launch_grad_x(dXin, M, L, dCin, N, dA, gD, gdev, c.at<float>(p.e), gX, st, c.s);
     tm.mark(2, c.s);
     tm.mark(3, c.s);
     if (M > 0) {
@@ -816,12 +875,20 @@ lbg_status lbg_distortion_backward(const float *X, int64_t M, int32_t L, const f
                            c.s);
             launch_cellsum(dXin, p.M, p.L, c.at<int32_t>(p.perm), off, nullptr, N, p.S,
                            c.at<float>(p.pieces), st, false, c.s);
-            launch_combine_grad(c.at<float>(p.pieces), off, N, L, p.S, dCin, gD, gC, c.s);
+            launch_combine_grad(c.at<float>(p.pieces), off, N, L, p.S, dCin, gD, gdev, gC, c.s);
         } else {
             CK(cudaMemsetAsync(gC, 0, cbytes, c.s));
         }
     }
     tm.mark(4, c.s);
+    if (res) {
+        if (M > 0)
+            LBG_COUNTED k_step_report<<<1, 1, 0, c.s>>>(st, res, 1);
+        else
+            CK(cudaMemsetAsync(res, 0, sizeof(*res), c.s));   // D = 0, LBG_OK
+        CK(cudaGetLastError());
+        return end_async(c);
+    }
     CK(cudaGetLastError());
     if (dC && wdC == 0) CK(cudaMemcpyAsync(dC, gC, cbytes, cudaMemcpyDeviceToHost, c.s));
     if (dX && wdX == 0 && M > 0)
@@ -1180,6 +1247,12 @@ lbg_status lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double del
     const int wX = where(X, c.dev), wC = where(C, c.dev);
     const int wA = assign ? where(assign, c.dev) : 0;
     if (wX < 0 || wC < 0 || wA < 0) return LBG_ERR_ARG;
+    // pass trace buffers: device memory of this device, with room for >= 1 pass
+    if ((o.trace_C || o.trace_assign) &&
+        (o.trace_cap < 1 || (o.trace_C && where(o.trace_C, c.dev) != 1) ||
+         (o.trace_assign && where(o.trace_assign, c.dev) != 1)))
+        return LBG_ERR_ARG;
+    const bool tracing = o.records || o.trace_C || o.trace_assign;
     int stages = 1;
     for (int n = n_init > 0 ? n_init : 1; n < N; n *= 2) ++stages;
     const int64_t max_total = (int64_t)stages * o.max_passes;
@@ -1216,6 +1289,7 @@ lbg_status lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double del
     auto pass = [&](cudaStream_t sst) {
         Call cs = c;
         cs.s = sst;
+        if (tracing) launch_trace_begin(st, Ccur, N, L, o.trace_C, o.trace_cap, sst);
         run_prepare(cs, p, Ccur, n_dev, N, mu, st);
         run_assign(cs, p, dX, Ccur, n_dev, N, mu, st, dA);
         run_exact(cs, p, dX, n_dev, N, st, dA);
@@ -1228,6 +1302,9 @@ lbg_status lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double del
             launch_reseed(cs.at<int32_t>(p.off), n_dev, N, L, delta, Ccur, st, true, sst);
         launch_split(Ccur, Calt, N, L, delta, o.split_multiplicative != 0, st, sst);
         launch_advance(Calt, Ccur, N, L, st, sst);
+        if (tracing)
+            launch_trace_end(st, dA, M, cs.at<int32_t>(p.counts), o.records ? rec : nullptr, max_rec,
+                             o.trace_assign, o.trace_cap, sst);
     };
     GraphPass gp;
     gp.build(c.s, pass);

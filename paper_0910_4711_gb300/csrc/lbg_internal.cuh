@@ -17,7 +17,7 @@ constexpr int NMAX = 8192;    // = LBG_MAX_CODEBOOK
 // Cell-table build: rows are cut into at most HIST_CHUNKS_MAX contiguous
 // chunks (one CTA each); the segmented centroid sums cut the cell-sorted
 // row order into pieces of SEG rows (one warp each).
-constexpr int HIST_CHUNKS_MAX = 304;   // 2 x 152 SMs
+constexpr int HIST_CHUNKS_MAX = 304;   // cap; plans use min(this, 2 x SMs)
 // The exact re-scoring kernel stages the original codebook in chunks of
 // EXACT_SW codevectors, stored k-major inside a chunk.
 constexpr int EXACT_SW = 128;
@@ -52,12 +52,17 @@ struct DevState {
     uint32_t done_ctr;    // CTAs done in a fused kernel (its last CTA finishes and resets it)
     double D;             // total distortion of the last pass
     double D_prev;        // distortion of the previous pass of the stage
+    uint64_t t_pass0;     // %globaltimer at the start of the traced pass (lbg_train trace)
+    int32_t trace_on;     // 1 while a traced pass of lbg_train is in progress
+    int32_t pad0;
 };
 
 // Device pass record (mirrors lbg_pass_record).
 struct PassRecord {
     int32_t stage_n, pass, action, n_exact;
     double D;
+    int32_t n_empty;      // cells with no row in the pass's allocation
+    float ms;             // device time of the pass (%globaltimer)
 };
 
 // One problem of a batched call (device-resident descriptor; every pointer
@@ -210,6 +215,15 @@ __device__ __forceinline__ bool mbar_wait_bounded_sleep(uint64_t *bar, uint32_t 
 
 __device__ __forceinline__ void flag_error(DevState *st, uint32_t bits) { atomicOr(&st->err, bits); }
 
+// ------------------------------------------------------------ host helpers
+// Kernel launches issued by the library, a diagnostic count read through
+// lbg_launch_count(); a replayed CUDA graph adds the kernels it holds.  Every
+// launch site is written `LBG_COUNTED kernel<<<...>>>(...)`.
+void note_launch();
+#define LBG_COUNTED ::lbg::note_launch(),
+// Multiprocessor count of the current device (queried once per device).
+int num_sms();
+
 // ------------------------------------------------------------ launchers
 // Codebook preparation (k_assign.cu).
 void launch_codebook_mean(const float *C, int N, int L, float *mu, cudaStream_t s);
@@ -220,10 +234,12 @@ void launch_prep(const float *C, int N_alloc, const int32_t *n_dev, int n_host, 
                  const float *mu, float *Cp, float *kn, float *CT, int NP, DevState *st,
                  cudaStream_t s);
 // Nearest codevector of rows [m_lo, M) of X (row indices, assign, e and flags
-// stay global).
+// stay global).  expire != 0 (test hook): every CTA's first bounded wait gives
+// up at once (the time-out path: drain, report LBG_ERR_TIMEOUT, no row written).
 void launch_assign(const float *X, int64_t M, int L, int Lp, const float *Cp, const float *kn,
                    const int32_t *n_dev, int n_host, const float *mu, const float *C, DevState *st,
-                   int32_t *assign, float *e, int32_t *flags, cudaStream_t s, int64_t m_lo = 0);
+                   int32_t *assign, float *e, int32_t *flags, cudaStream_t s, int64_t m_lo = 0,
+                   int expire = 0);
 void launch_exact(const float *X, int L, int Lp, const float *CT, const int32_t *n_dev, int n_host,
                   DevState *st, const int32_t *flags, int32_t *assign, float *e, int64_t M,
                   cudaStream_t s);
@@ -301,17 +317,25 @@ void launch_b_prep(const BatchSet *sets, int S, const int32_t *pre, int total_bl
                    cudaStream_t s);
 // Persistent batched nearest-codevector launch over (problem, row tile) work
 // items; tile_rows 64 or 128 (pre_tiles counts tiles of that height), grid =
-// 152 x ctas_per_sm CTAs.
+// SMs x ctas_per_sm CTAs.
 void launch_b_assign(const BatchSet *sets, int S, const int64_t *pre_tiles, int64_t total_tiles,
                      int L, int Lp, int *counter, int tile_rows, int ctas_per_sm, cudaStream_t s);
 void launch_b_exact(const BatchSet *sets, int S, int L, int Lp, int max_ngroups, cudaStream_t s);
 void launch_b_reset(const BatchSet *sets, int S, int *counter, cudaStream_t s);
 
+// Backward at a fixed cell table; the upstream gradient is gD, or *gD_dev
+// (device) when gD_dev is not null.
 void launch_grad_x(const float *X, int64_t M, int L, const float *C, int N, const int32_t *assign,
-                   float gD, float *e, float *dX, DevState *st, cudaStream_t s);
+                   float gD, const float *gD_dev, float *e, float *dX, DevState *st, cudaStream_t s);
 void launch_combine_grad(const float *pieces, const int32_t *off, int N, int L, int64_t S,
-                         const float *C, float gD, float *dC, cudaStream_t s);
+                         const float *C, float gD, const float *gD_dev, float *dC, cudaStream_t s);
 void launch_advance(const float *C_alt, float *C_cur, int N_alloc, int L, DevState *st,
                     cudaStream_t s);
+// Pass trace of lbg_train: start (stamp, codebook of the pass) and end (cell
+// table, empty cells and device time into the pass record).
+void launch_trace_begin(DevState *st, const float *C, int N, int L, float *trace_C, int cap,
+                        cudaStream_t s);
+void launch_trace_end(DevState *st, const int32_t *assign, int64_t M, const int32_t *counts,
+                      PassRecord *rec, int max_rec, int32_t *trace_A, int cap, cudaStream_t s);
 
 }  // namespace lbg

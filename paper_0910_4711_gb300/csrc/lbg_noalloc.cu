@@ -148,7 +148,7 @@ extern "C" lbg_status vq_encode_noalloc(const float *X, int64_t M, int32_t L, co
     int32_t *flags = reinterpret_cast<int32_t *>(base + OFF_FLAGS);
     const int Lp = round_up(L, 4);
 
-    k_noalloc_begin<<<1, 32, 0, s>>>(st, dtot, N);
+    LBG_COUNTED k_noalloc_begin<<<1, 32, 0, s>>>(st, dtot, N);
     launch_codebook_mean(C, N, L, mu, s);
     launch_prep(C, N, nullptr, N, L, Lp, mu, Cp, kn, CT, NA_NP, st, s);
     for (int64_t r0 = 0; r0 < M; r0 += NA_ROWS) {
@@ -166,10 +166,10 @@ extern "C" lbg_status vq_encode_noalloc(const float *X, int64_t M, int32_t L, co
         const int CH = (int)((mc + R - 1) / R);
         launch_hist(ic, e, mc, R, CH, nullptr, N, false, nullptr, dpart, st, false, s);
         launch_ctl(dpart, CH, st, MODE_STEP, 0.0, 1, N, nullptr, 0, s);
-        k_noalloc_accum<<<1, 32, 0, s>>>(st, dtot);
+        LBG_COUNTED k_noalloc_accum<<<1, 32, 0, s>>>(st, dtot);
     }
     NaResult *res = reinterpret_cast<NaResult *>(base + OFF_DPART);   // dpart is free again
-    k_noalloc_end<<<1, 32, 0, s>>>(st, dtot, res);
+    LBG_COUNTED k_noalloc_end<<<1, 32, 0, s>>>(st, dtot, res);
     NaResult h;
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(&h, res, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_status_strings_and_version(lib):
-    assert lib.lbg_version() == 1
+    assert lib.lbg_version() == 2
     for s in (0, 1, -1, -2, -3, -4, -5, -6, -7):
         assert lib.lbg_status_string(s)
 
@@ -101,15 +101,21 @@ def test_struct_layout_matches_header(tmp_path):
         '  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(lbg_opts), offsetof(lbg_opts, tune_report),\n'
         "         offsetof(lbg_opts, result_dev), sizeof(lbg_step_result),\n"
         "         offsetof(lbg_step_result, n_exact), offsetof(lbg_step_result, status));\n"
+        '  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(lbg_pass_record),\n'
+        "         offsetof(lbg_pass_record, D), offsetof(lbg_pass_record, n_empty),\n"
+        "         offsetof(lbg_pass_record, ms), offsetof(lbg_opts, trace_C),\n"
+        "         offsetof(lbg_opts, trace_cap), offsetof(lbg_opts, test_expire_wait));\n"
         "  return 0; }\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
                    check=True)
     got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
                                           text=True).stdout.split()]
-    O = _binding.Opts
+    O, R = _binding.Opts, _binding.PassRecord
     assert got[:3] == [ctypes.sizeof(O), O.tune_report.offset, O.result_dev.offset]
-    assert got[3:] == [_binding.STEP_RESULT_BYTES, 8, 12]
+    assert got[3:6] == [_binding.STEP_RESULT_BYTES, 8, 12]
+    assert got[6:] == [ctypes.sizeof(R), R.D.offset, R.n_empty.offset, R.ms.offset, O.trace_C.offset,
+                       O.trace_cap.offset, O.test_expire_wait.offset]
 
 
 def test_async_calls_reject_host_outs(lib):
@@ -174,7 +180,7 @@ def test_plain_c_program_links_and_calls(lib, tmp_path):
         "int main(void) {\n"
         "  float X[8 * 4] = {0}, C[3 * 4];\n"
         "  int32_t idx[8];\n"
-        "  if (lbg_version() != 1) return 1;\n"
+        "  if (lbg_version() != 2) return 1;\n"
         '  if (strcmp(lbg_status_string(LBG_ERR_NOT_POW2), "codebook size is not a power of 2")) return 2;\n'
         "  if (lbg_train(X, 8, 4, 3, 0.01, 1e-3, C, 0, NULL, NULL, NULL) != LBG_ERR_NOT_POW2) return 3;\n"
         "  if (vq_encode(X, 8, 4, NULL, 2, idx, NULL, NULL, NULL) != LBG_ERR_ARG) return 4;\n"

@@ -42,7 +42,8 @@ torch.from_numpy = FT
 torch.empty = lambda shape, dtype=None, device=None: FT(np.zeros(shape, dtype or np.float32))
 torch.empty_like = lambda t: FT(np.zeros_like(t.a))
 torch.cuda = types.SimpleNamespace(
-    is_available=lambda: True, current_device=lambda: 0, current_stream=lambda *a: None,
+    is_available=lambda: True, current_device=lambda: 0,
+    current_stream=lambda *a: types.SimpleNamespace(cuda_stream=0),
     synchronize=lambda: None, Event=Event,
     nvtx=types.SimpleNamespace(range_push=lambda s: None, range_pop=lambda: None))
 sys.modules["torch"] = torch
@@ -61,9 +62,15 @@ class Train:
         return [2] + [9] * 12 + [1]
 
 lbg.lbg_train = lambda *a, **k: Train
-lbg.lbg_lloyd_step = lambda *a, **k: types.SimpleNamespace(
-    D=1.0e9, n_exact=1248, phase_ms={"prep": 0.023, "assign": 0.506, "exact": 0.048,
-                                     "update": 0.072, "total": 0.649})
+LAUNCHES = [0]
+def step(*a, **k):   # each step: ten kernels, as the library would count them
+    LAUNCHES[0] += 10
+    return types.SimpleNamespace(
+        D=1.0e9, n_exact=1248, phase_ms={"prep": 0.023, "assign": 0.506, "exact": 0.048,
+                                         "update": 0.072, "total": 0.649})
+lbg.lbg_lloyd_step = step
+lbg.launch_count = lambda: LAUNCHES[0]
+lbg.measure_fp32_peak = lambda stream=None: (80.0, 152)
 lbg.step_result_buffer = lambda *a, **k: FT(np.zeros(2))
 lbg.read_step_result = lambda buf: (1.0e9, 1248, 0)
 if THROTTLE:   # the first timed region reports a thermal slowdown, the next one none
@@ -78,7 +85,7 @@ if THROTTLE:   # the first timed region reports a thermal slowdown, the next one
             return {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": bad}
     bench.ClockSampler = Clocks
 sys.argv = ["bench.py", "--steps", "2", "--warmup", "3", "--no-grad", "--no-batched",
-            "--no-small", "--cpu-seconds", "0.2"]
+            "--no-small", "--no-large", "--no-after-split", "--cpu-seconds", "0.2"]
 sys.exit(bench.run_ours(bench.parse()))
 '''
 
@@ -122,3 +129,7 @@ def test_gpu_arm_json_line():
     assert line["gpu_launches"] == 20
     assert "reasons" in line["clocks"] and "remeasured_after" not in line["clocks"]
     assert line["other_precision"]["precision"] == "fp32"
+    assert line["fp32_peak"] == {"tflops": 80.0, "sms": 152, "how": line["fp32_peak"]["how"]}
+    o = line["other_precision"]["roofline"]
+    assert o["bound"] == "alu" and o["peak"] == 80.0 and o["frac"] == o["achieved"] / 80.0
+    assert line["ms_per_step"] == 0.625 and line["ms_per_step_mean"] == 0.625

@@ -113,7 +113,16 @@ def test_small_leg_reports_whole_run_comparison():
 
     class FakeLib:
         @staticmethod
-        def lbg_train(X, N, delta, theta, precision="fp32"):
+        def lbg_train(X, N, delta, theta, precision="fp32", trace=0, trace_passes=0):
+            if trace_passes:   # a design traced pass by pass from the oracle's own steps
+                from test_trajectory_checker import traced_design
+                recs, pc, pa, C, a, D = traced_design(X.a, N, delta, theta)
+
+                class RT:
+                    records = [dict(r, ms=0.01) for r in recs]
+                    pass_C, pass_assign = T(pc), T(pa)
+                RT.C, RT.assign, RT.D = T(C), T(a), D
+                return RT
             t = oracle.lbg_train(X.a, N, delta, theta)
 
             class R:
@@ -139,6 +148,9 @@ def test_small_leg_reports_whole_run_comparison():
         assert v["D_rel_diff"] == 0.0
         assert v["codebook_max_rel_diff"] < 1e-6
         assert isinstance(v["near_tie_rows_in_oracle_run"], int)
+        pp = out[prec]["per_pass_vs_oracle"]
+        assert pp["passes_checked"] > 4 and pp["assign_rows_outside_tolerance"] == 0
+        assert pp["stop_decisions_wrong"] == 0 and pp["final_state_is_last_pass"]
 
 
 def test_throttle_rule():

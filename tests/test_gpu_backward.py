@@ -115,6 +115,37 @@ def test_autograd_function(lbg, gmm_problem):
     assert float(distortion(Xd, C2)) < float(D.detach())
 
 
+def test_autograd_needs_no_host_sync(lbg, gmm_problem):
+    """Forward and backward of the autograd function enqueue only: no torch operation on the
+    way synchronises with the device (the upstream gradient stays a device scalar), and the
+    results are those of the synchronous calls, scaled by the upstream gradient."""
+    from paper_0910_4711_gb300.autograd import distortion
+    X, Xd, C, idx = gmm_problem
+    Xg = Xd.clone().requires_grad_(True)
+    Cg = C.clone().requires_grad_(True)
+    torch.cuda.synchronize()
+    torch.cuda.set_sync_debug_mode("error")
+    try:
+        D = distortion(Xg, Cg)
+        (3.0 * D).backward()
+    finally:
+        torch.cuda.set_sync_debug_mode(0)
+    D2, dC, dX, _ = lbg.distortion_backward(Xd, C, idx, grad_D=3.0)
+    assert float(D.detach()) == D2
+    assert torch.equal(Cg.grad, dC) and torch.equal(Xg.grad, dX)
+
+
+def test_backward_async_report(lbg, gmm_problem):
+    X, Xd, C, idx = gmm_problem
+    buf = lbg.step_result_buffer()
+    g = torch.tensor([0.5], device="cuda")
+    _, dC, dX, _ = lbg.distortion_backward(Xd, C, idx, grad_scale=g, result_out=buf)
+    D, n_exact, status = lbg.read_step_result(buf)
+    D2, dC2, dX2, _ = lbg.distortion_backward(Xd, C, idx, grad_D=0.5)
+    assert status == 0 and D == D2
+    assert torch.equal(dC, dC2) and torch.equal(dX, dX2)
+
+
 def test_backward_empty_rows(lbg):
     C = torch.randn(8, 16, device="cuda")
     D, dC, dX, _ = lbg.distortion_backward(torch.zeros((0, 16), device="cuda"), C,
