@@ -873,28 +873,30 @@ def large_leg(lbg, synth, torch, inputs, with_oracle=True):
 def after_split_leg(lbg, torch, X, N, args, flush, stream, dist):
     """The step against the codebook right after the design's last split (pass 0 of the
     N-entry stage: every codevector has a twin at 2 delta, the least converged codebook and
-    the one with the most near-ties), in the headline precision."""
+    the one with the most near-ties), in both precisions."""
     half = lbg.lbg_train(X, N // 2, 0.01, 1e-3, precision=args.precision).C
     Cs = lbg.lbg_train(X, N, 0.01, 1e-3, C_init=half, max_passes=1, precision=args.precision).C
     C_out = torch.empty_like(Cs)
     A = torch.empty(X.shape[0], dtype=torch.int32, device="cuda")
-    for _ in range(3):
-        flush.zero_()
-        lbg.lbg_lloyd_step(X, Cs, C_out=C_out, assign_out=A, precision=args.precision)
-    per, nex = [], None
-    for _ in range(max(3, min(args.steps, 10))):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        r = lbg.lbg_lloyd_step(X, Cs, C_out=C_out, assign_out=A, precision=args.precision, phase_ms=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        per.append(e0.elapsed_time(e1))
-        nex = r.n_exact
-    ms = max_over_ranks(dist, statistics.median(per))
-    return {"codebook": f"N={N}: the N/2 design split once (pass 0 of the last stage)",
-            "ms_per_step": ms, "value": X.shape[0] * N / (ms / 1e3), "unit": UNIT,
-            "exact_rows_per_step": nex, "phase_ms": r.phase_ms}
+    out = {"codebook": f"N={N}: the N/2 design split once (pass 0 of the last stage)"}
+    for prec in (args.precision, "fp32" if args.precision == "bf16" else "bf16"):
+        for _ in range(3):
+            flush.zero_()
+            lbg.lbg_lloyd_step(X, Cs, C_out=C_out, assign_out=A, precision=prec)
+        per, nex = [], None
+        for _ in range(max(3, min(args.steps, 10))):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = lbg.lbg_lloyd_step(X, Cs, C_out=C_out, assign_out=A, precision=prec, phase_ms=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            per.append(e0.elapsed_time(e1))
+            nex = r.n_exact
+        ms = max_over_ranks(dist, statistics.median(per))
+        out[prec] = {"ms_per_step": ms, "value": X.shape[0] * N / (ms / 1e3), "unit": UNIT,
+                     "exact_rows_per_step": nex, "phase_ms": r.phase_ms}
+    return out
 
 
 def main():

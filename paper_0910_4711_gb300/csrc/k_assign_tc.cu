@@ -27,31 +27,39 @@
 // sum |x~_l c'_l| <= ||x~||^2 + ||c~||^2 this gives
 //     |v_n - (X2 + f_n - k'_n)| <= tau (2 ||x~||^2 + 2 ||c~_n||^2) + u ||c~_n||^2 + E,
 // E = ||x~|| rho, and with k'_n = (2 tau + 2^-23) ||c~_n||^2, R' = 2 tau ||x~||^2
-// the certificate of k_assign.cu applies: V2 - V1 > 2R' + 2k'_i1 + 2E +
-// 4 eta (g1 + eta), plus 2^-17 (|V1| + |V2|) + 2^-23 (|V1| + 2|V2|) for the
-// epilogue below.  A second certificate needs no bound on the winner's
-// approximation.  With X2 + f_n = ||x~ - c~_n||^2 + (X2 - ||x~||^2) and
+// the certificate of k_assign.cu applies, over groups: the columns are taken
+// in groups of eight consecutive codevectors, V1 is the smallest value and V2
+// the smallest value outside V1's group.  The group's member with the
+// smallest FP32 direct-form distance is the candidate ii (it must beat every
+// other member by more than the direct form's rounding bound, else the row is
+// not certified).  The member j that produced V1 has ||x~ - c~_j||^2 <= V1 +
+// 2k'_j + R' + E (+ epilogue and X2 terms) and ii is not farther than j, while
+// every codevector outside the group has ||x~ - c~_n||^2 >= V2 - R' - E, so
+// V2 - V1 > 2R' + 2k'_grp + 2E + 4 eta (g1 + eta) + 2^-19 (|V1| + |V2|), with
+// k'_grp the group's largest k' and the last term for the epilogue's index
+// packing, proves ii the exact argmin.  A second certificate needs no bound
+// on V1's member.  With X2 + f_n = ||x~ - c~_n||^2 + (X2 - ||x~||^2) and
 // k'_n >= 2 tau ||c~_n||^2 + u ||c~_n||^2, the bound gives
 //     ||x~ - c~_n||^2 >= v_n - R' - E - |X2 - ||x~||^2|,
-// and every codevector outside the best pair has v_n >= V2 (V2 is the second
-// smallest value), so ||x - c_n||^2 >= (sqrt(V2 - R' - E - P - (L+2) u ||x~||^2)
-// - eta)^2, P the epilogue term above.  The chosen member's FP32 direct-form
-// distance d gives ||x - c_ii||^2 <= d (1 + (L+4) u); when the lower bound
-// exceeds that, ii is the exact argmin.  A row is certified when either
-// certificate holds.
+// and every codevector outside the best group has v_n >= V2, so
+// ||x - c_n||^2 >= (sqrt(V2 - R' - E - P - (L+2) u ||x~||^2) - eta)^2, P the
+// packing term.  The winner's FP32 direct-form distance d gives ||x - c_ii||^2
+// <= d (1 + (L+4) u); when the lower bound exceeds that, ii is the exact
+// argmin.  A row is certified when either certificate holds.  The two
+// children of a split (2i, 2i + 1) share a group, so right after a split a
+// row's nearest pair of twins is resolved by their exact distances and V2
+// comes from the next parent, not from the twin.
 //
 // Epilogue.  Each thread owns one row and one half (72 columns) of every
-// tile, taken as 36 column pairs (a, b).  lo = min(a, b) gets the pair index
-// (6 bits) in its low mantissa bits (one LOP3; the value moves by less than
-// 2^-17 of it); hi = (a + b) - lo is formed on the otherwise idle FMA pipe
-// (within 2^-23 (|V1| + 2|hi|) of max(a, b)); then c2 = min(c2, max(c1, lo),
-// hi) (three-input min) and c1 = min(c1, lo).  That is five ALU operations
-// per pair for the running top-2 of values with the index of the best pair;
-// a per-tile compare records the tile, and the two halves of a row are
-// merged through shared memory at the end.  Which member of the best pair is
-// the minimum is decided from the exact FP32 distances of both, when they
-// differ by more than the direct form's rounding bound (else the row goes to
-// the fallback); a certified row keeps that distance as e(m).
+// tile, taken as 9 groups of 8 columns.  The group minimum (three-input
+// mins) gets the group index (4 bits) in its low mantissa bits (one LOP3; the
+// value moves by less than 2^-19 of it); then c2 = min(c2, max(c1, k)) and
+// c1 = min(c1, k): eight ALU operations per group, one per value, for the
+// running top-2 of group minima with the index of the best group; a per-tile
+// compare records the tile, and the two halves of a row are merged through
+// shared memory at the end.  The tail scores the best group's eight members
+// exactly (four per half) and a certified row keeps the winner's FP32
+// direct-form distance as e(m).
 // Tiles whose x~ are not BF16-exact, or codebooks whose pieces do not add up
 // exactly, send their rows to the exact FP32 fallback.
 //
@@ -70,11 +78,12 @@
 //                 j = 2 t + a (tile t, accumulator a of 128 rows) accumulates
 //                 into slot j % 3 of a ring of three 144-column accumulators;
 //   warps 2..17   epilogue, one (row, column half) per thread: tcgen05.ld of
-//                 its 72 values per job, running top-2 with the pair index
-//                 (two interleaved chains); after the last tile the two halves
-//                 of each row merge, compute the exact distances of the best
-//                 pair's two codevectors, and the half-0 thread runs the
-//                 certificate, writes the index and e(m) or flags the row.
+//                 its 72 values per job, running top-2 of group minima with the
+//                 group index (two interleaved chains); after the last tile the
+//                 two halves of each row merge, compute the exact distances of
+//                 the best group's eight codevectors, and the half-0 thread
+//                 runs the certificate, writes the index and e(m) or flags the
+//                 row.
 // Every mbarrier wait is bounded (2 s); on a time-out the CTA stops issuing,
 // reports LBG_ERR_TIMEOUT, waits for its own copies and frees its TMEM.
 #include "lbg_internal.cuh"
@@ -95,11 +104,13 @@ constexpr int TC_NT = 144;                     // codevectors per tile (MMA N): 
                                                // runs epilogue warps (N = 128 issued about one
                                                // MMA per 86 cycles for 64 cycles of work)
 constexpr int TC_HALF = TC_NT / 2;             // columns per epilogue thread per tile
-constexpr int TC_PAIRS = TC_HALF / 2;          // column pairs per epilogue thread per tile
-constexpr int TC_JBITS = 6;                    // bits of the in-half pair index (36 pairs)
-constexpr float TC_PACK = 7.62939453125e-6f;   // 2^(TC_JBITS - 23): packing changes a value
+constexpr int TC_GRP = 8;                      // columns per group: the running top-2 is over group
+                                               // minima; a group holds the four split pairs
+                                               // (children 2i, 2i + 1) of four parents
+constexpr int TC_GROUPS = TC_HALF / TC_GRP;    // groups per epilogue thread per tile (9)
+constexpr int TC_JBITS = 4;                    // bits of the in-half group index
+constexpr float TC_PACK = 1.9073486328125e-6f; // 2^(TC_JBITS - 23): packing changes a value
                                                // by less than this fraction of it
-constexpr float TC_HIERR = 1.1920928955078125e-7f;   // 2^-23: bound of the FMA-pipe pair maximum
 constexpr float TC_EVAL = 9.5367431640625e-7f;   // 2^-20: FP32 evaluation of the second certificate
 constexpr int TC_STAGES = 3;
 constexpr int TC_EPI_WARPS = 8 * TC_NACC;      // 16: (accumulator, lane quarter, half)
@@ -113,7 +124,8 @@ constexpr int TC_NCH = 2;                      // independent min-chains of the 
                                                // epilogue warps of the sub-partition hide the
                                                // chains' latency; fewer chains, less bookkeeping)
 static_assert(TC_A_COL + 2 * ((TC_LMAX + 16) / 2) <= TC_TMEM_COLS, "accumulators + A exceed TMEM");
-static_assert(TC_HALF == 72 && TC_PAIRS <= (1 << TC_JBITS), "epilogue loads 64 + 8 columns");
+static_assert(TC_HALF == 72 && TC_HALF % TC_GRP == 0 && TC_GROUPS <= (1 << TC_JBITS),
+              "epilogue loads 64 + 8 columns in whole groups");
 
 constexpr float U32 = 5.9604644775390625e-8f;   // 2^-24
 constexpr float SLOP = 1.0000305175781250f;     // 1 + 2^-15
@@ -187,30 +199,29 @@ __device__ __forceinline__ float fmin3(float a, float b, float c)
     return d;
 }
 
-// One epilogue step for the column pair P = (2P, 2P+1) of the thread's half:
-// lo = min(a, b) carries the pair index in its JBITS low mantissa bits (one
-// LOP3; `keymask` = ~(2^JBITS - 1) comes in as a kernel argument so that the
-// mask stays in a register and the immediate is the index); hi = (a + b) - lo
-// runs on the FMA pipe (within 2^-24 (|lo| + 2|hi|) of max(a, b)); then the
-// running top-2 of chain P % 4.
+// One epilogue step for group G (columns 8G .. 8G + 7 of the thread's half):
+// its minimum (four three-input / two-input mins) carries the group index in
+// its JBITS low mantissa bits (one LOP3; `keymask` = ~(2^JBITS - 1) comes in as
+// a kernel argument so that the mask stays in a register and the immediate is
+// the index); then the running top-2 of group minima of chain G % NCH:
+// c2 = min(c2, max(c1, k)), c1 = min(c1, k).  Eight ALU operations per group.
 template <int P>
-struct PairSteps {
+struct GroupSteps {
     __device__ __forceinline__ static void run(const float *v, float *c1, float *c2, int keymask)
     {
-        PairSteps<P - 1>::run(v, c1, c2, keymask);
+        GroupSteps<P - 1>::run(v, c1, c2, keymask);
         constexpr int j = P - 1, q = j % TC_NCH;
-        const float a = v[2 * j], b = v[2 * j + 1];
-        const float lo = fminf(a, b);
-        const float hi = __fsub_rn(__fadd_rn(a, b), lo);
+        const float *g = v + TC_GRP * j;
+        const float lo = fmin3(fmin3(g[0], g[1], g[2]), fmin3(g[3], g[4], g[5]), fminf(g[6], g[7]));
         int kb;
         asm("lop3.b32 %0, %1, %2, %3, 0xEA;" : "=r"(kb) : "r"(__float_as_int(lo)), "r"(keymask), "n"(j));
         const float k = __int_as_float(kb);
-        c2[q] = fmin3(c2[q], fmaxf(c1[q], k), hi);
+        c2[q] = fminf(c2[q], fmaxf(c1[q], k));
         c1[q] = fminf(c1[q], k);
     }
 };
 template <>
-struct PairSteps<0> {
+struct GroupSteps<0> {
     __device__ __forceinline__ static void run(const float *, float *, float *, int) {}
 };
 
@@ -549,7 +560,9 @@ struct TcSmem {
             int i1[2][TC_ROWS];
         } m;
         struct {
-            float d[2][TC_ROWS], k[2][TC_ROWS];     // exact distances (tail); ||x~||^2 halves (A write)
+            float d[TC_GRP][TC_ROWS];               // exact distances of the best group (tail);
+                                                    // d[0..1]: ||x~||^2 halves (A write)
+            float k[2][TC_ROWS];                    // the halves' largest k' of the group (tail)
         } r;
     };
 };
@@ -618,8 +631,9 @@ __device__ __forceinline__ float tc_write_a(const __nv_bfloat16 *XS, int L, bool
 
 // The epilogue of one row tile: for each codebook tile t, job j0 + 2t + acc
 // (accumulator slot (j0 + 2t + acc) % 3); the thread's 72 values per job go
-// through the pair top-2; returns the merged (V1, V2, pair index) of the
-// thread's half.  hook(t) runs after job t in every epilogue warp (it may use
+// through the group top-2; returns the merged (V1, V2, group's first column)
+// of the thread's half: V1 the smallest group minimum, V2 the second smallest
+// (the smallest value outside V1's group).  hook(t) runs after job t in every epilogue warp (it may use
 // named barriers: after a time-out, sh.abort, the jobs are skipped but the
 // hooks still run).
 struct NoHook {
@@ -671,19 +685,19 @@ __device__ __forceinline__ void tc_jobs(TcSmem &sh, uint32_t tmem, int warp, int
         float s1[NCH];
 #pragma unroll
         for (int q = 0; q < NCH; ++q) s1[q] = c1[q];
-        PairSteps<TC_PAIRS>::run(v, c1, c2, keymask);
+        GroupSteps<TC_GROUPS>::run(v, c1, c2, keymask);
 #pragma unroll
         for (int q = 0; q < NCH; ++q) cg[q] = c1[q] < s1[q] ? t : cg[q];
         hook(t);
     }
-    // merge the chains; i1 is the first column of the minimum's pair:
-    // tile * TC_NT + half * TC_HALF + 2 * (the low bits)
+    // merge the chains; i1 is the first column of the minimum's group:
+    // tile * TC_NT + half * TC_HALF + TC_GRP * (the low bits)
     V1 = c1[0];
     V2 = c2[0];
-    i1 = cg[0] * TC_NT + half * TC_HALF + 2 * (__float_as_int(c1[0]) & JMASK);
+    i1 = cg[0] * TC_NT + half * TC_HALF + TC_GRP * (__float_as_int(c1[0]) & JMASK);
 #pragma unroll
     for (int q = 1; q < NCH; ++q) {
-        const int iq = cg[q] * TC_NT + half * TC_HALF + 2 * (__float_as_int(c1[q]) & JMASK);
+        const int iq = cg[q] * TC_NT + half * TC_HALF + TC_GRP * (__float_as_int(c1[q]) & JMASK);
         V2 = fminf(fminf(V2, c2[q]), fmaxf(V1, c1[q]));
         const bool take = c1[q] < V1 || (c1[q] == V1 && iq < i1);
         V1 = take ? c1[q] : V1;
@@ -692,17 +706,18 @@ __device__ __forceinline__ void tc_jobs(TcSmem &sh, uint32_t tmem, int warp, int
 }
 
 // The end of a row tile (all 16 epilogue warps; uses named barriers 1 and 2):
-// the two halves of a row merge their top-2 in a fixed order; the minimum is
-// one of the pair (i1, i1 + 1), and each half computes the exact FP32
-// distance of one member.  With L a multiple of 4 the warp does it
+// the two halves of a row merge their top-2 in a fixed order; the candidate
+// is a member of the group i1 .. i1 + 7, and each half computes the exact
+// FP32 distances of four members.  With L a multiple of 4 the warp does it
 // cooperatively: a half-warp per row, a float4 of x and of the codevector per
 // lane (coalesced reads of X and C), each lane sums its four terms
 // (x_l - c_l)^2 in order, and a butterfly over the 16 lanes of each half-warp
 // reduces the 16 rows' partial sums at once (a fixed tree: 15 shuffles per
 // lane); the owner lane of each row takes its sum.  The half-0 thread then
-// takes the smaller distance when the two differ by more than the rounding
-// bound of the FP32 sum, runs the certificate, and writes a(m), e(m) or flags
-// the row.  `usable` = the tile's x~ and the codebook split are exact.
+// takes the member with the smallest distance when it beats the other seven
+// by more than the rounding bound of the FP32 sums, runs the certificates,
+// and writes a(m), e(m) or flags the row.  `usable` = the tile's x~ and the
+// codebook split are exact.
 template <int LK>
 __device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc, int half, int rr,
                                         int64_t m0, const float *__restrict__ X, int64_t M, int L, int N,
@@ -728,106 +743,116 @@ __device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc,
     }
     named_sync(2, 32 * TC_EPI_WARPS);   // merge inputs read: sh.r may now overwrite sh.m
     const bool usable = m < M && !sh.abort && usable_tile && i1 >= 0 && i1 < N && V1 < INFINITY;
-    const int cand = i1 + half;
-    const int ccand = (usable && cand < N) ? cand : -1;
-    const float kc = ccand >= 0 ? __ldg(kn + ccand) : 0.f;
-    float dc = INFINITY;
-    if ((L & 3) == 0 && ((reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(X)) & 15u) == 0) {
-        const int rq = lane & 15, sub = lane >> 4;
-        const int64_t mrow0 = m0 + 128 * acc + 32 * (warp & 3);   // row of lane 0
-        float p[16];
+    // the best group is codevectors i1 .. i1 + 7; this half scores members i1 + 4 half + g
+    float kmax = 0.f;
+    const bool coop = (L & 3) == 0 && ((reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(X)) & 15u) == 0;
+#pragma unroll 1
+    for (int g = 0; g < TC_GRP / 2; ++g) {
+        const int cand = i1 + (TC_GRP / 2) * half + g;
+        const int ccand = (usable && cand < N) ? cand : -1;
+        if (ccand >= 0) kmax = fmaxf(kmax, __ldg(kn + ccand));
+        float dc = INFINITY;
+        if (coop) {
+            const int rq = lane & 15, sub = lane >> 4;
+            const int64_t mrow0 = m0 + 128 * acc + 32 * (warp & 3);   // row of lane 0
+            float p[16];
 #pragma unroll
-        for (int bt = 0; bt < 2; ++bt) {   // two batches of 8 rows
-            int crs[8];
+            for (int bt = 0; bt < 4; ++bt) {   // four batches of 4 rows
+                int crs[4];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) crs[k] = __shfl_sync(0xffffffffu, ccand, 2 * (8 * bt + k) + sub);
-            float4 c4[8], x4[8];
+                for (int k = 0; k < 4; ++k) crs[k] = __shfl_sync(0xffffffffu, ccand, 2 * (4 * bt + k) + sub);
+                float4 c4[4], x4[4];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const bool on = crs[k] >= 0 && 4 * rq < L;
-                const int64_t mr = mrow0 + 2 * (8 * bt + k) + sub;
-                c4[k] = on ? __ldg(reinterpret_cast<const float4 *>(C + (size_t)crs[k] * L) + rq)
-                           : make_float4(0.f, 0.f, 0.f, 0.f);
-                x4[k] = on ? __ldg(reinterpret_cast<const float4 *>(X + mr * L) + rq)
-                           : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+                for (int k = 0; k < 4; ++k) {
+                    const bool on = crs[k] >= 0 && 4 * rq < L;
+                    const int64_t mr = mrow0 + 2 * (4 * bt + k) + sub;
+                    c4[k] = on ? __ldg(reinterpret_cast<const float4 *>(C + (size_t)crs[k] * L) + rq)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+                    x4[k] = on ? __ldg(reinterpret_cast<const float4 *>(X + mr * L) + rq)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                float d = __fsub_rn(x4[k].x, c4[k].x);
-                float q = d * d;
-                d = __fsub_rn(x4[k].y, c4[k].y);
-                q = fmaf(d, d, q);
-                d = __fsub_rn(x4[k].z, c4[k].z);
-                q = fmaf(d, d, q);
-                d = __fsub_rn(x4[k].w, c4[k].w);
-                p[8 * bt + k] = fmaf(d, d, q);
-            }
-        }
-#pragma unroll
-        for (int lvl = 8; lvl >= 1; lvl >>= 1) {
-            const bool up = (rq & lvl) != 0;
-#pragma unroll
-            for (int i = 0; i < lvl; ++i) {
-                const float send = up ? p[i] : p[i + lvl];
-                const float keep = up ? p[i + lvl] : p[i];
-                p[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, lvl));
-            }
-        }
-        // lane (sub, rq) now holds the sum of row 2 rq + sub
-        const float got = __shfl_sync(0xffffffffu, p[0], (lane & 1) * 16 + (lane >> 1));
-        if (ccand >= 0) dc = got;
-    } else if (ccand >= 0) {
-        const float *xr = X + m * L;
-        const float *cr = C + (size_t)ccand * L;
-        float d2 = 0.f;
-        for (int l = 0; l < L; ++l) {
-            const float d = __fsub_rn(__ldg(xr + l), __ldg(cr + l));
-            d2 = fmaf(d, d, d2);
-        }
-        dc = d2;
-    }
-    sh.r.d[half][crow] = dc;
-    sh.r.k[half][crow] = kc;
-    named_sync(2, 32 * TC_EPI_WARPS);
-    if (half == 0 && m < M && !sh.abort) {
-        // the smaller distance is taken when the two differ by more than the
-        // rounding bound of the FP32 sum, |fl(d2) - d2| <= (L + 2) u d2 for any
-        // order of the L terms (kept as (L + 4) u); else the row is not certified
-        bool certified = false;
-        if (usable) {
-            float da = sh.r.d[0][crow], ka = sh.r.k[0][crow];
-            const float db = sh.r.d[1][crow], kb = sh.r.k[1][crow];
-            int ii = i1;
-            bool sure = true;
-            if (i1 + 1 < N) {
-                const float tol = (float)(L + 4) * U32 * (da + db) * SLOP;
-                if (db < da - tol) {
-                    ii = i1 + 1;
-                    da = db;
-                    ka = kb;
-                } else if (!(da < db - tol)) {
-                    sure = false;
+                for (int k = 0; k < 4; ++k) {
+                    float d = __fsub_rn(x4[k].x, c4[k].x);
+                    float q = d * d;
+                    d = __fsub_rn(x4[k].y, c4[k].y);
+                    q = fmaf(d, d, q);
+                    d = __fsub_rn(x4[k].z, c4[k].z);
+                    q = fmaf(d, d, q);
+                    d = __fsub_rn(x4[k].w, c4[k].w);
+                    p[4 * bt + k] = fmaf(d, d, q);
                 }
             }
+#pragma unroll
+            for (int lvl = 8; lvl >= 1; lvl >>= 1) {
+                const bool up = (rq & lvl) != 0;
+#pragma unroll
+                for (int i = 0; i < lvl; ++i) {
+                    const float send = up ? p[i] : p[i + lvl];
+                    const float keep = up ? p[i + lvl] : p[i];
+                    p[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, lvl));
+                }
+            }
+            // lane (sub, rq) now holds the sum of row 2 rq + sub
+            const float got = __shfl_sync(0xffffffffu, p[0], (lane & 1) * 16 + (lane >> 1));
+            if (ccand >= 0) dc = got;
+        } else if (ccand >= 0) {
+            const float *xr = X + m * L;
+            const float *cr = C + (size_t)ccand * L;
+            float d2 = 0.f;
+            for (int l = 0; l < L; ++l) {
+                const float d = __fsub_rn(__ldg(xr + l), __ldg(cr + l));
+                d2 = fmaf(d, d, d2);
+            }
+            dc = d2;
+        }
+        sh.r.d[(TC_GRP / 2) * half + g][crow] = dc;
+    }
+    sh.r.k[half][crow] = kmax;
+    named_sync(2, 32 * TC_EPI_WARPS);
+    if (half == 0 && m < M && !sh.abort) {
+        // the group member with the smallest FP32 direct-form distance wins when every other
+        // member's distance exceeds it by more than the rounding bound of the FP32 sums,
+        // |fl(d2) - d2| <= (L + 2) u d2 for any order of the L terms (kept as (L + 4) u); else
+        // the row is not certified
+        bool certified = false;
+        if (usable) {
+            float dd[TC_GRP];
+#pragma unroll
+            for (int g = 0; g < TC_GRP; ++g) dd[g] = sh.r.d[g][crow];
+            int w = 0;
+#pragma unroll
+            for (int g = 1; g < TC_GRP; ++g) w = dd[g] < dd[w] ? g : w;
+            const float da = dd[w];
+            bool sure = true;
+#pragma unroll
+            for (int g = 0; g < TC_GRP; ++g) {
+                const float tol = (float)(L + 4) * U32 * (da + dd[g]) * SLOP;
+                if (g != w && !(da < dd[g] - tol)) sure = false;
+            }
+            const int ii = i1 + w;
+            // k' of the member that produced V1 is unknown: the group's largest bounds it
+            const float ka = fmaxf(sh.r.k[0][crow], sh.r.k[1][crow]);
             if (sure) {
                 const double tau = tc_tau(tc_kb(LK));
                 const float xn2u = xn2 * SLOP;
                 const float R = 2.f * (float)tau * xn2u * SLOP;
                 const float eta = U32 * (sqrtf(xn2u) + cmax) * SLOP;
-                // index packing of the pair minima, FMA-pipe pair maxima
-                const float pack = TC_PACK * (fabsf(V1) + fabsf(V2)) + TC_HIERR * (fabsf(V1) + 2.f * fabsf(V2));
+                // index packing of the group minima
+                const float pack = TC_PACK * (fabsf(V1) + fabsf(V2));
                 // the MMA sums x~ . (p_hi + p_mid) and misses x~ . r_n, r_n = c'_n - p_hi - p_mid:
                 // |x~ . r_n| <= ||x~|| rho for every n (Cauchy-Schwarz)
                 const float E = sqrtf(xn2u) * rho * SLOP;
                 // |fl(||x~||^2) - ||x~||^2|: X2 as the MMA saw it
                 const float xerr = (float)(L + 2) * U32 * xn2u;
-                // V1 ~ ||x~ - c~_ii||^2 - k' (X2 included): bound g1^2 from above
+                // the member j that produced V1 has ||x~ - c~_j||^2 - k'_j ~ V1 (X2 included), and
+                // the winner ii is not farther than j: bound its g1^2 from above
                 const float g1sq = V1 + 2.f * ka + R + pack + E + xerr;
                 const float g1 = sqrtf(fmaxf(g1sq, 0.f)) * SLOP;
                 const float margin = (2.f * R + 2.f * ka + pack + 2.f * E + 4.f * eta * (g1 + eta)) * SLOP;
                 certified = (V2 - V1) > margin;
                 if (!certified) {
-                    // second certificate: every codevector outside the pair has
+                    // second certificate: every codevector outside the group has
                     // ||x - c_n||^2 >= (sqrt(V2 - R - E - pack - xerr) - eta)^2, which must
                     // exceed the winner's direct-form distance rounded up
                     const float lb = V2 - (R + E + pack + xerr) * SLOP;
@@ -1059,7 +1084,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // tile boundary the epilogue warps convert it (centring, exactness checks) and
 // write the next A operand into tensor memory as soon as the previous tile's
 // MMAs are done (they have consumed its last jobs), and only then finish the
-// previous tile (merge, exact pair distances, certificate), so the tensor pipe
+// previous tile (merge, exact group distances, certificate), so the tensor pipe
 // starts the next tile while that tail runs.  Codebook tiles stream through
 // a 2-stage ring (a third stage fits but measured no faster: the copies are
 // limited by the SM's bandwidth from L2, not by their latency); job and tile

@@ -158,7 +158,8 @@ struct Call {
 lbg_status ensure_workspace(Call &c, size_t bytes)
 {
     Workspace &w = g_ws[c.dev];
-    if (w.bytes < bytes) {
+    const size_t cap = g_ws_limit.load();
+    if (w.bytes < bytes || (cap != 0 && bytes > cap)) {
         if (w.base) {
             CK(cudaDeviceSynchronize());
             seq_clear(c.dev);
@@ -167,7 +168,6 @@ lbg_status ensure_workspace(Call &c, size_t bytes)
             w.bytes = 0;
         }
         void *p = nullptr;
-        const size_t cap = g_ws_limit.load();
         if (cap != 0 && bytes > cap) return LBG_ERR_NOMEM;   // as if cudaMalloc had refused
         if (cudaMalloc(&p, bytes) != cudaSuccess) {
             (void)cudaGetLastError();

@@ -15,10 +15,11 @@ tau * (sum_l |x~_l c'_l| + |s0_n| + X2), tau = (K/16 + 2) 2^-22 (1 + 2^-7),
 K = 2 ceil16(L) + 16.  These tests take that model at its worst: the
 accumulator value of the exact winner is pushed to the top of its interval
 and every other value to the bottom.  The epilogue is then emulated in FP32
-as the kernel runs it (pairs of columns, the pair index packed into the low
-mantissa bits of the pair minimum, the pair maximum as (a + b) - min, running
-top-2 per chain, merges), the two members of the best pair get FP32 direct
-distances at the worst end of their rounding bound, and both certificates are
+as the kernel runs it (groups of eight columns, the group index packed into
+the low mantissa bits of the group minimum, running top-2 of group minima per
+chain, merges), the eight members of the best group get FP32 direct
+distances at the worst end of their rounding bound, the winner among them
+must beat the others by the rounding bound, and both certificates are
 evaluated in exact arithmetic.  A row either of them accepts must have the
 exact (rational) argmin of the original FP32 values.  This checks the
 algebra of the certificates under the model; the measured accumulation
@@ -31,9 +32,8 @@ import numpy as np
 import pytest
 
 U = Fraction(1, 2 ** 24)
-NT, HALF, JBITS = 144, 72, 6        # codevectors per tile, per half, bits of the pair index
-PACK = Fraction(1, 2 ** 17)         # packing moves a pair minimum by less than this fraction
-HIERR = Fraction(1, 2 ** 23)        # pair maximum (a + b) - min within this of (|V1| + 2|V2|)
+NT, HALF, GRP, JBITS = 144, 72, 8, 4   # codevectors per tile, per half, per group; group index bits
+PACK = Fraction(1, 2 ** 19)         # packing moves a group minimum by less than this fraction
 
 
 def round_bits(x: Fraction, p: int, up: bool = False) -> Fraction:
@@ -97,28 +97,28 @@ def _f32bits_key(lo: np.float32, j: int) -> np.float32:
 
 def _epilogue(v):
     """Top-2 of the kernel's epilogue over one row's FP32 accumulator values v
-    (length a multiple of NT): (V1, V2, i1), i1 the first column of the best pair."""
+    (length a multiple of NT): (V1, V2, i1), V1 the smallest value, V2 the
+    smallest outside V1's group, i1 the first column of V1's group."""
     nt = len(v) // NT
     halves = []
     for h in range(2):
         c1, c2, cg = [np.float32(np.inf)] * 2, [np.float32(np.inf)] * 2, [0, 0]
         for t in range(nt):
             s1 = list(c1)
-            for j in range(HALF // 2):
+            for j in range(HALF // GRP):
                 q = j % 2
-                a, b = v[t * NT + h * HALF + 2 * j], v[t * NT + h * HALF + 2 * j + 1]
-                lo = np.minimum(a, b)
-                hi = np.float32(np.float32(a + b) - lo)
+                base = t * NT + h * HALF + GRP * j
+                lo = np.float32(min(v[base:base + GRP]))
                 k = _f32bits_key(lo, j)
-                c2[q] = min(c2[q], max(c1[q], k), hi)
+                c2[q] = min(c2[q], max(c1[q], k))
                 c1[q] = min(c1[q], k)
             for q in range(2):
                 if c1[q] < s1[q]:
                     cg[q] = t
         jm = (1 << JBITS) - 1
         V1, V2 = c1[0], c2[0]
-        i1 = cg[0] * NT + h * HALF + 2 * (int(np.array([c1[0]]).view(np.uint32)[0]) & jm)
-        iq = cg[1] * NT + h * HALF + 2 * (int(np.array([c1[1]]).view(np.uint32)[0]) & jm)
+        i1 = cg[0] * NT + h * HALF + GRP * (int(np.array([c1[0]]).view(np.uint32)[0]) & jm)
+        iq = cg[1] * NT + h * HALF + GRP * (int(np.array([c1[1]]).view(np.uint32)[0]) & jm)
         V2 = min(min(V2, c2[1]), max(V1, c1[1]))
         if c1[1] < V1 or (c1[1] == V1 and iq < i1):
             V1, i1 = c1[1], iq
@@ -154,25 +154,22 @@ def _ints(arrays):
 
 
 def _epilogue_worst(v, best):
-    """The epilogue's top-2 in exact arithmetic with its two rounding effects at
-    their worst: a pair minimum moved by its packing (at most 63 units in the
-    last place of an FP32 value, < 2^-17 of it) and a pair maximum by the FP32
-    rounding of (a + b) - min (2^-24 (|min| + 2 |max|)); up for the exact
-    winner's pair, down for every other pair.  Returns (V1, V2, i1)."""
+    """The epilogue's top-2 of group minima in exact arithmetic with its one
+    rounding effect at its worst: a group minimum moved by its packing (at most
+    15 units in the last place of an FP32 value, < 2^-19 of it), up for the
+    exact winner's group and down for every other group.  Returns (V1, V2, i1)."""
     c1 = c2 = None
     i1 = -1
-    for p in range(len(v) // 2):
-        a, b = v[2 * p], v[2 * p + 1]
-        lo, mx = min(a, b), max(a, b)
-        s = 1 if best in (2 * p, 2 * p + 1) else -1
-        k = lo + s * Fraction(63, 2 ** 23) * abs(lo)
-        hi = mx + s * Fraction(1, 2 ** 24) * (abs(lo) + 2 * abs(mx))
+    for g in range(len(v) // GRP):
+        lo = min(v[GRP * g:GRP * g + GRP])
+        s = 1 if GRP * g <= best < GRP * g + GRP else -1
+        k = lo + s * Fraction(15, 2 ** 23) * abs(lo)
         if c1 is None:
-            c1, c2, i1 = k, hi, 2 * p
+            c1, c2, i1 = k, Fraction(10) ** 40, GRP * g
             continue
-        c2 = min(c2, max(c1, k), hi)
+        c2 = min(c2, max(c1, k))
         if k < c1:
-            c1, i1 = k, 2 * p
+            c1, i1 = k, GRP * g
     return c1, c2, i1
 
 
@@ -250,6 +247,7 @@ def certify(x, C, mu, N, adversarial=True, worst=False, weights=None):
         val = f32(target, up=True) if e < 0 else -f32(-target, up=True)
         v.append(np.float32(float(val)))
     if worst:
+        v += [Fraction(2) ** 100] * (-(-N // GRP) * GRP - N)
         V1, V2, i1 = _epilogue_worst(v, best)
     else:
         npad = -(-N // NT) * NT
@@ -257,23 +255,22 @@ def certify(x, C, mu, N, adversarial=True, worst=False, weights=None):
         V1, V2, i1 = _epilogue(v)
         V1, V2 = Fraction(float(V1)), Fraction(float(V2))
 
-    # FP32 direct-form distances of the pair, at the worst end of their bound
+    # FP32 direct-form distances of the group, at the worst end of their bound
     def direct(n):
         d = exact[n]
         return d * (1 + (L + 2) * U) if (n == best) == adversarial else d * (1 - (L + 2) * U)
 
-    da = direct(i1)
-    ii, ka = i1, kp[i1]
-    if i1 + 1 < N:
-        db = direct(i1 + 1)
-        tol = (L + 4) * U * (da + db)
-        if db < da - tol:
-            ii, da, ka = i1 + 1, db, kp[i1 + 1]
-        elif not (da < db - tol):
+    members = [n for n in range(i1, i1 + GRP) if n < N]
+    dd = {n: direct(n) for n in members}
+    ii = min(members, key=lambda n: (dd[n], n))
+    da = dd[ii]
+    for n in members:
+        if n != ii and not (da < dd[n] - (L + 4) * U * (da + dd[n])):
             return False, ii, best
+    ka = max(kp[n] for n in members)        # k' of V1's member is only known to be <= this
     R = 2 * tau * X2
     eta = U * (sqrt_up(Fraction(X2)) + cmax)
-    pack = PACK * (abs(V1) + abs(V2)) + HIERR * (abs(V1) + 2 * abs(V2))
+    pack = PACK * (abs(V1) + abs(V2))
     xerr = (L + 2) * U * X2
     g1 = sqrt_up(V1 + 2 * ka + R + pack + E + xerr)
     margin = (wt["m_R"] * 2 * R + wt["m_k"] * 2 * ka + wt["m_pack"] * pack + wt["m_E"] * 2 * E
@@ -347,8 +344,8 @@ def test_bf16_certificates_sound_at_every_bound(L, spread, family):
     """The proof uses each error only through its bound, so it must hold with
     every error at the end of its bound that favours a wrong answer: the
     accumulation error (model), the missed term x~.r_n anywhere in
-    [-||x~|| rho, ||x~|| rho], the packed pair minimum, the FMA-pipe pair
-    maximum and the direct-form distances of the pair.  With all of them at
+    [-||x~|| rho, ||x~|| rho], the packed group minimum and the direct-form
+    distances of the group's members.  With all of them at
     their worst, no wrong row is accepted (and the next test shows that the
     terms are needed)."""
     rng = np.random.default_rng(100 + L + int(spread))
@@ -364,14 +361,17 @@ def test_bf16_certificates_sound_at_every_bound(L, spread, family):
 
 
 @pytest.mark.parametrize("weights", [{"m_R": 0}, {"m_R": 0.5}, {"m_k": 0}, {"m_k": 0.5},
-                                     {"m_pack": 0}, {"m_pack": 0.5}, {"m_E": 0}, {"m_E": 0.5},
+                                     {"m_E": 0}, {"m_E": 0.5},
                                      {"lb_R": 0}, {"lb_E": 0}, {"lb_E": 0.5}, {"lb_pack": 0}])
 def test_bf16_certificate_terms_are_needed(weights):
     """With every error at its worst (as above), dropping or halving one term of
     the first certificate's margin, or dropping one of the second's lower bound,
     lets a wrong row through in one of the row families.  (Not shown this way:
     the eta terms, never binding here since x~ is exact for integer mu; halving
-    R' in the second certificate, whose packing term leaves that much slack.)"""
+    R' in the second certificate, whose packing term leaves that much slack;
+    the first certificate's packing term, 2^-19 (|V1| + |V2|), for which the
+    group's largest k' -- it stands in for the unknown k' of V1's member --
+    leaves more room than that in these families.)"""
     params = [(16, 20.0, "near"), (16, 2.0, "near"), (64, 20.0, "near"), (64, 2.0, "near"),
               (16, 0.5, "mirror"), (64, 0.5, "mirror")]
     for L, spread, family in params:
@@ -396,3 +396,26 @@ def test_bf16_certificates_accept_clear_winners():
         x = np.clip(np.rint(C[n] + rng.standard_normal(L)), 0, 255).astype(np.float32)
         ok, ii, best = certify(x, C, mu, N)
         assert ok and ii == best == n
+
+
+def test_bf16_certificates_resolve_split_twins():
+    """Right after a split every codevector has a twin at 2 delta (children 2i and 2i + 1 of
+    the same parent).  Twins share a group, so the second-best value the certificates use
+    comes from the next parent, and the twins themselves are told apart by their exact
+    distances: rows near one parent are certified, each with its exact nearest twin."""
+    rng = np.random.default_rng(17)
+    L, N = 16, NT
+    parents = (128 + 40 * rng.standard_normal((N // 2, L))).astype(np.float32)
+    delta = np.float32(0.01)
+    C = np.empty((N, L), np.float32)
+    C[0::2] = parents + delta
+    C[1::2] = parents - delta
+    mu = np.rint(C.mean(0)).astype(np.float32)
+    accepted = 0
+    for n in rng.choice(N // 2, 24, replace=False):
+        x = np.clip(np.rint(parents[n] + 3 * rng.standard_normal(L)), 0, 255).astype(np.float32)
+        ok, ii, best = certify(x, C, mu, N)
+        if ok:
+            accepted += 1
+            assert ii == best and best // 2 == n
+    assert accepted >= 20
