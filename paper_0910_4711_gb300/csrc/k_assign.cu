@@ -14,7 +14,8 @@
 //     bulk copy (cp.async.bulk + mbarrier, bounded waits);
 //   * every thread keeps an 8 x 8 register tile of accumulators whose FMA
 //     chain starts at a per-codevector constant, so the tile needs no
-//     epilogue arithmetic besides a running top-2 (3 FMNMX per distance);
+//     epilogue arithmetic besides a running top-2 over split pairs (the
+//     minimum of codevectors 2k, 2k + 1, then 3 FMNMX: 2 per distance);
 //   * the index of the minimum is recovered after the sweep by recomputing
 //     the one winning 8-codevector group bit-identically;
 //   * a rigorous rounding-error bound certifies the minimum; rows it cannot
@@ -27,12 +28,18 @@
 // The chain computes v_n ~ f_n - k_n with f_n = ||c~_n||^2 - 2 x~.c~_n and
 // |v_n - (f_n - k_n)| <= (L+1)(1+Lu) u (||c~_n||^2 + 2||x~|| ||c~_n||)
 //                     <= k_n + R          (2ab <= a^2 + b^2),
-// hence v_n - R <= f_n <= v_n + 2 k_n + R.  If V1 = v_i1 is the minimum and V2
-// the second smallest, V2 - V1 > 2R + 2k_i1 proves f_n > f_i1 for all n != i1,
-// i.e. ||x~ - c~_n|| > ||x~ - c~_i1||.  Centring moves each distance
-// ||x - c_n|| by at most eta = u (||x~|| + max ||c~||); the extra term
-// 4 eta (g1 + eta), g1 >= ||x~ - c~_i1||, keeps the proof valid for the
-// original x and c_n.  A certified i1 is therefore the exact argmin.
+// hence v_n - R <= f_n <= v_n + 2 k_n + R.  The codevectors are taken in pairs
+// P = (2k, 2k + 1) -- the two children of a split.  If V1 = v_i1 is the minimum,
+// P* its pair and V2 the smallest value outside P*, V2 - V1 > 2R + 2k_P*
+// (k_P* the larger k of the pair) proves f_n > f_i1 for all n outside P*, i.e.
+// ||x~ - c~_n|| > ||x~ - c~_i1||.  Centring moves each distance ||x - c_n|| by
+// at most eta = u (||x~|| + max ||c~||); the extra term 4 eta (g1 + eta),
+// g1 >= ||x~ - c~_i1||, keeps the proof valid for the original x and c_n.  The
+// exact argmin is then i1 or its partner: the one whose FP32 direct-form
+// distance is smaller by more than that form's rounding bound (else the row
+// is not certified).  Right after a split a row's two nearest codevectors are
+// often such twins; they are told apart exactly here instead of failing the
+// bound.
 #include "lbg_internal.cuh"
 
 #include <math.h>
@@ -314,8 +321,8 @@ __device__ __forceinline__ bool assign_f32_tile_t(
             for (int i = 0; i < 8; ++i) {
                 const float old = v1[i];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float a = acc[i][j];
+                for (int j = 0; j < 8; j += 2) {   // codevectors j, j + 1: a split pair (2k, 2k + 1)
+                    const float a = fminf(acc[i][j], acc[i][j + 1]);
                     v2[i] = fminf(v2[i], fmaxf(v1[i], a));
                     v1[i] = fminf(v1[i], a);
                 }
@@ -422,12 +429,14 @@ __device__ __forceinline__ bool assign_f32_tile_t(
         if (i1 < 0 && s[j] == V1) i1 = kw * BN + nl + (j < 4 ? j : 28 + j);
 
     bool certified = false;
+    const int ip = i1 ^ 1;                       // the other member of i1's pair
+    const bool pair = ip < N;
     if (i1 >= 0 && i1 < N && V1 < INFINITY) {
         float xn2 = 0.f;
         for (int l = 0; l < L; ++l) xn2 = fmaf(xs[l * TBM + r], xs[l * TBM + r], xn2);
         const float xn2u = xn2 * SLOP;
         const float R = (float)(L + 2) * U32 * xn2u * SLOP;
-        const float kc = kn[i1];
+        const float kc = pair ? fmaxf(kn[i1], kn[ip]) : kn[i1];
         const float cmax = __uint_as_float(st->cmax_bits);
         const float eta = U32 * (sqrtf(xn2u) + cmax) * SLOP;
         const float g1sq = xn2u + V1 + 2.f * kc + R + 4.f * U32 * (xn2u + fabsf(V1));
@@ -435,16 +444,38 @@ __device__ __forceinline__ bool assign_f32_tile_t(
         const float margin = (2.f * R + 2.f * kc + 4.f * eta * (g1 + eta)) * SLOP;
         certified = (V2 - V1) > margin;
     }
+    int win = i1;
+    float dwin = 0.f;
     if (certified) {
+        // the pair's exact FP32 direct-form distances decide between its members
         const float *xr = X + m * L;
-        const float *cr = C + (size_t)i1 * L;
-        float d2 = 0.f;
+        const float *ca = C + (size_t)i1 * L;
+        float da = 0.f;
         for (int l = 0; l < L; ++l) {
-            const float d = xr[l] - cr[l];
-            d2 = fmaf(d, d, d2);
+            const float d = xr[l] - ca[l];
+            da = fmaf(d, d, da);
         }
-        assign[m] = i1;
-        e[m] = d2;
+        dwin = da;
+        if (pair) {
+            const float *cb = C + (size_t)ip * L;
+            float db = 0.f;
+            for (int l = 0; l < L; ++l) {
+                const float d = xr[l] - cb[l];
+                db = fmaf(d, d, db);
+            }
+            // |fl(d2) - d2| <= (L + 2) u d2 for either sum (kept as (L + 4) u)
+            const float tol = (float)(L + 4) * U32 * (da + db) * SLOP;
+            if (db < da - tol) {
+                win = ip;
+                dwin = db;
+            } else if (!(da < db - tol)) {
+                certified = false;
+            }
+        }
+    }
+    if (certified) {
+        assign[m] = win;
+        e[m] = dwin;
     } else {
         flags[atomicAdd(&st->nflag, 1)] = (int32_t)m;
     }

@@ -104,12 +104,25 @@ constexpr int TC_NT = 144;                     // codevectors per tile (MMA N): 
                                                // runs epilogue warps (N = 128 issued about one
                                                // MMA per 86 cycles for 64 cycles of work)
 constexpr int TC_HALF = TC_NT / 2;             // columns per epilogue thread per tile
-constexpr int TC_GRP = 8;                      // columns per group: the running top-2 is over group
-                                               // minima; a group holds the four split pairs
-                                               // (children 2i, 2i + 1) of four parents
-constexpr int TC_GROUPS = TC_HALF / TC_GRP;    // groups per epilogue thread per tile (9)
-constexpr int TC_JBITS = 4;                    // bits of the in-half group index
-constexpr float TC_PACK = 1.9073486328125e-6f; // 2^(TC_JBITS - 23): packing changes a value
+// Columns per group (GRP = 2 or 8): the running top-2 is over group minima, and
+// a group holds whole split pairs (children 2i, 2i + 1).  Eight columns take one
+// ALU operation per value in the epilogue but eight exact distances per row in
+// the tail; two columns take 2.5 and two.  GrpCfg<GRP>: groups per epilogue
+// thread per tile, bits of the in-half group index, and the packing bound
+// 2^(JBITS - 23) (packing changes a value by less than this fraction of it).
+template <int GRP>
+struct GrpCfg;
+template <>
+struct GrpCfg<2> {
+    static constexpr int GROUPS = 36, JBITS = 6;
+    static constexpr float PACK = 7.62939453125e-6f;
+};
+template <>
+struct GrpCfg<8> {
+    static constexpr int GROUPS = 9, JBITS = 4;
+    static constexpr float PACK = 1.9073486328125e-6f;
+};
+constexpr int TC_GRP_MAX = 8;
                                                // by less than this fraction of it
 constexpr float TC_EVAL = 9.5367431640625e-7f;   // 2^-20: FP32 evaluation of the second certificate
 constexpr int TC_STAGES = 3;
@@ -124,7 +137,8 @@ constexpr int TC_NCH = 2;                      // independent min-chains of the 
                                                // epilogue warps of the sub-partition hide the
                                                // chains' latency; fewer chains, less bookkeeping)
 static_assert(TC_A_COL + 2 * ((TC_LMAX + 16) / 2) <= TC_TMEM_COLS, "accumulators + A exceed TMEM");
-static_assert(TC_HALF == 72 && TC_HALF % TC_GRP == 0 && TC_GROUPS <= (1 << TC_JBITS),
+static_assert(TC_HALF == 72 && GrpCfg<2>::GROUPS * 2 == TC_HALF && GrpCfg<8>::GROUPS * 8 == TC_HALF &&
+                  GrpCfg<2>::GROUPS <= (1 << GrpCfg<2>::JBITS) && GrpCfg<8>::GROUPS <= (1 << GrpCfg<8>::JBITS),
               "epilogue loads 64 + 8 columns in whole groups");
 
 constexpr float U32 = 5.9604644775390625e-8f;   // 2^-24
@@ -199,20 +213,24 @@ __device__ __forceinline__ float fmin3(float a, float b, float c)
     return d;
 }
 
-// One epilogue step for group G (columns 8G .. 8G + 7 of the thread's half):
-// its minimum (four three-input / two-input mins) carries the group index in
-// its JBITS low mantissa bits (one LOP3; `keymask` = ~(2^JBITS - 1) comes in as
-// a kernel argument so that the mask stays in a register and the immediate is
-// the index); then the running top-2 of group minima of chain G % NCH:
-// c2 = min(c2, max(c1, k)), c1 = min(c1, k).  Eight ALU operations per group.
-template <int P>
+// One epilogue step for group j (columns GRP j .. GRP j + GRP - 1 of the
+// thread's half): its minimum (three-input mins) carries the group index in its
+// JBITS low mantissa bits (one LOP3; `keymask` = ~(2^JBITS - 1) comes in as a
+// kernel argument so that the mask stays in a register and the immediate is the
+// index); then the running top-2 of group minima of chain j % NCH:
+// c2 = min(c2, max(c1, k)), c1 = min(c1, k).
+template <int GRP, int P>
 struct GroupSteps {
     __device__ __forceinline__ static void run(const float *v, float *c1, float *c2, int keymask)
     {
-        GroupSteps<P - 1>::run(v, c1, c2, keymask);
+        GroupSteps<GRP, P - 1>::run(v, c1, c2, keymask);
         constexpr int j = P - 1, q = j % TC_NCH;
-        const float *g = v + TC_GRP * j;
-        const float lo = fmin3(fmin3(g[0], g[1], g[2]), fmin3(g[3], g[4], g[5]), fminf(g[6], g[7]));
+        const float *g = v + GRP * j;
+        float lo;
+        if constexpr (GRP == 8)
+            lo = fmin3(fmin3(g[0], g[1], g[2]), fmin3(g[3], g[4], g[5]), fminf(g[6], g[7]));
+        else
+            lo = fminf(g[0], g[1]);
         int kb;
         asm("lop3.b32 %0, %1, %2, %3, 0xEA;" : "=r"(kb) : "r"(__float_as_int(lo)), "r"(keymask), "n"(j));
         const float k = __int_as_float(kb);
@@ -220,8 +238,8 @@ struct GroupSteps {
         c1[q] = fminf(c1[q], k);
     }
 };
-template <>
-struct GroupSteps<0> {
+template <int GRP>
+struct GroupSteps<GRP, 0> {
     __device__ __forceinline__ static void run(const float *, float *, float *, int) {}
 };
 
@@ -560,7 +578,7 @@ struct TcSmem {
             int i1[2][TC_ROWS];
         } m;
         struct {
-            float d[TC_GRP][TC_ROWS];               // exact distances of the best group (tail);
+            float d[TC_GRP_MAX][TC_ROWS];           // exact distances of the best group (tail);
                                                     // d[0..1]: ||x~||^2 halves (A write)
             float k[2][TC_ROWS];                    // the halves' largest k' of the group (tail)
         } r;
@@ -639,13 +657,13 @@ __device__ __forceinline__ float tc_write_a(const __nv_bfloat16 *XS, int L, bool
 struct NoHook {
     __device__ __forceinline__ void operator()(int) const {}
 };
-template <class Hook = NoHook>
+template <int GRP, class Hook = NoHook>
 __device__ __forceinline__ void tc_jobs(TcSmem &sh, uint32_t tmem, int warp, int lane, int acc, int half,
                                         int ntiles, int j0, int keymask, float &V1, float &V2, int &i1,
                                         const Hook &hook = Hook())
 {
     constexpr int NCH = TC_NCH;
-    constexpr int JMASK = (1 << TC_JBITS) - 1;
+    constexpr int JMASK = (1 << GrpCfg<GRP>::JBITS) - 1;
     float c1[NCH], c2[NCH];
     int cg[NCH];
 #pragma unroll
@@ -685,19 +703,19 @@ __device__ __forceinline__ void tc_jobs(TcSmem &sh, uint32_t tmem, int warp, int
         float s1[NCH];
 #pragma unroll
         for (int q = 0; q < NCH; ++q) s1[q] = c1[q];
-        GroupSteps<TC_GROUPS>::run(v, c1, c2, keymask);
+        GroupSteps<GRP, GrpCfg<GRP>::GROUPS>::run(v, c1, c2, keymask);
 #pragma unroll
         for (int q = 0; q < NCH; ++q) cg[q] = c1[q] < s1[q] ? t : cg[q];
         hook(t);
     }
     // merge the chains; i1 is the first column of the minimum's group:
-    // tile * TC_NT + half * TC_HALF + TC_GRP * (the low bits)
+    // tile * TC_NT + half * TC_HALF + GRP * (the low bits)
     V1 = c1[0];
     V2 = c2[0];
-    i1 = cg[0] * TC_NT + half * TC_HALF + TC_GRP * (__float_as_int(c1[0]) & JMASK);
+    i1 = cg[0] * TC_NT + half * TC_HALF + GRP * (__float_as_int(c1[0]) & JMASK);
 #pragma unroll
     for (int q = 1; q < NCH; ++q) {
-        const int iq = cg[q] * TC_NT + half * TC_HALF + TC_GRP * (__float_as_int(c1[q]) & JMASK);
+        const int iq = cg[q] * TC_NT + half * TC_HALF + GRP * (__float_as_int(c1[q]) & JMASK);
         V2 = fminf(fminf(V2, c2[q]), fmaxf(V1, c1[q]));
         const bool take = c1[q] < V1 || (c1[q] == V1 && iq < i1);
         V1 = take ? c1[q] : V1;
@@ -718,7 +736,7 @@ __device__ __forceinline__ void tc_jobs(TcSmem &sh, uint32_t tmem, int warp, int
 // by more than the rounding bound of the FP32 sums, runs the certificates,
 // and writes a(m), e(m) or flags the row.  `usable` = the tile's x~ and the
 // codebook split are exact.
-template <int LK>
+template <int LK, int GRP>
 __device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc, int half, int rr,
                                         int64_t m0, const float *__restrict__ X, int64_t M, int L, int N,
                                         const float *__restrict__ C, const float *__restrict__ kn, float xn2,
@@ -747,8 +765,8 @@ __device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc,
     float kmax = 0.f;
     const bool coop = (L & 3) == 0 && ((reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(X)) & 15u) == 0;
 #pragma unroll 1
-    for (int g = 0; g < TC_GRP / 2; ++g) {
-        const int cand = i1 + (TC_GRP / 2) * half + g;
+    for (int g = 0; g < GRP / 2; ++g) {
+        const int cand = i1 + (GRP / 2) * half + g;
         const int ccand = (usable && cand < N) ? cand : -1;
         if (ccand >= 0) kmax = fmaxf(kmax, __ldg(kn + ccand));
         float dc = INFINITY;
@@ -806,7 +824,7 @@ __device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc,
             }
             dc = d2;
         }
-        sh.r.d[(TC_GRP / 2) * half + g][crow] = dc;
+        sh.r.d[(GRP / 2) * half + g][crow] = dc;
     }
     sh.r.k[half][crow] = kmax;
     named_sync(2, 32 * TC_EPI_WARPS);
@@ -817,18 +835,18 @@ __device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc,
         // the row is not certified
         bool certified = false;
         if (usable) {
-            float dd[TC_GRP];
+            float dd[GRP];
 #pragma unroll
-            for (int g = 0; g < TC_GRP; ++g) dd[g] = sh.r.d[g][crow];
+            for (int g = 0; g < GRP; ++g) dd[g] = sh.r.d[g][crow];
             int w = 0;
 #pragma unroll
-            for (int g = 1; g < TC_GRP; ++g) w = dd[g] < dd[w] ? g : w;
+            for (int g = 1; g < GRP; ++g) w = dd[g] < dd[w] ? g : w;
             const float da = dd[w];
             bool sure = true;
 #pragma unroll
-            for (int g = 0; g < TC_GRP; ++g) {
+            for (int g = 0; g < GRP; ++g) {   // members past N have no distance (infinity)
                 const float tol = (float)(L + 4) * U32 * (da + dd[g]) * SLOP;
-                if (g != w && !(da < dd[g] - tol)) sure = false;
+                if (g != w && dd[g] < INFINITY && !(da < dd[g] - tol)) sure = false;
             }
             const int ii = i1 + w;
             // k' of the member that produced V1 is unknown: the group's largest bounds it
@@ -839,7 +857,7 @@ __device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc,
                 const float R = 2.f * (float)tau * xn2u * SLOP;
                 const float eta = U32 * (sqrtf(xn2u) + cmax) * SLOP;
                 // index packing of the group minima
-                const float pack = TC_PACK * (fabsf(V1) + fabsf(V2));
+                const float pack = GrpCfg<GRP>::PACK * (fabsf(V1) + fabsf(V2));
                 // the MMA sums x~ . (p_hi + p_mid) and misses x~ . r_n, r_n = c'_n - p_hi - p_mid:
                 // |x~ . r_n| <= ||x~|| rho for every n (Cauchy-Schwarz)
                 const float E = sqrtf(xn2u) * rho * SLOP;
@@ -870,21 +888,22 @@ __device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc,
 }
 
 // ---------------------------------------------------------------- one CTA per row tile
-template <int LK>
+template <int LK, int GRP>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_assign_tc(const float *__restrict__ X, int64_t M, int L,
                 const __nv_bfloat16 *__restrict__ Bp, const float *__restrict__ kn,
                 const int32_t *n_dev, int n_host, const float *__restrict__ mu,
                 const float *__restrict__ C, DevState *st, int32_t *__restrict__ assign,
                 float *__restrict__ e, int32_t *__restrict__ flags, int keymask,
-                int64_t flag_base)
+                int64_t flag_base, int n_lo, int n_hi)
 {
     if (st->finished) return;
+    const int N = cur_n(n_dev, n_host);
+    if (N < n_lo || N >= n_hi) return;   // the other group size serves this codebook size
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ TcSmem sh;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int N = cur_n(n_dev, n_host);
     const int ntiles = (N + TC_NT - 1) / TC_NT;
     constexpr int KB = tc_kb(LK);
     constexpr int XSTR = XsRow<LK>::STR;                       // staged row stride (BF16)
@@ -1051,8 +1070,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ---------------- epilogue: one (row, column half) per thread
         float V1, V2;
         int i1;
-        tc_jobs(sh, tmem, warp, lane, acc, half, ntiles, 0, keymask, V1, V2, i1);
-        tc_tail<LK>(sh, warp, lane, acc, half, rr, m0, X, M, L, N, C, kn, xn2, !sh.inexact && tc_exact_cb,
+        tc_jobs<GRP>(sh, tmem, warp, lane, acc, half, ntiles, 0, keymask, V1, V2, i1);
+        tc_tail<LK, GRP>(sh, warp, lane, acc, half, rr, m0, X, M, L, N, C, kn, xn2, !sh.inexact && tc_exact_cb,
                     cmax, rho, V1, V2, i1, st, assign, e, flags, flag_base);
     }
 
@@ -1092,21 +1111,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // Needs L % 4 == 0 and a 16-byte aligned X (the launcher checks).
 constexpr int TC_PSTAGES = 2;
 
-template <int LK>
+template <int LK, int GRP>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_assign_tc_p(const float *__restrict__ X, int64_t M, int L,
                   const __nv_bfloat16 *__restrict__ Bp, const float *__restrict__ kn,
                   const int32_t *n_dev, int n_host, const float *__restrict__ mu,
                   const float *__restrict__ C, DevState *st, int32_t *__restrict__ assign,
                   float *__restrict__ e, int32_t *__restrict__ flags, int keymask,
-                  int64_t flag_base)
+                  int64_t flag_base, int n_lo, int n_hi)
 {
     if (st->finished) return;
+    const int N = cur_n(n_dev, n_host);
+    if (N < n_lo || N >= n_hi) return;   // the other group size serves this codebook size
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ TcSmem sh;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int N = cur_n(n_dev, n_host);
     const int ntiles = (N + TC_NT - 1) / TC_NT;
     const int64_t nrt = (M + TC_ROWS - 1) / TC_ROWS;   // row tiles
     const int K = (int)((nrt - (int64_t)blockIdx.x + gridDim.x - 1) / gridDim.x);   // this CTA's
@@ -1361,10 +1381,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (tid == 64) mbar_arrive(&sh.aready);
             }
             if (k >= 1)
-                tc_tail<LK>(sh, warp, lane, acc, half, rr, tile_m0(k - 1), X, M, L, N, C, kn, pxn2, pusable,
+                tc_tail<LK, GRP>(sh, warp, lane, acc, half, rr, tile_m0(k - 1), X, M, L, N, C, kn, pxn2, pusable,
                             cmax, rho, pV1, pV2, pi1, st, assign, e, flags, flag_base);
             if (k < K) {
-                tc_jobs(sh, tmem, warp, lane, acc, half, ntiles, 2 * k * ntiles, keymask, pV1, pV2, pi1);
+                tc_jobs<GRP>(sh, tmem, warp, lane, acc, half, ntiles, 2 * k * ntiles, keymask, pV1, pV2, pi1);
                 pxn2 = xn2;
                 pusable = tile_exact && tc_exact_cb;
             }
@@ -1424,6 +1444,38 @@ void launch_prep_tc(const float *C, int N_alloc, const int32_t *n_dev, int n_hos
     }
 }
 
+// Group size by codebook size: eight columns where the epilogue's ALU work is
+// what bounds the launch (short rows, LK <= 32, and many codevectors), two
+// elsewhere (the tail then scores two members instead of eight).
+constexpr int TC_G8_MIN_N = 1024;
+
+template <int LK, int GRP>
+static void launch_tc_g(const float *X, int64_t M, int L, const __nv_bfloat16 *B, const float *kn,
+                        const int32_t *n_dev, int n_host, const float *mu, const float *C, DevState *st,
+                        int32_t *assign, float *e, int32_t *flags, cudaStream_t s, int64_t m_lo, int64_t grid,
+                        int n_lo, int n_hi)
+{
+    const int keymask = ~((1 << GrpCfg<GRP>::JBITS) - 1);
+    if ((L & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) {
+        // persistent: 2 codebook stages + staged BF16 rows + the FP32 x tile
+        const size_t need = (size_t)TC_PSTAGES * TC_NT * tc_kb(LK) * 2 + (size_t)TC_ROWS * XsRow<LK>::STR * 2 +
+                            (size_t)TC_ROWS * LK * 4;
+        // at least 120 KB so that a single CTA (and its 512 TMEM columns) owns the SM
+        const size_t smem = need > 120 * 1024 ? need : 120 * 1024;
+        cudaFuncSetAttribute(k_assign_tc_p<LK, GRP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int64_t g = grid < num_sms() ? grid : num_sms();
+        LBG_COUNTED k_assign_tc_p<LK, GRP><<<(unsigned)g, TC_THREADS, smem, s>>>(
+            X, M, L, B, kn, n_dev, n_host, mu, C, st, assign, e, flags, keymask, m_lo, n_lo, n_hi);
+        return;
+    }
+    const size_t need = (size_t)TC_ROWS * XsRow<LK>::STR * 2 + (size_t)TC_STAGES * TC_NT * tc_kb(LK) * 2;
+    // at least 120 KB so that a single CTA (and its 512 TMEM columns) owns the SM
+    const size_t smem = need > 120 * 1024 ? need : 120 * 1024;
+    cudaFuncSetAttribute(k_assign_tc<LK, GRP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    LBG_COUNTED k_assign_tc<LK, GRP><<<(unsigned)grid, TC_THREADS, smem, s>>>(
+        X, M, L, B, kn, n_dev, n_host, mu, C, st, assign, e, flags, keymask, m_lo, n_lo, n_hi);
+}
+
 template <int LK>
 static void launch_tc(const float *X, int64_t M, int L, const void *Bp, const float *kn,
                       const int32_t *n_dev, int n_host, const float *mu, const float *C, DevState *st,
@@ -1437,26 +1489,23 @@ static void launch_tc(const float *X, int64_t M, int L, const void *Bp, const fl
     M -= m_lo;
     const int64_t grid = (M + TC_ROWS - 1) / TC_ROWS;
     if (grid <= 0) return;
-    const int keymask = ~((1 << TC_JBITS) - 1);
     const __nv_bfloat16 *B = static_cast<const __nv_bfloat16 *>(Bp);
-    if ((L & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) {
-        // persistent: 2 codebook stages + staged BF16 rows + the FP32 x tile
-        const size_t need = (size_t)TC_PSTAGES * TC_NT * tc_kb(LK) * 2 + (size_t)TC_ROWS * XsRow<LK>::STR * 2 +
-                            (size_t)TC_ROWS * LK * 4;
-        // at least 120 KB so that a single CTA (and its 512 TMEM columns) owns the SM
-        const size_t smem = need > 120 * 1024 ? need : 120 * 1024;
-        cudaFuncSetAttribute(k_assign_tc_p<LK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        const int64_t g = grid < num_sms() ? grid : num_sms();
-        LBG_COUNTED k_assign_tc_p<LK><<<(unsigned)g, TC_THREADS, smem, s>>>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign,
-                                                               e, flags, keymask, m_lo);
-        return;
+    if constexpr (LK <= 32) {
+        if (!n_dev) {   // the size is known here: one launch
+            if (n_host >= TC_G8_MIN_N)
+                launch_tc_g<LK, 8>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo, grid, 0, 1 << 30);
+            else
+                launch_tc_g<LK, 2>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo, grid, 0, 1 << 30);
+        } else {        // training: the stage size is on the device, each kernel takes its range
+            launch_tc_g<LK, 2>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo, grid, 0,
+                               TC_G8_MIN_N);
+            if (n_host >= TC_G8_MIN_N)
+                launch_tc_g<LK, 8>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo, grid,
+                                   TC_G8_MIN_N, 1 << 30);
+        }
+    } else {
+        launch_tc_g<LK, 2>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo, grid, 0, 1 << 30);
     }
-    const size_t need = (size_t)TC_ROWS * XsRow<LK>::STR * 2 + (size_t)TC_STAGES * TC_NT * tc_kb(LK) * 2;
-    // at least 120 KB so that a single CTA (and its 512 TMEM columns) owns the SM
-    const size_t smem = need > 120 * 1024 ? need : 120 * 1024;
-    cudaFuncSetAttribute(k_assign_tc<LK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    LBG_COUNTED k_assign_tc<LK><<<(unsigned)grid, TC_THREADS, smem, s>>>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign,
-                                                             e, flags, keymask, m_lo);
 }
 
 void launch_assign_tc(const float *X, int64_t M, int L, const void *Bp, const float *kn,

@@ -13,14 +13,21 @@
 // every floating-point sum has a fixed order, so two runs give identical bits.
 //   k_hist     per-chunk cell counts (integer shared-memory atomics) and
 //              per-chunk distortion partials (fixed-order tree, FP64 out);
-//   k_ctl      D = fixed-order FP64 sum of the chunk partials, stop test;
-//   k_scan     per cell, exclusive prefix of its chunk counts + cell size;
-//   k_offsets  exclusive prefix of the cell sizes (cell start offsets);
+//   k_ctl      D = fixed-order FP64 sum of the chunk partials, stop test
+//              (k_hist_ctl: both in one launch, its last CTA doing k_ctl);
+//   k_scan_offsets_q  per cell, exclusive prefix of its chunk counts + cell
+//              size; its last CTA: exclusive prefix of the cell sizes (cell
+//              start offsets), the cell of each warp piece's first row, empty
+//              cells' codevectors copied;
 //   k_scatter  stable placement of every row into perm[] (rows grouped by
 //              cell, original order inside a cell);
-//   k_cellsum  one warp per SEG consecutive perm entries: FP32 sums of the
-//              gathered rows per cell piece (coalesced 16-byte row reads);
-//   k_combine  per codevector: FP64 sum of its pieces in order / count.
+//   k_cellsum_c  one warp per S consecutive perm entries: FP32 sums of the
+//              gathered rows per cell piece (coalesced 16-byte row reads); a
+//              cell held by one piece is divided by its count at once, the
+//              last piece of a longer cell (per-cell counter) sums the cell's
+//              pieces in order in FP64 and divides.
+// The distortion backward keeps separate cell sums (k_cellsum_v4) and their
+// gradient combine (k_combine_grad).
 #include "lbg_internal.cuh"
 
 #include <math.h>
@@ -38,7 +45,7 @@ __device__ __forceinline__ bool skip_update(const DevState *st, int train)
     return train && (st->finished || st->action != ACT_UPDATE);
 }
 
-// The cell sizes and offsets (k_scan, k_offsets) are computed on every pass of
+// The cell sizes and offsets (k_scan_offsets_q) are computed on every pass of
 // a training run, also on a pass that ends its stage: the pass trace reports
 // the empty cells of every allocation.
 __device__ __forceinline__ bool skip_counts(const DevState *st, int train)
@@ -120,27 +127,36 @@ __device__ __forceinline__ void body_hist(const int32_t *__restrict__ assign,
     if (do_hist)
         for (int n = tid; n < N; n += HIST_THREADS) h[n] = 0;
     __syncthreads();
+    // a thread's rows m0 + tid, + 256, ... in batches of eight (all loads in
+    // flight at once); each batch is one FP32 run of eight added to the FP64 sum
     double acc = 0.0;
-    float run = 0.f;
-    int cnt = 0;
     bool clamped = false;
-    for (int64_t m = m0 + tid; m < m1; m += HIST_THREADS) {
-        if (do_hist) {
-            int a = assign[m];
-            if (a < 0 || a >= N) {
-                clamped = true;
-                a = a < 0 ? 0 : N - 1;
+    for (int64_t base = m0 + tid; base < m1; base += 8 * HIST_THREADS) {
+        int a[8];
+        float ev[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t m = base + (int64_t)u * HIST_THREADS;
+            const bool ok = m < m1;
+            a[u] = (ok && do_hist) ? assign[m] : 0;
+            ev[u] = ok ? e[m] : 0.f;
+        }
+        float run = 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (base + (int64_t)u * HIST_THREADS >= m1) break;
+            if (do_hist) {
+                int c = a[u];
+                if (c < 0 || c >= N) {
+                    clamped = true;
+                    c = c < 0 ? 0 : N - 1;
+                }
+                atomicAdd(&h[c], 1);
             }
-            atomicAdd(&h[a], 1);
+            run += ev[u];
         }
-        run += e[m];
-        if (++cnt == 8) {
-            acc += run;
-            run = 0.f;
-            cnt = 0;
-        }
+        acc += run;
     }
-    acc += run;
     if (clamped) flag_error(st, ERR_INTERNAL);
     red[tid] = acc;
     __syncthreads();
@@ -254,13 +270,6 @@ __device__ __forceinline__ void body_scan(int32_t *__restrict__ table, int CH, i
         }
 }
 
-__global__ void __launch_bounds__(1024) k_scan(int32_t *__restrict__ table, int CH,
-                                               const int32_t *n_dev, int n_host,
-                                               int32_t *__restrict__ counts, DevState *st, int train)
-{
-    if (skip_counts(st, train)) return;
-    body_scan(table, CH, cur_n(n_dev, n_host), counts, blockIdx.x);
-}
 
 // One CTA: off[n] = sum_{n' < n} counts[n'], off[N] = total.
 __device__ __forceinline__ void body_offsets(const int32_t *__restrict__ counts, int N,
@@ -296,13 +305,6 @@ __device__ __forceinline__ void body_offsets(const int32_t *__restrict__ counts,
     if (t == 1023) off[N] = run;
 }
 
-__global__ void __launch_bounds__(1024) k_offsets(const int32_t *__restrict__ counts,
-                                                  const int32_t *n_dev, int n_host,
-                                                  int32_t *__restrict__ off, DevState *st, int train)
-{
-    if (skip_counts(st, train)) return;
-    body_offsets(counts, cur_n(n_dev, n_host), off);
-}
 
 // ---------------------------------------------------------------- fused (step forms)
 // The last CTA to finish (a counter in the state; __threadfence before it, so
@@ -361,10 +363,12 @@ __device__ __forceinline__ void body_scatter(const int32_t *__restrict__ assign,
     for (int i = tid; i < 2 * N; i += 256) reinterpret_cast<int *>(wcnt)[i] = 0;
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
+    int a_next = (m0 + tid < m1) ? assign[m0 + tid] : 0;   // the next round's cell, loaded ahead
     for (int64_t base = m0; base < m1; base += 256) {
         const int64_t m = base + tid;
         const bool valid = m < m1;
-        int a = valid ? assign[m] : -1 - w;
+        int a = valid ? a_next : -1 - w;
+        a_next = (m + 256 < m1) ? assign[m + 256] : 0;
         if (valid && (a < 0 || a >= N)) a = a < 0 ? 0 : N - 1;   // same clamp as k_hist
         const unsigned peers = __match_any_sync(0xffffffffu, a);
         const int rank = __popc(peers & lt);
@@ -542,12 +546,203 @@ __device__ __forceinline__ void body_combine(const float *__restrict__ pieces,
     C_out[i] = (float)s / (float)(b - a);
 }
 
-__global__ void k_combine(const float *__restrict__ pieces, const int32_t *__restrict__ off,
-                          const int32_t *n_dev, int n_host, int L, int64_t S, const float *C_in,
-                          float *C_out, DevState *st, int train)
+
+// ---------------------------------------------------------------- fused update (step, train)
+// k_scan_offsets_q: per cell, the exclusive prefix of its chunk counts and the
+// cell size (body_scan); its last CTA then computes the cell offsets
+// (body_offsets) and, for the centroid kernel below, the cell holding the first
+// row of every warp piece (qcell[q] = the cell n with off[n] <= q S < off[n+1]),
+// zeroes the per-cell piece counters and copies the codevector of every empty
+// cell to C_out (an empty cell keeps its codevector) when C_out is not C_in.
+__global__ void __launch_bounds__(1024)
+    k_scan_offsets_q(int32_t *__restrict__ table, int CH, const int32_t *n_dev, int n_host,
+                     int32_t *__restrict__ counts, int32_t *__restrict__ off, int32_t *__restrict__ qcell,
+                     int32_t *__restrict__ cell_done, int64_t S, int L, const float *C_in, float *C_out,
+                     DevState *st, int train)
+{
+    if (skip_counts(st, train)) return;
+    const int N = cur_n(n_dev, n_host);
+    if ((int)blockIdx.x * 32 < N) body_scan(table, CH, N, counts, blockIdx.x);
+    if (!last_cta(st)) return;
+    if (threadIdx.x == 0) st->done_ctr = 0u;
+    body_offsets(counts, N, off);
+    __syncthreads();   // off[] complete (this CTA wrote it)
+    const bool copy = C_out != C_in && !skip_update(st, train);
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        const int64_t a = off[n], b = off[n + 1];
+        cell_done[n] = 0;
+        if (b == a) {
+            if (copy)
+                for (int l = 0; l < L; ++l) C_out[(int64_t)n * L + l] = C_in[(int64_t)n * L + l];
+            continue;
+        }
+        for (int64_t q = (a + S - 1) / S; q * S < b; ++q) qcell[q] = n;
+    }
+}
+
+// The centroid of cell n straight from its pieces: FP64 sum of the pieces in
+// order, divided by the count (the arithmetic of body_combine).
+__device__ __forceinline__ void combine_cell(const float *__restrict__ pieces, int n, int64_t a, int64_t b,
+                                             int64_t S, int L, float *__restrict__ C_out, int lane)
+{
+    const int64_t q0 = a / S, q1 = (b - 1) / S;
+    for (int l = lane; l < L; l += 32) {
+        double s = 0.0;
+        for (int64_t q = q0; q <= q1; ++q) s += (double)__ldcg(pieces + (size_t)(n + q) * L + l);
+        C_out[(int64_t)n * L + l] = (float)s / (float)(b - a);
+    }
+}
+
+// A cell piece is finished: a cell held by one piece is divided by its count at
+// once; otherwise the piece is stored (slot n + q), and the warp that stores
+// the cell's last piece (a per-cell counter, after a fence) combines them.
+// Both give the bits body_combine gives.
+template <int G>
+__device__ __forceinline__ void finish_piece_v4(float4 acc, int n, int64_t q, int64_t a, int64_t b, int64_t S,
+                                                float *__restrict__ pieces, int32_t *__restrict__ cell_done,
+                                                float *__restrict__ C_out, int lane)
+{
+    constexpr int L = 4 * G;
+    const int rs = lane / G, qd = lane % G;
+    const int64_t q0 = a / S, q1 = (b - 1) / S;
+    if (q0 == q1) {
+        if (rs == 0) {
+            const float cnt = (float)(b - a);
+            reinterpret_cast<float4 *>(C_out + (size_t)n * L)[qd] =
+                make_float4(acc.x / cnt, acc.y / cnt, acc.z / cnt, acc.w / cnt);
+        }
+        return;
+    }
+    if (rs == 0) reinterpret_cast<float4 *>(pieces + (size_t)(n + q) * L)[qd] = acc;
+    __threadfence();
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) last = atomicAdd(&cell_done[n], 1) == (int)(q1 - q0);
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence();
+    combine_cell(pieces, n, a, b, S, L, C_out, lane);
+    if (lane == 0) cell_done[n] = 0;
+}
+
+// Warp q sums perm[q S, (q + 1) S) cell piece by cell piece, as
+// body_cellsum_v4 (same order, same bits), starting from qcell[q] instead of a
+// search of the offsets, and finishes every piece with finish_piece_v4.
+template <int G>
+__device__ __forceinline__ void body_cellsum_c(const float *__restrict__ X, int64_t M,
+                                               const int32_t *__restrict__ perm,
+                                               const int32_t *__restrict__ off,
+                                               const int32_t *__restrict__ qcell, int N, int64_t S,
+                                               float *__restrict__ pieces, int32_t *__restrict__ cell_done,
+                                               float *__restrict__ C_out, int blk)
+{
+    constexpr int RPG = 32 / G;
+    const int64_t q = (int64_t)blk * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int64_t p0 = q * S;
+    if (p0 >= M) return;
+    const int64_t p1 = p0 + S < M ? p0 + S : M;
+    const int rs = lane / G, qd = lane % G;
+    const float4 *X4 = reinterpret_cast<const float4 *>(X);
+    int n = qcell[q];
+    int64_t p = p0;
+    while (p < p1) {
+        const int64_t a = off[n], b = off[n + 1];
+        const int64_t pe = b < p1 ? b : p1;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        int64_t pp = p + rs;
+        for (; pp + 7 * RPG < pe; pp += 8 * RPG) {   // eight rows in flight per lane
+            int r[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) r[u] = perm[pp + u * RPG];
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldg(X4 + (int64_t)r[u] * G + qd);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) add4(acc, v[u]);
+        }
+        for (; pp < pe; pp += RPG) add4(acc, __ldg(X4 + (int64_t)perm[pp] * G + qd));
+#pragma unroll
+        for (int o = G; o < 32; o <<= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+            acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+            acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+        }
+        finish_piece_v4<G>(acc, n, q, a, b, S, pieces, cell_done, C_out, lane);
+        p = pe;
+        while (n + 1 < N && off[n + 1] <= p) ++n;
+    }
+}
+
+template <int G>
+__global__ void __launch_bounds__(256)
+    k_cellsum_c(const float *__restrict__ X, int64_t M, const int32_t *__restrict__ perm,
+                const int32_t *__restrict__ off, const int32_t *__restrict__ qcell, const int32_t *n_dev,
+                int n_host, int64_t S, float *__restrict__ pieces, int32_t *__restrict__ cell_done,
+                float *__restrict__ C_out, DevState *st, int train)
 {
     if (skip_update(st, train)) return;
-    body_combine(pieces, off, cur_n(n_dev, n_host), L, S, C_in, C_out, blockIdx.x);
+    body_cellsum_c<G>(X, M, perm, off, qcell, cur_n(n_dev, n_host), S, pieces, cell_done, C_out, blockIdx.x);
+}
+
+// Any L: as body_cellsum_any (lanes own dims l = lane, lane + 32, ...), with
+// the pieces finished as above.
+__global__ void __launch_bounds__(256)
+    k_cellsum_c_any(const float *__restrict__ X, int64_t M, int L, const int32_t *__restrict__ perm,
+                    const int32_t *__restrict__ off, const int32_t *__restrict__ qcell,
+                    const int32_t *n_dev, int n_host, int64_t S, float *__restrict__ pieces,
+                    int32_t *__restrict__ cell_done, float *__restrict__ C_out, DevState *st, int train)
+{
+    if (skip_update(st, train)) return;
+    const int N = cur_n(n_dev, n_host);
+    const int64_t q = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int64_t p0 = q * S;
+    if (p0 >= M) return;
+    const int64_t p1 = p0 + S < M ? p0 + S : M;
+    int n = qcell[q];
+    int64_t p = p0;
+    while (p < p1) {
+        const int64_t a = off[n], b = off[n + 1];
+        const int64_t pe = b < p1 ? b : p1;
+        float acc[LMAX / 32] = {0.f, 0.f, 0.f, 0.f};
+        for (int64_t pp = p; pp < pe; ++pp) {
+            const int64_t r = perm[pp];
+#pragma unroll
+            for (int k = 0; k < LMAX / 32; ++k) {
+                const int l = lane + 32 * k;
+                if (l < L) acc[k] += __ldg(X + r * L + l);
+            }
+        }
+        const int64_t q0 = a / S, q1 = (b - 1) / S;
+        if (q0 == q1) {
+            const float cnt = (float)(b - a);
+#pragma unroll
+            for (int k = 0; k < LMAX / 32; ++k) {
+                const int l = lane + 32 * k;
+                if (l < L) C_out[(int64_t)n * L + l] = acc[k] / cnt;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < LMAX / 32; ++k) {
+                const int l = lane + 32 * k;
+                if (l < L) pieces[(size_t)(n + q) * L + l] = acc[k];
+            }
+            __threadfence();
+            __syncwarp();
+            int last = 0;
+            if (lane == 0) last = atomicAdd(&cell_done[n], 1) == (int)(q1 - q0);
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __threadfence();
+                combine_cell(pieces, n, a, b, S, L, C_out, lane);
+                if (lane == 0) cell_done[n] = 0;
+            }
+        }
+        p = pe;
+        while (n + 1 < N && off[n + 1] <= p) ++n;
+    }
 }
 
 // ---------------------------------------------------------------- backward
@@ -942,18 +1137,7 @@ void launch_scan_offsets(int32_t *table, int CH, int N, int32_t *counts, int32_t
     LBG_COUNTED k_scan_offsets<<<(N + 31) / 32, 1024, 0, s>>>(table, CH, N, counts, off, st);
 }
 
-void launch_scan(int32_t *table, int CH, const int32_t *n_dev, int n_host, int32_t *counts,
-                 DevState *st, bool train, cudaStream_t s)
-{
-    LBG_COUNTED k_scan<<<(n_host + 31) / 32, 1024, 0, s>>>(table, CH, n_dev, n_host, counts, st, train ? 1 : 0);
-}
 
-void launch_offsets(const int32_t *counts, const int32_t *n_dev, int n_host, int64_t M,
-                    int32_t *off, DevState *st, bool train, cudaStream_t s)
-{
-    (void)M;
-    LBG_COUNTED k_offsets<<<1, 1024, 0, s>>>(counts, n_dev, n_host, off, st, train ? 1 : 0);
-}
 
 void launch_scatter(const int32_t *assign, int64_t M, int64_t R, int CH, const int32_t *table,
                     const int32_t *off, const int32_t *n_dev, int n_host, int32_t *perm,
@@ -986,13 +1170,33 @@ void launch_cellsum(const float *X, int64_t M, int L, const int32_t *perm, const
     }
 }
 
-void launch_combine(const float *pieces, const int32_t *off, const int32_t *n_dev, int n_host,
-                    int L, int64_t S, const float *C_in, float *C_out, DevState *st, bool train,
-                    cudaStream_t s)
+void launch_scan_offsets_q(int32_t *table, int CH, const int32_t *n_dev, int n_host, int32_t *counts,
+                           int32_t *off, int32_t *qcell, int32_t *cell_done, int64_t S, int L,
+                           const float *C_in, float *C_out, DevState *st, bool train, cudaStream_t s)
 {
-    const int64_t total = (int64_t)n_host * L;
-    LBG_COUNTED k_combine<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(pieces, off, n_dev, n_host, L, S, C_in,
-                                                             C_out, st, train ? 1 : 0);
+    LBG_COUNTED k_scan_offsets_q<<<(n_host + 31) / 32, 1024, 0, s>>>(table, CH, n_dev, n_host, counts, off, qcell,
+                                                                   cell_done, S, L, C_in, C_out, st,
+                                                                   train ? 1 : 0);
+}
+void launch_cellsum_c(const float *X, int64_t M, int L, const int32_t *perm, const int32_t *off,
+                      const int32_t *qcell, const int32_t *n_dev, int n_host, int64_t S, float *pieces,
+                      int32_t *cell_done, float *C_out, DevState *st, bool train, cudaStream_t s)
+{
+    const int64_t warps = (M + S - 1) / S;
+    if (warps == 0) return;
+    const unsigned blocks = (unsigned)((warps + 7) / 8);
+    const int t = train ? 1 : 0;
+    const bool al = ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(C_out)) & 15u) == 0;
+    switch (al ? L : 0) {
+    case 4: LBG_COUNTED k_cellsum_c<1><<<blocks, 256, 0, s>>>(X, M, perm, off, qcell, n_dev, n_host, S, pieces, cell_done, C_out, st, t); break;
+    case 8: LBG_COUNTED k_cellsum_c<2><<<blocks, 256, 0, s>>>(X, M, perm, off, qcell, n_dev, n_host, S, pieces, cell_done, C_out, st, t); break;
+    case 16: LBG_COUNTED k_cellsum_c<4><<<blocks, 256, 0, s>>>(X, M, perm, off, qcell, n_dev, n_host, S, pieces, cell_done, C_out, st, t); break;
+    case 32: LBG_COUNTED k_cellsum_c<8><<<blocks, 256, 0, s>>>(X, M, perm, off, qcell, n_dev, n_host, S, pieces, cell_done, C_out, st, t); break;
+    case 64: LBG_COUNTED k_cellsum_c<16><<<blocks, 256, 0, s>>>(X, M, perm, off, qcell, n_dev, n_host, S, pieces, cell_done, C_out, st, t); break;
+    case 128: LBG_COUNTED k_cellsum_c<32><<<blocks, 256, 0, s>>>(X, M, perm, off, qcell, n_dev, n_host, S, pieces, cell_done, C_out, st, t); break;
+    default:
+        LBG_COUNTED k_cellsum_c_any<<<blocks, 256, 0, s>>>(X, M, L, perm, off, qcell, n_dev, n_host, S, pieces, cell_done, C_out, st, t);
+    }
 }
 
 void launch_b_mean(const BatchSet *sets, int S, const int32_t *pre_mean, int total_blocks, int L,

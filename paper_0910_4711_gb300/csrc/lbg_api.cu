@@ -65,7 +65,7 @@ struct Plan {
     int L = 0, Lp = 0, N = 0, NP = 0, CH = 0, G = 0, max_rec = 0;
     bool tc = false;   // tensor-core (BF16) allocation
     size_t state, rec, Cp, kn, CT, mu, Ccur, Calt, assign, e, flags, table, dpart, counts, off, perm,
-        pieces, mpart, Xs, Cin, Cout, Xhat, Bp, xpart_d, xpart_i, xcnt;
+        pieces, mpart, Xs, Cin, Cout, Xhat, Bp, xpart_d, xpart_i, xcnt, qcell, cell_done;
     size_t total = 0;
     size_t take(size_t bytes)
     {
@@ -124,6 +124,8 @@ Plan make_plan(int64_t M, int L, int N, int max_rec, bool host_X, bool need_assi
     p.off = p.take(sizeof(int32_t) * (size_t)(N + 1));
     p.perm = p.take(sizeof(int32_t) * (size_t)(M > 0 ? M : 1));
     p.pieces = p.take(sizeof(float) * (size_t)(N + p.nq) * L);
+    p.qcell = p.take(sizeof(int32_t) * (size_t)(p.nq > 0 ? p.nq : 1));
+    p.cell_done = p.take(sizeof(int32_t) * (size_t)N);
     p.mpart = p.take(sizeof(double) * (size_t)p.G * L);
     p.Xs = host_X ? p.take(sizeof(float) * (size_t)M * L) : 0;
     p.Cin = host_C ? p.take(sizeof(float) * (size_t)N * L) : 0;
@@ -370,21 +372,20 @@ void run_exact(const Call &c, const Plan &p, const float *X, const int32_t *n_de
                        c.at<int32_t>(p.xcnt), p.M, c.s);
 }
 
+// Cell table and centroids after the histogram: cell sizes, offsets and piece
+// cells in one launch, the stable placement, then the cell sums with the
+// centroid division folded in (three launches).
 void run_update(const Call &c, const Plan &p, const float *X, const int32_t *n_dev, int n_host,
                 DevState *st, const int32_t *assign, const float *C_in, float *C_out, bool train)
 {
     int32_t *table = c.at<int32_t>(p.table), *off = c.at<int32_t>(p.off);
-    if (!train && !n_dev) {
-        launch_scan_offsets(table, p.CH, n_host, c.at<int32_t>(p.counts), off, st, c.s);
-    } else {
-        launch_scan(table, p.CH, n_dev, n_host, c.at<int32_t>(p.counts), st, train, c.s);
-        launch_offsets(c.at<int32_t>(p.counts), n_dev, n_host, p.M, off, st, train, c.s);
-    }
+    int32_t *qcell = c.at<int32_t>(p.qcell), *done = c.at<int32_t>(p.cell_done);
+    launch_scan_offsets_q(table, p.CH, n_dev, n_host, c.at<int32_t>(p.counts), off, qcell, done, p.S, p.L,
+                          C_in, C_out, st, train, c.s);
     launch_scatter(assign, p.M, p.R, p.CH, table, off, n_dev, n_host, c.at<int32_t>(p.perm), st,
                    train, c.s);
-    launch_cellsum(X, p.M, p.L, c.at<int32_t>(p.perm), off, n_dev, n_host, p.S,
-                   c.at<float>(p.pieces), st, train, c.s);
-    launch_combine(c.at<float>(p.pieces), off, n_dev, n_host, p.L, p.S, C_in, C_out, st, train, c.s);
+    launch_cellsum_c(X, p.M, p.L, c.at<int32_t>(p.perm), off, qcell, n_dev, n_host, p.S,
+                     c.at<float>(p.pieces), done, C_out, st, train, c.s);
 }
 
 // 0 = FP32, 1 = tensor cores, <0 = error status

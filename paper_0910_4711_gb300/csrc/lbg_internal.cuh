@@ -278,19 +278,22 @@ void launch_scan_offsets(int32_t *table, int CH, int N, int32_t *counts, int32_t
                          cudaStream_t s);
 void launch_ctl(const double *dpart, int CH, DevState *st, int mode, double theta, int max_passes,
                 int N_target, PassRecord *records, int max_records, cudaStream_t s);
-void launch_scan(int32_t *table, int CH, const int32_t *n_dev, int n_host, int32_t *counts,
-                 DevState *st, bool train, cudaStream_t s);
-void launch_offsets(const int32_t *counts, const int32_t *n_dev, int n_host, int64_t M,
-                    int32_t *off, DevState *st, bool train, cudaStream_t s);
 void launch_scatter(const int32_t *assign, int64_t M, int64_t R, int CH, const int32_t *table,
                     const int32_t *off, const int32_t *n_dev, int n_host, int32_t *perm,
                     DevState *st, bool train, cudaStream_t s);
 void launch_cellsum(const float *X, int64_t M, int L, const int32_t *perm, const int32_t *off,
                     const int32_t *n_dev, int n_host, int64_t S, float *pieces, DevState *st,
                     bool train, cudaStream_t s);
-void launch_combine(const float *pieces, const int32_t *off, const int32_t *n_dev, int n_host,
-                    int L, int64_t S, const float *C_in, float *C_out, DevState *st, bool train,
-                    cudaStream_t s);
+// Fused update of the step and training forms: k_scan + k_offsets in one
+// launch that also builds qcell[q] (the cell of the first row of warp piece q),
+// zeroes cell_done[N] and copies empty cells to C_out; then the cell sums with
+// the centroid division folded in (the last piece of a cell combines it).
+void launch_scan_offsets_q(int32_t *table, int CH, const int32_t *n_dev, int n_host, int32_t *counts,
+                           int32_t *off, int32_t *qcell, int32_t *cell_done, int64_t S, int L,
+                           const float *C_in, float *C_out, DevState *st, bool train, cudaStream_t s);
+void launch_cellsum_c(const float *X, int64_t M, int L, const int32_t *perm, const int32_t *off,
+                      const int32_t *qcell, const int32_t *n_dev, int n_host, int64_t S, float *pieces,
+                      int32_t *cell_done, float *C_out, DevState *st, bool train, cudaStream_t s);
 void launch_split(const float *C_cur, float *C_alt, int N_alloc, int L, double delta, bool mult,
                   DevState *st, cudaStream_t s);
 void launch_reseed(const int32_t *off, const int32_t *n_dev, int n_host, int L, double delta,

@@ -32,8 +32,10 @@ import numpy as np
 import pytest
 
 U = Fraction(1, 2 ** 24)
-NT, HALF, GRP, JBITS = 144, 72, 8, 4   # codevectors per tile, per half, per group; group index bits
-PACK = Fraction(1, 2 ** 19)         # packing moves a group minimum by less than this fraction
+NT, HALF = 144, 72                  # codevectors per tile, per half
+# group size -> bits of the in-half group index; packing moves a group minimum by less than
+# 2^(JBITS - 23) of it (at most 2^JBITS - 1 units in the last place)
+JBITS = {2: 6, 8: 4}
 
 
 def round_bits(x: Fraction, p: int, up: bool = False) -> Fraction:
@@ -89,16 +91,17 @@ def test_rounding_helpers():
     np.testing.assert_array_equal(bf16_rne(ties), [256.0, 260.0, -256.0, 1.0, 1.0 + 2.0 ** -6])
 
 
-def _f32bits_key(lo: np.float32, j: int) -> np.float32:
+def _f32bits_key(lo: np.float32, j: int, jbits: int) -> np.float32:
     b = np.array([lo], np.float32).view(np.uint32)
-    b = (b & np.uint32(~((1 << JBITS) - 1) & 0xFFFFFFFF)) | np.uint32(j)
+    b = (b & np.uint32(~((1 << jbits) - 1) & 0xFFFFFFFF)) | np.uint32(j)
     return b.view(np.float32)[0]
 
 
-def _epilogue(v):
+def _epilogue(v, GRP):
     """Top-2 of the kernel's epilogue over one row's FP32 accumulator values v
-    (length a multiple of NT): (V1, V2, i1), V1 the smallest value, V2 the
-    smallest outside V1's group, i1 the first column of V1's group."""
+    (length a multiple of NT), groups of GRP columns: (V1, V2, i1), V1 the
+    smallest value, V2 the smallest outside V1's group, i1 the first column of
+    V1's group."""
     nt = len(v) // NT
     halves = []
     for h in range(2):
@@ -109,13 +112,13 @@ def _epilogue(v):
                 q = j % 2
                 base = t * NT + h * HALF + GRP * j
                 lo = np.float32(min(v[base:base + GRP]))
-                k = _f32bits_key(lo, j)
+                k = _f32bits_key(lo, j, JBITS[GRP])
                 c2[q] = min(c2[q], max(c1[q], k))
                 c1[q] = min(c1[q], k)
             for q in range(2):
                 if c1[q] < s1[q]:
                     cg[q] = t
-        jm = (1 << JBITS) - 1
+        jm = (1 << JBITS[GRP]) - 1
         V1, V2 = c1[0], c2[0]
         i1 = cg[0] * NT + h * HALF + GRP * (int(np.array([c1[0]]).view(np.uint32)[0]) & jm)
         iq = cg[1] * NT + h * HALF + GRP * (int(np.array([c1[1]]).view(np.uint32)[0]) & jm)
@@ -153,17 +156,18 @@ def _ints(arrays):
     return out, S
 
 
-def _epilogue_worst(v, best):
+def _epilogue_worst(v, best, GRP):
     """The epilogue's top-2 of group minima in exact arithmetic with its one
     rounding effect at its worst: a group minimum moved by its packing (at most
-    15 units in the last place of an FP32 value, < 2^-19 of it), up for the
-    exact winner's group and down for every other group.  Returns (V1, V2, i1)."""
+    2^JBITS - 1 units in the last place of an FP32 value, < 2^(JBITS - 23) of
+    it), up for the exact winner's group and down for every other group.
+    Returns (V1, V2, i1)."""
     c1 = c2 = None
     i1 = -1
     for g in range(len(v) // GRP):
         lo = min(v[GRP * g:GRP * g + GRP])
         s = 1 if GRP * g <= best < GRP * g + GRP else -1
-        k = lo + s * Fraction(15, 2 ** 23) * abs(lo)
+        k = lo + s * Fraction((1 << JBITS[GRP]) - 1, 2 ** 23) * abs(lo)
         if c1 is None:
             c1, c2, i1 = k, Fraction(10) ** 40, GRP * g
             continue
@@ -173,7 +177,7 @@ def _epilogue_worst(v, best):
     return c1, c2, i1
 
 
-def certify(x, C, mu, N, adversarial=True, worst=False, weights=None):
+def certify(x, C, mu, N, adversarial=True, worst=False, weights=None, GRP=2):
     """Run one row through the model and the two certificates.  With
     worst=True every bounded quantity is at the end of its bound that favours
     a wrong answer (see test_bf16_certificates_sound_at_every_bound).
@@ -248,11 +252,11 @@ def certify(x, C, mu, N, adversarial=True, worst=False, weights=None):
         v.append(np.float32(float(val)))
     if worst:
         v += [Fraction(2) ** 100] * (-(-N // GRP) * GRP - N)
-        V1, V2, i1 = _epilogue_worst(v, best)
+        V1, V2, i1 = _epilogue_worst(v, best, GRP)
     else:
         npad = -(-N // NT) * NT
         v += [np.float32(2.0 ** 100)] * (npad - N)
-        V1, V2, i1 = _epilogue(v)
+        V1, V2, i1 = _epilogue(v, GRP)
         V1, V2 = Fraction(float(V1)), Fraction(float(V2))
 
     # FP32 direct-form distances of the group, at the worst end of their bound
@@ -270,7 +274,7 @@ def certify(x, C, mu, N, adversarial=True, worst=False, weights=None):
     ka = max(kp[n] for n in members)        # k' of V1's member is only known to be <= this
     R = 2 * tau * X2
     eta = U * (sqrt_up(Fraction(X2)) + cmax)
-    pack = PACK * (abs(V1) + abs(V2))
+    pack = Fraction(1, 2 ** (23 - JBITS[GRP])) * (abs(V1) + abs(V2))
     xerr = (L + 2) * U * X2
     g1 = sqrt_up(V1 + 2 * ka + R + pack + E + xerr)
     margin = (wt["m_R"] * 2 * R + wt["m_k"] * 2 * ka + wt["m_pack"] * pack + wt["m_E"] * 2 * E
@@ -321,26 +325,28 @@ def _rows(rng, L, N, spread, trials, family="near"):
         yield x, C, mu
 
 
+@pytest.mark.parametrize("GRP", [2, 8])
 @pytest.mark.parametrize("L,spread,family", [(16, 20.0, "near"), (16, 2.0, "near"),
                                               (64, 20.0, "near"), (64, 2.0, "near"),
                                               (16, 0.5, "mirror"), (64, 0.5, "mirror")])
-def test_bf16_certificates_sound_at_the_model_bound(L, spread, family):
+def test_bf16_certificates_sound_at_the_model_bound(L, spread, family, GRP):
     rng = np.random.default_rng(L + int(spread))
     N = NT
     trials = 60 if L == 64 else 120
     accepted = 0
     for x, C, mu in _rows(rng, L, N, spread, trials, family):
-        ok, ii, best = certify(x, C, mu, N)
+        ok, ii, best = certify(x, C, mu, N, GRP=GRP)
         if ok:
             accepted += 1
             assert ii == best, (ii, best)
     assert accepted > 0
 
 
+@pytest.mark.parametrize("GRP", [2, 8])
 @pytest.mark.parametrize("L,spread,family", [(16, 20.0, "near"), (16, 2.0, "near"),
                                               (64, 20.0, "near"), (64, 2.0, "near"),
                                               (16, 0.5, "mirror"), (64, 0.5, "mirror")])
-def test_bf16_certificates_sound_at_every_bound(L, spread, family):
+def test_bf16_certificates_sound_at_every_bound(L, spread, family, GRP):
     """The proof uses each error only through its bound, so it must hold with
     every error at the end of its bound that favours a wrong answer: the
     accumulation error (model), the missed term x~.r_n anywhere in
@@ -353,32 +359,35 @@ def test_bf16_certificates_sound_at_every_bound(L, spread, family):
     trials = 60 if L == 64 else 120
     accepted = 0
     for x, C, mu in _rows(rng, L, N, spread, trials, family):
-        ok, ii, best = certify(x, C, mu, N, worst=True)
+        ok, ii, best = certify(x, C, mu, N, worst=True, GRP=GRP)
         if ok:
             accepted += 1
             assert ii == best, (ii, best)
     assert accepted > 0
 
 
-@pytest.mark.parametrize("weights", [{"m_R": 0}, {"m_R": 0.5}, {"m_k": 0}, {"m_k": 0.5},
-                                     {"m_E": 0}, {"m_E": 0.5},
-                                     {"lb_R": 0}, {"lb_E": 0}, {"lb_E": 0.5}, {"lb_pack": 0}])
-def test_bf16_certificate_terms_are_needed(weights):
+@pytest.mark.parametrize("GRP,weights", [(2, w) for w in ({"m_R": 0}, {"m_R": 0.5}, {"m_k": 0},
+                                                          {"m_k": 0.5}, {"m_pack": 0}, {"m_pack": 0.5},
+                                                          {"m_E": 0}, {"m_E": 0.5}, {"lb_R": 0},
+                                                          {"lb_E": 0}, {"lb_E": 0.5}, {"lb_pack": 0})] +
+                                         [(8, w) for w in ({"m_R": 0}, {"m_k": 0}, {"m_E": 0},
+                                                          {"lb_R": 0}, {"lb_E": 0}, {"lb_pack": 0})])
+def test_bf16_certificate_terms_are_needed(GRP, weights):
     """With every error at its worst (as above), dropping or halving one term of
     the first certificate's margin, or dropping one of the second's lower bound,
     lets a wrong row through in one of the row families.  (Not shown this way:
     the eta terms, never binding here since x~ is exact for integer mu; halving
     R' in the second certificate, whose packing term leaves that much slack;
-    the first certificate's packing term, 2^-19 (|V1| + |V2|), for which the
-    group's largest k' -- it stands in for the unknown k' of V1's member --
-    leaves more room than that in these families.)"""
+    with groups of eight, the first certificate's packing term, 2^-19 (|V1| +
+    |V2|), for which the group's largest k' -- it stands in for the unknown k'
+    of V1's member -- leaves more room than that in these families.)"""
     params = [(16, 20.0, "near"), (16, 2.0, "near"), (64, 20.0, "near"), (64, 2.0, "near"),
               (16, 0.5, "mirror"), (64, 0.5, "mirror")]
     for L, spread, family in params:
         rng = np.random.default_rng(100 + L + int(spread))
         trials = 60 if L == 64 else 120
         for x, C, mu in _rows(rng, L, NT, spread, trials, family):
-            ok, ii, best = certify(x, C, mu, NT, worst=True, weights=weights)
+            ok, ii, best = certify(x, C, mu, NT, worst=True, weights=weights, GRP=GRP)
             if ok and ii != best:
                 return
     pytest.fail(f"weights {weights}: no wrong row accepted")
@@ -394,11 +403,13 @@ def test_bf16_certificates_accept_clear_winners():
     mu = np.rint(C.mean(0)).astype(np.float32)
     for n in rng.choice(N, 20, replace=False):
         x = np.clip(np.rint(C[n] + rng.standard_normal(L)), 0, 255).astype(np.float32)
-        ok, ii, best = certify(x, C, mu, N)
-        assert ok and ii == best == n
+        for GRP in (2, 8):
+            ok, ii, best = certify(x, C, mu, N, GRP=GRP)
+            assert ok and ii == best == n
 
 
-def test_bf16_certificates_resolve_split_twins():
+@pytest.mark.parametrize("GRP", [2, 8])
+def test_bf16_certificates_resolve_split_twins(GRP):
     """Right after a split every codevector has a twin at 2 delta (children 2i and 2i + 1 of
     the same parent).  Twins share a group, so the second-best value the certificates use
     comes from the next parent, and the twins themselves are told apart by their exact
@@ -414,7 +425,7 @@ def test_bf16_certificates_resolve_split_twins():
     accepted = 0
     for n in rng.choice(N // 2, 24, replace=False):
         x = np.clip(np.rint(parents[n] + 3 * rng.standard_normal(L)), 0, 255).astype(np.float32)
-        ok, ii, best = certify(x, C, mu, N)
+        ok, ii, best = certify(x, C, mu, N, GRP=GRP)
         if ok:
             accepted += 1
             assert ii == best and best // 2 == n

@@ -12,13 +12,17 @@ and claims (the proof in the header of the kernel source)
 
     v_n - R <= f_n <= v_n + 2 k_n + R,   f_n = ||c~_n||^2 - 2 x~.c~_n,  R = (L+2) u ||x~||^2,
 
-so that V2 - V1 > 2R + 2k_i1 + 4 eta (g1 + eta), with eta = u (||x~|| + max ||c~||)
-and g1 >= ||x~ - c~_i1||, proves that i1 is the exact argmin of ||x - c_n|| over
-the original FP32 values.  These tests emulate that chain with every FMA
-rounded exactly (integer arithmetic, round to nearest even), then check the
-bound against the exact f_n and, on constructed near-ties, that every row the
-certificate accepts has the exact (rational) argmin.  They test the
-mathematics of the certificate; the GPU parity tests test the kernel.
+so that, with the codevectors taken in split pairs (2k, 2k + 1), V1 = v_i1 the
+minimum and V2 the smallest value outside i1's pair, V2 - V1 > 2R + 2k_pair +
+4 eta (g1 + eta) (k_pair the larger k of the pair, eta = u (||x~|| + max ||c~||),
+g1 >= ||x~ - c~_i1||) proves that the exact argmin of ||x - c_n|| over the
+original FP32 values is a member of that pair; the members' FP32 direct-form
+distances then decide when they differ by more than their rounding bound.
+These tests emulate that chain with every FMA rounded exactly (integer
+arithmetic, round to nearest even), then check the bound against the exact f_n
+and, on constructed near-ties, that every row the certificate accepts has the
+exact (rational) argmin.  They test the mathematics of the certificate; the GPU
+parity tests test the kernel.
 """
 import math
 from fractions import Fraction
@@ -149,24 +153,57 @@ def test_chain_error_within_certificate_bound(L, scale, offset):
             assert Fraction(v) - R <= f <= Fraction(v) + 2 * Fraction(k) + R
 
 
+def _pair_top2(vals):
+    """(i1, V1, V2): the minimum, its index (lowest on ties) and the smallest
+    value outside i1's split pair (2k, 2k + 1)."""
+    i1 = min(range(len(vals)), key=lambda n: (vals[n], n))
+    out = [vals[n] for n in range(len(vals)) if n // 2 != i1 // 2]
+    return i1, vals[i1], (min(out) if out else Fraction(10) ** 60)
+
+
+def direct32(x, c):
+    """The FP32 direct-form distance sum_l (x_l - c_l)^2 in index order (FMA)."""
+    d = 0.0
+    for a, b in zip(x, c):
+        t = float(np.float32(a) - np.float32(b))
+        d = fma32(t, t, d)
+    return d
+
+
+def _resolve(i1, N, dist, L):
+    """The member of i1's pair with the smaller direct-form distance when the two
+    differ by more than (L + 4) u (da + db); None when they do not."""
+    ip = i1 ^ 1
+    if ip >= N:
+        return i1
+    da, db = Fraction(dist(i1)), Fraction(dist(ip))
+    tol = (L + 4) * U * (da + db)
+    if db < da - tol:
+        return ip
+    return i1 if da < db - tol else None
+
+
 def _certify(x_orig, C_orig, mu, L):
-    """(certified, i1) from the emulated chain and the certificate's margin,
-    evaluated in exact arithmetic (the kernel evaluates it in FP32 with a
-    2^-15 relative slack)."""
+    """(certified, chosen index) from the emulated chain and the certificate's
+    margin, evaluated in exact arithmetic (the kernel evaluates it in FP32 with
+    a 2^-15 relative slack), then the pair resolved by FP32 direct distances."""
     (xt,), ct = centred([x_orig], C_orig, mu)
     vk = chain(xt, ct, L)
     vals = [Fraction(v) for v, _ in vk]
-    order = sorted(range(len(vals)), key=lambda n: (vals[n], n))
-    i1 = order[0]
-    V1, V2 = vals[i1], vals[order[1]]
+    N = len(vals)
+    i1, V1, V2 = _pair_top2(vals)
     xn2 = sum(Fraction(v) ** 2 for v in xt)
     R = (L + 2) * U * xn2
     cmax = max(math.sqrt(sum(t * t for t in c)) for c in ct)
     eta = U * Fraction(math.sqrt(float(xn2)) * (1 + 2 ** -50) + cmax * (1 + 2 ** -50))
     g1 = Fraction(math.sqrt(float(sum((Fraction(a) - Fraction(b)) ** 2
                                       for a, b in zip(xt, ct[i1])))) * (1 + 2 ** -50))
-    margin = 2 * R + 2 * Fraction(vk[i1][1]) + 4 * eta * (g1 + eta)
-    return V2 - V1 > margin, i1
+    kp = max(Fraction(vk[n][1]) for n in (i1, i1 ^ 1) if n < N)
+    margin = 2 * R + 2 * kp + 4 * eta * (g1 + eta)
+    if not V2 - V1 > margin:
+        return False, i1
+    win = _resolve(i1, N, lambda n: direct32(x_orig, C_orig[n]), L)
+    return (win is not None), (i1 if win is None else win)
 
 
 @pytest.mark.parametrize("family", ["pair_near_row", "pair_far_row_at_mu", "mu_far_from_row"])
@@ -236,17 +273,21 @@ def _worst_case_margin_check(x, C, mu, L, weights=(1, 1, 1)):
         k = Fraction(f32_of(2 * (L + 2) * U * sq, up=True))
         f = sq - 2 * sum(a * t for a, t in zip(xq, cq))
         v.append((f + R, k) if n == b else (f - 2 * k - R, k))
-    order = sorted(range(len(v)), key=lambda n: (v[n][0], n))
-    i1 = order[0]
-    V1, V2 = v[i1][0], v[order[1]][0]
+    N = len(v)
+    i1, V1, V2 = _pair_top2([t[0] for t in v])
     cmax = max(math.sqrt(sum(t * t for t in c)) for c in ct)
     eta = U * Fraction(math.sqrt(float(xn2)) * (1 + 2 ** -50) + cmax * (1 + 2 ** -50))
     g1 = Fraction(math.sqrt(float(sum((a - Fraction(t)) ** 2 for a, t in zip(xq, ct[i1]))))
                   * (1 + 2 ** -50))
     wR, wk, we = (Fraction(w) for w in weights)
-    margin = wR * 2 * R + wk * 2 * v[i1][1] + we * 4 * eta * (g1 + eta)
+    kp = max(v[n][1] for n in (i1, i1 ^ 1) if n < N)
+    margin = wR * 2 * R + wk * 2 * kp + we * 4 * eta * (g1 + eta)
     if V2 - V1 > margin:
-        ok = i1 == b and exact[b] < min(e for n, e in enumerate(exact) if n != b)
+        # the pair's direct-form distances at the worst end of their rounding bound
+        win = _resolve(i1, N, lambda n: exact[n] * (1 + (L + 2) * U if n == b else 1 - (L + 2) * U), L)
+        if win is None:
+            return "refused"
+        ok = win == b and exact[b] < min(e for n, e in enumerate(exact) if n != b)
         return "right" if ok else "wrong"
     return "refused"
 
@@ -316,3 +357,28 @@ def test_certificate_accepts_clear_winners():
         x = (C[n] + rng.standard_normal(L)).astype(np.float32)
         ok, i1 = _certify(x, C, mu, L)
         assert ok and i1 == n
+
+
+def test_certificate_resolves_split_twins():
+    """Right after a split every codevector has a twin at 2 delta (children 2i, 2i + 1).
+    A row near one parent has the two twins as its nearest codevectors; they share a pair,
+    so the bound is taken against the next parent and the twins are told apart by their
+    exact distances: the row is certified with its exact nearest twin."""
+    rng = np.random.default_rng(12)
+    L = 16
+    parents = (128 + 50 * rng.standard_normal((8, L))).astype(np.float32)
+    C = np.empty((16, L), np.float32)
+    C[0::2] = parents + np.float32(0.01)
+    C[1::2] = parents - np.float32(0.01)
+    mu = C.mean(0, dtype=np.float32)
+    accepted = 0
+    for n in range(8):
+        for _ in range(3):
+            x = (parents[n] + 2 * rng.standard_normal(L)).astype(np.float32)
+            ok, i1 = _certify(x, C, mu, L)
+            exact = [sum((Fraction(float(a)) - Fraction(float(b))) ** 2 for a, b in zip(x, c)) for c in C]
+            best = min(range(16), key=lambda k: (exact[k], k))
+            if ok:
+                accepted += 1
+                assert i1 == best and best // 2 == n
+    assert accepted >= 20
