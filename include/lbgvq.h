@@ -109,6 +109,7 @@ typedef struct lbg_tune_report {
     int32_t cand_ctas_per_sm[8];
     float cand_ms[8];             /* device time of one batched assignment of all problems at
                                      their final codebook sizes, per candidate (best of 2) */
+    int32_t persistent;           /* 1: each pass ran as one persistent cooperative launch */
 } lbg_tune_report;
 
 /* Device-side report of an enqueued lbg_lloyd_step / vq_encode (see
@@ -173,6 +174,11 @@ typedef struct lbg_opts {
                                    reports; the call returns LBG_ERR_TIMEOUT.  Such calls are
                                    launched directly, never recorded into a graph.  Ignored by the
                                    other entry points and by LBG_PREC_BF16. */
+    int32_t batched_per_phase;  /* lbg_train_batched: 0 (default) runs each Lloyd pass of all
+                                   problems as one persistent cooperative launch (phases
+                                   separated by bounded grid-wide barriers); 1 issues one
+                                   launch per phase (the tile options and the autotuner apply
+                                   only there).  Results do not depend on it. */
     const float *grad_scale_dev; /* lbg_distortion_backward: DEVICE float or NULL.  When set, the
                                     upstream gradient is read from it on the device and the gD
                                     argument is ignored (an autograd caller then needs no host
@@ -247,8 +253,12 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
 /*
  * lbg_train_batched -- S independent LBG designs (Sec. 2.2 + Algorithm 1, as
  * lbg_train) of uneven sizes, advanced together: every Lloyd pass of all
- * problems is one captured sequence of launches, the nearest-codevector
- * search one persistent launch over (problem, row tile) work items.
+ * problems is one persistent cooperative launch (its phases separated by
+ * bounded grid-wide barriers, the nearest-codevector search over (problem,
+ * row tile) work items), recorded into a CUDA graph and replayed.  When the
+ * device cannot hold that launch (shared memory for large L and N), or with
+ * opts->batched_per_phase, a pass is a recorded sequence of one launch per
+ * phase instead.
  *
  *   S        number of problems, >= 1.
  *   X        rows of all problems concatenated in problem order, [sum M_s x L]
@@ -260,8 +270,10 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
  *   assign   [sum M_s] out, nullable: each problem's cell table (indices local
  *            to its codebook).
  *   D        HOST [S] out, nullable: each problem's final distortion.
- * opts: stream, max_passes, split_multiplicative are honoured; precision must
- * be LBG_PREC_FP32; n_records receives the largest pass count of a problem.
+ * opts: stream, max_passes, split_multiplicative, batched_per_phase, the tile
+ * options are honoured; precision must be LBG_PREC_FP32; n_records receives the
+ * largest pass count of a problem; tune_report gives the tile used (128 rows,
+ * resident CTAs per SM of the persistent launch, when that form ran).
  * Per problem the results are those lbg_train would give.
  */
 lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, int32_t L,

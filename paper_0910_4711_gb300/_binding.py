@@ -47,12 +47,12 @@ class TuneReport(ctypes.Structure):
     _fields_ = [("tile_rows", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("from_cache", ctypes.c_int32), ("n_candidates", ctypes.c_int32),
                 ("cand_tile_rows", ctypes.c_int32 * 8), ("cand_ctas_per_sm", ctypes.c_int32 * 8),
-                ("cand_ms", ctypes.c_float * 8)]
+                ("cand_ms", ctypes.c_float * 8), ("persistent", ctypes.c_int32)]
 
     def as_dict(self):
         n = self.n_candidates
         return {"tile_rows": self.tile_rows, "ctas_per_sm": self.ctas_per_sm,
-                "from_cache": bool(self.from_cache),
+                "from_cache": bool(self.from_cache), "persistent": bool(self.persistent),
                 "candidates": [{"tile_rows": self.cand_tile_rows[k],
                                 "ctas_per_sm": self.cand_ctas_per_sm[k], "ms": self.cand_ms[k]}
                                for k in range(n)]}
@@ -71,7 +71,7 @@ class Opts(ctypes.Structure):
                 ("result_dev", ctypes.c_void_p),
                 ("trace_C", ctypes.c_void_p), ("trace_assign", ctypes.c_void_p),
                 ("trace_cap", ctypes.c_int32), ("test_expire_wait", ctypes.c_int32),
-                ("grad_scale_dev", ctypes.c_void_p)]
+                ("batched_per_phase", ctypes.c_int32), ("grad_scale_dev", ctypes.c_void_p)]
 
 
 STEP_RESULT_BYTES = 16   # lbg_step_result: double D, int32 n_exact, int32 status
@@ -426,11 +426,12 @@ class BatchedResult:
 def lbg_train_batched(X, row_off, N, delta: float = 0.01, theta: float = 1e-3,
                       max_passes: int = 1000, phase_ms: bool = False, stream=None,
                       split_multiplicative: bool = False, autotune: bool = True,
-                      tile_rows: int = 0, ctas_per_sm: int = 0) -> BatchedResult:
+                      tile_rows: int = 0, ctas_per_sm: int = 0, per_phase: bool = False) -> BatchedResult:
     """S independent LBG designs at once (see lbg_train_batched in lbgvq.h).  X holds the rows
     of all problems concatenated; row_off (S+1 offsets) and N (S sizes) are Python sequences.
     The tile of the batched nearest-codevector launch is autotuned (or forced with tile_rows /
-    ctas_per_sm); the choice is in the result's ``tune``."""
+    ctas_per_sm); the choice is in the result's ``tune``.  Each pass is one persistent launch
+    unless per_phase (or a forced tile) asks for one launch per phase."""
     Xo, xp, _ = _prep(X, "f32", "X")
     L = int(X.shape[1])
     S = len(N)
@@ -452,6 +453,7 @@ def lbg_train_batched(X, row_off, N, delta: float = 0.01, theta: float = 1e-3,
     o.autotune = int(bool(autotune))
     o.tile_rows = int(tile_rows)
     o.ctas_per_sm = int(ctas_per_sm)
+    o.batched_per_phase = int(bool(per_phase))
     rep = TuneReport()
     o.tune_report = ctypes.pointer(rep)
     rc = _check(lib().lbg_train_batched(S, xp, ro.ctypes.data, L, Nn.ctypes.data, float(delta),

@@ -144,10 +144,6 @@ static_assert(TC_HALF == 72 && GrpCfg<2>::GROUPS * 2 == TC_HALF && GrpCfg<8>::GR
 constexpr float U32 = 5.9604644775390625e-8f;   // 2^-24
 constexpr float SLOP = 1.0000305175781250f;     // 1 + 2^-15
 
-__device__ __forceinline__ int cur_n(const int32_t *n_dev, int n_host)
-{
-    return n_dev ? *n_dev : n_host;
-}
 
 // Byte offset of element (row, k) in the canonical K-major, no-swizzle
 // layout: 8-row x 16-byte core matrices; core matrices along K are 128 bytes

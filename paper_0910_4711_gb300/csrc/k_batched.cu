@@ -1,0 +1,330 @@
+// k_batched.cu -- one Lloyd pass of every problem of lbg_train_batched in a
+// single persistent launch.
+//
+// Paper: the LBG iteration of Sec. 2.2 (and Algorithm 1's Cell Allocation,
+// IntegrateDistortions, stop test, Updation and Codebook Splitting), run for
+// S independent training sets at once; each set computes exactly what
+// lbg_train computes for it alone.
+//
+// GB300 design.  The phases of a pass depend on one another across the whole
+// grid (the cell table needs every row's cell, the offsets every cell's
+// count, ...), so they are separated by grid-wide barriers inside one
+// cooperative launch (all CTAs resident), instead of one launch per phase:
+//   0  reset: assignment work counter, per-problem max ||c~||
+//   1  codebook preparation (per problem, 32-codevector blocks)
+//   2  nearest codevector: CTAs take (problem, 128-row tile) items from a counter
+//   3  exact re-scoring of the uncertified rows (groups of 8 rows, all problems)
+//   4  per-chunk cell counts and distortion partials; the last block of a
+//      problem runs its stop test (sum in chunk order, (D_prev - D)/D <= theta)
+//   5  per-cell prefix over chunks; the last block of a problem computes its
+//      cell offsets and the cell of every warp piece
+//   6  stable placement of the rows by cell
+//   7  cell sums with the centroid division folded in (in place)
+//   8  split of a finished stage into the spare codebook
+//   9  copy back; the last block of a problem advances its stage
+// A phase's blocks are virtual: CTA b takes blocks b, b + grid, ... of the
+// launch-per-phase form and runs the same device body on each, so the bits
+// are those of lbg_train.  "Last block of a problem" is a per-problem counter
+// in its device state, reset by the block that finishes it.
+//
+// Every barrier wait is bounded (%globaltimer, 2 s): a CTA that gives up sets
+// the shared abort word and reports LBG_ERR_TIMEOUT in every problem's state;
+// every other CTA sees the abort word at its next barrier and returns.  The
+// abort word stays set for the rest of the call, so later passes return at
+// once and the host stops at its next check.
+#include "bodies_assign.cuh"
+#include "bodies_update.cuh"
+#include "lbg_internal.cuh"
+
+namespace lbg {
+namespace {
+
+constexpr int BP_THREADS = 256;
+
+// Grid-wide barrier: arrivals counted in bar[0]; the last arrival resets the
+// count and bumps the generation bar[1], for which the others wait (bounded).
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, const BatchSet *sets, int S)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *gen = bar + 1;
+        volatile unsigned *abort_word = bar + 2;
+        if (*abort_word) {
+            ok = 0;
+        } else {
+            const unsigned g = *gen;
+            __threadfence();
+            if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+                atomicExch(bar, 0u);
+                __threadfence();
+                atomicAdd(bar + 1, 1u);
+            } else {
+                const uint64_t t0 = global_ns();
+                while (*gen == g) {
+                    if (*abort_word) {
+                        ok = 0;
+                        break;
+                    }
+                    if (global_ns() - t0 > 2000000000ull) {
+                        atomicExch(bar + 2, 1u);
+                        for (int s = 0; s < S; ++s) flag_error(sets[s].st, ERR_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(100);
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// True in the one CTA whose arrival completes `count` arrivals on the
+// problem's counter (which it resets); every CTA's earlier writes are visible
+// to it.
+__device__ __forceinline__ bool last_block(DevState *st, unsigned count)
+{
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_last = atomicAdd(&st->done_ctr, 1u) == count - 1;
+        if (s_last) st->done_ctr = 0u;
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last != 0;
+}
+
+__device__ __forceinline__ void abort_all(unsigned *bar) { atomicExch(bar + 2, 1u); }
+
+template <int G>
+__device__ __forceinline__ void cellsum_phase(const BatchPass &a, const BatchSet &q, int b)
+{
+    body_cellsum_c<G>(q.X, q.M, q.perm, q.off, q.qcell, q.st->n_cur, q.S, q.pieces, q.cell_done, q.C, b);
+}
+
+__global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
+{
+    extern __shared__ __align__(128) float dsm[];   // each phase's dynamic shared memory
+    __shared__ AssignSmemT<BM> ash;
+    __shared__ __align__(16) ExactSmem esh;
+    __shared__ int64_t s_item;
+    __shared__ int s_total;
+    const BatchSet *sets = a.sets;
+    const int S = a.S, tid = threadIdx.x;
+    const int grid = (int)gridDim.x;
+
+    // 0: reset; the shared-memory barriers of the assignment and exact phases
+    if (tid == 0) {
+        mbar_init(&ash.bar[0], 1);
+        mbar_init(&ash.bar[1], 1);
+        ash.abort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    exact_init(esh);
+    if (blockIdx.x == 0) {
+        if (tid == 0) *a.counter = 0;
+        for (int s = tid; s < S; s += BP_THREADS) sets[s].st->cmax_bits = 0u;
+    }
+    if (!grid_barrier(a.bar, sets, S)) return;
+
+    // 1: codebook preparation
+    for (int vb = blockIdx.x; vb < a.tot_prep; vb += grid) {
+        const int s = find_set(a.pre_prep, S, vb);
+        const BatchSet &q = sets[s];
+        if (!q.st->finished)
+            body_prep(q.C, q.st->n_cur, a.L, a.Lp, q.mu, q.Cp, q.kn, q.CT, q.st, vb - a.pre_prep[s]);
+        __syncthreads();
+    }
+    if (!grid_barrier(a.bar, sets, S)) return;
+
+    // 2: nearest codevector, (problem, row tile) items from the counter
+    uint32_t u0 = 0, u1 = 0;
+    for (;;) {
+        if (tid == 0) s_item = (int64_t)atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= a.ntiles) break;
+        const int s = find_set64(a.pre_tiles, S, item);
+        const BatchSet &q = sets[s];
+        if (!q.st->finished) {
+            const int64_t tile = item - a.pre_tiles[s];
+            if (!assign_f32_tile_t<BM>(q.X, q.M, a.L, a.Lp, q.Cp, q.kn, q.st->n_cur, q.mu, q.C, q.st, q.assign,
+                                       q.e, q.flags, tile * BM, dsm, ash, u0, u1)) {
+                abort_all(a.bar);   // reported by the tile; its copies have been waited for
+                return;
+            }
+        }
+        __syncthreads();   // all reads of this item's shared data before the next item
+    }
+    if (!grid_barrier(a.bar, sets, S)) return;
+
+    // 3: exact re-scoring; the flagged groups of all problems in problem order
+    if (tid == 0) {
+        int t = 0;
+        for (int s = 0; s < S; ++s)
+            if (!sets[s].st->finished) t += (sets[s].st->nflag + EX_R - 1) / EX_R;
+        s_total = t;
+    }
+    __syncthreads();
+    {
+        uint32_t uses[2] = {0u, 0u};
+        const int total = s_total;
+        for (int item = blockIdx.x; item < total; item += grid) {
+            int s = 0, g = item;
+            for (; s < S; ++s) {
+                if (sets[s].st->finished) continue;
+                const int ng = (sets[s].st->nflag + EX_R - 1) / EX_R;
+                if (g < ng) break;
+                g -= ng;
+            }
+            const BatchSet &q = sets[s];
+            if (!exact_group(q.X, a.L, a.Lp, q.CT, q.st->n_cur, q.st, q.flags, q.st->nflag, q.assign, q.e, g,
+                             dsm, esh, uses)) {
+                abort_all(a.bar);
+                return;
+            }
+        }
+    }
+    if (!grid_barrier(a.bar, sets, S)) return;
+
+    // 4: cell counts and distortion partials per chunk; the stop test
+    for (int vb = blockIdx.x; vb < a.tot_hist; vb += grid) {
+        const int s = find_set(a.pre_hist, S, vb);
+        const BatchSet &q = sets[s];
+        if (!q.st->finished) {
+            body_hist(q.assign, q.e, q.M, q.R, q.st->n_cur, 1, q.table, q.dpart, q.st, vb - a.pre_hist[s]);
+            if (last_block(q.st, (unsigned)(a.pre_hist[s + 1] - a.pre_hist[s])))
+                body_ctl(q.dpart, q.CH, q.st, MODE_TRAIN, a.theta, a.max_passes, q.N, nullptr, 0);
+        }
+        __syncthreads();
+    }
+    if (!grid_barrier(a.bar, sets, S)) return;
+
+    // 5: cell sizes and chunk prefixes; offsets and piece cells
+    for (int vb = blockIdx.x; vb < a.tot_scan; vb += grid) {
+        const int s = find_set(a.pre_scan, S, vb);
+        const BatchSet &q = sets[s];
+        if (!skip_counts(q.st, 1)) {
+            const int N = q.st->n_cur;
+            body_scan<BP_THREADS / 32>(q.table, q.CH, N, q.counts, vb - a.pre_scan[s]);
+            if (last_block(q.st, (unsigned)(a.pre_scan[s + 1] - a.pre_scan[s]))) {
+                body_offsets<BP_THREADS>(q.counts, N, q.off);
+                __syncthreads();
+                body_piece_cells(q.off, N, q.S, a.L, q.qcell, q.cell_done, false, q.C, q.C);
+            }
+        }
+        __syncthreads();
+    }
+    if (!grid_barrier(a.bar, sets, S)) return;
+
+    // 6: stable placement by cell
+    for (int vb = blockIdx.x; vb < a.tot_hist; vb += grid) {
+        const int s = find_set(a.pre_hist, S, vb);
+        const BatchSet &q = sets[s];
+        if (!skip_update(q.st, 1))
+            body_scatter(q.assign, q.M, q.R, q.table, q.off, q.st->n_cur, q.perm, vb - a.pre_hist[s]);
+        __syncthreads();
+    }
+    if (!grid_barrier(a.bar, sets, S)) return;
+
+    // 7: cell sums and centroids (in place; an empty cell keeps its codevector)
+    for (int vb = blockIdx.x; vb < a.tot_cellsum; vb += grid) {
+        const int s = find_set(a.pre_cellsum, S, vb);
+        const BatchSet &q = sets[s];
+        const int b = vb - a.pre_cellsum[s];
+        if (!skip_update(q.st, 1)) {
+            switch (a.vec ? a.L : 0) {
+            case 4: cellsum_phase<1>(a, q, b); break;
+            case 8: cellsum_phase<2>(a, q, b); break;
+            case 16: cellsum_phase<4>(a, q, b); break;
+            case 32: cellsum_phase<8>(a, q, b); break;
+            case 64: cellsum_phase<16>(a, q, b); break;
+            case 128: cellsum_phase<32>(a, q, b); break;
+            default:
+                body_cellsum_c_any(q.X, q.M, a.L, q.perm, q.off, q.qcell, q.st->n_cur, q.S, q.pieces,
+                                   q.cell_done, q.C, b);
+            }
+        }
+        __syncthreads();
+    }
+    if (!grid_barrier(a.bar, sets, S)) return;
+
+    // 8: split of a finished stage
+    for (int vb = blockIdx.x; vb < a.tot_split; vb += grid) {
+        const int s = find_set(a.pre_split, S, vb);
+        const BatchSet &q = sets[s];
+        body_split(q.C, q.Calt, a.L, a.delta, a.mult, q.st, vb - a.pre_split[s]);
+    }
+    if (!grid_barrier(a.bar, sets, S)) return;
+
+    // 9: copy back; the stage advances once every block of the problem is done
+    for (int vb = blockIdx.x; vb < a.tot_copy; vb += grid) {
+        const int s = find_set(a.pre_copy, S, vb);
+        const BatchSet &q = sets[s];
+        body_copy_split(q.Calt, q.C, a.L, q.st, vb - a.pre_copy[s]);
+        if (last_block(q.st, (unsigned)(a.pre_copy[s + 1] - a.pre_copy[s]))) body_stage(q.st);
+        __syncthreads();
+    }
+}
+
+size_t pass_smem(int L, int NMAXB)
+{
+    const int Lp = round_up(L, 4);
+    const size_t assign = (size_t)(Lp * BM + 2 * (Lp + 1) * BN) * sizeof(float);
+    const size_t exact = (size_t)2 * Lp * EX_SW * sizeof(float);
+    const size_t hist = (size_t)NMAXB * sizeof(int);
+    const size_t scatter = (size_t)NMAXB * (sizeof(int) + 8);
+    size_t m = assign;
+    if (exact > m) m = exact;
+    if (hist > m) m = hist;
+    if (scatter > m) m = scatter;
+    return m;
+}
+
+}  // namespace
+
+int batch_pass_fit(int L, int NMAXB, size_t *smem)
+{
+    const size_t m = pass_smem(L, NMAXB);
+    *smem = m;
+    if (cudaFuncSetAttribute(kb_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kb_pass, BP_THREADS, m) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return per;
+}
+
+bool launch_b_pass(const BatchPass &a, int ctas_per_sm, size_t smem, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(num_sms() * ctas_per_sm));
+    cfg.blockDim = dim3(BP_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, kb_pass, a) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    note_launch();
+    return true;
+}
+
+}  // namespace lbg

@@ -28,70 +28,13 @@
 //              pieces in order in FP64 and divides.
 // The distortion backward keeps separate cell sums (k_cellsum_v4) and their
 // gradient combine (k_combine_grad).
+#include "bodies_update.cuh"
 #include "lbg_internal.cuh"
 
 #include <math.h>
 
 namespace lbg {
 namespace {
-
-__device__ __forceinline__ int cur_n(const int32_t *n_dev, int n_host)
-{
-    return n_dev ? *n_dev : n_host;
-}
-
-__device__ __forceinline__ bool skip_update(const DevState *st, int train)
-{
-    return train && (st->finished || st->action != ACT_UPDATE);
-}
-
-// The cell sizes and offsets (k_scan_offsets_q) are computed on every pass of
-// a training run, also on a pass that ends its stage: the pass trace reports
-// the empty cells of every allocation.
-__device__ __forceinline__ bool skip_counts(const DevState *st, int train)
-{
-    return train && st->finished;
-}
-
-// ---------------------------------------------------------------- mean
-// Column sums of X per CTA over a contiguous row range: FP32 runs of 8 rows
-// accumulated in FP64, then a fixed-order reduction.  part[b*L + l].
-__device__ __forceinline__ void body_mean_part(const float *__restrict__ X, int64_t M, int L,
-                                               double *__restrict__ part, DevState *st, int blk,
-                                               int nblk)
-{
-    __shared__ double red[256];
-    const int per = 256 / L;   // rows in parallel
-    const int t = threadIdx.x;
-    const int l = t % L, rr = t / L;
-    const int64_t R = (M + nblk - 1) / nblk;
-    const int64_t m0 = (int64_t)blk * R, m1 = m0 + R < M ? m0 + R : M;
-    double acc = 0.0;
-    bool bad = false;
-    if (rr < per) {
-        float run = 0.f;
-        int cnt = 0;
-        for (int64_t m = m0 + rr; m < m1; m += per) {
-            const float v = X[m * L + l];
-            bad = bad || !isfinite(v);
-            run += v;
-            if (++cnt == 8) {
-                acc += run;
-                run = 0.f;
-                cnt = 0;
-            }
-        }
-        acc += run;
-    }
-    if (bad) flag_error(st, ERR_NONFINITE);
-    red[t] = acc;
-    __syncthreads();
-    if (t < L) {
-        double s = 0.0;
-        for (int q = 0; q < per; ++q) s += red[q * L + t];
-        part[(size_t)blk * L + t] = s;
-    }
-}
 
 __global__ void __launch_bounds__(256) k_mean_part(const float *__restrict__ X, int64_t M, int L,
                                                    double *__restrict__ part, DevState *st)
@@ -112,63 +55,6 @@ __global__ void k_mean_final(const double *__restrict__ part, int G, int64_t M, 
     if (C0) C0[l] = c;
 }
 
-// ---------------------------------------------------------------- hist
-// CTA per chunk of R rows: cell counts of the chunk -> table[chunk][n]
-// (stride n_cur) and the chunk's distortion partial -> dpart[chunk].
-__device__ __forceinline__ void body_hist(const int32_t *__restrict__ assign,
-                                          const float *__restrict__ e, int64_t M, int64_t R, int N,
-                                          int do_hist, int32_t *__restrict__ table,
-                                          double *__restrict__ dpart, DevState *st, int blk)
-{
-    extern __shared__ int h[];
-    __shared__ double red[HIST_THREADS];
-    const int tid = threadIdx.x;
-    const int64_t m0 = (int64_t)blk * R, m1 = m0 + R < M ? m0 + R : M;
-    if (do_hist)
-        for (int n = tid; n < N; n += HIST_THREADS) h[n] = 0;
-    __syncthreads();
-    // a thread's rows m0 + tid, + 256, ... in batches of eight (all loads in
-    // flight at once); each batch is one FP32 run of eight added to the FP64 sum
-    double acc = 0.0;
-    bool clamped = false;
-    for (int64_t base = m0 + tid; base < m1; base += 8 * HIST_THREADS) {
-        int a[8];
-        float ev[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int64_t m = base + (int64_t)u * HIST_THREADS;
-            const bool ok = m < m1;
-            a[u] = (ok && do_hist) ? assign[m] : 0;
-            ev[u] = ok ? e[m] : 0.f;
-        }
-        float run = 0.f;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            if (base + (int64_t)u * HIST_THREADS >= m1) break;
-            if (do_hist) {
-                int c = a[u];
-                if (c < 0 || c >= N) {
-                    clamped = true;
-                    c = c < 0 ? 0 : N - 1;
-                }
-                atomicAdd(&h[c], 1);
-            }
-            run += ev[u];
-        }
-        acc += run;
-    }
-    if (clamped) flag_error(st, ERR_INTERNAL);
-    red[tid] = acc;
-    __syncthreads();
-    for (int s = HIST_THREADS / 2; s > 0; s >>= 1) {
-        if (tid < s) red[tid] += red[tid + s];
-        __syncthreads();
-    }
-    if (tid == 0) dpart[blk] = red[0];
-    if (do_hist)
-        for (int n = tid; n < N; n += HIST_THREADS) table[(size_t)blk * N + n] = h[n];
-}
-
 __global__ void __launch_bounds__(HIST_THREADS)
     k_hist(const int32_t *__restrict__ assign, const float *__restrict__ e, int64_t M, int64_t R,
            const int32_t *n_dev, int n_host, int do_hist, int32_t *__restrict__ table,
@@ -178,148 +64,11 @@ __global__ void __launch_bounds__(HIST_THREADS)
     body_hist(assign, e, M, R, cur_n(n_dev, n_host), do_hist, table, dpart, st, blockIdx.x);
 }
 
-// ---------------------------------------------------------------- control
-// D = sum of the chunk partials in chunk order.  In MODE_TRAIN also the
-// stop test of Sec. 2.2 with the readings of the library: the stage ends if
-// D == 0 or (D_prev - D)/D <= theta, or when it has run max_passes passes.
-__device__ __forceinline__ void body_ctl(const double *__restrict__ dpart, int CH, DevState *st,
-                                         int mode, double theta, int max_passes, int N_target,
-                                         PassRecord *rec, int max_rec)
-{
-    if (threadIdx.x >= 32) return;
-    if (mode == MODE_TRAIN && st->finished) return;
-    // lane partials over chunks lane, lane + 32, ..., then a fixed shuffle tree
-    double D = 0.0;
-    for (int c = threadIdx.x; c < CH; c += 32) D += dpart[c];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) D += __shfl_xor_sync(0xffffffffu, D, o);
-    if (threadIdx.x != 0) return;
-    const int nflag = st->nflag;
-    st->n_exact_last = nflag;
-    st->nflag = 0;
-    st->D = D;
-    if (mode != MODE_TRAIN) {
-        st->action = ACT_UPDATE;
-        return;
-    }
-    bool done = (D == 0.0) || ((st->D_prev - D) / D <= theta);
-    if (!done && st->pass + 1 >= max_passes) {
-        done = true;
-        st->warn = 1;
-    }
-    const int act = !done ? ACT_UPDATE : (st->n_cur >= N_target ? ACT_FINISH : ACT_SPLIT);
-    if (rec && st->total < max_rec) {
-        PassRecord r;
-        r.stage_n = st->n_cur;
-        r.pass = st->pass;
-        r.action = act;
-        r.n_exact = nflag;
-        r.D = D;
-        r.n_empty = -1;   // filled in at the end of a traced pass
-        r.ms = 0.f;
-        rec[st->total] = r;
-    }
-    st->total += 1;
-    st->action = act;
-    if (act == ACT_UPDATE) {
-        st->D_prev = D;
-        st->pass += 1;
-    }
-}
-
 __global__ void k_ctl(const double *__restrict__ dpart, int CH, DevState *st, int mode, double theta,
                       int max_passes, int N_target, PassRecord *rec, int max_rec)
 {
     if (blockIdx.x != 0) return;
     body_ctl(dpart, CH, st, mode, theta, max_passes, N_target, rec, max_rec);
-}
-
-// ---------------------------------------------------------------- scan
-// CTA of 1024 threads per 32 cells: lane = cell, warp w covers a range of
-// chunks.  table[c][n] becomes the exclusive prefix over c; counts[n] = total.
-__device__ __forceinline__ void body_scan(int32_t *__restrict__ table, int CH, int N,
-                                          int32_t *__restrict__ counts, int blk)
-{
-    if (blk * 32 >= N) return;
-    __shared__ int part[32][33];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int n = blk * 32 + lane;
-    const int per = (CH + 31) / 32;
-    const int c0 = w * per, c1 = c0 + per < CH ? c0 + per : CH;
-    int s = 0;
-    if (n < N)
-        for (int c = c0; c < c1; ++c) s += table[(size_t)c * N + n];
-    part[w][lane] = s;
-    __syncthreads();
-    if (w == 0) {
-        int run = 0;
-        for (int q = 0; q < 32; ++q) {
-            const int v = part[q][lane];
-            part[q][lane] = run;
-            run += v;
-        }
-        if (n < N) counts[n] = run;
-    }
-    __syncthreads();
-    int run = part[w][lane];
-    if (n < N)
-        for (int c = c0; c < c1; ++c) {
-            const int v = table[(size_t)c * N + n];
-            table[(size_t)c * N + n] = run;
-            run += v;
-        }
-}
-
-
-// One CTA: off[n] = sum_{n' < n} counts[n'], off[N] = total.
-__device__ __forceinline__ void body_offsets(const int32_t *__restrict__ counts, int N,
-                                             int32_t *__restrict__ off)
-{
-    __shared__ int wsum[32];
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const int per = (N + 1023) / 1024;
-    const int a = t * per, b = a + per < N ? a + per : N;
-    int loc = 0;
-    for (int i = a; i < b; ++i) loc += counts[i];
-    int inc = loc;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += v;
-    }
-    if (lane == 31) wsum[w] = inc;
-    __syncthreads();
-    if (w == 0) {
-        int v = wsum[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += y;
-        }
-        wsum[lane] = v;
-    }
-    __syncthreads();
-    int run = inc - loc + (w > 0 ? wsum[w - 1] : 0);
-    for (int i = a; i < b; ++i) {
-        off[i] = run;
-        run += counts[i];
-    }
-    if (t == 1023) off[N] = run;
-}
-
-
-// ---------------------------------------------------------------- fused (step forms)
-// The last CTA to finish (a counter in the state; __threadfence before it, so
-// that every CTA's partials are visible to it) runs the second kernel's body
-// and resets the counter.
-__device__ __forceinline__ bool last_cta(DevState *st)
-{
-    __shared__ int is_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) is_last = atomicAdd(&st->done_ctr, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!is_last) return false;
-    __threadfence();
-    return true;
 }
 
 __global__ void __launch_bounds__(HIST_THREADS)
@@ -342,54 +91,6 @@ __global__ void __launch_bounds__(1024)
     body_offsets(counts, N, off);
 }
 
-// ---------------------------------------------------------------- scatter
-// CTA per chunk (same chunks as k_hist).  Rows are taken in rounds of 256 in
-// index order; inside a round a row's slot is
-//   run[cell] + (rows of that cell in lower warps of the round) + (rank among
-//   equal cells in its warp, __match_any_sync),
-// which is the stable counting-sort position.  run[] starts at the cell
-// offset plus the chunk's exclusive prefix.  Integer atomics only.
-__device__ __forceinline__ void body_scatter(const int32_t *__restrict__ assign, int64_t M,
-                                             int64_t R, const int32_t *__restrict__ table,
-                                             const int32_t *__restrict__ off, int N,
-                                             int32_t *__restrict__ perm, int blk)
-{
-    extern __shared__ int sm[];
-    int *run = sm;                                                   // [N]
-    unsigned char *wcnt = reinterpret_cast<unsigned char *>(sm + N);  // [8][N]
-    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    const int64_t m0 = (int64_t)blk * R, m1 = m0 + R < M ? m0 + R : M;
-    for (int n = tid; n < N; n += 256) run[n] = off[n] + table[(size_t)blk * N + n];
-    for (int i = tid; i < 2 * N; i += 256) reinterpret_cast<int *>(wcnt)[i] = 0;
-    __syncthreads();
-    const unsigned lt = (1u << lane) - 1u;
-    int a_next = (m0 + tid < m1) ? assign[m0 + tid] : 0;   // the next round's cell, loaded ahead
-    for (int64_t base = m0; base < m1; base += 256) {
-        const int64_t m = base + tid;
-        const bool valid = m < m1;
-        int a = valid ? a_next : -1 - w;
-        a_next = (m + 256 < m1) ? assign[m + 256] : 0;
-        if (valid && (a < 0 || a >= N)) a = a < 0 ? 0 : N - 1;   // same clamp as k_hist
-        const unsigned peers = __match_any_sync(0xffffffffu, a);
-        const int rank = __popc(peers & lt);
-        const bool leader = (peers & lt) == 0u;
-        const int cnt = __popc(peers);
-        if (valid && leader) wcnt[w * N + a] = (unsigned char)cnt;
-        __syncthreads();
-        if (valid) {
-            int pre = 0;
-            for (int q = 0; q < w; ++q) pre += wcnt[q * N + a];
-            perm[run[a] + pre + rank] = (int32_t)m;
-        }
-        __syncthreads();
-        if (valid && leader) {
-            atomicAdd(&run[a], cnt);
-            wcnt[w * N + a] = 0;
-        }
-        __syncthreads();
-    }
-}
-
 __global__ void __launch_bounds__(256) k_scatter(const int32_t *__restrict__ assign, int64_t M,
                                                  int64_t R, const int32_t *__restrict__ table,
                                                  const int32_t *__restrict__ off,
@@ -398,77 +99,6 @@ __global__ void __launch_bounds__(256) k_scatter(const int32_t *__restrict__ ass
 {
     if (skip_update(st, train)) return;
     body_scatter(assign, M, R, table, off, cur_n(n_dev, n_host), perm, blockIdx.x);
-}
-
-// ---------------------------------------------------------------- cellsum
-__device__ __forceinline__ int first_cell(const int32_t *off, int N, int64_t p)
-{
-    // largest n with off[n] <= p (then off[n + 1] > p because off[N] = M > p)
-    int lo = 0, hi = N - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (off[mid] <= p)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ void add4(float4 &a, const float4 &b)
-{
-    a.x += b.x;
-    a.y += b.y;
-    a.z += b.z;
-    a.w += b.w;
-}
-
-// Warp q sums perm[q*S, (q+1)*S) cell piece by cell piece; G lanes cover a
-// row with float4 loads (L = 4G), 32/G rows per step, four steps in flight.
-// Piece (cell n, warp q) -> pieces[(n + q) * L ...] (unique slot per piece).
-template <int G>
-__device__ __forceinline__ void body_cellsum_v4(const float *__restrict__ X, int64_t M,
-                                                const int32_t *__restrict__ perm,
-                                                const int32_t *__restrict__ off, int N, int64_t S,
-                                                float *__restrict__ pieces, int blk)
-{
-    constexpr int RPG = 32 / G;
-    constexpr int L = 4 * G;
-    const int64_t q = (int64_t)blk * 8 + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    const int64_t p0 = q * S;
-    if (p0 >= M) return;
-    const int64_t p1 = p0 + S < M ? p0 + S : M;
-    const int rs = lane / G, qd = lane % G;
-    const float4 *X4 = reinterpret_cast<const float4 *>(X);
-    int n = first_cell(off, N, p0);
-    int64_t p = p0;
-    while (p < p1) {
-        const int64_t pe = (int64_t)off[n + 1] < p1 ? (int64_t)off[n + 1] : p1;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        int64_t pp = p + rs;
-        for (; pp + 7 * RPG < pe; pp += 8 * RPG) {   // eight rows in flight per lane
-            int r[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) r[u] = perm[pp + u * RPG];
-            float4 v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = __ldg(X4 + (int64_t)r[u] * G + qd);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) add4(acc, v[u]);
-        }
-        for (; pp < pe; pp += RPG) add4(acc, __ldg(X4 + (int64_t)perm[pp] * G + qd));
-#pragma unroll
-        for (int o = G; o < 32; o <<= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-            acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
-            acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
-        }
-        if (rs == 0) reinterpret_cast<float4 *>(pieces + (size_t)(n + q) * L)[qd] = acc;
-        p = pe;
-        while (n + 1 < N && off[n + 1] <= p) ++n;
-    }
 }
 
 template <int G>
@@ -481,40 +111,6 @@ __global__ void __launch_bounds__(256)
     body_cellsum_v4<G>(X, M, perm, off, cur_n(n_dev, n_host), S, pieces, blockIdx.x);
 }
 
-// Any L: lanes own dims l = lane, lane + 32, ...; rows in order.
-__device__ __forceinline__ void body_cellsum_any(const float *__restrict__ X, int64_t M, int L,
-                                                 const int32_t *__restrict__ perm,
-                                                 const int32_t *__restrict__ off, int N, int64_t S,
-                                                 float *__restrict__ pieces, int blk)
-{
-    const int64_t q = (int64_t)blk * 8 + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    const int64_t p0 = q * S;
-    if (p0 >= M) return;
-    const int64_t p1 = p0 + S < M ? p0 + S : M;
-    int n = first_cell(off, N, p0);
-    int64_t p = p0;
-    while (p < p1) {
-        const int64_t pe = (int64_t)off[n + 1] < p1 ? (int64_t)off[n + 1] : p1;
-        float acc[LMAX / 32] = {0.f, 0.f, 0.f, 0.f};
-        for (int64_t pp = p; pp < pe; ++pp) {
-            const int64_t r = perm[pp];
-#pragma unroll
-            for (int k = 0; k < LMAX / 32; ++k) {
-                const int l = lane + 32 * k;
-                if (l < L) acc[k] += __ldg(X + r * L + l);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < LMAX / 32; ++k) {
-            const int l = lane + 32 * k;
-            if (l < L) pieces[(size_t)(n + q) * L + l] = acc[k];
-        }
-        p = pe;
-        while (n + 1 < N && off[n + 1] <= p) ++n;
-    }
-}
-
 __global__ void __launch_bounds__(256)
     k_cellsum_any(const float *__restrict__ X, int64_t M, int L, const int32_t *__restrict__ perm,
                   const int32_t *__restrict__ off, const int32_t *n_dev, int n_host, int64_t S,
@@ -523,29 +119,6 @@ __global__ void __launch_bounds__(256)
     if (skip_update(st, train)) return;
     body_cellsum_any(X, M, L, perm, off, cur_n(n_dev, n_host), S, pieces, blockIdx.x);
 }
-
-// c_n = (sum of its pieces, in piece order, in FP64) / count_n; an empty
-// cell copies C_in (may alias C_out).
-__device__ __forceinline__ void body_combine(const float *__restrict__ pieces,
-                                             const int32_t *__restrict__ off, int N, int L, int64_t S,
-                                             const float *C_in, float *C_out, int blk)
-{
-    const int64_t i = (int64_t)blk * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)N * L) return;
-    const int n = (int)(i / L), l = (int)(i - (int64_t)n * L);
-    const int64_t a = off[n], b = off[n + 1];
-    if (b == a) {
-        C_out[i] = C_in[i];
-        return;
-    }
-    const int64_t q0 = a / S, q1 = (b - 1) / S;
-    double s = 0.0;
-    for (int64_t q = q0; q <= q1; ++q) s += (double)pieces[(size_t)(n + q) * L + l];
-    // FP32 division of the rounded sum (two roundings, ~1.2e-7 relative; FP64
-    // division is slow on this part)
-    C_out[i] = (float)s / (float)(b - a);
-}
-
 
 // ---------------------------------------------------------------- fused update (step, train)
 // k_scan_offsets_q: per cell, the exclusive prefix of its chunk counts and the
@@ -567,112 +140,7 @@ __global__ void __launch_bounds__(1024)
     if (threadIdx.x == 0) st->done_ctr = 0u;
     body_offsets(counts, N, off);
     __syncthreads();   // off[] complete (this CTA wrote it)
-    const bool copy = C_out != C_in && !skip_update(st, train);
-    for (int n = threadIdx.x; n < N; n += blockDim.x) {
-        const int64_t a = off[n], b = off[n + 1];
-        cell_done[n] = 0;
-        if (b == a) {
-            if (copy)
-                for (int l = 0; l < L; ++l) C_out[(int64_t)n * L + l] = C_in[(int64_t)n * L + l];
-            continue;
-        }
-        for (int64_t q = (a + S - 1) / S; q * S < b; ++q) qcell[q] = n;
-    }
-}
-
-// The centroid of cell n straight from its pieces: FP64 sum of the pieces in
-// order, divided by the count (the arithmetic of body_combine).
-__device__ __forceinline__ void combine_cell(const float *__restrict__ pieces, int n, int64_t a, int64_t b,
-                                             int64_t S, int L, float *__restrict__ C_out, int lane)
-{
-    const int64_t q0 = a / S, q1 = (b - 1) / S;
-    for (int l = lane; l < L; l += 32) {
-        double s = 0.0;
-        for (int64_t q = q0; q <= q1; ++q) s += (double)__ldcg(pieces + (size_t)(n + q) * L + l);
-        C_out[(int64_t)n * L + l] = (float)s / (float)(b - a);
-    }
-}
-
-// A cell piece is finished: a cell held by one piece is divided by its count at
-// once; otherwise the piece is stored (slot n + q), and the warp that stores
-// the cell's last piece (a per-cell counter, after a fence) combines them.
-// Both give the bits body_combine gives.
-template <int G>
-__device__ __forceinline__ void finish_piece_v4(float4 acc, int n, int64_t q, int64_t a, int64_t b, int64_t S,
-                                                float *__restrict__ pieces, int32_t *__restrict__ cell_done,
-                                                float *__restrict__ C_out, int lane)
-{
-    constexpr int L = 4 * G;
-    const int rs = lane / G, qd = lane % G;
-    const int64_t q0 = a / S, q1 = (b - 1) / S;
-    if (q0 == q1) {
-        if (rs == 0) {
-            const float cnt = (float)(b - a);
-            reinterpret_cast<float4 *>(C_out + (size_t)n * L)[qd] =
-                make_float4(acc.x / cnt, acc.y / cnt, acc.z / cnt, acc.w / cnt);
-        }
-        return;
-    }
-    if (rs == 0) reinterpret_cast<float4 *>(pieces + (size_t)(n + q) * L)[qd] = acc;
-    __threadfence();
-    __syncwarp();
-    int last = 0;
-    if (lane == 0) last = atomicAdd(&cell_done[n], 1) == (int)(q1 - q0);
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (!last) return;
-    __threadfence();
-    combine_cell(pieces, n, a, b, S, L, C_out, lane);
-    if (lane == 0) cell_done[n] = 0;
-}
-
-// Warp q sums perm[q S, (q + 1) S) cell piece by cell piece, as
-// body_cellsum_v4 (same order, same bits), starting from qcell[q] instead of a
-// search of the offsets, and finishes every piece with finish_piece_v4.
-template <int G>
-__device__ __forceinline__ void body_cellsum_c(const float *__restrict__ X, int64_t M,
-                                               const int32_t *__restrict__ perm,
-                                               const int32_t *__restrict__ off,
-                                               const int32_t *__restrict__ qcell, int N, int64_t S,
-                                               float *__restrict__ pieces, int32_t *__restrict__ cell_done,
-                                               float *__restrict__ C_out, int blk)
-{
-    constexpr int RPG = 32 / G;
-    const int64_t q = (int64_t)blk * 8 + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    const int64_t p0 = q * S;
-    if (p0 >= M) return;
-    const int64_t p1 = p0 + S < M ? p0 + S : M;
-    const int rs = lane / G, qd = lane % G;
-    const float4 *X4 = reinterpret_cast<const float4 *>(X);
-    int n = qcell[q];
-    int64_t p = p0;
-    while (p < p1) {
-        const int64_t a = off[n], b = off[n + 1];
-        const int64_t pe = b < p1 ? b : p1;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        int64_t pp = p + rs;
-        for (; pp + 7 * RPG < pe; pp += 8 * RPG) {   // eight rows in flight per lane
-            int r[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) r[u] = perm[pp + u * RPG];
-            float4 v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = __ldg(X4 + (int64_t)r[u] * G + qd);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) add4(acc, v[u]);
-        }
-        for (; pp < pe; pp += RPG) add4(acc, __ldg(X4 + (int64_t)perm[pp] * G + qd));
-#pragma unroll
-        for (int o = G; o < 32; o <<= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-            acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
-            acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
-        }
-        finish_piece_v4<G>(acc, n, q, a, b, S, pieces, cell_done, C_out, lane);
-        p = pe;
-        while (n + 1 < N && off[n + 1] <= p) ++n;
-    }
+    body_piece_cells(off, N, S, L, qcell, cell_done, C_out != C_in && !skip_update(st, train), C_in, C_out);
 }
 
 template <int G>
@@ -686,8 +154,7 @@ __global__ void __launch_bounds__(256)
     body_cellsum_c<G>(X, M, perm, off, qcell, cur_n(n_dev, n_host), S, pieces, cell_done, C_out, blockIdx.x);
 }
 
-// Any L: as body_cellsum_any (lanes own dims l = lane, lane + 32, ...), with
-// the pieces finished as above.
+// Any L: as body_cellsum_any, with the pieces finished as above.
 __global__ void __launch_bounds__(256)
     k_cellsum_c_any(const float *__restrict__ X, int64_t M, int L, const int32_t *__restrict__ perm,
                     const int32_t *__restrict__ off, const int32_t *__restrict__ qcell,
@@ -695,54 +162,8 @@ __global__ void __launch_bounds__(256)
                     int32_t *__restrict__ cell_done, float *__restrict__ C_out, DevState *st, int train)
 {
     if (skip_update(st, train)) return;
-    const int N = cur_n(n_dev, n_host);
-    const int64_t q = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    const int64_t p0 = q * S;
-    if (p0 >= M) return;
-    const int64_t p1 = p0 + S < M ? p0 + S : M;
-    int n = qcell[q];
-    int64_t p = p0;
-    while (p < p1) {
-        const int64_t a = off[n], b = off[n + 1];
-        const int64_t pe = b < p1 ? b : p1;
-        float acc[LMAX / 32] = {0.f, 0.f, 0.f, 0.f};
-        for (int64_t pp = p; pp < pe; ++pp) {
-            const int64_t r = perm[pp];
-#pragma unroll
-            for (int k = 0; k < LMAX / 32; ++k) {
-                const int l = lane + 32 * k;
-                if (l < L) acc[k] += __ldg(X + r * L + l);
-            }
-        }
-        const int64_t q0 = a / S, q1 = (b - 1) / S;
-        if (q0 == q1) {
-            const float cnt = (float)(b - a);
-#pragma unroll
-            for (int k = 0; k < LMAX / 32; ++k) {
-                const int l = lane + 32 * k;
-                if (l < L) C_out[(int64_t)n * L + l] = acc[k] / cnt;
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < LMAX / 32; ++k) {
-                const int l = lane + 32 * k;
-                if (l < L) pieces[(size_t)(n + q) * L + l] = acc[k];
-            }
-            __threadfence();
-            __syncwarp();
-            int last = 0;
-            if (lane == 0) last = atomicAdd(&cell_done[n], 1) == (int)(q1 - q0);
-            last = __shfl_sync(0xffffffffu, last, 0);
-            if (last) {
-                __threadfence();
-                combine_cell(pieces, n, a, b, S, L, C_out, lane);
-                if (lane == 0) cell_done[n] = 0;
-            }
-        }
-        p = pe;
-        while (n + 1 < N && off[n + 1] <= p) ++n;
-    }
+    body_cellsum_c_any(X, M, L, perm, off, qcell, cur_n(n_dev, n_host), S, pieces, cell_done, C_out,
+                       blockIdx.x);
 }
 
 // ---------------------------------------------------------------- backward
@@ -796,22 +217,6 @@ __global__ void k_combine_grad(const float *__restrict__ pieces, const int32_t *
         for (int64_t q = q0; q <= q1; ++q) s += (double)pieces[(size_t)(n + q) * L + l];
     }
     dC[i] = (float)(2.0 * (double)gD * ((double)(b - a) * (double)C[i] - s));
-}
-
-// ---------------------------------------------------------------- split
-// [c + delta], [c - delta] per centroid (or c (1 + delta), c (1 - delta) when
-// mult), interleaved, rounded once from FP64.
-__device__ __forceinline__ void body_split(const float *__restrict__ C_cur, float *__restrict__ C_alt,
-                                           int L, double delta, int mult, DevState *st, int blk)
-{
-    if (st->finished || st->action != ACT_SPLIT) return;
-    const int n = st->n_cur;
-    const int64_t i = (int64_t)blk * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)n * L) return;
-    const int64_t c = i / L, l = i - c * L;
-    const double v = (double)C_cur[i];
-    C_alt[(2 * c) * L + l] = (float)(mult ? v * (1.0 + delta) : v + delta);
-    C_alt[(2 * c + 1) * L + l] = (float)(mult ? v * (1.0 - delta) : v - delta);
 }
 
 __global__ void k_split(const float *__restrict__ C_cur, float *__restrict__ C_alt, int L,
@@ -883,33 +288,10 @@ __global__ void __launch_bounds__(1024) k_reseed(const int32_t *__restrict__ off
     }
 }
 
-__device__ __forceinline__ void body_copy_split(const float *__restrict__ C_alt,
-                                                float *__restrict__ C_cur, int L, DevState *st,
-                                                int blk)
-{
-    if (st->finished || st->action != ACT_SPLIT) return;
-    const int64_t i = (int64_t)blk * blockDim.x + threadIdx.x;
-    if (i < 2 * (int64_t)st->n_cur * L) C_cur[i] = C_alt[i];
-}
-
 __global__ void k_copy_split(const float *__restrict__ C_alt, float *__restrict__ C_cur, int L,
                              DevState *st)
 {
     body_copy_split(C_alt, C_cur, L, st, blockIdx.x);
-}
-
-// End of a training pass: a split doubles the stage size and resets the
-// stage (D_prev = +inf, reading of the library); a finish ends training.
-__device__ __forceinline__ void body_stage(DevState *st)
-{
-    if (threadIdx.x != 0 || st->finished) return;
-    if (st->action == ACT_SPLIT) {
-        st->n_cur *= 2;
-        st->pass = 0;
-        st->D_prev = INFINITY;
-    } else if (st->action == ACT_FINISH) {
-        st->finished = 1;
-    }
 }
 
 __global__ void k_stage(DevState *st) { body_stage(st); }
@@ -1136,8 +518,6 @@ void launch_scan_offsets(int32_t *table, int CH, int N, int32_t *counts, int32_t
 {
     LBG_COUNTED k_scan_offsets<<<(N + 31) / 32, 1024, 0, s>>>(table, CH, N, counts, off, st);
 }
-
-
 
 void launch_scatter(const int32_t *assign, int64_t M, int64_t R, int CH, const int32_t *table,
                     const int32_t *off, const int32_t *n_dev, int n_host, int32_t *perm,

@@ -446,6 +446,14 @@ struct GraphPass {
         cudaEventRecord(ev, cap);
         cudaStreamWaitEvent(user, ev, 0);
     }
+    // Forget the recorded pass (its recording was incomplete): passes launch directly.
+    void drop()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+    }
     ~GraphPass()
     {
         if (exec) cudaGraphExecDestroy(exec);
@@ -1032,6 +1040,7 @@ lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, 
     const size_t o_tiles = take(sizeof(int64_t) * (size_t)(S + 1));
     const size_t o_tiles64 = take(sizeof(int64_t) * (size_t)(S + 1));
     const size_t o_counter = take(sizeof(int) * 4);
+    const size_t o_bar = take(sizeof(unsigned) * 4);   // grid barrier of the persistent pass
     const size_t o_X = wX == 0 ? take(sizeof(float) * (size_t)Mtot * L) : 0;
     const size_t o_C = wC == 0 ? take(sizeof(float) * (size_t)Ntot * L) : 0;
     const size_t o_A = take(sizeof(int32_t) * (size_t)Mtot);
@@ -1085,6 +1094,9 @@ lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, 
         q.perm = reinterpret_cast<int32_t *>(b + p.perm);
         q.e = reinterpret_cast<float *>(b + p.e);
         q.pieces = reinterpret_cast<float *>(b + p.pieces);
+        q.qcell = reinterpret_cast<int32_t *>(b + p.qcell);
+        q.cell_done = reinterpret_cast<int32_t *>(b + p.cell_done);
+        q.nq = p.nq;
         q.dpart = reinterpret_cast<double *>(b + p.dpart);
         q.mpart = reinterpret_cast<double *>(b + p.mpart);
         coff += N[s];
@@ -1120,11 +1132,50 @@ lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, 
     for (int s = 0; s < S; ++s) max_groups += (int)((sub[s].p.M + 7) / 8);
     const bool vec = (reinterpret_cast<uintptr_t>(dX) & 15u) == 0;
 
+    // ---- one persistent launch per pass, unless asked otherwise or it does not fit
+    size_t pass_smem = 0;
+    int pass_ctas = 0;
+    if (!o.batched_per_phase && o.tile_rows == 0 && o.ctas_per_sm == 0) {
+        pass_ctas = batch_pass_fit(L, NMAXB, &pass_smem);
+        if (pass_ctas > 2) pass_ctas = 2;
+    }
+    unsigned *dbar = reinterpret_cast<unsigned *>(ws + o_bar);
+    CK(cudaMemsetAsync(dbar, 0, sizeof(unsigned) * 4, c.s));
+    BatchPass bp = {};
+    bp.sets = dsets;
+    bp.S = S;
+    bp.L = L;
+    bp.Lp = Lp;
+    bp.NMAXB = NMAXB;
+    bp.pre_prep = dP[2];
+    bp.tot_prep = P[2][S];
+    bp.pre_hist = dP[0];
+    bp.tot_hist = P[0][S];
+    bp.pre_scan = dP[1];
+    bp.tot_scan = P[1][S];
+    bp.pre_cellsum = dP[3];
+    bp.tot_cellsum = P[3][S];
+    bp.pre_split = dP[5];
+    bp.tot_split = P[5][S];
+    bp.pre_copy = dP[6];
+    bp.tot_copy = P[6][S];
+    bp.pre_tiles = dtiles;
+    bp.ntiles = tiles[S];
+    bp.counter = counter;
+    bp.bar = dbar;
+    bp.theta = theta;
+    bp.delta = delta;
+    bp.max_passes = o.max_passes;
+    bp.mult = o.split_multiplicative != 0;
+    bp.vec = vec && (reinterpret_cast<uintptr_t>(dC) & 15u) == 0;
+
     // ---- tile of the batched nearest-codevector launch (lbg_opts.autotune)
     int tile_rows = 128, ctas = 2;
     lbg_tune_report report;
     memset(&report, 0, sizeof(report));
-    if (o.tile_rows != 0 || o.ctas_per_sm != 0) {
+    if (pass_ctas > 0) {
+        ctas = pass_ctas;   // the persistent pass: 128-row tiles, its resident CTAs
+    } else if (o.tile_rows != 0 || o.ctas_per_sm != 0) {
         tile_rows = o.tile_rows != 0 ? o.tile_rows : 128;
         ctas = o.ctas_per_sm != 0 ? o.ctas_per_sm : (tile_rows == 64 ? 4 : 2);
     } else if (o.autotune) {
@@ -1146,7 +1197,6 @@ lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, 
     }
     report.tile_rows = tile_rows;
     report.ctas_per_sm = ctas;
-    if (o.tune_report) *o.tune_report = report;
     const int64_t *dtiles_use = tile_rows == 64 ? dtiles64 : dtiles;
     const int64_t ntiles_use = tile_rows == 64 ? tiles64[S] : tiles[S];
     Timer tm;
@@ -1155,7 +1205,18 @@ lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, 
     launch_b_mean(dsets, S, dP[7], P[7][S], L, c.s);
 
     // ---- one batched pass, recorded once into a graph and replayed
+    bool pass_refused = false, in_capture = false, capture_refused = false;
     auto pass = [&](cudaStream_t st) {
+        if (pass_ctas > 0 && !pass_refused) {
+            if (launch_b_pass(bp, pass_ctas, pass_smem, st)) return;
+            // refused while recording: the recording is dropped and the pass launched directly;
+            // refused directly: the per-phase launches from now on
+            if (in_capture) {
+                capture_refused = true;
+                return;
+            }
+            pass_refused = true;
+        }
         launch_b_reset(dsets, S, counter, st);
         launch_b_prep(dsets, S, dP[2], P[2][S], L, Lp, st);
         launch_b_assign(dsets, S, dtiles_use, ntiles_use, L, Lp, counter, tile_rows, ctas, st);
@@ -1178,7 +1239,10 @@ lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, 
     }
     const int64_t max_total = (int64_t)stages * o.max_passes;
     GraphPass gp;
+    in_capture = true;
     gp.build(c.s, pass);   // falls back to direct launches if capture is not possible
+    in_capture = false;
+    if (capture_refused) gp.drop();
     std::vector<DevState> hst(S);
     lbg_status out = LBG_OK;
     int64_t issued = 0;
@@ -1208,6 +1272,8 @@ lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, 
         if (batch < 32) batch *= 2;
     }
     tm.mark(4, c.s);
+    report.persistent = pass_ctas > 0 && !pass_refused;
+    if (o.tune_report) *o.tune_report = report;
     if (out != LBG_OK) return out;
     if (wC == 0) CK(cudaMemcpyAsync(C, dC, sizeof(float) * Ntot * L, cudaMemcpyDeviceToHost, c.s));
     if (assign && wA == 0)

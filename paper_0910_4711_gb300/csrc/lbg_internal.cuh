@@ -81,6 +81,8 @@ struct BatchSet {
     float *mu;             // [Lp] centring vector
     DevState *st;
     int32_t *assign, *flags, *table, *counts, *off, *perm;
+    int32_t *qcell, *cell_done;   // piece cells and per-cell piece counters (persistent pass)
+    int64_t nq;                   // warp pieces of the cell sums
     float *e, *pieces;
     double *dpart, *mpart;
 };
@@ -117,6 +119,9 @@ __host__ __device__ inline int find_set64(const int64_t *pre, int S, int64_t b)
     }
     return lo;
 }
+
+// Codebook size of a launch: the stage size on the device (training) or the host's.
+__device__ __forceinline__ int cur_n(const int32_t *n_dev, int n_host) { return n_dev ? *n_dev : n_host; }
 
 __host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 __host__ __device__ inline int64_t round_up64(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
@@ -325,6 +330,25 @@ void launch_b_assign(const BatchSet *sets, int S, const int64_t *pre_tiles, int6
                      int L, int Lp, int *counter, int tile_rows, int ctas_per_sm, cudaStream_t s);
 void launch_b_exact(const BatchSet *sets, int S, int L, int Lp, int max_ngroups, cudaStream_t s);
 void launch_b_reset(const BatchSet *sets, int S, int *counter, cudaStream_t s);
+// One Lloyd pass of every problem in one cooperative launch (k_batched.cu):
+// the phases of the launches above, separated by bounded grid-wide barriers.
+struct BatchPass {
+    const BatchSet *sets;
+    int S, L, Lp, NMAXB;
+    const int32_t *pre_prep, *pre_hist, *pre_scan, *pre_cellsum, *pre_split, *pre_copy;
+    int32_t tot_prep, tot_hist, tot_scan, tot_cellsum, tot_split, tot_copy;
+    const int64_t *pre_tiles;   // row tiles of BM rows
+    int64_t ntiles;
+    int *counter;               // assignment work items taken
+    unsigned *bar;              // [0] arrivals, [1] generation, [2] abort (zero before the first pass)
+    double theta, delta;
+    int max_passes, mult, vec;
+};
+// Resident CTAs per SM the persistent pass can have (0: it does not fit) and its
+// dynamic shared memory.
+int batch_pass_fit(int L, int NMAXB, size_t *smem);
+// false if the cooperative launch was refused (then the per-phase launches run)
+bool launch_b_pass(const BatchPass &a, int ctas_per_sm, size_t smem, cudaStream_t s);
 
 // Backward at a fixed cell table; the upstream gradient is gD, or *gD_dev
 // (device) when gD_dev is not null.

@@ -74,27 +74,55 @@ def test_tile_choice_does_not_change_results(lbg):
     per SM) gives the same bits as the fixed default and as the autotuned run."""
     parts, Xc, row_off, Ns = ragged_sets(70, [4096, 20000, 777, 9000], [64, 512, 16, 128])
     Xd = torch.from_numpy(Xc).cuda()
-    ref = lbg.lbg_train_batched(Xd, row_off, Ns, autotune=False)
-    assert ref.tune["tile_rows"] == 128 and ref.tune["ctas_per_sm"] == 2
+    ref = lbg.lbg_train_batched(Xd, row_off, Ns, autotune=False, per_phase=True)
+    assert ref.tune["tile_rows"] == 128 and ref.tune["ctas_per_sm"] == 2 and not ref.tune["persistent"]
     for rows, ctas in ((128, 1), (128, 2), (64, 2), (64, 4)):
         r = lbg.lbg_train_batched(Xd, row_off, Ns, tile_rows=rows, ctas_per_sm=ctas)
         assert (r.tune["tile_rows"], r.tune["ctas_per_sm"]) == (rows, ctas)
         assert torch.equal(r.C, ref.C) and torch.equal(r.assign, ref.assign) and r.D == ref.D, (rows, ctas)
-    tuned = lbg.lbg_train_batched(Xd, row_off, Ns)
+    tuned = lbg.lbg_train_batched(Xd, row_off, Ns, per_phase=True)
     assert torch.equal(tuned.C, ref.C) and torch.equal(tuned.assign, ref.assign) and tuned.D == ref.D
 
 
 def test_autotune_report_and_cache(lbg):
     parts, Xc, row_off, Ns = ragged_sets(90, [3000, 5000, 7000], [32, 64, 1024])
     Xd = torch.from_numpy(Xc).cuda()
-    first = lbg.lbg_train_batched(Xd, row_off, Ns)
+    first = lbg.lbg_train_batched(Xd, row_off, Ns, per_phase=True)
     t = first.tune
     if not t["from_cache"]:                  # a calibration ran in this call
         c = t["candidates"]
         assert len(c) == 4 and all(x["ms"] > 0 for x in c)
         best = min(c, key=lambda x: x["ms"])
         assert (t["tile_rows"], t["ctas_per_sm"]) == (best["tile_rows"], best["ctas_per_sm"])
-    again = lbg.lbg_train_batched(Xd, row_off, Ns)
+    again = lbg.lbg_train_batched(Xd, row_off, Ns, per_phase=True)
     assert again.tune["from_cache"] and again.tune["candidates"] == []
     assert (again.tune["tile_rows"], again.tune["ctas_per_sm"]) == (t["tile_rows"], t["ctas_per_sm"])
     assert torch.equal(again.C, first.C) and again.D == first.D
+
+
+def test_persistent_pass_equals_per_phase_launches(lbg):
+    """One cooperative launch per Lloyd pass of all problems (the default) gives the bits of the
+    one-launch-per-phase form and of lbg_train per problem; the library's launch count shows one
+    kernel per pass (plus the initial centroid's two) instead of thirteen."""
+    parts, Xc, row_off, Ns = ragged_sets(110, [4096, 20000, 777, 9000, 130], [64, 512, 16, 128, 256])
+    Xd = torch.from_numpy(Xc).cuda()
+    phased = lbg.lbg_train_batched(Xd, row_off, Ns, per_phase=True)
+    l0 = lbg.launch_count()
+    r = lbg.lbg_train_batched(Xd, row_off, Ns)
+    launches = lbg.launch_count() - l0
+    assert r.tune["persistent"] and r.tune["tile_rows"] == 128 and r.tune["ctas_per_sm"] >= 1
+    assert torch.equal(r.C, phased.C) and torch.equal(r.assign, phased.assign) and r.D == phased.D
+    passes = r.max_passes_run
+    assert passes <= launches <= 2 * passes + 2 + 3          # batches of passes; mean, final copies
+    single = lbg.lbg_train(torch.from_numpy(parts[1]).cuda(), Ns[1], 0.01, 1e-3)
+    assert torch.equal(r.codebook(1), single.C) and r.D[1] == single.D
+
+
+def test_persistent_pass_multiplicative_split_and_pass_cap(lbg):
+    parts, Xc, row_off, Ns = ragged_sets(120, [3000, 6000], [32, 128])
+    Xd = torch.from_numpy(Xc).cuda()
+    for kw in ({"split_multiplicative": True}, {"max_passes": 2}):
+        a = lbg.lbg_train_batched(Xd, row_off, Ns, **kw)
+        b = lbg.lbg_train_batched(Xd, row_off, Ns, per_phase=True, **kw)
+        assert a.tune["persistent"] and not b.tune["persistent"]
+        assert a.status == b.status and torch.equal(a.C, b.C) and a.D == b.D, kw

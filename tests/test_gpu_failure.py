@@ -58,7 +58,7 @@ def test_workspace_cap_refuses_then_recovers():
     Cd = Xd[::61][:256].contiguous()
     C0, A0, D0 = clean_step(Xd, Cd)
     try:
-        lbg.set_workspace_limit(1 << 20)                          # far below a step's scratch
+        lbg.set_workspace_limit(4096)                             # far below any call's scratch
         for call in (lambda: lbg.lbg_lloyd_step(Xd, Cd), lambda: lbg.vq_encode(Xd, Cd),
                      lambda: lbg.lbg_train(Xd, 16)):
             with pytest.raises(lbg.LBGError) as ei:
