@@ -784,8 +784,21 @@ def batched_leg(lbg, synth, torch):
     torch.cuda.synchronize()
     seq = time.perf_counter() - t0
     bt = statistics.median(ts)
+    # the same batch with one launch per phase of a pass (tuned tiles) instead of one
+    # persistent launch per pass
+    lbg.lbg_train_batched(X, row_off, Ns, max_passes=1, per_phase=True)
+    tp = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rp = lbg.lbg_train_batched(X, row_off, Ns, per_phase=True)
+        torch.cuda.synchronize()
+        tp.append(time.perf_counter() - t0)
     return {"workload": f"64 problems, sum M = {int(row_off[-1])}, L = 16, N in {{64..1024}}",
             "batched_s": bt, "sequential_s": seq, "speedup": seq / bt,
+            "one_launch_per_pass": bool(r.tune.get("persistent")),
+            "per_phase_launches_s": statistics.median(tp),
+            "per_phase_tile": {"tile_rows": rp.tune["tile_rows"], "ctas_per_sm": rp.tune["ctas_per_sm"]},
             "max_passes": r.max_passes_run, "passes_per_s": r.max_passes_run / bt,
             "assign_tile": {"chosen": {"tile_rows": r.tune["tile_rows"], "ctas_per_sm": r.tune["ctas_per_sm"]},
                             "calibration": tune["candidates"]}}

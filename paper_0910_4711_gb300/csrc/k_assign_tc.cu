@@ -732,36 +732,55 @@ __device__ __forceinline__ void tc_jobs(TcSmem &sh, uint32_t tmem, int warp, int
 // by more than the rounding bound of the FP32 sums, runs the certificates,
 // and writes a(m), e(m) or flags the row.  `usable` = the tile's x~ and the
 // codebook split are exact.
+// The tail of a row tile in stages, so that the persistent kernel can spread
+// them over the next tile's jobs: stage 0 merges the halves' top-2, stages
+// 1 .. GRP/2 each score one group member per half, the last stage decides and
+// certifies.  TailState carries a thread's row between stages.
+struct TailState {
+    float V1, V2, xn2, kmax;
+    int i1;
+    bool usable_tile, usable;
+    int64_t m0;
+};
+template <int GRP>
+__host__ __device__ constexpr int tail_stages() { return 2 + GRP / 2; }
+
+// Not inlined: the persistent kernel calls it between jobs, and its registers
+// must not add to those of the job loop.
 template <int LK, int GRP>
-__device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc, int half, int rr,
-                                        int64_t m0, const float *__restrict__ X, int64_t M, int L, int N,
-                                        const float *__restrict__ C, const float *__restrict__ kn, float xn2,
-                                        bool usable_tile, float cmax, float rho, float V1, float V2, int i1,
-                                        DevState *st,
-                                        int32_t *__restrict__ assign, float *__restrict__ e,
-                                        int32_t *__restrict__ flags, int64_t flag_base)
+__device__ __noinline__ void tc_tail_stage(int stage, TailState &ts, TcSmem &sh, int warp, int lane, int acc,
+                                              int half, int rr, const float *__restrict__ X, int64_t M, int L,
+                                              int N, const float *__restrict__ C, const float *__restrict__ kn,
+                                              float cmax, float rho, DevState *st, int32_t *__restrict__ assign,
+                                              float *__restrict__ e, int32_t *__restrict__ flags,
+                                              int64_t flag_base)
 {
     const int crow = 128 * acc + rr;
-    const int64_t m = m0 + crow;
-    sh.m.v1[half][crow] = V1;
-    sh.m.v2[half][crow] = V2;
-    sh.m.i1[half][crow] = i1;
-    named_sync(1, 32 * TC_EPI_WARPS);
-    {
+    const int64_t m0 = ts.m0, m = m0 + crow;
+    if (stage == 0) {
+        sh.m.v1[half][crow] = ts.V1;
+        sh.m.v2[half][crow] = ts.V2;
+        sh.m.i1[half][crow] = ts.i1;
+        named_sync(1, 32 * TC_EPI_WARPS);
         const float A1 = sh.m.v1[0][crow], A2 = sh.m.v2[0][crow], B1 = sh.m.v1[1][crow], B2 = sh.m.v2[1][crow];
         const int ai = sh.m.i1[0][crow], bi = sh.m.i1[1][crow];
-        V2 = fminf(fminf(A2, B2), fmaxf(A1, B1));
+        ts.V2 = fminf(fminf(A2, B2), fmaxf(A1, B1));
         const bool take = B1 < A1 || (B1 == A1 && bi < ai);
-        V1 = take ? B1 : A1;
-        i1 = take ? bi : ai;
+        ts.V1 = take ? B1 : A1;
+        ts.i1 = take ? bi : ai;
+        named_sync(2, 32 * TC_EPI_WARPS);   // merge inputs read: sh.r may now overwrite sh.m
+        ts.usable = m < M && !sh.abort && ts.usable_tile && ts.i1 >= 0 && ts.i1 < N && ts.V1 < INFINITY;
+        ts.kmax = 0.f;
+        return;
     }
-    named_sync(2, 32 * TC_EPI_WARPS);   // merge inputs read: sh.r may now overwrite sh.m
-    const bool usable = m < M && !sh.abort && usable_tile && i1 >= 0 && i1 < N && V1 < INFINITY;
-    // the best group is codevectors i1 .. i1 + 7; this half scores members i1 + 4 half + g
-    float kmax = 0.f;
-    const bool coop = (L & 3) == 0 && ((reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(X)) & 15u) == 0;
-#pragma unroll 1
-    for (int g = 0; g < GRP / 2; ++g) {
+    const int i1 = ts.i1;
+    const bool usable = ts.usable;
+    if (stage <= GRP / 2) {
+        // the best group is codevectors i1 .. i1 + GRP - 1; this half scores member
+        // i1 + (GRP / 2) half + g
+        const int g = stage - 1;
+        const bool coop = (L & 3) == 0 && ((reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(X)) & 15u) == 0;
+        float kmax = ts.kmax;
         const int cand = i1 + (GRP / 2) * half + g;
         const int ccand = (usable && cand < N) ? cand : -1;
         if (ccand >= 0) kmax = fmaxf(kmax, __ldg(kn + ccand));
@@ -821,8 +840,11 @@ __device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc,
             dc = d2;
         }
         sh.r.d[(GRP / 2) * half + g][crow] = dc;
+        ts.kmax = kmax;
+        return;
     }
-    sh.r.k[half][crow] = kmax;
+    const float V1 = ts.V1, V2 = ts.V2, xn2 = ts.xn2;
+    sh.r.k[half][crow] = ts.kmax;
     named_sync(2, 32 * TC_EPI_WARPS);
     if (half == 0 && m < M && !sh.abort) {
         // the group member with the smallest FP32 direct-form distance wins when every other
@@ -881,6 +903,23 @@ __device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc,
         }
         if (!certified) flags[atomicAdd(&st->nflag, 1)] = (int32_t)(flag_base + m);
     }
+}
+
+
+template <int LK, int GRP>
+__device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc, int half, int rr,
+                                        int64_t m0, const float *__restrict__ X, int64_t M, int L, int N,
+                                        const float *__restrict__ C, const float *__restrict__ kn, float xn2,
+                                        bool usable_tile, float cmax, float rho, float V1, float V2, int i1,
+                                        DevState *st,
+                                        int32_t *__restrict__ assign, float *__restrict__ e,
+                                        int32_t *__restrict__ flags, int64_t flag_base)
+{
+    TailState ts{V1, V2, xn2, 0.f, i1, usable_tile, false, m0};
+#pragma unroll 1
+    for (int sg = 0; sg < tail_stages<GRP>(); ++sg)
+        tc_tail_stage<LK, GRP>(sg, ts, sh, warp, lane, acc, half, rr, X, M, L, N, C, kn, cmax, rho, st, assign, e,
+                               flags, flag_base);
 }
 
 // ---------------------------------------------------------------- one CTA per row tile
@@ -1361,14 +1400,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (tid == 64 && !sh.abort) mbar_arrive(&sh.xempty);   // XF may take the next x tile
             }
         };
+        // Tile k's boundary: its x tile is converted (at tile k - 1's middle job,
+        // or here for tile 0), its A operand written once tile k - 1's MMAs are
+        // done (all 16 warps consumed its last jobs before the named barrier),
+        // and the tensor pipe released on it; tile k - 1's tail then runs in
+        // stages after tile k's first jobs, so the pipe is not left waiting on it.
+        constexpr int NST = tail_stages<GRP>();
+        const int conv_at = ntiles / 2;
+        bool converted = false;
         for (int k = 0; k <= K; ++k) {
             float xn2 = 0.f;
             bool tile_exact = false;
             if (k < K) {
-                // convert x tile k (it is in XF) into centred BF16 rows; then, all 16
-                // warps having consumed the previous tile's last jobs (before the
-                // conversion's named barrier), its MMAs are done and A may be rewritten
-                for (int c = 0; c < NCHUNK; ++c) convert(k, c);
+                if (!converted)
+                    for (int c = 0; c < NCHUNK; ++c) convert(k, c);
+                converted = false;
                 tile_exact = next_exact;
                 xn2 = L == LK ? tc_write_a<LK, true>(XS, L, tile_m0(k) + crow < M, crow, half, acc, warp, tmem, sh)
                               : tc_write_a<LK, false>(XS, L, tile_m0(k) + crow < M, crow, half, acc, warp, tmem, sh);
@@ -1376,13 +1422,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 named_sync(1, 32 * TC_EPI_WARPS);
                 if (tid == 64) mbar_arrive(&sh.aready);
             }
-            if (k >= 1)
-                tc_tail<LK, GRP>(sh, warp, lane, acc, half, rr, tile_m0(k - 1), X, M, L, N, C, kn, pxn2, pusable,
-                            cmax, rho, pV1, pV2, pi1, st, assign, e, flags, flag_base);
+            TailState ts{pV1, pV2, pxn2, 0.f, pi1, pusable, false, k >= 1 ? tile_m0(k - 1) : 0};
+            auto tail = [&](int sg) {
+                tc_tail_stage<LK, GRP>(sg, ts, sh, warp, lane, acc, half, rr, X, M, L, N, C, kn, cmax, rho, st,
+                                       assign, e, flags, flag_base);
+            };
             if (k < K) {
-                tc_jobs<GRP>(sh, tmem, warp, lane, acc, half, ntiles, 2 * k * ntiles, keymask, pV1, pV2, pi1);
+                auto hook = [&](int t) {
+                    if (k >= 1 && t < NST) tail(t);
+                    if (t == conv_at && k + 1 < K) {
+                        for (int c = 0; c < NCHUNK; ++c) convert(k + 1, c);
+                        converted = true;
+                    }
+                };
+                tc_jobs<GRP>(sh, tmem, warp, lane, acc, half, ntiles, 2 * k * ntiles, keymask, pV1, pV2, pi1, hook);
+                if (k >= 1)
+                    for (int sg = ntiles < NST ? ntiles : NST; sg < NST; ++sg) tail(sg);
                 pxn2 = xn2;
                 pusable = tile_exact && tc_exact_cb;
+            } else if (k >= 1) {
+                for (int sg = 0; sg < NST; ++sg) tail(sg);
             }
         }
     }

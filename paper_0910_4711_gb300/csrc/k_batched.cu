@@ -40,6 +40,60 @@ namespace lbg {
 namespace {
 
 constexpr int BP_THREADS = 256;
+constexpr int BP_MAX_SETS = 1024;   // problems the per-CTA state tables hold (more: per-phase launches)
+
+// Per-problem state as of a phase's start, read once per CTA after the barrier
+// into shared memory (a virtual block then reads no device state to decide
+// whether to run): bit 0 = not finished, bit 1 = the pass updates (stop test
+// said UPDATE); the stage size; the exact phase's group prefix.
+struct PassTables {
+    int *run, *ncur, *gpre;
+};
+
+__device__ __forceinline__ void load_states(const BatchSet *__restrict__ sets, int S, const PassTables &t)
+{
+    for (int s = threadIdx.x; s < S; s += BP_THREADS) {
+        const DevState *st = sets[s].st;
+        const int fin = st->finished;
+        t.run[s] = fin ? 0 : (1 | (st->action == ACT_UPDATE ? 2 : 0));
+        t.ncur[s] = st->n_cur;
+    }
+    __syncthreads();
+}
+
+// gpre[s] = flagged groups of problems before s (gpre[S] = all): a thread per
+// contiguous range of problems, then the ranges' sums in order.
+__device__ __forceinline__ void exact_prefix(const BatchSet *__restrict__ sets, int S, const PassTables &t)
+{
+    __shared__ int part[BP_THREADS];
+    const int per = (S + BP_THREADS - 1) / BP_THREADS;
+    const int a = threadIdx.x * per, b = a + per < S ? a + per : S;
+    int loc = 0;
+    for (int s = a; s < b; ++s) {
+        const int g = (t.run[s] & 1) ? (sets[s].st->nflag + EX_R - 1) / EX_R : 0;
+        t.gpre[s] = g;
+        loc += g;
+    }
+    part[threadIdx.x] = loc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int i = 0; i < BP_THREADS; ++i) {
+            const int v = part[i];
+            part[i] = run;
+            run += v;
+        }
+        t.gpre[S] = run;
+    }
+    __syncthreads();
+    int run = part[threadIdx.x];
+    for (int s = a; s < b; ++s) {
+        const int g = t.gpre[s];
+        t.gpre[s] = run;
+        run += g;
+    }
+    __syncthreads();
+}
 
 // Grid-wide barrier: arrivals counted in bar[0]; the last arrival resets the
 // count and bumps the generation bar[1], for which the others wait (bounded).
@@ -104,21 +158,22 @@ __device__ __forceinline__ bool last_block(DevState *st, unsigned count)
 __device__ __forceinline__ void abort_all(unsigned *bar) { atomicExch(bar + 2, 1u); }
 
 template <int G>
-__device__ __forceinline__ void cellsum_phase(const BatchPass &a, const BatchSet &q, int b)
+__device__ __forceinline__ void cellsum_phase(const BatchSet &q, int N, int b)
 {
-    body_cellsum_c<G>(q.X, q.M, q.perm, q.off, q.qcell, q.st->n_cur, q.S, q.pieces, q.cell_done, q.C, b);
+    body_cellsum_c<G>(q.X, q.M, q.perm, q.off, q.qcell, N, q.S, q.pieces, q.cell_done, q.C, b);
 }
 
 __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
 {
-    extern __shared__ __align__(128) float dsm[];   // each phase's dynamic shared memory
+    extern __shared__ __align__(128) float dsm[];   // each phase's dynamic shared memory, then the tables
     __shared__ AssignSmemT<BM> ash;
     __shared__ __align__(16) ExactSmem esh;
     __shared__ int64_t s_item;
-    __shared__ int s_total;
     const BatchSet *sets = a.sets;
     const int S = a.S, tid = threadIdx.x;
     const int grid = (int)gridDim.x;
+    int *tab = reinterpret_cast<int *>(reinterpret_cast<char *>(dsm) + a.phase_smem);
+    const PassTables T{tab, tab + S, tab + 2 * S};
 
     // 0: reset; the shared-memory barriers of the assignment and exact phases
     if (tid == 0) {
@@ -136,11 +191,12 @@ __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
     if (!grid_barrier(a.bar, sets, S)) return;
 
     // 1: codebook preparation
+    load_states(sets, S, T);
     for (int vb = blockIdx.x; vb < a.tot_prep; vb += grid) {
         const int s = find_set(a.pre_prep, S, vb);
         const BatchSet &q = sets[s];
-        if (!q.st->finished)
-            body_prep(q.C, q.st->n_cur, a.L, a.Lp, q.mu, q.Cp, q.kn, q.CT, q.st, vb - a.pre_prep[s]);
+        if (T.run[s] & 1)
+            body_prep(q.C, T.ncur[s], a.L, a.Lp, q.mu, q.Cp, q.kn, q.CT, q.st, vb - a.pre_prep[s]);
         __syncthreads();
     }
     if (!grid_barrier(a.bar, sets, S)) return;
@@ -154,9 +210,9 @@ __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
         if (item >= a.ntiles) break;
         const int s = find_set64(a.pre_tiles, S, item);
         const BatchSet &q = sets[s];
-        if (!q.st->finished) {
+        if (T.run[s] & 1) {
             const int64_t tile = item - a.pre_tiles[s];
-            if (!assign_f32_tile_t<BM>(q.X, q.M, a.L, a.Lp, q.Cp, q.kn, q.st->n_cur, q.mu, q.C, q.st, q.assign,
+            if (!assign_f32_tile_t<BM>(q.X, q.M, a.L, a.Lp, q.Cp, q.kn, T.ncur[s], q.mu, q.C, q.st, q.assign,
                                        q.e, q.flags, tile * BM, dsm, ash, u0, u1)) {
                 abort_all(a.bar);   // reported by the tile; its copies have been waited for
                 return;
@@ -167,26 +223,22 @@ __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
     if (!grid_barrier(a.bar, sets, S)) return;
 
     // 3: exact re-scoring; the flagged groups of all problems in problem order
-    if (tid == 0) {
-        int t = 0;
-        for (int s = 0; s < S; ++s)
-            if (!sets[s].st->finished) t += (sets[s].st->nflag + EX_R - 1) / EX_R;
-        s_total = t;
-    }
-    __syncthreads();
+    exact_prefix(sets, S, T);
     {
         uint32_t uses[2] = {0u, 0u};
-        const int total = s_total;
+        const int total = T.gpre[S];
         for (int item = blockIdx.x; item < total; item += grid) {
-            int s = 0, g = item;
-            for (; s < S; ++s) {
-                if (sets[s].st->finished) continue;
-                const int ng = (sets[s].st->nflag + EX_R - 1) / EX_R;
-                if (g < ng) break;
-                g -= ng;
+            int lo = 0, hi = S - 1;   // the problem s with gpre[s] <= item < gpre[s + 1]
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (T.gpre[mid] <= item)
+                    lo = mid;
+                else
+                    hi = mid - 1;
             }
+            const int s = lo, g = item - T.gpre[s];
             const BatchSet &q = sets[s];
-            if (!exact_group(q.X, a.L, a.Lp, q.CT, q.st->n_cur, q.st, q.flags, q.st->nflag, q.assign, q.e, g,
+            if (!exact_group(q.X, a.L, a.Lp, q.CT, T.ncur[s], q.st, q.flags, q.st->nflag, q.assign, q.e, g,
                              dsm, esh, uses)) {
                 abort_all(a.bar);
                 return;
@@ -199,8 +251,8 @@ __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
     for (int vb = blockIdx.x; vb < a.tot_hist; vb += grid) {
         const int s = find_set(a.pre_hist, S, vb);
         const BatchSet &q = sets[s];
-        if (!q.st->finished) {
-            body_hist(q.assign, q.e, q.M, q.R, q.st->n_cur, 1, q.table, q.dpart, q.st, vb - a.pre_hist[s]);
+        if (T.run[s] & 1) {
+            body_hist(q.assign, q.e, q.M, q.R, T.ncur[s], 1, q.table, q.dpart, q.st, vb - a.pre_hist[s]);
             if (last_block(q.st, (unsigned)(a.pre_hist[s + 1] - a.pre_hist[s])))
                 body_ctl(q.dpart, q.CH, q.st, MODE_TRAIN, a.theta, a.max_passes, q.N, nullptr, 0);
         }
@@ -209,11 +261,12 @@ __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
     if (!grid_barrier(a.bar, sets, S)) return;
 
     // 5: cell sizes and chunk prefixes; offsets and piece cells
+    load_states(sets, S, T);   // the stop tests of phase 4
     for (int vb = blockIdx.x; vb < a.tot_scan; vb += grid) {
         const int s = find_set(a.pre_scan, S, vb);
         const BatchSet &q = sets[s];
-        if (!skip_counts(q.st, 1)) {
-            const int N = q.st->n_cur;
+        if (T.run[s] & 1) {
+            const int N = T.ncur[s];
             body_scan<BP_THREADS / 32>(q.table, q.CH, N, q.counts, vb - a.pre_scan[s]);
             if (last_block(q.st, (unsigned)(a.pre_scan[s + 1] - a.pre_scan[s]))) {
                 body_offsets<BP_THREADS>(q.counts, N, q.off);
@@ -229,8 +282,8 @@ __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
     for (int vb = blockIdx.x; vb < a.tot_hist; vb += grid) {
         const int s = find_set(a.pre_hist, S, vb);
         const BatchSet &q = sets[s];
-        if (!skip_update(q.st, 1))
-            body_scatter(q.assign, q.M, q.R, q.table, q.off, q.st->n_cur, q.perm, vb - a.pre_hist[s]);
+        if (T.run[s] & 2)
+            body_scatter(q.assign, q.M, q.R, q.table, q.off, T.ncur[s], q.perm, vb - a.pre_hist[s]);
         __syncthreads();
     }
     if (!grid_barrier(a.bar, sets, S)) return;
@@ -240,16 +293,16 @@ __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
         const int s = find_set(a.pre_cellsum, S, vb);
         const BatchSet &q = sets[s];
         const int b = vb - a.pre_cellsum[s];
-        if (!skip_update(q.st, 1)) {
+        if (T.run[s] & 2) {
             switch (a.vec ? a.L : 0) {
-            case 4: cellsum_phase<1>(a, q, b); break;
-            case 8: cellsum_phase<2>(a, q, b); break;
-            case 16: cellsum_phase<4>(a, q, b); break;
-            case 32: cellsum_phase<8>(a, q, b); break;
-            case 64: cellsum_phase<16>(a, q, b); break;
-            case 128: cellsum_phase<32>(a, q, b); break;
+            case 4: cellsum_phase<1>(q, T.ncur[s], b); break;
+            case 8: cellsum_phase<2>(q, T.ncur[s], b); break;
+            case 16: cellsum_phase<4>(q, T.ncur[s], b); break;
+            case 32: cellsum_phase<8>(q, T.ncur[s], b); break;
+            case 64: cellsum_phase<16>(q, T.ncur[s], b); break;
+            case 128: cellsum_phase<32>(q, T.ncur[s], b); break;
             default:
-                body_cellsum_c_any(q.X, q.M, a.L, q.perm, q.off, q.qcell, q.st->n_cur, q.S, q.pieces,
+                body_cellsum_c_any(q.X, q.M, a.L, q.perm, q.off, q.qcell, T.ncur[s], q.S, q.pieces,
                                    q.cell_done, q.C, b);
             }
         }
@@ -275,7 +328,7 @@ __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
     }
 }
 
-size_t pass_smem(int L, int NMAXB)
+size_t pass_phase_smem(int L, int NMAXB)
 {
     const int Lp = round_up(L, 4);
     const size_t assign = (size_t)(Lp * BM + 2 * (Lp + 1) * BN) * sizeof(float);
@@ -286,14 +339,16 @@ size_t pass_smem(int L, int NMAXB)
     if (exact > m) m = exact;
     if (hist > m) m = hist;
     if (scatter > m) m = scatter;
-    return m;
+    return (m + 15) / 16 * 16;
 }
 
 }  // namespace
 
-int batch_pass_fit(int L, int NMAXB, size_t *smem)
+int batch_pass_fit(int S, int L, int NMAXB, size_t *phase_smem, size_t *smem)
 {
-    const size_t m = pass_smem(L, NMAXB);
+    if (S > BP_MAX_SETS) return 0;
+    *phase_smem = pass_phase_smem(L, NMAXB);
+    const size_t m = *phase_smem + sizeof(int) * (size_t)(3 * S + 1);
     *smem = m;
     if (cudaFuncSetAttribute(kb_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m) != cudaSuccess) {
         (void)cudaGetLastError();

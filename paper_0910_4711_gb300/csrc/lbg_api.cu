@@ -1133,10 +1133,10 @@ lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, 
     const bool vec = (reinterpret_cast<uintptr_t>(dX) & 15u) == 0;
 
     // ---- one persistent launch per pass, unless asked otherwise or it does not fit
-    size_t pass_smem = 0;
+    size_t pass_smem = 0, pass_phase_smem = 0;
     int pass_ctas = 0;
     if (!o.batched_per_phase && o.tile_rows == 0 && o.ctas_per_sm == 0) {
-        pass_ctas = batch_pass_fit(L, NMAXB, &pass_smem);
+        pass_ctas = batch_pass_fit(S, L, NMAXB, &pass_phase_smem, &pass_smem);
         if (pass_ctas > 2) pass_ctas = 2;
     }
     unsigned *dbar = reinterpret_cast<unsigned *>(ws + o_bar);
@@ -1168,6 +1168,7 @@ lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, 
     bp.max_passes = o.max_passes;
     bp.mult = o.split_multiplicative != 0;
     bp.vec = vec && (reinterpret_cast<uintptr_t>(dC) & 15u) == 0;
+    bp.phase_smem = pass_phase_smem;
 
     // ---- tile of the batched nearest-codevector launch (lbg_opts.autotune)
     int tile_rows = 128, ctas = 2;

@@ -343,10 +343,11 @@ struct BatchPass {
     unsigned *bar;              // [0] arrivals, [1] generation, [2] abort (zero before the first pass)
     double theta, delta;
     int max_passes, mult, vec;
+    size_t phase_smem;          // dynamic shared memory of the phases; the state tables follow
 };
 // Resident CTAs per SM the persistent pass can have (0: it does not fit) and its
 // dynamic shared memory.
-int batch_pass_fit(int L, int NMAXB, size_t *smem);
+int batch_pass_fit(int S, int L, int NMAXB, size_t *phase_smem, size_t *smem);
 // false if the cooperative launch was refused (then the per-phase launches run)
 bool launch_b_pass(const BatchPass &a, int ctas_per_sm, size_t smem, cudaStream_t s);
 
