@@ -137,6 +137,24 @@ constexpr int TC_NCH = 2;                      // independent min-chains of the 
                                                // epilogue warps of the sub-partition hide the
                                                // chains' latency; fewer chains, less bookkeeping)
 static_assert(TC_A_COL + 2 * ((TC_LMAX + 16) / 2) <= TC_TMEM_COLS, "accumulators + A exceed TMEM");
+
+// The A operand of a row (K BF16 elements, two per TMEM column): x~ and the
+// norm block.  For LK <= 32 the row also holds a second piece of x~:
+// x~ = x_hi + x_lo + rem with x_hi = bf16(x~), x_lo = bf16(x~ - x_hi) and
+// |rem| <= 2^-16 |x~|, so that rows whose centred values are not exact in BF16
+// (real-valued data) stay on the tensor cores: a tile with any x_lo != 0 gets
+// LK/16 more MMAs per job (x_lo . p_hi) and the certificate counts the terms
+// the pieces miss.  Layout [x_hi (LK) | x_lo (LK) | norm (16)], else
+// [x~ (LK) | norm (16)].
+template <int LK>
+struct TcA {
+    static constexpr bool SPLIT = LK <= 32;
+    static constexpr int KA = SPLIT ? 2 * LK + 16 : LK + 16;
+    static constexpr int COLS = KA / 2;                  // TMEM columns per accumulator
+    static constexpr int NORM = SPLIT ? 2 * LK : LK;    // element offset of the norm block
+};
+static_assert(TC_A_COL + 2 * TcA<32>::COLS <= TC_TMEM_COLS && TC_A_COL + 2 * TcA<64>::COLS <= TC_TMEM_COLS,
+              "accumulators + A exceed TMEM");
 static_assert(TC_HALF == 72 && GrpCfg<2>::GROUPS * 2 == TC_HALF && GrpCfg<8>::GROUPS * 8 == TC_HALF &&
                   GrpCfg<2>::GROUPS <= (1 << GrpCfg<2>::JBITS) && GrpCfg<8>::GROUPS <= (1 << GrpCfg<8>::JBITS),
               "epilogue loads 64 + 8 columns in whole groups");
@@ -348,27 +366,35 @@ __device__ __forceinline__ int xs_at(int r, int l)
 // past M), and the running sum of squares of those x~ in order.  Half 1 also
 // holds the norm block, filled in later.  FULL: L == LK, nothing to mask.
 template <int LK, int H, bool FULL>
-__device__ __forceinline__ void a_words(const __nv_bfloat16 *XS, int crow, int L, bool live, uint32_t *wv,
-                                        float &part)
+__device__ __forceinline__ void a_words(const __nv_bfloat16 *XS, const __nv_bfloat16 *XL, int crow, int L,
+                                        bool live, uint32_t *wv, float &part)
 {
-    constexpr int KA = LK + 16, HK = KA / 2, E0 = H * HK;
-    constexpr int XE = H == 0 ? HK : LK - HK;          // x~ elements in this half
+    constexpr int KA = TcA<LK>::KA, HK = KA / 2, E0 = H * HK;
+    constexpr int XEND = TcA<LK>::NORM;                // x~ elements (both pieces) end here
+    constexpr int XE = E0 + HK <= XEND ? HK : XEND - E0;   // x~ elements in this half
 #pragma unroll
     for (int w = 0; w < HK / 2; ++w) wv[w] = 0u;
 #pragma unroll
     for (int g = 0; g < XE / 8; ++g) {
-        const uint4 q = live ? *reinterpret_cast<const uint4 *>(XS + xs_at<LK>(crow, E0 + 8 * g))
+        // element E0 + 8 g: x_hi at l = e, or (split) x_lo at l = e - LK
+        const int e = E0 + 8 * g;
+        const bool lo_piece = TcA<LK>::SPLIT && e >= LK;
+        const int l8 = lo_piece ? e - LK : e;
+        const __nv_bfloat16 *src = lo_piece ? XL : XS;
+        const uint4 q = live ? *reinterpret_cast<const uint4 *>(src + xs_at<LK>(crow, l8))
                              : make_uint4(0u, 0u, 0u, 0u);
         const uint32_t qs[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int e0 = E0 + 8 * g + 2 * j;
+            const int e0 = l8 + 2 * j;
             const uint32_t lo = (FULL || e0 < L) ? (qs[j] & 0xFFFFu) : 0u;
             const uint32_t hi = (FULL || e0 + 1 < L) ? (qs[j] >> 16) : 0u;
             wv[4 * g + j] = lo | (hi << 16);
-            const float a = __uint_as_float(lo << 16), b = __uint_as_float(hi << 16);
-            part = fmaf(a, a, part);
-            part = fmaf(b, b, part);
+            if (!TcA<LK>::SPLIT) {   // ||x~||^2 of the exact form; the split form sums it apart
+                const float a = __uint_as_float(lo << 16), b = __uint_as_float(hi << 16);
+                part = fmaf(a, a, part);
+                part = fmaf(b, b, part);
+            }
         }
     }
 }
@@ -382,6 +408,15 @@ __host__ __device__ inline double tc_tau(int KB)
 
 // K of one B row: the pieces of c' (LK each) and the 16-element norm block.
 __host__ __device__ constexpr int tc_kb(int LK) { return TC_PIECES * LK + 16; }
+
+// Accumulated K of a job: x_hi . (p_hi + p_mid), x_lo . p_hi on a split tile,
+// the norm block.  tau of the split form also covers sum |x_lo p_hi| (below
+// 2^-7 of the rest): the factor 1 + 2^-6.
+__host__ __device__ constexpr int tc_keff(int LK) { return LK <= 32 ? 3 * LK + 16 : 2 * LK + 16; }
+__host__ __device__ inline double tc_tau_eff(int LK)
+{
+    return tc_tau(tc_keff(LK)) * (LK <= 32 ? 1.015625 : 1.0);
+}
 
 // Split an FP32 value into two BF16 pieces h + m; returns the remainder
 // v - h - m, which is exact in FP32 (each subtraction is; |v - h - m| <= 2^-16 |v|
@@ -476,7 +511,7 @@ __global__ void __launch_bounds__(256)
         uint32_t cbits = 0u;
         if (n < N) {
             const double sq = sqs[tid];
-            const double k = (2.0 * tc_tau(KB) + 1.1920928955078125e-7) * sq;   // 2 tau + 2^-23
+            const double k = (2.0 * tc_tau_eff(LK) + 1.1920928955078125e-7) * sq;   // 2 tau + 2^-23
             const float kf = __double2float_ru(k);
             s0s[tid] = __double2float_rn(sq - (double)kf);
             kn[n] = kf;
@@ -568,6 +603,8 @@ struct TcSmem {
     uint64_t full[3], empty[3], tfull[TC_SLOTS], tempty[TC_SLOTS], xfull, xempty, aready;
     uint32_t tmem_base;
     int abort, inexact, prod_last, mma_tile, mma_job, x_issued, x_done;
+    int xsplit;        // the (per-tile kernel's) tile has x_lo pieces
+    int xsplit2[2];    // the same per row tile of the persistent kernel, by parity
     union {   // the tail's two uses are separated by a named barrier
         struct {
             float v1[2][TC_ROWS], v2[2][TC_ROWS];   // the halves' top-2 (tail merge)
@@ -595,36 +632,55 @@ __device__ __forceinline__ bool named_sync_or(int id, int threads, bool v)
 
 // One centred x value into the staged BF16 rows; flags non-finite input and
 // values for which x~ = x - mu is not exact in FP32 (TwoSum error) or BF16.
+// In the split form (LK <= 32) x~ = fl(x - mu) need not be exact (the
+// certificate's centring term covers it) and its second BF16 piece goes to XL;
+// `split` records a nonzero second piece.
 template <int LK>
-__device__ __forceinline__ void tc_put_x(__nv_bfloat16 *XS, int i, int L, float xv,
-                                         const float *__restrict__ mu, bool &bad, bool &inexact)
+__device__ __forceinline__ void tc_put_x(__nv_bfloat16 *XS, __nv_bfloat16 *XL, int i, int L, float xv,
+                                         const float *__restrict__ mu, bool &bad, bool &inexact, bool &split)
 {
     const int r = i / L, l = i - r * L;
     bad = bad || !isfinite(xv);
     const float ml = __ldg(mu + l);
     const float v = __fsub_rn(xv, ml);
-    const float bb = __fsub_rn(v, xv);
-    const float err = __fadd_rn(__fsub_rn(xv, __fsub_rn(v, bb)), __fsub_rn(-ml, bb));
     const __nv_bfloat16 b = __float2bfloat16_rn(v);
-    inexact = inexact || err != 0.f || (__bfloat162float(b) != v);
+    if constexpr (TcA<LK>::SPLIT) {
+        const __nv_bfloat16 lo = __float2bfloat16_rn(__fsub_rn(v, __bfloat162float(b)));   // v - b exact
+        split = split || __bfloat162float(lo) != 0.f;
+        XL[xs_at<LK>(r, l)] = lo;
+    } else {
+        const float bb = __fsub_rn(v, xv);
+        const float err = __fadd_rn(__fsub_rn(xv, __fsub_rn(v, bb)), __fsub_rn(-ml, bb));
+        inexact = inexact || err != 0.f || (__bfloat162float(b) != v);
+    }
     XS[xs_at<LK>(r, l)] = b;
 }
 
 // The A operand in tensor memory: each epilogue thread writes its half of its
-// row's K = LK + 16 BF16 (two per column): x~ (zero past L and for rows past
-// M), then in half 1 the norm block 1 1 1 (x s0 pieces), X2 = ||x~||^2 in
-// three BF16 pieces, zeros.  ||x~||^2 is half 0's sum of squares plus half 1's
-// in that order.  Returns ||x~||^2 of the thread's row; the caller fences and
-// synchronises before the MMAs read A.
+// row's K = TcA<LK>::KA BF16 (two per column): x~ (both pieces in the split
+// form; zero past L and for rows past M), then in half 1 the norm block 1 1 1
+// (x s0 pieces), X2 = ||x~||^2 in three BF16 pieces, zeros.  ||x~||^2 is half
+// 0's sum of squares plus half 1's in that order.  Returns ||x~||^2 of the
+// thread's row; the caller fences and synchronises before the MMAs read A.
 template <int LK, bool FULL>
-__device__ __forceinline__ float tc_write_a(const __nv_bfloat16 *XS, int L, bool live, int crow, int half,
-                                            int acc, int warp, uint32_t tmem, TcSmem &sh)
+__device__ __forceinline__ float tc_write_a(const __nv_bfloat16 *XS, const __nv_bfloat16 *XL, int L, bool live,
+                                            int crow, int half, int acc, int warp, uint32_t tmem, TcSmem &sh)
 {
-    constexpr int KA = LK + 16, NW = KA / 4;
+    constexpr int KA = TcA<LK>::KA, NW = KA / 4;
     uint32_t wv[NW];
     float part = 0.f;
-    if (half == 0) a_words<LK, 0, FULL>(XS, crow, L, live, wv, part);
-    else a_words<LK, 1, FULL>(XS, crow, L, live, wv, part);
+    if (half == 0) a_words<LK, 0, FULL>(XS, XL, crow, L, live, wv, part);
+    else a_words<LK, 1, FULL>(XS, XL, crow, L, live, wv, part);
+    if (TcA<LK>::SPLIT && live) {
+        // ||x~||^2 as sum (x_hi + x_lo)^2 in index order, half 0 over l < LK / 2 (the rest in
+        // half 1); it differs from ||x~||^2 by less than 2^-14 ||x~||^2 besides rounding
+#pragma unroll
+        for (int l = half * (LK / 2); l < (half + 1) * (LK / 2); ++l) {
+            if (!FULL && l >= L) break;
+            const float v = __bfloat162float(XS[xs_at<LK>(crow, l)]) + __bfloat162float(XL[xs_at<LK>(crow, l)]);
+            part = fmaf(v, v, part);
+        }
+    }
     sh.r.d[half][crow] = part;
     named_sync(1, 32 * TC_EPI_WARPS);
     const float xn2 = __fadd_rn(sh.r.d[0][crow], sh.r.d[1][crow]);
@@ -632,7 +688,7 @@ __device__ __forceinline__ float tc_write_a(const __nv_bfloat16 *XS, int L, bool
         __nv_bfloat16 h, mi, lo;
         split3(xn2, h, mi, lo);
         const uint32_t one = __bfloat16_as_ushort(__float2bfloat16_rn(1.f));
-        constexpr int w0 = (LK - KA / 2) / 2;   // first norm-block word
+        constexpr int w0 = (TcA<LK>::NORM - KA / 2) / 2;   // first norm-block word of half 1
         wv[w0] = one | (one << 16);
         wv[w0 + 1] = one | ((uint32_t)__bfloat16_as_ushort(h) << 16);
         wv[w0 + 2] = (uint32_t)__bfloat16_as_ushort(mi) | ((uint32_t)__bfloat16_as_ushort(lo) << 16);
@@ -647,16 +703,10 @@ __device__ __forceinline__ float tc_write_a(const __nv_bfloat16 *XS, int L, bool
 // (accumulator slot (j0 + 2t + acc) % 3); the thread's 72 values per job go
 // through the group top-2; returns the merged (V1, V2, group's first column)
 // of the thread's half: V1 the smallest group minimum, V2 the second smallest
-// (the smallest value outside V1's group).  hook(t) runs after job t in every epilogue warp (it may use
-// named barriers: after a time-out, sh.abort, the jobs are skipped but the
-// hooks still run).
-struct NoHook {
-    __device__ __forceinline__ void operator()(int) const {}
-};
-template <int GRP, class Hook = NoHook>
+// (the smallest value outside V1's group).
+template <int GRP>
 __device__ __forceinline__ void tc_jobs(TcSmem &sh, uint32_t tmem, int warp, int lane, int acc, int half,
-                                        int ntiles, int j0, int keymask, float &V1, float &V2, int &i1,
-                                        const Hook &hook = Hook())
+                                        int ntiles, int j0, int keymask, float &V1, float &V2, int &i1)
 {
     constexpr int NCH = TC_NCH;
     constexpr int JMASK = (1 << GrpCfg<GRP>::JBITS) - 1;
@@ -682,7 +732,6 @@ __device__ __forceinline__ void tc_jobs(TcSmem &sh, uint32_t tmem, int warp, int
         }
         if (sh.abort || !mbar_wait_bounded_sleep(&sh.tfull[slot], par)) {
             sh.abort = 1;
-            hook(t);
             continue;
         }
         tc_fence_after();
@@ -702,7 +751,6 @@ __device__ __forceinline__ void tc_jobs(TcSmem &sh, uint32_t tmem, int warp, int
         GroupSteps<GRP, GrpCfg<GRP>::GROUPS>::run(v, c1, c2, keymask);
 #pragma unroll
         for (int q = 0; q < NCH; ++q) cg[q] = c1[q] < s1[q] ? t : cg[q];
-        hook(t);
     }
     // merge the chains; i1 is the first column of the minimum's group:
     // tile * TC_NT + half * TC_HALF + GRP * (the low bits)
@@ -732,55 +780,38 @@ __device__ __forceinline__ void tc_jobs(TcSmem &sh, uint32_t tmem, int warp, int
 // by more than the rounding bound of the FP32 sums, runs the certificates,
 // and writes a(m), e(m) or flags the row.  `usable` = the tile's x~ and the
 // codebook split are exact.
-// The tail of a row tile in stages, so that the persistent kernel can spread
-// them over the next tile's jobs: stage 0 merges the halves' top-2, stages
-// 1 .. GRP/2 each score one group member per half, the last stage decides and
-// certifies.  TailState carries a thread's row between stages.
-struct TailState {
-    float V1, V2, xn2, kmax;
-    int i1;
-    bool usable_tile, usable;
-    int64_t m0;
-};
-template <int GRP>
-__host__ __device__ constexpr int tail_stages() { return 2 + GRP / 2; }
-
-// Not inlined: the persistent kernel calls it between jobs, and its registers
-// must not add to those of the job loop.
+// `xsplit`: the tile's x~ has second BF16 pieces (split form).
 template <int LK, int GRP>
-__device__ __noinline__ void tc_tail_stage(int stage, TailState &ts, TcSmem &sh, int warp, int lane, int acc,
-                                              int half, int rr, const float *__restrict__ X, int64_t M, int L,
-                                              int N, const float *__restrict__ C, const float *__restrict__ kn,
-                                              float cmax, float rho, DevState *st, int32_t *__restrict__ assign,
-                                              float *__restrict__ e, int32_t *__restrict__ flags,
-                                              int64_t flag_base)
+__device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc, int half, int rr,
+                                        int64_t m0, const float *__restrict__ X, int64_t M, int L, int N,
+                                        const float *__restrict__ C, const float *__restrict__ kn, float xn2,
+                                        bool usable_tile, bool xsplit, float cmax, float rho, float V1, float V2,
+                                        int i1, DevState *st,
+                                        int32_t *__restrict__ assign, float *__restrict__ e,
+                                        int32_t *__restrict__ flags, int64_t flag_base)
 {
     const int crow = 128 * acc + rr;
-    const int64_t m0 = ts.m0, m = m0 + crow;
-    if (stage == 0) {
-        sh.m.v1[half][crow] = ts.V1;
-        sh.m.v2[half][crow] = ts.V2;
-        sh.m.i1[half][crow] = ts.i1;
-        named_sync(1, 32 * TC_EPI_WARPS);
+    const int64_t m = m0 + crow;
+    sh.m.v1[half][crow] = V1;
+    sh.m.v2[half][crow] = V2;
+    sh.m.i1[half][crow] = i1;
+    named_sync(1, 32 * TC_EPI_WARPS);
+    {
         const float A1 = sh.m.v1[0][crow], A2 = sh.m.v2[0][crow], B1 = sh.m.v1[1][crow], B2 = sh.m.v2[1][crow];
         const int ai = sh.m.i1[0][crow], bi = sh.m.i1[1][crow];
-        ts.V2 = fminf(fminf(A2, B2), fmaxf(A1, B1));
+        V2 = fminf(fminf(A2, B2), fmaxf(A1, B1));
         const bool take = B1 < A1 || (B1 == A1 && bi < ai);
-        ts.V1 = take ? B1 : A1;
-        ts.i1 = take ? bi : ai;
-        named_sync(2, 32 * TC_EPI_WARPS);   // merge inputs read: sh.r may now overwrite sh.m
-        ts.usable = m < M && !sh.abort && ts.usable_tile && ts.i1 >= 0 && ts.i1 < N && ts.V1 < INFINITY;
-        ts.kmax = 0.f;
-        return;
+        V1 = take ? B1 : A1;
+        i1 = take ? bi : ai;
     }
-    const int i1 = ts.i1;
-    const bool usable = ts.usable;
-    if (stage <= GRP / 2) {
-        // the best group is codevectors i1 .. i1 + GRP - 1; this half scores member
-        // i1 + (GRP / 2) half + g
-        const int g = stage - 1;
-        const bool coop = (L & 3) == 0 && ((reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(X)) & 15u) == 0;
-        float kmax = ts.kmax;
+    named_sync(2, 32 * TC_EPI_WARPS);   // merge inputs read: sh.r may now overwrite sh.m
+    const bool usable = m < M && !sh.abort && usable_tile && i1 >= 0 && i1 < N && V1 < INFINITY;
+    // the best group is codevectors i1 .. i1 + GRP - 1; this half scores members
+    // i1 + (GRP / 2) half + g
+    float kmax = 0.f;
+    const bool coop = (L & 3) == 0 && ((reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(X)) & 15u) == 0;
+#pragma unroll 1
+    for (int g = 0; g < GRP / 2; ++g) {
         const int cand = i1 + (GRP / 2) * half + g;
         const int ccand = (usable && cand < N) ? cand : -1;
         if (ccand >= 0) kmax = fmaxf(kmax, __ldg(kn + ccand));
@@ -840,11 +871,8 @@ __device__ __noinline__ void tc_tail_stage(int stage, TailState &ts, TcSmem &sh,
             dc = d2;
         }
         sh.r.d[(GRP / 2) * half + g][crow] = dc;
-        ts.kmax = kmax;
-        return;
     }
-    const float V1 = ts.V1, V2 = ts.V2, xn2 = ts.xn2;
-    sh.r.k[half][crow] = ts.kmax;
+    sh.r.k[half][crow] = kmax;
     named_sync(2, 32 * TC_EPI_WARPS);
     if (half == 0 && m < M && !sh.abort) {
         // the group member with the smallest FP32 direct-form distance wins when every other
@@ -870,17 +898,23 @@ __device__ __noinline__ void tc_tail_stage(int stage, TailState &ts, TcSmem &sh,
             // k' of the member that produced V1 is unknown: the group's largest bounds it
             const float ka = fmaxf(sh.r.k[0][crow], sh.r.k[1][crow]);
             if (sure) {
-                const double tau = tc_tau(tc_kb(LK));
+                const double tau = tc_tau_eff(LK);
                 const float xn2u = xn2 * SLOP;
                 const float R = 2.f * (float)tau * xn2u * SLOP;
                 const float eta = U32 * (sqrtf(xn2u) + cmax) * SLOP;
                 // index packing of the group minima
                 const float pack = GrpCfg<GRP>::PACK * (fabsf(V1) + fabsf(V2));
                 // the MMA sums x~ . (p_hi + p_mid) and misses x~ . r_n, r_n = c'_n - p_hi - p_mid:
-                // |x~ . r_n| <= ||x~|| rho for every n (Cauchy-Schwarz)
-                const float E = sqrtf(xn2u) * rho * SLOP;
-                // |fl(||x~||^2) - ||x~||^2|: X2 as the MMA saw it
-                const float xerr = (float)(L + 2) * U32 * xn2u;
+                // |x~ . r_n| <= ||x~|| rho for every n (Cauchy-Schwarz).  A split tile sums
+                // x_hi . (p_hi + p_mid) + x_lo . p_hi instead: it misses x_hi . r_n (<= ||x~|| rho
+                // (1 + 2^-8)), x_lo . (p_mid + r_n) and rem . c'_n, with ||x_lo|| <= 2^-8 ||x~||,
+                // ||p_mid|| <= 2^-8 (1 + 2^-8) ||c'||, ||rem|| <= 2^-16 ||x~|| and ||c'|| <= 2 cmax:
+                // all within ||x~|| (rho (1 + 2^-7) + 2^-14 (1 + 2^-7) cmax)
+                const float E = xsplit ? sqrtf(xn2u) * (rho + 6.103515625e-05f * cmax) * 1.0078125f * SLOP
+                                         : sqrtf(xn2u) * rho * SLOP;
+                // |fl(||x~||^2) - ||x~||^2|: X2 as the MMA saw it (a split tile's X2 is
+                // sum (x_hi + x_lo)^2: another 2^-14 ||x~||^2)
+                const float xerr = (float)(L + 2) * U32 * xn2u + (xsplit ? 6.103515625e-05f * xn2u : 0.f);
                 // the member j that produced V1 has ||x~ - c~_j||^2 - k'_j ~ V1 (X2 included), and
                 // the winner ii is not farther than j: bound its g1^2 from above
                 const float g1sq = V1 + 2.f * ka + R + pack + E + xerr;
@@ -906,20 +940,21 @@ __device__ __noinline__ void tc_tail_stage(int stage, TailState &ts, TcSmem &sh,
 }
 
 
-template <int LK, int GRP>
-__device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc, int half, int rr,
-                                        int64_t m0, const float *__restrict__ X, int64_t M, int L, int N,
-                                        const float *__restrict__ C, const float *__restrict__ kn, float xn2,
-                                        bool usable_tile, float cmax, float rho, float V1, float V2, int i1,
-                                        DevState *st,
-                                        int32_t *__restrict__ assign, float *__restrict__ e,
-                                        int32_t *__restrict__ flags, int64_t flag_base)
+// One job's MMAs (not the JOB9 form): x_hi . p_hi, x_hi . p_mid, x_lo . p_hi on
+// a split tile, and the norm block; d the accumulator, at the A operand.
+template <int LK>
+__device__ __forceinline__ void mma_job_elect(uint32_t d, uint32_t at, uint64_t bst, bool xsplit)
 {
-    TailState ts{V1, V2, xn2, 0.f, i1, usable_tile, false, m0};
-#pragma unroll 1
-    for (int sg = 0; sg < tail_stages<GRP>(); ++sg)
-        tc_tail_stage<LK, GRP>(sg, ts, sh, warp, lane, acc, half, rr, X, M, L, N, C, kn, cmax, rho, st, assign, e,
-                               flags, flag_base);
+#pragma unroll
+    for (int seg = 0; seg < TC_PIECES; ++seg)
+#pragma unroll
+        for (int kk = 0; kk < LK / 16; ++kk)
+            mma_bf16_ta_elect(d, at + (uint32_t)(8 * kk), bst + (uint64_t)(seg * LK + kk * 16), (seg | kk) ? 1u : 0u);
+    if (TcA<LK>::SPLIT && xsplit)
+#pragma unroll
+        for (int kk = 0; kk < LK / 16; ++kk)
+            mma_bf16_ta_elect(d, at + (uint32_t)(LK / 2 + 8 * kk), bst + (uint64_t)(kk * 16), 1u);
+    mma_bf16_ta_elect(d, at + (uint32_t)(TcA<LK>::NORM / 2), bst + (uint64_t)(TC_PIECES * LK), 1u);
 }
 
 // ---------------------------------------------------------------- one CTA per row tile
@@ -944,9 +979,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     constexpr int XSTR = XsRow<LK>::STR;                       // staged row stride (BF16)
     constexpr uint32_t sbo_b = (uint32_t)(KB / 8) * 128u;
     constexpr uint32_t xs_bytes = (uint32_t)TC_ROWS * XSTR * 2u;
+    constexpr uint32_t xl_bytes = TcA<LK>::SPLIT ? xs_bytes : 0u;   // x_lo rows (split form)
     constexpr uint32_t stage_bytes = (uint32_t)TC_NT * KB * 2u;
     __nv_bfloat16 *XS = reinterpret_cast<__nv_bfloat16 *>(smem);
-    uint8_t *Bs = smem + xs_bytes;
+    __nv_bfloat16 *XL = reinterpret_cast<__nv_bfloat16 *>(smem + xs_bytes);
+    uint8_t *Bs = smem + xs_bytes + xl_bytes;
     const int64_t m0 = (int64_t)blockIdx.x * TC_ROWS;
 
     if (tid == 0) {
@@ -961,6 +998,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         fence_mbar_init();
         sh.abort = 0;
         sh.inexact = 0;
+        sh.xsplit = 0;
         sh.prod_last = -1;
         sh.mma_tile = -1;
         sh.mma_job = -1;
@@ -988,7 +1026,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         constexpr int ST = 32 * TC_EPI_WARPS;                 // 512 staging threads
         const int et = tid - 64;
         const int64_t rows = M - m0 < TC_ROWS ? M - m0 : TC_ROWS;
-        bool inexact = false, bad = false;
+        bool inexact = false, bad = false, split = false;
         const float *Xt = X + m0 * L;
         const int total = (int)rows * L;
         if ((L & 3) == 0 && (reinterpret_cast<uintptr_t>(Xt) & 15u) == 0) {
@@ -1002,24 +1040,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int f = 4 * (i + u * ST);
-                    tc_put_x<LK>(XS, f, L, q[u].x, mu, bad, inexact);
-                    tc_put_x<LK>(XS, f + 1, L, q[u].y, mu, bad, inexact);
-                    tc_put_x<LK>(XS, f + 2, L, q[u].z, mu, bad, inexact);
-                    tc_put_x<LK>(XS, f + 3, L, q[u].w, mu, bad, inexact);
+                    tc_put_x<LK>(XS, XL, f, L, q[u].x, mu, bad, inexact, split);
+                    tc_put_x<LK>(XS, XL, f + 1, L, q[u].y, mu, bad, inexact, split);
+                    tc_put_x<LK>(XS, XL, f + 2, L, q[u].z, mu, bad, inexact, split);
+                    tc_put_x<LK>(XS, XL, f + 3, L, q[u].w, mu, bad, inexact, split);
                 }
             }
             for (; i < total4; i += ST) {
                 const float4 q = __ldg(X4 + i);
-                tc_put_x<LK>(XS, 4 * i, L, q.x, mu, bad, inexact);
-                tc_put_x<LK>(XS, 4 * i + 1, L, q.y, mu, bad, inexact);
-                tc_put_x<LK>(XS, 4 * i + 2, L, q.z, mu, bad, inexact);
-                tc_put_x<LK>(XS, 4 * i + 3, L, q.w, mu, bad, inexact);
+                tc_put_x<LK>(XS, XL, 4 * i, L, q.x, mu, bad, inexact, split);
+                tc_put_x<LK>(XS, XL, 4 * i + 1, L, q.y, mu, bad, inexact, split);
+                tc_put_x<LK>(XS, XL, 4 * i + 2, L, q.z, mu, bad, inexact, split);
+                tc_put_x<LK>(XS, XL, 4 * i + 3, L, q.w, mu, bad, inexact, split);
             }
         } else {
-            for (int i = et; i < total; i += ST) tc_put_x<LK>(XS, i, L, __ldg(Xt + i), mu, bad, inexact);
+            for (int i = et; i < total; i += ST)
+                tc_put_x<LK>(XS, XL, i, L, __ldg(Xt + i), mu, bad, inexact, split);
         }
         if (bad) flag_error(st, ERR_NONFINITE);
         if (inexact) sh.inexact = 1;
+        if (split) sh.xsplit = 1;
     }
     tc_fence_before();
     __syncthreads();
@@ -1031,9 +1071,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const float rho = __uint_as_float(st->rho_bits);
 
     float xn2 = 0.f;
+    const bool xsplit = sh.xsplit != 0;
     if (epi)
-        xn2 = L == LK ? tc_write_a<LK, true>(XS, L, m < M, crow, half, acc, warp, tmem, sh)
-                      : tc_write_a<LK, false>(XS, L, m < M, crow, half, acc, warp, tmem, sh);
+        xn2 = L == LK ? tc_write_a<LK, true>(XS, XL, L, m < M, crow, half, acc, warp, tmem, sh)
+                      : tc_write_a<LK, false>(XS, XL, L, m < M, crow, half, acc, warp, tmem, sh);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -1084,14 +1125,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(slot * TC_NT);
-                const uint32_t at = tmem + (uint32_t)(TC_A_COL + a * ((LK + 16) / 2));
-#pragma unroll
-                for (int seg = 0; seg < TC_PIECES; ++seg)
-#pragma unroll
-                    for (int kk = 0; kk < LK / 16; ++kk)
-                        mma_bf16_ta_elect(d, at + (uint32_t)(8 * kk), bst + (uint64_t)(seg * LK + kk * 16),
-                                          (seg | kk) ? 1u : 0u);
-                mma_bf16_ta_elect(d, at + (uint32_t)(LK / 2), bst + (uint64_t)(TC_PIECES * LK), 1u);
+                const uint32_t at = tmem + (uint32_t)(TC_A_COL + a * TcA<LK>::COLS);
+                mma_job_elect<LK>(d, at, bst, xsplit);
                 mma_commit_elect(&sh.tfull[slot]);
                 if (lane == 0) sh.mma_job = j;
             }
@@ -1107,7 +1142,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         int i1;
         tc_jobs<GRP>(sh, tmem, warp, lane, acc, half, ntiles, 0, keymask, V1, V2, i1);
         tc_tail<LK, GRP>(sh, warp, lane, acc, half, rr, m0, X, M, L, N, C, kn, xn2, !sh.inexact && tc_exact_cb,
-                    cmax, rho, V1, V2, i1, st, assign, e, flags, flag_base);
+                         xsplit, cmax, rho, V1, V2, i1, st, assign, e, flags, flag_base);
     }
 
     tc_fence_before();
@@ -1170,9 +1205,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     constexpr uint32_t sbo_b = (uint32_t)(KB / 8) * 128u;
     constexpr uint32_t stage_bytes = (uint32_t)TC_NT * KB * 2u;
     constexpr uint32_t xs_bytes = (uint32_t)TC_ROWS * XSTR * 2u;
+    constexpr uint32_t xl_bytes = TcA<LK>::SPLIT ? xs_bytes : 0u;   // x_lo rows (split form)
     uint8_t *Bs = smem;
     __nv_bfloat16 *XS = reinterpret_cast<__nv_bfloat16 *>(smem + TC_PSTAGES * stage_bytes);
-    float *XF = reinterpret_cast<float *>(smem + TC_PSTAGES * stage_bytes + xs_bytes);
+    __nv_bfloat16 *XL = reinterpret_cast<__nv_bfloat16 *>(smem + TC_PSTAGES * stage_bytes + xs_bytes);
+    float *XF = reinterpret_cast<float *>(smem + TC_PSTAGES * stage_bytes + xs_bytes + xl_bytes);
     auto tile_m0 = [&](int k) -> int64_t {
         return ((int64_t)blockIdx.x + (int64_t)k * gridDim.x) * TC_ROWS;
     };
@@ -1200,6 +1237,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         sh.mma_job = -1;
         sh.x_issued = -1;
         sh.x_done = -1;
+        sh.xsplit2[0] = sh.xsplit2[1] = 0;
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -1281,6 +1319,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 ok = false;
                 break;
             }
+            const bool xsp = sh.xsplit2[k & 1] != 0;   // published before aready
             for (int t = 0; t < ntiles && ok; ++t) {
                 if (!__all_sync(0xffffffffu, mbar_wait_bounded_sleep(&sh.full[s], gpar))) {
                     ok = false;
@@ -1297,17 +1336,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tc_fence_after();
                     const uint32_t d = tmem + (uint32_t)(slot * TC_NT);
                     if (JOB9) {
-                        job9_elect(d, tmem + (uint32_t)(TC_A_COL + a * ((LK + 16) / 2)), bst,
+                        job9_elect(d, tmem + (uint32_t)(TC_A_COL + a * TcA<LK>::COLS), bst,
                                    smem_addr(&sh.tfull[slot]));
                     } else {
-                        const uint32_t at = tmem + (uint32_t)(TC_A_COL + a * ((LK + 16) / 2));
-#pragma unroll
-                        for (int seg = 0; seg < TC_PIECES; ++seg)
-#pragma unroll
-                            for (int kk = 0; kk < LK / 16; ++kk)
-                                mma_bf16_ta_elect(d, at + (uint32_t)(8 * kk),
-                                                  bst + (uint64_t)(seg * LK + kk * 16), (seg | kk) ? 1u : 0u);
-                        mma_bf16_ta_elect(d, at + (uint32_t)(LK / 2), bst + (uint64_t)(TC_PIECES * LK), 1u);
+                        mma_job_elect<LK>(d, tmem + (uint32_t)(TC_A_COL + a * TcA<LK>::COLS), bst, xsp);
                         mma_commit_elect(&sh.tfull[slot]);
                     }
                     last_job = j++;
@@ -1340,14 +1372,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int et = tid - 64;
         float pV1 = INFINITY, pV2 = INFINITY, pxn2 = 0.f;
         int pi1 = -1;
-        bool pusable = false, next_exact = false;
-        bool cv_bad = false, cv_inexact = false;
+        bool pusable = false, next_exact = false, next_split = false, psplit = false;
+        bool cv_bad = false, cv_inexact = false, cv_split = false;
         // Convert piece c (of NCHUNK) of x tile kk from XF into centred BF16
         // rows in XS; the last piece publishes the tile's exactness and frees XF.
         auto convert = [&](int kk, int c) {
             if (c == 0) {
                 cv_bad = false;
                 cv_inexact = false;
+                cv_split = false;
                 if (!sh.abort) {
                     if (!mbar_wait_bounded_sleep(&sh.xfull, (uint32_t)kk & 1u)) sh.abort = 1;
                     else if (tid == 64) sh.x_done = kk;   // xfull phases observed: 0 .. kk
@@ -1370,78 +1403,76 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         const float4 q = X4[i];
                         const float xv[4] = {q.x, q.y, q.z, q.w};
                         const float mv[4] = {m4.x, m4.y, m4.z, m4.w};
-                        uint32_t bits[4];
+                        uint32_t bits[4], lbits[4];
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             cv_bad = cv_bad || !isfinite(xv[u]);
                             const float v = __fsub_rn(xv[u], mv[u]);
-                            const float bb = __fsub_rn(v, xv[u]);
-                            const float err = __fadd_rn(__fsub_rn(xv[u], __fsub_rn(v, bb)), __fsub_rn(-mv[u], bb));
                             const __nv_bfloat16 b = __float2bfloat16_rn(v);
-                            cv_inexact = cv_inexact || err != 0.f || (__bfloat162float(b) != v);
+                            if constexpr (TcA<LK>::SPLIT) {
+                                const __nv_bfloat16 lo = __float2bfloat16_rn(__fsub_rn(v, __bfloat162float(b)));
+                                cv_split = cv_split || __bfloat162float(lo) != 0.f;
+                                lbits[u] = __bfloat16_as_ushort(lo);
+                            } else {
+                                const float bb = __fsub_rn(v, xv[u]);
+                                const float err =
+                                    __fadd_rn(__fsub_rn(xv[u], __fsub_rn(v, bb)), __fsub_rn(-mv[u], bb));
+                                cv_inexact = cv_inexact || err != 0.f || (__bfloat162float(b) != v);
+                                lbits[u] = 0u;
+                            }
                             bits[u] = __bfloat16_as_ushort(b);
                         }
                         *reinterpret_cast<uint2 *>(XS + xs_at<LK>(r, l0)) =
                             make_uint2(bits[0] | (bits[1] << 16), bits[2] | (bits[3] << 16));
+                        if (TcA<LK>::SPLIT)
+                            *reinterpret_cast<uint2 *>(XL + xs_at<LK>(r, l0)) =
+                                make_uint2(lbits[0] | (lbits[1] << 16), lbits[2] | (lbits[3] << 16));
                     }
                 } else {
                     for (int i = lo + et; i < hi; i += ST) {
                         const float4 q = X4[i];
-                        tc_put_x<LK>(XS, 4 * i, L, q.x, mu, cv_bad, cv_inexact);
-                        tc_put_x<LK>(XS, 4 * i + 1, L, q.y, mu, cv_bad, cv_inexact);
-                        tc_put_x<LK>(XS, 4 * i + 2, L, q.z, mu, cv_bad, cv_inexact);
-                        tc_put_x<LK>(XS, 4 * i + 3, L, q.w, mu, cv_bad, cv_inexact);
+                        tc_put_x<LK>(XS, XL, 4 * i, L, q.x, mu, cv_bad, cv_inexact, cv_split);
+                        tc_put_x<LK>(XS, XL, 4 * i + 1, L, q.y, mu, cv_bad, cv_inexact, cv_split);
+                        tc_put_x<LK>(XS, XL, 4 * i + 2, L, q.z, mu, cv_bad, cv_inexact, cv_split);
+                        tc_put_x<LK>(XS, XL, 4 * i + 3, L, q.w, mu, cv_bad, cv_inexact, cv_split);
                     }
                 }
             }
             if (c == NCHUNK - 1) {
                 if (cv_bad) flag_error(st, ERR_NONFINITE);
                 next_exact = !named_sync_or(1, 32 * TC_EPI_WARPS, cv_inexact);
+                next_split = TcA<LK>::SPLIT && named_sync_or(1, 32 * TC_EPI_WARPS, cv_split);
                 if (tid == 64 && !sh.abort) mbar_arrive(&sh.xempty);   // XF may take the next x tile
             }
         };
-        // Tile k's boundary: its x tile is converted (at tile k - 1's middle job,
-        // or here for tile 0), its A operand written once tile k - 1's MMAs are
-        // done (all 16 warps consumed its last jobs before the named barrier),
-        // and the tensor pipe released on it; tile k - 1's tail then runs in
-        // stages after tile k's first jobs, so the pipe is not left waiting on it.
-        constexpr int NST = tail_stages<GRP>();
-        const int conv_at = ntiles / 2;
-        bool converted = false;
         for (int k = 0; k <= K; ++k) {
             float xn2 = 0.f;
-            bool tile_exact = false;
+            bool tile_exact = false, tile_split = false;
             if (k < K) {
-                if (!converted)
-                    for (int c = 0; c < NCHUNK; ++c) convert(k, c);
-                converted = false;
+                // convert x tile k (it is in XF) into centred BF16 rows; then, all 16
+                // warps having consumed the previous tile's last jobs (before the
+                // conversion's named barrier), its MMAs are done and A may be rewritten
+                for (int c = 0; c < NCHUNK; ++c) convert(k, c);
                 tile_exact = next_exact;
-                xn2 = L == LK ? tc_write_a<LK, true>(XS, L, tile_m0(k) + crow < M, crow, half, acc, warp, tmem, sh)
-                              : tc_write_a<LK, false>(XS, L, tile_m0(k) + crow < M, crow, half, acc, warp, tmem, sh);
+                tile_split = next_split;
+                xn2 = L == LK ? tc_write_a<LK, true>(XS, XL, L, tile_m0(k) + crow < M, crow, half, acc, warp, tmem, sh)
+                              : tc_write_a<LK, false>(XS, XL, L, tile_m0(k) + crow < M, crow, half, acc, warp, tmem, sh);
                 tc_fence_before();
                 named_sync(1, 32 * TC_EPI_WARPS);
-                if (tid == 64) mbar_arrive(&sh.aready);
+                if (tid == 64) {
+                    sh.xsplit2[k & 1] = tile_split ? 1 : 0;   // read by the MMA issuer after aready
+                    mbar_arrive(&sh.aready);
+                }
             }
-            TailState ts{pV1, pV2, pxn2, 0.f, pi1, pusable, false, k >= 1 ? tile_m0(k - 1) : 0};
-            auto tail = [&](int sg) {
-                tc_tail_stage<LK, GRP>(sg, ts, sh, warp, lane, acc, half, rr, X, M, L, N, C, kn, cmax, rho, st,
-                                       assign, e, flags, flag_base);
-            };
+            // the previous tile's tail runs while the tensor pipe starts on this one
+            if (k >= 1)
+                tc_tail<LK, GRP>(sh, warp, lane, acc, half, rr, tile_m0(k - 1), X, M, L, N, C, kn, pxn2, pusable,
+                                 psplit, cmax, rho, pV1, pV2, pi1, st, assign, e, flags, flag_base);
             if (k < K) {
-                auto hook = [&](int t) {
-                    if (k >= 1 && t < NST) tail(t);
-                    if (t == conv_at && k + 1 < K) {
-                        for (int c = 0; c < NCHUNK; ++c) convert(k + 1, c);
-                        converted = true;
-                    }
-                };
-                tc_jobs<GRP>(sh, tmem, warp, lane, acc, half, ntiles, 2 * k * ntiles, keymask, pV1, pV2, pi1, hook);
-                if (k >= 1)
-                    for (int sg = ntiles < NST ? ntiles : NST; sg < NST; ++sg) tail(sg);
+                tc_jobs<GRP>(sh, tmem, warp, lane, acc, half, ntiles, 2 * k * ntiles, keymask, pV1, pV2, pi1);
                 pxn2 = xn2;
                 pusable = tile_exact && tc_exact_cb;
-            } else if (k >= 1) {
-                for (int sg = 0; sg < NST; ++sg) tail(sg);
+                psplit = tile_split;
             }
         }
     }
@@ -1513,8 +1544,8 @@ static void launch_tc_g(const float *X, int64_t M, int L, const __nv_bfloat16 *B
     const int keymask = ~((1 << GrpCfg<GRP>::JBITS) - 1);
     if ((L & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) {
         // persistent: 2 codebook stages + staged BF16 rows + the FP32 x tile
-        const size_t need = (size_t)TC_PSTAGES * TC_NT * tc_kb(LK) * 2 + (size_t)TC_ROWS * XsRow<LK>::STR * 2 +
-                            (size_t)TC_ROWS * LK * 4;
+        const size_t need = (size_t)TC_PSTAGES * TC_NT * tc_kb(LK) * 2 +
+                            (size_t)(TcA<LK>::SPLIT ? 2 : 1) * TC_ROWS * XsRow<LK>::STR * 2 + (size_t)TC_ROWS * LK * 4;
         // at least 120 KB so that a single CTA (and its 512 TMEM columns) owns the SM
         const size_t smem = need > 120 * 1024 ? need : 120 * 1024;
         cudaFuncSetAttribute(k_assign_tc_p<LK, GRP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1523,7 +1554,8 @@ static void launch_tc_g(const float *X, int64_t M, int L, const __nv_bfloat16 *B
             X, M, L, B, kn, n_dev, n_host, mu, C, st, assign, e, flags, keymask, m_lo, n_lo, n_hi);
         return;
     }
-    const size_t need = (size_t)TC_ROWS * XsRow<LK>::STR * 2 + (size_t)TC_STAGES * TC_NT * tc_kb(LK) * 2;
+    const size_t need = (size_t)(TcA<LK>::SPLIT ? 2 : 1) * TC_ROWS * XsRow<LK>::STR * 2 +
+                        (size_t)TC_STAGES * TC_NT * tc_kb(LK) * 2;
     // at least 120 KB so that a single CTA (and its 512 TMEM columns) owns the SM
     const size_t smem = need > 120 * 1024 ? need : 120 * 1024;
     cudaFuncSetAttribute(k_assign_tc<LK, GRP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -177,27 +177,45 @@ def _epilogue_worst(v, best, GRP):
     return c1, c2, i1
 
 
+def tau_model(Lk):
+    """The accumulation-error coefficient the library assumes, (K/16 + 2) 2^-22
+    (1 + 2^-7) of (sum |products| + |s0| + X2), with K = 3 Lk + 16 accumulated
+    elements for Lk <= 32 (the split form's x_lo . p_hi included), 2 Lk + 16
+    otherwise."""
+    K = 3 * Lk + 16 if Lk <= 32 else 2 * Lk + 16
+    return Fraction(K // 16 + 2, 2 ** 22) * Fraction(129, 128)
+
+
+def tau_of(Lk):
+    """The coefficient of the kernel's margins (k', R'): the model's, times
+    1 + 2^-6 for Lk <= 32, where the split form's products may exceed
+    ||x~||^2 + ||c~||^2 by 2^-7 of it."""
+    return tau_model(Lk) * (Fraction(65, 64) if Lk <= 32 else 1)
+
+
 def certify(x, C, mu, N, adversarial=True, worst=False, weights=None, GRP=2):
     """Run one row through the model and the two certificates.  With
     worst=True every bounded quantity is at the end of its bound that favours
     a wrong answer (see test_bf16_certificates_sound_at_every_bound).
     `weights` (keys m_R, m_k, m_pack, m_E, lb_R, lb_E, lb_pack) scale terms of
     the first certificate's margin and of the second one's lower bound, to show
-    that each is needed.  Returns (accepted, chosen index, exact argmin)."""
+    that each is needed.  Rows whose centred values are not integers take the
+    split form (x~ = x_hi + x_lo + rem in BF16 pieces; only Lk <= 32).
+    Returns (accepted, chosen index, exact argmin)."""
     wt = {k: Fraction(1) for k in ("m_R", "m_k", "m_pack", "m_E", "lb_R", "lb_E", "lb_pack")}
     wt.update({k: Fraction(v) for k, v in (weights or {}).items()})
     L = len(x)
     Lk = -(-L // 16) * 16
-    K = 2 * Lk + 16
-    tau = Fraction(K // 16 + 2, 2 ** 22) * Fraction(129, 128)
+    tau = tau_of(Lk)
+    taum = tau_model(Lk)
     x = np.asarray(x, np.float32)
     C = np.asarray(C, np.float32)
     mu = np.asarray(mu, np.float32)
-    xt = (x - mu).astype(np.float64)
-    assert np.all(xt == np.rint(xt))
-    xt = np.array([int(v) for v in xt], dtype=object)
-    X2 = int((xt * xt).sum())
-    assert X2 < 2 ** 24          # exact in FP32 for these data
+    xt32 = (x - mu).astype(np.float32)             # x~ = fl32(x - mu), as the kernel forms it
+    split = not np.all(xt32 == np.rint(xt32))
+    assert not split or Lk <= 32
+    xh = bf16_rne(xt32)
+    xl = bf16_rne((xt32 - xh).astype(np.float32))   # x~ - x_hi is exact in FP32
     # exact squared distances of the original FP32 values
     (xi, ci), Sd = _ints([x, C])
     diff = ci - xi[None, :]
@@ -210,9 +228,21 @@ def certify(x, C, mu, N, adversarial=True, worst=False, weights=None, GRP=2):
     r1 = (cp - ph).astype(np.float32)
     pm = bf16_rne(r1)
     r = (r1 - pm).astype(np.float32)
-    (cti, cpi, phi, pmi, ri, r1i), S = _ints([ct, cp, ph, pm, r, r1])
+    (cti, cpi, phi, pmi, ri, r1i, xti, xhi, xli), S = _ints([ct, cp, ph, pm, r, r1, xt32, xh, xl])
     assert np.all(cpi == phi + r1i) and np.all(r1i == pmi + ri)
     sq_exact = [Fraction(int(v), 1 << (2 * S)) for v in (cti * cti).sum(1)]
+    scale = 1 << S
+    xn2 = Fraction(int((xti * xti).sum()), scale * scale)        # ||x~||^2
+    if split:
+        # X2 as the kernel forms it: sum (x_hi + x_lo)^2 in FP32, at the top of its bound in
+        # the worst case
+        # (|fl(sum (x_hi + x_lo)^2) - ||x~||^2| <= ((L + 2) u + 2^-14) ||x~||^2)
+        hl = xhi + xli
+        X2 = Fraction(int((hl * hl).sum()), scale * scale)
+        X2 = xn2 * (1 + (L + 2) * U + Fraction(1, 2 ** 14)) if worst else Fraction(f32(X2))
+    else:
+        X2 = xn2
+        assert X2 < 2 ** 24          # exact in FP32 for these data
     # k'_n rounded up and s0_n rounded to nearest from the FP64 norm, as the preparation does
     s0 = np.empty(N, np.float32)
     kp = []
@@ -225,24 +255,28 @@ def certify(x, C, mu, N, adversarial=True, worst=False, weights=None, GRP=2):
         kp.append(Fraction(float(kf)))
         s0[n] = np.float32(sq - float(kf))
     (s0i,), S0 = _ints([s0])
-    scale = 1 << S
-    dot = (phi + pmi) @ xt                         # x~ . (p_hi + p_mid), scaled by 2**S
-    adot = np.abs(cpi) @ np.abs(xt)                # sum_l |x~_l c'_l|, scaled by 2**S
-    rnorm = [sqrt_up(Fraction(int(v), scale * scale)) for v in (ri * ri).sum(1)]
+    sc2 = scale * scale
+    # what the MMAs sum: x_hi . (p_hi + p_mid) (+ x_lo . p_hi on a split row)
+    dot = (phi + pmi) @ xhi + (phi @ xli if split else 0)
+    adot = (np.abs(phi) + np.abs(pmi)) @ np.abs(xhi) + (np.abs(phi) @ np.abs(xli) if split else 0)
+    rnorm = [sqrt_up(Fraction(int(v), sc2)) for v in (ri * ri).sum(1)]
     rho = max(rnorm)
     cmax = max(sqrt_up(q) for q in sq_exact)
-    E = sqrt_up(Fraction(X2)) * rho
-    dotc = cpi @ xt                                # x~ . c', scaled by 2**S
+    if split:   # the terms the pieces miss, as the kernel bounds them
+        E = sqrt_up(xn2) * (rho + Fraction(1, 2 ** 14) * cmax) * Fraction(129, 128)
+    else:
+        E = sqrt_up(xn2) * rho
+    dotc = cpi @ xti                               # x~ . c'
     v = []
     for n in range(N):
         s0n = Fraction(int(s0i[n]), 1 << S0)
         up = (n == best) == adversarial
-        if worst:   # the missed term -x~.r_n anywhere in [-E, E]
-            G = X2 + s0n + Fraction(int(dotc[n]), scale) + (E if up else -E)
+        if worst:   # the missed terms anywhere in [-E, E]
+            G = X2 + s0n + Fraction(int(dotc[n]), sc2) + (E if up else -E)
         else:
-            G = X2 + s0n + Fraction(int(dot[n]), scale)
-        Sn = Fraction(int(adot[n]), scale) + abs(s0n) + X2
-        e = tau * Sn if up else -tau * Sn
+            G = X2 + s0n + Fraction(int(dot[n]), sc2)
+        Sn = Fraction(int(adot[n]), sc2) + abs(s0n) + X2
+        e = taum * Sn if up else -taum * Sn
         if worst:
             v.append(G + e)
             continue
@@ -275,7 +309,7 @@ def certify(x, C, mu, N, adversarial=True, worst=False, weights=None, GRP=2):
     R = 2 * tau * X2
     eta = U * (sqrt_up(Fraction(X2)) + cmax)
     pack = Fraction(1, 2 ** (23 - JBITS[GRP])) * (abs(V1) + abs(V2))
-    xerr = (L + 2) * U * X2
+    xerr = (L + 2) * U * X2 + (Fraction(1, 2 ** 14) * X2 if split else 0)
     g1 = sqrt_up(V1 + 2 * ka + R + pack + E + xerr)
     margin = (wt["m_R"] * 2 * R + wt["m_k"] * 2 * ka + wt["m_pack"] * pack + wt["m_E"] * 2 * E
               + 4 * eta * (g1 + eta))
@@ -430,3 +464,58 @@ def test_bf16_certificates_resolve_split_twins(GRP):
             accepted += 1
             assert ii == best and best // 2 == n
     assert accepted >= 20
+
+
+def _rows_real(rng, L, N, spread, trials):
+    """Real-valued rows (not exact in BF16 after centring: the split form) with a
+    near-tie pair as in _rows, codevectors around the row, an integer mu (the
+    kernel rounds the centring vector)."""
+    for trial in range(trials):
+        x = (rng.random(L) + 0.3 * rng.standard_normal(L)).astype(np.float32)
+        c0 = (x + spread * rng.standard_normal(L)).astype(np.float32)
+        w = rng.standard_normal(L)
+        w /= np.linalg.norm(w)
+        d = c0.astype(np.float64) - x
+        c1 = x + d - 2 * np.dot(d, w) * w
+        eps = 0.0 if trial % 4 == 0 else spread * 10 ** rng.uniform(-7, 0)
+        dv = rng.standard_normal(L)
+        c1 = (c1 + eps * dv / np.linalg.norm(dv)).astype(np.float32)
+        C = (x + spread * (2.5 + rng.standard_normal((N, L)))).astype(np.float32)
+        p0 = 2 * int(rng.integers(0, N // 2))
+        p1 = {0: p0 + 1, 1: (p0 + 6) % N, 2: (p0 + HALF + 3) % N}[trial % 3]
+        C[p0], C[p1] = (c0, c1) if trial % 2 else (c1, c0)
+        mu = np.rint(C.mean(0)).astype(np.float32)
+        yield x, C, mu
+
+
+@pytest.mark.parametrize("GRP", [2, 8])
+@pytest.mark.parametrize("L,spread", [(16, 0.2), (16, 0.02), (32, 0.2), (32, 0.02)])
+def test_bf16_split_form_sound(L, spread, GRP):
+    """Real-valued rows take the split form (x~ in two BF16 pieces, the remainder
+    and the pieces' missed products bounded in E, X2 from the pieces): at the
+    model's bound and with every bounded quantity at its worst, every accepted
+    row has the exact argmin, and rows are accepted."""
+    for worst in (False, True):
+        rng = np.random.default_rng(300 + L + int(100 * spread) + (7 if worst else 0))
+        accepted = 0
+        for x, C, mu in _rows_real(rng, L, NT, spread, 60):
+            assert not np.all((x - mu) == np.rint(x - mu))
+            ok, ii, best = certify(x, C, mu, NT, worst=worst, GRP=GRP)
+            if ok:
+                accepted += 1
+                assert ii == best, (ii, best)
+        assert accepted > 0
+
+
+def test_bf16_split_form_accepts_clear_winners():
+    """Gaussian-mixture-like real data: a row near one codevector of a spread
+    codebook is accepted in the split form."""
+    rng = np.random.default_rng(21)
+    L, N = 32, NT
+    C = rng.random((N, L)).astype(np.float32)
+    mu = np.rint(C.mean(0)).astype(np.float32)
+    for n in rng.choice(N, 12, replace=False):
+        x = (C[n] + 0.1 * rng.standard_normal(L)).astype(np.float32)
+        for GRP in (2, 8):
+            ok, ii, best = certify(x, C, mu, N, GRP=GRP)
+            assert ok and ii == best == n

@@ -3,8 +3,9 @@ FP64 oracle and vs the FP32 path, through the C ABI (precision = LBG_PREC_BF16).
 
 Same parity rules as tests/test_gpu_parity.py.  On integer image data the
 BF16 path must give the oracle's assignments outside near-ties (it certifies
-every row or re-scores it exactly); on data that is not BF16-exact it must
-stay correct by sending every row to the exact fallback.
+every row or re-scores it exactly).  On real-valued data with L <= 32 the x
+rows go in two BF16 pieces and most rows are still certified; with L > 32 a
+tile that is not BF16-exact sends every row to the exact fallback.
 """
 import numpy as np
 import pytest
@@ -69,8 +70,10 @@ def test_encode_bf16_equals_fp32(lbg):
 
 
 def test_bf16_non_integer_data_falls_back_exactly(lbg):
+    """L = 64 has no second x piece: x~ not exact in BF16 sends every row to the
+    exact fallback."""
     rng = np.random.default_rng(9)
-    X = (rng.standard_normal((3000, 32)) * 3.3).astype(np.float32)
+    X = (rng.standard_normal((3000, 64)) * 3.3).astype(np.float32)
     C = codebook_from(X, 100, 3)
     r = lbg.vq_encode(dev(X), dev(C), precision="bf16")
     a_ref, e_ref, gap = oracle.assign(X, C.astype(np.float64))
@@ -78,12 +81,58 @@ def test_bf16_non_integer_data_falls_back_exactly(lbg):
     assert r.n_exact == X.shape[0]
 
 
-@pytest.mark.parametrize("M,N,L", [(64, 4096, 16), (20000, 1024, 16), (3001, 512, 64), (33, 129, 5)])
+@pytest.mark.parametrize("M,N,L", [(20000, 1024, 32), (30001, 512, 16), (4099, 129, 5), (5000, 4096, 24)])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_split_form_certifies_non_integer_data(lbg, M, N, L, offset):
+    """L <= 32: x~ = x_hi + x_lo + rem in two BF16 pieces; rows of real-valued data are
+    certified by the tensor-core pass (the split terms in the certificate) instead of all
+    falling back.  offset = 1 starts X 4 bytes past a 16-byte boundary (the per-tile
+    kernel); both kernels give the same cells."""
+    rng = np.random.default_rng(M + N + L)
+    X = (rng.standard_normal((M, L)) * 3.3 + 0.7).astype(np.float32)
+    C = (X[rng.choice(M, N, replace=False)] + rng.normal(0, 0.05, (N, L))).astype(np.float32)
+    if offset:
+        buf = torch.empty(M * L + 1, dtype=torch.float32, device="cuda")
+        Xd = buf[1:].view(M, L)
+        Xd.copy_(torch.from_numpy(X))
+        assert Xd.data_ptr() % 16 == 4
+    else:
+        Xd = dev(X)
+    r = lbg.vq_encode(Xd, dev(C), precision="bf16")
+    a_ref, e_ref, gap = oracle.assign(X, C.astype(np.float64))
+    check_assign(X, C, host(r.idx), a_ref, e_ref, gap)
+    check_D(r.D, float(e_ref.sum()))
+    assert r.n_exact < 0.05 * M, r.n_exact
+    if offset:
+        # same cells; e(m) is the FP32 direct form summed in another order (scalar
+        # loads instead of the aligned path's float4 butterfly)
+        al = lbg.vq_encode(dev(X), dev(C), precision="bf16")
+        assert torch.equal(al.idx, r.idx)
+        check_D(al.D, r.D)
+
+
+def test_split_form_gmm_train_every_pass(lbg):
+    """LBG in BF16 on mixture data (L = 32, not integer), checked pass by pass."""
+    from paper_0910_4711_gb300 import synth
+    from oracle import trajectory as tj
+    X, _, _ = synth.gmm(6, 20000, 32, 64, 0.1)
+    r = lbg.lbg_train(dev(X), 64, 0.01, 1e-3, precision="bf16", trace=512, trace_passes=512)
+    rep = tj.compare(X, 64, 0.01, 1e-3, r.records, host(r.pass_C), host(r.pass_assign),
+                     host(r.C), host(r.assign), r.D)
+    s = rep.summary()
+    assert s["assign_rows_outside_tolerance"] == 0 and s["worst_D_rel"] <= 1e-5, s
+    assert s["worst_codebook_rel"] <= 1e-4 and s["stop_decisions_wrong"] == 0, s
+    assert s["final_state_is_last_pass"], s
+    assert sum(rec["n_exact"] for rec in r.records) < 0.05 * X.shape[0] * len(r.records)
+
+
+@pytest.mark.parametrize("M,N,L", [(64, 4096, 48), (20000, 1024, 64), (3001, 512, 64), (33, 129, 37)])
 def test_exact_fallback_spread_over_ctas(lbg, M, N, L):
-    """Every row re-scored exactly, at sizes where a group of 32 flagged rows is cut across
-    many CTAs (its per-CTA minima merged), across two, or held whole by one, with a ragged
-    last group and chunk.  A codebook that repeats its first half must give the first half's
-    result bit for bit: equal FP32 distances in different CTAs keep the lowest index."""
+    """Every row re-scored exactly (L > 32 and data not exact in BF16), at sizes where a
+    group of 32 flagged rows is cut across many CTAs (its per-CTA minima merged), across
+    two, or held whole by one, with a ragged last group and chunk.  A codebook that
+    repeats its first half must give the first half's result bit for bit: equal FP32
+    distances in different CTAs keep the lowest index."""
     rng = np.random.default_rng(M + N + L)
     X = (rng.standard_normal((M, L)) * 3.3).astype(np.float32)
     C = (rng.standard_normal((N, L)) * 3.3).astype(np.float32)
