@@ -183,6 +183,12 @@ typedef struct lbg_opts {
                                     upstream gradient is read from it on the device and the gD
                                     argument is ignored (an autograd caller then needs no host
                                     read of it); every array must be device memory. */
+    int32_t tc_group;           /* LBG_PREC_BF16: codevectors per group of the tensor-core
+                                   search's running top-2 (the best group is re-scored exactly
+                                   per row): 0 (default) chooses by L and N; 2, 4 or 8 forces
+                                   it (other values: LBG_ERR_ARG).  Assignments do not depend on
+                                   it; e(m) of a row may differ in its last bits (the exact
+                                   fallback sums in another order). */
 } lbg_opts;
 
 /* Fill *opts with the defaults (FP32, 1000 passes, default stream, no trace,

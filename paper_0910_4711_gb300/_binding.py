@@ -71,7 +71,8 @@ class Opts(ctypes.Structure):
                 ("result_dev", ctypes.c_void_p),
                 ("trace_C", ctypes.c_void_p), ("trace_assign", ctypes.c_void_p),
                 ("trace_cap", ctypes.c_int32), ("test_expire_wait", ctypes.c_int32),
-                ("batched_per_phase", ctypes.c_int32), ("grad_scale_dev", ctypes.c_void_p)]
+                ("batched_per_phase", ctypes.c_int32), ("grad_scale_dev", ctypes.c_void_p),
+                ("tc_group", ctypes.c_int32)]
 
 
 STEP_RESULT_BYTES = 16   # lbg_step_result: double D, int32 n_exact, int32 status
@@ -183,11 +184,12 @@ PRECISION = {"fp32": 0, "bf16": 1}
 
 def _opts(cuda_ref, max_passes=1000, records=0, phase=False, stream=None, precision="fp32",
           split_multiplicative=False, reseed_empty=False, delta_reseed=0.0, result=None,
-          test_expire_wait=False):
+          test_expire_wait=False, tc_group=0):
     o = Opts()
     lib().lbg_opts_init(ctypes.byref(o))
     o.max_passes = int(max_passes)
     o.test_expire_wait = int(bool(test_expire_wait))
+    o.tc_group = int(tc_group)
     o.split_multiplicative = int(bool(split_multiplicative))
     o.reseed_empty = int(bool(reseed_empty))
     o.delta_reseed = float(delta_reseed)
@@ -282,7 +284,7 @@ def lbg_train(X, N: int, delta: float = 0.01, theta: float = 1e-3, C_init=None,
               max_passes: int = 1000, trace: int = 4096, phase_ms: bool = False, C_out=None,
               assign_out=None, stream=None, precision: str = "fp32",
               split_multiplicative: bool = False, reseed_empty: bool = False,
-              trace_passes: int = 0) -> TrainResult:
+              trace_passes: int = 0, tc_group: int = 0) -> TrainResult:
     """Design an N-entry codebook from X [M, L] (see lbg_train in lbgvq.h).  With
     trace_passes > 0 (X on a CUDA device) the codebook and the cell table of each of the first
     trace_passes passes are kept on the device (result.pass_C, result.pass_assign, one entry
@@ -298,7 +300,7 @@ def lbg_train(X, N: int, delta: float = 0.01, theta: float = 1e-3, C_init=None,
     Co, cp, _ = _prep(C, "f32", "C")
     Ao, ap, _ = _prep(A, "i32", "assign")
     o, keep = _opts(_cuda_ref(X, C, A), max_passes, trace, phase_ms, stream, precision,
-                    split_multiplicative, reseed_empty)
+                    split_multiplicative, reseed_empty, tc_group=tc_group)
     pC = pA = None
     if trace_passes > 0:
         ref = _cuda_ref(X)
@@ -326,7 +328,7 @@ def lbg_train(X, N: int, delta: float = 0.01, theta: float = 1e-3, C_init=None,
 def lbg_lloyd_step(X, C_in, C_out=None, assign_out=None, phase_ms: bool = False,
                    stream=None, precision: str = "fp32", reseed_empty: bool = False,
                    delta_reseed: float = 0.01, result_out=None,
-                   test_expire_wait: bool = False) -> StepResult:
+                   test_expire_wait: bool = False, tc_group: int = 0) -> StepResult:
     """One Lloyd pass from C_in (see lbg_lloyd_step in lbgvq.h).  With result_out (a
     step_result_buffer) the pass is only enqueued on the stream: D, n_exact and the
     device status land in result_out (read_step_result)."""
@@ -340,7 +342,7 @@ def lbg_lloyd_step(X, C_in, C_out=None, assign_out=None, phase_ms: bool = False,
     A, ap, _ = _prep(A, "i32", "assign")
     o, keep = _opts(_cuda_ref(X, C_in, Co, A), stream=stream, phase=phase_ms, precision=precision,
                     reseed_empty=reseed_empty, delta_reseed=delta_reseed, result=result_out,
-                    test_expire_wait=test_expire_wait)
+                    test_expire_wait=test_expire_wait, tc_group=tc_group)
     if result_out is not None:
         rc = _check(lib().lbg_lloyd_step(xp, M, L, N, cip, cop, ap, None, ctypes.byref(o)))
         return StepResult(rc, Co, A, float("nan"), -1, None, result_out)
@@ -351,7 +353,7 @@ def lbg_lloyd_step(X, C_in, C_out=None, assign_out=None, phase_ms: bool = False,
 
 def vq_encode(X, C, decode: bool = False, with_distortion: bool = True, phase_ms: bool = False,
               idx_out=None, stream=None, precision: str = "fp32", result_out=None,
-              test_expire_wait: bool = False) -> EncodeResult:
+              test_expire_wait: bool = False, tc_group: int = 0) -> EncodeResult:
     """Nearest codevector of every row of X (see vq_encode in lbgvq.h).  With result_out
     (a step_result_buffer) the call is only enqueued, as for lbg_lloyd_step."""
     Xo, xp, _ = _prep(X, "f32", "X")
@@ -363,7 +365,7 @@ def vq_encode(X, C, decode: bool = False, with_distortion: bool = True, phase_ms
     H = _empty_like_src(X, (M, L), "f32") if decode else None
     H, hp, _ = _prep(H, "f32", "Xhat")
     o, keep = _opts(_cuda_ref(X, C, I), stream=stream, phase=phase_ms, precision=precision,
-                    result=result_out, test_expire_wait=test_expire_wait)
+                    result=result_out, test_expire_wait=test_expire_wait, tc_group=tc_group)
     if result_out is not None:
         rc = _check(lib().vq_encode(xp, M, L, cp, N, ip, hp, None, ctypes.byref(o)))
         return EncodeResult(rc, I, H, float("nan"), -1, None, result_out)

@@ -19,7 +19,16 @@
 // in V2 - V1.  (A third piece would make x~.c' exact at 3/2 the MMAs and
 // codebook bytes; on the image workloads the remainder term certifies all
 // but a few tenths of a percent of the rows.)
-//
+// Real-valued data (Lk <= 32, the split form): x~ = fl(x - mu) is cut into
+// x_hi = bf16(x~) and x_lo = bf16(x~ - x_hi) with an FP32 remainder rem
+// (|rem| <= 2^-16 |x~|); A = [ x_hi | x_lo | norm block ], and a row tile with
+// any x_lo != 0 adds the Lk/16 MMAs x_lo . p_hi per job.  The pieces miss
+// x_hi . r_n, x_lo . (p_mid + r_n) and rem . c'_n, all within
+// ||x~|| (rho + 2^-14 cmax)(1 + 2^-7); X2 of such a tile is sum (x_hi + x_lo)^2,
+// within 2^-14 ||x~||^2 of ||x~||^2.  Both go into E and the X2 term of the
+// certificates below; the centring error of fl(x - mu) is the eta term.  With
+// Lk = 48 or 64 a tile whose x~ is not exact in BF16 sends its rows to the
+// exact fallback.
 // Accumulation model.  Measured on GB300 (BF16 products, K up to 256, mixed
 // exponents) the error stayed below (K/16) * 2^-24 * (sum of |products|); the
 // library assumes tau = (K/16 + 2) * 2^-22 * (1 + 2^-7) of (sum of |products| +
@@ -28,15 +37,15 @@
 //     |v_n - (X2 + f_n - k'_n)| <= tau (2 ||x~||^2 + 2 ||c~_n||^2) + u ||c~_n||^2 + E,
 // E = ||x~|| rho, and with k'_n = (2 tau + 2^-23) ||c~_n||^2, R' = 2 tau ||x~||^2
 // the certificate of k_assign.cu applies, over groups: the columns are taken
-// in groups of eight consecutive codevectors, V1 is the smallest value and V2
-// the smallest value outside V1's group.  The group's member with the
+// in groups of G = 2, 4 or 8 consecutive codevectors, V1 is the smallest value
+// and V2 the smallest value outside V1's group.  The group's member with the
 // smallest FP32 direct-form distance is the candidate ii (it must beat every
 // other member by more than the direct form's rounding bound, else the row is
 // not certified).  The member j that produced V1 has ||x~ - c~_j||^2 <= V1 +
 // 2k'_j + R' + E (+ epilogue and X2 terms) and ii is not farther than j, while
 // every codevector outside the group has ||x~ - c~_n||^2 >= V2 - R' - E, so
-// V2 - V1 > 2R' + 2k'_grp + 2E + 4 eta (g1 + eta) + 2^-19 (|V1| + |V2|), with
-// k'_grp the group's largest k' and the last term for the epilogue's index
+// V2 - V1 > 2R' + 2k'_grp + 2E + 4 eta (g1 + eta) + 2^(JBITS-23) (|V1| + |V2|),
+// with k'_grp the group's largest k' and the last term for the epilogue's index
 // packing, proves ii the exact argmin.  A second certificate needs no bound
 // on V1's member.  With X2 + f_n = ||x~ - c~_n||^2 + (X2 - ||x~||^2) and
 // k'_n >= 2 tau ||c~_n||^2 + u ||c~_n||^2, the bound gives
@@ -51,18 +60,18 @@
 // comes from the next parent, not from the twin.
 //
 // Epilogue.  Each thread owns one row and one half (72 columns) of every
-// tile, taken as 9 groups of 8 columns.  The group minimum (three-input
-// mins) gets the group index (4 bits) in its low mantissa bits (one LOP3; the
-// value moves by less than 2^-19 of it); then c2 = min(c2, max(c1, k)) and
-// c1 = min(c1, k): eight ALU operations per group, one per value, for the
-// running top-2 of group minima with the index of the best group; a per-tile
-// compare records the tile, and the two halves of a row are merged through
-// shared memory at the end.  The tail scores the best group's eight members
-// exactly (four per half) and a certified row keeps the winner's FP32
-// direct-form distance as e(m).
-// Tiles whose x~ are not BF16-exact, or codebooks whose pieces do not add up
-// exactly, send their rows to the exact FP32 fallback.
-//
+// tile, taken as 72/G groups of G columns.  The group minimum (three-input
+// mins) gets the in-half group index (JBITS = 6, 5, 4 bits for G = 2, 4, 8)
+// in its low mantissa bits (one LOP3; the value moves by less than
+// 2^(JBITS-23) of it); two groups at a time then enter the running top-2 of
+// group minima (five ALU operations for the two): 2.25, 1.375 and 0.94 ALU
+// operations per value; a per-tile compare records the tile, and the two
+// halves of a row are merged through shared memory at the end.  The tail
+// scores the best group's G members exactly (G/2 per half) and a certified
+// row keeps the winner's FP32 direct-form distance as e(m).  G is chosen per
+// launch by Lk and N (lbg_opts.tc_group forces it).
+// Codebooks whose pieces do not add up exactly send their rows to the exact
+// FP32 fallback.
 // Kernel layout (256 rows per CTA; k_assign_tc takes one row tile per CTA,
 // k_assign_tc_p walks the row tiles with one CTA per SM):
 //   prologue      the epilogue warps stage the x tile (coalesced) as centred
@@ -81,7 +90,7 @@
 //                 its 72 values per job, running top-2 of group minima with the
 //                 group index (two interleaved chains); after the last tile the
 //                 two halves of each row merge, compute the exact distances of
-//                 the best group's eight codevectors, and the half-0 thread
+//                 the best group's G codevectors, and the half-0 thread
 //                 runs the certificate, writes the index and e(m) or flags the
 //                 row.
 // Every mbarrier wait is bounded (2 s); on a time-out the CTA stops issuing,
@@ -104,10 +113,10 @@ constexpr int TC_NT = 144;                     // codevectors per tile (MMA N): 
                                                // runs epilogue warps (N = 128 issued about one
                                                // MMA per 86 cycles for 64 cycles of work)
 constexpr int TC_HALF = TC_NT / 2;             // columns per epilogue thread per tile
-// Columns per group (GRP = 2 or 8): the running top-2 is over group minima, and
-// a group holds whole split pairs (children 2i, 2i + 1).  Eight columns take one
-// ALU operation per value in the epilogue but eight exact distances per row in
-// the tail; two columns take 2.5 and two.  GrpCfg<GRP>: groups per epilogue
+// Columns per group (GRP = 2, 4 or 8): the running top-2 is over group minima,
+// and a group holds whole split pairs (children 2i, 2i + 1).  Eight columns take
+// 0.94 ALU operations per value in the epilogue but eight exact distances per
+// row in the tail; four take 1.375 and four, two 2.25 and two.  GrpCfg<GRP>: groups per epilogue
 // thread per tile, bits of the in-half group index, and the packing bound
 // 2^(JBITS - 23) (packing changes a value by less than this fraction of it).
 template <int GRP>
@@ -116,6 +125,11 @@ template <>
 struct GrpCfg<2> {
     static constexpr int GROUPS = 36, JBITS = 6;
     static constexpr float PACK = 7.62939453125e-6f;
+};
+template <>
+struct GrpCfg<4> {
+    static constexpr int GROUPS = 18, JBITS = 5;
+    static constexpr float PACK = 3.814697265625e-6f;
 };
 template <>
 struct GrpCfg<8> {
@@ -227,34 +241,50 @@ __device__ __forceinline__ float fmin3(float a, float b, float c)
     return d;
 }
 
-// One epilogue step for group j (columns GRP j .. GRP j + GRP - 1 of the
-// thread's half): its minimum (three-input mins) carries the group index in its
-// JBITS low mantissa bits (one LOP3; `keymask` = ~(2^JBITS - 1) comes in as a
-// kernel argument so that the mask stays in a register and the immediate is the
-// index); then the running top-2 of group minima of chain j % NCH:
-// c2 = min(c2, max(c1, k)), c1 = min(c1, k).
+// The epilogue steps of one job: group j holds columns GRP j .. GRP j + GRP - 1
+// of the thread's half; its minimum (three-input mins) carries the group index
+// in its JBITS low mantissa bits (one LOP3; `keymask` = ~(2^JBITS - 1) comes in
+// as a kernel argument so that the mask stays in a register and the immediate
+// is the index).  Groups enter the running top-2 of their chain two at a time:
+// with m = min(k1, k2), h = max(k1, k2), the top-2 of {c1, c2, k1, k2} is
+// c1' = min(c1, m), c2' = min(c2, max(c1, m), h) (five operations for two
+// groups instead of six; the same values as one group at a time).  Pair p of
+// groups goes to chain p % NCH; an odd last group enters chain (GROUPS / 2) % NCH
+// alone.
+template <int GRP, int J>
+__device__ __forceinline__ float group_key(const float *v, int keymask)
+{
+    const float *g = v + GRP * J;
+    float lo;
+    if constexpr (GRP == 8)
+        lo = fmin3(fmin3(g[0], g[1], g[2]), fmin3(g[3], g[4], g[5]), fminf(g[6], g[7]));
+    else if constexpr (GRP == 4)
+        lo = fminf(fmin3(g[0], g[1], g[2]), g[3]);
+    else
+        lo = fminf(g[0], g[1]);
+    int kb;
+    asm("lop3.b32 %0, %1, %2, %3, 0xEA;" : "=r"(kb) : "r"(__float_as_int(lo)), "r"(keymask), "n"(J));
+    return __int_as_float(kb);
+}
 template <int GRP, int P>
 struct GroupSteps {
     __device__ __forceinline__ static void run(const float *v, float *c1, float *c2, int keymask)
     {
-        GroupSteps<GRP, P - 1>::run(v, c1, c2, keymask);
-        constexpr int j = P - 1, q = j % TC_NCH;
-        const float *g = v + GRP * j;
-        float lo;
-        if constexpr (GRP == 8)
-            lo = fmin3(fmin3(g[0], g[1], g[2]), fmin3(g[3], g[4], g[5]), fminf(g[6], g[7]));
-        else
-            lo = fminf(g[0], g[1]);
-        int kb;
-        asm("lop3.b32 %0, %1, %2, %3, 0xEA;" : "=r"(kb) : "r"(__float_as_int(lo)), "r"(keymask), "n"(j));
-        const float k = __int_as_float(kb);
-        c2[q] = fminf(c2[q], fmaxf(c1[q], k));
-        c1[q] = fminf(c1[q], k);
+        if constexpr (P % 2 == 1) {   // an odd last group enters alone
+            GroupSteps<GRP, P - 1>::run(v, c1, c2, keymask);
+            constexpr int q = ((P - 1) / 2) % TC_NCH;
+            const float k = group_key<GRP, P - 1>(v, keymask);
+            c2[q] = fminf(c2[q], fmaxf(c1[q], k));
+            c1[q] = fminf(c1[q], k);
+        } else if constexpr (P >= 2) {
+            GroupSteps<GRP, P - 2>::run(v, c1, c2, keymask);
+            constexpr int q = ((P - 2) / 2) % TC_NCH;
+            const float k1 = group_key<GRP, P - 2>(v, keymask), k2 = group_key<GRP, P - 1>(v, keymask);
+            const float m = fminf(k1, k2), h = fmaxf(k1, k2);
+            c2[q] = fmin3(c2[q], fmaxf(c1[q], m), h);
+            c1[q] = fminf(c1[q], m);
+        }
     }
-};
-template <int GRP>
-struct GroupSteps<GRP, 0> {
-    __device__ __forceinline__ static void run(const float *, float *, float *, int) {}
 };
 
 __device__ __forceinline__ void named_sync(int id, int threads)
@@ -1533,7 +1563,16 @@ void launch_prep_tc(const float *C, int N_alloc, const int32_t *n_dev, int n_hos
 // Group size by codebook size: eight columns where the epilogue's ALU work is
 // what bounds the launch (short rows, LK <= 32, and many codevectors), two
 // elsewhere (the tail then scores two members instead of eight).
-constexpr int TC_G8_MIN_N = 1024;
+// Group size of the epilogue by codebook size: larger groups cut the per-value
+// epilogue work and the flagged rows, smaller ones the tail's exact distances
+// per row.  Measured on GB300 (search + exact re-scoring, ms): image blocks
+// L = 64, N = 4096: G = 2 0.509, 4 0.497, 8 0.556; N = 2048: 0.325, 0.336,
+// 0.400; L = 16, N = 4096: 3.54, 3.04, 3.19; N = 1024: 1.339, 1.355, 1.701;
+// mixture L = 32, N = 4096: 0.339, 0.272, 0.265; N = 512: 0.088, 0.089, 0.113.
+template <int LK>
+struct TcGroups {
+    static constexpr int SMALL = 2, LARGE = 4, AT = LK <= 32 ? 2048 : 4096;
+};
 
 template <int LK, int GRP>
 static void launch_tc_g(const float *X, int64_t M, int L, const __nv_bfloat16 *B, const float *kn,
@@ -1566,7 +1605,7 @@ static void launch_tc_g(const float *X, int64_t M, int L, const __nv_bfloat16 *B
 template <int LK>
 static void launch_tc(const float *X, int64_t M, int L, const void *Bp, const float *kn,
                       const int32_t *n_dev, int n_host, const float *mu, const float *C, DevState *st,
-                      int32_t *assign, float *e, int32_t *flags, cudaStream_t s, int64_t m_lo)
+                      int32_t *assign, float *e, int32_t *flags, cudaStream_t s, int64_t m_lo, int grp)
 {
     // rows [m_lo, M): the kernels see them as rows [0, M - m_lo) of offset arrays and add
     // m_lo back only to the flag list entries (global row numbers)
@@ -1577,34 +1616,38 @@ static void launch_tc(const float *X, int64_t M, int L, const void *Bp, const fl
     const int64_t grid = (M + TC_ROWS - 1) / TC_ROWS;
     if (grid <= 0) return;
     const __nv_bfloat16 *B = static_cast<const __nv_bfloat16 *>(Bp);
-    if constexpr (LK <= 32) {
-        if (!n_dev) {   // the size is known here: one launch
-            if (n_host >= TC_G8_MIN_N)
-                launch_tc_g<LK, 8>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo, grid, 0, 1 << 30);
-            else
-                launch_tc_g<LK, 2>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo, grid, 0, 1 << 30);
-        } else {        // training: the stage size is on the device, each kernel takes its range
-            launch_tc_g<LK, 2>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo, grid, 0,
-                               TC_G8_MIN_N);
-            if (n_host >= TC_G8_MIN_N)
-                launch_tc_g<LK, 8>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo, grid,
-                                   TC_G8_MIN_N, 1 << 30);
-        }
-    } else {
-        launch_tc_g<LK, 2>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo, grid, 0, 1 << 30);
+    auto go = [&](int G, int n_lo, int n_hi) {
+        if (G == 8)
+            launch_tc_g<LK, 8>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo, grid, n_lo, n_hi);
+        else if (G == 4)
+            launch_tc_g<LK, 4>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo, grid, n_lo, n_hi);
+        else
+            launch_tc_g<LK, 2>(X, M, L, B, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo, grid, n_lo, n_hi);
+    };
+    if (grp) {   // forced
+        go(grp, 0, 1 << 30);
+        return;
+    }
+    // by size: TcGroups<LK>::SMALL below AT codevectors, LARGE from there on
+    constexpr int small = TcGroups<LK>::SMALL, large = TcGroups<LK>::LARGE, at = TcGroups<LK>::AT;
+    if (small == large || !n_dev) {   // one kernel; the size is known here, or both agree
+        go(n_host >= at ? large : small, 0, 1 << 30);
+    } else {   // training: the stage size is on the device, each kernel takes its range
+        go(small, 0, at);
+        if (n_host >= at) go(large, at, 1 << 30);
     }
 }
 
 void launch_assign_tc(const float *X, int64_t M, int L, const void *Bp, const float *kn,
                       const int32_t *n_dev, int n_host, const float *mu, const float *C,
                       DevState *st, int32_t *assign, float *e, int32_t *flags, cudaStream_t s,
-                      int64_t m_lo)
+                      int64_t m_lo, int grp)
 {
     switch (round_up(L, 16)) {
-    case 16: launch_tc<16>(X, M, L, Bp, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo); break;
-    case 32: launch_tc<32>(X, M, L, Bp, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo); break;
-    case 48: launch_tc<48>(X, M, L, Bp, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo); break;
-    default: launch_tc<64>(X, M, L, Bp, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo); break;
+    case 16: launch_tc<16>(X, M, L, Bp, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo, grp); break;
+    case 32: launch_tc<32>(X, M, L, Bp, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo, grp); break;
+    case 48: launch_tc<48>(X, M, L, Bp, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo, grp); break;
+    default: launch_tc<64>(X, M, L, Bp, kn, n_dev, n_host, mu, C, st, assign, e, flags, s, m_lo, grp); break;
     }
 }
 

@@ -63,6 +63,7 @@ void seq_clear(int dev);
 struct Plan {
     int64_t M = 0, R = 0, S = 0, nq = 0;
     int L = 0, Lp = 0, N = 0, NP = 0, CH = 0, G = 0, max_rec = 0;
+    int grp = 0;       // tensor-core search: codevectors per top-2 group (0: by L and N)
     bool tc = false;   // tensor-core (BF16) allocation
     size_t state, rec, Cp, kn, CT, mu, Ccur, Calt, assign, e, flags, table, dpart, counts, off, perm,
         pieces, mpart, Xs, Cin, Cout, Xhat, Bp, xpart_d, xpart_i, xcnt, qcell, cell_done;
@@ -305,7 +306,7 @@ void run_assign(const Call &c, const Plan &p, const float *X, const float *C, co
     const int64_t M = m_hi < 0 ? p.M : m_hi;
     if (p.tc)
         launch_assign_tc(X, M, p.L, c.at<void>(p.Bp), c.at<float>(p.kn), n_dev, n_host, mu, C, st,
-                         assign, c.at<float>(p.e), c.at<int32_t>(p.flags), c.s, m_lo);
+                         assign, c.at<float>(p.e), c.at<int32_t>(p.flags), c.s, m_lo, p.grp);
     else
         launch_assign(X, M, p.L, p.Lp, c.at<float>(p.Cp), c.at<float>(p.kn), n_dev, n_host, mu, C,
                       st, assign, c.at<float>(p.e), c.at<int32_t>(p.flags), c.s, m_lo, expire);
@@ -391,6 +392,7 @@ void run_update(const Call &c, const Plan &p, const float *X, const int32_t *n_d
 // 0 = FP32, 1 = tensor cores, <0 = error status
 int precision_mode(const lbg_opts &o, int L)
 {
+    if (o.tc_group != 0 && o.tc_group != 2 && o.tc_group != 4 && o.tc_group != 8) return LBG_ERR_ARG;
     if (o.precision == LBG_PREC_FP32) return 0;
     if (o.precision == LBG_PREC_BF16) return tc_supported(L) ? 1 : LBG_ERR_UNSUPPORTED;
     return LBG_ERR_ARG;
@@ -468,7 +470,8 @@ struct GraphPass {
 // its options, so the sequence is recorded once into a graph under that key
 // and later calls with the same key launch the graph on their own stream.
 struct SeqKey {
-    int dev, op, mode, flags;   // op: 0 step, 1 encode; flags: bit 0 reseed, 1 D, 2 decode
+    int dev, op, mode, flags;   // op: 0 step, 1 encode; flags: bit 0 reseed, 1 D, 2 decode,
+                                // bits 8..: the tensor-core group option
     int64_t M;
     int L, N;
     size_t total;               // workspace plan size (fixes every scratch offset)
@@ -657,7 +660,8 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
     const int wH = Xhat ? where(Xhat, c.dev) : 1;
     if (wX < 0 || wC < 0 || wI < 0 || wH < 0) return LBG_ERR_ARG;
     if (res && (wX != 1 || wC != 1 || wI != 1 || wH != 1)) return LBG_ERR_ARG;
-    const Plan p = make_plan(M, L, N, 0, wX == 0, wI == 0, wC == 0, wH == 0, mode == 1);
+    Plan p = make_plan(M, L, N, 0, wX == 0, wI == 0, wC == 0, wH == 0, mode == 1);
+    p.grp = o.tc_group;
     if ((rc = ensure_workspace(c, p.total)) != LBG_OK) return rc;
     DevState *st = c.at<DevState>(p.state);
     // host X: copied piece by piece inside the assignment step (run_assign_host)
@@ -702,7 +706,7 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
         if (!host_ok) return LBG_ERR_CUDA;
         CK(cudaGetLastError());
     } else {
-        const SeqKey key{c.dev, 1, mode, (wantD ? 2 : 0) | (dH ? 4 : 0), M, L, N, p.total, 0.0,
+        const SeqKey key{c.dev, 1, mode, (wantD ? 2 : 0) | (dH ? 4 : 0) | (p.grp << 8), M, L, N, p.total, 0.0,
                          dX, dC, nullptr, dI, dH, res, c.ws};
         if ((rc = seq_run(c, key, issue)) != LBG_OK) return rc;
     }
@@ -740,7 +744,8 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
         return LBG_ERR_ARG;
     const bool hostC = (wCi == 0) || (wCo == 0);
     const bool wsA = !(assign && wA == 1);
-    const Plan p = make_plan(M, L, N, 0, wX == 0, wsA, hostC, false, mode == 1);
+    Plan p = make_plan(M, L, N, 0, wX == 0, wsA, hostC, false, mode == 1);
+    p.grp = o.tc_group;
     if ((rc = ensure_workspace(c, p.total)) != LBG_OK) return rc;
     const size_t cbytes = sizeof(float) * (size_t)N * L;
     if (M == 0) {
@@ -801,7 +806,7 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
         if (!host_ok) return LBG_ERR_CUDA;
         CK(cudaGetLastError());
     } else {
-        const SeqKey key{c.dev, 0, mode, o.reseed_empty ? 1 : 0, M, L, N, p.total,
+        const SeqKey key{c.dev, 0, mode, (o.reseed_empty ? 1 : 0) | (p.grp << 8), M, L, N, p.total,
                          o.reseed_empty ? o.delta_reseed : 0.0, dX, dCi, dCo, dA, nullptr, res, c.ws};
         if ((rc = seq_run(c, key, issue)) != LBG_OK) return rc;
     }
@@ -1325,7 +1330,8 @@ lbg_status lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double del
     for (int n = n_init > 0 ? n_init : 1; n < N; n *= 2) ++stages;
     const int64_t max_total = (int64_t)stages * o.max_passes;
     const int max_rec = o.max_records < max_total ? o.max_records : (int)max_total;
-    const Plan p = make_plan(M, L, N, max_rec, wX == 0, !(assign && wA == 1), false, false, mode == 1);
+    Plan p = make_plan(M, L, N, max_rec, wX == 0, !(assign && wA == 1), false, false, mode == 1);
+    p.grp = o.tc_group;
     if ((rc = ensure_workspace(c, p.total)) != LBG_OK) return rc;
     DevState *st = c.at<DevState>(p.state);
     DevState h;

@@ -267,7 +267,8 @@ void launch_prep_tc(const float *C, int N_alloc, const int32_t *n_dev, int n_hos
                     const float *mu, void *Bp, float *kn, float *CT, DevState *st, cudaStream_t s);
 void launch_assign_tc(const float *X, int64_t M, int L, const void *Bp, const float *kn,
                       const int32_t *n_dev, int n_host, const float *mu, const float *C,
-                      DevState *st, int32_t *assign, float *e, int32_t *flags, cudaStream_t s, int64_t m_lo = 0);
+                      DevState *st, int32_t *assign, float *e, int32_t *flags, cudaStream_t s, int64_t m_lo = 0,
+                      int grp = 0);
 
 // Cell table, distortion and centroid update (k_update.cu).
 void launch_mean(const float *X, int64_t M, int L, double *part, int G, float *mu, float *C0,

@@ -105,6 +105,7 @@ def test_struct_layout_matches_header(tmp_path):
         "         offsetof(lbg_pass_record, D), offsetof(lbg_pass_record, n_empty),\n"
         "         offsetof(lbg_pass_record, ms), offsetof(lbg_opts, trace_C),\n"
         "         offsetof(lbg_opts, trace_cap), offsetof(lbg_opts, test_expire_wait));\n"
+        '  printf("%zu %zu\\n", offsetof(lbg_opts, grad_scale_dev), offsetof(lbg_opts, tc_group));\n'
         "  return 0; }\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
@@ -114,8 +115,25 @@ def test_struct_layout_matches_header(tmp_path):
     O, R = _binding.Opts, _binding.PassRecord
     assert got[:3] == [ctypes.sizeof(O), O.tune_report.offset, O.result_dev.offset]
     assert got[3:6] == [_binding.STEP_RESULT_BYTES, 8, 12]
-    assert got[6:] == [ctypes.sizeof(R), R.D.offset, R.n_empty.offset, R.ms.offset, O.trace_C.offset,
-                       O.trace_cap.offset, O.test_expire_wait.offset]
+    assert got[6:13] == [ctypes.sizeof(R), R.D.offset, R.n_empty.offset, R.ms.offset, O.trace_C.offset,
+                         O.trace_cap.offset, O.test_expire_wait.offset]
+    assert got[13:] == [O.grad_scale_dev.offset, O.tc_group.offset]
+
+
+def test_tc_group_option_is_checked(lib):
+    """tc_group accepts 0, 2, 4 and 8; any other value is LBG_ERR_ARG before any device
+    work (the pointers are never dereferenced)."""
+    from paper_0910_4711_gb300 import _binding
+    fake = ctypes.c_void_p(0x1000)
+    D = ctypes.c_double(0.0)
+    for g, bad in ((3, True), (16, True), (-2, True), (4, False), (0, False)):
+        o = _binding.Opts()
+        lib.lbg_opts_init(ctypes.byref(o))
+        assert o.tc_group == 0
+        o.tc_group = g
+        o.precision = 1
+        rc = lib.vq_encode(fake, 8, 4, fake, 2, fake, None, ctypes.byref(D), ctypes.byref(o))
+        assert (rc == -1) == bad, (g, rc)
 
 
 def test_async_calls_reject_host_outs(lib):

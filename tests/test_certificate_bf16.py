@@ -35,7 +35,7 @@ U = Fraction(1, 2 ** 24)
 NT, HALF = 144, 72                  # codevectors per tile, per half
 # group size -> bits of the in-half group index; packing moves a group minimum by less than
 # 2^(JBITS - 23) of it (at most 2^JBITS - 1 units in the last place)
-JBITS = {2: 6, 8: 4}
+JBITS = {2: 6, 4: 5, 8: 4}
 
 
 def round_bits(x: Fraction, p: int, up: bool = False) -> Fraction:
@@ -108,11 +108,19 @@ def _epilogue(v, GRP):
         c1, c2, cg = [np.float32(np.inf)] * 2, [np.float32(np.inf)] * 2, [0, 0]
         for t in range(nt):
             s1 = list(c1)
+            keys = []
             for j in range(HALF // GRP):
-                q = j % 2
                 base = t * NT + h * HALF + GRP * j
                 lo = np.float32(min(v[base:base + GRP]))
-                k = _f32bits_key(lo, j, JBITS[GRP])
+                keys.append(_f32bits_key(lo, j, JBITS[GRP]))
+            # groups enter two at a time, pair p into chain p % 2 (an odd last one alone)
+            for p in range(0, len(keys) - 1, 2):
+                q = (p // 2) % 2
+                m, hh = min(keys[p], keys[p + 1]), max(keys[p], keys[p + 1])
+                c2[q] = min(c2[q], max(c1[q], m), hh)
+                c1[q] = min(c1[q], m)
+            if len(keys) % 2:
+                q, k = (len(keys) // 2) % 2, keys[-1]
                 c2[q] = min(c2[q], max(c1[q], k))
                 c1[q] = min(c1[q], k)
             for q in range(2):
@@ -359,7 +367,7 @@ def _rows(rng, L, N, spread, trials, family="near"):
         yield x, C, mu
 
 
-@pytest.mark.parametrize("GRP", [2, 8])
+@pytest.mark.parametrize("GRP", [2, 4, 8])
 @pytest.mark.parametrize("L,spread,family", [(16, 20.0, "near"), (16, 2.0, "near"),
                                               (64, 20.0, "near"), (64, 2.0, "near"),
                                               (16, 0.5, "mirror"), (64, 0.5, "mirror")])
@@ -376,7 +384,7 @@ def test_bf16_certificates_sound_at_the_model_bound(L, spread, family, GRP):
     assert accepted > 0
 
 
-@pytest.mark.parametrize("GRP", [2, 8])
+@pytest.mark.parametrize("GRP", [2, 4, 8])
 @pytest.mark.parametrize("L,spread,family", [(16, 20.0, "near"), (16, 2.0, "near"),
                                               (64, 20.0, "near"), (64, 2.0, "near"),
                                               (16, 0.5, "mirror"), (64, 0.5, "mirror")])
@@ -437,12 +445,12 @@ def test_bf16_certificates_accept_clear_winners():
     mu = np.rint(C.mean(0)).astype(np.float32)
     for n in rng.choice(N, 20, replace=False):
         x = np.clip(np.rint(C[n] + rng.standard_normal(L)), 0, 255).astype(np.float32)
-        for GRP in (2, 8):
+        for GRP in (2, 4, 8):
             ok, ii, best = certify(x, C, mu, N, GRP=GRP)
             assert ok and ii == best == n
 
 
-@pytest.mark.parametrize("GRP", [2, 8])
+@pytest.mark.parametrize("GRP", [2, 4, 8])
 def test_bf16_certificates_resolve_split_twins(GRP):
     """Right after a split every codevector has a twin at 2 delta (children 2i and 2i + 1 of
     the same parent).  Twins share a group, so the second-best value the certificates use
@@ -488,7 +496,7 @@ def _rows_real(rng, L, N, spread, trials):
         yield x, C, mu
 
 
-@pytest.mark.parametrize("GRP", [2, 8])
+@pytest.mark.parametrize("GRP", [2, 4, 8])
 @pytest.mark.parametrize("L,spread", [(16, 0.2), (16, 0.02), (32, 0.2), (32, 0.02)])
 def test_bf16_split_form_sound(L, spread, GRP):
     """Real-valued rows take the split form (x~ in two BF16 pieces, the remainder
@@ -516,6 +524,6 @@ def test_bf16_split_form_accepts_clear_winners():
     mu = np.rint(C.mean(0)).astype(np.float32)
     for n in rng.choice(N, 12, replace=False):
         x = (C[n] + 0.1 * rng.standard_normal(L)).astype(np.float32)
-        for GRP in (2, 8):
+        for GRP in (2, 4, 8):
             ok, ii, best = certify(x, C, mu, N, GRP=GRP)
             assert ok and ii == best == n

@@ -147,6 +147,37 @@ def test_exact_fallback_spread_over_ctas(lbg, M, N, L):
     assert np.array_equal(host(dup.idx), host(half.idx)) and dup.D == half.D
 
 
+@pytest.mark.parametrize("L,N,real", [(16, 1500, False), (64, 700, False), (32, 1024, True), (48, 333, True)])
+def test_group_sizes_give_the_same_cells(lbg, L, N, real):
+    """Every epilogue group size (2, 4, 8 codevectors; forced by tc_group) gives the
+    oracle's cells, the same ones; a lloyd step and a training run too."""
+    rng = np.random.default_rng(L * N)
+    if real:
+        X = (rng.standard_normal((9000, L)) * 2.0).astype(np.float32)
+        C = (X[rng.choice(9000, N, replace=False)] + rng.normal(0, 0.1, (N, L))).astype(np.float32)
+    else:
+        X = image_data(L + N, 512, 512, int(round(L ** 0.5)))[:9000]
+        C = codebook_from(X, N, 5)
+    a_ref, e_ref, gap = oracle.assign(X, C.astype(np.float64))
+    first = None
+    for g in (2, 4, 8):
+        r = lbg.vq_encode(dev(X), dev(C), precision="bf16", tc_group=g)
+        check_assign(X, C, host(r.idx), a_ref, e_ref, gap)
+        check_D(r.D, float(e_ref.sum()))
+        s = lbg.lbg_lloyd_step(dev(X), dev(C), precision="bf16", tc_group=g)
+        assert torch.equal(s.assign, r.idx)
+        if first is None:
+            first = (host(r.idx), host(s.C))
+        else:
+            assert np.array_equal(host(r.idx), first[0])
+            check_codebook(host(s.C), first[1])
+    t = [lbg.lbg_train(dev(X), 64, 0.01, 1e-3, precision="bf16", tc_group=g) for g in (2, 8)]
+    assert torch.equal(t[0].assign, t[1].assign) and t[0].records == [
+        dict(r, n_exact=t[0].records[i]["n_exact"], ms=t[0].records[i]["ms"], D=t[0].records[i]["D"])
+        for i, r in enumerate(t[1].records)]
+    check_D(t[0].D, t[1].D)
+
+
 def test_bf16_rejects_large_dimension(lbg):
     X = np.zeros((10, 128), np.float32)
     with pytest.raises(lbg.LBGError) as ei:
