@@ -71,7 +71,7 @@ __device__ __forceinline__ void body_hist(const int32_t *__restrict__ assign,
                                           double *__restrict__ dpart, DevState *st, int blk)
 {
     extern __shared__ int h[];
-    __shared__ double red[HIST_THREADS];
+    __shared__ double red[HIST_THREADS / 32];
     const int tid = threadIdx.x;
     const int64_t m0 = (int64_t)blk * R, m1 = m0 + R < M ? m0 + R : M;
     if (do_hist)
@@ -108,13 +108,17 @@ __device__ __forceinline__ void body_hist(const int32_t *__restrict__ assign,
         acc += run;
     }
     if (clamped) flag_error(st, ERR_INTERNAL);
-    red[tid] = acc;
-    __syncthreads();
-    for (int s = HIST_THREADS / 2; s > 0; s >>= 1) {
-        if (tid < s) red[tid] += red[tid + s];
-        __syncthreads();
+    // the chunk's distortion: a fixed xor tree in each warp, then the warp sums in order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();   // also: every histogram atomic done
+    if (tid == 0) {
+        double d = 0.0;
+#pragma unroll
+        for (int w = 0; w < HIST_THREADS / 32; ++w) d += red[w];
+        dpart[blk] = d;
     }
-    if (tid == 0) dpart[blk] = red[0];
     if (do_hist)
         for (int n = tid; n < N; n += HIST_THREADS) table[(size_t)blk * N + n] = h[n];
 }
@@ -336,13 +340,53 @@ __device__ __forceinline__ void add4(float4 &a, const float4 &b)
 // Warp q sums perm[q*S, (q+1)*S) cell piece by cell piece; G lanes cover a
 // row with float4 loads (L = 4G), 32/G rows per step, four steps in flight.
 // Piece (cell n, warp q) -> pieces[(n + q) * L ...] (unique slot per piece).
+// acc += the rows pp, pp + RPG, ... < pe (RPG = 32 / G; row r = perm[.] of X,
+// this lane's float4 qd), in that order: batches of eight rows in flight per
+// lane, the next batch's perm entries loaded while the current rows are in
+// flight, and the last (fewer than eight) rows in one predicated batch.
+template <int G>
+__device__ __forceinline__ void sum_rows_v4(const float4 *__restrict__ X4, const int32_t *__restrict__ perm,
+                                            int64_t pp, int64_t pe, int qd, float4 &acc)
+{
+    constexpr int RPG = 32 / G;
+    if (pp + 7 * RPG < pe) {
+        int r[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) r[u] = perm[pp + u * RPG];
+        for (;;) {
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldg(X4 + (int64_t)r[u] * G + qd);
+            pp += 8 * RPG;
+            const bool more = pp + 7 * RPG < pe;
+            if (more)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) r[u] = perm[pp + u * RPG];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) add4(acc, v[u]);
+            if (!more) break;
+        }
+    }
+    if (pp < pe) {
+        int r[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) r[u] = pp + u * RPG < pe ? perm[pp + u * RPG] : -1;
+        float4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            v[u] = r[u] >= 0 ? __ldg(X4 + (int64_t)r[u] * G + qd) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (r[u] >= 0) add4(acc, v[u]);
+    }
+}
+
 template <int G>
 __device__ __forceinline__ void body_cellsum_v4(const float *__restrict__ X, int64_t M,
                                                 const int32_t *__restrict__ perm,
                                                 const int32_t *__restrict__ off, int N, int64_t S,
                                                 float *__restrict__ pieces, int blk)
 {
-    constexpr int RPG = 32 / G;
     constexpr int L = 4 * G;
     const int64_t q = (int64_t)blk * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -356,18 +400,7 @@ __device__ __forceinline__ void body_cellsum_v4(const float *__restrict__ X, int
     while (p < p1) {
         const int64_t pe = (int64_t)off[n + 1] < p1 ? (int64_t)off[n + 1] : p1;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        int64_t pp = p + rs;
-        for (; pp + 7 * RPG < pe; pp += 8 * RPG) {   // eight rows in flight per lane
-            int r[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) r[u] = perm[pp + u * RPG];
-            float4 v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = __ldg(X4 + (int64_t)r[u] * G + qd);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) add4(acc, v[u]);
-        }
-        for (; pp < pe; pp += RPG) add4(acc, __ldg(X4 + (int64_t)perm[pp] * G + qd));
+        sum_rows_v4<G>(X4, perm, p + rs, pe, qd, acc);
 #pragma unroll
         for (int o = G; o < 32; o <<= 1) {
             acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
@@ -415,8 +448,64 @@ __device__ __forceinline__ void body_cellsum_any(const float *__restrict__ X, in
     }
 }
 
-// c_n = (sum of its pieces, in piece order, in FP64) / count_n; an empty
-// cell copies C_in (may alias C_out).
+// Combining a cell's pieces (FP32 sums of up to S rows each, pieces q0 .. q1 of
+// cell n in slots n + q0 .. n + q1).  A cell of at most COMBINE_GROUP pieces:
+// the FP64 sum of its pieces in order.  A larger cell (small codebooks: up to
+// M / S pieces in one cell) is combined in two levels so that no warp sums
+// thousands of pieces alone: group k = pieces q0 + CG k .. q0 + CG k + CG - 1
+// is summed in order in FP64 and kept as hi = fl32(s), lo = fl32(s - hi)
+// (exact for the sums of integer pixel rows, and within 2^-48 of s
+// otherwise) in the group's first two piece slots; the cell is the FP64 sum,
+// in group order, of hi then lo of each group.  The same arithmetic runs in
+// the fused form (the warp completing a group or the cell does the sums) and
+// in body_combine (one thread per value), so both give the same bits.
+constexpr int COMBINE_GROUP = 32;
+
+__device__ __forceinline__ int64_t combine_groups(int64_t q0, int64_t q1)
+{
+    return q1 - q0 < COMBINE_GROUP ? 1 : (q1 - q0) / COMBINE_GROUP + 1;
+}
+
+// FP64 sum of pieces [ga, gb] of cell n, component l, in order.
+__device__ __forceinline__ double sum_pieces(const float *__restrict__ pieces, int n, int64_t ga, int64_t gb,
+                                             int L, int l)
+{
+    double s = 0.0;
+    int64_t q = ga;
+    for (; q + 7 <= gb; q += 8) {   // eight loads in flight, added in order
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldcg(pieces + (size_t)(n + q + u) * L + l);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += (double)v[u];
+    }
+    for (; q <= gb; ++q) s += (double)__ldcg(pieces + (size_t)(n + q) * L + l);
+    return s;
+}
+
+// Component l of the centroid of a cell (pieces q0 .. q1, count b - a).  With
+// more than one group, each group's (hi, lo) are in its first two slots (a
+// one-piece group: its piece, lo = 0).
+__device__ __forceinline__ float cell_value(const float *__restrict__ pieces, int n, int64_t q0, int64_t q1,
+                                            int64_t count, int L, int l)
+{
+    double s;
+    if (q1 - q0 < COMBINE_GROUP) {
+        s = sum_pieces(pieces, n, q0, q1, L, l);
+    } else {
+        s = 0.0;
+        for (int64_t g = q0; g <= q1; g += COMBINE_GROUP) {
+            s += (double)__ldcg(pieces + (size_t)(n + g) * L + l);
+            if (g < q1) s += (double)__ldcg(pieces + (size_t)(n + g + 1) * L + l);
+        }
+    }
+    // FP32 division of the rounded sum (two roundings, ~1.2e-7 relative; FP64
+    // division is slow on this part)
+    return (float)s / (float)count;
+}
+
+// c_n = (FP64 sum of its pieces, in the order and levels of piece_done) /
+// count_n, one thread per value; an empty cell copies C_in (may alias C_out).
 __device__ __forceinline__ void body_combine(const float *__restrict__ pieces,
                                              const int32_t *__restrict__ off, int N, int L, int64_t S,
                                              const float *C_in, float *C_out, int blk)
@@ -431,7 +520,21 @@ __device__ __forceinline__ void body_combine(const float *__restrict__ pieces,
     }
     const int64_t q0 = a / S, q1 = (b - 1) / S;
     double s = 0.0;
-    for (int64_t q = q0; q <= q1; ++q) s += (double)pieces[(size_t)(n + q) * L + l];
+    if (q1 - q0 < COMBINE_GROUP) {
+        s = sum_pieces(pieces, n, q0, q1, L, l);
+    } else {   // the two levels of piece_done, with (hi, lo) of each group in registers
+        for (int64_t g = q0; g <= q1; g += COMBINE_GROUP) {
+            const int64_t g1 = g + COMBINE_GROUP - 1 < q1 ? g + COMBINE_GROUP - 1 : q1;
+            if (g1 == g) {
+                s += (double)__ldcg(pieces + (size_t)(n + g) * L + l);
+            } else {
+                const double sg = sum_pieces(pieces, n, g, g1, L, l);
+                const float hi = (float)sg;
+                s += (double)hi;
+                s += (double)(float)(sg - (double)hi);
+            }
+        }
+    }
     // FP32 division of the rounded sum (two roundings, ~1.2e-7 relative; FP64
     // division is slow on this part)
     C_out[i] = (float)s / (float)(b - a);
@@ -476,26 +579,57 @@ __device__ __forceinline__ void body_stage(DevState *st)
     }
 }
 
-// The centroid of cell n straight from its pieces: FP64 sum of the pieces in
-// order, divided by the count (the arithmetic of body_combine).
-__device__ __forceinline__ void combine_cell(const float *__restrict__ pieces, int n, int64_t a, int64_t b,
-                                             int64_t S, int L, float *__restrict__ C_out, int lane)
+// The warp that has stored piece q of cell n (rows [a, b)): counts it; the
+// warp completing a group stores the group's (hi, lo), and the warp completing
+// the cell writes its centroid.  cell_done[0 .. N) counts finished pieces (a
+// cell of one group) or finished groups per cell, gdone = cell_done + N counts finished pieces per group (indexed by the
+// slot of the group's first piece); each counter is reset by the warp that
+// completes it.
+__device__ __forceinline__ void piece_done(float *__restrict__ pieces, int32_t *__restrict__ cell_done, int N,
+                                           int n, int64_t q, int64_t a, int64_t b, int64_t S, int L,
+                                           float *__restrict__ C_out, int lane)
 {
     const int64_t q0 = a / S, q1 = (b - 1) / S;
-    for (int l = lane; l < L; l += 32) {
-        double s = 0.0;
-        for (int64_t q = q0; q <= q1; ++q) s += (double)__ldcg(pieces + (size_t)(n + q) * L + l);
-        C_out[(int64_t)n * L + l] = (float)s / (float)(b - a);
+    const int64_t ng = combine_groups(q0, q1);
+    __threadfence();
+    __syncwarp();
+    if (ng > 1) {
+        int32_t *gdone = cell_done + N;
+        const int64_t g0 = q0 + (q - q0) / COMBINE_GROUP * COMBINE_GROUP;
+        const int64_t g1 = g0 + COMBINE_GROUP - 1 < q1 ? g0 + COMBINE_GROUP - 1 : q1;
+        int last = 0;
+        if (lane == 0) last = atomicAdd(&gdone[n + g0], 1) == (int)(g1 - g0);
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (!last) return;
+        __threadfence();
+        if (g1 > g0)
+            for (int l = lane; l < L; l += 32) {
+                const double sg = sum_pieces(pieces, n, g0, g1, L, l);
+                const float hi = (float)sg;
+                pieces[(size_t)(n + g0) * L + l] = hi;
+                pieces[(size_t)(n + g0 + 1) * L + l] = (float)(sg - (double)hi);
+            }
+        if (lane == 0) gdone[n + g0] = 0;
+        __threadfence();
+        __syncwarp();
     }
+    // the cell counter counts pieces (one group) or completed groups
+    const int expect = ng > 1 ? (int)(ng - 1) : (int)(q1 - q0);
+    int last = 0;
+    if (lane == 0) last = atomicAdd(&cell_done[n], 1) == expect;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence();
+    for (int l = lane; l < L; l += 32) C_out[(int64_t)n * L + l] = cell_value(pieces, n, q0, q1, b - a, L, l);
+    if (lane == 0) cell_done[n] = 0;
 }
 
-// A cell piece is finished: a cell held by one piece is divided by its count at
-// once; otherwise the piece is stored (slot n + q), and the warp that stores
-// the cell's last piece (a per-cell counter, after a fence) combines them.
-// Both give the bits body_combine gives.
+// End of the warp's piece of cell n (rows [a, b), L = 4 G, lanes (rs, qd) hold
+// the reduced sums in rs == 0): a cell that lies in this one piece gets its
+// centroid at once; else the piece is stored and piece_done combines.
 template <int G>
 __device__ __forceinline__ void finish_piece_v4(float4 acc, int n, int64_t q, int64_t a, int64_t b, int64_t S,
-                                                float *__restrict__ pieces, int32_t *__restrict__ cell_done,
+                                                float *__restrict__ pieces, int32_t *__restrict__ cell_done, int N,
                                                 float *__restrict__ C_out, int lane)
 {
     constexpr int L = 4 * G;
@@ -510,15 +644,7 @@ __device__ __forceinline__ void finish_piece_v4(float4 acc, int n, int64_t q, in
         return;
     }
     if (rs == 0) reinterpret_cast<float4 *>(pieces + (size_t)(n + q) * L)[qd] = acc;
-    __threadfence();
-    __syncwarp();
-    int last = 0;
-    if (lane == 0) last = atomicAdd(&cell_done[n], 1) == (int)(q1 - q0);
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (!last) return;
-    __threadfence();
-    combine_cell(pieces, n, a, b, S, L, C_out, lane);
-    if (lane == 0) cell_done[n] = 0;
+    piece_done(pieces, cell_done, N, n, q, a, b, S, L, C_out, lane);
 }
 
 // Warp q sums perm[q S, (q + 1) S) cell piece by cell piece, as
@@ -530,10 +656,8 @@ __device__ __forceinline__ void body_cellsum_c(const float *__restrict__ X, int6
                                                const int32_t *__restrict__ off,
                                                const int32_t *__restrict__ qcell, int N, int64_t S,
                                                float *__restrict__ pieces, int32_t *__restrict__ cell_done,
-                                               float *__restrict__ C_out, int blk)
+                                               float *__restrict__ C_out, int64_t q)
 {
-    constexpr int RPG = 32 / G;
-    const int64_t q = (int64_t)blk * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const int64_t p0 = q * S;
     if (p0 >= M) return;
@@ -546,18 +670,7 @@ __device__ __forceinline__ void body_cellsum_c(const float *__restrict__ X, int6
         const int64_t a = off[n], b = off[n + 1];
         const int64_t pe = b < p1 ? b : p1;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        int64_t pp = p + rs;
-        for (; pp + 7 * RPG < pe; pp += 8 * RPG) {   // eight rows in flight per lane
-            int r[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) r[u] = perm[pp + u * RPG];
-            float4 v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = __ldg(X4 + (int64_t)r[u] * G + qd);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) add4(acc, v[u]);
-        }
-        for (; pp < pe; pp += RPG) add4(acc, __ldg(X4 + (int64_t)perm[pp] * G + qd));
+        sum_rows_v4<G>(X4, perm, p + rs, pe, qd, acc);
 #pragma unroll
         for (int o = G; o < 32; o <<= 1) {
             acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
@@ -565,7 +678,7 @@ __device__ __forceinline__ void body_cellsum_c(const float *__restrict__ X, int6
             acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
             acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
         }
-        finish_piece_v4<G>(acc, n, q, a, b, S, pieces, cell_done, C_out, lane);
+        finish_piece_v4<G>(acc, n, q, a, b, S, pieces, cell_done, N, C_out, lane);
         p = pe;
         while (n + 1 < N && off[n + 1] <= p) ++n;
     }
@@ -587,6 +700,9 @@ __device__ __forceinline__ void body_piece_cells(const int32_t *__restrict__ off
             continue;
         }
         for (int64_t q = (a + S - 1) / S; q * S < b; ++q) qcell[q] = n;
+        const int64_t q0 = a / S, q1 = (b - 1) / S;   // group counters of a large cell
+        if (combine_groups(q0, q1) > 1)
+            for (int64_t g = q0; g <= q1; g += COMBINE_GROUP) cell_done[N + n + g] = 0;
     }
 }
 
@@ -597,9 +713,8 @@ __device__ __forceinline__ void body_cellsum_c_any(const float *__restrict__ X, 
                                                    const int32_t *__restrict__ off,
                                                    const int32_t *__restrict__ qcell, int N, int64_t S,
                                                    float *__restrict__ pieces, int32_t *__restrict__ cell_done,
-                                                   float *__restrict__ C_out, int blk)
+                                                   float *__restrict__ C_out, int64_t q)
 {
-    const int64_t q = (int64_t)blk * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const int64_t p0 = q * S;
     if (p0 >= M) return;
@@ -632,16 +747,7 @@ __device__ __forceinline__ void body_cellsum_c_any(const float *__restrict__ X, 
                 const int l = lane + 32 * k;
                 if (l < L) pieces[(size_t)(n + q) * L + l] = acc[k];
             }
-            __threadfence();
-            __syncwarp();
-            int last = 0;
-            if (lane == 0) last = atomicAdd(&cell_done[n], 1) == (int)(q1 - q0);
-            last = __shfl_sync(0xffffffffu, last, 0);
-            if (last) {
-                __threadfence();
-                combine_cell(pieces, n, a, b, S, L, C_out, lane);
-                if (lane == 0) cell_done[n] = 0;
-            }
+            piece_done(pieces, cell_done, N, n, q, a, b, S, L, C_out, lane);
         }
         p = pe;
         while (n + 1 < N && off[n + 1] <= p) ++n;

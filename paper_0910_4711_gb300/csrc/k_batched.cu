@@ -158,9 +158,9 @@ __device__ __forceinline__ bool last_block(DevState *st, unsigned count)
 __device__ __forceinline__ void abort_all(unsigned *bar) { atomicExch(bar + 2, 1u); }
 
 template <int G>
-__device__ __forceinline__ void cellsum_phase(const BatchSet &q, int N, int b)
+__device__ __forceinline__ void cellsum_phase(const BatchSet &q, int N, int64_t w)
 {
-    body_cellsum_c<G>(q.X, q.M, q.perm, q.off, q.qcell, N, q.S, q.pieces, q.cell_done, q.C, b);
+    body_cellsum_c<G>(q.X, q.M, q.perm, q.off, q.qcell, N, q.S, q.pieces, q.cell_done, q.C, w);
 }
 
 __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
@@ -288,25 +288,31 @@ __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
     }
     if (!grid_barrier(a.bar, sets, S)) return;
 
-    // 7: cell sums and centroids (in place; an empty cell keeps its codevector)
-    for (int vb = blockIdx.x; vb < a.tot_cellsum; vb += grid) {
-        const int s = find_set(a.pre_cellsum, S, vb);
-        const BatchSet &q = sets[s];
-        const int b = vb - a.pre_cellsum[s];
-        if (T.run[s] & 2) {
-            switch (a.vec ? a.L : 0) {
-            case 4: cellsum_phase<1>(q, T.ncur[s], b); break;
-            case 8: cellsum_phase<2>(q, T.ncur[s], b); break;
-            case 16: cellsum_phase<4>(q, T.ncur[s], b); break;
-            case 32: cellsum_phase<8>(q, T.ncur[s], b); break;
-            case 64: cellsum_phase<16>(q, T.ncur[s], b); break;
-            case 128: cellsum_phase<32>(q, T.ncur[s], b); break;
-            default:
-                body_cellsum_c_any(q.X, q.M, a.L, q.perm, q.off, q.qcell, T.ncur[s], q.S, q.pieces,
-                                   q.cell_done, q.C, b);
+    // 7: cell sums and centroids (in place; an empty cell keeps its codevector).  The
+    // bodies are per warp and use no shared memory: warps take the pieces one by one
+    // (piece w of the launch-per-phase form's block w / 8), with no block-wide step.
+    {
+        constexpr int WPB = BP_THREADS / 32;
+        const int64_t nw = (int64_t)grid * WPB, tot = (int64_t)a.tot_cellsum * WPB;
+        for (int64_t w = (int64_t)blockIdx.x * WPB + (tid >> 5); w < tot; w += nw) {
+            const int vb = (int)(w / WPB);
+            const int s = find_set(a.pre_cellsum, S, vb);
+            const BatchSet &q = sets[s];
+            const int64_t qq = (int64_t)(vb - a.pre_cellsum[s]) * WPB + (w % WPB);
+            if (T.run[s] & 2) {
+                switch (a.vec ? a.L : 0) {
+                case 4: cellsum_phase<1>(q, T.ncur[s], qq); break;
+                case 8: cellsum_phase<2>(q, T.ncur[s], qq); break;
+                case 16: cellsum_phase<4>(q, T.ncur[s], qq); break;
+                case 32: cellsum_phase<8>(q, T.ncur[s], qq); break;
+                case 64: cellsum_phase<16>(q, T.ncur[s], qq); break;
+                case 128: cellsum_phase<32>(q, T.ncur[s], qq); break;
+                default:
+                    body_cellsum_c_any(q.X, q.M, a.L, q.perm, q.off, q.qcell, T.ncur[s], q.S, q.pieces,
+                                       q.cell_done, q.C, qq);
+                }
             }
         }
-        __syncthreads();
     }
     if (!grid_barrier(a.bar, sets, S)) return;
 

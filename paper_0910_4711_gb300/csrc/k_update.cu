@@ -151,7 +151,8 @@ __global__ void __launch_bounds__(256)
                 float *__restrict__ C_out, DevState *st, int train)
 {
     if (skip_update(st, train)) return;
-    body_cellsum_c<G>(X, M, perm, off, qcell, cur_n(n_dev, n_host), S, pieces, cell_done, C_out, blockIdx.x);
+    body_cellsum_c<G>(X, M, perm, off, qcell, cur_n(n_dev, n_host), S, pieces, cell_done, C_out,
+                      (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5));
 }
 
 // Any L: as body_cellsum_any, with the pieces finished as above.
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(256)
 {
     if (skip_update(st, train)) return;
     body_cellsum_c_any(X, M, L, perm, off, qcell, cur_n(n_dev, n_host), S, pieces, cell_done, C_out,
-                       blockIdx.x);
+                       (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5));
 }
 
 // ---------------------------------------------------------------- backward

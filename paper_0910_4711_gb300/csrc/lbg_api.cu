@@ -126,7 +126,7 @@ Plan make_plan(int64_t M, int L, int N, int max_rec, bool host_X, bool need_assi
     p.perm = p.take(sizeof(int32_t) * (size_t)(M > 0 ? M : 1));
     p.pieces = p.take(sizeof(float) * (size_t)(N + p.nq) * L);
     p.qcell = p.take(sizeof(int32_t) * (size_t)(p.nq > 0 ? p.nq : 1));
-    p.cell_done = p.take(sizeof(int32_t) * (size_t)N);
+    p.cell_done = p.take(sizeof(int32_t) * (size_t)(2 * N + p.nq));   // per cell, then per piece group
     p.mpart = p.take(sizeof(double) * (size_t)p.G * L);
     p.Xs = host_X ? p.take(sizeof(float) * (size_t)M * L) : 0;
     p.Cin = host_C ? p.take(sizeof(float) * (size_t)N * L) : 0;
