@@ -122,26 +122,38 @@ struct AssignSmemT {
 
 using AssignSmem = AssignSmemT<BM>;
 
+// Barrier of the 2 TBM threads running one tile: the whole CTA (id 0), or a
+// named barrier of a thread group (id > 0) when a CTA runs several tiles.
+__device__ __forceinline__ void tile_sync(int id, int threads)
+{
+    if (id == 0)
+        __syncthreads();
+    else
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
 // Nearest codevector of the TBM rows starting at m0 (see the file header);
 // 2 TBM threads: warps are 4x8 thread grids of 8x8 (row, codevector) tiles,
 // TBM / 32 warp rows x 2 warp columns.
 // The two chunk barriers persist across calls of one CTA: use0/use1 count
 // their completed phases.  Returns false (after reporting) if a bulk copy
-// timed out; every thread of the CTA returns the same value.  `expire`
+// timed out; every thread of the tile returns the same value.  `expire`
 // (a test hook) makes the first chunk wait give up at once, as a wait that
-// ran out of time would.
+// ran out of time would.  The tile's threads are threadIdx.x = tbase ..
+// tbase + 2 TBM - 1, synchronised by tile_sync(sync_id) (0: the whole CTA).
 template <int TBM>
 __device__ __forceinline__ bool assign_f32_tile_t(
     const float *__restrict__ X, int64_t M, int L, int Lp, const float *__restrict__ Cp,
     const float *__restrict__ kn, int N, const float *__restrict__ mu, const float *__restrict__ C,
     DevState *st, int32_t *__restrict__ assign, float *__restrict__ e, int32_t *__restrict__ flags,
-    int64_t m0, float *smem, AssignSmemT<TBM> &sh, uint32_t &use0, uint32_t &use1, int expire = 0)
+    int64_t m0, float *smem, AssignSmemT<TBM> &sh, uint32_t &use0, uint32_t &use1, int expire = 0,
+    int tbase = 0, int sync_id = 0)
 {
     uint64_t *bar = sh.bar;
     auto &rec_v1 = sh.rec_v1;
     auto &rec_v2 = sh.rec_v2;
     auto &rec_id = sh.rec_id;
-    const int tid = threadIdx.x;
+    const int tid = (int)threadIdx.x - tbase;
     const int nchunk = (N + BN - 1) / BN;
     const int chunk_floats = (Lp + 1) * BN;
     const uint32_t chunk_bytes = (uint32_t)chunk_floats * 4u;
@@ -187,7 +199,7 @@ __device__ __forceinline__ bool assign_f32_tile_t(
         v2[i] = INFINITY;
         mk[i] = 0;
     }
-    __syncthreads();
+    tile_sync(sync_id, 2 * TBM);
 
     int k_stop = nchunk;
     for (int k = 0; k < nchunk; ++k) {
@@ -232,7 +244,7 @@ __device__ __forceinline__ bool assign_f32_tile_t(
                 mk[i] = (v1[i] < old) ? k : mk[i];
             }
         }
-        __syncthreads();
+        tile_sync(sync_id, 2 * TBM);
         if (sh.abort) {
             k_stop = k;
             break;
@@ -278,7 +290,7 @@ __device__ __forceinline__ bool assign_f32_tile_t(
             rec_id[wc][r] = id;
         }
     }
-    __syncthreads();
+    tile_sync(sync_id, 2 * TBM);
     const int r = tid;
     const int64_t m = m0 + r;
     if (tid >= TBM || m >= M) return true;

@@ -840,67 +840,92 @@ __device__ __forceinline__ void tc_tail(TcSmem &sh, int warp, int lane, int acc,
     // i1 + (GRP / 2) half + g
     float kmax = 0.f;
     const bool coop = (L & 3) == 0 && ((reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(X)) & 15u) == 0;
+    // members in passes of CPB: the x rows are loaded once per pass for all its members
+    constexpr int CPB = GRP / 2 < 2 ? GRP / 2 : 2;
 #pragma unroll 1
-    for (int g = 0; g < GRP / 2; ++g) {
-        const int cand = i1 + (GRP / 2) * half + g;
-        const int ccand = (usable && cand < N) ? cand : -1;
-        if (ccand >= 0) kmax = fmaxf(kmax, __ldg(kn + ccand));
-        float dc = INFINITY;
+    for (int g0 = 0; g0 < GRP / 2; g0 += CPB) {
+        int ccand[CPB];
+#pragma unroll
+        for (int c = 0; c < CPB; ++c) {
+            const int cand = i1 + (GRP / 2) * half + g0 + c;
+            ccand[c] = (usable && cand < N) ? cand : -1;
+            if (ccand[c] >= 0) kmax = fmaxf(kmax, __ldg(kn + ccand[c]));
+        }
+        float dc[CPB];
+#pragma unroll
+        for (int c = 0; c < CPB; ++c) dc[c] = INFINITY;
         if (coop) {
             const int rq = lane & 15, sub = lane >> 4;
             const int64_t mrow0 = m0 + 128 * acc + 32 * (warp & 3);   // row of lane 0
-            float p[16];
+            float p[CPB][16];
 #pragma unroll
             for (int bt = 0; bt < 4; ++bt) {   // four batches of 4 rows
-                int crs[4];
+                int crs[CPB][4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) crs[k] = __shfl_sync(0xffffffffu, ccand, 2 * (4 * bt + k) + sub);
-                float4 c4[4], x4[4];
+                for (int c = 0; c < CPB; ++c)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) crs[c][k] = __shfl_sync(0xffffffffu, ccand[c], 2 * (4 * bt + k) + sub);
+                float4 c4[CPB][4], x4[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const bool on = crs[k] >= 0 && 4 * rq < L;
                     const int64_t mr = mrow0 + 2 * (4 * bt + k) + sub;
-                    c4[k] = on ? __ldg(reinterpret_cast<const float4 *>(C + (size_t)crs[k] * L) + rq)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
-                    x4[k] = on ? __ldg(reinterpret_cast<const float4 *>(X + mr * L) + rq)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
+                    bool any = false;
+#pragma unroll
+                    for (int c = 0; c < CPB; ++c) {
+                        const bool on = crs[c][k] >= 0 && 4 * rq < L;
+                        any = any || on;
+                        c4[c][k] = on ? __ldg(reinterpret_cast<const float4 *>(C + (size_t)crs[c][k] * L) + rq)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                    x4[k] = any ? __ldg(reinterpret_cast<const float4 *>(X + mr * L) + rq)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    float d = __fsub_rn(x4[k].x, c4[k].x);
-                    float q = d * d;
-                    d = __fsub_rn(x4[k].y, c4[k].y);
-                    q = fmaf(d, d, q);
-                    d = __fsub_rn(x4[k].z, c4[k].z);
-                    q = fmaf(d, d, q);
-                    d = __fsub_rn(x4[k].w, c4[k].w);
-                    p[4 * bt + k] = fmaf(d, d, q);
-                }
+                for (int c = 0; c < CPB; ++c)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        float d = __fsub_rn(x4[k].x, c4[c][k].x);
+                        float q = d * d;
+                        d = __fsub_rn(x4[k].y, c4[c][k].y);
+                        q = fmaf(d, d, q);
+                        d = __fsub_rn(x4[k].z, c4[c][k].z);
+                        q = fmaf(d, d, q);
+                        d = __fsub_rn(x4[k].w, c4[c][k].w);
+                        p[c][4 * bt + k] = fmaf(d, d, q);
+                    }
             }
 #pragma unroll
-            for (int lvl = 8; lvl >= 1; lvl >>= 1) {
-                const bool up = (rq & lvl) != 0;
+            for (int c = 0; c < CPB; ++c) {
 #pragma unroll
-                for (int i = 0; i < lvl; ++i) {
-                    const float send = up ? p[i] : p[i + lvl];
-                    const float keep = up ? p[i + lvl] : p[i];
-                    p[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, lvl));
+                for (int lvl = 8; lvl >= 1; lvl >>= 1) {
+                    const bool up = (rq & lvl) != 0;
+#pragma unroll
+                    for (int i = 0; i < lvl; ++i) {
+                        const float send = up ? p[c][i] : p[c][i + lvl];
+                        const float keep = up ? p[c][i + lvl] : p[c][i];
+                        p[c][i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, lvl));
+                    }
                 }
+                // lane (sub, rq) now holds the sum of row 2 rq + sub
+                const float got = __shfl_sync(0xffffffffu, p[c][0], (lane & 1) * 16 + (lane >> 1));
+                if (ccand[c] >= 0) dc[c] = got;
             }
-            // lane (sub, rq) now holds the sum of row 2 rq + sub
-            const float got = __shfl_sync(0xffffffffu, p[0], (lane & 1) * 16 + (lane >> 1));
-            if (ccand >= 0) dc = got;
-        } else if (ccand >= 0) {
-            const float *xr = X + m * L;
-            const float *cr = C + (size_t)ccand * L;
-            float d2 = 0.f;
-            for (int l = 0; l < L; ++l) {
-                const float d = __fsub_rn(__ldg(xr + l), __ldg(cr + l));
-                d2 = fmaf(d, d, d2);
-            }
-            dc = d2;
+        } else {
+#pragma unroll
+            for (int c = 0; c < CPB; ++c)
+                if (ccand[c] >= 0) {
+                    const float *xr = X + m * L;
+                    const float *cr = C + (size_t)ccand[c] * L;
+                    float d2 = 0.f;
+                    for (int l = 0; l < L; ++l) {
+                        const float d = __fsub_rn(__ldg(xr + l), __ldg(cr + l));
+                        d2 = fmaf(d, d, d2);
+                    }
+                    dc[c] = d2;
+                }
         }
-        sh.r.d[(GRP / 2) * half + g][crow] = dc;
+#pragma unroll
+        for (int c = 0; c < CPB; ++c) sh.r.d[(GRP / 2) * half + g0 + c][crow] = dc[c];
     }
     sh.r.k[half][crow] = kmax;
     named_sync(2, 32 * TC_EPI_WARPS);
@@ -1566,12 +1591,13 @@ void launch_prep_tc(const float *C, int N_alloc, const int32_t *n_dev, int n_hos
 // Group size of the epilogue by codebook size: larger groups cut the per-value
 // epilogue work and the flagged rows, smaller ones the tail's exact distances
 // per row.  Measured on GB300 (search + exact re-scoring, ms): image blocks
-// L = 64, N = 4096: G = 2 0.509, 4 0.497, 8 0.556; N = 2048: 0.325, 0.336,
-// 0.400; L = 16, N = 4096: 3.54, 3.04, 3.19; N = 1024: 1.339, 1.355, 1.701;
-// mixture L = 32, N = 4096: 0.339, 0.272, 0.265; N = 512: 0.088, 0.089, 0.113.
+// L = 64, N = 4096: G = 2 0.491, 4 0.474, 8 0.519; N = 2048: 0.312, 0.308,
+// 0.368; N = 1024: 0.206, 0.216, 0.276; L = 16, N = 4096: 3.36, 2.83, 2.99;
+// N = 1024: 1.206, 1.165, 1.564; mixture L = 32, N = 4096: 0.324, 0.257, 0.257;
+// N = 512: 0.077, 0.077, 0.105.
 template <int LK>
 struct TcGroups {
-    static constexpr int SMALL = 2, LARGE = 4, AT = LK <= 32 ? 2048 : 4096;
+    static constexpr int SMALL = 2, LARGE = 4, AT = LK <= 32 ? 1024 : 2048;
 };
 
 template <int LK, int GRP>

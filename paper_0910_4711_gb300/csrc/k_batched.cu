@@ -12,7 +12,9 @@
 // cooperative launch (all CTAs resident), instead of one launch per phase:
 //   0  reset: assignment work counter, per-problem max ||c~||
 //   1  codebook preparation (per problem, 32-codevector blocks)
-//   2  nearest codevector: CTAs take (problem, 128-row tile) items from a counter
+//   2  nearest codevector: each half of a CTA (128 threads, its own named
+//      barrier and shared buffers) takes (problem, 64-row tile) items from a
+//      counter
 //   3  exact re-scoring of the uncertified rows (groups of 8 rows, all problems)
 //   4  per-chunk cell counts and distortion partials; the last block of a
 //      problem runs its stop test (sum in chunk order, (D_prev - D)/D <= theta)
@@ -40,6 +42,13 @@ namespace lbg {
 namespace {
 
 constexpr int BP_THREADS = 256;
+constexpr int BP_TILE = 64;         // rows per assignment tile: two tiles of 128 threads per CTA
+
+// Floats of one assignment tile's dynamic shared memory: the x tile, two codebook chunks.
+__host__ __device__ constexpr size_t assign_floats(int Lp, int tbm)
+{
+    return (size_t)Lp * tbm + 2 * (size_t)(Lp + 1) * BN;
+}
 constexpr int BP_MAX_SETS = 1024;   // problems the per-CTA state tables hold (more: per-phase launches)
 
 // Per-problem state as of a phase's start, read once per CTA after the barrier
@@ -166,9 +175,9 @@ __device__ __forceinline__ void cellsum_phase(const BatchSet &q, int N, int64_t 
 __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
 {
     extern __shared__ __align__(128) float dsm[];   // each phase's dynamic shared memory, then the tables
-    __shared__ AssignSmemT<BM> ash;
+    __shared__ AssignSmemT<BP_TILE> ash[2];
     __shared__ __align__(16) ExactSmem esh;
-    __shared__ int64_t s_item;
+    __shared__ int64_t s_item[2];
     const BatchSet *sets = a.sets;
     const int S = a.S, tid = threadIdx.x;
     const int grid = (int)gridDim.x;
@@ -177,9 +186,11 @@ __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
 
     // 0: reset; the shared-memory barriers of the assignment and exact phases
     if (tid == 0) {
-        mbar_init(&ash.bar[0], 1);
-        mbar_init(&ash.bar[1], 1);
-        ash.abort = 0;
+        for (int h = 0; h < 2; ++h) {
+            mbar_init(&ash[h].bar[0], 1);
+            mbar_init(&ash[h].bar[1], 1);
+            ash[h].abort = 0;
+        }
         fence_mbar_init();
     }
     __syncthreads();
@@ -201,24 +212,37 @@ __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
     }
     if (!grid_barrier(a.bar, sets, S)) return;
 
-    // 2: nearest codevector, (problem, row tile) items from the counter
-    uint32_t u0 = 0, u1 = 0;
-    for (;;) {
-        if (tid == 0) s_item = (int64_t)atomicAdd(a.counter, 1);
-        __syncthreads();
-        const int64_t item = s_item;
-        if (item >= a.ntiles) break;
-        const int s = find_set64(a.pre_tiles, S, item);
-        const BatchSet &q = sets[s];
-        if (T.run[s] & 1) {
-            const int64_t tile = item - a.pre_tiles[s];
-            if (!assign_f32_tile_t<BM>(q.X, q.M, a.L, a.Lp, q.Cp, q.kn, T.ncur[s], q.mu, q.C, q.st, q.assign,
-                                       q.e, q.flags, tile * BM, dsm, ash, u0, u1)) {
-                abort_all(a.bar);   // reported by the tile; its copies have been waited for
-                return;
+    // 2: nearest codevector.  The two halves of the CTA work independently (named
+    // barriers 1 and 2), each taking (problem, 64-row tile) items from the counter
+    // into its own shared buffers; a half whose copy timed out stops, and the CTA
+    // leaves once both halves are done.
+    {
+        const int half = tid >> 7;
+        uint32_t u0 = 0, u1 = 0;
+        float *hsm = dsm + half * assign_floats(a.Lp, BP_TILE);
+        bool failed = false;
+        for (;;) {
+            if ((tid & 127) == 0) s_item[half] = (int64_t)atomicAdd(a.counter, 1);
+            tile_sync(1 + half, 2 * BP_TILE);
+            const int64_t item = s_item[half];
+            if (item >= a.ntiles) break;
+            const int s = find_set64(a.pre_tiles, S, item);
+            const BatchSet &q = sets[s];
+            if (T.run[s] & 1) {
+                const int64_t tile = item - a.pre_tiles[s];
+                if (!assign_f32_tile_t<BP_TILE>(q.X, q.M, a.L, a.Lp, q.Cp, q.kn, T.ncur[s], q.mu, q.C, q.st,
+                                               q.assign, q.e, q.flags, tile * BP_TILE, hsm, ash[half], u0, u1,
+                                               0, half * 2 * BP_TILE, 1 + half)) {
+                    failed = true;   // reported by the tile; its copies have been waited for
+                    break;
+                }
             }
+            tile_sync(1 + half, 2 * BP_TILE);   // this item's shared data read before the next
         }
-        __syncthreads();   // all reads of this item's shared data before the next item
+        if (__syncthreads_or(failed)) {
+            if (tid == 0) abort_all(a.bar);
+            return;
+        }
     }
     if (!grid_barrier(a.bar, sets, S)) return;
 
@@ -337,7 +361,7 @@ __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
 size_t pass_phase_smem(int L, int NMAXB)
 {
     const int Lp = round_up(L, 4);
-    const size_t assign = (size_t)(Lp * BM + 2 * (Lp + 1) * BN) * sizeof(float);
+    const size_t assign = 2 * assign_floats(Lp, BP_TILE) * sizeof(float);
     const size_t exact = (size_t)2 * Lp * EX_SW * sizeof(float);
     const size_t hist = (size_t)NMAXB * sizeof(int);
     const size_t scatter = (size_t)NMAXB * (sizeof(int) + 8);

@@ -1164,8 +1164,8 @@ lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, 
     bp.tot_split = P[5][S];
     bp.pre_copy = dP[6];
     bp.tot_copy = P[6][S];
-    bp.pre_tiles = dtiles;
-    bp.ntiles = tiles[S];
+    bp.pre_tiles = dtiles64;
+    bp.ntiles = tiles64[S];
     bp.counter = counter;
     bp.bar = dbar;
     bp.theta = theta;
@@ -1180,7 +1180,8 @@ lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, 
     lbg_tune_report report;
     memset(&report, 0, sizeof(report));
     if (pass_ctas > 0) {
-        ctas = pass_ctas;   // the persistent pass: 128-row tiles, its resident CTAs
+        tile_rows = 64;     // the persistent pass: two 64-row tiles per CTA, its resident CTAs
+        ctas = pass_ctas;
     } else if (o.tile_rows != 0 || o.ctas_per_sm != 0) {
         tile_rows = o.tile_rows != 0 ? o.tile_rows : 128;
         ctas = o.ctas_per_sm != 0 ? o.ctas_per_sm : (tile_rows == 64 ? 4 : 2);

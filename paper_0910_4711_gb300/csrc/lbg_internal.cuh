@@ -338,7 +338,7 @@ struct BatchPass {
     int S, L, Lp, NMAXB;
     const int32_t *pre_prep, *pre_hist, *pre_scan, *pre_cellsum, *pre_split, *pre_copy;
     int32_t tot_prep, tot_hist, tot_scan, tot_cellsum, tot_split, tot_copy;
-    const int64_t *pre_tiles;   // row tiles of BM rows
+    const int64_t *pre_tiles;   // row tiles of 64 rows (each CTA runs two at a time)
     int64_t ntiles;
     int *counter;               // assignment work items taken
     unsigned *bar;              // [0] arrivals, [1] generation, [2] abort (zero before the first pass)
