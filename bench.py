@@ -682,7 +682,37 @@ def grad_leg(lbg, synth, torch, stream, flush, args, dist, with_oracle=True):
     fwd = max_over_ranks(dist, statistics.median(fw))
     bwd = max_over_ranks(dist, statistics.median(bw))
     bytes_bwd = 3 * Mg * Lg * 4 + 2 * Mg * 4 + 2 * Ng * Lg * 4
-    full = {"gpu_fp32_s": gpu_lbg_s, "gpu_passes": tr.n_passes, "gpu_D": tr.D}
+    # the mixture's real values on the tensor cores (two BF16 pieces per x, L = 32) against
+    # the FP32 form: enqueue-only encodes of the designed codebook, the same cells expected
+    encode, ref_idx = {}, None
+    buf = lbg.step_result_buffer()
+    for prec in ("fp32", "bf16"):
+        out_idx = torch.empty(Mg, dtype=torch.int32, device="cuda")
+        for _ in range(3):
+            lbg.vq_encode(Xg, Cg, idx_out=out_idx, precision=prec)
+        ts = []
+        for _ in range(max(3, args.steps)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lbg.vq_encode(Xg, Cg, idx_out=out_idx, precision=prec, result_out=buf)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        Dp, nex, status = lbg.read_step_result(buf)
+        ms = max_over_ranks(dist, statistics.median(ts))
+        encode[prec] = {"ms": ms, "evals_per_s": Mg * Ng / (ms / 1e3), "exact_rows": nex, "D": Dp,
+                        "status": status}
+        if ref_idx is None:
+            ref_idx = out_idx.clone()
+        else:
+            encode[prec]["rows_differing_from_fp32"] = int((out_idx != ref_idx).sum().item())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    trb = lbg.lbg_train(Xg, Ng, delta=0.01, theta=1e-3, precision="bf16")
+    torch.cuda.synchronize()
+    full = {"gpu_fp32_s": gpu_lbg_s, "gpu_passes": tr.n_passes, "gpu_D": tr.D,
+            "gpu_bf16_s": time.perf_counter() - t0, "gpu_bf16_passes": trb.n_passes, "gpu_bf16_D": trb.D}
     if with_oracle:
         try:
             import oracle
@@ -699,6 +729,7 @@ def grad_leg(lbg, synth, torch, stream, flush, args, dist, with_oracle=True):
     return {"workload": "gmm262144_l32_n512: 262144 Gaussian-mixture vectors, L=32, 512 components "
                         "(sigma 0.1, means U[0,1]^32), codebook from LBG to N=512",
             "full_lbg": full,
+            "encode": encode,
             "forward_ms": fwd, "backward_ms": bwd, "D": D,
             "backward_gbs": bytes_bwd / (bwd / 1e3) / 1e9,
             "backward_bytes": bytes_bwd,
