@@ -28,14 +28,22 @@ constexpr int EX_THREADS = 256;
 // stores.
 constexpr int PREP_TILE = 32;
 
+// Shared memory of body_prep (static in its own kernels, in the phase buffer of
+// the persistent batched pass).
+struct PrepSmem {
+    float orig[PREP_TILE][LMAX + 1];
+    float cen[PREP_TILE][LMAX + 1];
+    double sqs[PREP_TILE];
+};
+
 __device__ __forceinline__ void body_prep(const float *__restrict__ C, int N, int L, int Lp,
                                           const float *__restrict__ mu, float *__restrict__ Cp,
                                           float *__restrict__ kn, float *__restrict__ CT,
-                                          DevState *st, int blk)
+                                          DevState *st, int blk, PrepSmem &ps)
 {
-    __shared__ float orig[PREP_TILE][LMAX + 1];
-    __shared__ float cen[PREP_TILE][LMAX + 1];
-    __shared__ double sqs[PREP_TILE];
+    auto &orig = ps.orig;
+    auto &cen = ps.cen;
+    auto &sqs = ps.sqs;
     const int npad = round_up(N, BN);
     const int n0 = blk * PREP_TILE;
     if (n0 >= npad) return;

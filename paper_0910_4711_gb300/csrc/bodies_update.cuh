@@ -385,10 +385,10 @@ template <int G>
 __device__ __forceinline__ void body_cellsum_v4(const float *__restrict__ X, int64_t M,
                                                 const int32_t *__restrict__ perm,
                                                 const int32_t *__restrict__ off, int N, int64_t S,
-                                                float *__restrict__ pieces, int blk)
+                                                float *__restrict__ pieces, int blk, int64_t qw = -1)
 {
     constexpr int L = 4 * G;
-    const int64_t q = (int64_t)blk * 8 + (threadIdx.x >> 5);
+    const int64_t q = qw >= 0 ? qw : (int64_t)blk * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const int64_t p0 = q * S;
     if (p0 >= M) return;
@@ -418,9 +418,9 @@ __device__ __forceinline__ void body_cellsum_v4(const float *__restrict__ X, int
 __device__ __forceinline__ void body_cellsum_any(const float *__restrict__ X, int64_t M, int L,
                                                  const int32_t *__restrict__ perm,
                                                  const int32_t *__restrict__ off, int N, int64_t S,
-                                                 float *__restrict__ pieces, int blk)
+                                                 float *__restrict__ pieces, int blk, int64_t qw = -1)
 {
-    const int64_t q = (int64_t)blk * 8 + (threadIdx.x >> 5);
+    const int64_t q = qw >= 0 ? qw : (int64_t)blk * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const int64_t p0 = q * S;
     if (p0 >= M) return;
@@ -556,13 +556,16 @@ __device__ __forceinline__ void body_split(const float *__restrict__ C_cur, floa
     C_alt[(2 * c + 1) * L + l] = (float)(mult ? v * (1.0 - delta) : v - delta);
 }
 
+// n_cur: the stage size before the split (the state's, unless the caller holds
+// it from before a concurrent stage advance).
 __device__ __forceinline__ void body_copy_split(const float *__restrict__ C_alt,
                                                 float *__restrict__ C_cur, int L, DevState *st,
-                                                int blk)
+                                                int blk, int n_cur = -1)
 {
     if (st->finished || st->action != ACT_SPLIT) return;
+    const int64_t n = n_cur >= 0 ? n_cur : st->n_cur;
     const int64_t i = (int64_t)blk * blockDim.x + threadIdx.x;
-    if (i < 2 * (int64_t)st->n_cur * L) C_cur[i] = C_alt[i];
+    if (i < 2 * n * L) C_cur[i] = C_alt[i];
 }
 
 // End of a training pass: a split doubles the stage size and resets the

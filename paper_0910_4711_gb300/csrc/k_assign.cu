@@ -102,7 +102,8 @@ __global__ void __launch_bounds__(256)
 {
     if (st->finished) return;
     (void)NP;
-    body_prep(C, cur_n(n_dev, n_host), L, Lp, mu, Cp, kn, CT, st, blockIdx.x);
+    __shared__ PrepSmem ps;
+    body_prep(C, cur_n(n_dev, n_host), L, Lp, mu, Cp, kn, CT, st, blockIdx.x, ps);
 }
 
 __global__ void __launch_bounds__(ASSIGN_THREADS, 2)
@@ -480,7 +481,8 @@ __global__ void __launch_bounds__(256) kb_prep(const BatchSet *__restrict__ sets
     const int b = blockIdx.x - pre[s];
     const BatchSet &q = sets[s];
     if (q.st->finished) return;
-    body_prep(q.C, q.st->n_cur, L, Lp, q.mu, q.Cp, q.kn, q.CT, q.st, b);
+    __shared__ PrepSmem ps;
+    body_prep(q.C, q.st->n_cur, L, Lp, q.mu, q.Cp, q.kn, q.CT, q.st, b, ps);
 }
 
 __global__ void kb_reset(const BatchSet *__restrict__ sets, int S, int *counter)

@@ -10,24 +10,25 @@
 // grid (the cell table needs every row's cell, the offsets every cell's
 // count, ...), so they are separated by grid-wide barriers inside one
 // cooperative launch (all CTAs resident), instead of one launch per phase:
-//   0  reset: assignment work counter, per-problem max ||c~||
 //   1  codebook preparation (per problem, 32-codevector blocks)
 //   2  nearest codevector: each half of a CTA (128 threads, its own named
 //      barrier and shared buffers) takes (problem, 64-row tile) items from a
 //      counter
 //   3  exact re-scoring of the uncertified rows (groups of 8 rows, all problems)
-//   4  per-chunk cell counts and distortion partials; the last block of a
-//      problem runs its stop test (sum in chunk order, (D_prev - D)/D <= theta)
-//   5  per-cell prefix over chunks; the last block of a problem computes its
-//      cell offsets and the cell of every warp piece
+//   4  per-chunk cell counts and distortion partials
+//   5  each problem's stop test (sum in chunk order, (D_prev - D)/D <= theta;
+//      problem s in CTA s mod grid) and the per-cell prefixes over chunks
+//   5b each problem's cell offsets
 //   6  stable placement of the rows by cell
-//   7  cell sums with the centroid division folded in (in place)
-//   8  split of a finished stage into the spare codebook
-//   9  copy back; the last block of a problem advances its stage
+//   7  per-warp piece sums of the cells
+//   8  centroids, one thread per value (in place), and the split of a
+//      finished stage into the spare codebook
+//   9  copy back, each problem's stage advance, and the next pass's resets
 // A phase's blocks are virtual: CTA b takes blocks b, b + grid, ... of the
 // launch-per-phase form and runs the same device body on each, so the bits
-// are those of lbg_train.  "Last block of a problem" is a per-problem counter
-// in its device state, reset by the block that finishes it.
+// are those of lbg_train.  The per-problem steps (5's stop test, 5b, 9's advance) run in
+// one CTA each, after a grid barrier, instead of in whichever block of the
+// problem finishes last (a fence and an atomic per block).
 //
 // Every barrier wait is bounded (%globaltimer, 2 s): a CTA that gives up sets
 // the shared abort word and reports LBG_ERR_TIMEOUT in every problem's state;
@@ -147,30 +148,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, const BatchSet *sets
     return s_ok != 0;
 }
 
-// True in the one CTA whose arrival completes `count` arrivals on the
-// problem's counter (which it resets); every CTA's earlier writes are visible
-// to it.
-__device__ __forceinline__ bool last_block(DevState *st, unsigned count)
-{
-    __shared__ int s_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        s_last = atomicAdd(&st->done_ctr, 1u) == count - 1;
-        if (s_last) st->done_ctr = 0u;
-    }
-    __syncthreads();
-    if (s_last) __threadfence();
-    return s_last != 0;
-}
-
 __device__ __forceinline__ void abort_all(unsigned *bar) { atomicExch(bar + 2, 1u); }
-
-template <int G>
-__device__ __forceinline__ void cellsum_phase(const BatchSet &q, int N, int64_t w)
-{
-    body_cellsum_c<G>(q.X, q.M, q.perm, q.off, q.qcell, N, q.S, q.pieces, q.cell_done, q.C, w);
-}
 
 __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
 {
@@ -184,7 +162,9 @@ __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
     int *tab = reinterpret_cast<int *>(reinterpret_cast<char *>(dsm) + a.phase_smem);
     const PassTables T{tab, tab + S, tab + 2 * S};
 
-    // 0: reset; the shared-memory barriers of the assignment and exact phases
+    // 0: the shared-memory barriers of the assignment and exact phases (the work counter
+    // and the problems' max ||c~|| were zeroed at the end of the previous pass, or by the
+    // host before the first)
     if (tid == 0) {
         for (int h = 0; h < 2; ++h) {
             mbar_init(&ash[h].bar[0], 1);
@@ -195,11 +175,6 @@ __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
     }
     __syncthreads();
     exact_init(esh);
-    if (blockIdx.x == 0) {
-        if (tid == 0) *a.counter = 0;
-        for (int s = tid; s < S; s += BP_THREADS) sets[s].st->cmax_bits = 0u;
-    }
-    if (!grid_barrier(a.bar, sets, S)) return;
 
     // 1: codebook preparation
     load_states(sets, S, T);
@@ -207,7 +182,8 @@ __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
         const int s = find_set(a.pre_prep, S, vb);
         const BatchSet &q = sets[s];
         if (T.run[s] & 1)
-            body_prep(q.C, T.ncur[s], a.L, a.Lp, q.mu, q.Cp, q.kn, q.CT, q.st, vb - a.pre_prep[s]);
+            body_prep(q.C, T.ncur[s], a.L, a.Lp, q.mu, q.Cp, q.kn, q.CT, q.st, vb - a.pre_prep[s],
+                      *reinterpret_cast<PrepSmem *>(dsm));
         __syncthreads();
     }
     if (!grid_barrier(a.bar, sets, S)) return;
@@ -271,32 +247,37 @@ __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
     }
     if (!grid_barrier(a.bar, sets, S)) return;
 
-    // 4: cell counts and distortion partials per chunk; the stop test
+    // 4: cell counts and distortion partials per chunk
     for (int vb = blockIdx.x; vb < a.tot_hist; vb += grid) {
         const int s = find_set(a.pre_hist, S, vb);
         const BatchSet &q = sets[s];
-        if (T.run[s] & 1) {
+        if (T.run[s] & 1)
             body_hist(q.assign, q.e, q.M, q.R, T.ncur[s], 1, q.table, q.dpart, q.st, vb - a.pre_hist[s]);
-            if (last_block(q.st, (unsigned)(a.pre_hist[s + 1] - a.pre_hist[s])))
-                body_ctl(q.dpart, q.CH, q.st, MODE_TRAIN, a.theta, a.max_passes, q.N, nullptr, 0);
-        }
         __syncthreads();
     }
     if (!grid_barrier(a.bar, sets, S)) return;
 
-    // 5: cell sizes and chunk prefixes; offsets and piece cells
-    load_states(sets, S, T);   // the stop tests of phase 4
+    // 4b + 5: each problem's stop test (one warp; problem s in CTA s mod grid) and the
+    // per-cell prefixes over chunks of every running problem; the two do not depend on each
+    // other (the prefixes are used only by an update, which the next phases gate)
+    for (int s = blockIdx.x; s < S; s += grid) {
+        const BatchSet &q = sets[s];
+        if (T.run[s] & 1) body_ctl(q.dpart, q.CH, q.st, MODE_TRAIN, a.theta, a.max_passes, q.N, nullptr, 0);
+    }
     for (int vb = blockIdx.x; vb < a.tot_scan; vb += grid) {
         const int s = find_set(a.pre_scan, S, vb);
         const BatchSet &q = sets[s];
+        if (T.run[s] & 1) body_scan<BP_THREADS / 32>(q.table, q.CH, T.ncur[s], q.counts, vb - a.pre_scan[s]);
+        __syncthreads();
+    }
+    if (!grid_barrier(a.bar, sets, S)) return;
+
+    // 5b: each problem's cell offsets (problem s in CTA s mod grid)
+    load_states(sets, S, T);   // the stop tests of phase 4b
+    for (int s = blockIdx.x; s < S; s += grid) {
+        const BatchSet &q = sets[s];
         if (T.run[s] & 1) {
-            const int N = T.ncur[s];
-            body_scan<BP_THREADS / 32>(q.table, q.CH, N, q.counts, vb - a.pre_scan[s]);
-            if (last_block(q.st, (unsigned)(a.pre_scan[s + 1] - a.pre_scan[s]))) {
-                body_offsets<BP_THREADS>(q.counts, N, q.off);
-                __syncthreads();
-                body_piece_cells(q.off, N, q.S, a.L, q.qcell, q.cell_done, false, q.C, q.C);
-            }
+            body_offsets<BP_THREADS>(q.counts, T.ncur[s], q.off);
         }
         __syncthreads();
     }
@@ -312,9 +293,9 @@ __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
     }
     if (!grid_barrier(a.bar, sets, S)) return;
 
-    // 7: cell sums and centroids (in place; an empty cell keeps its codevector).  The
-    // bodies are per warp and use no shared memory: warps take the pieces one by one
-    // (piece w of the launch-per-phase form's block w / 8), with no block-wide step.
+    // 7: per-warp piece sums of the cells (the bodies are per warp and use no shared
+    // memory: warps take the pieces one by one, piece w of the launch-per-phase form's
+    // block w / 8, with no block-wide step)
     {
         constexpr int WPB = BP_THREADS / 32;
         const int64_t nw = (int64_t)grid * WPB, tot = (int64_t)a.tot_cellsum * WPB;
@@ -324,23 +305,32 @@ __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
             const BatchSet &q = sets[s];
             const int64_t qq = (int64_t)(vb - a.pre_cellsum[s]) * WPB + (w % WPB);
             if (T.run[s] & 2) {
+                const int N = T.ncur[s];
                 switch (a.vec ? a.L : 0) {
-                case 4: cellsum_phase<1>(q, T.ncur[s], qq); break;
-                case 8: cellsum_phase<2>(q, T.ncur[s], qq); break;
-                case 16: cellsum_phase<4>(q, T.ncur[s], qq); break;
-                case 32: cellsum_phase<8>(q, T.ncur[s], qq); break;
-                case 64: cellsum_phase<16>(q, T.ncur[s], qq); break;
-                case 128: cellsum_phase<32>(q, T.ncur[s], qq); break;
-                default:
-                    body_cellsum_c_any(q.X, q.M, a.L, q.perm, q.off, q.qcell, T.ncur[s], q.S, q.pieces,
-                                       q.cell_done, q.C, qq);
+                case 4: body_cellsum_v4<1>(q.X, q.M, q.perm, q.off, N, q.S, q.pieces, 0, qq); break;
+                case 8: body_cellsum_v4<2>(q.X, q.M, q.perm, q.off, N, q.S, q.pieces, 0, qq); break;
+                case 16: body_cellsum_v4<4>(q.X, q.M, q.perm, q.off, N, q.S, q.pieces, 0, qq); break;
+                case 32: body_cellsum_v4<8>(q.X, q.M, q.perm, q.off, N, q.S, q.pieces, 0, qq); break;
+                case 64: body_cellsum_v4<16>(q.X, q.M, q.perm, q.off, N, q.S, q.pieces, 0, qq); break;
+                case 128: body_cellsum_v4<32>(q.X, q.M, q.perm, q.off, N, q.S, q.pieces, 0, qq); break;
+                default: body_cellsum_any(q.X, q.M, a.L, q.perm, q.off, N, q.S, q.pieces, 0, qq);
                 }
             }
         }
     }
     if (!grid_barrier(a.bar, sets, S)) return;
 
-    // 8: split of a finished stage
+    // 7b + 8: centroids of the updating problems, one thread per value (the FP64 sums of
+    // the pieces in the order and levels of the fused form, divided by the counts; in
+    // place, empty cells keep theirs), and the split of the problems whose stage ended
+    // (disjoint problems: an update and a split never meet in one pass)
+    for (int vb = blockIdx.x; vb < a.tot_combine; vb += grid) {
+        const int s = find_set(a.pre_combine, S, vb);
+        const BatchSet &q = sets[s];
+        const int b = vb - a.pre_combine[s];
+        if ((T.run[s] & 2) && (int64_t)b * BP_THREADS < (int64_t)T.ncur[s] * a.L)
+            body_combine(q.pieces, q.off, T.ncur[s], a.L, q.S, q.C, q.C, b);
+    }
     for (int vb = blockIdx.x; vb < a.tot_split; vb += grid) {
         const int s = find_set(a.pre_split, S, vb);
         const BatchSet &q = sets[s];
@@ -348,13 +338,18 @@ __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
     }
     if (!grid_barrier(a.bar, sets, S)) return;
 
-    // 9: copy back; the stage advances once every block of the problem is done
+    // 9: copy back (sized by the stage size read at phase 5) and each problem's stage
+    // advance (problem s in CTA s mod grid): the copy does not read what the advance writes
     for (int vb = blockIdx.x; vb < a.tot_copy; vb += grid) {
         const int s = find_set(a.pre_copy, S, vb);
         const BatchSet &q = sets[s];
-        body_copy_split(q.Calt, q.C, a.L, q.st, vb - a.pre_copy[s]);
-        if (last_block(q.st, (unsigned)(a.pre_copy[s + 1] - a.pre_copy[s]))) body_stage(q.st);
-        __syncthreads();
+        body_copy_split(q.Calt, q.C, a.L, q.st, vb - a.pre_copy[s], T.ncur[s]);
+    }
+    for (int s = blockIdx.x; s < S; s += grid) body_stage(sets[s].st);
+    // for the next pass: the work counter and the problems' max ||c~|| (phase 1)
+    if (blockIdx.x == 0) {
+        if (tid == 0) *a.counter = 0;
+        for (int s = tid; s < S; s += BP_THREADS) sets[s].st->cmax_bits = 0u;
     }
 }
 
@@ -366,6 +361,7 @@ size_t pass_phase_smem(int L, int NMAXB)
     const size_t hist = (size_t)NMAXB * sizeof(int);
     const size_t scatter = (size_t)NMAXB * (sizeof(int) + 8);
     size_t m = assign;
+    if (sizeof(PrepSmem) > m) m = sizeof(PrepSmem);
     if (exact > m) m = exact;
     if (hist > m) m = hist;
     if (scatter > m) m = scatter;

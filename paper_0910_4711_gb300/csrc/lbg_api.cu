@@ -1146,6 +1146,7 @@ lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, 
     }
     unsigned *dbar = reinterpret_cast<unsigned *>(ws + o_bar);
     CK(cudaMemsetAsync(dbar, 0, sizeof(unsigned) * 4, c.s));
+    CK(cudaMemsetAsync(counter, 0, sizeof(int) * 4, c.s));   // the persistent pass zeroes it after each pass
     BatchPass bp = {};
     bp.sets = dsets;
     bp.S = S;
@@ -1160,6 +1161,8 @@ lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, 
     bp.tot_scan = P[1][S];
     bp.pre_cellsum = dP[3];
     bp.tot_cellsum = P[3][S];
+    bp.pre_combine = dP[4];
+    bp.tot_combine = P[4][S];
     bp.pre_split = dP[5];
     bp.tot_split = P[5][S];
     bp.pre_copy = dP[6];

@@ -336,8 +336,8 @@ void launch_b_reset(const BatchSet *sets, int S, int *counter, cudaStream_t s);
 struct BatchPass {
     const BatchSet *sets;
     int S, L, Lp, NMAXB;
-    const int32_t *pre_prep, *pre_hist, *pre_scan, *pre_cellsum, *pre_split, *pre_copy;
-    int32_t tot_prep, tot_hist, tot_scan, tot_cellsum, tot_split, tot_copy;
+    const int32_t *pre_prep, *pre_hist, *pre_scan, *pre_cellsum, *pre_combine, *pre_split, *pre_copy;
+    int32_t tot_prep, tot_hist, tot_scan, tot_cellsum, tot_combine, tot_split, tot_copy;
     const int64_t *pre_tiles;   // row tiles of 64 rows (each CTA runs two at a time)
     int64_t ntiles;
     int *counter;               // assignment work items taken
