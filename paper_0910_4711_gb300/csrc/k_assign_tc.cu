@@ -1585,9 +1585,6 @@ void launch_prep_tc(const float *C, int N_alloc, const int32_t *n_dev, int n_hos
     }
 }
 
-// Group size by codebook size: eight columns where the epilogue's ALU work is
-// what bounds the launch (short rows, LK <= 32, and many codevectors), two
-// elsewhere (the tail then scores two members instead of eight).
 // Group size of the epilogue by codebook size: larger groups cut the per-value
 // epilogue work and the flagged rows, smaller ones the tail's exact distances
 // per row.  Measured on GB300 (search + exact re-scoring, ms): image blocks
