@@ -341,42 +341,42 @@ __device__ __forceinline__ void add4(float4 &a, const float4 &b)
 // row with float4 loads (L = 4G), 32/G rows per step, four steps in flight.
 // Piece (cell n, warp q) -> pieces[(n + q) * L ...] (unique slot per piece).
 // acc += the rows pp, pp + RPG, ... < pe (RPG = 32 / G; row r = perm[.] of X,
-// this lane's float4 qd), in that order: batches of eight rows in flight per
-// lane, the next batch's perm entries loaded while the current rows are in
-// flight, and the last (fewer than eight) rows in one predicated batch.
-template <int G>
+// this lane's float4 qd), in that order: batches of B rows in flight per lane,
+// the next batch's perm entries loaded while the current rows are in flight,
+// and the last (fewer than B) rows in one predicated batch.
+template <int G, int B = 8>
 __device__ __forceinline__ void sum_rows_v4(const float4 *__restrict__ X4, const int32_t *__restrict__ perm,
                                             int64_t pp, int64_t pe, int qd, float4 &acc)
 {
     constexpr int RPG = 32 / G;
-    if (pp + 7 * RPG < pe) {
-        int r[8];
+    if (pp + (B - 1) * RPG < pe) {
+        int r[B];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) r[u] = perm[pp + u * RPG];
+        for (int u = 0; u < B; ++u) r[u] = perm[pp + u * RPG];
         for (;;) {
-            float4 v[8];
+            float4 v[B];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = __ldg(X4 + (int64_t)r[u] * G + qd);
-            pp += 8 * RPG;
-            const bool more = pp + 7 * RPG < pe;
+            for (int u = 0; u < B; ++u) v[u] = __ldg(X4 + (int64_t)r[u] * G + qd);
+            pp += B * RPG;
+            const bool more = pp + (B - 1) * RPG < pe;
             if (more)
 #pragma unroll
-                for (int u = 0; u < 8; ++u) r[u] = perm[pp + u * RPG];
+                for (int u = 0; u < B; ++u) r[u] = perm[pp + u * RPG];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) add4(acc, v[u]);
+            for (int u = 0; u < B; ++u) add4(acc, v[u]);
             if (!more) break;
         }
     }
     if (pp < pe) {
-        int r[8];
+        int r[B];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) r[u] = pp + u * RPG < pe ? perm[pp + u * RPG] : -1;
-        float4 v[8];
+        for (int u = 0; u < B; ++u) r[u] = pp + u * RPG < pe ? perm[pp + u * RPG] : -1;
+        float4 v[B];
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
+        for (int u = 0; u < B; ++u)
             v[u] = r[u] >= 0 ? __ldg(X4 + (int64_t)r[u] * G + qd) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
+        for (int u = 0; u < B; ++u)
             if (r[u] >= 0) add4(acc, v[u]);
     }
 }
