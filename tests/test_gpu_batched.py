@@ -126,3 +126,32 @@ def test_persistent_pass_multiplicative_split_and_pass_cap(lbg):
         b = lbg.lbg_train_batched(Xd, row_off, Ns, per_phase=True, **kw)
         assert a.tune["persistent"] and not b.tune["persistent"]
         assert a.status == b.status and torch.equal(a.C, b.C) and a.D == b.D, kw
+
+
+@pytest.mark.parametrize("L,real", [(5, True), (64, False), (32, True)])
+def test_persistent_pass_other_dimensions(lbg, L, real):
+    """One launch per pass, one launch per phase and lbg_train per problem agree bit for bit
+    at an odd L (scalar loads, the any-L cell sums), at L = 64 and on real values; one problem
+    has a codebook of 2 over 40,000 rows, so its cells hold hundreds of pieces (the two-level
+    combine); the final states re-anchor to the oracle."""
+    rng = np.random.default_rng(L)
+    sizes, Ns = [40000, 3000, 777, 12000], [2, 64, 16, 256]
+    if real:
+        parts = [(rng.standard_normal((M, L)) * 3.0 + k).astype(np.float32) for k, M in enumerate(sizes)]
+    else:
+        from paper_0910_4711_gb300 import synth
+        parts = [synth.blocks(synth.make_image(500 + k, 2048, 2048), 8)[:M] for k, M in enumerate(sizes)]
+    row_off = np.concatenate([[0], np.cumsum([p.shape[0] for p in parts])])
+    Xd = torch.from_numpy(np.concatenate(parts)).cuda()
+    a = lbg.lbg_train_batched(Xd, row_off, Ns)
+    b = lbg.lbg_train_batched(Xd, row_off, Ns, per_phase=True)
+    assert a.tune["persistent"] and not b.tune["persistent"]
+    assert torch.equal(a.C, b.C) and torch.equal(a.assign, b.assign) and a.D == b.D
+    A = a.assign.cpu().numpy()
+    for s, X in enumerate(parts):
+        single = lbg.lbg_train(torch.from_numpy(X).cuda(), Ns[s], 0.01, 1e-3)
+        assert torch.equal(a.codebook(s), single.C) and a.D[s] == single.D
+        C = a.codebook(s).cpu().numpy()
+        a_ref, e_ref, gap = oracle.assign(X, C.astype(np.float64))
+        check_assign(X, C, A[row_off[s]:row_off[s + 1]], a_ref, e_ref, gap)
+        check_D(a.D[s], float(e_ref.sum()))
