@@ -133,9 +133,19 @@ __device__ __forceinline__ void body_ctl(const double *__restrict__ dpart, int C
 {
     if (threadIdx.x >= 32) return;
     if (mode == MODE_TRAIN && st->finished) return;
-    // lane partials over chunks lane, lane + 32, ..., then a fixed shuffle tree
+    // lane partials over chunks lane, lane + 32, ... (all loads in flight, then added
+    // in that order), then a fixed shuffle tree
+    constexpr int PER = (HIST_CHUNKS_MAX + 31) / 32;
+    double pv[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int c = (int)threadIdx.x + 32 * u;
+        pv[u] = c < CH ? dpart[c] : 0.0;
+    }
     double D = 0.0;
-    for (int c = threadIdx.x; c < CH; c += 32) D += dpart[c];
+#pragma unroll
+    for (int u = 0; u < PER; ++u)
+        if ((int)threadIdx.x + 32 * u < CH) D += pv[u];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) D += __shfl_xor_sync(0xffffffffu, D, o);
     if (threadIdx.x != 0) return;
@@ -215,17 +225,33 @@ __device__ __forceinline__ void body_scan(int32_t *__restrict__ table, int CH, i
 }
 
 // One CTA of NT threads: off[n] = sum_{n' < n} counts[n'], off[N] = total.
-template <int NT = 1024>
+// Thread t takes the cells [t per, (t + 1) per); with per <= OFF_REG their
+// counts stay in registers (all loads in flight).  `cell(n, a, b)` is then
+// called for each of the thread's cells with its rows [a, b) = [off[n], off[n+1]).
+constexpr int OFF_REG = 8;
+struct NoCell {
+    __device__ void operator()(int, int64_t, int64_t) const {}
+};
+template <int NT = 1024, class Cell = NoCell>
 __device__ __forceinline__ void body_offsets(const int32_t *__restrict__ counts, int N,
-                                             int32_t *__restrict__ off)
+                                             int32_t *__restrict__ off, Cell cell = Cell())
 {
     static_assert(NT % 32 == 0 && NT <= 1024, "whole warps");
     __shared__ int wsum[32];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int per = (N + NT - 1) / NT;
     const int a = t * per, b = a + per < N ? a + per : N;
+    const bool in_reg = per <= OFF_REG;
+    int cv[OFF_REG];
     int loc = 0;
-    for (int i = a; i < b; ++i) loc += counts[i];
+    if (in_reg) {
+#pragma unroll
+        for (int u = 0; u < OFF_REG; ++u) cv[u] = a + u < b ? counts[a + u] : 0;
+#pragma unroll
+        for (int u = 0; u < OFF_REG; ++u) loc += cv[u];
+    } else {
+        for (int i = a; i < b; ++i) loc += counts[i];
+    }
     int inc = loc;
     for (int o = 1; o < 32; o <<= 1) {
         const int v = __shfl_up_sync(0xffffffffu, inc, o);
@@ -243,9 +269,21 @@ __device__ __forceinline__ void body_offsets(const int32_t *__restrict__ counts,
     }
     __syncthreads();
     int run = inc - loc + (w > 0 ? wsum[w - 1] : 0);
-    for (int i = a; i < b; ++i) {
-        off[i] = run;
-        run += counts[i];
+    if (in_reg) {
+#pragma unroll
+        for (int u = 0; u < OFF_REG; ++u)
+            if (a + u < b) {
+                off[a + u] = run;
+                cell(a + u, run, run + cv[u]);
+                run += cv[u];
+            }
+    } else {
+        for (int i = a; i < b; ++i) {
+            const int c = counts[i];
+            off[i] = run;
+            cell(i, run, run + c);
+            run += c;
+        }
     }
     if (t == NT - 1) off[N] = run;
 }
@@ -283,7 +321,19 @@ __device__ __forceinline__ void body_scatter(const int32_t *__restrict__ assign,
     unsigned char *wcnt = reinterpret_cast<unsigned char *>(sm + N);  // [8][N]
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int64_t m0 = (int64_t)blk * R, m1 = m0 + R < M ? m0 + R : M;
-    for (int n = tid; n < N; n += 256) run[n] = off[n] + table[(size_t)blk * N + n];
+    // run[] in rounds of eight cells per thread, every load of a round in flight
+    for (int n0 = tid; n0 < N; n0 += 8 * 256) {
+        int o[8], c[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int n = n0 + 256 * u;
+            o[u] = n < N ? off[n] : 0;
+            c[u] = n < N ? table[(size_t)blk * N + n] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (n0 + 256 * u < N) run[n0 + 256 * u] = o[u] + c[u];
+    }
     for (int i = tid; i < 2 * N; i += 256) reinterpret_cast<int *>(wcnt)[i] = 0;
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
@@ -687,27 +737,32 @@ __device__ __forceinline__ void body_cellsum_c(const float *__restrict__ X, int6
     }
 }
 
-// After the cell offsets: qcell[q] = the cell n holding row position q S
-// (off[n] <= q S < off[n+1]), the per-cell piece counters zeroed, and, when
-// `copy`, every empty cell's codevector copied from C_in to C_out.  One CTA.
-__device__ __forceinline__ void body_piece_cells(const int32_t *__restrict__ off, int N, int64_t S, int L,
-                                                 int32_t *__restrict__ qcell, int32_t *__restrict__ cell_done,
-                                                 bool copy, const float *C_in, float *C_out)
-{
-    for (int n = threadIdx.x; n < N; n += blockDim.x) {
-        const int64_t a = off[n], b = off[n + 1];
+// Per cell, given its rows [a, b) after the offsets (the `cell` step of
+// body_offsets): qcell[q] = n for every piece q whose first row position q S
+// lies in the cell (off[n] <= q S < off[n+1]), the cell's piece counters
+// zeroed, and, when `copy`, an empty cell's codevector copied from C_in to C_out.
+struct PieceCells {
+    int N;
+    int64_t S;
+    int L;
+    int32_t *qcell, *cell_done;
+    bool copy;
+    const float *C_in;
+    float *C_out;
+    __device__ __forceinline__ void operator()(int n, int64_t a, int64_t b) const
+    {
         cell_done[n] = 0;
         if (b == a) {
             if (copy)
                 for (int l = 0; l < L; ++l) C_out[(int64_t)n * L + l] = C_in[(int64_t)n * L + l];
-            continue;
+            return;
         }
         for (int64_t q = (a + S - 1) / S; q * S < b; ++q) qcell[q] = n;
         const int64_t q0 = a / S, q1 = (b - 1) / S;   // group counters of a large cell
         if (combine_groups(q0, q1) > 1)
             for (int64_t g = q0; g <= q1; g += COMBINE_GROUP) cell_done[N + n + g] = 0;
     }
-}
+};
 
 // Any L: the cell sums of body_cellsum_any (lanes own dims l = lane, lane + 32,
 // ...; rows in order) with the pieces finished as in finish_piece_v4.

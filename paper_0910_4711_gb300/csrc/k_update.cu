@@ -123,10 +123,11 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------- fused update (step, train)
 // k_scan_offsets_q: per cell, the exclusive prefix of its chunk counts and the
 // cell size (body_scan); its last CTA then computes the cell offsets
-// (body_offsets) and, for the centroid kernel below, the cell holding the first
-// row of every warp piece (qcell[q] = the cell n with off[n] <= q S < off[n+1]),
-// zeroes the per-cell piece counters and copies the codevector of every empty
-// cell to C_out (an empty cell keeps its codevector) when C_out is not C_in.
+// (body_offsets) and, in the same pass over each thread's cells, for the centroid
+// kernel below, the cell holding the first row of every warp piece (qcell[q] =
+// the cell n with off[n] <= q S < off[n+1]), zeroes the per-cell piece counters
+// and copies the codevector of every empty cell to C_out (an empty cell keeps
+// its codevector) when C_out is not C_in (PieceCells).
 __global__ void __launch_bounds__(1024)
     k_scan_offsets_q(int32_t *__restrict__ table, int CH, const int32_t *n_dev, int n_host,
                      int32_t *__restrict__ counts, int32_t *__restrict__ off, int32_t *__restrict__ qcell,
@@ -138,9 +139,8 @@ __global__ void __launch_bounds__(1024)
     if ((int)blockIdx.x * 32 < N) body_scan(table, CH, N, counts, blockIdx.x);
     if (!last_cta(st)) return;
     if (threadIdx.x == 0) st->done_ctr = 0u;
-    body_offsets(counts, N, off);
-    __syncthreads();   // off[] complete (this CTA wrote it)
-    body_piece_cells(off, N, S, L, qcell, cell_done, C_out != C_in && !skip_update(st, train), C_in, C_out);
+    body_offsets(counts, N, off,
+                 PieceCells{N, S, L, qcell, cell_done, C_out != C_in && !skip_update(st, train), C_in, C_out});
 }
 
 template <int G>

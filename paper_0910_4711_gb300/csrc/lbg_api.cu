@@ -318,50 +318,94 @@ void run_assign(const Call &c, const Plan &p, const float *X, const float *C, co
 // from host memory) overlaps the search.  A piece is one wave of the search
 // (SMs x 256 rows; the FP32 kernel's wave, 2 x SMs x 128 rows, is the
 // same), so that each piece's search keeps pace with the next piece's copy
-// (measured ~210 GB/s host-to-device); at most HOST_CHUNKS pieces.  Returns
-// false if a CUDA call failed.
+// (measured ~210 GB/s host-to-device); at most HOST_CHUNKS pieces.  Every
+// piece's copy is issued at the start of the call, right after the codebook's,
+// before any kernel, so that the link is busy from the start.
 constexpr int HOST_CHUNKS = 32;
+constexpr int EV_BEGIN = HOST_CHUNKS, EV_RESULT = HOST_CHUNKS + 1, EV_D2H = HOST_CHUNKS + 2;
 int64_t host_piece_rows() { return (int64_t)num_sms() * 256; }
 cudaStream_t g_copy[MAX_DEVICES];
-cudaEvent_t g_copy_ev[MAX_DEVICES][HOST_CHUNKS + 1];
+cudaEvent_t g_copy_ev[MAX_DEVICES][HOST_CHUNKS + 3];
+
+bool ensure_copy_stream(int d)
+{
+    if (g_copy[d]) return true;
+    if (cudaStreamCreateWithFlags(&g_copy[d], cudaStreamNonBlocking) != cudaSuccess) return false;
+    for (auto &e : g_copy_ev[d])
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
+    return true;
+}
+
+// Piece k of np: rows [r0, r1), in whole 256-row tiles.
+int host_pieces(const Plan &p)
+{
+    const int64_t piece = host_piece_rows();
+    const int64_t np = (p.M + piece - 1) / piece;
+    return (int)(np > HOST_CHUNKS ? HOST_CHUNKS : np);
+}
+void host_piece(const Plan &p, int k, int np, int64_t &r0, int64_t &r1)
+{
+    const int64_t tiles = (p.M + 255) / 256;
+    r0 = std::min<int64_t>(p.M, tiles * k / np * 256);
+    r1 = std::min<int64_t>(p.M, tiles * (k + 1) / np * 256);
+}
 
 // The copies may start once everything issued so far on c.s (earlier users of
-// Xs) is done: called at the start of the call's device work, so that they
-// overlap the codebook preparation too.
+// Xs) is done: host_copy_begin records that point.  The call then issues its
+// codebook's copy (small) and host_copy_pieces every piece's copy, each
+// recording its event: copies are served in the order they are issued, so the
+// codebook's copy goes first rather than behind the whole of X.
 bool host_copy_begin(const Call &c)
 {
     const int d = c.dev;
-    if (!g_copy[d]) {
-        if (cudaStreamCreateWithFlags(&g_copy[d], cudaStreamNonBlocking) != cudaSuccess) return false;
-        for (auto &e : g_copy_ev[d])
-            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
-    }
-    return cudaEventRecord(g_copy_ev[d][HOST_CHUNKS], c.s) == cudaSuccess &&
-           cudaStreamWaitEvent(g_copy[d], g_copy_ev[d][HOST_CHUNKS], 0) == cudaSuccess;
+    return ensure_copy_stream(d) && cudaEventRecord(g_copy_ev[d][EV_BEGIN], c.s) == cudaSuccess &&
+           cudaStreamWaitEvent(g_copy[d], g_copy_ev[d][EV_BEGIN], 0) == cudaSuccess;
 }
-
-bool run_assign_host(const Call &c, const Plan &p, const float *hostX, float *Xs, const float *C,
-                     const int32_t *n_dev, int n_host, const float *mu, DevState *st, int32_t *assign,
-                     int expire = 0)
+bool host_copy_pieces(const Call &c, const Plan &p, const float *hostX, float *Xs)
 {
     const int d = c.dev;
-    // pieces in whole 256-row tiles
-    const int64_t tiles = (p.M + 255) / 256;
-    const int64_t piece = host_piece_rows();
-    int64_t np = (p.M + piece - 1) / piece;
-    if (np > HOST_CHUNKS) np = HOST_CHUNKS;
+    const int np = host_pieces(p);
     for (int k = 0; k < np; ++k) {
-        const int64_t r0 = std::min<int64_t>(p.M, tiles * k / np * 256);
-        const int64_t r1 = std::min<int64_t>(p.M, tiles * (k + 1) / np * 256);
+        int64_t r0, r1;
+        host_piece(p, k, np, r0, r1);
         if (r1 <= r0) continue;
         const size_t off = (size_t)r0 * p.L, bytes = sizeof(float) * (size_t)(r1 - r0) * p.L;
         if (cudaMemcpyAsync(Xs + off, hostX + off, bytes, cudaMemcpyHostToDevice, g_copy[d]) != cudaSuccess ||
-            cudaEventRecord(g_copy_ev[d][k], g_copy[d]) != cudaSuccess ||
-            cudaStreamWaitEvent(c.s, g_copy_ev[d][k], 0) != cudaSuccess)
+            cudaEventRecord(g_copy_ev[d][k], g_copy[d]) != cudaSuccess)
             return false;
+    }
+    return true;
+}
+
+// The search of each piece once its copy (host_copy_pieces) has landed.
+bool run_assign_host(const Call &c, const Plan &p, float *Xs, const float *C, const int32_t *n_dev, int n_host,
+                     const float *mu, DevState *st, int32_t *assign, int expire = 0)
+{
+    const int d = c.dev;
+    const int np = host_pieces(p);
+    for (int k = 0; k < np; ++k) {
+        int64_t r0, r1;
+        host_piece(p, k, np, r0, r1);
+        if (r1 <= r0) continue;
+        if (cudaStreamWaitEvent(c.s, g_copy_ev[d][k], 0) != cudaSuccess) return false;
         run_assign(c, p, Xs, C, n_dev, n_host, mu, st, assign, r0, r1, expire);
     }
     return true;
+}
+
+// A result that is final at this point of c.s goes to the host on the copy
+// stream while c.s carries on; host_d2h_join makes c.s wait for it.
+bool host_d2h_after(const Call &c, void *dst, const void *src, size_t bytes)
+{
+    const int d = c.dev;
+    return ensure_copy_stream(d) && cudaEventRecord(g_copy_ev[d][EV_RESULT], c.s) == cudaSuccess &&
+           cudaStreamWaitEvent(g_copy[d], g_copy_ev[d][EV_RESULT], 0) == cudaSuccess &&
+           cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, g_copy[d]) == cudaSuccess &&
+           cudaEventRecord(g_copy_ev[d][EV_D2H], g_copy[d]) == cudaSuccess;
+}
+bool host_d2h_join(const Call &c)
+{
+    return cudaStreamWaitEvent(c.s, g_copy_ev[c.dev][EV_D2H], 0) == cudaSuccess;
 }
 
 void run_exact(const Call &c, const Plan &p, const float *X, const int32_t *n_dev, int n_host,
@@ -664,7 +708,12 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
     p.grp = o.tc_group;
     if ((rc = ensure_workspace(c, p.total)) != LBG_OK) return rc;
     DevState *st = c.at<DevState>(p.state);
-    // host X: copied piece by piece inside the assignment step (run_assign_host)
+    // host X: every piece's copy is issued up front (after C's); the search takes the
+    // pieces as they land
+    if (wX == 0 && !host_copy_begin(c)) {
+        (void)cudaGetLastError();
+        return LBG_ERR_CUDA;
+    }
     const float *dX = wX == 0 ? c.at<float>(p.Xs) : X;
     const float *dC = C;
     if (wC == 0) {
@@ -672,9 +721,15 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
                            cudaMemcpyHostToDevice, c.s));
         dC = c.at<float>(p.Cin);
     }
+    if (wX == 0 && !host_copy_pieces(c, p, X, c.at<float>(p.Xs))) {
+        (void)cudaGetLastError();
+        return LBG_ERR_CUDA;
+    }
     int32_t *dI = wI ? idx : c.at<int32_t>(p.assign);
     float *dH = Xhat ? (wH ? Xhat : c.at<float>(p.Xhat)) : nullptr;
     const bool wantD = D || res;
+    // host X and idx (always issued directly): idx goes back while the distortion is summed
+    const bool d2h_early = wX == 0 && wI == 0;
     bool host_ok = true;
     Timer tm;
     if ((rc = tm.init(o.phase_ms != nullptr)) != LBG_OK) return rc;
@@ -682,13 +737,12 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
     auto issue = [&](cudaStream_t s) {
         Call k = c;
         k.s = s;
-        if (wX == 0 && !host_copy_begin(k)) host_ok = false;
         tm.mark(0, s);
         launch_begin(dC, N, L, mu, p.tc, st, s);   // also the initial state (cmax, rho zero)
         run_prepare(k, p, dC, nullptr, N, mu, st, false);
         tm.mark(1, s);
         if (wX == 0) {
-            if (!run_assign_host(k, p, X, c.at<float>(p.Xs), dC, nullptr, N, mu, st, dI, o.test_expire_wait))
+            if (!run_assign_host(k, p, c.at<float>(p.Xs), dC, nullptr, N, mu, st, dI, o.test_expire_wait))
                 host_ok = false;
         } else {
             run_assign(k, p, dX, dC, nullptr, N, mu, st, dI, 0, -1, o.test_expire_wait);
@@ -696,6 +750,7 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
         tm.mark(2, s);
         run_exact(k, p, dX, nullptr, N, st, dI);
         tm.mark(3, s);
+        if (d2h_early && !host_d2h_after(k, idx, dI, sizeof(int32_t) * M)) host_ok = false;
         if (wantD) launch_hist_ctl(dI, k.at<float>(p.e), M, p.R, p.CH, N, false, nullptr, k.at<double>(p.dpart), st, s);
         if (dH) launch_decode(dI, M, L, dC, dH, s);
         if (res) LBG_COUNTED k_step_report<<<1, 1, 0, s>>>(st, res, 1);
@@ -711,7 +766,8 @@ lbg_status vq_encode(const float *X, int64_t M, int32_t L, const float *C, int32
         if ((rc = seq_run(c, key, issue)) != LBG_OK) return rc;
     }
     if (res) return end_async(c);
-    if (wI == 0) CK(cudaMemcpyAsync(idx, dI, sizeof(int32_t) * M, cudaMemcpyDeviceToHost, c.s));
+    if (d2h_early && !host_d2h_join(c)) return LBG_ERR_CUDA;
+    if (wI == 0 && !d2h_early) CK(cudaMemcpyAsync(idx, dI, sizeof(int32_t) * M, cudaMemcpyDeviceToHost, c.s));
     if (Xhat && wH == 0)
         CK(cudaMemcpyAsync(Xhat, dH, sizeof(float) * M * L, cudaMemcpyDeviceToHost, c.s));
     DevState h;
@@ -762,7 +818,12 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
         return LBG_OK;
     }
     DevState *st = c.at<DevState>(p.state);
-    // host X: copied piece by piece inside the assignment step (run_assign_host)
+    // host X: every piece's copy is issued up front (after C's); the search takes the
+    // pieces as they land
+    if (wX == 0 && !host_copy_begin(c)) {
+        (void)cudaGetLastError();
+        return LBG_ERR_CUDA;
+    }
     const float *dX = wX == 0 ? c.at<float>(p.Xs) : X;
     const float *dCi = C_in;
     float *dCo = C_out;
@@ -771,7 +832,13 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
         dCi = c.at<float>(p.Cin);
         dCo = c.at<float>(p.Cout);
     }
+    if (wX == 0 && !host_copy_pieces(c, p, X, c.at<float>(p.Xs))) {
+        (void)cudaGetLastError();
+        return LBG_ERR_CUDA;
+    }
     int32_t *dA = wsA ? c.at<int32_t>(p.assign) : assign;
+    // host X and assignment (always issued directly): the assignment goes back during the update
+    const bool d2h_early = wX == 0 && assign && wA == 0 && !res;
     bool host_ok = true;
     Timer tm;
     if ((rc = tm.init(o.phase_ms != nullptr)) != LBG_OK) return rc;
@@ -779,13 +846,12 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
     auto issue = [&](cudaStream_t s) {
         Call k = c;
         k.s = s;
-        if (wX == 0 && !host_copy_begin(k)) host_ok = false;
         tm.mark(0, s);
         launch_begin(dCi, N, L, mu, p.tc, st, s);   // also the initial state (cmax, rho zero)
         run_prepare(k, p, dCi, nullptr, N, mu, st, false);
         tm.mark(1, s);
         if (wX == 0) {
-            if (!run_assign_host(k, p, X, c.at<float>(p.Xs), dCi, nullptr, N, mu, st, dA, o.test_expire_wait))
+            if (!run_assign_host(k, p, c.at<float>(p.Xs), dCi, nullptr, N, mu, st, dA, o.test_expire_wait))
                 host_ok = false;
         } else {
             run_assign(k, p, dX, dCi, nullptr, N, mu, st, dA, 0, -1, o.test_expire_wait);
@@ -793,6 +859,7 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
         tm.mark(2, s);
         run_exact(k, p, dX, nullptr, N, st, dA);
         tm.mark(3, s);
+        if (d2h_early && !host_d2h_after(k, assign, dA, sizeof(int32_t) * M)) host_ok = false;
         launch_hist_ctl(dA, k.at<float>(p.e), M, p.R, p.CH, N, true, k.at<int32_t>(p.table),
                         k.at<double>(p.dpart), st, s);
         run_update(k, p, dX, nullptr, N, st, dA, dCi, dCo, false);
@@ -812,7 +879,8 @@ lbg_status lbg_lloyd_step(const float *X, int64_t M, int32_t L, int32_t N, const
     }
     if (res) return end_async(c);
     if (hostC) CK(cudaMemcpyAsync(C_out, dCo, cbytes, cudaMemcpyDefault, c.s));
-    if (assign && wA == 0)
+    if (d2h_early && !host_d2h_join(c)) return LBG_ERR_CUDA;
+    if (assign && wA == 0 && !d2h_early)
         CK(cudaMemcpyAsync(assign, dA, sizeof(int32_t) * M, cudaMemcpyDeviceToHost, c.s));
     DevState h;
     CK(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, c.s));

@@ -76,6 +76,27 @@ def test_encode_host_buffers_match_device(lbg):
     assert rd.D == rh.D
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("b", [4, 8])
+def test_host_buffers_many_pieces_match_device(lbg, precision, b):
+    """Host X of several copy pieces (pageable numpy and pinned torch): encode and a
+    Lloyd step give the bits of the device-resident calls, the assignment included
+    (its copy back runs on the copy stream during the update)."""
+    X = image_data(13, 2048, 2048 if b == 8 else 1024, b)[:200000]
+    C = random_codebook(X, 512, 3)
+    rd = lbg.vq_encode(dev(X), dev(C), precision=precision)
+    sd = lbg.lbg_lloyd_step(dev(X), dev(C), precision=precision)
+    for Xh in (X, torch.from_numpy(X).pin_memory()):
+        rh = lbg.vq_encode(Xh, C, precision=precision)
+        np.testing.assert_array_equal(host(rd.idx), host(torch.as_tensor(rh.idx)))
+        assert rd.D == rh.D
+        Ah = torch.empty(X.shape[0], dtype=torch.int32).pin_memory()
+        sh = lbg.lbg_lloyd_step(Xh, C, assign_out=Ah, precision=precision)
+        np.testing.assert_array_equal(host(sd.assign), Ah.numpy())
+        np.testing.assert_array_equal(host(sd.C), host(torch.as_tensor(sh.C)))
+        assert sd.D == sh.D
+
+
 def test_encode_empty_input(lbg):
     r = lbg.vq_encode(dev(np.zeros((0, 16), np.float32)), dev(np.zeros((4, 16), np.float32)))
     assert r.D == 0.0 and r.idx.numel() == 0
