@@ -738,14 +738,15 @@ __device__ __forceinline__ void body_cellsum_c(const float *__restrict__ X, int6
 }
 
 // Per cell, given its rows [a, b) after the offsets (the `cell` step of
-// body_offsets): qcell[q] = n for every piece q whose first row position q S
-// lies in the cell (off[n] <= q S < off[n+1]), the cell's piece counters
-// zeroed, and, when `copy`, an empty cell's codevector copied from C_in to C_out.
+// body_offsets): the cell's piece counters zeroed and, when `copy`, an empty
+// cell's codevector copied from C_in to C_out.  (The cell of each piece is
+// found afterwards by all threads at once: one thread per large cell writing
+// thousands of entries was the longest step of a pass at small N.)
 struct PieceCells {
     int N;
     int64_t S;
     int L;
-    int32_t *qcell, *cell_done;
+    int32_t *cell_done;
     bool copy;
     const float *C_in;
     float *C_out;
@@ -757,7 +758,6 @@ struct PieceCells {
                 for (int l = 0; l < L; ++l) C_out[(int64_t)n * L + l] = C_in[(int64_t)n * L + l];
             return;
         }
-        for (int64_t q = (a + S - 1) / S; q * S < b; ++q) qcell[q] = n;
         const int64_t q0 = a / S, q1 = (b - 1) / S;   // group counters of a large cell
         if (combine_groups(q0, q1) > 1)
             for (int64_t g = q0; g <= q1; g += COMBINE_GROUP) cell_done[N + n + g] = 0;

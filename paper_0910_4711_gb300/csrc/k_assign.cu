@@ -100,10 +100,111 @@ __global__ void __launch_bounds__(256)
            const float *__restrict__ mu, float *__restrict__ Cp, float *__restrict__ kn,
            float *__restrict__ CT, int NP, DevState *st)
 {
-    if (st->finished) return;
+    if (st->finished || cur_n(n_dev, n_host) <= st->direct_max) return;
     (void)NP;
     __shared__ PrepSmem ps;
     body_prep(C, cur_n(n_dev, n_host), L, Lp, mu, Cp, kn, CT, st, blockIdx.x, ps);
+}
+
+// Small codebooks (the early stages of lbg_train, N <= DevState::direct_max):
+// every row against all N codevectors in the FP32 direct form, the sum over l
+// in index order of fl(x_l - c_l)^2 (an fmaf chain from 0), lowest index on
+// ties.  These are the values and the choice the certified search and its
+// exact re-scoring produce for every row (a certified winner beats every other
+// codevector by more than the rounding of these sums, and a flagged row is
+// re-scored this way), so the results do not depend on which kernel ran; at a
+// few codevectors the search's tiles, certificate and re-scoring cost far more
+// than this arithmetic, which reads X once.  One row per thread (x in
+// registers after a coalesced staging of the CTA's 256 rows, L <= LK,
+// L % 4 == 0), codevectors read by broadcast loads (the same address in every
+// lane), four codevectors' sums at a time.
+template <int LK>
+__global__ void __launch_bounds__(256)
+    k_assign_direct(const float *__restrict__ X, int64_t M, int L, const float *__restrict__ C,
+                    const int32_t *n_dev, int n_host, DevState *st, int32_t *__restrict__ assign,
+                    float *__restrict__ e)
+{
+    if (st->finished) return;
+    const int N = cur_n(n_dev, n_host);
+    if (N > st->direct_max) return;
+    if (blockIdx.x == 0) {   // non-finite codevectors (the preparation that checks them is skipped)
+        bool bad = false;
+        for (int i = threadIdx.x; i < N * L; i += blockDim.x) bad = bad || !isfinite(C[i]);
+        if (bad) flag_error(st, ERR_NONFINITE);
+    }
+    // the CTA's rows, staged through shared memory with coalesced loads (row
+    // stride L + 4 floats: a warp's reads of its 32 rows are conflict-free)
+    extern __shared__ float4 xs4[];
+    const int L4 = L >> 2, rs4 = L4 + 1;
+    const int64_t m0 = (int64_t)blockIdx.x * 256;
+    const int rows = M - m0 < 256 ? (int)(M - m0) : 256;
+    const float4 *Xt = reinterpret_cast<const float4 *>(X + m0 * L);
+    const int total4 = rows * L4;
+    for (int i0 = threadIdx.x; i0 < total4; i0 += 8 * 256) {   // eight loads in flight per thread
+        float4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + 256 * u;
+            v[u] = i < total4 ? __ldg(Xt + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + 256 * u, r = i / L4;
+            if (i < total4) xs4[r * rs4 + (i - r * L4)] = v[u];
+        }
+    }
+    __syncthreads();
+    const int64_t m = m0 + threadIdx.x;
+    if (m >= M) return;
+    float x[LK];
+    bool bad = false;
+    const float4 *xr = xs4 + threadIdx.x * rs4;
+#pragma unroll
+    for (int q = 0; q < LK / 4; ++q) {
+        const float4 v = q < L4 ? xr[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        x[4 * q] = v.x;
+        x[4 * q + 1] = v.y;
+        x[4 * q + 2] = v.z;
+        x[4 * q + 3] = v.w;
+        bad = bad || !isfinite(v.x) || !isfinite(v.y) || !isfinite(v.z) || !isfinite(v.w);
+    }
+    if (bad) flag_error(st, ERR_NONFINITE);
+    const float4 *C4 = reinterpret_cast<const float4 *>(C);
+    float best = INFINITY;
+    int bi = 0;
+    for (int n = 0; n < N; n += 4) {   // four codevectors' sums at a time (the last ones repeated)
+        const float4 *cp[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cp[k] = C4 + (size_t)(n + k < N ? n + k : n) * L4;
+        float dk[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int q = 0; q < LK / 4; ++q) {
+            if (q < L4) {
+                float4 c[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) c[k] = __ldg(cp[k] + q);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float d = __fsub_rn(x[4 * q], c[k].x);
+                    dk[k] = fmaf(d, d, dk[k]);
+                    d = __fsub_rn(x[4 * q + 1], c[k].y);
+                    dk[k] = fmaf(d, d, dk[k]);
+                    d = __fsub_rn(x[4 * q + 2], c[k].z);
+                    dk[k] = fmaf(d, d, dk[k]);
+                    d = __fsub_rn(x[4 * q + 3], c[k].w);
+                    dk[k] = fmaf(d, d, dk[k]);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)   // in index order: the lowest index wins a tie
+            if (n + k < N && dk[k] < best) {
+                best = dk[k];
+                bi = n + k;
+            }
+    }
+    assign[m] = bi;
+    e[m] = best;
 }
 
 __global__ void __launch_bounds__(ASSIGN_THREADS, 2)
@@ -113,7 +214,7 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 2)
                  int32_t *__restrict__ assign, float *__restrict__ e, int32_t *__restrict__ flags,
                  int64_t m_lo, int expire)
 {
-    if (st->finished) return;
+    if (st->finished || cur_n(n_dev, n_host) <= st->direct_max) return;   // k_assign_direct's stages
     extern __shared__ __align__(128) float smem[];
     __shared__ AssignSmem sh;
     if (threadIdx.x == 0) {
@@ -512,6 +613,30 @@ void launch_begin(const float *C, int N, int L, float *mu, bool round_mu, DevSta
 void launch_codebook_mean(const float *C, int N, int L, float *mu, cudaStream_t s)
 {
     LBG_COUNTED k_codebook_mean<<<L, 256, 0, s>>>(C, N, L, mu);
+}
+
+// k_assign_direct serves rows of L % 4 == 0, L <= 64 with X and C 16-byte aligned.
+bool direct_supported(int L, const void *X, const void *C)
+{
+    return (L & 3) == 0 && L <= 64 && ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(C)) & 15u) == 0;
+}
+
+void launch_assign_direct(const float *X, int64_t M, int L, const float *C, const int32_t *n_dev, int n_host,
+                          DevState *st, int32_t *assign, float *e, cudaStream_t s)
+{
+    const int64_t grid = (M + 255) / 256;
+    if (grid <= 0) return;
+    const size_t smem = (size_t)256 * (L / 4 + 1) * sizeof(float4);
+#define LBG_DIRECT(LK)                                                                                      \
+    cudaFuncSetAttribute(k_assign_direct<LK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+    LBG_COUNTED k_assign_direct<LK><<<(unsigned)grid, 256, smem, s>>>(X, M, L, C, n_dev, n_host, st, assign, e)
+    switch (round_up(L, 16)) {
+    case 16: LBG_DIRECT(16); break;
+    case 32: LBG_DIRECT(32); break;
+    case 48: LBG_DIRECT(48); break;
+    default: LBG_DIRECT(64); break;
+    }
+#undef LBG_DIRECT
 }
 
 void launch_prep(const float *C, int N_alloc, const int32_t *n_dev, int n_host, int L, int Lp,

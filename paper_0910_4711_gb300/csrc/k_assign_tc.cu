@@ -496,6 +496,7 @@ __global__ void __launch_bounds__(256)
 {
     if (st->finished) return;
     const int N = cur_n(n_dev, n_host);
+    if (N <= st->direct_max) return;   // k_assign_direct's stages need no prepared codebook
     const int n0 = blockIdx.x * PT_N;
     if (n0 >= tc_prep_rows(N)) return;
     const int NPk = round_up(N, BN);      // k'_n and CT entries (BN-padded)
@@ -1024,7 +1025,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 {
     if (st->finished) return;
     const int N = cur_n(n_dev, n_host);
-    if (N < n_lo || N >= n_hi) return;   // the other group size serves this codebook size
+    if (N < n_lo || N >= n_hi || N <= st->direct_max) return;   // another kernel serves this size
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ TcSmem sh;
 
@@ -1247,7 +1248,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 {
     if (st->finished) return;
     const int N = cur_n(n_dev, n_host);
-    if (N < n_lo || N >= n_hi) return;   // the other group size serves this codebook size
+    if (N < n_lo || N >= n_hi || N <= st->direct_max) return;   // another kernel serves this size
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ TcSmem sh;
 

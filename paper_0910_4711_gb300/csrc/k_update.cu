@@ -139,8 +139,11 @@ __global__ void __launch_bounds__(1024)
     if ((int)blockIdx.x * 32 < N) body_scan(table, CH, N, counts, blockIdx.x);
     if (!last_cta(st)) return;
     if (threadIdx.x == 0) st->done_ctr = 0u;
-    body_offsets(counts, N, off,
-                 PieceCells{N, S, L, qcell, cell_done, C_out != C_in && !skip_update(st, train), C_in, C_out});
+    body_offsets(counts, N, off, PieceCells{N, S, L, cell_done, C_out != C_in && !skip_update(st, train), C_in, C_out});
+    __syncthreads();   // off[] complete (this CTA wrote it)
+    // qcell[q] = the cell holding row position q S: the largest n with off[n] <= q S
+    const int64_t nq = ((int64_t)off[N] + S - 1) / S;
+    for (int64_t q = threadIdx.x; q < nq; q += blockDim.x) qcell[q] = first_cell(off, N, q * S);
 }
 
 template <int G>

@@ -433,6 +433,12 @@ void run_update(const Call &c, const Plan &p, const float *X, const int32_t *n_d
                      c.at<float>(p.pieces), done, C_out, st, train, c.s);
 }
 
+// Training stages of at most this many codevectors take k_assign_direct (every
+// row against every codevector, FP32 direct form): measured per pass on the
+// 8 x 8 image blocks, the tiled search with its certificate and re-scoring
+// costs more below these sizes.
+constexpr int DIRECT_MAX_TC = 8, DIRECT_MAX_F32 = 128;
+
 // 0 = FP32, 1 = tensor cores, <0 = error status
 int precision_mode(const lbg_opts &o, int L)
 {
@@ -1408,6 +1414,12 @@ lbg_status lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double del
     DevState *st = c.at<DevState>(p.state);
     DevState h;
     init_state(h, n_init > 0 ? n_init : 1);
+    // stages of at most direct_max cells: every row against every codevector
+    // (k_assign_direct) instead of the tiled search, its certificate and re-scoring
+    const int direct_max = direct_supported(L, wX == 0 ? c.at<float>(p.Xs) : X, c.at<float>(p.Ccur))
+                               ? (p.tc ? DIRECT_MAX_TC : DIRECT_MAX_F32)
+                               : 0;
+    h.direct_max = direct_max;
     CK(cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, c.s));
     const float *dX = X;
     if (wX == 0) {
@@ -1438,6 +1450,7 @@ lbg_status lbg_train(const float *X, int64_t M, int32_t L, int32_t N, double del
         if (tracing) launch_trace_begin(st, Ccur, N, L, o.trace_C, o.trace_cap, sst);
         run_prepare(cs, p, Ccur, n_dev, N, mu, st);
         run_assign(cs, p, dX, Ccur, n_dev, N, mu, st, dA);
+        if (direct_max > 0) launch_assign_direct(dX, M, L, Ccur, n_dev, N, st, dA, cs.at<float>(p.e), sst);
         run_exact(cs, p, dX, n_dev, N, st, dA);
         launch_hist(dA, cs.at<float>(p.e), M, p.R, p.CH, n_dev, N, true, cs.at<int32_t>(p.table),
                     cs.at<double>(p.dpart), st, true, sst);

@@ -54,7 +54,7 @@ struct DevState {
     double D_prev;        // distortion of the previous pass of the stage
     uint64_t t_pass0;     // %globaltimer at the start of the traced pass (lbg_train trace)
     int32_t trace_on;     // 1 while a traced pass of lbg_train is in progress
-    int32_t pad0;
+    int32_t direct_max;   // stages of at most this many cells take k_assign_direct (lbg_train; 0: none)
 };
 
 // Device pass record (mirrors lbg_pass_record).
@@ -265,6 +265,12 @@ bool tc_supported(int L);
 void launch_round_mu(float *mu, int L, cudaStream_t s);
 void launch_prep_tc(const float *C, int N_alloc, const int32_t *n_dev, int n_host, int L,
                     const float *mu, void *Bp, float *kn, float *CT, DevState *st, cudaStream_t s);
+// Every row against all N codevectors in the FP32 direct form (k_assign_direct,
+// k_assign.cu): the kernel runs only when N <= st->direct_max, the search and
+// preparation kernels only when N > st->direct_max.
+bool direct_supported(int L, const void *X, const void *C);
+void launch_assign_direct(const float *X, int64_t M, int L, const float *C, const int32_t *n_dev, int n_host,
+                          DevState *st, int32_t *assign, float *e, cudaStream_t s);
 void launch_assign_tc(const float *X, int64_t M, int L, const void *Bp, const float *kn,
                       const int32_t *n_dev, int n_host, const float *mu, const float *C,
                       DevState *st, int32_t *assign, float *e, int32_t *flags, cudaStream_t s, int64_t m_lo = 0,
