@@ -105,6 +105,85 @@ __device__ __forceinline__ void exact_prefix(const BatchSet *__restrict__ sets, 
     __syncthreads();
 }
 
+// Rows [r0, r0 + 64) of problem q at a small stage (N codevectors) in the FP32
+// direct form, sum over l in index order of fl(x_l - c_l)^2, lowest index on
+// ties: the values and the choice the tiled search and its exact re-scoring
+// give (as k_assign_direct in the per-step path), without a certificate or
+// flagged rows.  The half's 128 threads: two per row, each over one contiguous
+// half of the codevectors; the lower half wins a tie.  L <= 64, L % 4 == 0,
+// rows 16-byte aligned.
+__device__ __forceinline__ void direct_tile(const BatchSet &q, int L, int N, int64_t r0, float *hsm, int t,
+                                            int bar_id)
+{
+    const int r = t & 63, part = t >> 6;
+    const int64_t m = r0 + r;
+    const int h = (N + 1) >> 1;
+    const int n_lo = part ? h : 0, n_hi = part ? N : h;
+    const int L4 = L >> 2;
+    float best = INFINITY;
+    int bi = n_lo;
+    bool bad = false;
+    if (m < q.M) {
+        float x[64];
+        const float4 *xr = reinterpret_cast<const float4 *>(q.X + m * L);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const float4 v = k < L4 ? __ldg(xr + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+            x[4 * k] = v.x;
+            x[4 * k + 1] = v.y;
+            x[4 * k + 2] = v.z;
+            x[4 * k + 3] = v.w;
+            bad = bad || !isfinite(v.x) || !isfinite(v.y) || !isfinite(v.z) || !isfinite(v.w);
+        }
+        const float4 *C4 = reinterpret_cast<const float4 *>(q.C);
+        for (int n = n_lo; n < n_hi; n += 4) {   // four sums at a time (the last ones repeated)
+            const float4 *cr[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) cr[j] = C4 + (size_t)(n + j < n_hi ? n + j : n) * L4;
+            float d2[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                if (k < L4) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float4 c = __ldg(cr[j] + k);
+                        float d = __fsub_rn(x[4 * k], c.x);
+                        d2[j] = fmaf(d, d, d2[j]);
+                        d = __fsub_rn(x[4 * k + 1], c.y);
+                        d2[j] = fmaf(d, d, d2[j]);
+                        d = __fsub_rn(x[4 * k + 2], c.z);
+                        d2[j] = fmaf(d, d, d2[j]);
+                        d = __fsub_rn(x[4 * k + 3], c.w);
+                        d2[j] = fmaf(d, d, d2[j]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)   // in index order: the lowest index wins a tie
+                if (n + j < n_hi && d2[j] < best) {
+                    best = d2[j];
+                    bi = n + j;
+                }
+        }
+    }
+    float *sd = hsm;
+    int *si = reinterpret_cast<int *>(hsm + 64);
+    if (part == 1) {
+        sd[r] = best;
+        si[r] = bi;
+    }
+    tile_sync(bar_id, 2 * BP_TILE);
+    if (part == 0 && m < q.M) {
+        if (bad) flag_error(q.st, ERR_NONFINITE);
+        if (sd[r] < best) {
+            best = sd[r];
+            bi = si[r];
+        }
+        q.assign[m] = bi;
+        q.e[m] = best;
+    }
+}
+
 // Grid-wide barrier: arrivals counted in bar[0]; the last arrival resets the
 // count and bumps the generation bar[1], for which the others wait (bounded).
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, const BatchSet *sets, int S)
@@ -181,7 +260,7 @@ __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
     for (int vb = blockIdx.x; vb < a.tot_prep; vb += grid) {
         const int s = find_set(a.pre_prep, S, vb);
         const BatchSet &q = sets[s];
-        if (T.run[s] & 1)
+        if ((T.run[s] & 1) && T.ncur[s] > a.direct_max)   // the direct tiles read C as it is
             body_prep(q.C, T.ncur[s], a.L, a.Lp, q.mu, q.Cp, q.kn, q.CT, q.st, vb - a.pre_prep[s],
                       *reinterpret_cast<PrepSmem *>(dsm));
         __syncthreads();
@@ -204,7 +283,9 @@ __global__ void __launch_bounds__(BP_THREADS, 2) kb_pass(const BatchPass a)
             if (item >= a.ntiles) break;
             const int s = find_set64(a.pre_tiles, S, item);
             const BatchSet &q = sets[s];
-            if (T.run[s] & 1) {
+            if ((T.run[s] & 1) && T.ncur[s] <= a.direct_max) {
+                direct_tile(q, a.L, T.ncur[s], (item - a.pre_tiles[s]) * BP_TILE, hsm, tid & 127, 1 + half);
+            } else if (T.run[s] & 1) {
                 const int64_t tile = item - a.pre_tiles[s];
                 if (!assign_f32_tile_t<BP_TILE>(q.X, q.M, a.L, a.Lp, q.Cp, q.kn, T.ncur[s], q.mu, q.C, q.st,
                                                q.assign, q.e, q.flags, tile * BP_TILE, hsm, ash[half], u0, u1,

@@ -1250,6 +1250,9 @@ lbg_status lbg_train_batched(int32_t S, const float *X, const int64_t *row_off, 
     bp.max_passes = o.max_passes;
     bp.mult = o.split_multiplicative != 0;
     bp.vec = vec && (reinterpret_cast<uintptr_t>(dC) & 15u) == 0;
+    // small stages in the one-launch pass: every row against every codevector (the per-phase
+    // launches keep the tiled search; both give the same bits)
+    bp.direct_max = bp.vec && (L & 3) == 0 && L <= 64 ? DIRECT_MAX_F32 : 0;
     bp.phase_smem = pass_phase_smem;
 
     // ---- tile of the batched nearest-codevector launch (lbg_opts.autotune)

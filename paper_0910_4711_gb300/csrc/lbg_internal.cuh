@@ -350,6 +350,8 @@ struct BatchPass {
     unsigned *bar;              // [0] arrivals, [1] generation, [2] abort (zero before the first pass)
     double theta, delta;
     int max_passes, mult, vec;
+    int direct_max;             // problems at stages of at most this many cells: every row against
+                                // every codevector (direct_tile); 0: none
     size_t phase_smem;          // dynamic shared memory of the phases; the state tables follow
 };
 // Resident CTAs per SM the persistent pass can have (0: it does not fit) and its
