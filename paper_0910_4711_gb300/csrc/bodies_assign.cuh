@@ -371,21 +371,46 @@ __device__ __forceinline__ bool assign_f32_tile_t(
     float dwin = 0.f;
     if (certified) {
         // the pair's exact FP32 direct-form distances decide between its members
+        // (each sum in index order; both in one loop, float4 loads when the rows allow)
         const float *xr = X + m * L;
         const float *ca = C + (size_t)i1 * L;
-        float da = 0.f;
-        for (int l = 0; l < L; ++l) {
-            const float d = xr[l] - ca[l];
-            da = fmaf(d, d, da);
+        const float *cb = C + (size_t)(pair ? ip : i1) * L;
+        float da = 0.f, db = 0.f;
+        if ((L & 3) == 0 && ((reinterpret_cast<uintptr_t>(xr) | reinterpret_cast<uintptr_t>(ca) |
+                              reinterpret_cast<uintptr_t>(cb)) & 15u) == 0) {
+#pragma unroll 4
+            for (int q = 0; q < (L >> 2); ++q) {
+                const float4 x4 = __ldg(reinterpret_cast<const float4 *>(xr) + q);
+                const float4 a4 = __ldg(reinterpret_cast<const float4 *>(ca) + q);
+                const float4 b4 = __ldg(reinterpret_cast<const float4 *>(cb) + q);
+                float d = __fsub_rn(x4.x, a4.x);
+                da = fmaf(d, d, da);
+                d = __fsub_rn(x4.y, a4.y);
+                da = fmaf(d, d, da);
+                d = __fsub_rn(x4.z, a4.z);
+                da = fmaf(d, d, da);
+                d = __fsub_rn(x4.w, a4.w);
+                da = fmaf(d, d, da);
+                d = __fsub_rn(x4.x, b4.x);
+                db = fmaf(d, d, db);
+                d = __fsub_rn(x4.y, b4.y);
+                db = fmaf(d, d, db);
+                d = __fsub_rn(x4.z, b4.z);
+                db = fmaf(d, d, db);
+                d = __fsub_rn(x4.w, b4.w);
+                db = fmaf(d, d, db);
+            }
+        } else {
+            for (int l = 0; l < L; ++l) {
+                const float x = xr[l];
+                float d = __fsub_rn(x, ca[l]);
+                da = fmaf(d, d, da);
+                d = __fsub_rn(x, cb[l]);
+                db = fmaf(d, d, db);
+            }
         }
         dwin = da;
         if (pair) {
-            const float *cb = C + (size_t)ip * L;
-            float db = 0.f;
-            for (int l = 0; l < L; ++l) {
-                const float d = xr[l] - cb[l];
-                db = fmaf(d, d, db);
-            }
             // |fl(d2) - d2| <= (L + 2) u d2 for either sum (kept as (L + 4) u)
             const float tol = (float)(L + 4) * U32 * (da + db) * SLOP;
             if (db < da - tol) {
