@@ -437,7 +437,7 @@ void run_update(const Call &c, const Plan &p, const float *X, const int32_t *n_d
 // row against every codevector, FP32 direct form): measured per pass on the
 // 8 x 8 image blocks, the tiled search with its certificate and re-scoring
 // costs more below these sizes.
-constexpr int DIRECT_MAX_TC = 8, DIRECT_MAX_F32 = 128;
+constexpr int DIRECT_MAX_TC = 8, DIRECT_MAX_F32 = 64;
 
 // 0 = FP32, 1 = tensor cores, <0 = error status
 int precision_mode(const lbg_opts &o, int L)

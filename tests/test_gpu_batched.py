@@ -158,12 +158,12 @@ def test_persistent_pass_other_dimensions(lbg, L, real):
 
 
 def test_small_codebook_stages_score_every_codevector(lbg):
-    """Training stages of at most 128 (FP32) or 8 (BF16) codevectors score every row against
+    """Training stages of at most 64 (FP32) or 8 (BF16) codevectors score every row against
     every codevector in the FP32 direct form: such passes re-score no row, and the FP32 run
     still equals the batched pass (which keeps the tiled search) bit for bit."""
     parts, Xc, row_off, Ns = ragged_sets(70, [60000], [256])
     X = torch.from_numpy(parts[0]).cuda()
-    for precision, direct in (("fp32", 128), ("bf16", 8)):
+    for precision, direct in (("fp32", 64), ("bf16", 8)):
         r = lbg.lbg_train(X, 256, 0.01, 1e-3, precision=precision)
         small = [rec for rec in r.records if rec["stage_n"] <= direct]
         assert small and all(rec["n_exact"] == 0 for rec in small), precision
